@@ -1,0 +1,340 @@
+"""Camera system models (Sec. II-C..F and Sec. III) - oracle, test infrastructure.
+
+Conventions (shared with the descriptors in the inputs module, not with any
+CUDA code):
+  * the camera's optical axis passes through the volume centre, the main lens
+    is d_obj in front of it; slice n sits at object distance
+    d_n = d_obj + (n - (nz-1)/2) dz and has its s and t axes along the
+    volume's x and y axes (Sec. III: camera and object axes aligned);
+  * pixel / voxel / lenslet centres are (index - (count-1)/2) * pitch;
+  * the angular plane is the main lens (Sec. II-F); the lens is divided into
+    ks x kt cells of width 2 r / ks tiling [-r, r]^2, and cells whose centre is
+    strictly inside the aperture disc are kept (reading of Sec. II-B for a
+    round lens), ordered with the s cell index fastest;
+  * images are [nt][ns] with s fastest (Sec. IV, column-major views).
+
+Scale factors.  The paper's detector model writes sqrt(V^d) sum_k f^d_k and the
+plenoptic model sqrt(V^mu) B^{d mu}; with the un-normalised indicator bases of
+eq. lf,disc the detector integral of basis element (k, i) is exactly
+B^{ds}_k applied to the source coefficients, so (reading of Sec. II-E/F):
+      single lens :  y = sum_k sum_n B^{dn}_k w^n,            w^n = dz x^n
+      plenoptic   :  y = sum_k sum_mu B^{d mu}_k M_mu (1/V^a) sum_n B^{an}_k w^n
+with V^a = (Da_s D0_s / D_mum) (Da_t D0_t / D_mum) the array-plane basis
+volume.  The slice collapse w^n = dz x^n follows Sec. III (small angle, no
+obliquity factor).  The mask M is binary: an array pixel belongs to lenslet mu
+when its centre lies strictly inside mu's disc, and B^{d mu} acts only on mu's
+own pixels.
+"""
+import numpy as np
+
+from . import optics, transport
+
+
+# ---------------------------------------------------------------------------
+# grids and cells
+# ---------------------------------------------------------------------------
+
+def centers(n, pitch):
+    return (np.arange(n, dtype=np.float64) - (n - 1) / 2.0) * pitch
+
+
+def lens_cells(cam):
+    """Angular cells on the main lens: list of (s_k, t_k, D0_s, D0_t)."""
+    r = cam.r_main
+    d0s = 2.0 * r / cam.ks
+    d0t = 2.0 * r / cam.kt
+    cells = []
+    for kt in range(cam.kt):
+        for ks in range(cam.ks):
+            sk = -r + (ks + 0.5) * d0s
+            tk = -r + (kt + 0.5) * d0t
+            if sk * sk + tk * tk < r * r:
+                cells.append((sk, tk, d0s, d0t))
+    return cells
+
+
+def slice_distances(vol, cam):
+    return cam.d_obj + centers(vol.nz, vol.dz)
+
+
+def _entry(cam):
+    return transport.dirac_entry if cam.basis == 1 else transport.pillbox_entry
+
+
+def matrix_1d(cam, Xpq, X0q, tgt, dp, s_k, d0, src, dsrc):
+    """Dense 1-D transport matrix [len(tgt), len(src)] for one angular cell."""
+    tgt = np.asarray(tgt, dtype=np.float64)[:, None]
+    src = np.asarray(src, dtype=np.float64)[None, :]
+    return _entry(cam)(optics.s_row(Xpq), optics.s_row(X0q), tgt, dp, s_k, d0,
+                       src - dsrc / 2.0, src + dsrc / 2.0)
+
+
+def slice_maps(cam, d, d_img):
+    """Maps from a slice at object distance d: to the angular plane (the
+    main lens, T_d) and through the main lens to an image plane d_img behind
+    it (T_{d_img} o R_f o T_d)."""
+    X0q = optics.propagate(d)
+    Xpq = optics.compose(optics.propagate(d_img), optics.refract(cam.f_main),
+                         optics.propagate(d))
+    return Xpq, X0q
+
+
+def slice_operators(vol, cam, n, cell, d_img, tgt_ns, tgt_nt, tgt_ps, tgt_pt):
+    """(Bs, Bt) of the transport from slice n to an image plane (eq. xport,sep)."""
+    sk, tk, d0s, d0t = cell
+    d = slice_distances(vol, cam)[n]
+    Xpq, X0q = slice_maps(cam, d, d_img)
+    Bs = matrix_1d(cam, Xpq, X0q, centers(tgt_ns, tgt_ps), tgt_ps, sk, d0s,
+                   centers(vol.nx, vol.dx), vol.dx)
+    Bt = matrix_1d(cam, Xpq, X0q, centers(tgt_nt, tgt_pt), tgt_pt, tk, d0t,
+                   centers(vol.ny, vol.dy), vol.dy)
+    return Bs, Bt
+
+
+# ---------------------------------------------------------------------------
+# single-lens camera (Sec. II-F1, Sec. III)
+# ---------------------------------------------------------------------------
+
+def single_forward(vol, cam, x):
+    """y = sum_k sum_n B^{dn}_k (dz x^n), image [nt][ns]."""
+    X = np.asarray(x, dtype=np.float64).reshape(vol.shape)
+    y = np.zeros((cam.det_nt, cam.det_ns))
+    for cell in lens_cells(cam):
+        for n in range(vol.nz):
+            Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_det,
+                                     cam.det_ns, cam.det_nt, cam.det_ps, cam.det_pt)
+            y += vol.dz * (Bt @ X[n] @ Bs.T)
+    return y
+
+
+def single_adjoint(vol, cam, y):
+    """x = A^T y = sum_k sum_n dz (B^{dn}_k)^T y  (Sec. IV-A: B^{pq} = (B^{qp})^T)."""
+    Y = np.asarray(y, dtype=np.float64).reshape(cam.det_nt, cam.det_ns)
+    x = np.zeros(vol.shape)
+    for cell in lens_cells(cam):
+        for n in range(vol.nz):
+            Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_det,
+                                     cam.det_ns, cam.det_nt, cam.det_ps, cam.det_pt)
+            x[n] += vol.dz * (Bt.T @ Y @ Bs)
+    return x
+
+
+def single_matrix(vol, cam):
+    """Explicit A (M x N) for tiny cameras: column blocks dz kron(Bt, Bs)."""
+    M, N = cam.det_ns * cam.det_nt, vol.n
+    A = np.zeros((M, N))
+    blk = vol.nx * vol.ny
+    for cell in lens_cells(cam):
+        for n in range(vol.nz):
+            Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_det,
+                                     cam.det_ns, cam.det_nt, cam.det_ps, cam.det_pt)
+            A[:, n * blk:(n + 1) * blk] += vol.dz * np.kron(Bt, Bs)
+    return A
+
+
+# ---------------------------------------------------------------------------
+# plenoptic camera (Sec. II-F2, eq. plenoptic,factor)
+# ---------------------------------------------------------------------------
+
+def array_basis_volume(cam, cell):
+    """V^a of the array-plane basis; X^{0a}: array plane back to the lens."""
+    _, _, d0s, d0t = cell
+    su = optics.s_row(optics.propagate(-cam.d_lens_mla))[1]
+    return (transport.basis_volume(su, cam.arr_ps, d0s) *
+            transport.basis_volume(su, cam.arr_pt, d0t))
+
+
+def lenslet_centers(cam):
+    return centers(cam.mla_ns, cam.mla_pitch), centers(cam.mla_nt, cam.mla_pitch)
+
+
+def lenslet_owner(cam):
+    """owner[jt, js] = mt * mla_ns + ms of the lenslet whose disc strictly
+    contains the array-pixel centre, -1 where the mask M blocks (Sec. II-D)."""
+    s = centers(cam.arr_ns, cam.arr_ps)
+    t = centers(cam.arr_nt, cam.arr_pt)
+    cs, ct = lenslet_centers(cam)
+    ms = np.rint(s / cam.mla_pitch + (cam.mla_ns - 1) / 2.0).astype(np.int64)
+    mt = np.rint(t / cam.mla_pitch + (cam.mla_nt - 1) / 2.0).astype(np.int64)
+    oks = (ms >= 0) & (ms < cam.mla_ns)
+    okt = (mt >= 0) & (mt < cam.mla_nt)
+    msc = np.clip(ms, 0, cam.mla_ns - 1)
+    mtc = np.clip(mt, 0, cam.mla_nt - 1)
+    ds = s - cs[msc]
+    dt = t - ct[mtc]
+    inside = (ds[None, :] ** 2 + dt[:, None] ** 2 < cam.mla_radius ** 2)
+    inside &= oks[None, :] & okt[:, None]
+    return np.where(inside, mtc[:, None] * cam.mla_ns + msc[None, :], -1)
+
+
+def lenslet_maps(cam, f_mu, c_mu):
+    """Array plane -> detector through lenslet mu (T_{D_mud} o R_{f_mu, c_mu})
+    and array plane -> main lens (propagation back by D_mum)."""
+    Xdq = optics.compose(optics.propagate(cam.d_mla_det), optics.refract(f_mu, c_mu))
+    X0q = optics.propagate(-cam.d_lens_mla)
+    return Xdq, X0q
+
+
+class _StageTwo:
+    """Per-lenslet 1-D matrices of the array -> detector transport, memoised by
+    (axis, lenslet column/row, focal length, cell)."""
+
+    def __init__(self, cam):
+        self.cam = cam
+        self.owner = lenslet_owner(cam)
+        self.cs, self.ct = lenslet_centers(cam)
+        self.arr_s = centers(cam.arr_ns, cam.arr_ps)
+        self.arr_t = centers(cam.arr_nt, cam.arr_pt)
+        self.det_s = centers(cam.det_ns, cam.det_ps)
+        self.det_t = centers(cam.det_nt, cam.det_pt)
+        self.cache = {}
+        # array columns / rows holding each lenslet's pixels
+        self.cols = {}
+        self.rows = {}
+        for ms in range(cam.mla_ns):
+            sel = np.nonzero(np.any((self.owner >= 0) & (self.owner % cam.mla_ns == ms), axis=0))[0]
+            self.cols[ms] = sel
+        for mt in range(cam.mla_nt):
+            sel = np.nonzero(np.any((self.owner >= 0) & (self.owner // cam.mla_ns == mt), axis=1))[0]
+            self.rows[mt] = sel
+
+    def mat(self, axis, m, f_mu, cell_idx, cell):
+        key = (axis, m, float(f_mu), cell_idx)
+        if key not in self.cache:
+            cam = self.cam
+            sk, tk, d0s, d0t = cell
+            if axis == 0:
+                Xdq, X0q = lenslet_maps(cam, f_mu, self.cs[m])
+                B = matrix_1d(cam, Xdq, X0q, self.det_s, cam.det_ps, sk, d0s,
+                              self.arr_s[self.cols[m]], cam.arr_ps)
+            else:
+                Xdq, X0q = lenslet_maps(cam, f_mu, self.ct[m])
+                B = matrix_1d(cam, Xdq, X0q, self.det_t, cam.det_pt, tk, d0t,
+                              self.arr_t[self.rows[m]], cam.arr_pt)
+            nz = np.nonzero(np.any(B != 0.0, axis=1))[0]
+            self.cache[key] = (nz, B[nz])
+        return self.cache[key]
+
+
+def plenoptic_array_field(vol, cam, x, cell):
+    """Masked array-plane coefficients M (1/V^a) sum_n B^{an}_k (dz x^n)."""
+    X = np.asarray(x, dtype=np.float64).reshape(vol.shape)
+    Fa = np.zeros((cam.arr_nt, cam.arr_ns))
+    for n in range(vol.nz):
+        Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_mla,
+                                 cam.arr_ns, cam.arr_nt, cam.arr_ps, cam.arr_pt)
+        Fa += vol.dz * (Bt @ X[n] @ Bs.T)
+    Fa /= array_basis_volume(cam, cell)
+    return np.where(lenslet_owner(cam) >= 0, Fa, 0.0)
+
+
+def plenoptic_forward(vol, cam, x, return_array=False):
+    """y = sum_k sum_mu B^{d mu}_k M_mu (1/V^a) sum_n B^{an}_k w^n."""
+    st = _StageTwo(cam)
+    y = np.zeros((cam.det_nt, cam.det_ns))
+    fields = []
+    for ci, cell in enumerate(lens_cells(cam)):
+        Fa = plenoptic_array_field(vol, cam, x, cell)
+        fields.append(Fa)
+        for mt in range(cam.mla_nt):
+            for ms in range(cam.mla_ns):
+                mu = mt * cam.mla_ns + ms
+                f_mu = cam.mla_focal[mt, ms]
+                rs, Bs = st.mat(0, ms, f_mu, ci, cell)
+                rt, Bt = st.mat(1, mt, f_mu, ci, cell)
+                if len(rs) == 0 or len(rt) == 0:
+                    continue
+                rows, cols = st.rows[mt], st.cols[ms]
+                sub = Fa[np.ix_(rows, cols)] * (st.owner[np.ix_(rows, cols)] == mu)
+                y[np.ix_(rt, rs)] += Bt @ sub @ Bs.T
+    if return_array:
+        return y, np.stack(fields)
+    return y
+
+
+def plenoptic_adjoint(vol, cam, y, return_array=False):
+    """x = sum_k sum_n dz (B^{an}_k)^T (1/V^a) M sum_mu (B^{d mu}_k)^T y."""
+    st = _StageTwo(cam)
+    Y = np.asarray(y, dtype=np.float64).reshape(cam.det_nt, cam.det_ns)
+    x = np.zeros(vol.shape)
+    fields = []
+    for ci, cell in enumerate(lens_cells(cam)):
+        Ga = np.zeros((cam.arr_nt, cam.arr_ns))
+        for mt in range(cam.mla_nt):
+            for ms in range(cam.mla_ns):
+                mu = mt * cam.mla_ns + ms
+                f_mu = cam.mla_focal[mt, ms]
+                rs, Bs = st.mat(0, ms, f_mu, ci, cell)
+                rt, Bt = st.mat(1, mt, f_mu, ci, cell)
+                if len(rs) == 0 or len(rt) == 0:
+                    continue
+                rows, cols = st.rows[mt], st.cols[ms]
+                g = Bt.T @ Y[np.ix_(rt, rs)] @ Bs
+                own = st.owner[np.ix_(rows, cols)] == mu
+                Ga[np.ix_(rows, cols)] += np.where(own, g, 0.0)
+        Ga /= array_basis_volume(cam, cell)
+        fields.append(Ga)
+        for n in range(vol.nz):
+            Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_mla,
+                                     cam.arr_ns, cam.arr_nt, cam.arr_ps, cam.arr_pt)
+            x[n] += vol.dz * (Bt.T @ Ga @ Bs)
+    if return_array:
+        return x, np.stack(fields)
+    return x
+
+
+def plenoptic_matrix(vol, cam):
+    """Explicit A for tiny plenoptic cameras, built term by term from the
+    factorised model (eq. plenoptic,factor)."""
+    owner = lenslet_owner(cam)
+    cs, ct = lenslet_centers(cam)
+    arr_s = centers(cam.arr_ns, cam.arr_ps)
+    arr_t = centers(cam.arr_nt, cam.arr_pt)
+    det_s = centers(cam.det_ns, cam.det_ps)
+    det_t = centers(cam.det_nt, cam.det_pt)
+    Na = cam.arr_ns * cam.arr_nt
+    blk = vol.nx * vol.ny
+    A = np.zeros((cam.det_ns * cam.det_nt, vol.n))
+    for cell in lens_cells(cam):
+        sk, tk, d0s, d0t = cell
+        S1 = np.zeros((Na, vol.n))
+        for n in range(vol.nz):
+            Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_mla,
+                                     cam.arr_ns, cam.arr_nt, cam.arr_ps, cam.arr_pt)
+            S1[:, n * blk:(n + 1) * blk] = vol.dz * np.kron(Bt, Bs)
+        S2 = np.zeros((cam.det_ns * cam.det_nt, Na))
+        for mt in range(cam.mla_nt):
+            for ms in range(cam.mla_ns):
+                mu = mt * cam.mla_ns + ms
+                f_mu = cam.mla_focal[mt, ms]
+                Xs, X0 = lenslet_maps(cam, f_mu, cs[ms])
+                Xt, _ = lenslet_maps(cam, f_mu, ct[mt])
+                Bs = matrix_1d(cam, Xs, X0, det_s, cam.det_ps, sk, d0s, arr_s, cam.arr_ps)
+                Bt = matrix_1d(cam, Xt, X0, det_t, cam.det_pt, tk, d0t, arr_t, cam.arr_pt)
+                own = (owner.reshape(-1) == mu).astype(np.float64)
+                S2 += np.kron(Bt, Bs) * own[None, :]
+        mask = (owner.reshape(-1) >= 0).astype(np.float64)
+        A += S2 @ (mask[:, None] * S1) / array_basis_volume(cam, cell)
+    return A
+
+
+# ---------------------------------------------------------------------------
+# dispatch
+# ---------------------------------------------------------------------------
+
+def forward(vol, cam, x):
+    if cam.kind == 1:
+        return plenoptic_forward(vol, cam, x)
+    return single_forward(vol, cam, x)
+
+
+def adjoint(vol, cam, y):
+    if cam.kind == 1:
+        return plenoptic_adjoint(vol, cam, y)
+    return single_adjoint(vol, cam, y)
+
+
+def system_matrix(vol, cam):
+    if cam.kind == 1:
+        return plenoptic_matrix(vol, cam)
+    return single_matrix(vol, cam)
