@@ -1,0 +1,143 @@
+/*
+ * lt.h - C ABI of the B300 light-transport camera library.
+ *
+ * The library evaluates the matrix-free camera model of McGaffin, Chen,
+ * Fessler and Sick ("A practical light transport system model for
+ * chemiluminescence distribution reconstruction"): the projector y = A x of
+ * single-lens and plenoptic cameras (Sec. II-C..F, Sec. III), its exact
+ * adjoint x = A^T y (Sec. IV-A), and the reconstruction of Table V (Sec. V).
+ *
+ * Conventions (all calls):
+ *   - Lengths in millimetres, angles in radians.
+ *   - A volume is float32 [nz][ny][nx] (x fastest), voxel (ix, iy, iz)
+ *     centred at ((ix-(nx-1)/2) dx, (iy-(ny-1)/2) dy, (iz-(nz-1)/2) dz).
+ *   - A camera image is float32 [det_nt][det_ns] (s fastest, Sec. IV).
+ *     y of a plan is the concatenation over cameras: camera c occupies
+ *     [det_offsets[c], det_offsets[c+1]) of each frame's row.
+ *   - With F frames, x is [F][n_vox] and y is [F][det_offsets[n_cams]].
+ *   - Data pointers passed to lt_forward / lt_adjoint / lt_recon_* are DEVICE
+ *     pointers owned by the caller (borrowed for the call); the library keeps
+ *     no reference after the call returns.  Host descriptor arrays are copied.
+ *   - Calls are asynchronous on the given cudaStream_t (NULL = legacy default
+ *     stream).  Validation errors are returned synchronously; CUDA launch
+ *     errors are returned as LT_ECUDA.  Nothing aborts, exits or traps; no C++
+ *     exception crosses the ABI.  lt_last_error() describes the last failure
+ *     of the calling thread.
+ *   - A plan owns device tables and a scratch buffer (the plenoptic array
+ *     plane); two calls on the same plan must not overlap in time on
+ *     different streams.
+ */
+#ifndef LT_H
+#define LT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LT_API __attribute__((visibility("default")))
+#else
+#define LT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LT_OK = 0,
+  LT_EINVAL = 1,        /* invalid descriptor or argument                    */
+  LT_ENOMEM = 2,        /* device or host allocation failed                  */
+  LT_ECUDA = 3,         /* CUDA runtime error (launch, copy)                  */
+  LT_EUNSUPPORTED = 4,  /* valid but not supported by this build             */
+  LT_ETIMEOUT = 5       /* a bounded device wait gave up                      */
+} lt_status;
+
+enum { LT_BASIS_PILLBOX = 0, LT_BASIS_DIRAC = 1 };    /* angular basis a(.), Sec. II-B */
+enum { LT_CAM_SINGLE = 0, LT_CAM_PLENOPTIC = 1 };     /* Sec. II-F                     */
+
+/* Pillbox voxel grid (Sec. III, eq. voxel), centred on the object origin. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+} lt_volume_desc;
+
+/* One camera (Sec. II-F).  The optical axis passes through the volume centre;
+ * the main lens is d_obj in front of it.  The angular plane is the main lens,
+ * divided into ks x kt cells tiling [-r_main, r_main]^2 (cells whose centre is
+ * inside the aperture disc are kept).  yaw rotates the camera about the
+ * volume's y axis (Sec. III-A). */
+typedef struct {
+  int32_t kind;            /* LT_CAM_SINGLE or LT_CAM_PLENOPTIC                  */
+  int32_t basis;           /* LT_BASIS_PILLBOX or LT_BASIS_DIRAC                 */
+  double f_main, r_main;   /* main-lens focal length and aperture radius         */
+  double d_obj;            /* main lens -> volume centre                         */
+  double yaw;              /* radians                                            */
+  int32_t det_ns, det_nt;  /* detector pixels                                    */
+  double det_ps, det_pt;   /* detector pitch                                     */
+  double d_lens_det;       /* single lens: main lens -> detector (D)             */
+  int32_t ks, kt;          /* angular cells per axis                             */
+  /* plenoptic only (Sec. II-F2) */
+  double d_lens_mla;       /* D_mu_m: main lens -> microlens array               */
+  double d_mla_det;        /* D_mu_d: microlens array -> detector                */
+  int32_t mla_ns, mla_nt;  /* square lenslet grid                                */
+  double mla_pitch;        /* lenslet centre spacing                             */
+  double mla_radius;       /* lenslet disc radius (<= mla_pitch / 2)             */
+  const double* mla_focal; /* host [mla_nt*mla_ns] focal lengths, copied         */
+  int32_t arr_ns, arr_nt;  /* array-plane (mask) grid, Sec. II-D                */
+  double arr_ps, arr_pt;
+} lt_camera_desc;
+
+typedef struct lt_plan lt_plan;
+
+/* Build a plan for n_cams cameras looking at one volume, for batches of
+ * n_frames volumes (Sec. III-A "System models": A maps R^N to R^M).  Computes
+ * every transport parameter (Tables II/III) in float64 on the host and
+ * uploads them.  Uses the current CUDA device.
+ * Errors: LT_EINVAL for non-positive sizes/pitches/focal lengths, a slice at
+ * or behind the lens, a lenslet radius above half the pitch, footprints
+ * wider than the kernels' windows (LT_EUNSUPPORTED); LT_ENOMEM. */
+LT_API lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_desc* cams,
+                         int32_t n_cams, int32_t n_frames, lt_plan** out);
+
+/* Frees all device memory of the plan (synchronises the device first). */
+LT_API lt_status lt_plan_destroy(lt_plan* plan);
+
+/* n_vox = nx*ny*nz; det_offsets[0..n_cams] (host array of n_cams+1). */
+LT_API lt_status lt_plan_sizes(const lt_plan* plan, int64_t* n_vox, int64_t* det_offsets);
+
+/* Forward projection y = A x for every camera and frame (Sec. II-F, Sec. III,
+ * eq. plenoptic,factor).  x: device [F][n_vox]; y: device [F][M] (overwritten). */
+LT_API lt_status lt_forward(lt_plan* plan, const float* x, float* y, void* stream);
+
+/* Exact adjoint x = A^T y = sum_c A_c^T y_c (Sec. IV-A), computed as a gather
+ * per voxel (one writer per output, no atomics).  x is overwritten. */
+LT_API lt_status lt_adjoint(lt_plan* plan, const float* y, float* x, void* stream);
+
+/* Per-camera forward / adjoint.  y_cam: device [F][M_c] (the camera's own
+ * image).  lt_adjoint_camera writes x (accumulate = 0) or adds to it
+ * (accumulate = 1). */
+LT_API lt_status lt_forward_camera(lt_plan* plan, int32_t cam, const float* x, float* y_cam,
+                            void* stream);
+LT_API lt_status lt_adjoint_camera(lt_plan* plan, int32_t cam, const float* y_cam, float* x,
+                            int32_t accumulate, void* stream);
+
+/* Plenoptic stages, exposed for testing and composition (eq. plenoptic,factor):
+ *   stage 1:  fa[F][K][arr_nt][arr_ns] = M (1/V^a) sum_n B^{an}_k (dz x^n)
+ *   stage 2:  y[F][M_c] = sum_k sum_mu B^{d mu}_k fa_k
+ * and their adjoints (stage 2^T writes M sum_mu (B^{d mu}_k)^T y).
+ * n_cells() gives K of a camera (kept angular cells). */
+LT_API lt_status lt_camera_cells(const lt_plan* plan, int32_t cam, int32_t* n_cells);
+LT_API lt_status lt_plenoptic_stage1(lt_plan* plan, int32_t cam, const float* x, float* fa, void* stream);
+LT_API lt_status lt_plenoptic_stage1_adjoint(lt_plan* plan, int32_t cam, const float* fa, float* x,
+                                      int32_t accumulate, void* stream);
+LT_API lt_status lt_plenoptic_stage2(lt_plan* plan, int32_t cam, const float* fa, float* y_cam, void* stream);
+LT_API lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, const float* y_cam, float* fa,
+                                      void* stream);
+
+/* Description of the last error on the calling thread ("" if none). */
+LT_API const char* lt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LT_H */

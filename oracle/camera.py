@@ -228,14 +228,13 @@ def plenoptic_array_field(vol, cam, x, cell):
     return np.where(lenslet_owner(cam) >= 0, Fa, 0.0)
 
 
-def plenoptic_forward(vol, cam, x, return_array=False):
-    """y = sum_k sum_mu B^{d mu}_k M_mu (1/V^a) sum_n B^{an}_k w^n."""
-    st = _StageTwo(cam)
+def plenoptic_stage2(cam, fields, st=None):
+    """y = sum_k sum_mu B^{d mu}_k fa_k for given (masked) array-plane fields
+    [K][arr_nt][arr_ns]."""
+    st = _StageTwo(cam) if st is None else st
     y = np.zeros((cam.det_nt, cam.det_ns))
-    fields = []
     for ci, cell in enumerate(lens_cells(cam)):
-        Fa = plenoptic_array_field(vol, cam, x, cell)
-        fields.append(Fa)
+        Fa = np.asarray(fields[ci], dtype=np.float64)
         for mt in range(cam.mla_nt):
             for ms in range(cam.mla_ns):
                 mu = mt * cam.mla_ns + ms
@@ -247,17 +246,14 @@ def plenoptic_forward(vol, cam, x, return_array=False):
                 rows, cols = st.rows[mt], st.cols[ms]
                 sub = Fa[np.ix_(rows, cols)] * (st.owner[np.ix_(rows, cols)] == mu)
                 y[np.ix_(rt, rs)] += Bt @ sub @ Bs.T
-    if return_array:
-        return y, np.stack(fields)
     return y
 
 
-def plenoptic_adjoint(vol, cam, y, return_array=False):
-    """x = sum_k sum_n dz (B^{an}_k)^T (1/V^a) M sum_mu (B^{d mu}_k)^T y."""
-    st = _StageTwo(cam)
+def plenoptic_stage2_adjoint(cam, y, st=None):
+    """M sum_mu (B^{d mu}_k)^T y for every cell: fields [K][arr_nt][arr_ns]."""
+    st = _StageTwo(cam) if st is None else st
     Y = np.asarray(y, dtype=np.float64).reshape(cam.det_nt, cam.det_ns)
-    x = np.zeros(vol.shape)
-    fields = []
+    out = []
     for ci, cell in enumerate(lens_cells(cam)):
         Ga = np.zeros((cam.arr_nt, cam.arr_ns))
         for mt in range(cam.mla_nt):
@@ -272,14 +268,37 @@ def plenoptic_adjoint(vol, cam, y, return_array=False):
                 g = Bt.T @ Y[np.ix_(rt, rs)] @ Bs
                 own = st.owner[np.ix_(rows, cols)] == mu
                 Ga[np.ix_(rows, cols)] += np.where(own, g, 0.0)
-        Ga /= array_basis_volume(cam, cell)
-        fields.append(Ga)
+        out.append(Ga)
+    return np.stack(out)
+
+
+def plenoptic_stage1_adjoint(vol, cam, fields):
+    """sum_k sum_n dz (B^{an}_k)^T (1/V^a) g_k for given fields g."""
+    x = np.zeros(vol.shape)
+    for ci, cell in enumerate(lens_cells(cam)):
+        Ga = np.asarray(fields[ci], dtype=np.float64) / array_basis_volume(cam, cell)
         for n in range(vol.nz):
             Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_mla,
                                      cam.arr_ns, cam.arr_nt, cam.arr_ps, cam.arr_pt)
             x[n] += vol.dz * (Bt.T @ Ga @ Bs)
+    return x
+
+
+def plenoptic_forward(vol, cam, x, return_array=False):
+    """y = sum_k sum_mu B^{d mu}_k M_mu (1/V^a) sum_n B^{an}_k w^n."""
+    fields = np.stack([plenoptic_array_field(vol, cam, x, cell) for cell in lens_cells(cam)])
+    y = plenoptic_stage2(cam, fields)
     if return_array:
-        return x, np.stack(fields)
+        return y, fields
+    return y
+
+
+def plenoptic_adjoint(vol, cam, y, return_array=False):
+    """x = sum_k sum_n dz (B^{an}_k)^T (1/V^a) M sum_mu (B^{d mu}_k)^T y."""
+    fields = plenoptic_stage2_adjoint(cam, y)
+    x = plenoptic_stage1_adjoint(vol, cam, fields)
+    if return_array:
+        return x, fields
     return x
 
 

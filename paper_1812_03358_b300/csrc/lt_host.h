@@ -1,0 +1,62 @@
+// Host-side plan structures shared by the C-ABI translation units.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "lt.h"
+#include "lt_internal.h"
+
+namespace lt {
+
+// Kernel window limits (must match lt_kernels.cu).
+constexpr int kMaxForwardWindow = 8;
+constexpr int kMaxAdjointWindow = 16;
+constexpr int kMaxLensletPixels = 16;
+
+struct Cell {
+  double sk, tk, d0s, d0t;   // angular cell centre and widths on the main lens
+};
+
+struct CameraPlan {
+  lt_camera_desc desc{};
+  std::vector<double> focal;
+  std::vector<Cell> cells;
+  int K = 0;
+  int64_t M = 0;
+  int64_t offset = 0;
+  SliceParam* d_slice = nullptr;   // [K][nz]
+  int wmax_s = 0, wmax_t = 0, wimax_s = 0, wimax_t = 0;
+  // plenoptic
+  int64_t Na = 0;
+  LensletParam* d_lens = nullptr;
+  int2* d_cand_s = nullptr;
+  int2* d_cand_t = nullptr;
+  int2* d_cols = nullptr;
+  int2* d_rows = nullptr;
+  int32_t* d_col_owner = nullptr;
+  int32_t* d_row_owner = nullptr;
+  uint8_t* d_mask = nullptr;
+  float* d_fa = nullptr;           // scratch array plane [F][K][Na]
+  StageTwo s2{};
+};
+
+lt_status set_error(lt_status s, const char* fmt, ...);
+lt_status cuda_error(cudaError_t e, const char* where);
+void clear_error();
+
+lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long long y_fs,
+                         cudaStream_t st);
+lt_status camera_adjoint(lt_plan* p, int cam, const float* y, long long y_fs, float* x,
+                         int accumulate, cudaStream_t st);
+
+}  // namespace lt
+
+struct lt_plan {
+  lt_volume_desc vol{};
+  int frames = 1;
+  int64_t nvox = 0;
+  int64_t m_total = 0;
+  int device = 0;
+  std::vector<lt::CameraPlan> cams;
+};

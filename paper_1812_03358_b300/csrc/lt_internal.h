@@ -1,0 +1,89 @@
+// Internal data structures shared by the host planner and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lt {
+
+// Footprint of a target pixel i on a source grid, for one axis, one angular
+// cell and one source plane (Sec. II-C, eq. xport,int).  The set of source
+// rays that cross angular cell k and land in target pixel i, pushed to the
+// source plane, has a trapezoidal density: the convolution of two boxes whose
+// widths are the cell and the pixel seen from the source plane (Table III; a
+// box for the Dirac basis, Table II).  In source-index units (source cell j
+// spans [j-1/2, j+1/2]) its centre is xi(i) = c0 + c1 * i, its plateau
+// half-width P and its outer half-width Q.  The transport entry is
+//     B[i][j] = H * dsrc * integral_{j-1/2}^{j+1/2} T(xi - xi(i)) dxi
+// with T the unit-height trapezoid; H * dsrc is folded into a per-plane scale.
+struct AxisParam {
+  float c0_hi, c0_lo;   // xi(i) = (c0_hi + c0_lo) + (c1_hi + c1_lo) * i
+  float c1_hi, c1_lo;
+  float P, Q;           // 0 <= P <= Q
+  float hir;            // 1 / (2 (Q - P)); 0 when Q == P (box)
+  float inv_c1;         // 1 / c1, for the adjoint's target-pixel windows
+};
+
+// One (angular cell k, slice n) of a slice -> image-plane transport.
+struct SliceParam {
+  AxisParam s, t;
+  float scale;          // Hs*dx * Ht*dy * dz  (/ V^a for the plenoptic array plane)
+  int32_t ws, wt;       // forward windows: source cells per target pixel
+  int32_t wis, wit;     // adjoint windows: target pixels per source cell
+  int32_t pad[3];
+};
+
+// Array plane -> detector through one lenslet, one angular cell (Sec. II-F2).
+// Source grid = the array plane, target = detector pixels.
+struct LensletParam {
+  AxisParam s, t;
+  float scale;          // Hs*arr_ps * Ht*arr_pt
+  int32_t pad[3];
+};
+
+// Device tables of one plenoptic camera's array -> detector stage.
+struct StageTwo {
+  const LensletParam* lens;   // [K][mla_nt*mla_ns]
+  const int2* cand_s;         // [K][det_ns]: lenslet columns that can reach detector column
+  const int2* cand_t;         // [K][det_nt]
+  const int2* cols;           // [mla_ns]: array columns [x, y) of lenslet column
+  const int2* rows;           // [mla_nt]
+  const int32_t* col_owner;   // [arr_ns]: lenslet column of an array column, -1 if none
+  const int32_t* row_owner;   // [arr_nt]
+  const uint8_t* mask;        // [arr_nt*arr_ns] 1 if the pixel centre is inside its lenslet disc
+  int32_t mla_ns, mla_nt;
+  int32_t arr_ns, arr_nt;
+  int32_t det_ns, det_nt;
+  int32_t K;
+  int32_t wis, wit;           // adjoint windows (detector pixels per array pixel)
+  int32_t max_cols, max_rows; // forward windows (array pixels per lenslet)
+};
+
+// ---- kernel launchers (lt_kernels.cu) -------------------------------------
+
+// Slice -> plane beam integration (single-lens detector or plenoptic array
+// plane).  If per_cell, output is [F][K][nt][ns] (blockIdx.y = cell), else
+// the cells are summed into [F][...][nt][ns] at out + f*out_frame_stride.
+cudaError_t launch_beam_forward(const float* x, float* out, const SliceParam* prm,
+                                int nx, int ny, int nz, int ns, int nt, int K,
+                                int per_cell, const uint8_t* mask, int frames,
+                                long long x_frame_stride, long long out_frame_stride,
+                                int wmax_s, int wmax_t, cudaStream_t st);
+
+// Gather adjoint of the above: x[F][nz][ny][nx] (= or +=) sum_k sum_n ...
+// in = [F][K][nt][ns] if per_cell else [F][nt][ns] shared by all cells.
+cudaError_t launch_beam_adjoint(const float* in, float* x, const SliceParam* prm,
+                                int nx, int ny, int nz, int ns, int nt, int K,
+                                int per_cell, int accumulate, int frames,
+                                long long in_frame_stride, long long x_frame_stride,
+                                int wimax_s, int wimax_t, cudaStream_t st);
+
+cudaError_t launch_stage2_forward(const float* fa, float* y, StageTwo s2, int frames,
+                                  long long fa_frame_stride, long long y_frame_stride,
+                                  cudaStream_t st);
+
+cudaError_t launch_stage2_adjoint(const float* y, float* fa, StageTwo s2, int frames,
+                                  long long y_frame_stride, long long fa_frame_stride,
+                                  cudaStream_t st);
+
+}  // namespace lt

@@ -1,0 +1,663 @@
+// Host side of the C ABI: descriptor validation, float64 transport planning
+// (Sec. II-A/C, Tables II and III), device tables and the operator entry
+// points of include/lt.h.
+#include "lt.h"
+#include "lt_internal.h"
+#include "lt_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+using lt::AxisParam;
+using lt::LensletParam;
+using lt::SliceParam;
+
+namespace {
+thread_local std::string g_last_error;
+}  // namespace
+
+namespace lt {
+
+lt_status set_error(lt_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+lt_status cuda_error(cudaError_t e, const char* where) {
+  return set_error(LT_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+// Position row (X_ss, X_su, Xbar_s) of an affine ray map (Sec. II-A).
+struct Row {
+  double ss, su, b;
+};
+
+// Slice at object distance d -> image plane d_img behind a lens of focal
+// length f: T_{d_img} o R_f o T_d (Table I).  Angular plane: T_d.
+static void slice_rows(double d, double d_img, double f, Row* P, Row* L) {
+  L->ss = 1.0;
+  L->su = d;
+  L->b = 0.0;
+  P->ss = 1.0 - d_img / f;
+  P->su = d + d_img - d * d_img / f;
+  P->b = 0.0;
+}
+
+// Array plane -> detector through a lenslet (focal f, centre c) and a
+// propagation D_mud: T_{D_mud} o R_{f,c}; angular plane: back by D_mum.
+static void lenslet_rows(double d_mud, double d_mum, double f, double c, Row* P, Row* L) {
+  L->ss = 1.0;
+  L->su = -d_mum;
+  L->b = 0.0;
+  P->ss = 1.0 - d_mud / f;
+  P->su = d_mud;
+  P->b = d_mud * c / f;
+}
+
+static void split(double v, float* hi, float* lo) {
+  *hi = (float)v;
+  *lo = (float)(v - (double)*hi);
+}
+
+// Footprint of target pixel i (centre tgt_first + i*tgt_pitch, width
+// tgt_pitch) through angular cell [cell_c +- cell_w/2] on the source grid
+// (cell j centred at src_first + j*src_pitch).  The map (s,u) -> (lens
+// crossing l, target position p) is affine with Jacobian J = Lss Psu - Lsu Pss;
+// inverting it, s = sig_l l + sig_p p + sig_0, so the pixel-and-cell
+// rectangle pushes forward to the convolution of boxes of widths
+// |sig_l| cell_w and |sig_p| tgt_pitch (Table III's trapezoid) with height
+// H = min(cell_w/|Lsu|, tgt_pitch/|Psu|) in the (s,u) measure.  For the Dirac
+// basis the cell width collapses and H = cell_w/|Lsu| (Table II).
+struct Footprint {
+  AxisParam a;
+  double H;       // kernel height
+  double C0, C1;  // centre in source-index units
+  double P, Q;
+};
+
+static bool footprint(const Row& L, const Row& P, double cell_c, double cell_w,
+                      double tgt_first, double tgt_pitch, double src_first, double src_pitch,
+                      int basis, Footprint* out) {
+  const double J = L.ss * P.su - L.su * P.ss;
+  if (!(std::fabs(J) > 0.0) || !(std::fabs(L.su) > 0.0)) return false;
+  const double sig_l = P.su / J;
+  const double sig_p = -L.su / J;
+  const double sig_0 = (L.su * P.b - P.su * L.b) / J;
+  const double C1 = sig_p * tgt_pitch / src_pitch;
+  const double C0 = (sig_l * cell_c + sig_p * tgt_first + sig_0 - src_first) / src_pitch;
+  const double w2 = std::fabs(sig_p) * tgt_pitch / src_pitch;
+  double Pw, Qw, H;
+  if (basis == LT_BASIS_DIRAC) {
+    Pw = Qw = 0.5 * w2;
+    H = cell_w / std::fabs(L.su);
+  } else {
+    const double w1 = std::fabs(sig_l) * cell_w / src_pitch;
+    Pw = 0.5 * std::fabs(w1 - w2);
+    Qw = 0.5 * (w1 + w2);
+    H = cell_w / std::fabs(L.su);
+    if (P.su != 0.0) H = std::min(H, tgt_pitch / std::fabs(P.su));
+  }
+  if (!std::isfinite(C0) || !std::isfinite(C1) || !std::isfinite(Qw) || C1 == 0.0) return false;
+  split(C0, &out->a.c0_hi, &out->a.c0_lo);
+  split(C1, &out->a.c1_hi, &out->a.c1_lo);
+  out->a.P = (float)Pw;
+  out->a.Q = (float)Qw;
+  out->a.hir = (out->a.Q > out->a.P) ? (float)(0.5 / ((double)out->a.Q - (double)out->a.P)) : 0.0f;
+  out->a.inv_c1 = (float)(1.0 / C1);
+  out->H = H;
+  out->C0 = C0;
+  out->C1 = C1;
+  out->P = Pw;
+  out->Q = Qw;
+  return true;
+}
+
+// Forward window: source cells a target pixel's footprint can touch.
+static int fwd_window(float Q) { return (int)std::floor(2.0 * (double)Q) + 2; }
+// Adjoint window: target pixels whose footprints can touch one source cell
+// (with one pixel of margin on each side for rounding).
+static int adj_window(float Q, double C1) {
+  return (int)std::floor((2.0 * (double)Q + 1.0) / std::fabs(C1)) + 4;
+}
+
+static inline double centre(int i, int n, double pitch) { return (i - 0.5 * (n - 1)) * pitch; }
+
+}  // namespace lt
+
+using namespace lt;
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+
+static lt_status validate_volume(const lt_volume_desc* v) {
+  if (!v) return set_error(LT_EINVAL, "volume descriptor is NULL");
+  if (v->nx <= 0 || v->ny <= 0 || v->nz <= 0)
+    return set_error(LT_EINVAL, "volume sizes must be positive (got %d %d %d)", v->nx, v->ny, v->nz);
+  if (!(v->dx > 0) || !(v->dy > 0) || !(v->dz > 0) || !std::isfinite(v->dx) ||
+      !std::isfinite(v->dy) || !std::isfinite(v->dz))
+    return set_error(LT_EINVAL, "voxel sizes must be positive and finite");
+  if ((long long)v->nx * v->ny * v->nz > (1LL << 34))
+    return set_error(LT_EINVAL, "volume too large");
+  return LT_OK;
+}
+
+static bool pos(double v) { return v > 0.0 && std::isfinite(v); }
+
+static lt_status validate_camera(const lt_volume_desc* v, const lt_camera_desc* c, int idx) {
+  if (c->kind != LT_CAM_SINGLE && c->kind != LT_CAM_PLENOPTIC)
+    return set_error(LT_EINVAL, "camera %d: unknown kind %d", idx, c->kind);
+  if (c->basis != LT_BASIS_PILLBOX && c->basis != LT_BASIS_DIRAC)
+    return set_error(LT_EINVAL, "camera %d: unknown basis %d", idx, c->basis);
+  if (!pos(c->f_main) || !pos(c->r_main) || !pos(c->d_obj))
+    return set_error(LT_EINVAL, "camera %d: f_main, r_main, d_obj must be positive", idx);
+  if (!std::isfinite(c->yaw)) return set_error(LT_EINVAL, "camera %d: yaw not finite", idx);
+  if (c->yaw != 0.0)
+    return set_error(LT_EUNSUPPORTED, "camera %d: rotated cameras (yaw != 0) are not supported by this build", idx);
+  if (c->det_ns <= 0 || c->det_nt <= 0 || !pos(c->det_ps) || !pos(c->det_pt))
+    return set_error(LT_EINVAL, "camera %d: detector sizes/pitches must be positive", idx);
+  if (c->ks <= 0 || c->kt <= 0 || c->ks > 256 || c->kt > 256)
+    return set_error(LT_EINVAL, "camera %d: angular cells ks, kt must be in [1, 256]", idx);
+  const double dmin = c->d_obj - 0.5 * v->nz * v->dz;
+  if (!(dmin > 0.0))
+    return set_error(LT_EINVAL, "camera %d: the volume reaches the main lens (d_obj - nz*dz/2 = %g)", idx, dmin);
+  if (c->kind == LT_CAM_SINGLE) {
+    if (!pos(c->d_lens_det)) return set_error(LT_EINVAL, "camera %d: d_lens_det must be positive", idx);
+  } else {
+    if (!pos(c->d_lens_mla) || !pos(c->d_mla_det))
+      return set_error(LT_EINVAL, "camera %d: d_lens_mla, d_mla_det must be positive", idx);
+    if (c->mla_ns <= 0 || c->mla_nt <= 0 || !pos(c->mla_pitch) || !pos(c->mla_radius))
+      return set_error(LT_EINVAL, "camera %d: lenslet grid must be non-empty with positive pitch/radius", idx);
+    if (c->mla_radius > 0.5 * c->mla_pitch * (1.0 + 1e-12))
+      return set_error(LT_EINVAL, "camera %d: lenslet radius exceeds half the pitch (discs overlap)", idx);
+    if (!c->mla_focal) return set_error(LT_EINVAL, "camera %d: mla_focal is NULL", idx);
+    for (long long m = 0; m < (long long)c->mla_ns * c->mla_nt; ++m)
+      if (!pos(c->mla_focal[m])) return set_error(LT_EINVAL, "camera %d: lenslet %lld focal length not positive", idx, m);
+    if (c->arr_ns <= 0 || c->arr_nt <= 0 || !pos(c->arr_ps) || !pos(c->arr_pt))
+      return set_error(LT_EINVAL, "camera %d: array-plane grid must be non-empty with positive pitch", idx);
+  }
+  return LT_OK;
+}
+
+template <typename T>
+static lt_status upload(const std::vector<T>& h, T** d, const char* what) {
+  if (h.empty()) {
+    *d = nullptr;
+    return LT_OK;
+  }
+  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+  if (e != cudaSuccess) {
+    *d = nullptr;
+    return set_error(LT_ENOMEM, "cudaMalloc(%s, %zu bytes): %s", what, h.size() * sizeof(T),
+                     cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, what);
+  return LT_OK;
+}
+
+static void free_camera(CameraPlan& c) {
+  cudaFree(c.d_slice);
+  cudaFree(c.d_lens);
+  cudaFree(c.d_cand_s);
+  cudaFree(c.d_cand_t);
+  cudaFree(c.d_cols);
+  cudaFree(c.d_rows);
+  cudaFree(c.d_col_owner);
+  cudaFree(c.d_row_owner);
+  cudaFree(c.d_mask);
+  cudaFree(c.d_fa);
+  c = CameraPlan();
+}
+
+// Per (cell, slice) parameters of the slice -> image-plane transport.
+static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_img, int tgt_ns,
+                             int tgt_nt, double tgt_ps, double tgt_pt, double extra_scale, int idx) {
+  const lt_camera_desc& d = c.desc;
+  std::vector<SliceParam> sp((size_t)c.K * v.nz);
+  for (int k = 0; k < c.K; ++k) {
+    for (int n = 0; n < v.nz; ++n) {
+      const double dist = d.d_obj + centre(n, v.nz, v.dz);
+      Row P, L;
+      slice_rows(dist, d_img, d.f_main, &P, &L);
+      Footprint fs, ft;
+      if (!footprint(L, P, c.cells[k].sk, c.cells[k].d0s, centre(0, tgt_ns, tgt_ps), tgt_ps,
+                     centre(0, v.nx, v.dx), v.dx, d.basis, &fs) ||
+          !footprint(L, P, c.cells[k].tk, c.cells[k].d0t, centre(0, tgt_nt, tgt_pt), tgt_pt,
+                     centre(0, v.ny, v.dy), v.dy, d.basis, &ft))
+        return set_error(LT_EINVAL, "camera %d: degenerate transport at slice %d", idx, n);
+      SliceParam& p = sp[(size_t)k * v.nz + n];
+      std::memset(&p, 0, sizeof(p));
+      p.s = fs.a;
+      p.t = ft.a;
+      p.scale = (float)(fs.H * v.dx * ft.H * v.dy * v.dz * extra_scale);
+      p.ws = fwd_window(p.s.Q);
+      p.wt = fwd_window(p.t.Q);
+      p.wis = adj_window(p.s.Q, fs.C1);
+      p.wit = adj_window(p.t.Q, ft.C1);
+      c.wmax_s = std::max(c.wmax_s, p.ws);
+      c.wmax_t = std::max(c.wmax_t, p.wt);
+      c.wimax_s = std::max(c.wimax_s, p.wis);
+      c.wimax_t = std::max(c.wimax_t, p.wit);
+    }
+  }
+  if (c.wmax_s > kMaxForwardWindow || c.wmax_t > kMaxForwardWindow)
+    return set_error(LT_EUNSUPPORTED,
+                     "camera %d: a pixel footprint spans %d x %d voxels (kernel limit %d); use finer pixels or coarser voxels",
+                     idx, c.wmax_s, c.wmax_t, kMaxForwardWindow);
+  if (c.wimax_s > kMaxAdjointWindow || c.wimax_t > kMaxAdjointWindow)
+    return set_error(LT_EUNSUPPORTED,
+                     "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
+                     idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
+  return upload(sp, &c.d_slice, "slice parameters");
+}
+
+// Array -> detector stage of a plenoptic camera (Sec. II-D, II-F2).
+static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
+  const lt_camera_desc& d = c.desc;
+  const int mns = d.mla_ns, mnt = d.mla_nt;
+  const int nmu = mns * mnt;
+  // Lenslet grid cells [c - pitch/2, c + pitch/2) own the array columns/rows
+  // whose centres fall inside them.
+  std::vector<int32_t> col_owner(d.arr_ns, -1), row_owner(d.arr_nt, -1);
+  std::vector<int2> cols(mns, make_int2(0, 0)), rows(mnt, make_int2(0, 0));
+  for (int m = 0; m < mns; ++m) cols[m] = make_int2(INT32_MAX, -1);
+  for (int m = 0; m < mnt; ++m) rows[m] = make_int2(INT32_MAX, -1);
+  const double edge_s = centre(0, mns, d.mla_pitch) - 0.5 * d.mla_pitch;
+  const double edge_t = centre(0, mnt, d.mla_pitch) - 0.5 * d.mla_pitch;
+  for (int j = 0; j < d.arr_ns; ++j) {
+    const double m = std::floor((centre(j, d.arr_ns, d.arr_ps) - edge_s) / d.mla_pitch);
+    if (m >= 0 && m < mns) {
+      col_owner[j] = (int)m;
+      cols[(int)m].x = std::min(cols[(int)m].x, j);
+      cols[(int)m].y = std::max(cols[(int)m].y, j + 1);
+    }
+  }
+  for (int j = 0; j < d.arr_nt; ++j) {
+    const double m = std::floor((centre(j, d.arr_nt, d.arr_pt) - edge_t) / d.mla_pitch);
+    if (m >= 0 && m < mnt) {
+      row_owner[j] = (int)m;
+      rows[(int)m].x = std::min(rows[(int)m].x, j);
+      rows[(int)m].y = std::max(rows[(int)m].y, j + 1);
+    }
+  }
+  int max_cols = 0, max_rows = 0;
+  for (auto& r : cols) {
+    if (r.y < 0) r = make_int2(0, 0);
+    max_cols = std::max(max_cols, r.y - r.x);
+  }
+  for (auto& r : rows) {
+    if (r.y < 0) r = make_int2(0, 0);
+    max_rows = std::max(max_rows, r.y - r.x);
+  }
+  if (max_cols > kMaxLensletPixels || max_rows > kMaxLensletPixels)
+    return set_error(LT_EUNSUPPORTED, "camera %d: %d x %d array pixels per lenslet (kernel limit %d)",
+                     idx, max_cols, max_rows, kMaxLensletPixels);
+  // Binary mask M: array-pixel centre strictly inside its lenslet's disc.
+  std::vector<uint8_t> mask((size_t)d.arr_ns * d.arr_nt, 0);
+  const double r2 = d.mla_radius * d.mla_radius;
+  for (int jt = 0; jt < d.arr_nt; ++jt) {
+    if (row_owner[jt] < 0) continue;
+    const double dt = centre(jt, d.arr_nt, d.arr_pt) - centre(row_owner[jt], mnt, d.mla_pitch);
+    for (int js = 0; js < d.arr_ns; ++js) {
+      if (col_owner[js] < 0) continue;
+      const double ds = centre(js, d.arr_ns, d.arr_ps) - centre(col_owner[js], mns, d.mla_pitch);
+      mask[(size_t)jt * d.arr_ns + js] = (ds * ds + dt * dt < r2) ? 1 : 0;
+    }
+  }
+  // Per (cell, lenslet) footprints of detector pixels on the array plane.
+  std::vector<LensletParam> lens((size_t)c.K * nmu);
+  std::vector<int2> cand_s((size_t)c.K * d.det_ns, make_int2(INT32_MAX, -1));
+  std::vector<int2> cand_t((size_t)c.K * d.det_nt, make_int2(INT32_MAX, -1));
+  int wis = 0, wit = 0;
+  for (int k = 0; k < c.K; ++k) {
+    for (int mt = 0; mt < mnt; ++mt) {
+      for (int ms = 0; ms < mns; ++ms) {
+        const double f = c.focal[(size_t)mt * mns + ms];
+        Row Ps, Ls, Pt, Lt;
+        lenslet_rows(d.d_mla_det, d.d_lens_mla, f, centre(ms, mns, d.mla_pitch), &Ps, &Ls);
+        lenslet_rows(d.d_mla_det, d.d_lens_mla, f, centre(mt, mnt, d.mla_pitch), &Pt, &Lt);
+        Footprint fs, ft;
+        if (!footprint(Ls, Ps, c.cells[k].sk, c.cells[k].d0s, centre(0, d.det_ns, d.det_ps), d.det_ps,
+                       centre(0, d.arr_ns, d.arr_ps), d.arr_ps, d.basis, &fs) ||
+            !footprint(Lt, Pt, c.cells[k].tk, c.cells[k].d0t, centre(0, d.det_nt, d.det_pt), d.det_pt,
+                       centre(0, d.arr_nt, d.arr_pt), d.arr_pt, d.basis, &ft))
+          return set_error(LT_EINVAL, "camera %d: degenerate microlens transport (lenslet %d,%d)", idx, mt, ms);
+        LensletParam& L = lens[(size_t)k * nmu + (size_t)mt * mns + ms];
+        std::memset(&L, 0, sizeof(L));
+        L.s = fs.a;
+        L.t = ft.a;
+        L.scale = (float)(fs.H * d.arr_ps * ft.H * d.arr_pt);
+        wis = std::max(wis, adj_window(L.s.Q, fs.C1));
+        wit = std::max(wit, adj_window(L.t.Q, ft.C1));
+        // detector columns whose footprints can reach this lenslet's columns
+        if (cols[ms].y > cols[ms].x) {
+          const double lo = cols[ms].x - 0.5 - fs.Q, hi = cols[ms].y - 0.5 + fs.Q;
+          double a = (lo - fs.C0) / fs.C1, b = (hi - fs.C0) / fs.C1;
+          if (a > b) std::swap(a, b);
+          const long long i0 = std::max<long long>(0, (long long)std::floor(a) - 1);
+          const long long i1 = std::min<long long>(d.det_ns - 1, (long long)std::ceil(b) + 1);
+          for (long long i = i0; i <= i1; ++i) {
+            int2& cs = cand_s[(size_t)k * d.det_ns + i];
+            cs.x = std::min(cs.x, ms);
+            cs.y = std::max(cs.y, ms);
+          }
+        }
+        if (rows[mt].y > rows[mt].x) {
+          const double lo = rows[mt].x - 0.5 - ft.Q, hi = rows[mt].y - 0.5 + ft.Q;
+          double a = (lo - ft.C0) / ft.C1, b = (hi - ft.C0) / ft.C1;
+          if (a > b) std::swap(a, b);
+          const long long i0 = std::max<long long>(0, (long long)std::floor(a) - 1);
+          const long long i1 = std::min<long long>(d.det_nt - 1, (long long)std::ceil(b) + 1);
+          for (long long i = i0; i <= i1; ++i) {
+            int2& ct = cand_t[(size_t)k * d.det_nt + i];
+            ct.x = std::min(ct.x, mt);
+            ct.y = std::max(ct.y, mt);
+          }
+        }
+      }
+    }
+  }
+  for (auto& r : cand_s)
+    if (r.y < 0) r = make_int2(0, -1);
+  for (auto& r : cand_t)
+    if (r.y < 0) r = make_int2(0, -1);
+  if (wis > kMaxAdjointWindow || wit > kMaxAdjointWindow)
+    return set_error(LT_EUNSUPPORTED, "camera %d: an array pixel is covered by %d x %d detector footprints (kernel limit %d)",
+                     idx, wis, wit, kMaxAdjointWindow);
+  lt_status s;
+  if ((s = upload(lens, &c.d_lens, "lenslet parameters")) != LT_OK) return s;
+  if ((s = upload(cand_s, &c.d_cand_s, "candidate columns")) != LT_OK) return s;
+  if ((s = upload(cand_t, &c.d_cand_t, "candidate rows")) != LT_OK) return s;
+  if ((s = upload(cols, &c.d_cols, "lenslet columns")) != LT_OK) return s;
+  if ((s = upload(rows, &c.d_rows, "lenslet rows")) != LT_OK) return s;
+  if ((s = upload(col_owner, &c.d_col_owner, "column owners")) != LT_OK) return s;
+  if ((s = upload(row_owner, &c.d_row_owner, "row owners")) != LT_OK) return s;
+  if ((s = upload(mask, &c.d_mask, "mask")) != LT_OK) return s;
+  c.Na = (int64_t)d.arr_ns * d.arr_nt;
+  const size_t fa_bytes = (size_t)frames * c.K * c.Na * sizeof(float);
+  cudaError_t e = cudaMalloc((void**)&c.d_fa, fa_bytes);
+  if (e != cudaSuccess) {
+    c.d_fa = nullptr;
+    return set_error(LT_ENOMEM, "cudaMalloc(array plane, %zu bytes): %s", fa_bytes, cudaGetErrorString(e));
+  }
+  lt::StageTwo& s2 = c.s2;
+  s2.lens = c.d_lens;
+  s2.cand_s = c.d_cand_s;
+  s2.cand_t = c.d_cand_t;
+  s2.cols = c.d_cols;
+  s2.rows = c.d_rows;
+  s2.col_owner = c.d_col_owner;
+  s2.row_owner = c.d_row_owner;
+  s2.mask = c.d_mask;
+  s2.mla_ns = mns;
+  s2.mla_nt = mnt;
+  s2.arr_ns = d.arr_ns;
+  s2.arr_nt = d.arr_nt;
+  s2.det_ns = d.det_ns;
+  s2.det_nt = d.det_nt;
+  s2.K = c.K;
+  s2.wis = wis;
+  s2.wit = wit;
+  s2.max_cols = max_cols;
+  s2.max_rows = max_rows;
+  return LT_OK;
+}
+
+static lt_status plan_camera(const lt_volume_desc& v, const lt_camera_desc& src, int frames,
+                             CameraPlan& c, int idx) {
+  c.desc = src;
+  if (src.kind == LT_CAM_PLENOPTIC) {
+    c.focal.assign(src.mla_focal, src.mla_focal + (size_t)src.mla_ns * src.mla_nt);
+    c.desc.mla_focal = nullptr;
+  }
+  // angular cells tiling [-r, r]^2, kept when the centre is inside the disc
+  const double r = src.r_main;
+  const double d0s = 2.0 * r / src.ks, d0t = 2.0 * r / src.kt;
+  for (int kt = 0; kt < src.kt; ++kt)
+    for (int ks = 0; ks < src.ks; ++ks) {
+      const double sk = -r + (ks + 0.5) * d0s, tk = -r + (kt + 0.5) * d0t;
+      if (sk * sk + tk * tk < r * r) c.cells.push_back({sk, tk, d0s, d0t});
+    }
+  c.K = (int)c.cells.size();
+  if (c.K == 0) return set_error(LT_EINVAL, "camera %d: no angular cell inside the aperture", idx);
+  c.M = (int64_t)src.det_ns * src.det_nt;
+  if (src.kind == LT_CAM_SINGLE)
+    return plan_slices(v, c, src.d_lens_det, src.det_ns, src.det_nt, src.det_ps, src.det_pt, 1.0, idx);
+  // plenoptic: V^a = (Da_s D0_s / D_mum)(Da_t D0_t / D_mum)
+  const double va = (src.arr_ps * d0s / src.d_lens_mla) * (src.arr_pt * d0t / src.d_lens_mla);
+  lt_status s = plan_slices(v, c, src.d_lens_mla, src.arr_ns, src.arr_nt, src.arr_ps, src.arr_pt,
+                            1.0 / va, idx);
+  if (s != LT_OK) return s;
+  return plan_stage_two(c, frames, idx);
+}
+
+extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_desc* cams,
+                                    int32_t n_cams, int32_t n_frames, lt_plan** out) {
+  clear_error();
+  if (!out) return set_error(LT_EINVAL, "out is NULL");
+  *out = nullptr;
+  lt_status s = validate_volume(vol);
+  if (s != LT_OK) return s;
+  if (n_cams <= 0 || !cams) return set_error(LT_EINVAL, "need at least one camera");
+  if (n_frames <= 0) return set_error(LT_EINVAL, "n_frames must be positive");
+  for (int c = 0; c < n_cams; ++c)
+    if ((s = validate_camera(vol, &cams[c], c)) != LT_OK) return s;
+  lt_plan* p = new (std::nothrow) lt_plan();
+  if (!p) return set_error(LT_ENOMEM, "host allocation failed");
+  p->vol = *vol;
+  p->frames = n_frames;
+  p->nvox = (int64_t)vol->nx * vol->ny * vol->nz;
+  cudaGetDevice(&p->device);
+  p->cams.resize(n_cams);
+  int64_t off = 0;
+  for (int c = 0; c < n_cams; ++c) {
+    s = plan_camera(*vol, cams[c], n_frames, p->cams[c], c);
+    if (s != LT_OK) {
+      lt_plan_destroy(p);
+      return s;
+    }
+    p->cams[c].offset = off;
+    off += p->cams[c].M;
+  }
+  p->m_total = off;
+  *out = p;
+  return LT_OK;
+}
+
+extern "C" lt_status lt_plan_destroy(lt_plan* plan) {
+  if (!plan) return LT_OK;
+  cudaDeviceSynchronize();
+  for (auto& c : plan->cams) free_camera(c);
+  delete plan;
+  return LT_OK;
+}
+
+extern "C" lt_status lt_plan_sizes(const lt_plan* plan, int64_t* n_vox, int64_t* det_offsets) {
+  clear_error();
+  if (!plan) return set_error(LT_EINVAL, "plan is NULL");
+  if (n_vox) *n_vox = plan->nvox;
+  if (det_offsets) {
+    for (size_t c = 0; c < plan->cams.size(); ++c) det_offsets[c] = plan->cams[c].offset;
+    det_offsets[plan->cams.size()] = plan->m_total;
+  }
+  return LT_OK;
+}
+
+extern "C" lt_status lt_camera_cells(const lt_plan* plan, int32_t cam, int32_t* n_cells) {
+  clear_error();
+  if (!plan || cam < 0 || cam >= (int)plan->cams.size() || !n_cells)
+    return set_error(LT_EINVAL, "bad plan/camera/out argument");
+  *n_cells = plan->cams[cam].K;
+  return LT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+
+namespace lt {
+
+lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, long long fa_fs,
+                         cudaStream_t st) {
+  const lt_volume_desc& v = p->vol;
+  cudaError_t e = launch_beam_forward(x, fa, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt,
+                                      c.K, 1, c.d_mask, p->frames, p->nvox, fa_fs, c.wmax_s, c.wmax_t, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 1");
+}
+
+lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
+                         int accumulate, cudaStream_t st) {
+  const lt_volume_desc& v = p->vol;
+  cudaError_t e = launch_beam_adjoint(fa, x, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt,
+                                      c.K, 1, accumulate, p->frames, fa_fs, p->nvox, c.wimax_s,
+                                      c.wimax_t, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 1 adjoint");
+}
+
+lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long long y_fs,
+                         cudaStream_t st) {
+  CameraPlan& c = p->cams[cam];
+  const lt_volume_desc& v = p->vol;
+  if (c.desc.kind == LT_CAM_SINGLE) {
+    cudaError_t e = launch_beam_forward(x, y, c.d_slice, v.nx, v.ny, v.nz, c.desc.det_ns, c.desc.det_nt,
+                                        c.K, 0, nullptr, p->frames, p->nvox, y_fs, c.wmax_s, c.wmax_t, st);
+    return e == cudaSuccess ? LT_OK : cuda_error(e, "single-lens forward");
+  }
+  const long long fa_fs = (long long)c.K * c.Na;
+  lt_status s = stage1_forward(p, c, x, c.d_fa, fa_fs, st);
+  if (s != LT_OK) return s;
+  cudaError_t e = launch_stage2_forward(c.d_fa, y, c.s2, p->frames, fa_fs, y_fs, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 2");
+}
+
+lt_status camera_adjoint(lt_plan* p, int cam, const float* y, long long y_fs, float* x,
+                         int accumulate, cudaStream_t st) {
+  CameraPlan& c = p->cams[cam];
+  const lt_volume_desc& v = p->vol;
+  if (c.desc.kind == LT_CAM_SINGLE) {
+    cudaError_t e = launch_beam_adjoint(y, x, c.d_slice, v.nx, v.ny, v.nz, c.desc.det_ns, c.desc.det_nt,
+                                        c.K, 0, accumulate, p->frames, y_fs, p->nvox, c.wimax_s,
+                                        c.wimax_t, st);
+    return e == cudaSuccess ? LT_OK : cuda_error(e, "single-lens adjoint");
+  }
+  const long long fa_fs = (long long)c.K * c.Na;
+  cudaError_t e = launch_stage2_adjoint(y, c.d_fa, c.s2, p->frames, y_fs, fa_fs, st);
+  if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2 adjoint");
+  return stage1_adjoint(p, c, c.d_fa, fa_fs, x, accumulate, st);
+}
+
+}  // namespace lt
+
+static lt_status check_cam(const lt_plan* p, int cam) {
+  if (!p) return set_error(LT_EINVAL, "plan is NULL");
+  if (cam < 0 || cam >= (int)p->cams.size()) return set_error(LT_EINVAL, "camera index %d out of range", cam);
+  return LT_OK;
+}
+
+static lt_status check_plenoptic(const lt_plan* p, int cam) {
+  lt_status s = check_cam(p, cam);
+  if (s != LT_OK) return s;
+  if (p->cams[cam].desc.kind != LT_CAM_PLENOPTIC)
+    return set_error(LT_EINVAL, "camera %d is not plenoptic", cam);
+  return LT_OK;
+}
+
+extern "C" lt_status lt_forward(lt_plan* plan, const float* x, float* y, void* stream) {
+  clear_error();
+  if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
+  for (int c = 0; c < (int)plan->cams.size(); ++c) {
+    lt_status s = camera_forward(plan, c, x, y + plan->cams[c].offset, plan->m_total, (cudaStream_t)stream);
+    if (s != LT_OK) return s;
+  }
+  return LT_OK;
+}
+
+extern "C" lt_status lt_adjoint(lt_plan* plan, const float* y, float* x, void* stream) {
+  clear_error();
+  if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
+  for (int c = 0; c < (int)plan->cams.size(); ++c) {
+    lt_status s = camera_adjoint(plan, c, y + plan->cams[c].offset, plan->m_total, x, c > 0,
+                                 (cudaStream_t)stream);
+    if (s != LT_OK) return s;
+  }
+  return LT_OK;
+}
+
+extern "C" lt_status lt_forward_camera(lt_plan* plan, int32_t cam, const float* x, float* y_cam,
+                                       void* stream) {
+  clear_error();
+  lt_status s = check_cam(plan, cam);
+  if (s != LT_OK) return s;
+  if (!x || !y_cam) return set_error(LT_EINVAL, "NULL argument");
+  return camera_forward(plan, cam, x, y_cam, plan->cams[cam].M, (cudaStream_t)stream);
+}
+
+extern "C" lt_status lt_adjoint_camera(lt_plan* plan, int32_t cam, const float* y_cam, float* x,
+                                       int32_t accumulate, void* stream) {
+  clear_error();
+  lt_status s = check_cam(plan, cam);
+  if (s != LT_OK) return s;
+  if (!x || !y_cam) return set_error(LT_EINVAL, "NULL argument");
+  return camera_adjoint(plan, cam, y_cam, plan->cams[cam].M, x, accumulate != 0, (cudaStream_t)stream);
+}
+
+extern "C" lt_status lt_plenoptic_stage1(lt_plan* plan, int32_t cam, const float* x, float* fa,
+                                         void* stream) {
+  clear_error();
+  lt_status s = check_plenoptic(plan, cam);
+  if (s != LT_OK) return s;
+  if (!x || !fa) return set_error(LT_EINVAL, "NULL argument");
+  CameraPlan& c = plan->cams[cam];
+  return stage1_forward(plan, c, x, fa, (long long)c.K * c.Na, (cudaStream_t)stream);
+}
+
+extern "C" lt_status lt_plenoptic_stage1_adjoint(lt_plan* plan, int32_t cam, const float* fa,
+                                                 float* x, int32_t accumulate, void* stream) {
+  clear_error();
+  lt_status s = check_plenoptic(plan, cam);
+  if (s != LT_OK) return s;
+  if (!x || !fa) return set_error(LT_EINVAL, "NULL argument");
+  CameraPlan& c = plan->cams[cam];
+  return stage1_adjoint(plan, c, fa, (long long)c.K * c.Na, x, accumulate != 0, (cudaStream_t)stream);
+}
+
+extern "C" lt_status lt_plenoptic_stage2(lt_plan* plan, int32_t cam, const float* fa, float* y_cam,
+                                         void* stream) {
+  clear_error();
+  lt_status s = check_plenoptic(plan, cam);
+  if (s != LT_OK) return s;
+  if (!fa || !y_cam) return set_error(LT_EINVAL, "NULL argument");
+  CameraPlan& c = plan->cams[cam];
+  cudaError_t e = launch_stage2_forward(fa, y_cam, c.s2, plan->frames, (long long)c.K * c.Na, c.M,
+                                        (cudaStream_t)stream);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 2");
+}
+
+extern "C" lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, const float* y_cam,
+                                                 float* fa, void* stream) {
+  clear_error();
+  lt_status s = check_plenoptic(plan, cam);
+  if (s != LT_OK) return s;
+  if (!fa || !y_cam) return set_error(LT_EINVAL, "NULL argument");
+  CameraPlan& c = plan->cams[cam];
+  cudaError_t e = launch_stage2_adjoint(y_cam, fa, c.s2, plan->frames, c.M, (long long)c.K * c.Na,
+                                        (cudaStream_t)stream);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 2 adjoint");
+}
+
+extern "C" const char* lt_last_error(void) { return g_last_error.c_str(); }

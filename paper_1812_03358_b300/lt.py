@@ -1,0 +1,277 @@
+"""Python binding of the C ABI in include/lt.h (argument marshalling only).
+
+Every function named lt_* here calls the C entry point of the same name in
+_lib/liblt.so; device pointers are passed as integers (e.g. tensor.data_ptr()).
+The ``Plan`` class is a thin owner of a plan handle that accepts torch CUDA
+tensors.  There is no fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+from . import inputs
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblt.so")
+
+LT_OK, LT_EINVAL, LT_ENOMEM, LT_ECUDA, LT_EUNSUPPORTED, LT_ETIMEOUT = range(6)
+
+
+class lt_volume_desc(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32),
+                ("dx", c_double), ("dy", c_double), ("dz", c_double)]
+
+
+class lt_camera_desc(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("basis", c_int32),
+                ("f_main", c_double), ("r_main", c_double), ("d_obj", c_double), ("yaw", c_double),
+                ("det_ns", c_int32), ("det_nt", c_int32), ("det_ps", c_double), ("det_pt", c_double),
+                ("d_lens_det", c_double), ("ks", c_int32), ("kt", c_int32),
+                ("d_lens_mla", c_double), ("d_mla_det", c_double),
+                ("mla_ns", c_int32), ("mla_nt", c_int32), ("mla_pitch", c_double),
+                ("mla_radius", c_double), ("mla_focal", POINTER(c_double)),
+                ("arr_ns", c_int32), ("arr_nt", c_int32), ("arr_ps", c_double), ("arr_pt", c_double)]
+
+
+class LtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lt status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_SIGS = {
+    "lt_plan_create": (c_int32, [POINTER(lt_volume_desc), POINTER(lt_camera_desc), c_int32, c_int32,
+                                 POINTER(c_void_p)]),
+    "lt_plan_destroy": (c_int32, [c_void_p]),
+    "lt_plan_sizes": (c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
+    "lt_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lt_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lt_forward_camera": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "lt_adjoint_camera": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
+    "lt_camera_cells": (c_int32, [c_void_p, c_int32, POINTER(c_int32)]),
+    "lt_plenoptic_stage1": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "lt_plenoptic_stage1_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
+    "lt_plenoptic_stage2": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "lt_plenoptic_stage2_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "lt_last_error": (c_char_p, []),
+}
+
+
+def lib():
+    """Load liblt.so (built in-tree); raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1812_03358_b300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != LT_OK:
+        raise LtError(status, lib().lt_last_error().decode())
+
+
+def lt_last_error() -> str:
+    return lib().lt_last_error().decode()
+
+
+def volume_desc(vol: inputs.Volume) -> lt_volume_desc:
+    return lt_volume_desc(vol.nx, vol.ny, vol.nz, vol.dx, vol.dy, vol.dz)
+
+
+def camera_desc(cam: inputs.Camera, keep: list) -> lt_camera_desc:
+    d = lt_camera_desc()
+    for name, _ in lt_camera_desc._fields_:
+        if name == "mla_focal":
+            continue
+        setattr(d, name, getattr(cam, name))
+    if cam.mla_focal is not None:
+        arr = np.ascontiguousarray(cam.mla_focal, dtype=np.float64)
+        keep.append(arr)
+        d.mla_focal = arr.ctypes.data_as(POINTER(c_double))
+    return d
+
+
+def lt_plan_create(vol: inputs.Volume, cams, n_frames: int = 1) -> c_void_p:
+    keep = []
+    cams = list(cams)
+    arr = (lt_camera_desc * len(cams))(*[camera_desc(c, keep) for c in cams])
+    v = volume_desc(vol)
+    h = c_void_p()
+    _check(lib().lt_plan_create(byref(v), arr, len(cams), n_frames, byref(h)))
+    return h
+
+
+def lt_plan_destroy(plan) -> None:
+    _check(lib().lt_plan_destroy(plan))
+
+
+def lt_plan_sizes(plan, n_cams: int):
+    nv = c_int64()
+    offs = (c_int64 * (n_cams + 1))()
+    _check(lib().lt_plan_sizes(plan, byref(nv), offs))
+    return nv.value, list(offs)
+
+
+def lt_forward(plan, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    _check(lib().lt_forward(plan, x_ptr, y_ptr, stream))
+
+
+def lt_adjoint(plan, y_ptr: int, x_ptr: int, stream: int = 0) -> None:
+    _check(lib().lt_adjoint(plan, y_ptr, x_ptr, stream))
+
+
+def lt_forward_camera(plan, cam: int, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    _check(lib().lt_forward_camera(plan, cam, x_ptr, y_ptr, stream))
+
+
+def lt_adjoint_camera(plan, cam: int, y_ptr: int, x_ptr: int, accumulate: int = 0, stream: int = 0) -> None:
+    _check(lib().lt_adjoint_camera(plan, cam, y_ptr, x_ptr, accumulate, stream))
+
+
+def lt_camera_cells(plan, cam: int) -> int:
+    k = c_int32()
+    _check(lib().lt_camera_cells(plan, cam, byref(k)))
+    return k.value
+
+
+def lt_plenoptic_stage1(plan, cam, x_ptr, fa_ptr, stream=0):
+    _check(lib().lt_plenoptic_stage1(plan, cam, x_ptr, fa_ptr, stream))
+
+
+def lt_plenoptic_stage1_adjoint(plan, cam, fa_ptr, x_ptr, accumulate=0, stream=0):
+    _check(lib().lt_plenoptic_stage1_adjoint(plan, cam, fa_ptr, x_ptr, accumulate, stream))
+
+
+def lt_plenoptic_stage2(plan, cam, fa_ptr, y_ptr, stream=0):
+    _check(lib().lt_plenoptic_stage2(plan, cam, fa_ptr, y_ptr, stream))
+
+
+def lt_plenoptic_stage2_adjoint(plan, cam, y_ptr, fa_ptr, stream=0):
+    _check(lib().lt_plenoptic_stage2_adjoint(plan, cam, y_ptr, fa_ptr, stream))
+
+
+# ---------------------------------------------------------------------------
+# torch convenience wrapper (plumbing: allocation and the current stream)
+# ---------------------------------------------------------------------------
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev_f32(t, numel, what):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{what} must be a contiguous float32 CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+class Plan:
+    """Owner of an lt_plan handle for a volume and a list of cameras."""
+
+    def __init__(self, vol: inputs.Volume, cams, frames: int = 1):
+        self.vol = vol
+        self.cams = list(cams)
+        self.frames = frames
+        self.handle = lt_plan_create(vol, self.cams, frames)
+        self.nvox, self.offsets = lt_plan_sizes(self.handle, len(self.cams))
+        self.m_total = self.offsets[-1]
+        self.cells = [lt_camera_cells(self.handle, c) for c in range(len(self.cams))]
+
+    def close(self):
+        if self.handle is not None:
+            lt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_x(self):
+        import torch
+        return torch.empty(self.frames, self.nvox, device="cuda", dtype=torch.float32)
+
+    def new_y(self):
+        import torch
+        return torch.empty(self.frames, self.m_total, device="cuda", dtype=torch.float32)
+
+    def forward(self, x, y=None):
+        y = self.new_y() if y is None else y
+        lt_forward(self.handle, _dev_f32(x, self.frames * self.nvox, "x"),
+                   _dev_f32(y, self.frames * self.m_total, "y"), _stream())
+        return y
+
+    def adjoint(self, y, x=None):
+        x = self.new_x() if x is None else x
+        lt_adjoint(self.handle, _dev_f32(y, self.frames * self.m_total, "y"),
+                   _dev_f32(x, self.frames * self.nvox, "x"), _stream())
+        return x
+
+    def forward_camera(self, cam, x, y=None):
+        import torch
+        m = self.offsets[cam + 1] - self.offsets[cam]
+        y = torch.empty(self.frames, m, device="cuda", dtype=torch.float32) if y is None else y
+        lt_forward_camera(self.handle, cam, _dev_f32(x, self.frames * self.nvox, "x"),
+                          _dev_f32(y, self.frames * m, "y"), _stream())
+        return y
+
+    def adjoint_camera(self, cam, y, x=None, accumulate=False):
+        m = self.offsets[cam + 1] - self.offsets[cam]
+        x = self.new_x() if x is None else x
+        lt_adjoint_camera(self.handle, cam, _dev_f32(y, self.frames * m, "y"),
+                          _dev_f32(x, self.frames * self.nvox, "x"), int(accumulate), _stream())
+        return x
+
+    def array_shape(self, cam):
+        c = self.cams[cam]
+        return (self.frames, self.cells[cam], c.arr_nt, c.arr_ns)
+
+    def stage1(self, cam, x, fa=None):
+        import torch
+        shp = self.array_shape(cam)
+        fa = torch.empty(shp, device="cuda", dtype=torch.float32) if fa is None else fa
+        lt_plenoptic_stage1(self.handle, cam, _dev_f32(x, self.frames * self.nvox, "x"),
+                            _dev_f32(fa, int(np.prod(shp)), "fa"), _stream())
+        return fa
+
+    def stage1_adjoint(self, cam, fa, x=None, accumulate=False):
+        shp = self.array_shape(cam)
+        x = self.new_x() if x is None else x
+        lt_plenoptic_stage1_adjoint(self.handle, cam, _dev_f32(fa, int(np.prod(shp)), "fa"),
+                                    _dev_f32(x, self.frames * self.nvox, "x"), int(accumulate), _stream())
+        return x
+
+    def stage2(self, cam, fa, y=None):
+        import torch
+        shp = self.array_shape(cam)
+        m = self.offsets[cam + 1] - self.offsets[cam]
+        y = torch.empty(self.frames, m, device="cuda", dtype=torch.float32) if y is None else y
+        lt_plenoptic_stage2(self.handle, cam, _dev_f32(fa, int(np.prod(shp)), "fa"),
+                            _dev_f32(y, self.frames * m, "y"), _stream())
+        return y
+
+    def stage2_adjoint(self, cam, y, fa=None):
+        import torch
+        shp = self.array_shape(cam)
+        m = self.offsets[cam + 1] - self.offsets[cam]
+        fa = torch.empty(shp, device="cuda", dtype=torch.float32) if fa is None else fa
+        lt_plenoptic_stage2_adjoint(self.handle, cam, _dev_f32(y, self.frames * m, "y"),
+                                    _dev_f32(fa, int(np.prod(shp)), "fa"), _stream())
+        return fa

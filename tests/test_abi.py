@@ -1,0 +1,68 @@
+"""The C-ABI library loads, exports every entry point include/*.h declares, and
+rejects invalid descriptors on the host (no GPU needed for any of this)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1812_03358_b300 import build, inputs as I, lt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(lt_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def library():
+    build.build()
+    return lt.lib()
+
+
+def test_every_declared_symbol_is_exported(library):
+    names = declared_symbols()
+    assert "lt_forward" in names and "lt_adjoint" in names and "lt_plan_create" in names
+    missing = [n for n in names if not hasattr(library, n)]
+    assert not missing, missing
+
+
+def test_only_declared_symbols_are_exported(library):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", lt.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    ours = {n for n in exported if n.startswith("lt_")}
+    assert ours == set(declared_symbols())
+
+
+def test_invalid_descriptors_rejected_on_host(library):
+    vol, cam = I.config_single_small()
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_create(I.Volume(0, 4, 4, 1, 1, 1), [cam])
+    assert e.value.status == lt.LT_EINVAL and "positive" in str(e.value)
+    bad = I.Camera(**{**cam.__dict__, "f_main": -1.0})
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_create(vol, [bad])
+    assert e.value.status == lt.LT_EINVAL
+    near = I.Camera(**{**cam.__dict__, "d_obj": 10.0})
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_create(vol, [near])
+    assert e.value.status == lt.LT_EINVAL and "main lens" in str(e.value)
+    _, pc = I.config_plenoptic()
+    wide = I.Camera(**{**pc.__dict__, "mla_radius": pc.mla_pitch})
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_create(vol, [wide])
+    assert e.value.status == lt.LT_EINVAL and "radius" in str(e.value)
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_create(vol, [cam], n_frames=0)
+    assert e.value.status == lt.LT_EINVAL
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_sizes(None, 1)
+    assert e.value.status == lt.LT_EINVAL
