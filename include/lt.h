@@ -133,6 +133,83 @@ LT_API lt_status lt_plenoptic_stage2(lt_plan* plan, int32_t cam, const float* fa
 LT_API lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, const float* y_cam, float* fa,
                                       void* stream);
 
+/* Analytic work counts of one camera for one frame, computed on the host in
+ * float64 from the plan's footprints (used for throughput and roofline
+ * figures).  A ray-sample is one (beam, slice) pair: a beam is a target pixel
+ * and an angular cell (Sec. II-B); stage 1 = slices -> detector (single lens)
+ * or array plane (plenoptic), stage 2 = array plane -> detector (plenoptic,
+ * one sample per detector pixel and cell).  nnz counts the nonzero matrix
+ * entries each stage evaluates (the separable s x t footprint products). */
+typedef struct {
+  int64_t n_cells;          /* K                                              */
+  int64_t stage1_samples;   /* target pixels x K x nz                         */
+  int64_t stage2_samples;   /* det pixels x K (plenoptic), else 0             */
+  int64_t ray_samples;      /* stage1_samples + stage2_samples                */
+  int64_t hit_samples;      /* stage-1 samples whose footprint meets the volume */
+  int64_t stage1_nnz;       /* nonzero (pixel, cell, voxel) entries of stage 1 */
+  int64_t stage2_nnz;       /* nonzero (pixel, cell, array pixel) entries      */
+} lt_camera_stats;
+
+LT_API lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_camera_stats* out);
+
+/* ------------------------------------------------------------------------
+ * Reconstruction (Sec. V, Table V): penalised weighted non-negative least
+ * squares with unknown camera gains (eq. pls), solved by FISTA with the
+ * diagonal majoriser D = diag(sum_c A_c^T W_c A_c 1) (Appendix A).  Every
+ * frame of the plan is an independent problem.
+ * ------------------------------------------------------------------------ */
+typedef struct lt_recon lt_recon;
+
+typedef struct {
+  double beta;            /* regulariser weight (eq. reg)                       */
+  double nu;              /* l1 weight; x = [w - nu]_+ as in Table V            */
+  int32_t psi;            /* 0: psi(t) = t^2/2; 1: delta^2 (sqrt(1+(t/delta)^2)-1) */
+  double psi_delta;       /* delta of the hyperbola                             */
+  double reg_scale;       /* curvature bound: 26 (as printed) or 36 (exact)     */
+  int32_t estimate_gains; /* 1: gamma_c (c > 0) per Table V step 1b; 0: all 1   */
+} lt_recon_params;
+
+/* Copies y (device [F][M]) and the optional weights w (device [F][M], NULL =
+ * W = I) and computes D (one forward and one adjoint).  x0: optional device
+ * [F][N] initial x = z (NULL = 0, as in Table V).  Allocates the solver state
+ * on the device.  Errors: LT_EINVAL (NULL plan/y/params, negative beta/nu,
+ * psi_delta <= 0 with psi = 1), LT_ENOMEM, LT_ECUDA. */
+LT_API lt_status lt_recon_create(lt_plan* plan, const float* y, const float* w,
+                                 const lt_recon_params* params, const float* x0,
+                                 void* stream, lt_recon** out);
+
+/* Runs n_iter iterations of Table V on the stream.  The first call captures
+ * one iteration into a CUDA graph (one per z buffer parity) that later calls
+ * replay; no host synchronisation happens inside. */
+LT_API lt_status lt_recon_iterate(lt_recon* rec, int32_t n_iter, void* stream);
+
+/* Copies the current x (device [F][N], may be NULL), and, synchronising the
+ * stream, the gains (host [F][n_cams] or NULL) and the data-fit term
+ * 1/2 sum_c ||A_c z - gamma_c y_c||^2_W of the last iteration (host [F] or
+ * NULL; 0 before the first iteration). */
+LT_API lt_status lt_recon_get(lt_recon* rec, float* x, double* gains, double* data_fit,
+                              void* stream);
+
+/* Replaces the measurements (and weights, if w is not NULL; the majoriser D
+ * is then recomputed) of an existing reconstruction without resetting x, z,
+ * t or the iteration count: for streams of frames where each new image warm
+ * starts from the previous estimate.  Asynchronous on the stream. */
+LT_API lt_status lt_recon_set_data(lt_recon* rec, const float* y, const float* w, void* stream);
+
+/* Number of kernel launches one iteration performs (the nodes of its graph). */
+LT_API lt_status lt_recon_kernels_per_iteration(lt_recon* rec, int32_t* n);
+
+/* Iterations completed so far. */
+LT_API lt_status lt_recon_iterations(const lt_recon* rec, int64_t* n_iter);
+
+/* Checkpoint / resume: the solver state (x, z, t, gains, iteration count) as
+ * an opaque host byte buffer of lt_recon_state_size bytes.  Synchronous. */
+LT_API lt_status lt_recon_state_size(const lt_recon* rec, int64_t* bytes);
+LT_API lt_status lt_recon_get_state(lt_recon* rec, void* host_buf);
+LT_API lt_status lt_recon_set_state(lt_recon* rec, const void* host_buf);
+
+LT_API lt_status lt_recon_destroy(lt_recon* rec);
+
 /* Description of the last error on the calling thread ("" if none). */
 LT_API const char* lt_last_error(void);
 

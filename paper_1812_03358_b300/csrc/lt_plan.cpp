@@ -507,6 +507,89 @@ extern "C" lt_status lt_camera_cells(const lt_plan* plan, int32_t cam, int32_t* 
 }
 
 // ---------------------------------------------------------------------------
+// analytic work counts
+// ---------------------------------------------------------------------------
+
+// For target pixels [i0, i1] of a footprint, the number of source cells in
+// [0, n_src) each footprint overlaps (open interval (xi - Q, xi + Q)),
+// summed (nnz) and the number of pixels with at least one (hits).
+static void count_cells(const lt::Footprint& f, long long i0, long long i1, long long c_lo,
+                        long long c_hi, long long* nnz, long long* hits) {
+  *nnz = 0;
+  *hits = 0;
+  for (long long i = i0; i <= i1; ++i) {
+    const double xi = f.C0 + f.C1 * (double)i;
+    long long jl = (long long)std::floor(xi - f.Q - 0.5) + 1;
+    long long jh = (long long)std::ceil(xi + f.Q + 0.5) - 1;
+    jl = std::max(jl, c_lo);
+    jh = std::min(jh, c_hi);
+    if (jh >= jl) {
+      *nnz += jh - jl + 1;
+      *hits += 1;
+    }
+  }
+}
+
+extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_camera_stats* out) {
+  clear_error();
+  if (!plan || !out || cam < 0 || cam >= (int)plan->cams.size())
+    return set_error(LT_EINVAL, "bad plan/camera/out argument");
+  const CameraPlan& c = plan->cams[cam];
+  const lt_camera_desc& d = c.desc;
+  const lt_volume_desc& v = plan->vol;
+  const bool plen = d.kind == LT_CAM_PLENOPTIC;
+  const int tns = plen ? d.arr_ns : d.det_ns, tnt = plen ? d.arr_nt : d.det_nt;
+  const double tps = plen ? d.arr_ps : d.det_ps, tpt = plen ? d.arr_pt : d.det_pt;
+  const double d_img = plen ? d.d_lens_mla : d.d_lens_det;
+  lt_camera_stats st{};
+  st.n_cells = c.K;
+  st.stage1_samples = (int64_t)tns * tnt * c.K * v.nz;
+  for (int k = 0; k < c.K; ++k)
+    for (int n = 0; n < v.nz; ++n) {
+      Row P, L;
+      slice_rows(d.d_obj + centre(n, v.nz, v.dz), d_img, d.f_main, &P, &L);
+      Footprint fs, ft;
+      footprint(L, P, c.cells[k].sk, c.cells[k].d0s, centre(0, tns, tps), tps, centre(0, v.nx, v.dx), v.dx,
+                d.basis, &fs);
+      footprint(L, P, c.cells[k].tk, c.cells[k].d0t, centre(0, tnt, tpt), tpt, centre(0, v.ny, v.dy), v.dy,
+                d.basis, &ft);
+      long long ns_, hs, nt_, ht;
+      count_cells(fs, 0, tns - 1, 0, v.nx - 1, &ns_, &hs);
+      count_cells(ft, 0, tnt - 1, 0, v.ny - 1, &nt_, &ht);
+      st.stage1_nnz += ns_ * nt_;
+      st.hit_samples += hs * ht;
+    }
+  if (plen) {
+    st.stage2_samples = (int64_t)d.det_ns * d.det_nt * c.K;
+    const int mns = d.mla_ns, mnt = d.mla_nt;
+    std::vector<int2> cols(mns), rows(mnt);
+    cudaMemcpy(cols.data(), c.d_cols, mns * sizeof(int2), cudaMemcpyDeviceToHost);
+    cudaMemcpy(rows.data(), c.d_rows, mnt * sizeof(int2), cudaMemcpyDeviceToHost);
+    for (int k = 0; k < c.K; ++k)
+      for (int mt = 0; mt < mnt; ++mt)
+        for (int ms = 0; ms < mns; ++ms) {
+          if (cols[ms].y <= cols[ms].x || rows[mt].y <= rows[mt].x) continue;
+          const double f = c.focal[(size_t)mt * mns + ms];
+          Row Ps, Ls, Pt, Lt;
+          lenslet_rows(d.d_mla_det, d.d_lens_mla, f, centre(ms, mns, d.mla_pitch), &Ps, &Ls);
+          lenslet_rows(d.d_mla_det, d.d_lens_mla, f, centre(mt, mnt, d.mla_pitch), &Pt, &Lt);
+          Footprint fs, ft;
+          footprint(Ls, Ps, c.cells[k].sk, c.cells[k].d0s, centre(0, d.det_ns, d.det_ps), d.det_ps,
+                    centre(0, d.arr_ns, d.arr_ps), d.arr_ps, d.basis, &fs);
+          footprint(Lt, Pt, c.cells[k].tk, c.cells[k].d0t, centre(0, d.det_nt, d.det_pt), d.det_pt,
+                    centre(0, d.arr_nt, d.arr_pt), d.arr_pt, d.basis, &ft);
+          long long ns_, hs, nt_, ht;
+          count_cells(fs, 0, d.det_ns - 1, cols[ms].x, cols[ms].y - 1, &ns_, &hs);
+          count_cells(ft, 0, d.det_nt - 1, rows[mt].x, rows[mt].y - 1, &nt_, &ht);
+          st.stage2_nnz += ns_ * nt_;
+        }
+  }
+  st.ray_samples = st.stage1_samples + st.stage2_samples;
+  *out = st;
+  return LT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // operators
 // ---------------------------------------------------------------------------
 

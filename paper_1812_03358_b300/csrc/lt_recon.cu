@@ -1,0 +1,491 @@
+// Reconstruction of Sec. V (Table V): FISTA on the penalised weighted
+// non-negative least-squares problem with camera gains (eq. pls), the
+// 26-neighbour regulariser (eq. reg) and the diagonal majoriser of Appendix A.
+//
+// All solver state lives on the device: the gains and the FISTA scalars are
+// computed by kernels, so one iteration is a fixed launch sequence that is
+// captured once into a CUDA graph and replayed (no host round trip for the
+// gain inner products, unlike the paper's implementation).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lt.h"
+#include "lt_host.h"
+
+namespace lt {
+namespace {
+
+struct Scalars {
+  double t;        // t^{(n)}
+  double mom;      // (t^{(n)} - 1) / t^{(n+1)} for the update in flight
+  long long iter;  // completed iterations
+};
+
+constexpr int RED_BLOCKS = 148;
+constexpr int RED_THREADS = 256;
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// part[(f*C + c)*RED_BLOCKS + b] = sum over block b's share of camera c's
+// pixels of w * a * b (w = 1 if NULL).  grid = (RED_BLOCKS, F).
+__global__ void __launch_bounds__(RED_THREADS)
+dot_partials(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ w,
+             long long off, long long len, long long m_total, int C, int c, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const long long base = (long long)blockIdx.y * m_total + off;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double wi = w ? (double)w[base + i] : 1.0;
+    acc += wi * (double)a[base + i] * (double)b[base + i];
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[((long long)blockIdx.y * C + c) * RED_BLOCKS + blockIdx.x] = acc;
+}
+
+// Table V step 1b (gamma_c = y^T W p / y^T W y, c > 0) and the FISTA scalars
+// t^{(n+1)} = (1 + sqrt(1 + 4 t^2)) / 2, mom = (t^{(n)} - 1) / t^{(n+1)}.
+__global__ void finalize_gains(const double* __restrict__ part, const double* __restrict__ ywy,
+                               double* __restrict__ gains, int F, int C, int estimate,
+                               Scalars* __restrict__ sc) {
+  for (int idx = threadIdx.x; idx < F * C; idx += blockDim.x) {
+    const int c = idx % C;
+    if (c == 0 || !estimate) {
+      gains[idx] = 1.0;
+      continue;
+    }
+    double s = 0.0;
+    for (int b = 0; b < RED_BLOCKS; ++b) s += part[(long long)idx * RED_BLOCKS + b];
+    gains[idx] = ywy[idx] > 0.0 ? s / ywy[idx] : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    const double t = sc->t;
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sc->mom = (t - 1.0) / tn;
+    sc->t = tn;
+    sc->iter += 1;
+  }
+}
+
+// r = W (p - gamma_c y) over camera c's pixels; fit partials of
+// 1/2 sum W (p - gamma y)^2.  grid = (RED_BLOCKS, F).
+__global__ void __launch_bounds__(RED_THREADS)
+residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const float* __restrict__ p,
+                float* __restrict__ r, const double* __restrict__ gains, long long off, long long len,
+                long long m_total, int C, int c, double* __restrict__ fit_part) {
+  __shared__ double sh[32];
+  const long long base = (long long)blockIdx.y * m_total + off;
+  const float g = (float)gains[blockIdx.y * C + c];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float d = p[base + i] - g * y[base + i];
+    const float wi = w ? w[base + i] : 1.0f;
+    r[base + i] = wi * d;
+    acc += (double)wi * (double)d * (double)d;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) fit_part[((long long)blockIdx.y * C + c) * RED_BLOCKS + blockIdx.x] = 0.5 * acc;
+}
+
+// Table V step 3: w = [z - (D + s beta)^-1 (g + grad R(z))]_+, x' = [w - nu]_+,
+// z' = x' + mom (x' - x).  grad R(z)_j = beta sum_{l in N26(j)} psi'(z_j - z_l).
+__global__ void __launch_bounds__(256)
+update_kernel(float* __restrict__ x, const float* __restrict__ z, float* __restrict__ zn,
+              const float* __restrict__ g, const float* __restrict__ D, int nx, int ny, int nz,
+              long long nvox, float beta, float nu, int psi, float inv_delta, float sbeta,
+              const Scalars* __restrict__ sc) {
+  const int ix = blockIdx.x * 32 + threadIdx.x;
+  const int iy = blockIdx.y * 8 + threadIdx.y;
+  const int iz = blockIdx.z % nz;
+  const int f = blockIdx.z / nz;
+  if (ix >= nx || iy >= ny) return;
+  const float* zf = z + (long long)f * nvox;
+  const long long j = ((long long)iz * ny + iy) * nx + ix;
+  const float zc = zf[j];
+  float reg = 0.0f;
+  if (beta != 0.0f) {
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int kz = iz + dz;
+      if (kz < 0 || kz >= nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int ky = iy + dy;
+        if (ky < 0 || ky >= ny) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int kx = ix + dx;
+          if (kx < 0 || kx >= nx || (dx == 0 && dy == 0 && dz == 0)) continue;
+          const float d = zc - __ldg(zf + ((long long)kz * ny + ky) * nx + kx);
+          reg += psi ? d * rsqrtf(1.0f + (d * inv_delta) * (d * inv_delta)) : d;
+        }
+      }
+    }
+    reg *= beta;
+  }
+  const long long jf = (long long)f * nvox + j;
+  const float den = D[jf] + sbeta;
+  const float wv = den > 0.0f ? fmaxf(zc - (g[jf] + reg) / den, 0.0f) : 0.0f;
+  const float xn = fmaxf(wv - nu, 0.0f);
+  const float mom = (float)sc->mom;
+  zn[jf] = xn + mom * (xn - x[jf]);
+  x[jf] = xn;
+}
+
+__global__ void finalize_dots(const double* __restrict__ part, double* __restrict__ out, int n) {
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < RED_BLOCKS; ++b) acc += part[(long long)idx * RED_BLOCKS + b];
+    out[idx] = acc;
+  }
+}
+
+__global__ void fill_kernel(float* a, long long n, float v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+__global__ void mul_kernel(float* out, const float* a, const float* b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = b ? a[i] * b[i] : a[i];
+}
+
+}  // namespace
+}  // namespace lt
+
+using namespace lt;
+
+struct lt_recon {
+  lt_plan* plan = nullptr;
+  lt_recon_params prm{};
+  int F = 0, C = 0;
+  int64_t N = 0, M = 0;
+  float *y = nullptr, *w = nullptr, *p = nullptr, *r = nullptr, *g = nullptr, *D = nullptr, *x = nullptr;
+  float* z[2] = {nullptr, nullptr};
+  double *ywy = nullptr, *gains = nullptr, *part = nullptr, *fit_part = nullptr;
+  Scalars* sc = nullptr;
+  int zsel = 0;
+  int64_t iters = 0;
+  bool captured = false;
+  int kernels_per_iter = 0;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaStream_t cap = nullptr;
+};
+
+static void recon_free(lt_recon* R) {
+  if (!R) return;
+  for (int i = 0; i < 2; ++i)
+    if (R->exec[i]) cudaGraphExecDestroy(R->exec[i]);
+  if (R->cap) cudaStreamDestroy(R->cap);
+  void* bufs[] = {R->y, R->w, R->p, R->r, R->g, R->D, R->x, R->z[0], R->z[1],
+                  R->ywy, R->gains, R->part, R->fit_part, R->sc};
+  for (void* b : bufs) cudaFree(b);
+  delete R;
+}
+
+template <typename T>
+static lt_status dalloc(T** p, size_t n, const char* what) {
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return set_error(LT_ENOMEM, "cudaMalloc(%s, %zu bytes): %s", what, n * sizeof(T), cudaGetErrorString(e));
+  }
+  return LT_OK;
+}
+
+static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 16); }
+
+// One iteration of Table V from z[sel] to z[1-sel].
+static lt_status recon_step(lt_recon* R, int sel, cudaStream_t st) {
+  lt_plan* P = R->plan;
+  const float* z = R->z[sel];
+  for (int c = 0; c < R->C; ++c) {  // step 1a: p_c = A_c z
+    lt_status s = camera_forward(P, c, z, R->p + P->cams[c].offset, R->M, st);
+    if (s != LT_OK) return s;
+  }
+  const int est = R->prm.estimate_gains && R->C > 1;
+  if (est)  // step 1b inner products
+    for (int c = 1; c < R->C; ++c)
+      dot_partials<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
+          R->y, R->p, R->w, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->part);
+  finalize_gains<<<1, 256, 0, st>>>(R->part, R->ywy, R->gains, R->F, R->C, est, R->sc);
+  for (int c = 0; c < R->C; ++c)  // W (p - gamma y)
+    residual_kernel<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
+        R->y, R->w, R->p, R->r, R->gains, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->fit_part);
+  for (int c = 0; c < R->C; ++c) {  // step 1c + 2: g = sum_c A_c^T r_c
+    lt_status s = camera_adjoint(P, c, R->r + P->cams[c].offset, R->M, R->g, c > 0, st);
+    if (s != LT_OK) return s;
+  }
+  const lt_volume_desc& v = P->vol;
+  dim3 grid((v.nx + 31) / 32, (v.ny + 7) / 8, v.nz * R->F);
+  const float beta = (float)R->prm.beta;
+  update_kernel<<<grid, dim3(32, 8), 0, st>>>(
+      R->x, z, R->z[1 - sel], R->g, R->D, v.nx, v.ny, v.nz, R->N, beta, (float)R->prm.nu, R->prm.psi,
+      R->prm.psi == 1 ? (float)(1.0 / R->prm.psi_delta) : 1.0f, (float)(R->prm.reg_scale * R->prm.beta), R->sc);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "reconstruction iteration");
+}
+
+// Copies y (and w), recomputes y^T W y per (frame, camera) on the device and,
+// if the weights changed, the majoriser D = diag(sum_c A_c^T W_c A_c 1).
+static lt_status load_data(lt_recon* R, const float* y, const float* w, bool new_weights, cudaStream_t st) {
+  lt_plan* P = R->plan;
+  const size_t FN = (size_t)R->F * R->N, FM = (size_t)R->F * R->M;
+  cudaMemcpyAsync(R->y, y, FM * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (w && R->w) cudaMemcpyAsync(R->w, w, FM * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  lt_status s = LT_OK;
+  if (new_weights) {
+    fill_kernel<<<grid_for(FN), 256, 0, st>>>(R->g, (long long)FN, 1.0f);
+    for (int c = 0; c < R->C && s == LT_OK; ++c)
+      s = camera_forward(P, c, R->g, R->p + P->cams[c].offset, R->M, st);
+    mul_kernel<<<grid_for(FM), 256, 0, st>>>(R->r, R->p, R->w, (long long)FM);
+    for (int c = 0; c < R->C && s == LT_OK; ++c)
+      s = camera_adjoint(P, c, R->r + P->cams[c].offset, R->M, R->D, c > 0, st);
+    if (s != LT_OK) return s;
+  }
+  for (int c = 0; c < R->C; ++c)
+    dot_partials<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(R->y, R->y, R->w, P->cams[c].offset,
+                                                                 P->cams[c].M, R->M, R->C, c, R->part);
+  finalize_dots<<<1, 256, 0, st>>>(R->part, R->ywy, R->F * R->C);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "loading measurements");
+}
+
+extern "C" lt_status lt_recon_create(lt_plan* plan, const float* y, const float* w,
+                                     const lt_recon_params* params, const float* x0, void* stream,
+                                     lt_recon** out) {
+  clear_error();
+  if (!out) return set_error(LT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!plan || !y || !params) return set_error(LT_EINVAL, "plan, y and params are required");
+  const lt_recon_params& q = *params;
+  if (!(q.beta >= 0.0) || !(q.nu >= 0.0) || !std::isfinite(q.beta) || !std::isfinite(q.nu))
+    return set_error(LT_EINVAL, "beta and nu must be finite and non-negative");
+  if (q.psi != 0 && q.psi != 1) return set_error(LT_EINVAL, "psi must be 0 (quadratic) or 1 (hyperbola)");
+  if (q.psi == 1 && !(q.psi_delta > 0.0)) return set_error(LT_EINVAL, "psi_delta must be positive");
+  if (!(q.reg_scale >= 0.0)) return set_error(LT_EINVAL, "reg_scale must be non-negative");
+  cudaStream_t st = (cudaStream_t)stream;
+  lt_recon* R = new (std::nothrow) lt_recon();
+  if (!R) return set_error(LT_ENOMEM, "host allocation failed");
+  R->plan = plan;
+  R->prm = q;
+  R->F = plan->frames;
+  R->C = (int)plan->cams.size();
+  R->N = plan->nvox;
+  R->M = plan->m_total;
+  const size_t FN = (size_t)R->F * R->N, FM = (size_t)R->F * R->M;
+  lt_status s;
+  if ((s = dalloc(&R->y, FM, "y")) || (w && (s = dalloc(&R->w, FM, "w"))) || (s = dalloc(&R->p, FM, "p")) ||
+      (s = dalloc(&R->r, FM, "r")) || (s = dalloc(&R->g, FN, "g")) || (s = dalloc(&R->D, FN, "D")) ||
+      (s = dalloc(&R->x, FN, "x")) || (s = dalloc(&R->z[0], FN, "z")) || (s = dalloc(&R->z[1], FN, "z")) ||
+      (s = dalloc(&R->ywy, (size_t)R->F * R->C, "ywy")) || (s = dalloc(&R->gains, (size_t)R->F * R->C, "gains")) ||
+      (s = dalloc(&R->part, (size_t)R->F * R->C * RED_BLOCKS, "partials")) ||
+      (s = dalloc(&R->fit_part, (size_t)R->F * R->C * RED_BLOCKS, "fit partials")) ||
+      (s = dalloc(&R->sc, 1, "scalars"))) {
+    recon_free(R);
+    return s;
+  }
+  s = load_data(R, y, w, true, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (s != LT_OK || e != cudaSuccess) {
+    recon_free(R);
+    return s != LT_OK ? s : cuda_error(e, "reconstruction setup");
+  }
+  std::vector<double> g0((size_t)R->F * R->C, 0.0);
+  for (int f = 0; f < R->F; ++f) g0[(size_t)f * R->C] = 1.0;   // gamma_1 = 1, gamma_c = 0
+  if (!q.estimate_gains)
+    for (auto& v : g0) v = 1.0;
+  Scalars sc0{1.0, 0.0, 0};
+  cudaMemcpy(R->gains, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(R->sc, &sc0, sizeof(sc0), cudaMemcpyHostToDevice);
+  cudaMemset(R->fit_part, 0, (size_t)R->F * R->C * RED_BLOCKS * sizeof(double));
+  if (x0) {
+    cudaMemcpy(R->x, x0, FN * sizeof(float), cudaMemcpyDeviceToDevice);
+    cudaMemcpy(R->z[0], x0, FN * sizeof(float), cudaMemcpyDeviceToDevice);
+  } else {
+    cudaMemset(R->x, 0, FN * sizeof(float));
+    cudaMemset(R->z[0], 0, FN * sizeof(float));
+  }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    recon_free(R);
+    return cuda_error(e, "reconstruction setup");
+  }
+  *out = R;
+  return LT_OK;
+}
+
+static lt_status capture(lt_recon* R) {
+  cudaError_t e = cudaStreamCreateWithFlags(&R->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_error(e, "capture stream");
+  for (int sel = 0; sel < 2; ++sel) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(R->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_error(e, "begin capture");
+    lt_status s = recon_step(R, sel, R->cap);
+    e = cudaStreamEndCapture(R->cap, &graph);
+    if (s != LT_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "end capture");
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    cudaGraphGetNodes(graph, nodes.data(), &n_nodes);
+    int nk = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    R->kernels_per_iter = nk;
+    e = cudaGraphInstantiate(&R->exec[sel], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_error(e, "graph instantiate");
+  }
+  R->captured = true;
+  return LT_OK;
+}
+
+extern "C" lt_status lt_recon_iterate(lt_recon* R, int32_t n_iter, void* stream) {
+  clear_error();
+  if (!R) return set_error(LT_EINVAL, "recon is NULL");
+  if (n_iter < 0) return set_error(LT_EINVAL, "n_iter must be non-negative");
+  if (!R->captured) {
+    lt_status s = capture(R);
+    if (s != LT_OK) return s;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < n_iter; ++i) {
+    cudaError_t e = cudaGraphLaunch(R->exec[R->zsel], st);
+    if (e != cudaSuccess) return cuda_error(e, "graph launch");
+    R->zsel = 1 - R->zsel;
+    R->iters++;
+  }
+  return LT_OK;
+}
+
+extern "C" lt_status lt_recon_get(lt_recon* R, float* x, double* gains, double* data_fit, void* stream) {
+  clear_error();
+  if (!R) return set_error(LT_EINVAL, "recon is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t FN = (size_t)R->F * R->N;
+  if (x) cudaMemcpyAsync(x, R->x, FN * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (gains || data_fit) {
+    std::vector<double> g((size_t)R->F * R->C), fp((size_t)R->F * R->C * RED_BLOCKS);
+    cudaMemcpyAsync(g.data(), R->gains, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(fp.data(), R->fit_part, fp.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "lt_recon_get");
+    if (gains) std::memcpy(gains, g.data(), g.size() * sizeof(double));
+    if (data_fit)
+      for (int f = 0; f < R->F; ++f) {
+        double acc = 0.0;
+        for (int c = 0; c < R->C; ++c)
+          for (int b = 0; b < RED_BLOCKS; ++b) acc += fp[((size_t)f * R->C + c) * RED_BLOCKS + b];
+        data_fit[f] = acc;
+      }
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "lt_recon_get");
+}
+
+extern "C" lt_status lt_recon_iterations(const lt_recon* R, int64_t* n_iter) {
+  clear_error();
+  if (!R || !n_iter) return set_error(LT_EINVAL, "NULL argument");
+  *n_iter = R->iters;
+  return LT_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  int64_t F, N, C, iters;
+};
+constexpr uint64_t kStateMagic = 0x4c54524543535431ull;  // "LTRECST1"
+}  // namespace
+
+extern "C" lt_status lt_recon_state_size(const lt_recon* R, int64_t* bytes) {
+  clear_error();
+  if (!R || !bytes) return set_error(LT_EINVAL, "NULL argument");
+  *bytes = (int64_t)(sizeof(StateHeader) + 2 * (size_t)R->F * R->N * sizeof(float) +
+                     (size_t)R->F * R->C * sizeof(double) + sizeof(Scalars));
+  return LT_OK;
+}
+
+extern "C" lt_status lt_recon_get_state(lt_recon* R, void* host_buf) {
+  clear_error();
+  if (!R || !host_buf) return set_error(LT_EINVAL, "NULL argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "lt_recon_get_state");
+  char* b = (char*)host_buf;
+  StateHeader h{kStateMagic, R->F, R->N, R->C, R->iters};
+  std::memcpy(b, &h, sizeof(h));
+  b += sizeof(h);
+  const size_t FN = (size_t)R->F * R->N * sizeof(float);
+  cudaMemcpy(b, R->x, FN, cudaMemcpyDeviceToHost);
+  b += FN;
+  cudaMemcpy(b, R->z[R->zsel], FN, cudaMemcpyDeviceToHost);
+  b += FN;
+  cudaMemcpy(b, R->gains, (size_t)R->F * R->C * sizeof(double), cudaMemcpyDeviceToHost);
+  b += (size_t)R->F * R->C * sizeof(double);
+  e = cudaMemcpy(b, R->sc, sizeof(Scalars), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "lt_recon_get_state");
+}
+
+extern "C" lt_status lt_recon_set_state(lt_recon* R, const void* host_buf) {
+  clear_error();
+  if (!R || !host_buf) return set_error(LT_EINVAL, "NULL argument");
+  const char* b = (const char*)host_buf;
+  StateHeader h;
+  std::memcpy(&h, b, sizeof(h));
+  if (h.magic != kStateMagic || h.F != R->F || h.N != R->N || h.C != R->C)
+    return set_error(LT_EINVAL, "state buffer does not match this reconstruction");
+  b += sizeof(h);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "lt_recon_set_state");
+  const size_t FN = (size_t)R->F * R->N * sizeof(float);
+  cudaMemcpy(R->x, b, FN, cudaMemcpyHostToDevice);
+  b += FN;
+  cudaMemcpy(R->z[R->zsel], b, FN, cudaMemcpyHostToDevice);
+  b += FN;
+  cudaMemcpy(R->gains, b, (size_t)R->F * R->C * sizeof(double), cudaMemcpyHostToDevice);
+  b += (size_t)R->F * R->C * sizeof(double);
+  e = cudaMemcpy(R->sc, b, sizeof(Scalars), cudaMemcpyHostToDevice);
+  R->iters = h.iters;
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "lt_recon_set_state");
+}
+
+extern "C" lt_status lt_recon_destroy(lt_recon* R) {
+  if (!R) return LT_OK;
+  cudaDeviceSynchronize();
+  recon_free(R);
+  return LT_OK;
+}
+
+extern "C" lt_status lt_recon_set_data(lt_recon* R, const float* y, const float* w, void* stream) {
+  clear_error();
+  if (!R || !y) return set_error(LT_EINVAL, "recon and y are required");
+  if (w && !R->w) return set_error(LT_EINVAL, "this reconstruction was created without weights");
+  return load_data(R, y, w, w != nullptr, (cudaStream_t)stream);
+}
+
+extern "C" lt_status lt_recon_kernels_per_iteration(lt_recon* R, int32_t* n) {
+  clear_error();
+  if (!R || !n) return set_error(LT_EINVAL, "NULL argument");
+  if (!R->captured) {
+    lt_status s = capture(R);
+    if (s != LT_OK) return s;
+  }
+  *n = R->kernels_per_iter;
+  return LT_OK;
+}

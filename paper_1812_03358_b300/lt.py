@@ -36,6 +36,17 @@ class lt_camera_desc(ctypes.Structure):
                 ("arr_ns", c_int32), ("arr_nt", c_int32), ("arr_ps", c_double), ("arr_pt", c_double)]
 
 
+class lt_recon_params(ctypes.Structure):
+    _fields_ = [("beta", c_double), ("nu", c_double), ("psi", c_int32), ("psi_delta", c_double),
+                ("reg_scale", c_double), ("estimate_gains", c_int32)]
+
+
+class lt_camera_stats(ctypes.Structure):
+    _fields_ = [("n_cells", c_int64), ("stage1_samples", c_int64), ("stage2_samples", c_int64),
+                ("ray_samples", c_int64), ("hit_samples", c_int64), ("stage1_nnz", c_int64),
+                ("stage2_nnz", c_int64)]
+
+
 class LtError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"lt status {status}: {msg}")
@@ -58,6 +69,18 @@ _SIGS = {
     "lt_plenoptic_stage1_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     "lt_plenoptic_stage2": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_plenoptic_stage2_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "lt_recon_create": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(lt_recon_params), c_void_p,
+                                  c_void_p, POINTER(c_void_p)]),
+    "lt_recon_iterate": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "lt_recon_get": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "lt_recon_iterations": (c_int32, [c_void_p, POINTER(c_int64)]),
+    "lt_recon_state_size": (c_int32, [c_void_p, POINTER(c_int64)]),
+    "lt_recon_get_state": (c_int32, [c_void_p, c_void_p]),
+    "lt_recon_set_state": (c_int32, [c_void_p, c_void_p]),
+    "lt_recon_destroy": (c_int32, [c_void_p]),
+    "lt_camera_stats_get": (c_int32, [c_void_p, c_int32, POINTER(lt_camera_stats)]),
+    "lt_recon_set_data": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lt_recon_kernels_per_iteration": (c_int32, [c_void_p, POINTER(c_int32)]),
     "lt_last_error": (c_char_p, []),
 }
 
@@ -163,6 +186,63 @@ def lt_plenoptic_stage2_adjoint(plan, cam, y_ptr, fa_ptr, stream=0):
     _check(lib().lt_plenoptic_stage2_adjoint(plan, cam, y_ptr, fa_ptr, stream))
 
 
+def lt_camera_stats_get(plan, cam: int) -> dict:
+    st = lt_camera_stats()
+    _check(lib().lt_camera_stats_get(plan, cam, byref(st)))
+    return {name: getattr(st, name) for name, _ in lt_camera_stats._fields_}
+
+
+def lt_recon_set_data(rec, y_ptr: int, w_ptr: int = 0, stream: int = 0) -> None:
+    _check(lib().lt_recon_set_data(rec, y_ptr, w_ptr or None, stream))
+
+
+def lt_recon_kernels_per_iteration(rec) -> int:
+    n = c_int32()
+    _check(lib().lt_recon_kernels_per_iteration(rec, byref(n)))
+    return n.value
+
+
+def lt_recon_create(plan, y_ptr: int, w_ptr: int, params: lt_recon_params, x0_ptr: int = 0,
+                    stream: int = 0) -> c_void_p:
+    h = c_void_p()
+    _check(lib().lt_recon_create(plan, y_ptr, w_ptr or None, byref(params), x0_ptr or None, stream, byref(h)))
+    return h
+
+
+def lt_recon_iterate(rec, n_iter: int, stream: int = 0) -> None:
+    _check(lib().lt_recon_iterate(rec, n_iter, stream))
+
+
+def lt_recon_get(rec, x_ptr: int, n_frames: int, n_cams: int, stream: int = 0):
+    gains = (c_double * (n_frames * n_cams))()
+    fit = (c_double * n_frames)()
+    _check(lib().lt_recon_get(rec, x_ptr or None, gains, fit, stream))
+    return np.array(gains).reshape(n_frames, n_cams), np.array(fit)
+
+
+def lt_recon_iterations(rec) -> int:
+    n = c_int64()
+    _check(lib().lt_recon_iterations(rec, byref(n)))
+    return n.value
+
+
+def lt_recon_get_state(rec) -> bytes:
+    n = c_int64()
+    _check(lib().lt_recon_state_size(rec, byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().lt_recon_get_state(rec, buf))
+    return buf.raw
+
+
+def lt_recon_set_state(rec, state: bytes) -> None:
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(lib().lt_recon_set_state(rec, buf))
+
+
+def lt_recon_destroy(rec) -> None:
+    _check(lib().lt_recon_destroy(rec))
+
+
 # ---------------------------------------------------------------------------
 # torch convenience wrapper (plumbing: allocation and the current stream)
 # ---------------------------------------------------------------------------
@@ -239,6 +319,9 @@ class Plan:
                           _dev_f32(x, self.frames * self.nvox, "x"), int(accumulate), _stream())
         return x
 
+    def stats(self, cam):
+        return lt_camera_stats_get(self.handle, cam)
+
     def array_shape(self, cam):
         c = self.cams[cam]
         return (self.frames, self.cells[cam], c.arr_nt, c.arr_ns)
@@ -275,3 +358,56 @@ class Plan:
         lt_plenoptic_stage2_adjoint(self.handle, cam, _dev_f32(y, self.frames * m, "y"),
                                     _dev_f32(fa, int(np.prod(shp)), "fa"), _stream())
         return fa
+
+
+class Recon:
+    """Owner of an lt_recon handle (Table V solver) for a Plan and measurements y."""
+
+    def __init__(self, plan: Plan, y, w=None, beta=0.0, nu=0.0, psi=0, psi_delta=1.0,
+                 reg_scale=26.0, estimate_gains=True, x0=None):
+        self.plan = plan
+        n = plan.frames * plan.m_total
+        prm = lt_recon_params(float(beta), float(nu), int(psi), float(psi_delta), float(reg_scale),
+                              int(bool(estimate_gains)))
+        self.handle = lt_recon_create(plan.handle, _dev_f32(y, n, "y"),
+                                      _dev_f32(w, n, "w") if w is not None else 0, prm,
+                                      _dev_f32(x0, plan.frames * plan.nvox, "x0") if x0 is not None else 0,
+                                      _stream())
+
+    def iterate(self, n_iter: int):
+        lt_recon_iterate(self.handle, n_iter, _stream())
+
+    def set_data(self, y, w=None):
+        n = self.plan.frames * self.plan.m_total
+        lt_recon_set_data(self.handle, _dev_f32(y, n, "y"), _dev_f32(w, n, "w") if w is not None else 0,
+                          _stream())
+
+    def kernels_per_iteration(self) -> int:
+        return lt_recon_kernels_per_iteration(self.handle)
+
+    def get(self, x=None):
+        x = self.plan.new_x() if x is None else x
+        gains, fit = lt_recon_get(self.handle, _dev_f32(x, self.plan.frames * self.plan.nvox, "x"),
+                                  self.plan.frames, len(self.plan.cams), _stream())
+        return x, gains, fit
+
+    @property
+    def iterations(self):
+        return lt_recon_iterations(self.handle)
+
+    def state(self) -> bytes:
+        return lt_recon_get_state(self.handle)
+
+    def load_state(self, state: bytes):
+        lt_recon_set_state(self.handle, state)
+
+    def close(self):
+        if self.handle is not None:
+            lt_recon_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
