@@ -120,6 +120,24 @@ LT_API lt_status lt_forward_camera(lt_plan* plan, int32_t cam, const float* x, f
 LT_API lt_status lt_adjoint_camera(lt_plan* plan, int32_t cam, const float* y_cam, float* x,
                             int32_t accumulate, void* stream);
 
+/* Allocation-free plenoptic forward projection (no counterpart in the paper).
+ * Same result as lt_forward_camera for a plenoptic camera, for callers that
+ * cannot allocate device memory when they project (frameworks whose memory
+ * pools forbid raw cudaMalloc, real-time loops where an allocation and its
+ * implicit synchronisation are not allowed): the array-plane intermediate is
+ * staged in a static 16 MiB device array inside the library instead of the
+ * plan's buffer, and the call allocates and frees nothing.
+ *   - frames x cells x array pixels must be <= 4,194,304 floats, else
+ *     LT_EINVAL with a message; non-plenoptic cameras give LT_EINVAL.
+ *   - Every GPU that loads the library reserves the array until exit.
+ *   - All calls share the array and it keeps the last call's contents; every
+ *     element a call reads is first written by that call, but calls that
+ *     overlap in time on the GPU (any plan, any stream) race on it.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture. */
+LT_API lt_status lt_forward_camera_noalloc(lt_plan* plan, int32_t cam, const float* x, float* y_cam,
+                                           void* stream);
+
 /* Plenoptic stages, exposed for testing and composition (eq. plenoptic,factor):
  *   stage 1:  fa[F][K][arr_nt][arr_ns] = M (1/V^a) sum_n B^{an}_k (dz x^n)
  *   stage 2:  y[F][M_c] = sum_k sum_mu B^{d mu}_k fa_k

@@ -64,6 +64,7 @@ _SIGS = {
     "lt_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lt_forward_camera": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_adjoint_camera": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
+    "lt_forward_camera_noalloc": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_camera_cells": (c_int32, [c_void_p, c_int32, POINTER(c_int32)]),
     "lt_plenoptic_stage1": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_plenoptic_stage1_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
@@ -162,6 +163,10 @@ def lt_forward_camera(plan, cam: int, x_ptr: int, y_ptr: int, stream: int = 0) -
 
 def lt_adjoint_camera(plan, cam: int, y_ptr: int, x_ptr: int, accumulate: int = 0, stream: int = 0) -> None:
     _check(lib().lt_adjoint_camera(plan, cam, y_ptr, x_ptr, accumulate, stream))
+
+
+def lt_forward_camera_noalloc(plan, cam: int, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    _check(lib().lt_forward_camera_noalloc(plan, cam, x_ptr, y_ptr, stream))
 
 
 def lt_camera_cells(plan, cam: int) -> int:
