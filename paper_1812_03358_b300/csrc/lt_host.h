@@ -26,6 +26,8 @@ struct CameraPlan {
   int64_t M = 0;
   int64_t offset = 0;
   SliceParam* d_slice = nullptr;   // [K][nz]
+  int2* d_srange = nullptr;        // [K][tiles_s] slice interval per forward tile column
+  int2* d_trange = nullptr;        // [K][tiles_t] slice interval per forward tile row
   int wmax_s = 0, wmax_t = 0, wimax_s = 0, wimax_t = 0;
   // plenoptic
   int64_t Na = 0;
@@ -37,6 +39,11 @@ struct CameraPlan {
   int32_t* d_col_owner = nullptr;
   int32_t* d_row_owner = nullptr;
   uint8_t* d_mask = nullptr;
+  int4* d_det_range = nullptr;
+  int4* d_det_union = nullptr;
+  int2* d_cand_all_s = nullptr;
+  int2* d_cand_all_t = nullptr;
+  float* d_zbuf = nullptr;         // scratch [F][N_mu][window^2]
   float* d_fa = nullptr;           // scratch array plane [F][K][Na]
   StageTwo s2{};
 };

@@ -57,7 +57,22 @@ struct StageTwo {
   int32_t K;
   int32_t wis, wit;           // adjoint windows (detector pixels per array pixel)
   int32_t max_cols, max_rows; // forward windows (array pixels per lenslet)
+  const int4* det_range;      // [K][mla_nt*mla_ns]: detector pixels a lenslet can reach (s0, s1, t0, t1), inclusive
+  const int4* det_union;      // [mla_nt*mla_ns]: union over cells of det_range
+  const int2* cand_all_s;     // [det_ns]: lenslet columns whose union window holds the column
+  const int2* cand_all_t;     // [det_nt]
+  float* zbuf;                // scratch [F][mla_nt*mla_ns][kStage2Window^2]: per-lenslet sub-images
+  int32_t full_cover;         // 1 if every array pixel lies in some lenslet block
 };
+
+// Largest detector window (per axis) of one lenslet's sub-image.
+constexpr int kStage2Window = 24;
+
+// Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.
+// The planner computes, per (cell, tile column) and (cell, tile row), the
+// slice interval [x, y) outside of which the tile's footprints miss the volume.
+constexpr int kBeamTileS = 32;
+constexpr int kBeamTileT = 32;
 
 // ---- kernel launchers (lt_kernels.cu) -------------------------------------
 
@@ -68,7 +83,8 @@ cudaError_t launch_beam_forward(const float* x, float* out, const SliceParam* pr
                                 int nx, int ny, int nz, int ns, int nt, int K,
                                 int per_cell, const uint8_t* mask, int frames,
                                 long long x_frame_stride, long long out_frame_stride,
-                                int wmax_s, int wmax_t, cudaStream_t st);
+                                int wmax_s, int wmax_t, const int2* srange, const int2* trange,
+                                cudaStream_t st);
 
 // Gather adjoint of the above: x[F][nz][ny][nx] (= or +=) sum_k sum_n ...
 // in = [F][K][nt][ns] if per_cell else [F][nt][ns] shared by all cells.
@@ -78,9 +94,11 @@ cudaError_t launch_beam_adjoint(const float* in, float* x, const SliceParam* prm
                                 long long in_frame_stride, long long x_frame_stride,
                                 int wimax_s, int wimax_t, cudaStream_t st);
 
+// zbuf: per-lenslet sub-image scratch [F][N_mu][kStage2Window^2] (the plan's,
+// or any buffer of that size).
 cudaError_t launch_stage2_forward(const float* fa, float* y, StageTwo s2, int frames,
                                   long long fa_frame_stride, long long y_frame_stride,
-                                  cudaStream_t st);
+                                  float* zbuf, cudaStream_t st);
 
 cudaError_t launch_stage2_adjoint(const float* y, float* fa, StageTwo s2, int frames,
                                   long long y_frame_stride, long long fa_frame_stride,

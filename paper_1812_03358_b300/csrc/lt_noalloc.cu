@@ -7,7 +7,8 @@
 // where an allocation (and the implicit device synchronisation it can cause)
 // is not allowed, or callers holding a plan built elsewhere whose memory
 // budget is fixed.  For them, lt_forward_camera_noalloc stages the
-// intermediate in a fixed static device array instead and allocates nothing.
+// intermediate in a fixed static device array instead and allocates nothing
+// (the per-lenslet sub-image buffer it also uses was allocated with the plan).
 //
 // Limits and sharing rules (also in include/lt.h):
 //   * the array holds kNoAllocScratchFloats floats (16 MiB); every GPU that
@@ -77,8 +78,9 @@ extern "C" lt_status lt_forward_camera_noalloc(lt_plan* plan, int32_t cam, const
   const long long fa_fs = (long long)c.K * c.Na;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = lt::launch_beam_forward(x, fa, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt, c.K, 1,
-                                          c.d_mask, plan->frames, plan->nvox, fa_fs, c.wmax_s, c.wmax_t, st);
+                                          c.d_mask, plan->frames, plan->nvox, fa_fs, c.wmax_s, c.wmax_t,
+                                          c.d_srange, c.d_trange, st);
   if (e != cudaSuccess) return lt::cuda_error(e, "allocation-free stage 1");
-  e = lt::launch_stage2_forward(fa, y_cam, c.s2, plan->frames, fa_fs, c.M, st);
+  e = lt::launch_stage2_forward(fa, y_cam, c.s2, plan->frames, fa_fs, c.M, c.d_zbuf, st);
   return e == cudaSuccess ? LT_OK : lt::cuda_error(e, "allocation-free stage 2");
 }

@@ -212,6 +212,8 @@ static lt_status upload(const std::vector<T>& h, T** d, const char* what) {
 
 static void free_camera(CameraPlan& c) {
   cudaFree(c.d_slice);
+  cudaFree(c.d_srange);
+  cudaFree(c.d_trange);
   cudaFree(c.d_lens);
   cudaFree(c.d_cand_s);
   cudaFree(c.d_cand_t);
@@ -220,6 +222,11 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.d_col_owner);
   cudaFree(c.d_row_owner);
   cudaFree(c.d_mask);
+  cudaFree(c.d_det_range);
+  cudaFree(c.d_det_union);
+  cudaFree(c.d_cand_all_s);
+  cudaFree(c.d_cand_all_t);
+  cudaFree(c.d_zbuf);
   cudaFree(c.d_fa);
   c = CameraPlan();
 }
@@ -229,6 +236,25 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
                              int tgt_nt, double tgt_ps, double tgt_pt, double extra_scale, int idx) {
   const lt_camera_desc& d = c.desc;
   std::vector<SliceParam> sp((size_t)c.K * v.nz);
+  const int tiles_s = (tgt_ns + kBeamTileS - 1) / kBeamTileS;
+  const int tiles_t = (tgt_nt + kBeamTileT - 1) / kBeamTileT;
+  std::vector<int2> srange((size_t)c.K * tiles_s, make_int2(INT32_MAX, -1));
+  std::vector<int2> trange((size_t)c.K * tiles_t, make_int2(INT32_MAX, -1));
+  // Slice n is active for a tile when the union of its pixels' footprints
+  // (centres c0 + c1 i, half-width Q, cells [-1/2, n_src - 1/2]) meets the grid.
+  auto mark = [](std::vector<int2>& rng, size_t base, int tiles, int tile_w, int n_tgt, int n_src,
+                 const Footprint& f, int n) {
+    for (int tile = 0; tile < tiles; ++tile) {
+      const int i0 = tile * tile_w, i1 = std::min(n_tgt, i0 + tile_w) - 1;
+      const double a = f.C0 + f.C1 * i0, b = f.C0 + f.C1 * i1;
+      const double lo = std::min(a, b) - f.Q - 1e-3, hi = std::max(a, b) + f.Q + 1e-3;
+      if (hi > -0.5 && lo < n_src - 0.5) {
+        int2& r = rng[base + tile];
+        r.x = std::min(r.x, n);
+        r.y = std::max(r.y, n + 1);
+      }
+    }
+  };
   for (int k = 0; k < c.K; ++k) {
     for (int n = 0; n < v.nz; ++n) {
       const double dist = d.d_obj + centre(n, v.nz, v.dz);
@@ -240,6 +266,8 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
           !footprint(L, P, c.cells[k].tk, c.cells[k].d0t, centre(0, tgt_nt, tgt_pt), tgt_pt,
                      centre(0, v.ny, v.dy), v.dy, d.basis, &ft))
         return set_error(LT_EINVAL, "camera %d: degenerate transport at slice %d", idx, n);
+      mark(srange, (size_t)k * tiles_s, tiles_s, kBeamTileS, tgt_ns, v.nx, fs, n);
+      mark(trange, (size_t)k * tiles_t, tiles_t, kBeamTileT, tgt_nt, v.ny, ft, n);
       SliceParam& p = sp[(size_t)k * v.nz + n];
       std::memset(&p, 0, sizeof(p));
       p.s = fs.a;
@@ -263,6 +291,13 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
     return set_error(LT_EUNSUPPORTED,
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
+  for (auto& r : srange)
+    if (r.y < 0) r = make_int2(0, 0);
+  for (auto& r : trange)
+    if (r.y < 0) r = make_int2(0, 0);
+  lt_status s = upload(srange, &c.d_srange, "tile slice ranges");
+  if (s == LT_OK) s = upload(trange, &c.d_trange, "tile slice ranges");
+  if (s != LT_OK) return s;
   return upload(sp, &c.d_slice, "slice parameters");
 }
 
@@ -323,6 +358,7 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   std::vector<LensletParam> lens((size_t)c.K * nmu);
   std::vector<int2> cand_s((size_t)c.K * d.det_ns, make_int2(INT32_MAX, -1));
   std::vector<int2> cand_t((size_t)c.K * d.det_nt, make_int2(INT32_MAX, -1));
+  std::vector<int4> det_range((size_t)c.K * nmu, make_int4(0, -1, 0, -1));
   int wis = 0, wit = 0;
   for (int k = 0; k < c.K; ++k) {
     for (int mt = 0; mt < mnt; ++mt) {
@@ -351,6 +387,8 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
           if (a > b) std::swap(a, b);
           const long long i0 = std::max<long long>(0, (long long)std::floor(a) - 1);
           const long long i1 = std::min<long long>(d.det_ns - 1, (long long)std::ceil(b) + 1);
+          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].x = (int)i0;
+          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].y = (int)i1;
           for (long long i = i0; i <= i1; ++i) {
             int2& cs = cand_s[(size_t)k * d.det_ns + i];
             cs.x = std::min(cs.x, ms);
@@ -363,6 +401,8 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
           if (a > b) std::swap(a, b);
           const long long i0 = std::max<long long>(0, (long long)std::floor(a) - 1);
           const long long i1 = std::min<long long>(d.det_nt - 1, (long long)std::ceil(b) + 1);
+          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].z = (int)i0;
+          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].w = (int)i1;
           for (long long i = i0; i <= i1; ++i) {
             int2& ct = cand_t[(size_t)k * d.det_nt + i];
             ct.x = std::min(ct.x, mt);
@@ -376,6 +416,40 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
     if (r.y < 0) r = make_int2(0, -1);
   for (auto& r : cand_t)
     if (r.y < 0) r = make_int2(0, -1);
+  // union over cells of each lenslet's detector window, and the lenslets
+  // whose union window covers each detector column / row
+  std::vector<int4> det_union(nmu, make_int4(INT32_MAX, -1, INT32_MAX, -1));
+  for (int k = 0; k < c.K; ++k)
+    for (int m = 0; m < nmu; ++m) {
+      const int4 r = det_range[(size_t)k * nmu + m];
+      int4& u = det_union[m];
+      if (r.y >= r.x) { u.x = std::min(u.x, r.x); u.y = std::max(u.y, r.y); }
+      if (r.w >= r.z) { u.z = std::min(u.z, r.z); u.w = std::max(u.w, r.w); }
+    }
+  std::vector<int2> cand_all_s(d.det_ns, make_int2(INT32_MAX, -1)), cand_all_t(d.det_nt, make_int2(INT32_MAX, -1));
+  for (int m = 0; m < nmu; ++m) {
+    int4& u = det_union[m];
+    if (u.y < u.x || u.w < u.z) { u = make_int4(0, -1, 0, -1); continue; }
+    if (u.y - u.x + 1 > kStage2Window || u.w - u.z + 1 > kStage2Window)
+      return set_error(LT_EUNSUPPORTED, "camera %d: a lenslet's sub-image spans %d x %d detector pixels (kernel limit %d)",
+                       idx, u.y - u.x + 1, u.w - u.z + 1, kStage2Window);
+    const int ms = m % mns, mt = m / mns;
+    for (int i = u.x; i <= u.y; ++i) {
+      cand_all_s[i].x = std::min(cand_all_s[i].x, ms);
+      cand_all_s[i].y = std::max(cand_all_s[i].y, ms);
+    }
+    for (int i = u.z; i <= u.w; ++i) {
+      cand_all_t[i].x = std::min(cand_all_t[i].x, mt);
+      cand_all_t[i].y = std::max(cand_all_t[i].y, mt);
+    }
+  }
+  for (auto& r : cand_all_s)
+    if (r.y < 0) r = make_int2(0, -1);
+  for (auto& r : cand_all_t)
+    if (r.y < 0) r = make_int2(0, -1);
+  int full_cover = 1;
+  for (int j = 0; j < d.arr_ns; ++j) full_cover &= col_owner[j] >= 0;
+  for (int j = 0; j < d.arr_nt; ++j) full_cover &= row_owner[j] >= 0;
   if (wis > kMaxAdjointWindow || wit > kMaxAdjointWindow)
     return set_error(LT_EUNSUPPORTED, "camera %d: an array pixel is covered by %d x %d detector footprints (kernel limit %d)",
                      idx, wis, wit, kMaxAdjointWindow);
@@ -388,6 +462,18 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   if ((s = upload(col_owner, &c.d_col_owner, "column owners")) != LT_OK) return s;
   if ((s = upload(row_owner, &c.d_row_owner, "row owners")) != LT_OK) return s;
   if ((s = upload(mask, &c.d_mask, "mask")) != LT_OK) return s;
+  if ((s = upload(det_range, &c.d_det_range, "lenslet detector ranges")) != LT_OK) return s;
+  if ((s = upload(det_union, &c.d_det_union, "lenslet detector windows")) != LT_OK) return s;
+  if ((s = upload(cand_all_s, &c.d_cand_all_s, "candidate columns")) != LT_OK) return s;
+  if ((s = upload(cand_all_t, &c.d_cand_all_t, "candidate rows")) != LT_OK) return s;
+  {
+    const size_t zb = (size_t)frames * nmu * kStage2Window * kStage2Window * sizeof(float);
+    cudaError_t ez = cudaMalloc((void**)&c.d_zbuf, zb);
+    if (ez != cudaSuccess) {
+      c.d_zbuf = nullptr;
+      return set_error(LT_ENOMEM, "cudaMalloc(lenslet sub-images, %zu bytes): %s", zb, cudaGetErrorString(ez));
+    }
+  }
   c.Na = (int64_t)d.arr_ns * d.arr_nt;
   const size_t fa_bytes = (size_t)frames * c.K * c.Na * sizeof(float);
   cudaError_t e = cudaMalloc((void**)&c.d_fa, fa_bytes);
@@ -415,6 +501,12 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   s2.wit = wit;
   s2.max_cols = max_cols;
   s2.max_rows = max_rows;
+  s2.det_range = c.d_det_range;
+  s2.det_union = c.d_det_union;
+  s2.cand_all_s = c.d_cand_all_s;
+  s2.cand_all_t = c.d_cand_all_t;
+  s2.zbuf = c.d_zbuf;
+  s2.full_cover = full_cover;
   return LT_OK;
 }
 
@@ -599,7 +691,8 @@ lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, l
                          cudaStream_t st) {
   const lt_volume_desc& v = p->vol;
   cudaError_t e = launch_beam_forward(x, fa, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt,
-                                      c.K, 1, c.d_mask, p->frames, p->nvox, fa_fs, c.wmax_s, c.wmax_t, st);
+                                      c.K, 1, c.d_mask, p->frames, p->nvox, fa_fs, c.wmax_s, c.wmax_t,
+                                      c.d_srange, c.d_trange, st);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 1");
 }
 
@@ -618,13 +711,14 @@ lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long lon
   const lt_volume_desc& v = p->vol;
   if (c.desc.kind == LT_CAM_SINGLE) {
     cudaError_t e = launch_beam_forward(x, y, c.d_slice, v.nx, v.ny, v.nz, c.desc.det_ns, c.desc.det_nt,
-                                        c.K, 0, nullptr, p->frames, p->nvox, y_fs, c.wmax_s, c.wmax_t, st);
+                                        c.K, 0, nullptr, p->frames, p->nvox, y_fs, c.wmax_s, c.wmax_t,
+                                        c.d_srange, c.d_trange, st);
     return e == cudaSuccess ? LT_OK : cuda_error(e, "single-lens forward");
   }
   const long long fa_fs = (long long)c.K * c.Na;
   lt_status s = stage1_forward(p, c, x, c.d_fa, fa_fs, st);
   if (s != LT_OK) return s;
-  cudaError_t e = launch_stage2_forward(c.d_fa, y, c.s2, p->frames, fa_fs, y_fs, st);
+  cudaError_t e = launch_stage2_forward(c.d_fa, y, c.s2, p->frames, fa_fs, y_fs, c.d_zbuf, st);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 2");
 }
 
@@ -727,7 +821,7 @@ extern "C" lt_status lt_plenoptic_stage2(lt_plan* plan, int32_t cam, const float
   if (!fa || !y_cam) return set_error(LT_EINVAL, "NULL argument");
   CameraPlan& c = plan->cams[cam];
   cudaError_t e = launch_stage2_forward(fa, y_cam, c.s2, plan->frames, (long long)c.K * c.Na, c.M,
-                                        (cudaStream_t)stream);
+                                        c.d_zbuf, (cudaStream_t)stream);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 2");
 }
 
