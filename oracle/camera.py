@@ -338,19 +338,71 @@ def plenoptic_matrix(vol, cam):
 
 
 # ---------------------------------------------------------------------------
-# dispatch
+# rotated cameras (Sec. III-A: A_c = C_c o rotation) and dispatch
 # ---------------------------------------------------------------------------
 
-def forward(vol, cam, x):
+class Grid:
+    """Plain voxel-grid description (duck-types the volume descriptor)."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz):
+        self.nx, self.ny, self.nz, self.dx, self.dy, self.dz = nx, ny, nz, dx, dy, dz
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+class _Aligned:
+    """The camera descriptor with the yaw removed (it sees the rotated grid)."""
+
+    def __init__(self, cam):
+        self.__dict__.update(cam.__dict__)
+        self.yaw = 0.0
+
+    @property
+    def m(self):
+        return self.det_ns * self.det_nt
+
+
+def rotated_volume(vol, cam, x):
+    from . import rotation
+    Xr, sr = rotation.rotate(np.asarray(x, dtype=np.float64).reshape(vol.shape),
+                             (vol.dx, vol.dy, vol.dz), cam.yaw)
+    g = Grid(Xr.shape[2], Xr.shape[1], Xr.shape[0], sr[0], sr[1], sr[2])
+    return g, Xr
+
+
+def _aligned_forward(vol, cam, x):
     if cam.kind == 1:
         return plenoptic_forward(vol, cam, x)
     return single_forward(vol, cam, x)
 
 
-def adjoint(vol, cam, y):
+def _aligned_adjoint(vol, cam, y):
     if cam.kind == 1:
         return plenoptic_adjoint(vol, cam, y)
     return single_adjoint(vol, cam, y)
+
+
+def forward(vol, cam, x):
+    if cam.yaw != 0.0:
+        g, Xr = rotated_volume(vol, cam, x)
+        return _aligned_forward(g, _Aligned(cam), Xr)
+    return _aligned_forward(vol, cam, x)
+
+
+def adjoint(vol, cam, y):
+    if cam.yaw != 0.0:
+        from . import rotation
+        shape_r, sr, _ = rotation.rotated_grid(vol.shape, (vol.dx, vol.dy, vol.dz), cam.yaw)
+        g = Grid(shape_r[2], shape_r[1], shape_r[0], sr[0], sr[1], sr[2])
+        Gr = _aligned_adjoint(g, _Aligned(cam), y)
+        return rotation.rotate_adjoint(Gr, vol.shape, (vol.dx, vol.dy, vol.dz), cam.yaw)
+    return _aligned_adjoint(vol, cam, y)
 
 
 def system_matrix(vol, cam):

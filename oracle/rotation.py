@@ -32,8 +32,10 @@ def yaw_matrix(theta):
 
 
 def split_angle(theta):
-    """theta = n * 90 deg + residual, |residual| <= 45 deg, n in {0,1,2,3}."""
-    n = int(round(theta / (math.pi / 2)))
+    """theta = n * 90 deg + residual, |residual| <= 45 deg, n in {0,1,2,3}.
+    Sec. III-A takes residuals below 45 degrees; at exactly 45 degrees the
+    quarter-turn count is rounded half up: n = floor(theta / 90 deg + 1/2)."""
+    n = int(math.floor(theta / (math.pi / 2) + 0.5))
     return n % 4, theta - n * (math.pi / 2)
 
 
@@ -156,3 +158,61 @@ def rotation_matrix(shape, sizes, theta):
         R, _ = rotate(e.reshape(shape), sizes, theta)
         cols.append(R.ravel())
     return np.stack(cols, axis=1)
+
+
+def shear_z_adjoint(G, sizes, b, nz):
+    """(E^z)^T: from the padded grid [nz'][ny][nx] back to [nz][ny][nx]."""
+    dx, dy, dz = sizes
+    nzo, ny, nx = G.shape
+    zs, zo, xs = _centres(nz, dz), _centres(nzo, dz), _centres(nx, dx)
+    out = np.zeros((nz, ny, nx))
+    for ix in range(nx):
+        E = np.zeros((nzo, nz))
+        for i in range(nzo):
+            for j in range(nz):
+                if abs(zo[i] - (zs[j] - b * xs[ix])) < dz + abs(b) * dx / 2 + 1e-12:
+                    E[i, j] = shear_entry(zo[i], zs[j], dz, xs[ix], dx, b)
+        out[:, :, ix] = E.T @ G[:, :, ix]
+    return out
+
+
+def shear_x_adjoint(G, sizes, a, nx):
+    """(E^x)^T: from [nz][ny][nx'] back to [nz][ny][nx]."""
+    dx, dy, dz = sizes
+    nz, ny, nxo = G.shape
+    xs, xo, zs = _centres(nx, dx), _centres(nxo, dx), _centres(nz, dz)
+    out = np.zeros((nz, ny, nx))
+    for iz in range(nz):
+        E = np.zeros((nxo, nx))
+        for i in range(nxo):
+            for j in range(nx):
+                if abs(xo[i] - (xs[j] - a * zs[iz])) < dx + abs(a) * dz / 2 + 1e-12:
+                    E[i, j] = shear_entry(xo[i], xs[j], dx, zs[iz], dz, a)
+        out[iz] = G[iz] @ E
+    return out
+
+
+def quarter_turn_adjoint(P, n, shape):
+    """Inverse (= transpose) of the quarter-turn permutation, back to shape."""
+    nz, ny, nx = shape
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    if n == 0:
+        return P.copy()
+    if n == 1:
+        return P[ix, iy, nz - 1 - iz]
+    if n == 2:
+        return P[nz - 1 - iz, iy, nx - 1 - ix]
+    return P[nx - 1 - ix, iy, iz]
+
+
+def rotate_adjoint(G, shape, sizes, theta):
+    """P^T (E^z)^T (E^x)^T applied to a rotated-grid array G."""
+    n, tr = split_angle(theta)
+    nz, ny, nx = shape
+    nzp, nxp = (nx, nz) if n % 2 else (nz, nx)
+    sp = (sizes[2], sizes[1], sizes[0]) if n % 2 else sizes
+    Dg, a, b = shear_factors(tr)
+    sr = (sp[0] / Dg[0], sp[1], sp[2] / Dg[2])
+    Z = shear_x_adjoint(np.asarray(G, dtype=np.float64), sr, a, nxp)
+    Xp = shear_z_adjoint(Z, sr, b, nzp)
+    return quarter_turn_adjoint(Xp, n, shape)

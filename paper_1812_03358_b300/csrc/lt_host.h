@@ -25,6 +25,13 @@ struct CameraPlan {
   int K = 0;
   int64_t M = 0;
   int64_t offset = 0;
+  // the grid this camera sees: the object volume, or its rotated view
+  bool rotated = false;
+  RotParam rot{};
+  lt_volume_desc vol_c{};
+  int64_t nvox_c = 0;
+  float* d_rz = nullptr;           // scratch [F][nzr][ny][nxp] (rotated cameras)
+  float* d_xr = nullptr;           // scratch [F][nzr][ny][nxr] (rotated cameras)
   SliceParam* d_slice = nullptr;   // [K][nz]
   int2* d_srange = nullptr;        // [K][tiles_s] slice interval per forward tile column
   int2* d_trange = nullptr;        // [K][tiles_t] slice interval per forward tile row

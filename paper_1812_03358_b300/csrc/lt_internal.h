@@ -68,6 +68,24 @@ struct StageTwo {
 // Largest detector window (per axis) of one lenslet's sub-image.
 constexpr int kStage2Window = 24;
 
+// Rotated view of the object volume (Sec. III-A): quarter turns nq about y,
+// then the z shear E^z and the x shear E^x of the residual rotation.  The
+// permuted grid is [nzp][ny][nxp]; after E^z it is [nzr][ny][nxp] with
+// nzr = nzp + 2 pz, after E^x [nzr][ny][nxr] with nxr = nxp + 2 px.  Entry
+// between output cell i and source cell j of column c (E^z) / row c (E^x):
+// the average of the box-overlap hat over the sheared cell,
+//   u = (i - j - pad) + slope * (c - (n_c - 1)/2),  width beta = |slope|.
+struct RotParam {
+  int32_t nq;
+  int32_t nx, ny, nz;      // original volume
+  int32_t nxp, nzp;        // after the quarter turns
+  int32_t pz, px;
+  int32_t nzr, nxr;        // rotated volume
+  float bz, betaz;         // E^z slope (b dx'/dz') and |bz|
+  float ax, betax;         // E^x slope (a dz'/dx') and |ax|
+  int32_t wz, wx;          // source windows
+};
+
 // Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.
 // The planner computes, per (cell, tile column) and (cell, tile row), the
 // slice interval [x, y) outside of which the tile's footprints miss the volume.
@@ -103,5 +121,12 @@ cudaError_t launch_stage2_forward(const float* fa, float* y, StageTwo s2, int fr
 cudaError_t launch_stage2_adjoint(const float* y, float* fa, StageTwo s2, int frames,
                                   long long y_frame_stride, long long fa_frame_stride,
                                   cudaStream_t st);
+
+// Rotation passes (lt_rotate.cu).  Frames are consecutive volumes.
+cudaError_t launch_rotate_forward(const float* x, float* rz, float* xr, const RotParam& r, int frames,
+                                  cudaStream_t st);
+// g_xr (rotated grid) -> x (= or +=), using rz as scratch.
+cudaError_t launch_rotate_adjoint(const float* g_xr, float* rz, float* x, const RotParam& r, int frames,
+                                  int accumulate, cudaStream_t st);
 
 }  // namespace lt

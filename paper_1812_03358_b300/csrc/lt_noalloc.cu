@@ -65,6 +65,8 @@ extern "C" lt_status lt_forward_camera_noalloc(lt_plan* plan, int32_t cam, const
   lt::CameraPlan& c = plan->cams[cam];
   if (c.desc.kind != LT_CAM_PLENOPTIC)
     return lt::set_error(LT_EINVAL, "camera %d is not plenoptic (the allocation-free path stages the array plane)", cam);
+  if (c.rotated)
+    return lt::set_error(LT_EUNSUPPORTED, "camera %d is rotated; the allocation-free path takes aligned cameras only", cam);
   const long long need = (long long)plan->frames * c.K * c.Na;
   if (need > kNoAllocScratchFloats)
     return lt::set_error(LT_EINVAL,

@@ -6,6 +6,7 @@
 #include "lt_host.h"
 
 #include <algorithm>
+#define _USE_MATH_DEFINES
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -166,15 +167,15 @@ static lt_status validate_camera(const lt_volume_desc* v, const lt_camera_desc* 
   if (!pos(c->f_main) || !pos(c->r_main) || !pos(c->d_obj))
     return set_error(LT_EINVAL, "camera %d: f_main, r_main, d_obj must be positive", idx);
   if (!std::isfinite(c->yaw)) return set_error(LT_EINVAL, "camera %d: yaw not finite", idx);
-  if (c->yaw != 0.0)
-    return set_error(LT_EUNSUPPORTED, "camera %d: rotated cameras (yaw != 0) are not supported by this build", idx);
   if (c->det_ns <= 0 || c->det_nt <= 0 || !pos(c->det_ps) || !pos(c->det_pt))
     return set_error(LT_EINVAL, "camera %d: detector sizes/pitches must be positive", idx);
   if (c->ks <= 0 || c->kt <= 0 || c->ks > 256 || c->kt > 256)
     return set_error(LT_EINVAL, "camera %d: angular cells ks, kt must be in [1, 256]", idx);
-  const double dmin = c->d_obj - 0.5 * v->nz * v->dz;
+  // the rotated view's z extent is at most the volume's diagonal in (x, z)
+  const double half = 0.5 * std::sqrt((double)v->nz * v->dz * v->nz * v->dz + (double)v->nx * v->dx * v->nx * v->dx);
+  const double dmin = c->d_obj - (c->yaw != 0.0 ? 2.0 * half : 0.5 * v->nz * v->dz);
   if (!(dmin > 0.0))
-    return set_error(LT_EINVAL, "camera %d: the volume reaches the main lens (d_obj - nz*dz/2 = %g)", idx, dmin);
+    return set_error(LT_EINVAL, "camera %d: the volume reaches the main lens (nearest slice at %g)", idx, dmin);
   if (c->kind == LT_CAM_SINGLE) {
     if (!pos(c->d_lens_det)) return set_error(LT_EINVAL, "camera %d: d_lens_det must be positive", idx);
   } else {
@@ -212,6 +213,8 @@ static lt_status upload(const std::vector<T>& h, T** d, const char* what) {
 
 static void free_camera(CameraPlan& c) {
   cudaFree(c.d_slice);
+  cudaFree(c.d_rz);
+  cudaFree(c.d_xr);
   cudaFree(c.d_srange);
   cudaFree(c.d_trange);
   cudaFree(c.d_lens);
@@ -510,9 +513,64 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   return LT_OK;
 }
 
-static lt_status plan_camera(const lt_volume_desc& v, const lt_camera_desc& src, int frames,
+// Rotated view of the volume for a camera with yaw (Sec. III-A): quarter
+// turns, then D = diag(cos, 1, 1/cos) rescales the voxels and the shears
+// S_z (z += b x, b = -sin cos) and S_x (x += a z, a = tan) are applied as LS
+// re-projections onto grids padded to hold every sheared cell.
+static lt_status plan_rotation(const lt_volume_desc& v, CameraPlan& c, int frames, int idx) {
+  const double yaw = c.desc.yaw;
+  const double q = std::floor(yaw / (M_PI / 2) + 0.5);   // half up at exactly 45 degrees
+  const double tr = yaw - q * (M_PI / 2);
+  int nq = (int)(((long long)q % 4 + 4) % 4);
+  RotParam& r = c.rot;
+  r.nq = nq;
+  r.nx = v.nx;
+  r.ny = v.ny;
+  r.nz = v.nz;
+  const bool odd = nq % 2 == 1;
+  r.nxp = odd ? v.nz : v.nx;
+  r.nzp = odd ? v.nx : v.nz;
+  const double dxp = odd ? v.dz : v.dx, dzp = odd ? v.dx : v.dz;
+  const double cs = std::cos(tr), sn = std::sin(tr);
+  const double a = sn / cs, b = -sn * cs;
+  const double dxr = dxp / cs, dzr = dzp * cs;    // voxel sizes after D
+  r.pz = (int)std::ceil(std::fabs(b) * r.nxp * dxr / 2.0 / dzr) + 1;
+  r.nzr = r.nzp + 2 * r.pz;
+  r.px = (int)std::ceil(std::fabs(a) * r.nzr * dzr / 2.0 / dxr) + 1;
+  r.nxr = r.nxp + 2 * r.px;
+  r.bz = (float)(b * dxr / dzr);
+  r.betaz = std::fabs(r.bz);
+  r.ax = (float)(a * dzr / dxr);
+  r.betax = std::fabs(r.ax);
+  r.wz = (int)std::floor(2.0 + r.betaz) + 4;
+  r.wx = (int)std::floor(2.0 + r.betax) + 4;
+  c.vol_c.nx = r.nxr;
+  c.vol_c.ny = v.ny;
+  c.vol_c.nz = r.nzr;
+  c.vol_c.dx = dxr;
+  c.vol_c.dy = v.dy;
+  c.vol_c.dz = dzr;
+  c.nvox_c = (int64_t)r.nxr * v.ny * r.nzr;
+  if (c.desc.d_obj - 0.5 * r.nzr * dzr <= 0.0)
+    return set_error(LT_EINVAL, "camera %d: the rotated volume reaches the main lens", idx);
+  const size_t brz = (size_t)frames * r.nzr * v.ny * r.nxp * sizeof(float);
+  const size_t bxr = (size_t)frames * c.nvox_c * sizeof(float);
+  if (cudaMalloc((void**)&c.d_rz, brz) != cudaSuccess || cudaMalloc((void**)&c.d_xr, bxr) != cudaSuccess)
+    return set_error(LT_ENOMEM, "camera %d: rotated-view scratch (%zu + %zu bytes)", idx, brz, bxr);
+  return LT_OK;
+}
+
+static lt_status plan_camera(const lt_volume_desc& v0, const lt_camera_desc& src, int frames,
                              CameraPlan& c, int idx) {
   c.desc = src;
+  c.vol_c = v0;
+  c.nvox_c = (int64_t)v0.nx * v0.ny * v0.nz;
+  c.rotated = src.yaw != 0.0;
+  if (c.rotated) {
+    lt_status s = plan_rotation(v0, c, frames, idx);
+    if (s != LT_OK) return s;
+  }
+  const lt_volume_desc& v = c.vol_c;
   if (src.kind == LT_CAM_PLENOPTIC) {
     c.focal.assign(src.mla_focal, src.mla_focal + (size_t)src.mla_ns * src.mla_nt);
     c.desc.mla_focal = nullptr;
@@ -628,7 +686,7 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
     return set_error(LT_EINVAL, "bad plan/camera/out argument");
   const CameraPlan& c = plan->cams[cam];
   const lt_camera_desc& d = c.desc;
-  const lt_volume_desc& v = plan->vol;
+  const lt_volume_desc& v = c.vol_c;
   const bool plen = d.kind == LT_CAM_PLENOPTIC;
   const int tns = plen ? d.arr_ns : d.det_ns, tnt = plen ? d.arr_nt : d.det_nt;
   const double tps = plen ? d.arr_ps : d.det_ps, tpt = plen ? d.arr_pt : d.det_pt;
@@ -687,31 +745,63 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
 
 namespace lt {
 
+// The grid this camera sees: x itself, or its rotated view (into c.d_xr).
+static lt_status to_camera_grid(lt_plan* p, CameraPlan& c, const float* x, const float** xc, cudaStream_t st) {
+  if (!c.rotated) {
+    *xc = x;
+    return LT_OK;
+  }
+  cudaError_t e = launch_rotate_forward(x, c.d_rz, c.d_xr, c.rot, p->frames, st);
+  if (e != cudaSuccess) return cuda_error(e, "rotated view");
+  *xc = c.d_xr;
+  return LT_OK;
+}
+
+// Adjoint of the slice -> plane transport from `in` back to x (through the
+// transposed rotation for rotated cameras).
+static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* in, long long in_fs,
+                                        int tgt_ns, int tgt_nt, int per_cell, float* x, int accumulate,
+                                        cudaStream_t st) {
+  const lt_volume_desc& v = c.vol_c;
+  float* dst = c.rotated ? c.d_xr : x;
+  cudaError_t e = launch_beam_adjoint(in, dst, c.d_slice, v.nx, v.ny, v.nz, tgt_ns, tgt_nt, c.K, per_cell,
+                                      c.rotated ? 0 : accumulate, p->frames, in_fs, c.nvox_c, c.wimax_s,
+                                      c.wimax_t, st);
+  if (e != cudaSuccess) return cuda_error(e, "beam adjoint");
+  if (c.rotated) {
+    e = launch_rotate_adjoint(c.d_xr, c.d_rz, x, c.rot, p->frames, accumulate, st);
+    if (e != cudaSuccess) return cuda_error(e, "rotated view adjoint");
+  }
+  return LT_OK;
+}
+
 lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, long long fa_fs,
                          cudaStream_t st) {
-  const lt_volume_desc& v = p->vol;
-  cudaError_t e = launch_beam_forward(x, fa, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt,
-                                      c.K, 1, c.d_mask, p->frames, p->nvox, fa_fs, c.wmax_s, c.wmax_t,
+  const float* xc = nullptr;
+  lt_status s = to_camera_grid(p, c, x, &xc, st);
+  if (s != LT_OK) return s;
+  const lt_volume_desc& v = c.vol_c;
+  cudaError_t e = launch_beam_forward(xc, fa, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt,
+                                      c.K, 1, c.d_mask, p->frames, c.nvox_c, fa_fs, c.wmax_s, c.wmax_t,
                                       c.d_srange, c.d_trange, st);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 1");
 }
 
 lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
                          int accumulate, cudaStream_t st) {
-  const lt_volume_desc& v = p->vol;
-  cudaError_t e = launch_beam_adjoint(fa, x, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt,
-                                      c.K, 1, accumulate, p->frames, fa_fs, p->nvox, c.wimax_s,
-                                      c.wimax_t, st);
-  return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 1 adjoint");
+  return beam_adjoint_to_volume(p, c, fa, fa_fs, c.desc.arr_ns, c.desc.arr_nt, 1, x, accumulate, st);
 }
 
 lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long long y_fs,
                          cudaStream_t st) {
   CameraPlan& c = p->cams[cam];
-  const lt_volume_desc& v = p->vol;
   if (c.desc.kind == LT_CAM_SINGLE) {
-    cudaError_t e = launch_beam_forward(x, y, c.d_slice, v.nx, v.ny, v.nz, c.desc.det_ns, c.desc.det_nt,
-                                        c.K, 0, nullptr, p->frames, p->nvox, y_fs, c.wmax_s, c.wmax_t,
+    const float* xc = nullptr;
+    lt_status s = to_camera_grid(p, c, x, &xc, st);
+    if (s != LT_OK) return s;
+    const lt_volume_desc& v = c.vol_c;
+    cudaError_t e = launch_beam_forward(xc, y, c.d_slice, v.nx, v.ny, v.nz, c.desc.det_ns, c.desc.det_nt,
+                                        c.K, 0, nullptr, p->frames, c.nvox_c, y_fs, c.wmax_s, c.wmax_t,
                                         c.d_srange, c.d_trange, st);
     return e == cudaSuccess ? LT_OK : cuda_error(e, "single-lens forward");
   }
@@ -725,13 +815,8 @@ lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long lon
 lt_status camera_adjoint(lt_plan* p, int cam, const float* y, long long y_fs, float* x,
                          int accumulate, cudaStream_t st) {
   CameraPlan& c = p->cams[cam];
-  const lt_volume_desc& v = p->vol;
-  if (c.desc.kind == LT_CAM_SINGLE) {
-    cudaError_t e = launch_beam_adjoint(y, x, c.d_slice, v.nx, v.ny, v.nz, c.desc.det_ns, c.desc.det_nt,
-                                        c.K, 0, accumulate, p->frames, y_fs, p->nvox, c.wimax_s,
-                                        c.wimax_t, st);
-    return e == cudaSuccess ? LT_OK : cuda_error(e, "single-lens adjoint");
-  }
+  if (c.desc.kind == LT_CAM_SINGLE)
+    return beam_adjoint_to_volume(p, c, y, y_fs, c.desc.det_ns, c.desc.det_nt, 0, x, accumulate, st);
   const long long fa_fs = (long long)c.K * c.Na;
   cudaError_t e = launch_stage2_adjoint(y, c.d_fa, c.s2, p->frames, y_fs, fa_fs, st);
   if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2 adjoint");

@@ -1,0 +1,89 @@
+"""GPU parity of rotated cameras (Sec. III-A: quarter turns + z/x shear
+re-projections, then the aligned camera) against the FP64 oracle, forward and
+adjoint, single-lens and plenoptic, and inside the reconstruction."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import camera as O
+from oracle import recon as OR
+from paper_1812_03358_b300 import build, inputs as I, lt
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("yaw", [0.3, -0.7, math.pi / 4, 1.9, math.pi / 2, 3.0, -2.2])
+def test_rotated_single_lens_matches_oracle(yaw):
+    vol = I.Volume(12, 9, 10, 4.0, 4.5, 5.0)
+    cam = I.table_single_lens(28, 0.3, yaw=yaw, ks=2, kt=2)
+    x = I.gaussian_blobs(vol, seed=1010)
+    y = I.uniform_random(cam.m, seed=31)
+    plan = lt.Plan(vol, [cam])
+    yg = host(plan.forward(dev(x).reshape(1, -1)))
+    xg = host(plan.adjoint(dev(y).reshape(1, -1)))
+    yo = O.forward(vol, cam, x).ravel()
+    xo = O.adjoint(vol, cam, y).ravel()
+    assert rel_l2(yg, yo) < TOL, rel_l2(yg, yo)
+    assert rel_l2(xg, xo) < TOL, rel_l2(xg, xo)
+
+
+def test_rotated_plenoptic_matches_oracle():
+    vol, cam = I.tiny_plenoptic()
+    cam.yaw = 0.4
+    x = I.gaussian_blobs(vol, seed=1011)
+    y = I.uniform_random(cam.m, seed=32)
+    plan = lt.Plan(vol, [cam])
+    assert rel_l2(host(plan.forward(dev(x).reshape(1, -1))), O.forward(vol, cam, x)) < TOL
+    assert rel_l2(host(plan.adjoint(dev(y).reshape(1, -1))), O.adjoint(vol, cam, y)) < TOL
+
+
+def test_multiview_dot_product_identity():
+    vol = I.Volume(64, 64, 64, 1.6, 1.6, 1.6)
+    cams = [I.table_single_lens(128, 0.01, yaw=y, ks=2, kt=2) for y in (0.0, 0.5, 2.1, -1.2)]
+    plan = lt.Plan(vol, cams)
+    rng = np.random.default_rng(0)
+    x = rng.random(vol.n).astype(np.float32)
+    y = rng.random(plan.m_total).astype(np.float32)
+    ax = host(plan.forward(dev(x).reshape(1, -1)))
+    aty = host(plan.adjoint(dev(y).reshape(1, -1)))
+    lhs = float(np.dot(ax.ravel(), y.astype(np.float64)))
+    rhs = float(np.dot(x.astype(np.float64), aty.ravel()))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_multiview_reconstruction_iterations_match_oracle():
+    vol = I.Volume(12, 10, 12, 5.0, 5.0, 5.0)
+    cams = [I.table_single_lens(24, 0.35, yaw=y) for y in (0.0, 0.9, -1.8)]
+    x_true = I.gaussian_blobs(vol, seed=1012)
+    ys = [O.forward(vol, c, x_true).ravel() for c in cams]
+    ys[2] = ys[2] / 1.7
+    plan = lt.Plan(vol, cams)
+    rec = lt.Recon(plan, dev(np.concatenate(ys)).reshape(1, -1), beta=1e-4)
+    rec.iterate(20)
+    xg = host(rec.get()[0])
+    ops = [(lambda v, c=c: O.forward(vol, c, v).ravel(), lambda r, c=c: O.adjoint(vol, c, r).ravel()) for c in cams]
+    ref = OR.fista(ops, ys, [None] * 3, vol.shape, 20, beta=1e-4)
+    assert rel_l2(xg, ref["x"]) < 1e-4
