@@ -151,6 +151,19 @@ LT_API lt_status lt_plenoptic_stage2(lt_plan* plan, int32_t cam, const float* fa
 LT_API lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, const float* y_cam, float* fa,
                                       void* stream);
 
+/* Autotuner (no counterpart in the paper): times each forward kernel variant
+ * (slices per weight batch x warp groups per work item) on this plan's own
+ * cameras and frames and keeps the fastest for later calls.  Allocates and
+ * frees temporary device buffers and synchronises the stream; call it once
+ * after lt_plan_create and before capturing graphs.  times_ms (host array of
+ * lt_autotune_variants() entries, may be NULL) receives each variant's best
+ * time; *chosen (may be NULL) the index kept. */
+LT_API int32_t lt_autotune_variants(void);
+LT_API lt_status lt_plan_autotune(lt_plan* plan, void* stream, double* times_ms, int32_t* chosen);
+/* Pins the forward variant (0 .. lt_autotune_variants()-1) instead of tuning;
+ * every variant computes the same operator (summation order differs). */
+LT_API lt_status lt_plan_set_forward_variant(lt_plan* plan, int32_t variant);
+
 /* Analytic work counts of one camera for one frame, computed on the host in
  * float64 from the plan's footprints (used for throughput and roofline
  * figures).  A ray-sample is one (beam, slice) pair: a beam is a target pixel

@@ -33,6 +33,11 @@ struct CameraPlan {
   float* d_rz = nullptr;           // scratch [F][nzr][ny][nxp] (rotated cameras)
   float* d_xr = nullptr;           // scratch [F][nzr][ny][nxr] (rotated cameras)
   SliceParam* d_slice = nullptr;   // [K][nz]
+  std::vector<int2> h_srange, h_trange;   // host copies of the tile slice intervals
+  int tiles_s = 0, tiles_t = 0;           // forward tiles of the target plane
+  std::vector<int4> h_items;              // forward work items {cam, k or -1, tile, cost}
+  int4* d_items = nullptr;                // this camera's items, longest first
+  int n_items = 0;
   int2* d_srange = nullptr;        // [K][tiles_s] slice interval per forward tile column
   int2* d_trange = nullptr;        // [K][tiles_t] slice interval per forward tile row
   int wmax_s = 0, wmax_t = 0, wimax_s = 0, wimax_t = 0;
@@ -72,5 +77,17 @@ struct lt_plan {
   int64_t nvox = 0;
   int64_t m_total = 0;
   int device = 0;
+  int sms = 148;
   std::vector<lt::CameraPlan> cams;
+  int4* d_items = nullptr;         // every camera's forward items, longest first
+  int n_items = 0;
+  int* d_counter = nullptr;        // persistent-launch work counter
+  int wclass = 2;                  // forward window class of the whole plan
+  int fwd_variant = 0;             // forward kernel variant (autotuned)
 };
+
+namespace lt {
+// Plan-level operators over every camera (one batched launch per stage).
+lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st);
+lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st);
+}  // namespace lt

@@ -92,25 +92,50 @@ struct RotParam {
 constexpr int kBeamTileS = 32;
 constexpr int kBeamTileT = 32;
 
+// One camera's slice -> plane transport inside a batched launch.
+constexpr int kMaxBatchCams = 24;
+struct BeamCam {
+  const float* x;          // camera-grid volume [F][nz][ny][nx] (forward input)
+  float* out;              // forward output: [F][K][nt][ns] if per_cell, else [F][..][nt][ns]
+  const float* in;         // adjoint input, same layout as out
+  const SliceParam* prm;   // [K][nz]
+  const uint8_t* mask;     // per-pixel output mask (plenoptic array plane) or null
+  const int2* srange;      // [K][tiles_s]
+  const int2* trange;      // [K][tiles_t]
+  long long x_fs, out_fs;  // frame strides
+  int32_t nx, ny, nz, ns, nt, K, per_cell, tiles_s, tiles_t;
+  int32_t wis, wit;        // adjoint windows (max over cells and slices)
+};
+struct BeamBatch {
+  BeamCam cam[kMaxBatchCams];
+  int32_t n_cams;
+  int32_t frames;
+};
+
+// Forward kernel variants chosen by the autotuner: slices per weight batch
+// and warp groups (128 threads each) splitting a tile's slices.
+constexpr int kForwardVariants = 5;
+struct ForwardVariant {
+  int32_t sb, groups;
+};
+constexpr ForwardVariant kForwardVariantTable[kForwardVariants] = {{4, 2}, {4, 1}, {2, 2}, {2, 4}, {8, 1}};
+
 // ---- kernel launchers (lt_kernels.cu) -------------------------------------
 
-// Slice -> plane beam integration (single-lens detector or plenoptic array
-// plane).  If per_cell, output is [F][K][nt][ns] (blockIdx.y = cell), else
-// the cells are summed into [F][...][nt][ns] at out + f*out_frame_stride.
-cudaError_t launch_beam_forward(const float* x, float* out, const SliceParam* prm,
-                                int nx, int ny, int nz, int ns, int nt, int K,
-                                int per_cell, const uint8_t* mask, int frames,
-                                long long x_frame_stride, long long out_frame_stride,
-                                int wmax_s, int wmax_t, const int2* srange, const int2* trange,
-                                cudaStream_t st);
+// Batched persistent forward: work items (int4 {cam, k or -1 for all cells,
+// tile, cost}) for every frame, processed in list order (longest first) by
+// a grid of resident CTAs that take the next item from *counter (zeroed by
+// the launcher).  Every output tile of every camera appears once in items.
+cudaError_t launch_beam_forward_batched(const BeamBatch& b, const int4* items, int n_items, int* counter,
+                                        int wclass, int variant, int ctas, cudaStream_t st);
+// CTAs per SM of a forward variant (for the persistent grid).
+int beam_forward_occupancy(int wclass, int variant);
+int window_class(int w);
 
-// Gather adjoint of the above: x[F][nz][ny][nx] (= or +=) sum_k sum_n ...
-// in = [F][K][nt][ns] if per_cell else [F][nt][ns] shared by all cells.
-cudaError_t launch_beam_adjoint(const float* in, float* x, const SliceParam* prm,
-                                int nx, int ny, int nz, int ns, int nt, int K,
-                                int per_cell, int accumulate, int frames,
-                                long long in_frame_stride, long long x_frame_stride,
-                                int wimax_s, int wimax_t, cudaStream_t st);
+// Batched gather adjoint over cameras that share one grid (cam[0]'s dims):
+// x[F][nz][ny][nx] (= or +=) sum over cameras and cells.
+cudaError_t launch_beam_adjoint_batched(const BeamBatch& b, float* x, long long x_fs, int accumulate,
+                                        cudaStream_t st);
 
 // zbuf: per-lenslet sub-image scratch [F][N_mu][kStage2Window^2] (the plan's,
 // or any buffer of that size).

@@ -13,6 +13,8 @@
 // no atomics (Sec. IV).  Forward and adjoint evaluate every matrix entry with
 // the same device functions on the same (target, source) pair, so the two are
 // exact transposes up to float32 summation order (Sec. IV-A).
+#include <algorithm>
+
 #include "lt_internal.h"
 
 namespace lt {
@@ -93,162 +95,220 @@ __device__ __forceinline__ int window_start(const AxisParam& a, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// Beam integration, forward.  CTA = 32 x 32 target pixels of one frame (and
-// one cell if per_cell); 4 warps, warp w owns rows w, w+4, ..., w+28 and lane
-// l column l.  Only the slices in the tile's interval (host table: where the
-// tile's footprints can meet the volume) are visited.  For a batch of SB
-// slices all threads first evaluate the s-weights of the 32 columns and the
-// t-weights of the 32 rows into shared memory (the separable O(S+T) weight
-// work of Sec. IV-B, shared by the tile), then every thread accumulates its
-// 8 pixels from the L1-resident slices.  WS/WT are compile-time windows; a
-// weight beyond a slice's own window is exactly zero.
+// Beam integration, forward: one persistent launch for every camera, cell,
+// output tile and frame of a plan.  Work items (host-built, longest first)
+// name a camera, a cell (or all cells of a single-lens camera, whose image
+// sums them) and a 32 x 32 tile of target pixels; resident CTAs take items
+// from a counter.  Per item, only the slices of the tile's interval (host
+// table: where the tile's footprints can meet the volume) are visited.  The
+// CTA's G warp groups (128 threads each) take alternate batches of SB
+// slices; for each batch a group evaluates the s-weights of the 32 columns
+// and the t-weights of the 32 rows into shared memory (the separable O(S+T)
+// weight work of Sec. IV-B, shared by the tile), then each thread (lane =
+// column, warp w of the group = rows w, w+4, ..., w+28) accumulates its 8
+// pixels from the L1-resident slices.  W is a compile-time window: a weight
+// beyond a slice's own window is exactly zero.
 // ---------------------------------------------------------------------------
 constexpr int FT_S = kBeamTileS;
 constexpr int FT_T = kBeamTileT;
-constexpr int FT_GROUPS = 2;                 // warp groups splitting the slice range
-constexpr int FT_GTHREADS = 128;             // threads per group
-constexpr int FT_THREADS = FT_GROUPS * FT_GTHREADS;
+constexpr int FT_GTHREADS = 128;
 constexpr int FT_ROWS = FT_T / 4;
-constexpr int FT_SB = 4;
+constexpr int FT_TR = 16;   // voxel rows of a tile's s-contracted slice kept in shared memory
 
 __device__ __forceinline__ void group_barrier(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(FT_GTHREADS) : "memory");
 }
 
-template <int WS, int WT>
-__global__ void __launch_bounds__(FT_THREADS)
-beam_forward_kernel(const float* __restrict__ x, float* __restrict__ out,
-                    const SliceParam* __restrict__ prm, int nx, int ny, int nz,
-                    int ns, int nt, int K, int per_cell, const uint8_t* __restrict__ mask,
-                    long long x_fs, long long out_fs, int tiles_s, int tiles_t,
-                    const int2* __restrict__ srange, const int2* __restrict__ trange) {
-  __shared__ float sw[FT_GROUPS][FT_SB][WS][FT_S];
-  __shared__ int sx[FT_GROUPS][FT_SB][WS][FT_S];
-  __shared__ float tw[FT_GROUPS][FT_SB][WT][FT_T];
-  __shared__ int ty[FT_GROUPS][FT_SB][WT][FT_T];
-  __shared__ float red[FT_T][FT_S + 1];
+template <int W, int SB, int G>
+__global__ void __launch_bounds__(G * FT_GTHREADS)
+beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict__ items, int n_items,
+                     int* __restrict__ counter) {
+  __shared__ float sw[G][SB][W][FT_S];
+  __shared__ int sx[G][SB][W][FT_S];
+  __shared__ float tw[G][SB][W][FT_T];
+  __shared__ int ty[G][SB][W][FT_T];
+  __shared__ float red[G > 1 ? G - 1 : 1][FT_T][FT_S + 1];
+  __shared__ float T[G][SB][FT_TR][FT_S];
+  __shared__ int s_item;
 
   const int grp = threadIdx.x / FT_GTHREADS;
   const int gt = threadIdx.x - grp * FT_GTHREADS;
   const int lane = gt & 31;
   const int warp = gt >> 5;
-  const int tile_s = blockIdx.x % tiles_s;
-  const int tile_t = blockIdx.x / tiles_s;
-  const int is0 = tile_s * FT_S;
-  const int it0 = tile_t * FT_T;
-  const int frame = blockIdx.z;
-  const int k_begin = per_cell ? (int)blockIdx.y : 0;
-  const int k_end = per_cell ? (int)blockIdx.y + 1 : K;
-  const float* xf = x + (long long)frame * x_fs;
+  const long long total = (long long)n_items * B.frames;
 
-  float acc[FT_ROWS];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= total) break;
+    const int4 item = items[it / B.frames];
+    const int frame = (int)(it % B.frames);
+    const BeamCam& C = B.cam[item.x];
+    const int nx = C.nx, ny = C.ny, nz = C.nz;
+    const int tile_s = item.z % C.tiles_s;
+    const int tile_t = item.z / C.tiles_s;
+    const int is0 = tile_s * FT_S;
+    const int it0 = tile_t * FT_T;
+    const int k_begin = item.y >= 0 ? item.y : 0;
+    const int k_end = item.y >= 0 ? item.y + 1 : C.K;
+    const float* xf = C.x + (long long)frame * C.x_fs;
+
+    float acc[FT_ROWS];
 #pragma unroll
-  for (int r = 0; r < FT_ROWS; ++r) acc[r] = 0.0f;
+    for (int r = 0; r < FT_ROWS; ++r) acc[r] = 0.0f;
 
-  for (int k = k_begin; k < k_end; ++k) {
-    const int2 rs = srange[k * tiles_s + tile_s];
-    const int2 rt = trange[k * tiles_t + tile_t];
-    const int n0 = max(rs.x, rt.x);
-    const int n1 = min(rs.y, rt.y);
-    const SliceParam* pk = prm + (long long)k * nz;
-    // group g takes slice batches g, g + 2, g + 4, ... of the tile's interval
-    for (int nb = n0 + grp * FT_SB; nb < n1; nb += FT_GROUPS * FT_SB) {
-      // phase A: weights of SB slices x (32 columns + 32 rows)
-      for (int task = gt; task < FT_SB * (FT_S + FT_T); task += FT_GTHREADS) {
-        const int sl = task / (FT_S + FT_T);
-        const int q = task - sl * (FT_S + FT_T);
-        const int n = nb + sl;
-        if (n >= n1) continue;
-        const SliceParam* p = pk + n;
-        if (q < FT_S) {
+    for (int k = k_begin; k < k_end; ++k) {
+      const int2 rs = C.srange[k * C.tiles_s + tile_s];
+      const int2 rt = C.trange[k * C.tiles_t + tile_t];
+      const int n0 = max(rs.x, rt.x);
+      const int n1 = min(rs.y, rt.y);
+      const SliceParam* pk = C.prm + (long long)k * nz;
+      for (int nb = n0 + grp * SB; nb < n1; nb += G * SB) {
+        // phase A: weights of SB slices x (32 columns + 32 rows)
+        for (int task = gt; task < SB * (FT_S + FT_T); task += FT_GTHREADS) {
+          const int sl = task / (FT_S + FT_T);
+          const int q = task - sl * (FT_S + FT_T);
+          const int n = nb + sl;
+          if (n >= n1) continue;
+          const SliceParam* p = pk + n;
+          const bool s_axis = q < FT_S;
+          const AxisParam& ap = s_axis ? p->s : p->t;
+          const int lim = s_axis ? nx : ny;
+          const int rr = s_axis ? q : q - FT_S;
           int jc;
           float fr;
-          footprint_centre(p->s, is0 + q, jc, fr);
-          const int mlo = (int)floorf(fr - p->s.Q + 0.5f);
-          float Flo = edge_F(mlo, fr, p->s);
+          footprint_centre(ap, (s_axis ? is0 : it0) + rr, jc, fr);
+          const int mlo = (int)floorf(fr - ap.Q + 0.5f);
+          float Flo = edge_F(mlo, fr, ap);
 #pragma unroll
-          for (int a = 0; a < WS; ++a) {
+          for (int a = 0; a < W; ++a) {
             const int j = jc + mlo + a;
-            const float Fhi = edge_F(mlo + a + 1, fr, p->s);
+            const float Fhi = edge_F(mlo + a + 1, fr, ap);
             float w = __fsub_rn(Fhi, Flo);
             Flo = Fhi;
-            if (j < 0 || j >= nx) w = 0.0f;
-            sw[grp][sl][a][q] = w;
-            sx[grp][sl][a][q] = min(max(j, 0), nx - 1);
+            if (j < 0 || j >= lim) w = 0.0f;
+            const int jj = min(max(j, 0), lim - 1);
+            if (s_axis) {
+              sw[grp][sl][a][rr] = w;
+              sx[grp][sl][a][rr] = jj;
+            } else {
+              tw[grp][sl][a][rr] = w;
+              ty[grp][sl][a][rr] = jj;   // voxel row
+            }
+          }
+        }
+        group_barrier(1 + grp);
+        // phase B.  Voxel rows the batch's pixel rows reach (monotone in the
+        // pixel row, so the tile's first and last rows bound them).
+        const int nsl = min(SB, n1 - nb);
+        int r_lo[SB], nrows_max = 0;
+#pragma unroll
+        for (int sl = 0; sl < SB; ++sl) {
+          r_lo[sl] = 0;
+          if (sl < nsl) {
+            const int a0 = ty[grp][sl][0][0], a1 = ty[grp][sl][0][FT_T - 1];
+            const int b0 = ty[grp][sl][W - 1][0], b1 = ty[grp][sl][W - 1][FT_T - 1];
+            r_lo[sl] = min(a0, a1);
+            nrows_max = max(nrows_max, max(b0, b1) - r_lo[sl] + 1);
+          }
+        }
+        if (nrows_max <= FT_TR) {
+          // B1: s-contraction T[sl][r][col] = sum_a ws[col][a] x[n][r_lo + r][sx_a(col)]
+          for (int sl = 0; sl < nsl; ++sl) {
+            const float* xs = xf + (long long)(nb + sl) * ny * nx + (long long)r_lo[sl] * nx;
+            float wsr[W];
+            int sxr[W];
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+              wsr[a] = sw[grp][sl][a][lane];
+              sxr[a] = sx[grp][sl][a][lane];
+            }
+            // rows past the volume are never referenced by B2 (clamped indices)
+            const int r_end = min(nrows_max, ny - r_lo[sl]);
+            for (int r = warp; r < r_end; r += 4) {
+              const float* xr = xs + r * nx;
+              float u = 0.0f;
+#pragma unroll
+              for (int a = 0; a < W; ++a) u = fmaf(wsr[a], __ldg(xr + sxr[a]), u);
+              T[grp][sl][r][lane] = u;
+            }
+          }
+          group_barrier(1 + grp);
+          // B2: t-contraction per pixel from shared memory
+          for (int sl = 0; sl < nsl; ++sl) {
+            const float scale = pk[nb + sl].scale;
+            const int base = r_lo[sl];
+#pragma unroll
+            for (int r = 0; r < FT_ROWS; ++r) {
+              const int row = warp + 4 * r;
+              float v = 0.0f;
+#pragma unroll
+              for (int b = 0; b < W; ++b) {
+                const int tr = min(max(ty[grp][sl][b][row] - base, 0), nrows_max - 1);
+                v = fmaf(tw[grp][sl][b][row], T[grp][sl][tr][lane], v);
+              }
+              acc[r] = fmaf(scale, v, acc[r]);
+            }
           }
         } else {
-          const int r = q - FT_S;
-          int jc;
-          float fr;
-          footprint_centre(p->t, it0 + r, jc, fr);
-          const int mlo = (int)floorf(fr - p->t.Q + 0.5f);
-          float Flo = edge_F(mlo, fr, p->t);
+          // direct gather (footprints spanning many voxel rows)
+          for (int sl = 0; sl < nsl; ++sl) {
+            const int n = nb + sl;
+            const float scale = pk[n].scale;
+            const float* xs = xf + (long long)n * ny * nx;
+            float wsr[W];
+            int sxr[W];
 #pragma unroll
-          for (int b = 0; b < WT; ++b) {
-            const int j = jc + mlo + b;
-            const float Fhi = edge_F(mlo + b + 1, fr, p->t);
-            float w = __fsub_rn(Fhi, Flo);
-            Flo = Fhi;
-            if (j < 0 || j >= ny) w = 0.0f;
-            tw[grp][sl][b][r] = w;
-            ty[grp][sl][b][r] = min(max(j, 0), ny - 1) * nx;
+            for (int a = 0; a < W; ++a) {
+              wsr[a] = sw[grp][sl][a][lane];
+              sxr[a] = sx[grp][sl][a][lane];
+            }
+#pragma unroll
+            for (int r = 0; r < FT_ROWS; ++r) {
+              const int row = warp + 4 * r;
+              float v = 0.0f;
+#pragma unroll
+              for (int b = 0; b < W; ++b) {
+                const float* xr = xs + ty[grp][sl][b][row] * nx;
+                float u = 0.0f;
+#pragma unroll
+                for (int a = 0; a < W; ++a) u = fmaf(wsr[a], __ldg(xr + sxr[a]), u);
+                v = fmaf(tw[grp][sl][b][row], u, v);
+              }
+              acc[r] = fmaf(scale, v, acc[r]);
+            }
           }
         }
+        group_barrier(1 + grp);
       }
-      group_barrier(1 + grp);
-      // phase B: accumulate (loads are always in bounds; zero weights are cheap)
-      const int nsl = min(FT_SB, n1 - nb);
-      for (int sl = 0; sl < nsl; ++sl) {
-        const int n = nb + sl;
-        const float scale = pk[n].scale;
-        const float* xs = xf + (long long)n * ny * nx;
-        float wsr[WS];
-        int sxr[WS];
+    }
+
+    // combine the groups' partial sums and write the tile
+    if (G > 1 && grp > 0) {
 #pragma unroll
-        for (int a = 0; a < WS; ++a) {
-          wsr[a] = sw[grp][sl][a][lane];
-          sxr[a] = sx[grp][sl][a][lane];
-        }
+      for (int r = 0; r < FT_ROWS; ++r) red[grp - 1][warp + 4 * r][lane] = acc[r];
+    }
+    __syncthreads();
+    if (grp == 0) {
+      const int is = is0 + lane;
+      if (is < C.ns) {
+        float* o = C.out + (long long)frame * C.out_fs + (C.per_cell ? (long long)k_begin * C.ns * C.nt : 0);
 #pragma unroll
         for (int r = 0; r < FT_ROWS; ++r) {
           const int row = warp + 4 * r;
-          float v = 0.0f;
+          const int itp = it0 + row;
+          if (itp < C.nt) {
+            float v = acc[r];
 #pragma unroll
-          for (int b = 0; b < WT; ++b) {
-            const float* xr = xs + ty[grp][sl][b][row];
-            float u = 0.0f;
-#pragma unroll
-            for (int a = 0; a < WS; ++a) u = fmaf(wsr[a], __ldg(xr + sxr[a]), u);
-            v = fmaf(tw[grp][sl][b][row], u, v);
+            for (int g = 1; g < G; ++g) v += red[g - 1][row][lane];
+            if (C.mask && !C.mask[(long long)itp * C.ns + is]) v = 0.0f;
+            o[(long long)itp * C.ns + is] = v;
           }
-          acc[r] = fmaf(scale, v, acc[r]);
-        }
-      }
-      group_barrier(1 + grp);
-    }
-  }
-
-  // combine the two groups' partial sums
-  if (grp == 1) {
-#pragma unroll
-    for (int r = 0; r < FT_ROWS; ++r) red[warp + 4 * r][lane] = acc[r];
-  }
-  __syncthreads();
-  if (grp == 0) {
-    const int is = is0 + lane;
-    if (is < ns) {
-      float* o = out + (long long)frame * out_fs + (per_cell ? (long long)blockIdx.y * ns * nt : 0);
-#pragma unroll
-      for (int r = 0; r < FT_ROWS; ++r) {
-        const int row = warp + 4 * r;
-        const int it = it0 + row;
-        if (it < nt) {
-          float v = acc[r] + red[row][lane];
-          if (mask && !mask[(long long)it * ns + is]) v = 0.0f;
-          o[(long long)it * ns + is] = v;
         }
       }
     }
+    __syncthreads();
   }
 }
 
@@ -264,18 +324,18 @@ constexpr int AT_T = 8;
 constexpr int AT_THREADS = 256;
 constexpr int AT_UCOLS = 256;   // pixel columns of the t-contracted rows kept in shared memory
 
-// CTA = 32 x 8 voxels of one slice and frame (lane = voxel column, warp =
-// voxel row).  Per cell: all threads evaluate the windows of target pixels
-// whose footprints may cover each voxel column / row and the matching entries
-// (the same cell_weight of the same (pixel, cell) pair as the forward); then
-// warp r contracts along t for its voxel row with coalesced image-row reads,
-// U[r][c] = sum_b Bt[r][b] g[row_b][c_lo + c], and each voxel contracts along
-// s from shared memory (the separable O(S+T) scheme of Sec. IV-B).
+// Gather adjoint of the batched beam integration over cameras sharing one
+// grid.  CTA = 32 x 8 voxels of one slice and frame (lane = voxel column,
+// warp = voxel row).  Per (camera, cell): all threads evaluate the windows of
+// target pixels whose footprints may cover each voxel column / row and the
+// matching entries (the same cell_weight of the same (pixel, cell) pair as
+// the forward); then warp r contracts along t for its voxel row with
+// coalesced image-row reads, U[r][c] = sum_b Bt[r][b] g[row_b][c_lo + c], and
+// each voxel contracts along s from shared memory (the separable O(S+T)
+// scheme of Sec. IV-B).  One writer per voxel, no atomics.
 __global__ void __launch_bounds__(AT_THREADS)
-beam_adjoint_kernel(const float* __restrict__ in, float* __restrict__ x,
-                    const SliceParam* __restrict__ prm, int nx, int ny, int nz,
-                    int ns, int nt, int K, int per_cell, int accumulate,
-                    long long in_fs, long long x_fs, int tiles_x) {
+beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x, long long x_fs,
+                     int accumulate, int tiles_x) {
   __shared__ float sw[WIMAX][AT_S];
   __shared__ int si[WIMAX][AT_S];
   __shared__ float tw[WIMAX][AT_T];
@@ -284,44 +344,51 @@ beam_adjoint_kernel(const float* __restrict__ in, float* __restrict__ x,
 
   const int lane = threadIdx.x & 31;
   const int row = threadIdx.x >> 5;
+  const int nx = B.cam[0].nx, ny = B.cam[0].ny, nz = B.cam[0].nz;
   const int jx0 = (blockIdx.x % tiles_x) * AT_S;
   const int jy0 = (blockIdx.x / tiles_x) * AT_T;
   const int jx1 = min(jx0 + AT_S, nx) - 1;
   const int n = blockIdx.y;
   const int frame = blockIdx.z;
-  const float* inf = in + (long long)frame * in_fs;
 
   float acc = 0.0f;
-  for (int k = 0; k < K; ++k) {
-    const SliceParam* p = prm + (long long)k * nz + n;
-    const int wis = p->wis;
-    const int wit = p->wit;
-    const float* g = inf + (per_cell ? (long long)k * ns * nt : 0);
-    // pixel columns covering every voxel column's window (monotone in the voxel index)
-    const int a0 = window_start(p->s, jx0), a1 = window_start(p->s, jx1);
-    const int c_lo = max(min(a0, a1), 0), c_hi = min(max(a0, a1) + wis - 1, ns - 1);
-    const int ncols = c_hi - c_lo + 1;
-    const bool sep = ncols > 0 && ncols <= AT_UCOLS;
-    int flag_s = 0, flag_t = 0;
-    for (int task = threadIdx.x; task < AT_S * wis + AT_T * wit; task += AT_THREADS) {
-      if (task < AT_S * wis) {
-        const int col = task / wis, q = task - col * wis;
-        const int jx = jx0 + col;
-        const int i = window_start(p->s, jx) + q;
-        float w = 0.0f;
-        if (i >= 0 && i < ns && jx < nx) {
-          int jc;
-          float fr;
-          footprint_centre(p->s, i, jc, fr);
-          w = cell_weight(jx - jc, fr, p->s);
+  for (int cam = 0; cam < B.n_cams; ++cam) {
+    const BeamCam& C = B.cam[cam];
+    const int ns = C.ns, nt = C.nt;
+    const float* inf = C.in + (long long)frame * C.out_fs;
+    for (int k = 0; k < C.K; ++k) {
+      const SliceParam* p = C.prm + (long long)k * nz + n;
+      const int wis = p->wis;
+      const int wit = p->wit;
+      const float* g = inf + (C.per_cell ? (long long)k * ns * nt : 0);
+      // pixel columns covering every voxel column's window (monotone in the voxel index)
+      const int a0 = window_start(p->s, jx0), a1 = window_start(p->s, jx1);
+      const int c_lo = max(min(a0, a1), 0), c_hi = min(max(a0, a1) + wis - 1, ns - 1);
+      const int ncols = c_hi - c_lo + 1;
+      const bool sep = ncols > 0 && ncols <= AT_UCOLS;
+      int flag_s = 0, flag_t = 0;
+      // s windows: lane = voxel column, warp r takes window entries r, r+8, ...
+      {
+        const int jx = jx0 + lane;
+        const int i0 = window_start(p->s, jx);
+        for (int q = row; q < wis; q += AT_T) {
+          const int i = i0 + q;
+          float w = 0.0f;
+          if (i >= 0 && i < ns && jx < nx) {
+            int jc;
+            float fr;
+            footprint_centre(p->s, i, jc, fr);
+            w = cell_weight(jx - jc, fr, p->s);
+          }
+          const int ic = min(max(i, 0), ns - 1);
+          sw[q][lane] = w;
+          si[q][lane] = sep ? min(max(ic - c_lo, 0), ncols - 1) : ic;
+          flag_s |= (w != 0.0f);
         }
-        const int ic = min(max(i, 0), ns - 1);
-        sw[q][col] = w;
-        si[q][col] = sep ? min(max(ic - c_lo, 0), ncols - 1) : ic;
-        flag_s |= (w != 0.0f);
-      } else {
-        const int u = task - AT_S * wis;
-        const int r = u / wit, q = u - r * wit;
+      }
+      // t windows: thread t -> voxel row t & 7, entry t >> 3
+      for (int tt = threadIdx.x; tt < AT_T * wit; tt += AT_THREADS) {
+        const int r = tt & (AT_T - 1), q = tt >> 3;
         const int jy = jy0 + r;
         const int i = window_start(p->t, jy) + q;
         float w = 0.0f;
@@ -335,32 +402,32 @@ beam_adjoint_kernel(const float* __restrict__ in, float* __restrict__ x,
         ti[q][r] = min(max(i, 0), nt - 1) * ns;
         flag_t |= (w != 0.0f);
       }
-    }
-    const int any_s = __syncthreads_or(flag_s);
-    const int any_t = __syncthreads_or(flag_t);
-    if (any_s && any_t) {
-      if (sep) {
-        for (int c = lane; c < ncols; c += 32) {
-          float u = 0.0f;
-          for (int b = 0; b < wit; ++b) u = fmaf(tw[b][row], __ldg(g + ti[b][row] + c_lo + c), u);
-          U[row][c] = u;
+      const int any_s = __syncthreads_or(flag_s);
+      const int any_t = __syncthreads_or(flag_t);
+      if (any_s && any_t) {
+        if (sep) {
+          for (int c = lane; c < ncols; c += 32) {
+            float u = 0.0f;
+            for (int b = 0; b < wit; ++b) u = fmaf(tw[b][row], __ldg(g + ti[b][row] + c_lo + c), u);
+            U[row][c] = u;
+          }
+          __syncwarp();
+          float v = 0.0f;
+          for (int q = 0; q < wis; ++q) v = fmaf(sw[q][lane], U[row][si[q][lane]], v);
+          acc = fmaf(p->scale, v, acc);
+        } else {
+          float v = 0.0f;
+          for (int b = 0; b < wit; ++b) {
+            const float* gr = g + ti[b][row];
+            float u = 0.0f;
+            for (int q = 0; q < wis; ++q) u = fmaf(sw[q][lane], __ldg(gr + si[q][lane]), u);
+            v = fmaf(tw[b][row], u, v);
+          }
+          acc = fmaf(p->scale, v, acc);
         }
-        __syncwarp();
-        float v = 0.0f;
-        for (int q = 0; q < wis; ++q) v = fmaf(sw[q][lane], U[row][si[q][lane]], v);
-        acc = fmaf(p->scale, v, acc);
-      } else {
-        float v = 0.0f;
-        for (int b = 0; b < wit; ++b) {
-          const float* gr = g + ti[b][row];
-          float u = 0.0f;
-          for (int q = 0; q < wis; ++q) u = fmaf(sw[q][lane], __ldg(gr + si[q][lane]), u);
-          v = fmaf(tw[b][row], u, v);
-        }
-        acc = fmaf(p->scale, v, acc);
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
   const int jx = jx0 + lane;
   const int jy = jy0 + row;
@@ -541,53 +608,73 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
 
 }  // namespace
 
-template <int WS, int WT>
-static void launch_fw(dim3 grid, cudaStream_t st, const float* x, float* out, const SliceParam* prm, int nx,
-                      int ny, int nz, int ns, int nt, int K, int per_cell, const uint8_t* mask, long long xfs,
-                      long long ofs, int tiles_s, int tiles_t, const int2* sr, const int2* tr) {
-  beam_forward_kernel<WS, WT><<<grid, FT_THREADS, 0, st>>>(x, out, prm, nx, ny, nz, ns, nt, K, per_cell, mask,
-                                                           xfs, ofs, tiles_s, tiles_t, sr, tr);
+int window_class(int w) { return w <= 2 ? 2 : w <= 3 ? 3 : w <= 4 ? 4 : 8; }
+
+template <int W, int SB, int G>
+static const void* fw_kernel() {
+  return (const void*)beam_forward_batched<W, SB, G>;
 }
 
-static int window_class(int w) { return w <= 2 ? 2 : w <= 3 ? 3 : w <= 4 ? 4 : 8; }
-
-cudaError_t launch_beam_forward(const float* x, float* out, const SliceParam* prm,
-                                int nx, int ny, int nz, int ns, int nt, int K,
-                                int per_cell, const uint8_t* mask, int frames,
-                                long long x_frame_stride, long long out_frame_stride,
-                                int wmax_s, int wmax_t, const int2* srange, const int2* trange,
-                                cudaStream_t st) {
-  if (wmax_s > WMAX || wmax_t > WMAX) return cudaErrorInvalidValue;
-  const int tiles_s = (ns + FT_S - 1) / FT_S;
-  const int tiles_t = (nt + FT_T - 1) / FT_T;
-  dim3 grid(tiles_s * tiles_t, per_cell ? K : 1, frames);
-  const int cs = window_class(wmax_s), ct = window_class(wmax_t);
-#define LT_FW(A, B)                                                                                     \
-  if (cs == A && ct == B) {                                                                           \
-    launch_fw<A, B>(grid, st, x, out, prm, nx, ny, nz, ns, nt, K, per_cell, mask, x_frame_stride,     \
-                    out_frame_stride, tiles_s, tiles_t, srange, trange);                              \
-    return cudaGetLastError();                                                                        \
+// Variants (slices per batch SB, warp groups G): {4,2} {4,1} {2,2} {2,4} {8,1};
+// windows of 8 use SB = 2 so that shared memory stays within 48 KB.
+template <int W>
+static const void* fw_select(int variant) {
+  if constexpr (W >= 8) {
+    return variant == 1 ? fw_kernel<W, 2, 1>() : fw_kernel<W, 2, 2>();
+  } else {
+    switch (variant) {
+      case 1: return fw_kernel<W, 4, 1>();
+      case 2: return fw_kernel<W, 2, 2>();
+      case 3: return fw_kernel<W, 2, 4>();
+      case 4: return fw_kernel<W, 8, 1>();
+      default: return fw_kernel<W, 4, 2>();
+    }
   }
-  LT_FW(2, 2) LT_FW(2, 3) LT_FW(2, 4) LT_FW(2, 8)
-  LT_FW(3, 2) LT_FW(3, 3) LT_FW(3, 4) LT_FW(3, 8)
-  LT_FW(4, 2) LT_FW(4, 3) LT_FW(4, 4) LT_FW(4, 8)
-  LT_FW(8, 2) LT_FW(8, 3) LT_FW(8, 4) LT_FW(8, 8)
-#undef LT_FW
-  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_beam_adjoint(const float* in, float* x, const SliceParam* prm,
-                                int nx, int ny, int nz, int ns, int nt, int K,
-                                int per_cell, int accumulate, int frames,
-                                long long in_frame_stride, long long x_frame_stride,
-                                int wimax_s, int wimax_t, cudaStream_t st) {
-  if (wimax_s > WIMAX || wimax_t > WIMAX) return cudaErrorInvalidValue;
+static const void* fw_select_class(int wclass, int variant) {
+  switch (wclass) {
+    case 2: return fw_select<2>(variant);
+    case 3: return fw_select<3>(variant);
+    case 4: return fw_select<4>(variant);
+    default: return fw_select<8>(variant);
+  }
+}
+
+static int fw_threads(int wclass, int variant) {
+  if (wclass >= 8) return (variant == 1 ? 1 : 2) * FT_GTHREADS;
+  return kForwardVariantTable[variant < 0 || variant >= kForwardVariants ? 0 : variant].groups * FT_GTHREADS;
+}
+
+int beam_forward_occupancy(int wclass, int variant) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fw_select_class(wclass, variant), fw_threads(wclass, variant), 0) !=
+      cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_beam_forward_batched(const BeamBatch& b, const int4* items, int n_items, int* counter,
+                                        int wclass, int variant, int ctas, cudaStream_t st) {
+  if (wclass > WMAX) return cudaErrorInvalidValue;
+  if (n_items <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)n_items * b.frames;
+  const int grid = (int)std::min<long long>(ctas, total);
+  void* args[] = {(void*)&b, (void*)&items, (void*)&n_items, (void*)&counter};
+  return cudaLaunchKernel(fw_select_class(wclass, variant), dim3(grid), dim3(fw_threads(wclass, variant)), args, 0, st);
+}
+
+cudaError_t launch_beam_adjoint_batched(const BeamBatch& b, float* x, long long x_fs, int accumulate,
+                                        cudaStream_t st) {
+  for (int c = 0; c < b.n_cams; ++c)
+    if (b.cam[c].wis > WIMAX || b.cam[c].wit > WIMAX) return cudaErrorInvalidValue;
+  const int nx = b.cam[0].nx, ny = b.cam[0].ny, nz = b.cam[0].nz;
   const int tiles_x = (nx + AT_S - 1) / AT_S;
   const int tiles_y = (ny + AT_T - 1) / AT_T;
-  dim3 grid(tiles_x * tiles_y, nz, frames);
-  beam_adjoint_kernel<<<grid, AT_THREADS, 0, st>>>(in, x, prm, nx, ny, nz, ns, nt, K, per_cell,
-                                                   accumulate, in_frame_stride, x_frame_stride,
-                                                   tiles_x);
+  dim3 grid(tiles_x * tiles_y, nz, b.frames);
+  beam_adjoint_batched<<<grid, AT_THREADS, 0, st>>>(b, x, x_fs, accumulate, tiles_x);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 //   * the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call
 //     before any stream capture.
+#include <algorithm>
 #include <mutex>
 
 #include "lt.h"
@@ -76,12 +77,32 @@ extern "C" lt_status lt_forward_camera_noalloc(lt_plan* plan, int32_t cam, const
   float* fa = nullptr;
   lt_status s = scratch_on_current_device(&fa);
   if (s != LT_OK) return s;
-  const lt_volume_desc& v = plan->vol;
   const long long fa_fs = (long long)c.K * c.Na;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = lt::launch_beam_forward(x, fa, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt, c.K, 1,
-                                          c.d_mask, plan->frames, plan->nvox, fa_fs, c.wmax_s, c.wmax_t,
-                                          c.d_srange, c.d_trange, st);
+  lt::BeamBatch b{};
+  b.n_cams = 1;
+  b.frames = plan->frames;
+  b.cam[0].x = x;
+  b.cam[0].out = fa;
+  b.cam[0].prm = c.d_slice;
+  b.cam[0].mask = c.d_mask;
+  b.cam[0].srange = c.d_srange;
+  b.cam[0].trange = c.d_trange;
+  b.cam[0].x_fs = c.nvox_c;
+  b.cam[0].out_fs = fa_fs;
+  b.cam[0].nx = c.vol_c.nx;
+  b.cam[0].ny = c.vol_c.ny;
+  b.cam[0].nz = c.vol_c.nz;
+  b.cam[0].ns = c.desc.arr_ns;
+  b.cam[0].nt = c.desc.arr_nt;
+  b.cam[0].K = c.K;
+  b.cam[0].per_cell = 1;
+  b.cam[0].tiles_s = c.tiles_s;
+  b.cam[0].tiles_t = c.tiles_t;
+  const int wclass = lt::window_class(std::max(c.wmax_s, c.wmax_t));
+  const int ctas = plan->sms * lt::beam_forward_occupancy(wclass, plan->fwd_variant);
+  cudaError_t e = lt::launch_beam_forward_batched(b, c.d_items, c.n_items, plan->d_counter, wclass,
+                                                  plan->fwd_variant, ctas, st);
   if (e != cudaSuccess) return lt::cuda_error(e, "allocation-free stage 1");
   e = lt::launch_stage2_forward(fa, y_cam, c.s2, plan->frames, fa_fs, c.M, c.d_zbuf, st);
   return e == cudaSuccess ? LT_OK : lt::cuda_error(e, "allocation-free stage 2");

@@ -213,6 +213,7 @@ static lt_status upload(const std::vector<T>& h, T** d, const char* what) {
 
 static void free_camera(CameraPlan& c) {
   cudaFree(c.d_slice);
+  cudaFree(c.d_items);
   cudaFree(c.d_rz);
   cudaFree(c.d_xr);
   cudaFree(c.d_srange);
@@ -298,7 +299,33 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
     if (r.y < 0) r = make_int2(0, 0);
   for (auto& r : trange)
     if (r.y < 0) r = make_int2(0, 0);
-  lt_status s = upload(srange, &c.d_srange, "tile slice ranges");
+  c.h_srange = srange;
+  c.h_trange = trange;
+  c.tiles_s = tiles_s;
+  c.tiles_t = tiles_t;
+  // forward work items: one per (cell, tile) when each cell has its own
+  // output plane (plenoptic array plane), one per tile over all cells when
+  // the cells sum into one image (single lens); cost = slices visited
+  const bool per_cell = c.desc.kind == LT_CAM_PLENOPTIC;
+  c.h_items.clear();
+  for (int tile = 0; tile < tiles_s * tiles_t; ++tile) {
+    const int ts = tile % tiles_s, tt = tile / tiles_s;
+    int total = 0;
+    for (int k = 0; k < c.K; ++k) {
+      const int2 a = srange[(size_t)k * tiles_s + ts], b = trange[(size_t)k * tiles_t + tt];
+      const int cost = std::max(0, std::min(a.y, b.y) - std::max(a.x, b.x));
+      if (per_cell) c.h_items.push_back(make_int4(idx, k, tile, cost));
+      total += cost;
+    }
+    if (!per_cell) c.h_items.push_back(make_int4(idx, -1, tile, total));
+  }
+  std::stable_sort(c.h_items.begin(), c.h_items.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+  std::vector<int4> local = c.h_items;
+  for (auto& it : local) it.x = 0;   // a single-camera batch names this camera 0
+  c.n_items = (int)local.size();
+  lt_status s = upload(local, &c.d_items, "forward work items");
+  if (s != LT_OK) return s;
+  s = upload(srange, &c.d_srange, "tile slice ranges");
   if (s == LT_OK) s = upload(trange, &c.d_trange, "tile slice ranges");
   if (s != LT_OK) return s;
   return upload(sp, &c.d_slice, "slice parameters");
@@ -625,6 +652,23 @@ extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_d
     off += p->cams[c].M;
   }
   p->m_total = off;
+  {
+    std::vector<int4> all;
+    for (auto& c : p->cams) {
+      all.insert(all.end(), c.h_items.begin(), c.h_items.end());
+      p->wclass = std::max(p->wclass, window_class(std::max(c.wmax_s, c.wmax_t)));
+    }
+    std::stable_sort(all.begin(), all.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+    p->n_items = (int)all.size();
+    s = upload(all, &p->d_items, "forward work items");
+    if (s == LT_OK && cudaMalloc((void**)&p->d_counter, sizeof(int)) != cudaSuccess)
+      s = set_error(LT_ENOMEM, "cudaMalloc(work counter)");
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (s != LT_OK) {
+      lt_plan_destroy(p);
+      return s;
+    }
+  }
   *out = p;
   return LT_OK;
 }
@@ -633,6 +677,8 @@ extern "C" lt_status lt_plan_destroy(lt_plan* plan) {
   if (!plan) return LT_OK;
   cudaDeviceSynchronize();
   for (auto& c : plan->cams) free_camera(c);
+  cudaFree(plan->d_items);
+  cudaFree(plan->d_counter);
   delete plan;
   return LT_OK;
 }
@@ -757,16 +803,54 @@ static lt_status to_camera_grid(lt_plan* p, CameraPlan& c, const float* x, const
   return LT_OK;
 }
 
-// Adjoint of the slice -> plane transport from `in` back to x (through the
-// transposed rotation for rotated cameras).
-static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* in, long long in_fs,
-                                        int tgt_ns, int tgt_nt, int per_cell, float* x, int accumulate,
-                                        cudaStream_t st) {
-  const lt_volume_desc& v = c.vol_c;
+// Description of camera c's slice -> plane transport for a batched launch:
+// camera-grid volume xc, forward output `out` / adjoint input `in`, both with
+// frame stride out_fs.
+static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const float* in, long long out_fs) {
+  const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
+  BeamCam b{};
+  b.x = xc;
+  b.out = out;
+  b.in = in;
+  b.prm = c.d_slice;
+  b.mask = plen ? c.d_mask : nullptr;
+  b.srange = c.d_srange;
+  b.trange = c.d_trange;
+  b.x_fs = c.nvox_c;
+  b.out_fs = out_fs;
+  b.nx = c.vol_c.nx;
+  b.ny = c.vol_c.ny;
+  b.nz = c.vol_c.nz;
+  b.ns = plen ? c.desc.arr_ns : c.desc.det_ns;
+  b.nt = plen ? c.desc.arr_nt : c.desc.det_nt;
+  b.K = c.K;
+  b.per_cell = plen ? 1 : 0;
+  b.tiles_s = c.tiles_s;
+  b.tiles_t = c.tiles_t;
+  b.wis = c.wimax_s;
+  b.wit = c.wimax_t;
+  return b;
+}
+
+static lt_status run_forward(lt_plan* p, const BeamBatch& b, const int4* items, int n_items, int wclass,
+                             cudaStream_t st) {
+  const int ctas = p->sms * beam_forward_occupancy(wclass, p->fwd_variant);
+  cudaError_t e = launch_beam_forward_batched(b, items, n_items, p->d_counter, wclass, p->fwd_variant, ctas, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward");
+}
+
+static int cam_class(const CameraPlan& c) { return window_class(std::max(c.wmax_s, c.wmax_t)); }
+
+// Adjoint of one camera's slice -> plane transport from `in` back to x
+// (through the transposed rotation for rotated cameras).
+static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* in, long long in_fs, float* x,
+                                        int accumulate, cudaStream_t st) {
+  BeamBatch b{};
+  b.n_cams = 1;
+  b.frames = p->frames;
+  b.cam[0] = beam_cam(c, nullptr, nullptr, in, in_fs);
   float* dst = c.rotated ? c.d_xr : x;
-  cudaError_t e = launch_beam_adjoint(in, dst, c.d_slice, v.nx, v.ny, v.nz, tgt_ns, tgt_nt, c.K, per_cell,
-                                      c.rotated ? 0 : accumulate, p->frames, in_fs, c.nvox_c, c.wimax_s,
-                                      c.wimax_t, st);
+  cudaError_t e = launch_beam_adjoint_batched(b, dst, c.nvox_c, c.rotated ? 0 : accumulate, st);
   if (e != cudaSuccess) return cuda_error(e, "beam adjoint");
   if (c.rotated) {
     e = launch_rotate_adjoint(c.d_xr, c.d_rz, x, c.rot, p->frames, accumulate, st);
@@ -780,31 +864,22 @@ lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, l
   const float* xc = nullptr;
   lt_status s = to_camera_grid(p, c, x, &xc, st);
   if (s != LT_OK) return s;
-  const lt_volume_desc& v = c.vol_c;
-  cudaError_t e = launch_beam_forward(xc, fa, c.d_slice, v.nx, v.ny, v.nz, c.desc.arr_ns, c.desc.arr_nt,
-                                      c.K, 1, c.d_mask, p->frames, c.nvox_c, fa_fs, c.wmax_s, c.wmax_t,
-                                      c.d_srange, c.d_trange, st);
-  return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 1");
+  BeamBatch b{};
+  b.n_cams = 1;
+  b.frames = p->frames;
+  b.cam[0] = beam_cam(c, xc, fa, nullptr, fa_fs);
+  return run_forward(p, b, c.d_items, c.n_items, cam_class(c), st);
 }
 
 lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
                          int accumulate, cudaStream_t st) {
-  return beam_adjoint_to_volume(p, c, fa, fa_fs, c.desc.arr_ns, c.desc.arr_nt, 1, x, accumulate, st);
+  return beam_adjoint_to_volume(p, c, fa, fa_fs, x, accumulate, st);
 }
 
 lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long long y_fs,
                          cudaStream_t st) {
   CameraPlan& c = p->cams[cam];
-  if (c.desc.kind == LT_CAM_SINGLE) {
-    const float* xc = nullptr;
-    lt_status s = to_camera_grid(p, c, x, &xc, st);
-    if (s != LT_OK) return s;
-    const lt_volume_desc& v = c.vol_c;
-    cudaError_t e = launch_beam_forward(xc, y, c.d_slice, v.nx, v.ny, v.nz, c.desc.det_ns, c.desc.det_nt,
-                                        c.K, 0, nullptr, p->frames, c.nvox_c, y_fs, c.wmax_s, c.wmax_t,
-                                        c.d_srange, c.d_trange, st);
-    return e == cudaSuccess ? LT_OK : cuda_error(e, "single-lens forward");
-  }
+  if (c.desc.kind == LT_CAM_SINGLE) return stage1_forward(p, c, x, y, y_fs, st);
   const long long fa_fs = (long long)c.K * c.Na;
   lt_status s = stage1_forward(p, c, x, c.d_fa, fa_fs, st);
   if (s != LT_OK) return s;
@@ -815,12 +890,87 @@ lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long lon
 lt_status camera_adjoint(lt_plan* p, int cam, const float* y, long long y_fs, float* x,
                          int accumulate, cudaStream_t st) {
   CameraPlan& c = p->cams[cam];
-  if (c.desc.kind == LT_CAM_SINGLE)
-    return beam_adjoint_to_volume(p, c, y, y_fs, c.desc.det_ns, c.desc.det_nt, 0, x, accumulate, st);
+  if (c.desc.kind == LT_CAM_SINGLE) return beam_adjoint_to_volume(p, c, y, y_fs, x, accumulate, st);
   const long long fa_fs = (long long)c.K * c.Na;
   cudaError_t e = launch_stage2_adjoint(y, c.d_fa, c.s2, p->frames, y_fs, fa_fs, st);
   if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2 adjoint");
   return stage1_adjoint(p, c, c.d_fa, fa_fs, x, accumulate, st);
+}
+
+// Every camera at once: rotated views, ONE persistent beam launch over all
+// cameras' work items (longest first), then the plenoptic microlens stages.
+lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st) {
+  const int nc = (int)p->cams.size();
+  if (nc > kMaxBatchCams) {
+    for (int c = 0; c < nc; ++c) {
+      lt_status s = camera_forward(p, c, x, y + p->cams[c].offset, p->m_total, st);
+      if (s != LT_OK) return s;
+    }
+    return LT_OK;
+  }
+  BeamBatch b{};
+  b.n_cams = nc;
+  b.frames = p->frames;
+  for (int i = 0; i < nc; ++i) {
+    CameraPlan& c = p->cams[i];
+    const float* xc = nullptr;
+    lt_status s = to_camera_grid(p, c, x, &xc, st);
+    if (s != LT_OK) return s;
+    const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
+    b.cam[i] = beam_cam(c, xc, plen ? c.d_fa : y + c.offset, nullptr, plen ? (long long)c.K * c.Na : p->m_total);
+  }
+  lt_status s = run_forward(p, b, p->d_items, p->n_items, p->wclass, st);
+  if (s != LT_OK) return s;
+  for (int i = 0; i < nc; ++i) {
+    CameraPlan& c = p->cams[i];
+    if (c.desc.kind != LT_CAM_PLENOPTIC) continue;
+    cudaError_t e = launch_stage2_forward(c.d_fa, y + c.offset, c.s2, p->frames, (long long)c.K * c.Na, p->m_total,
+                                          c.d_zbuf, st);
+    if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2");
+  }
+  return LT_OK;
+}
+
+// x = sum_c A_c^T y_c: microlens-stage adjoints, ONE gather launch over all
+// cameras that see the volume unrotated (one writer per voxel), then each
+// rotated camera through its own grid and the transposed rotation.
+lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st) {
+  const int nc = (int)p->cams.size();
+  for (int i = 0; i < nc; ++i) {
+    CameraPlan& c = p->cams[i];
+    if (c.desc.kind != LT_CAM_PLENOPTIC) continue;
+    cudaError_t e = launch_stage2_adjoint(y + c.offset, c.d_fa, c.s2, p->frames, p->m_total, (long long)c.K * c.Na,
+                                          st);
+    if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2 adjoint");
+  }
+  BeamBatch b{};
+  b.frames = p->frames;
+  int written = 0;
+  for (int i = 0; i <= nc; ++i) {
+    const bool flush = (i == nc && b.n_cams > 0) || b.n_cams == kMaxBatchCams;
+    if (flush) {
+      cudaError_t e = launch_beam_adjoint_batched(b, x, p->nvox, written ? 1 : 0, st);
+      if (e != cudaSuccess) return cuda_error(e, "beam adjoint");
+      written = 1;
+      b.n_cams = 0;
+    }
+    if (i == nc) break;
+    CameraPlan& c = p->cams[i];
+    if (c.rotated) continue;
+    const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
+    b.cam[b.n_cams++] = beam_cam(c, nullptr, nullptr, plen ? c.d_fa : y + c.offset,
+                                 plen ? (long long)c.K * c.Na : p->m_total);
+  }
+  for (int i = 0; i < nc; ++i) {
+    CameraPlan& c = p->cams[i];
+    if (!c.rotated) continue;
+    const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
+    lt_status s = beam_adjoint_to_volume(p, c, plen ? c.d_fa : y + c.offset,
+                                         plen ? (long long)c.K * c.Na : p->m_total, x, written, st);
+    if (s != LT_OK) return s;
+    written = 1;
+  }
+  return LT_OK;
 }
 
 }  // namespace lt
@@ -842,22 +992,13 @@ static lt_status check_plenoptic(const lt_plan* p, int cam) {
 extern "C" lt_status lt_forward(lt_plan* plan, const float* x, float* y, void* stream) {
   clear_error();
   if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
-  for (int c = 0; c < (int)plan->cams.size(); ++c) {
-    lt_status s = camera_forward(plan, c, x, y + plan->cams[c].offset, plan->m_total, (cudaStream_t)stream);
-    if (s != LT_OK) return s;
-  }
-  return LT_OK;
+  return plan_forward(plan, x, y, (cudaStream_t)stream);
 }
 
 extern "C" lt_status lt_adjoint(lt_plan* plan, const float* y, float* x, void* stream) {
   clear_error();
   if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
-  for (int c = 0; c < (int)plan->cams.size(); ++c) {
-    lt_status s = camera_adjoint(plan, c, y + plan->cams[c].offset, plan->m_total, x, c > 0,
-                                 (cudaStream_t)stream);
-    if (s != LT_OK) return s;
-  }
-  return LT_OK;
+  return plan_adjoint(plan, y, x, (cudaStream_t)stream);
 }
 
 extern "C" lt_status lt_forward_camera(lt_plan* plan, int32_t cam, const float* x, float* y_cam,
@@ -923,3 +1064,65 @@ extern "C" lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, con
 }
 
 extern "C" const char* lt_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int32_t lt_autotune_variants(void) { return kForwardVariants; }
+
+extern "C" lt_status lt_plan_autotune(lt_plan* plan, void* stream, double* times_ms, int32_t* chosen) {
+  clear_error();
+  if (!plan) return set_error(LT_EINVAL, "plan is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nx = (size_t)plan->frames * plan->nvox, ny = (size_t)plan->frames * plan->m_total;
+  float *x = nullptr, *y = nullptr;
+  if (cudaMalloc((void**)&x, nx * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&y, ny * sizeof(float)) != cudaSuccess) {
+    cudaFree(x);
+    return set_error(LT_ENOMEM, "autotune buffers");
+  }
+  cudaMemsetAsync(x, 0, nx * sizeof(float), st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  int best_v = 0;
+  lt_status s = LT_OK;
+  const int saved = plan->fwd_variant;
+  for (int v = 0; v < kForwardVariants && s == LT_OK; ++v) {
+    plan->fwd_variant = v;
+    double tv = 1e30;
+    for (int rep = 0; rep < 4 && s == LT_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      s = plan_forward(plan, x, y, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tv = std::min(tv, (double)ms);   // first run warms up
+    }
+    if (times_ms) times_ms[v] = tv;
+    if (tv < best) {
+      best = tv;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (s != LT_OK) {
+    plan->fwd_variant = saved;
+    return s;
+  }
+  plan->fwd_variant = best_v;
+  if (chosen) *chosen = best_v;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "autotune");
+}
+
+extern "C" lt_status lt_plan_set_forward_variant(lt_plan* plan, int32_t variant) {
+  clear_error();
+  if (!plan) return set_error(LT_EINVAL, "plan is NULL");
+  if (variant < 0 || variant >= kForwardVariants)
+    return set_error(LT_EINVAL, "forward variant %d outside [0, %d)", variant, kForwardVariants);
+  plan->fwd_variant = variant;
+  return LT_OK;
+}

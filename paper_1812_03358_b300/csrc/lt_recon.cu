@@ -208,10 +208,8 @@ static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 2
 static lt_status recon_step(lt_recon* R, int sel, cudaStream_t st) {
   lt_plan* P = R->plan;
   const float* z = R->z[sel];
-  for (int c = 0; c < R->C; ++c) {  // step 1a: p_c = A_c z
-    lt_status s = camera_forward(P, c, z, R->p + P->cams[c].offset, R->M, st);
-    if (s != LT_OK) return s;
-  }
+  lt_status s = plan_forward(P, z, R->p, st);  // step 1a: p_c = A_c z for every camera
+  if (s != LT_OK) return s;
   const int est = R->prm.estimate_gains && R->C > 1;
   if (est)  // step 1b inner products
     for (int c = 1; c < R->C; ++c)
@@ -221,10 +219,8 @@ static lt_status recon_step(lt_recon* R, int sel, cudaStream_t st) {
   for (int c = 0; c < R->C; ++c)  // W (p - gamma y)
     residual_kernel<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
         R->y, R->w, R->p, R->r, R->gains, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->fit_part);
-  for (int c = 0; c < R->C; ++c) {  // step 1c + 2: g = sum_c A_c^T r_c
-    lt_status s = camera_adjoint(P, c, R->r + P->cams[c].offset, R->M, R->g, c > 0, st);
-    if (s != LT_OK) return s;
-  }
+  s = plan_adjoint(P, R->r, R->g, st);  // step 1c + 2: g = sum_c A_c^T r_c
+  if (s != LT_OK) return s;
   const lt_volume_desc& v = P->vol;
   dim3 grid((v.nx + 31) / 32, (v.ny + 7) / 8, v.nz * R->F);
   const float beta = (float)R->prm.beta;
@@ -245,11 +241,10 @@ static lt_status load_data(lt_recon* R, const float* y, const float* w, bool new
   lt_status s = LT_OK;
   if (new_weights) {
     fill_kernel<<<grid_for(FN), 256, 0, st>>>(R->g, (long long)FN, 1.0f);
-    for (int c = 0; c < R->C && s == LT_OK; ++c)
-      s = camera_forward(P, c, R->g, R->p + P->cams[c].offset, R->M, st);
+    s = plan_forward(P, R->g, R->p, st);
+    if (s != LT_OK) return s;
     mul_kernel<<<grid_for(FM), 256, 0, st>>>(R->r, R->p, R->w, (long long)FM);
-    for (int c = 0; c < R->C && s == LT_OK; ++c)
-      s = camera_adjoint(P, c, R->r + P->cams[c].offset, R->M, R->D, c > 0, st);
+    s = plan_adjoint(P, R->r, R->D, st);
     if (s != LT_OK) return s;
   }
   for (int c = 0; c < R->C; ++c)

@@ -82,6 +82,9 @@ _SIGS = {
     "lt_camera_stats_get": (c_int32, [c_void_p, c_int32, POINTER(lt_camera_stats)]),
     "lt_recon_set_data": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lt_recon_kernels_per_iteration": (c_int32, [c_void_p, POINTER(c_int32)]),
+    "lt_autotune_variants": (c_int32, []),
+    "lt_plan_autotune": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
+    "lt_plan_set_forward_variant": (c_int32, [c_void_p, c_int32]),
     "lt_last_error": (c_char_p, []),
 }
 
@@ -189,6 +192,18 @@ def lt_plenoptic_stage2(plan, cam, fa_ptr, y_ptr, stream=0):
 
 def lt_plenoptic_stage2_adjoint(plan, cam, y_ptr, fa_ptr, stream=0):
     _check(lib().lt_plenoptic_stage2_adjoint(plan, cam, y_ptr, fa_ptr, stream))
+
+
+def lt_plan_autotune(plan, stream: int = 0):
+    n = lib().lt_autotune_variants()
+    times = (c_double * n)()
+    chosen = c_int32()
+    _check(lib().lt_plan_autotune(plan, stream, times, byref(chosen)))
+    return chosen.value, list(times)
+
+
+def lt_plan_set_forward_variant(plan, variant: int) -> None:
+    _check(lib().lt_plan_set_forward_variant(plan, variant))
 
 
 def lt_camera_stats_get(plan, cam: int) -> dict:
@@ -323,6 +338,10 @@ class Plan:
         lt_adjoint_camera(self.handle, cam, _dev_f32(y, self.frames * m, "y"),
                           _dev_f32(x, self.frames * self.nvox, "x"), int(accumulate), _stream())
         return x
+
+    def autotune(self):
+        """Times the forward kernel variants on this plan and keeps the fastest."""
+        return lt_plan_autotune(self.handle, _stream())
 
     def stats(self, cam):
         return lt_camera_stats_get(self.handle, cam)
