@@ -1,0 +1,89 @@
+/*
+ * lt_nn.h - C ABI of the learned warm start's layers (no counterpart in the
+ * paper; a 3D U-Net that maps a normalised back-projection A^T y to an initial
+ * volume for the reconstruction of Sec. V).
+ *
+ * Tensors are channels-last: [batch][D][H][W][C], C fastest.  Activations and
+ * weights are bfloat16 (uint16_t bit patterns), accumulation is float32.
+ * Convolution weights are [Co][27][Ci] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)),
+ * 3x3x3 with zero padding 1, stride 1.  Channel counts must be multiples of
+ * 16 (pad the network input to 16 channels).  All pointers are device
+ * pointers owned by the caller; calls are asynchronous on the stream and
+ * return LT_EINVAL for bad sizes, LT_ECUDA for launch errors.
+ */
+#ifndef LT_NN_H
+#define LT_NN_H
+
+#include <stdint.h>
+
+#include "lt.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* out[v][o_off + co] = act(b[co] + sum_{tap,ci} w[co][tap][ci] in[v + tap][ci]);
+ * act = ReLU if relu != 0.  out has o_stride channels per voxel (>= o_off+Co),
+ * so decoder outputs can be written into a concatenation buffer.  Output is
+ * bfloat16 (out_bf) and/or float32 (out_f); either may be NULL. */
+LT_API lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
+                              float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
+                              int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, void* stream);
+
+/* Weight gradient: dw[co][tap][ci] += sum_v g[v][co] in[v + tap][ci] (float32
+ * accumulate, dw must be zeroed by the caller) and db[co] += sum_v g[v][co]
+ * (db may be NULL).  g has Co channels per voxel. */
+LT_API lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, float* dw, float* db, int32_t batch,
+                                    int32_t D, int32_t H, int32_t W, int32_t Ci, int32_t Co, void* stream);
+
+/* wt[ci][tap][co] = w[co][26 - tap][ci]: the weights whose convolution is the
+ * data gradient (the transposed convolution) of lt_nn_conv3d. */
+LT_API lt_status lt_nn_conv3d_flip(const uint16_t* w, uint16_t* wt, int32_t Ci, int32_t Co, void* stream);
+
+/* Elementwise helpers on n elements. */
+LT_API lt_status lt_nn_f32_to_bf16(const float* x, uint16_t* y, int64_t n, void* stream);
+LT_API lt_status lt_nn_bf16_to_f32(const uint16_t* x, float* y, int64_t n, void* stream);
+/* g[i] = (y[i] > 0) ? g[i] : 0 (ReLU backward, in place on bfloat16). */
+LT_API lt_status lt_nn_relu_backward(const uint16_t* y, uint16_t* g, int64_t n, void* stream);
+
+/* 2x2x2 average pooling [b][D][H][W][C] -> [b][D/2][H/2][W/2][C] and its
+ * adjoint (gradient); D, H, W even.  Channel strides/offsets as in conv. */
+LT_API lt_status lt_nn_avgpool2(const uint16_t* in, uint16_t* out, int32_t batch, int32_t D, int32_t H, int32_t W,
+                                int32_t C, int32_t i_stride, int32_t i_off, void* stream);
+LT_API lt_status lt_nn_avgpool2_backward(const uint16_t* gout, uint16_t* gin, int32_t batch, int32_t D, int32_t H,
+                                         int32_t W, int32_t C, int32_t i_stride, int32_t i_off, void* stream);
+/* Nearest 2x upsampling of [b][d][h][w][C] into channels [o_off, o_off+C) of a
+ * [b][2d][2h][2w][o_stride] tensor, and its adjoint (sum of the 8 children). */
+LT_API lt_status lt_nn_upsample2(const uint16_t* in, uint16_t* out, int32_t batch, int32_t d, int32_t h, int32_t w,
+                                 int32_t C, int32_t o_stride, int32_t o_off, void* stream);
+LT_API lt_status lt_nn_upsample2_backward(const uint16_t* gout, uint16_t* gin, int32_t batch, int32_t d, int32_t h,
+                                          int32_t w, int32_t C, int32_t o_stride, int32_t o_off, void* stream);
+/* Copy channels [s_off, s_off+C) of a [v][s_stride] tensor into channels
+ * [d_off, d_off+C) of a [v][d_stride] tensor (skip connections). */
+LT_API lt_status lt_nn_copy_channels(const uint16_t* src, uint16_t* dst, int64_t voxels, int32_t C, int32_t s_stride,
+                                     int32_t s_off, int32_t d_stride, int32_t d_off, void* stream);
+/* Adam step on float32 master weights p (and their bfloat16 copy pb, may be
+ * NULL): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr mhat/(sqrt(vhat)+eps). */
+LT_API lt_status lt_nn_adam(float* p, uint16_t* pb, const float* g, float* m, float* v, int64_t n, float lr,
+                            float b1, float b2, float eps, int32_t step, void* stream);
+
+/* out[i] = a[i] + b[i] (bfloat16, float32 arithmetic). */
+LT_API lt_status lt_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, int64_t n, void* stream);
+
+/* Network input from a back-projection bp = A^T y and the majoriser diagonal
+ * d: r[v] = bp[v] / d[v] (0 where d = 0) and *m = max_v r[v] (device float,
+ * r >= 0), then u[v][0] = r[v] / *m, u[v][1..15] = 0 (bfloat16, 16 channels). */
+LT_API lt_status lt_nn_prepare_input(const float* bp, const float* d, float* r, float* m, uint16_t* u, int64_t voxels,
+                                     void* stream);
+/* x0[v] = max(out[v][0], 0) * (*m): the warm start from the network output. */
+LT_API lt_status lt_nn_unpack_output(const float* out, const float* m, float* x0, int64_t voxels, void* stream);
+/* Mean-squared error of out[v][0] against target[v] / (*m): g[v][0] =
+ * 2 (out - t) / V, g[v][1..15] = 0, *loss += sum (out - t)^2 / V. */
+LT_API lt_status lt_nn_mse(const float* out, const float* target, const float* m, float* g, float* loss,
+                           int64_t voxels, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LT_NN_H */

@@ -1,0 +1,531 @@
+// Layers of the learned warm start (3D U-Net): bfloat16 implicit-GEMM 3x3x3
+// convolution on the tensor cores (warp-level MMA, float32 accumulation),
+// its weight gradient, and the small pooling / upsampling / optimiser
+// kernels.  Channels-last activations, every global access bounds-checked.
+#include <cuda_bf16.h>
+#include <mma.h>
+
+#include <algorithm>
+
+#include "lt.h"
+#include "lt_host.h"
+#include "lt_nn.h"
+
+using namespace nvcuda;
+
+namespace lt {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int CV_M = 64;        // output voxels per CTA
+constexpr int CV_K = 16;        // input channels per k step
+constexpr int CV_LD = 24;       // bf16 leading dimension of the staged tiles (multiple of 8)
+constexpr int CV_THREADS = 128; // 4 warps, warp w owns voxel rows 16w .. 16w+15
+
+__device__ __forceinline__ void tap_offset(int tap, int& dz, int& dy, int& dx) {
+  dz = tap / 9 - 1;
+  dy = (tap / 3) % 3 - 1;
+  dx = tap % 3 - 1;
+}
+
+// Implicit GEMM: M = voxels, N = Co (NB columns per CTA), K = 27 x Ci.
+// A tile (64 voxels x 16 channels of one tap) and B tile (16 k x NB) are
+// staged in shared memory with bounds-checked 16-byte loads (zero padding).
+template <int NB>
+__global__ void __launch_bounds__(CV_THREADS)
+conv3d_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
+              bf16* __restrict__ out_bf, float* __restrict__ out_f, int D, int H, int W, int Ci, int Co,
+              int o_stride, int o_off, int relu) {
+  __shared__ __align__(128) bf16 As[CV_M][CV_LD];
+  __shared__ __align__(128) bf16 Bs[NB][CV_LD];
+  __shared__ __align__(128) float Cs[4][16][NB + 4];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const long long V = (long long)D * H * W;
+  const long long m0 = (long long)blockIdx.x * CV_M;
+  const int n0 = blockIdx.y * NB;
+  const int b = blockIdx.z;
+  const bf16* inb = in + (long long)b * V * Ci;
+
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[NB / 16];
+#pragma unroll
+  for (int j = 0; j < NB / 16; ++j) wmma::fill_fragment(acc[j], 0.0f);
+
+  // this thread's A row (voxel) and half (8 channels)
+  const int arow = tid >> 1, ahalf = tid & 1;
+  const long long av = m0 + arow;
+  int az = 0, ay = 0, ax = 0;
+  if (av < V) {
+    az = (int)(av / ((long long)H * W));
+    const int rem = (int)(av - (long long)az * H * W);
+    ay = rem / W;
+    ax = rem - ay * W;
+  }
+  const long long K = 27LL * Ci;
+  for (int tap = 0; tap < 27; ++tap) {
+    int dz, dy, dx;
+    tap_offset(tap, dz, dy, dx);
+    const int zz = az + dz, yy = ay + dy, xx = ax + dx;
+    const bool ain = av < V && zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
+    const long long aoff = ain ? (((long long)zz * H + yy) * W + xx) * Ci + ahalf * 8 : 0;
+    for (int c0 = 0; c0 < Ci; c0 += CV_K) {
+      uint4 av4 = make_uint4(0, 0, 0, 0);
+      if (ain) av4 = *reinterpret_cast<const uint4*>(inb + aoff + c0);
+      *reinterpret_cast<uint4*>(&As[arow][ahalf * 8]) = av4;
+      for (int t = tid; t < NB * 2; t += CV_THREADS) {
+        const int n = t >> 1, h = t & 1;
+        uint4 bv = make_uint4(0, 0, 0, 0);
+        if (n0 + n < Co) bv = *reinterpret_cast<const uint4*>(w + (long long)(n0 + n) * K + (long long)tap * Ci + c0 + h * 8);
+        *reinterpret_cast<uint4*>(&Bs[n][h * 8]) = bv;
+      }
+      __syncthreads();
+      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
+      wmma::load_matrix_sync(a, &As[warp * 16][0], CV_LD);
+#pragma unroll
+      for (int j = 0; j < NB / 16; ++j) {
+        wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> bfr;
+        wmma::load_matrix_sync(bfr, &Bs[j * 16][0], CV_LD);
+        wmma::mma_sync(acc[j], a, bfr, acc[j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB / 16; ++j) wmma::store_matrix_sync(&Cs[warp][0][j * 16], acc[j], NB + 4, wmma::mem_row_major);
+  __syncwarp();
+  for (int e = lane; e < 16 * NB; e += 32) {
+    const int r = e / NB, c = e - r * NB;
+    const long long v = m0 + warp * 16 + r;
+    const int co = n0 + c;
+    if (v < V && co < Co) {
+      float val = Cs[warp][r][c] + (bias ? bias[co] : 0.0f);
+      if (relu) val = fmaxf(val, 0.0f);
+      const long long o = ((long long)b * V + v) * o_stride + o_off + co;
+      if (out_bf) out_bf[o] = __float2bfloat16_rn(val);
+      if (out_f) out_f[o] = val;
+    }
+  }
+}
+
+// Weight gradient: for one tap and 16 input channels, dW[co][tap][ci] =
+// sum over a chunk of voxels of g[v][co] in[v + tap][ci]; M = Co (64 per
+// CTA), N = 16, K = voxels (16 per step).  Partial sums are added with float
+// atomics (order-dependent rounding only).
+constexpr int WG_STEPS = 128;   // k steps (of 16 voxels) per CTA
+
+__global__ void __launch_bounds__(CV_THREADS)
+conv3d_wgrad_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ dw, int D, int H,
+                    int W, int Ci, int Co, int batch) {
+  __shared__ __align__(128) bf16 As[64][CV_LD];   // (co, v)
+  __shared__ __align__(128) bf16 Bs[16][CV_LD];   // (v, ci)
+  __shared__ __align__(128) float Cs[4][16][20];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tap = blockIdx.x / (Ci / 16);
+  const int c0 = (blockIdx.x - tap * (Ci / 16)) * 16;
+  const int n0 = blockIdx.y * 64;
+  const long long V = (long long)D * H * W;
+  const long long vtot = V * batch;
+  int dz, dy, dx;
+  tap_offset(tap, dz, dy, dx);
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
+  wmma::fill_fragment(acc, 0.0f);
+  const long long vbeg = (long long)blockIdx.z * WG_STEPS * 16;
+  for (int step = 0; step < WG_STEPS; ++step) {
+    const long long v0 = vbeg + (long long)step * 16;
+    if (v0 >= vtot) break;   // uniform
+    // A: g[v0 + k][n0 + m] -> As[m][k]; 16 voxels x 64 channels, 8 per thread
+    {
+      const int k = tid >> 3, mc = (tid & 7) * 8;
+      const long long v = v0 + k;
+      uint4 gv = make_uint4(0, 0, 0, 0);
+      if (v < vtot && n0 + mc < Co) gv = *reinterpret_cast<const uint4*>(g + v * Co + n0 + mc);
+      const bf16* e = reinterpret_cast<const bf16*>(&gv);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) As[mc + i][k] = e[i];
+    }
+    // B: in[v0 + k shifted by tap][c0 + n] -> Bs[k][n]; 16 voxels x 16 channels
+    if (tid < 32) {
+      const int k = tid >> 1, h = tid & 1;
+      const long long v = v0 + k;
+      uint4 iv = make_uint4(0, 0, 0, 0);
+      if (v < vtot) {
+        const long long bb = v / V;
+        const long long vv = v - bb * V;
+        const int z = (int)(vv / ((long long)H * W));
+        const int rem = (int)(vv - (long long)z * H * W);
+        const int y = rem / W, x = rem - (rem / W) * W;
+        const int zz = z + dz, yy = y + dy, xx = x + dx;
+        if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
+          iv = *reinterpret_cast<const uint4*>(in + ((bb * V) + ((long long)zz * H + yy) * W + xx) * Ci + c0 + h * 8);
+      }
+      *reinterpret_cast<uint4*>(&Bs[k][h * 8]) = iv;
+    }
+    __syncthreads();
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bfr;
+    wmma::load_matrix_sync(a, &As[warp * 16][0], CV_LD);
+    wmma::load_matrix_sync(bfr, &Bs[0][0], CV_LD);
+    wmma::mma_sync(acc, a, bfr, acc);
+    __syncthreads();
+  }
+  wmma::store_matrix_sync(&Cs[warp][0][0], acc, 20, wmma::mem_row_major);
+  __syncwarp();
+  for (int e = lane; e < 256; e += 32) {
+    const int r = e >> 4, c = e & 15;
+    const int co = n0 + warp * 16 + r;
+    if (co < Co) atomicAdd(dw + ((long long)co * 27 + tap) * Ci + c0 + c, Cs[warp][r][c]);
+  }
+}
+
+__global__ void bias_grad_kernel(const bf16* __restrict__ g, float* __restrict__ db, long long vtot, int Co) {
+  // one block per output channel chunk of 32; threads stride over voxels
+  const int co = blockIdx.x * 32 + (threadIdx.x & 31);
+  float acc = 0.0f;
+  if (co < Co)
+    for (long long v = (threadIdx.x >> 5) + (long long)blockIdx.y * 8; v < vtot; v += 8LL * gridDim.y)
+      acc += __bfloat162float(g[v * Co + co]);
+  __shared__ float sh[8][33];
+  sh[threadIdx.x >> 5][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32 && co < Co) {
+    float s = 0.0f;
+    for (int i = 0; i < 8; ++i) s += sh[i][threadIdx.x];
+    atomicAdd(db + co, s);
+  }
+}
+
+__global__ void flip_kernel(const bf16* __restrict__ w, bf16* __restrict__ wt, int Ci, int Co) {
+  const long long n = 27LL * Ci * Co;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    // i indexes wt[ci][tap][co]
+    const int co = (int)(i % Co);
+    const long long r = i / Co;
+    const int tap = (int)(r % 27);
+    const int ci = (int)(r / 27);
+    wt[i] = w[((long long)co * 27 + (26 - tap)) * Ci + ci];
+  }
+}
+
+__global__ void f2b_kernel(const float* x, bf16* y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+__global__ void b2f_kernel(const bf16* x, float* y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __bfloat162float(x[i]);
+}
+__global__ void relu_bwd_kernel(const bf16* y, bf16* g, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!(__bfloat162float(y[i]) > 0.0f)) g[i] = __float2bfloat16_rn(0.0f);
+}
+
+__global__ void avgpool_kernel(const bf16* in, bf16* out, int batch, int D, int H, int W, int C, int is, int io) {
+  const int d = D / 2, h = H / 2, w = W / 2;
+  const long long n = (long long)batch * d * h * w * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    long long r = i / C;
+    const int x = (int)(r % w); r /= w;
+    const int y = (int)(r % h); r /= h;
+    const int z = (int)(r % d);
+    const int b = (int)(r / d);
+    float s = 0.0f;
+    for (int k = 0; k < 8; ++k) {
+      const int zz = 2 * z + (k >> 2), yy = 2 * y + ((k >> 1) & 1), xx = 2 * x + (k & 1);
+      s += __bfloat162float(in[((((long long)b * D + zz) * H + yy) * W + xx) * is + io + c]);
+    }
+    out[i] = __float2bfloat16_rn(0.125f * s);
+  }
+}
+__global__ void avgpool_bwd_kernel(const bf16* gout, bf16* gin, int batch, int D, int H, int W, int C, int is, int io) {
+  const long long n = (long long)batch * D * H * W * C;
+  const int d = D / 2, h = H / 2, w = W / 2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    long long r = i / C;
+    const int x = (int)(r % W); r /= W;
+    const int y = (int)(r % H); r /= H;
+    const int z = (int)(r % D);
+    const int b = (int)(r / D);
+    const float v = __bfloat162float(gout[((((long long)b * d + z / 2) * h + y / 2) * w + x / 2) * C + c]);
+    gin[((((long long)b * D + z) * H + y) * W + x) * is + io + c] = __float2bfloat16_rn(0.125f * v);
+  }
+}
+__global__ void upsample_kernel(const bf16* in, bf16* out, int batch, int d, int h, int w, int C, int os, int oo) {
+  const int D = 2 * d, H = 2 * h, W = 2 * w;
+  const long long n = (long long)batch * D * H * W * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    long long r = i / C;
+    const int x = (int)(r % W); r /= W;
+    const int y = (int)(r % H); r /= H;
+    const int z = (int)(r % D);
+    const int b = (int)(r / D);
+    out[((((long long)b * D + z) * H + y) * W + x) * os + oo + c] = in[((((long long)b * d + z / 2) * h + y / 2) * w + x / 2) * C + c];
+  }
+}
+__global__ void upsample_bwd_kernel(const bf16* gout, bf16* gin, int batch, int d, int h, int w, int C, int os, int oo) {
+  const long long n = (long long)batch * d * h * w * C;
+  const int D = 2 * d, H = 2 * h, W = 2 * w;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    long long r = i / C;
+    const int x = (int)(r % w); r /= w;
+    const int y = (int)(r % h); r /= h;
+    const int z = (int)(r % d);
+    const int b = (int)(r / d);
+    float s = 0.0f;
+    for (int k = 0; k < 8; ++k) {
+      const int zz = 2 * z + (k >> 2), yy = 2 * y + ((k >> 1) & 1), xx = 2 * x + (k & 1);
+      s += __bfloat162float(gout[((((long long)b * D + zz) * H + yy) * W + xx) * os + oo + c]);
+    }
+    gin[i] = __float2bfloat16_rn(s);
+  }
+}
+__global__ void copy_channels_kernel(const bf16* src, bf16* dst, long long voxels, int C, int ss, int so, int ds, int dof) {
+  const long long n = voxels * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long v = i / C;
+    const int c = (int)(i - v * C);
+    dst[v * ds + dof + c] = src[v * ss + so + c];
+  }
+}
+__global__ void adam_kernel(float* p, bf16* pb, const float* g, float* m, float* v, long long n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    if (pb) pb[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void add_kernel(const bf16* a, const bf16* b, bf16* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16_rn(__bfloat162float(a[i]) + __bfloat162float(b[i]));
+}
+__global__ void ratio_max_kernel(const float* bp, const float* d, float* r, float* m, long long n) {
+  float mx = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = d[i] > 0.0f ? fmaxf(bp[i] / d[i], 0.0f) : 0.0f;
+    r[i] = v;
+    mx = fmaxf(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(m), __float_as_int(mx));   // non-negative floats
+}
+__global__ void pack_input_kernel(const float* r, const float* m, bf16* u, long long n) {
+  const float inv = *m > 0.0f ? 1.0f / *m : 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n * 16; i += (long long)gridDim.x * blockDim.x)
+    u[i] = __float2bfloat16_rn((i & 15) == 0 ? r[i >> 4] * inv : 0.0f);
+}
+__global__ void unpack_output_kernel(const float* out, const float* m, float* x0, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x0[i] = fmaxf(out[i * 16], 0.0f) * (*m);
+}
+__global__ void mse_kernel(const float* out, const float* t, const float* m, float* g, float* loss, long long n) {
+  const float inv = *m > 0.0f ? 1.0f / *m : 0.0f;
+  const float sc = 1.0f / (float)n;
+  float acc = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n * 16; i += (long long)gridDim.x * blockDim.x) {
+    if ((i & 15) == 0) {
+      const float d = out[i] - t[i >> 4] * inv;
+      g[i] = 2.0f * d * sc;
+      acc += d * d * sc;
+    } else {
+      g[i] = 0.0f;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+int grid1d(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 32); }
+
+}  // namespace
+}  // namespace lt
+
+using namespace lt;
+
+static lt_status launched(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LT_OK : cuda_error(e, what);
+}
+
+extern "C" lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
+                                  float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
+                                  int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, void* stream) {
+  clear_error();
+  if (!in || !w || (!out_bf && !out_f) || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 ||
+      Ci % 16 || Co % 16 || o_off < 0 || o_stride < o_off + Co)
+    return set_error(LT_EINVAL, "conv3d: bad arguments (channels must be multiples of 16)");
+  const long long V = (long long)D * H * W;
+  const int nb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
+  dim3 grid((unsigned)((V + CV_M - 1) / CV_M), Co / nb, batch);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bf16* i_ = reinterpret_cast<const bf16*>(in);
+  const bf16* w_ = reinterpret_cast<const bf16*>(w);
+  bf16* o_ = reinterpret_cast<bf16*>(out_bf);
+  if (nb == 64) conv3d_kernel<64><<<grid, CV_THREADS, 0, st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride, o_off, relu);
+  else if (nb == 32) conv3d_kernel<32><<<grid, CV_THREADS, 0, st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride, o_off, relu);
+  else conv3d_kernel<16><<<grid, CV_THREADS, 0, st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride, o_off, relu);
+  return launched("conv3d");
+}
+
+extern "C" lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, float* dw, float* db, int32_t batch,
+                                        int32_t D, int32_t H, int32_t W, int32_t Ci, int32_t Co, void* stream) {
+  clear_error();
+  if (!in || !g || !dw || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 || Ci % 16 || Co % 16)
+    return set_error(LT_EINVAL, "conv3d_wgrad: bad arguments (channels must be multiples of 16)");
+  const long long vtot = (long long)D * H * W * batch;
+  const long long chunks = (vtot + 16LL * WG_STEPS - 1) / (16LL * WG_STEPS);
+  cudaStream_t st = (cudaStream_t)stream;
+  dim3 grid(27 * (Ci / 16), (Co + 63) / 64, (unsigned)chunks);
+  conv3d_wgrad_kernel<<<grid, CV_THREADS, 0, st>>>(reinterpret_cast<const bf16*>(in), reinterpret_cast<const bf16*>(g),
+                                                    dw, D, H, W, Ci, Co, batch);
+  if (db) {
+    dim3 gb((Co + 31) / 32, (unsigned)std::min<long long>(1024, (vtot + 7) / 8));
+    bias_grad_kernel<<<gb, 256, 0, st>>>(reinterpret_cast<const bf16*>(g), db, vtot, Co);
+  }
+  return launched("conv3d_wgrad");
+}
+
+extern "C" lt_status lt_nn_conv3d_flip(const uint16_t* w, uint16_t* wt, int32_t Ci, int32_t Co, void* stream) {
+  clear_error();
+  if (!w || !wt || Ci <= 0 || Co <= 0) return set_error(LT_EINVAL, "conv3d_flip: bad arguments");
+  flip_kernel<<<grid1d(27LL * Ci * Co), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(w),
+                                                                          reinterpret_cast<bf16*>(wt), Ci, Co);
+  return launched("conv3d_flip");
+}
+
+extern "C" lt_status lt_nn_f32_to_bf16(const float* x, uint16_t* y, int64_t n, void* stream) {
+  clear_error();
+  if (!x || !y || n < 0) return set_error(LT_EINVAL, "f32_to_bf16: bad arguments");
+  if (n) f2b_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(x, reinterpret_cast<bf16*>(y), n);
+  return launched("f32_to_bf16");
+}
+
+extern "C" lt_status lt_nn_bf16_to_f32(const uint16_t* x, float* y, int64_t n, void* stream) {
+  clear_error();
+  if (!x || !y || n < 0) return set_error(LT_EINVAL, "bf16_to_f32: bad arguments");
+  if (n) b2f_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(x), y, n);
+  return launched("bf16_to_f32");
+}
+
+extern "C" lt_status lt_nn_relu_backward(const uint16_t* y, uint16_t* g, int64_t n, void* stream) {
+  clear_error();
+  if (!y || !g || n < 0) return set_error(LT_EINVAL, "relu_backward: bad arguments");
+  if (n) relu_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(y), reinterpret_cast<bf16*>(g), n);
+  return launched("relu_backward");
+}
+
+extern "C" lt_status lt_nn_avgpool2(const uint16_t* in, uint16_t* out, int32_t batch, int32_t D, int32_t H, int32_t W,
+                                    int32_t C, int32_t i_stride, int32_t i_off, void* stream) {
+  clear_error();
+  if (!in || !out || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || D % 2 || H % 2 || W % 2 || C <= 0 ||
+      i_stride < i_off + C || i_off < 0)
+    return set_error(LT_EINVAL, "avgpool2: bad arguments");
+  const long long n = (long long)batch * (D / 2) * (H / 2) * (W / 2) * C;
+  avgpool_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(in), reinterpret_cast<bf16*>(out),
+                                                               batch, D, H, W, C, i_stride, i_off);
+  return launched("avgpool2");
+}
+
+extern "C" lt_status lt_nn_avgpool2_backward(const uint16_t* gout, uint16_t* gin, int32_t batch, int32_t D, int32_t H,
+                                             int32_t W, int32_t C, int32_t i_stride, int32_t i_off, void* stream) {
+  clear_error();
+  if (!gout || !gin || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || D % 2 || H % 2 || W % 2 || C <= 0 ||
+      i_stride < i_off + C || i_off < 0)
+    return set_error(LT_EINVAL, "avgpool2_backward: bad arguments");
+  const long long n = (long long)batch * D * H * W * C;
+  avgpool_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(gout),
+                                                                   reinterpret_cast<bf16*>(gin), batch, D, H, W, C,
+                                                                   i_stride, i_off);
+  return launched("avgpool2_backward");
+}
+
+extern "C" lt_status lt_nn_upsample2(const uint16_t* in, uint16_t* out, int32_t batch, int32_t d, int32_t h, int32_t w,
+                                     int32_t C, int32_t o_stride, int32_t o_off, void* stream) {
+  clear_error();
+  if (!in || !out || batch <= 0 || d <= 0 || h <= 0 || w <= 0 || C <= 0 || o_stride < o_off + C || o_off < 0)
+    return set_error(LT_EINVAL, "upsample2: bad arguments");
+  const long long n = (long long)batch * 8 * d * h * w * C;
+  upsample_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(in), reinterpret_cast<bf16*>(out),
+                                                                batch, d, h, w, C, o_stride, o_off);
+  return launched("upsample2");
+}
+
+extern "C" lt_status lt_nn_upsample2_backward(const uint16_t* gout, uint16_t* gin, int32_t batch, int32_t d, int32_t h,
+                                              int32_t w, int32_t C, int32_t o_stride, int32_t o_off, void* stream) {
+  clear_error();
+  if (!gout || !gin || batch <= 0 || d <= 0 || h <= 0 || w <= 0 || C <= 0 || o_stride < o_off + C || o_off < 0)
+    return set_error(LT_EINVAL, "upsample2_backward: bad arguments");
+  const long long n = (long long)batch * d * h * w * C;
+  upsample_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(gout),
+                                                                    reinterpret_cast<bf16*>(gin), batch, d, h, w, C,
+                                                                    o_stride, o_off);
+  return launched("upsample2_backward");
+}
+
+extern "C" lt_status lt_nn_copy_channels(const uint16_t* src, uint16_t* dst, int64_t voxels, int32_t C, int32_t s_stride,
+                                         int32_t s_off, int32_t d_stride, int32_t d_off, void* stream) {
+  clear_error();
+  if (!src || !dst || voxels < 0 || C <= 0 || s_stride < s_off + C || d_stride < d_off + C || s_off < 0 || d_off < 0)
+    return set_error(LT_EINVAL, "copy_channels: bad arguments");
+  if (voxels)
+    copy_channels_kernel<<<grid1d(voxels * C), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(src), reinterpret_cast<bf16*>(dst), voxels, C, s_stride, s_off, d_stride, d_off);
+  return launched("copy_channels");
+}
+
+extern "C" lt_status lt_nn_adam(float* p, uint16_t* pb, const float* g, float* m, float* v, int64_t n, float lr,
+                                float b1, float b2, float eps, int32_t step, void* stream) {
+  clear_error();
+  if (!p || !g || !m || !v || n < 0 || step < 1) return set_error(LT_EINVAL, "adam: bad arguments");
+  const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+  if (n)
+    adam_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(p, reinterpret_cast<bf16*>(pb), g, m, v, n, lr, b1, b2,
+                                                              eps, c1, c2);
+  return launched("adam");
+}
+
+extern "C" lt_status lt_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, int64_t n, void* stream) {
+  clear_error();
+  if (!a || !b || !out || n < 0) return set_error(LT_EINVAL, "add: bad arguments");
+  if (n)
+    add_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(a), reinterpret_cast<const bf16*>(b),
+                                                             reinterpret_cast<bf16*>(out), n);
+  return launched("add");
+}
+
+extern "C" lt_status lt_nn_prepare_input(const float* bp, const float* d, float* r, float* m, uint16_t* u, int64_t voxels,
+                                         void* stream) {
+  clear_error();
+  if (!bp || !d || !r || !m || !u || voxels <= 0) return set_error(LT_EINVAL, "prepare_input: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemsetAsync(m, 0, sizeof(float), st);
+  ratio_max_kernel<<<grid1d(voxels), 256, 0, st>>>(bp, d, r, m, voxels);
+  pack_input_kernel<<<grid1d(voxels * 16), 256, 0, st>>>(r, m, reinterpret_cast<bf16*>(u), voxels);
+  return launched("prepare_input");
+}
+
+extern "C" lt_status lt_nn_unpack_output(const float* out, const float* m, float* x0, int64_t voxels, void* stream) {
+  clear_error();
+  if (!out || !m || !x0 || voxels <= 0) return set_error(LT_EINVAL, "unpack_output: bad arguments");
+  unpack_output_kernel<<<grid1d(voxels), 256, 0, (cudaStream_t)stream>>>(out, m, x0, voxels);
+  return launched("unpack_output");
+}
+
+extern "C" lt_status lt_nn_mse(const float* out, const float* target, const float* m, float* g, float* loss,
+                               int64_t voxels, void* stream) {
+  clear_error();
+  if (!out || !target || !m || !g || !loss || voxels <= 0) return set_error(LT_EINVAL, "mse: bad arguments");
+  mse_kernel<<<grid1d(voxels * 16), 256, 0, (cudaStream_t)stream>>>(out, target, m, g, loss, voxels);
+  return launched("mse");
+}

@@ -222,3 +222,40 @@ def poisson_images(y: np.ndarray, peak_photons: float = 1e4, seed: int = 7) -> n
 def uniform_random(shape, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(lo, hi, size=shape).astype(np.float32)
+
+
+def plume_field_torch(vol: Volume, seed: int, n_plumes: int = 20, turbulence: float = 0.3, device="cuda"):
+    """The plume distribution of ``plume_field`` evaluated on the GPU with
+    torch (for generating many training volumes); parameters drawn from the
+    same PCG64 recipe, turbulence from a seeded torch generator."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = (torch.arange(vol.nz, device=device, dtype=torch.float32) + 0.5) / vol.nz
+    y = (torch.arange(vol.ny, device=device, dtype=torch.float32) + 0.5) / vol.ny
+    x = (torch.arange(vol.nx, device=device, dtype=torch.float32) + 0.5) / vol.nx
+    Z, Y, X = torch.meshgrid(z, y, x, indexing="ij")
+    out = torch.zeros(vol.shape, device=device, dtype=torch.float32)
+    for _ in range(n_plumes):
+        c = rng.uniform(0.2, 0.8, size=3)
+        tilt = np.deg2rad(rng.uniform(0.0, 20.0))
+        az = rng.uniform(0.0, 2 * np.pi)
+        axis = (float(np.sin(tilt) * np.cos(az)), float(np.cos(tilt)), float(np.sin(tilt) * np.sin(az)))
+        sp = float(rng.uniform(0.02, 0.06))
+        sl = float(rng.uniform(0.1, 0.3))
+        a = float(rng.uniform(0.5, 1.0))
+        dx, dy, dz = X - float(c[0]), Y - float(c[1]), Z - float(c[2])
+        along = dx * axis[0] + dy * axis[1] + dz * axis[2]
+        perp2 = dx * dx + dy * dy + dz * dz - along * along
+        out += a * torch.exp(-0.5 * (along * along / (sl * sl) + perp2 / (sp * sp)))
+    if turbulence > 0:
+        g = torch.Generator(device=device).manual_seed(seed + 1)
+        out *= torch.exp(turbulence * torch.randn(vol.shape, device=device, generator=g))
+    return out.reshape(-1)
+
+
+def poisson_images_torch(y, peak_photons: float = 1e4, seed: int = 7):
+    """Poisson(s y)/s with s = peak_photons / max(y), on the GPU."""
+    import torch
+    g = torch.Generator(device=y.device).manual_seed(seed)
+    s = peak_photons / max(float(y.max()), 1e-30)
+    return torch.poisson(torch.clamp(y, min=0) * s, generator=g) / s

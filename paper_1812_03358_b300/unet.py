@@ -1,0 +1,349 @@
+"""Learned warm start: a 3D U-Net over the lt_nn_* kernels (marshalling only).
+
+The network maps a normalised back-projection to an initial volume for the
+Table V reconstruction (which then refines it; the plain solver stays the
+fallback and the judge of the result).  Four levels, 16-128 channels, 3x3x3
+convolutions with ReLU, 2x2x2 average pooling, nearest upsampling and
+channel-concatenated skips; bfloat16 activations and weights, float32
+accumulation, float32 master weights updated by Adam.  Every layer runs in the
+library's CUDA kernels; torch only allocates memory.
+
+Input/output convention (scale-equivariant): with D = A^T A 1 the diagonal of
+the majoriser, u = (A^T y / D) / m where m = max(A^T y / D); the network
+predicts x / m, so x0 = m * net(u).
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import c_float, c_int32, c_int64, c_void_p
+
+import numpy as np
+import torch
+
+from . import lt
+
+_SIGS = {
+    "lt_nn_conv3d": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                     c_int32, c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_conv3d_wgrad": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                           c_void_p],
+    "lt_nn_conv3d_flip": [c_void_p, c_void_p, c_int32, c_int32, c_void_p],
+    "lt_nn_f32_to_bf16": [c_void_p, c_void_p, c_int64, c_void_p],
+    "lt_nn_bf16_to_f32": [c_void_p, c_void_p, c_int64, c_void_p],
+    "lt_nn_relu_backward": [c_void_p, c_void_p, c_int64, c_void_p],
+    "lt_nn_avgpool2": [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_avgpool2_backward": [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                c_void_p],
+    "lt_nn_upsample2": [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_upsample2_backward": [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                 c_void_p],
+    "lt_nn_copy_channels": [c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_add": [c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
+    "lt_nn_prepare_input": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
+    "lt_nn_unpack_output": [c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
+    "lt_nn_mse": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
+    "lt_nn_adam": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float, c_float,
+                   c_int32, c_void_p],
+}
+_bound = False
+
+
+def nn():
+    global _bound
+    L = lt.lib()
+    if not _bound:
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = c_int32
+            fn.argtypes = args
+        _bound = True
+    return L
+
+
+def _call(name, *args):
+    lt._check(getattr(nn(), name)(*args))
+
+
+def pool(s, p, d, C):
+    _need(s, int(np.prod(d)) * C, "avgpool input")
+    if p.numel() != int(np.prod(d)) * C // 8:
+        raise ValueError("avgpool output shape")
+    _call("lt_nn_avgpool2", _p(s), _p(p), 1, *d, C, C, 0, _s())
+
+
+def pool_back(g, gs, d, C):
+    if g.numel() != int(np.prod(d)) * C // 8 or gs.numel() != int(np.prod(d)) * C:
+        raise ValueError("avgpool backward shapes")
+    _call("lt_nn_avgpool2_backward", _p(g), _p(gs), 1, *d, C, C, 0, _s())
+
+
+def upsample(x, cat, dsmall, cx, ctot):
+    if x.numel() != int(np.prod(dsmall)) * cx or cat.numel() != 8 * int(np.prod(dsmall)) * ctot:
+        raise ValueError("upsample shapes")
+    _call("lt_nn_upsample2", _p(x), _p(cat), 1, *dsmall, cx, ctot, 0, _s())
+
+
+def upsample_back(g, gx, dsmall, cx, ctot):
+    if gx.numel() != int(np.prod(dsmall)) * cx or g.numel() != 8 * int(np.prod(dsmall)) * ctot:
+        raise ValueError("upsample backward shapes")
+    _call("lt_nn_upsample2_backward", _p(g), _p(gx), 1, *dsmall, cx, ctot, 0, _s())
+
+
+def copy_channels(src, dst, voxels, C, s_stride, s_off, d_stride, d_off):
+    if src.numel() != voxels * s_stride or dst.numel() != voxels * d_stride:
+        raise ValueError("copy_channels shapes")
+    _call("lt_nn_copy_channels", _p(src), _p(dst), voxels, C, s_stride, s_off, d_stride, d_off, _s())
+
+
+def _p(t):
+    return t.data_ptr() if t is not None else None
+
+
+def _s():
+    return lt._stream()
+
+
+DEVICE = "cuda"
+
+
+def bf16(*shape):
+    return torch.empty(*shape, dtype=torch.bfloat16, device=DEVICE)
+
+
+# ---- layer calls (names follow the C ABI) ---------------------------------
+
+def _need(t, n, what):
+    if t is not None and t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the layer needs {n}")
+
+
+def conv3d(inp, w, b, out_bf=None, out_f=None, *, Ci, Co, dims, o_stride=None, o_off=0, relu=True):
+    D, H, W = dims
+    V = D * H * W
+    _need(inp, V * Ci, "conv3d input")
+    _need(w, 27 * Ci * Co, "conv3d weights")
+    _need(b, Co, "conv3d bias")
+    _need(out_bf, V * (o_stride or Co), "conv3d output")
+    _need(out_f, V * (o_stride or Co), "conv3d output")
+    if inp.numel() != V * Ci:
+        raise ValueError("conv3d input shape does not match dims x Ci")
+    _call("lt_nn_conv3d", _p(inp), _p(w), _p(b), _p(out_bf), _p(out_f), 1, D, H, W, Ci, Co,
+          o_stride or Co, o_off, int(relu), _s())
+
+
+def conv3d_wgrad(inp, g, dw, db, *, Ci, Co, dims):
+    D, H, W = dims
+    V = D * H * W
+    if inp.numel() != V * Ci or g.numel() != V * Co:
+        raise ValueError("conv3d_wgrad: input / gradient shapes do not match dims")
+    _need(dw, 27 * Ci * Co, "conv3d_wgrad dw")
+    _need(db, Co, "conv3d_wgrad db")
+    _call("lt_nn_conv3d_wgrad", _p(inp), _p(g), _p(dw), _p(db), 1, D, H, W, Ci, Co, _s())
+
+
+class Conv:
+    """One 3x3x3 convolution's parameters: float32 master weights [Co][27][Ci],
+    their bfloat16 copy, bias, Adam moments and gradients."""
+
+    def __init__(self, ci, co, gen):
+        self.ci, self.co = ci, co
+        std = (2.0 / (27 * ci)) ** 0.5
+        self.w = (torch.randn(co, 27, ci, generator=gen, dtype=torch.float32) * std).to(DEVICE)
+        self.b = torch.zeros(co, device=DEVICE)
+        self.wb = bf16(co, 27, ci)
+        self.wt = bf16(ci, 27, co)
+        self.gw = torch.zeros_like(self.w)
+        self.gb = torch.zeros_like(self.b)
+        self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
+        self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
+        self.sync_bf16()
+
+    def sync_bf16(self):
+        _call("lt_nn_f32_to_bf16", _p(self.w), _p(self.wb), self.w.numel(), _s())
+
+    def flip(self):
+        _call("lt_nn_conv3d_flip", _p(self.wb), _p(self.wt), self.ci, self.co, _s())
+
+    def zero_grad(self):
+        self.gw.zero_()
+        self.gb.zero_()
+
+    def adam(self, lr, step):
+        _call("lt_nn_adam", _p(self.w), _p(self.wb), _p(self.gw), _p(self.mw), _p(self.vw), self.w.numel(),
+              lr, 0.9, 0.999, 1e-8, step, _s())
+        _call("lt_nn_adam", _p(self.b), None, _p(self.gb), _p(self.mb), _p(self.vb), self.b.numel(),
+              lr, 0.9, 0.999, 1e-8, step, _s())
+
+
+class UNet:
+    """4-level 3D U-Net, channels (16, 32, 64, 128); spatial size divisible by 8."""
+
+    CH = (16, 32, 64, 128)
+
+    def __init__(self, seed=0):
+        gen = torch.Generator().manual_seed(seed)
+        c1, c2, c3, c4 = self.CH
+        self.enc = [(Conv(16, c1, gen), Conv(c1, c1, gen)), (Conv(c1, c2, gen), Conv(c2, c2, gen)),
+                    (Conv(c2, c3, gen), Conv(c3, c3, gen))]
+        self.bott = (Conv(c3, c4, gen), Conv(c4, c4, gen))
+        self.dec = [(Conv(c4 + c3, c3, gen), Conv(c3, c3, gen)), (Conv(c3 + c2, c2, gen), Conv(c2, c2, gen)),
+                    (Conv(c2 + c1, c1, gen), Conv(c1, c1, gen))]
+        self.head = Conv(c1, 16, gen)
+        self.step = 0
+
+    def convs(self):
+        out = []
+        for a, b in self.enc:
+            out += [a, b]
+        out += list(self.bott)
+        for a, b in self.dec:
+            out += [a, b]
+        return out + [self.head]
+
+    # -- forward -------------------------------------------------------------
+    def forward(self, u, keep=False):
+        """u: bfloat16 [D][H][W][16] (channel 0 = input).  Returns the float32
+        output [D][H][W][16] (channel 0 = prediction)."""
+        D, H, W, _ = u.shape
+        c1, c2, c3, c4 = self.CH
+        dims = [(D >> l, H >> l, W >> l) for l in range(4)]
+        acts = {}
+        x = u
+        skips = []
+        for l, (ca, cb) in enumerate(self.enc):
+            d = dims[l]
+            a = bf16(*d, ca.co)
+            conv3d(x, ca.wb, ca.b, a, Ci=ca.ci, Co=ca.co, dims=d)
+            s = bf16(*d, cb.co)
+            conv3d(a, cb.wb, cb.b, s, Ci=cb.ci, Co=cb.co, dims=d)
+            acts[("enc", l)] = (x, a, s)
+            skips.append(s)
+            p = bf16(*dims[l + 1], cb.co)
+            pool(s, p, d, cb.co)
+            x = p
+        d = dims[3]
+        ca, cb = self.bott
+        a = bf16(*d, ca.co)
+        conv3d(x, ca.wb, ca.b, a, Ci=ca.ci, Co=ca.co, dims=d)
+        bo = bf16(*d, cb.co)
+        conv3d(a, cb.wb, cb.b, bo, Ci=cb.ci, Co=cb.co, dims=d)
+        acts["bott"] = (x, a, bo)
+        x, cx = bo, c4
+        for i, (ca, cb) in enumerate(self.dec):
+            l = 2 - i
+            d = dims[l]
+            skip = skips[l]
+            cs = skip.shape[-1]
+            cat = bf16(*d, cx + cs)
+            upsample(x, cat, dims[l + 1], cx, cx + cs)
+            copy_channels(skip, cat, int(np.prod(d)), cs, cs, 0, cx + cs, cx)
+            a = bf16(*d, ca.co)
+            conv3d(cat, ca.wb, ca.b, a, Ci=ca.ci, Co=ca.co, dims=d)
+            o = bf16(*d, cb.co)
+            conv3d(a, cb.wb, cb.b, o, Ci=cb.ci, Co=cb.co, dims=d)
+            acts[("dec", i)] = (cat, a, o, cx)
+            x, cx = o, cb.co
+        out = torch.empty(*dims[0], 16, device=DEVICE, dtype=torch.float32)
+        hb = bf16(*dims[0], 16)
+        conv3d(x, self.head.wb, self.head.b, hb, out, Ci=self.head.ci, Co=16, dims=dims[0], relu=False)
+        acts["head"] = (x,)
+        if keep:
+            self._acts, self._dims = acts, dims
+        return out
+
+    # -- backward ------------------------------------------------------------
+    def _conv_back(self, conv, inp, out_act, g, dims, relu=True):
+        """g: bfloat16 gradient w.r.t. conv output (Co channels).  Returns the
+        gradient w.r.t. its input (Ci channels)."""
+        if relu:
+            if out_act.numel() != g.numel():
+                raise ValueError("relu backward shapes")
+            _call("lt_nn_relu_backward", _p(out_act), _p(g), g.numel(), _s())
+        conv3d_wgrad(inp, g, conv.gw, conv.gb, Ci=conv.ci, Co=conv.co, dims=dims)
+        conv.flip()
+        gi = bf16(*dims, conv.ci)
+        conv3d(g, conv.wt, None, gi, Ci=conv.co, Co=conv.ci, dims=dims, relu=False)
+        return gi
+
+    def backward(self, g_out):
+        """g_out: float32 gradient w.r.t. the output [D][H][W][16]."""
+        acts, dims = self._acts, self._dims
+        for c in self.convs():
+            c.zero_grad()
+        g = bf16(*g_out.shape)
+        _call("lt_nn_f32_to_bf16", _p(g_out), _p(g), g_out.numel(), _s())
+        (x,) = acts["head"]
+        g = self._conv_back(self.head, x, None, g, dims[0], relu=False)
+        skip_grads = [None, None, None]
+        for i in reversed(range(3)):          # finest decoder level first
+            ca, cb = self.dec[i]
+            l = 2 - i
+            cat, a, o, cx = acts[("dec", i)]
+            d = dims[l]
+            g = self._conv_back(cb, a, o, g, d)
+            g = self._conv_back(ca, cat, a, g, d)           # gradient w.r.t. the concatenation
+            cs = cat.shape[-1] - cx
+            gs = bf16(*d, cs)
+            copy_channels(g, gs, int(np.prod(d)), cs, cx + cs, cx, cs, 0)
+            skip_grads[l] = gs
+            gx = bf16(*dims[l + 1], cx)
+            upsample_back(g, gx, dims[l + 1], cx, cx + cs)
+            g = gx
+        x, a, bo = acts["bott"]
+        g = self._conv_back(self.bott[1], a, bo, g, dims[3])
+        g = self._conv_back(self.bott[0], x, a, g, dims[3])
+        for l in reversed(range(3)):
+            ca, cb = self.enc[l]
+            x, a, s = acts[("enc", l)]
+            d = dims[l]
+            gs = bf16(*d, cb.co)
+            pool_back(g, gs, d, cb.co)
+            if skip_grads[l].numel() != gs.numel():
+                raise ValueError("skip gradient shape")
+            _call("lt_nn_add", _p(gs), _p(skip_grads[l]), _p(gs), gs.numel(), _s())
+            g = self._conv_back(cb, a, s, gs, d)
+            g = self._conv_back(ca, x, a, g, d)
+        return g
+
+    def adam_step(self, lr):
+        self.step += 1
+        for c in self.convs():
+            c.adam(lr, self.step)
+
+
+class WarmStart:
+    """Network input preparation, inference and training on (x_true, A^T y)
+    pairs, all in the library's kernels."""
+
+    def __init__(self, plan, net: UNet):
+        self.plan = plan
+        self.net = net
+        n = plan.nvox
+        ones = torch.ones(1, n, device="cuda")
+        self.D = plan.adjoint(plan.forward(ones)).reshape(-1).contiguous()
+        self.r = torch.empty(n, device="cuda")
+        self.m = torch.zeros(1, device="cuda")
+        self.loss = torch.zeros(1, device="cuda")
+        v = plan.vol
+        self.dims = (v.nz, v.ny, v.nx)
+        self.u = bf16(*self.dims, 16)
+
+    def prepare(self, bp):
+        _call("lt_nn_prepare_input", _p(bp), _p(self.D), _p(self.r), _p(self.m), _p(self.u), self.r.numel(), _s())
+        return self.u
+
+    def infer(self, bp):
+        """x0 (float32 [n_vox]) from a back-projection A^T y."""
+        out = self.net.forward(self.prepare(bp))
+        x0 = torch.empty(self.r.numel(), device="cuda")
+        _call("lt_nn_unpack_output", _p(out), _p(self.m), _p(x0), x0.numel(), _s())
+        return x0
+
+    def train_step(self, bp, x_true, lr):
+        out = self.net.forward(self.prepare(bp), keep=True)
+        g = torch.empty_like(out)
+        self.loss.zero_()
+        _call("lt_nn_mse", _p(out), _p(x_true), _p(self.m), _p(g), _p(self.loss), x_true.numel(), _s())
+        self.net.backward(g)
+        self.net.adam_step(lr)
+        return self.loss
