@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default forward variant (fixed launch sequence, e.g. for profiling)")
     return ap.parse_args()
 
 
@@ -197,7 +199,10 @@ def run_ours(args):
     vol, cam = I.config_plenoptic()
     x_true = I.plume_field(vol, seed=2000 + rank)
     plan = lt.Plan(vol, [cam])
-    tuned, tune_ms = plan.autotune()
+    if args.no_autotune:
+        tuned, tune_ms = 0, None
+    else:
+        tuned, tune_ms = plan.autotune()
     stats = plan.stats(0)
     xt = torch.from_numpy(x_true.reshape(1, -1)).cuda()
     y_clean = plan.forward(xt)
