@@ -168,6 +168,55 @@ def traffic_for(kernel):
     return None
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) of the B300s, else the
+    fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def shear_passes(flush, stream, reps=20):
+    """The rotation passes of a yawed camera (quarter turn + z shear + x shear,
+    and the transposed passes) on a 128^3 volume: CUDA-event time per call, L2
+    flushed before each, against the HBM roofline.  Algorithmic bytes per
+    pass = 4 (N_in + N_out)."""
+    import math
+    import torch
+    from paper_1812_03358_b300 import inputs as I
+    from paper_1812_03358_b300 import lt
+    yaw = math.radians(30.0)
+    vol = I.Volume(128, 128, 128, 1.0, 1.0, 1.0)
+    plan = lt.Plan(vol, [I.table_single_lens(64, 0.08, yaw=yaw)])
+    (nzr, ny, nxr), _ = plan.camera_grid(0)
+    q = math.floor(yaw / (math.pi / 2) + 0.5)
+    nxp = vol.nz if q % 2 else vol.nx
+    n_in, n_mid, n_out = vol.n, nzr * ny * nxp, nzr * ny * nxr
+    nbytes = 4 * (n_in + n_mid) + 4 * (n_mid + n_out)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.rand(1, vol.n, device="cuda", generator=g)
+    xc = plan.rotate(0, x)
+    xa = plan.rotate_adjoint(0, xc)
+    peak, src = hbm_peak()
+    out = {"workload": f"128^3 volume (1 mm), yaw 30 deg -> camera grid {nzr}x{ny}x{nxr}",
+           "bytes_per_call": nbytes, "peak_GBps": peak, "peak_source": src}
+    for name, fn in (("forward", lambda: plan.rotate(0, x, xc)), ("adjoint", lambda: plan.rotate_adjoint(0, xc, xa))):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+        out[name + "_ms"] = ms
+        out[name + "_GBps"] = nbytes / (ms * 1e-3) / 1e9
+        out[name + "_frac"] = out[name + "_GBps"] / peak
+    plan.close()
+    return out
+
+
 def cpu_baseline_sample(vol, cam, x):
     """The FP64 oracle, as it stands, on one projector + adjoint pass of the
     full workload (its BLAS threads on the host cores)."""
@@ -284,6 +333,9 @@ def run_ours(args):
                 "work": "2 flop (one FMA) per nonzero (pixel, cell, voxel) entry evaluated",
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts and max clock)"}
 
+    # --- a2: the rotation passes of a yawed camera (HBM-bound streams) ---
+    shear = shear_passes(flush, stream)
+
     # --- end to end through the public API: pinned host y in, data fit out ---
     y_pin = torch.from_numpy(y_host.reshape(1, -1)).pin_memory()
     y_stage = torch.empty_like(y_dev)
@@ -331,6 +383,7 @@ def run_ours(args):
                        "forward_variant": tuned, "autotune_ms": tune_ms},
             "stages_ms": stage_ms,
             "roofline": roofline,
+            "shear_passes": shear,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "e2e": e2e,

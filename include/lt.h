@@ -138,6 +138,24 @@ LT_API lt_status lt_adjoint_camera(lt_plan* plan, int32_t cam, const float* y_ca
 LT_API lt_status lt_forward_camera_noalloc(lt_plan* plan, int32_t cam, const float* x, float* y_cam,
                                            void* stream);
 
+/* Rotated perspectives (Sec. III-A, eq. rot): camera `cam`'s yaw is split
+ * into quarter turns P and a residual |theta_r| <= 45 deg applied as two 1-D
+ * least-squares shear re-projections, x_c = E^x E^z P x, onto the camera's
+ * own grid.
+ *   lt_camera_grid            the camera grid (sizes and spacings of x_c);
+ *                             equal to the plan's volume for yaw = 0.
+ *   lt_rotate_volume          x [F][nz][ny][nx] -> xc [F][grid], device
+ *                             pointers owned by the caller.
+ *   lt_rotate_volume_adjoint  xc -> x (= or += with accumulate), the exact
+ *                             transpose (same entries, same rounding).
+ * For an unrotated camera both are plain copies.  The passes use the
+ * camera's plan-owned scratch, so calls for the same camera must not overlap
+ * in time.  LT_EINVAL for a bad plan, camera or pointer. */
+LT_API lt_status lt_camera_grid(const lt_plan* plan, int32_t cam, lt_volume_desc* grid);
+LT_API lt_status lt_rotate_volume(lt_plan* plan, int32_t cam, const float* x, float* xc, void* stream);
+LT_API lt_status lt_rotate_volume_adjoint(lt_plan* plan, int32_t cam, const float* xc, float* x, int32_t accumulate,
+                                          void* stream);
+
 /* Plenoptic stages, exposed for testing and composition (eq. plenoptic,factor):
  *   stage 1:  fa[F][K][arr_nt][arr_ns] = M (1/V^a) sum_n B^{an}_k (dz x^n)
  *   stage 2:  y[F][M_c] = sum_k sum_mu B^{d mu}_k fa_k

@@ -84,6 +84,15 @@ struct RotParam {
   float bz, betaz;         // E^z slope (b dx'/dz') and |bz|
   float ax, betax;         // E^x slope (a dz'/dx') and |ax|
   int32_t wz, wx;          // source windows
+  // Per-column shear entries, filled once at plan time by launch_shear_tables:
+  // column c of E^z (c < nxp) has window offset jz[c] and entries
+  // tz[c * nwz + q] = E^z(i, i - pz + jz[c] + q) for every output i (zero for
+  // q >= wz); row r of E^x (r < nzr) likewise with jx[r], tx[r * wx + q].
+  int32_t nwz;             // 8 or 16, >= wz (register window of the z passes)
+  float* tz;
+  int32_t* jz;
+  float* tx;
+  int32_t* jx;
 };
 
 // Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.
@@ -153,5 +162,11 @@ cudaError_t launch_rotate_forward(const float* x, float* rz, float* xr, const Ro
 // g_xr (rotated grid) -> x (= or +=), using rz as scratch.
 cudaError_t launch_rotate_adjoint(const float* g_xr, float* rz, float* x, const RotParam& r, int frames,
                                   int accumulate, cudaStream_t st);
+
+// Fills r.tz/jz/tx/jx (device arrays of nxp*nwz, nxp, nzr*wx, nzr entries).
+cudaError_t launch_shear_tables(const RotParam& r, cudaStream_t st);
+
+// x[i] += y[i], i < n.
+cudaError_t launch_add_inplace(float* x, const float* y, long long n, cudaStream_t st);
 
 }  // namespace lt

@@ -216,6 +216,10 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.d_items);
   cudaFree(c.d_rz);
   cudaFree(c.d_xr);
+  cudaFree(c.rot.tz);
+  cudaFree(c.rot.jz);
+  cudaFree(c.rot.tx);
+  cudaFree(c.rot.jx);
   cudaFree(c.d_srange);
   cudaFree(c.d_trange);
   cudaFree(c.d_lens);
@@ -584,6 +588,18 @@ static lt_status plan_rotation(const lt_volume_desc& v, CameraPlan& c, int frame
   const size_t bxr = (size_t)frames * c.nvox_c * sizeof(float);
   if (cudaMalloc((void**)&c.d_rz, brz) != cudaSuccess || cudaMalloc((void**)&c.d_xr, bxr) != cudaSuccess)
     return set_error(LT_ENOMEM, "camera %d: rotated-view scratch (%zu + %zu bytes)", idx, brz, bxr);
+  if (r.wz > 16 || r.wx > 64)
+    return set_error(LT_EUNSUPPORTED, "camera %d: voxel aspect ratio too large for the shear passes "
+                     "(windows %d, %d)", idx, r.wz, r.wx);
+  r.nwz = r.wz <= 8 ? 8 : 16;
+  if (cudaMalloc((void**)&r.tz, (size_t)r.nxp * r.nwz * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&r.jz, (size_t)r.nxp * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc((void**)&r.tx, (size_t)r.nzr * r.wx * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&r.jx, (size_t)r.nzr * sizeof(int32_t)) != cudaSuccess)
+    return set_error(LT_ENOMEM, "camera %d: shear tables", idx);
+  cudaError_t e = launch_shear_tables(r, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) return cuda_error(e, "shear tables");
   return LT_OK;
 }
 
@@ -700,6 +716,46 @@ extern "C" lt_status lt_camera_cells(const lt_plan* plan, int32_t cam, int32_t* 
     return set_error(LT_EINVAL, "bad plan/camera/out argument");
   *n_cells = plan->cams[cam].K;
   return LT_OK;
+}
+
+extern "C" lt_status lt_camera_grid(const lt_plan* plan, int32_t cam, lt_volume_desc* grid) {
+  clear_error();
+  if (!plan || cam < 0 || cam >= (int)plan->cams.size() || !grid)
+    return set_error(LT_EINVAL, "bad plan/camera/out argument");
+  *grid = plan->cams[cam].vol_c;
+  return LT_OK;
+}
+
+extern "C" lt_status lt_rotate_volume(lt_plan* plan, int32_t cam, const float* x, float* xc, void* stream) {
+  clear_error();
+  if (!plan || cam < 0 || cam >= (int)plan->cams.size() || !x || !xc)
+    return set_error(LT_EINVAL, "bad plan/camera/pointer argument");
+  CameraPlan& c = plan->cams[cam];
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = c.rotated ? launch_rotate_forward(x, c.d_rz, xc, c.rot, plan->frames, st)
+                            : cudaMemcpyAsync(xc, x, (size_t)plan->frames * plan->nvox * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "rotate volume");
+}
+
+extern "C" lt_status lt_rotate_volume_adjoint(lt_plan* plan, int32_t cam, const float* xc, float* x,
+                                              int32_t accumulate, void* stream) {
+  clear_error();
+  if (!plan || cam < 0 || cam >= (int)plan->cams.size() || !x || !xc)
+    return set_error(LT_EINVAL, "bad plan/camera/pointer argument");
+  CameraPlan& c = plan->cams[cam];
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c.rotated) {
+    cudaError_t e = launch_rotate_adjoint(xc, c.d_rz, x, c.rot, plan->frames, accumulate, st);
+    return e == cudaSuccess ? LT_OK : cuda_error(e, "rotate volume adjoint");
+  }
+  const long long n = (long long)plan->frames * plan->nvox;
+  if (!accumulate) {
+    cudaError_t e = cudaMemcpyAsync(x, xc, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? LT_OK : cuda_error(e, "rotate volume adjoint");
+  }
+  cudaError_t e = launch_add_inplace(x, xc, n, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "rotate volume adjoint");
 }
 
 // ---------------------------------------------------------------------------

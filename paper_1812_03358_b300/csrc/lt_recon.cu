@@ -101,44 +101,85 @@ residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const 
 
 // Table V step 3: w = [z - (D + s beta)^-1 (g + grad R(z))]_+, x' = [w - nu]_+,
 // z' = x' + mom (x' - x).  grad R(z)_j = beta sum_{l in N26(j)} psi'(z_j - z_l).
-__global__ void __launch_bounds__(256)
+//
+// A CTA owns a 32 x 8 (x, y) column of UPD_ZB slices.  With beta != 0 the z
+// values slide through three shared-memory planes of (8 + 2) x (32 + 2)
+// (one-voxel halo, zero outside the volume), so each z value is read from
+// memory about 1.7 times instead of 27; neighbours outside the volume drop
+// out of the sum through per-axis validity masks (no branches).
+constexpr int UPD_TX = 32, UPD_TY = 8, UPD_ZB = 8;
+constexpr int UPD_PX = UPD_TX + 2, UPD_PY = UPD_TY + 2;
+
+__device__ __forceinline__ void load_plane(float* __restrict__ dst, const float* __restrict__ zf, int kz, int x0,
+                                           int y0, int nx, int ny, int nz, int tid) {
+  for (int i = tid; i < UPD_PX * UPD_PY; i += UPD_TX * UPD_TY) {
+    const int ly = i / UPD_PX, lx = i - ly * UPD_PX;
+    const int gy = y0 + ly - 1, gx = x0 + lx - 1;
+    float v = 0.0f;
+    if (kz >= 0 && kz < nz && gy >= 0 && gy < ny && gx >= 0 && gx < nx)
+      v = zf[((long long)kz * ny + gy) * nx + gx];
+    dst[i] = v;
+  }
+}
+
+__global__ void __launch_bounds__(UPD_TX * UPD_TY)
 update_kernel(float* __restrict__ x, const float* __restrict__ z, float* __restrict__ zn,
               const float* __restrict__ g, const float* __restrict__ D, int nx, int ny, int nz,
               long long nvox, float beta, float nu, int psi, float inv_delta, float sbeta,
               const Scalars* __restrict__ sc) {
-  const int ix = blockIdx.x * 32 + threadIdx.x;
-  const int iy = blockIdx.y * 8 + threadIdx.y;
-  const int iz = blockIdx.z % nz;
-  const int f = blockIdx.z / nz;
-  if (ix >= nx || iy >= ny) return;
+  __shared__ float pl[3][UPD_PY * UPD_PX];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * UPD_TX + tx;
+  const int nzb = (nz + UPD_ZB - 1) / UPD_ZB;
+  const int f = blockIdx.z / nzb;
+  const int z0 = (blockIdx.z - f * nzb) * UPD_ZB;
+  const int x0 = blockIdx.x * UPD_TX, y0 = blockIdx.y * UPD_TY;
+  const int ix = x0 + tx, iy = y0 + ty;
+  const bool inside = ix < nx && iy < ny;
   const float* zf = z + (long long)f * nvox;
-  const long long j = ((long long)iz * ny + iy) * nx + ix;
-  const float zc = zf[j];
-  float reg = 0.0f;
-  if (beta != 0.0f) {
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int kz = iz + dz;
-      if (kz < 0 || kz >= nz) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int ky = iy + dy;
-        if (ky < 0 || ky >= ny) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int kx = ix + dx;
-          if (kx < 0 || kx >= nx || (dx == 0 && dy == 0 && dz == 0)) continue;
-          const float d = zc - __ldg(zf + ((long long)kz * ny + ky) * nx + kx);
-          reg += psi ? d * rsqrtf(1.0f + (d * inv_delta) * (d * inv_delta)) : d;
-        }
-      }
-    }
-    reg *= beta;
-  }
-  const long long jf = (long long)f * nvox + j;
-  const float den = D[jf] + sbeta;
-  const float wv = den > 0.0f ? fmaxf(zc - (g[jf] + reg) / den, 0.0f) : 0.0f;
-  const float xn = fmaxf(wv - nu, 0.0f);
+  const bool reg_on = beta != 0.0f;   // uniform
+  const bool vy[3] = {iy > 0, true, iy + 1 < ny};
+  const bool vx[3] = {ix > 0, true, ix + 1 < nx};
   const float mom = (float)sc->mom;
-  zn[jf] = xn + mom * (xn - x[jf]);
-  x[jf] = xn;
+  if (reg_on) {
+    load_plane(pl[0], zf, z0 - 1, x0, y0, nx, ny, nz, tid);
+    load_plane(pl[1], zf, z0, x0, y0, nx, ny, nz, tid);
+  }
+  for (int k = 0; k < UPD_ZB; ++k) {
+    const int iz = z0 + k;
+    if (iz >= nz) break;   // uniform over the CTA
+    if (reg_on) {
+      load_plane(pl[(k + 2) % 3], zf, iz + 1, x0, y0, nx, ny, nz, tid);
+      __syncthreads();
+    }
+    if (inside) {
+      const long long j = ((long long)iz * ny + iy) * nx + ix;
+      const long long jf = (long long)f * nvox + j;
+      const float* p3[3] = {pl[k % 3], pl[(k + 1) % 3], pl[(k + 2) % 3]};
+      const float zc = reg_on ? p3[1][(ty + 1) * UPD_PX + tx + 1] : zf[j];
+      float reg = 0.0f;
+      if (reg_on) {
+        const bool vz[3] = {iz > 0, true, iz + 1 < nz};
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+              if (dz == 1 && dy == 1 && dx == 1) continue;
+              const float d = zc - p3[dz][(ty + dy) * UPD_PX + tx + dx];
+              const float c = psi ? d * rsqrtf(1.0f + (d * inv_delta) * (d * inv_delta)) : d;
+              reg += (vz[dz] && vy[dy] && vx[dx]) ? c : 0.0f;
+            }
+        reg *= beta;
+      }
+      const float den = D[jf] + sbeta;
+      const float wv = den > 0.0f ? fmaxf(zc - (g[jf] + reg) / den, 0.0f) : 0.0f;
+      const float xn = fmaxf(wv - nu, 0.0f);
+      zn[jf] = xn + mom * (xn - x[jf]);
+      x[jf] = xn;
+    }
+    if (reg_on) __syncthreads();   // plane k % 3 is overwritten next
+  }
 }
 
 __global__ void finalize_dots(const double* __restrict__ part, double* __restrict__ out, int n) {
@@ -222,9 +263,10 @@ static lt_status recon_step(lt_recon* R, int sel, cudaStream_t st) {
   s = plan_adjoint(P, R->r, R->g, st);  // step 1c + 2: g = sum_c A_c^T r_c
   if (s != LT_OK) return s;
   const lt_volume_desc& v = P->vol;
-  dim3 grid((v.nx + 31) / 32, (v.ny + 7) / 8, v.nz * R->F);
+  dim3 grid((v.nx + UPD_TX - 1) / UPD_TX, (v.ny + UPD_TY - 1) / UPD_TY,
+            ((v.nz + UPD_ZB - 1) / UPD_ZB) * R->F);
   const float beta = (float)R->prm.beta;
-  update_kernel<<<grid, dim3(32, 8), 0, st>>>(
+  update_kernel<<<grid, dim3(UPD_TX, UPD_TY), 0, st>>>(
       R->x, z, R->z[1 - sel], R->g, R->D, v.nx, v.ny, v.nz, R->N, beta, (float)R->prm.nu, R->prm.psi,
       R->prm.psi == 1 ? (float)(1.0 / R->prm.psi_delta) : 1.0f, (float)(R->prm.reg_scale * R->prm.beta), R->sc);
   cudaError_t e = cudaGetLastError();

@@ -40,150 +40,233 @@ __device__ __forceinline__ float column_shift(float slope, int c, int n_c) {
   return __fmul_rn(slope, __fsub_rn((float)c, 0.5f * (float)(n_c - 1)));
 }
 
-// Index in the original volume of permuted-grid voxel (jz, iy, jx).
+// Index in the original volume of permuted-grid voxel (jz, iy, jx) after NQ
+// quarter turns.
+template <int NQ>
 __device__ __forceinline__ long long perm_index(const RotParam& r, int jz, int iy, int jx) {
   int iz, ix;
-  switch (r.nq) {
-    case 1: iz = r.nz - 1 - jx; ix = jz; break;
-    case 2: iz = r.nz - 1 - jz; ix = r.nx - 1 - jx; break;
-    case 3: iz = jx; ix = r.nx - 1 - jz; break;
-    default: iz = jz; ix = jx; break;
-  }
+  if (NQ == 1) { iz = r.nz - 1 - jx; ix = jz; }
+  else if (NQ == 2) { iz = r.nz - 1 - jz; ix = r.nx - 1 - jx; }
+  else if (NQ == 3) { iz = jx; ix = r.nx - 1 - jz; }
+  else { iz = jz; ix = jx; }
   return ((long long)iz * r.ny + iy) * r.nx + ix;
 }
 
-// rz[f][izr][iy][ixp] = sum_j E^z(izr, j; ixp) xp[f][j][iy][ixp]
-__global__ void shear_z_forward(const float* __restrict__ x, float* __restrict__ rz, RotParam r, int frames) {
-  const long long per = (long long)r.nzr * r.ny * r.nxp;
-  const long long nvox = (long long)r.nx * r.ny * r.nz;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < per * frames;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)(idx / per);
-    long long rem = idx - (long long)f * per;
-    const int ixp = (int)(rem % r.nxp);
-    rem /= r.nxp;
-    const int iy = (int)(rem % r.ny);
-    const int izr = (int)(rem / r.ny);
-    const float sh = column_shift(r.bz, ixp, r.nxp);
-    const int j0 = (int)floorf((float)(izr - r.pz) + sh - 1.0f - 0.5f * r.betaz) - 1;
-    const float* xf = x + (long long)f * nvox;
-    float acc = 0.0f;
-    for (int q = 0; q < r.wz; ++q) {
-      const int j = j0 + q;
-      if (j < 0 || j >= r.nzp) continue;
-      const float w = hat_avg(shear_u(izr, j, r.pz, sh), r.betaz);
-      if (w != 0.0f) acc = fmaf(w, __ldg(xf + perm_index(r, j, iy, ixp)), acc);
-    }
-    rz[idx] = acc;
+// Entries of a shear pass depend on the output/source offset and the
+// column's shift only, so each column's band is tabulated once (plan time):
+// window offset J = floor(sh - 1 - beta/2) - 1 and, for q = 0..nw-1, the entry
+// between output i and source i - pad + J + q, hat_avg(-J - q + sh, beta) --
+// the same float operations as shear_u(i, i - pad + J + q, pad, sh), so the
+// forward and adjoint passes below read identical entries.
+__global__ void shear_tables_kernel(RotParam r) {
+  const int n = r.nxp + r.nzr;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const bool zcol = t < r.nxp;
+    const int c = zcol ? t : t - r.nxp;
+    const float slope = zcol ? r.bz : r.ax, beta = zcol ? r.betaz : r.betax;
+    const float sh = column_shift(slope, c, zcol ? r.nxp : r.nzr);
+    const int J = (int)floorf(sh - 1.0f - 0.5f * beta) - 1;
+    const int w = zcol ? r.wz : r.wx, nw = zcol ? r.nwz : r.wx;
+    float* tab = zcol ? r.tz + (long long)c * nw : r.tx + (long long)c * nw;
+    for (int q = 0; q < nw; ++q) tab[q] = q < w ? hat_avg(shear_u(0, J + q, 0, sh), beta) : 0.0f;
+    (zcol ? r.jz : r.jx)[c] = J;
   }
 }
 
-// xr[f][izr][iy][ixr] = sum_j E^x(ixr, j; izr) rz[f][izr][iy][j]
-__global__ void shear_x_forward(const float* __restrict__ rz, float* __restrict__ xr, RotParam r, int frames) {
-  const long long per = (long long)r.nzr * r.ny * r.nxr;
+constexpr int kShearZChunk = 16;   // outputs along the sheared axis per thread
+
+// rz[f][izr][iy][c] = sum_q tz[c][q] xp[f][izr - pz + jz[c] + q][iy][c], xp the
+// quarter-turned volume.  Thread = (iy, c) column; the NW source values slide
+// through registers along izr, one load per output.
+template <int NW, int NQ>
+__global__ void __launch_bounds__(256) shear_z_forward(const float* __restrict__ x, float* __restrict__ rz,
+                                                       RotParam r, int frames) {
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int iy = blockIdx.y * 8 + threadIdx.y;
+  const int z0 = blockIdx.z * kShearZChunk;
+  if (c >= r.nxp || iy >= r.ny) return;
+  const long long nvox = (long long)r.nx * r.ny * r.nz;
+  const long long per = (long long)r.nzr * r.ny * r.nxp;
+  const long long zstride = (long long)r.ny * r.nxp;
+  float w[NW];
+#pragma unroll
+  for (int q = 0; q < NW; ++q) w[q] = __ldg(r.tz + (long long)c * NW + q);
+  const int J = __ldg(r.jz + c);
+  const int zend = min(z0 + kShearZChunk, r.nzr);
+  for (int f = 0; f < frames; ++f) {
+    const float* xf = x + (long long)f * nvox;
+    float* out = rz + (long long)f * per + (long long)iy * r.nxp + c;
+    const int jb = z0 - r.pz + J;   // first source of output z0
+    float v[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      const int j = jb + q;
+      v[q] = (j >= 0 && j < r.nzp) ? __ldg(xf + perm_index<NQ>(r, j, iy, c)) : 0.0f;
+    }
+    for (int izr = z0; izr < zend; ++izr) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) acc = fmaf(w[q], v[q], acc);
+      out[(long long)izr * zstride] = acc;
+#pragma unroll
+      for (int q = 0; q < NW - 1; ++q) v[q] = v[q + 1];
+      const int j = izr + 1 - r.pz + J + NW - 1;
+      v[NW - 1] = (j >= 0 && j < r.nzp) ? __ldg(xf + perm_index<NQ>(r, j, iy, c)) : 0.0f;
+    }
+  }
+}
+
+// xr[f][izr][iy][ixr] = sum_q tx[izr][q] rz[f][izr][iy][ixr - px + jx[izr] + q]
+__global__ void __launch_bounds__(256) shear_x_forward(const float* __restrict__ rz, float* __restrict__ xr,
+                                                       RotParam r, int frames) {
+  const int ixr = blockIdx.x * 32 + threadIdx.x;
+  const int iy = blockIdx.y * 8 + threadIdx.y;
+  const int izr = blockIdx.z;
+  if (ixr >= r.nxr || iy >= r.ny) return;
   const long long per_in = (long long)r.nzr * r.ny * r.nxp;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < per * frames;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)(idx / per);
-    long long rem = idx - (long long)f * per;
-    const int ixr = (int)(rem % r.nxr);
-    rem /= r.nxr;
-    const int iy = (int)(rem % r.ny);
-    const int izr = (int)(rem / r.ny);
-    const float sh = column_shift(r.ax, izr, r.nzr);
-    const int j0 = (int)floorf((float)(ixr - r.px) + sh - 1.0f - 0.5f * r.betax) - 1;
+  const long long per = (long long)r.nzr * r.ny * r.nxr;
+  const float* tab = r.tx + (long long)izr * r.wx;
+  const int jb = ixr - r.px + __ldg(r.jx + izr);
+  for (int f = 0; f < frames; ++f) {
     const float* row = rz + (long long)f * per_in + ((long long)izr * r.ny + iy) * r.nxp;
     float acc = 0.0f;
     for (int q = 0; q < r.wx; ++q) {
-      const int j = j0 + q;
-      if (j < 0 || j >= r.nxp) continue;
-      const float w = hat_avg(shear_u(ixr, j, r.px, sh), r.betax);
-      if (w != 0.0f) acc = fmaf(w, __ldg(row + j), acc);
+      const int j = jb + q;
+      if (j >= 0 && j < r.nxp) acc = fmaf(__ldg(tab + q), __ldg(row + j), acc);
     }
-    xr[idx] = acc;
+    xr[(long long)f * per + ((long long)izr * r.ny + iy) * r.nxr + ixr] = acc;
   }
 }
 
-// grz[f][izr][iy][j] = sum_ixr E^x(ixr, j; izr) g[f][izr][iy][ixr]
-__global__ void shear_x_adjoint(const float* __restrict__ g, float* __restrict__ grz, RotParam r, int frames) {
-  const long long per = (long long)r.nzr * r.ny * r.nxp;
+// grz[f][izr][iy][j] = sum_ixr E^x(ixr, j; izr) g[f][izr][iy][ixr]: outputs
+// i = j + px - jx[izr] - q, visited in ascending i.
+__global__ void __launch_bounds__(256) shear_x_adjoint(const float* __restrict__ g, float* __restrict__ grz,
+                                                       RotParam r, int frames) {
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int iy = blockIdx.y * 8 + threadIdx.y;
+  const int izr = blockIdx.z;
+  if (j >= r.nxp || iy >= r.ny) return;
   const long long per_in = (long long)r.nzr * r.ny * r.nxr;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < per * frames;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)(idx / per);
-    long long rem = idx - (long long)f * per;
-    const int j = (int)(rem % r.nxp);
-    rem /= r.nxp;
-    const int iy = (int)(rem % r.ny);
-    const int izr = (int)(rem / r.ny);
-    const float sh = column_shift(r.ax, izr, r.nzr);
-    // outputs i with |i - j - px + sh| < 1 + beta/2
-    const int i0 = (int)floorf((float)(j + r.px) - sh - 1.0f - 0.5f * r.betax) - 1;
+  const long long per = (long long)r.nzr * r.ny * r.nxp;
+  const float* tab = r.tx + (long long)izr * r.wx;
+  const int ib = j + r.px - __ldg(r.jx + izr);
+  for (int f = 0; f < frames; ++f) {
     const float* row = g + (long long)f * per_in + ((long long)izr * r.ny + iy) * r.nxr;
     float acc = 0.0f;
-    for (int q = 0; q < r.wx; ++q) {
-      const int i = i0 + q;
-      if (i < 0 || i >= r.nxr) continue;
-      const float w = hat_avg(shear_u(i, j, r.px, sh), r.betax);
-      if (w != 0.0f) acc = fmaf(w, __ldg(row + i), acc);
+    for (int q = r.wx - 1; q >= 0; --q) {
+      const int i = ib - q;
+      if (i >= 0 && i < r.nxr) acc = fmaf(__ldg(tab + q), __ldg(row + i), acc);
     }
-    grz[idx] = acc;
+    grz[(long long)f * per + ((long long)izr * r.ny + iy) * r.nxp + j] = acc;
   }
 }
 
-// x[f][iz][iy][ix] (= or +=) sum_izr E^z(izr, jz; jx) grz[f][izr][iy][jx], (jz, jx) the permuted indices
-__global__ void shear_z_adjoint(const float* __restrict__ grz, float* __restrict__ x, RotParam r, int frames,
-                                int accumulate) {
+// x[f][perm(jz, iy, c)] (= or +=) sum_i E^z(i, jz; c) grz[f][i][iy][c]:
+// outputs i = jz + pz - jz_tab[c] - q in ascending order; the NW values of
+// grz slide through registers along jz.
+template <int NW, int NQ>
+__global__ void __launch_bounds__(256) shear_z_adjoint(const float* __restrict__ grz, float* __restrict__ x,
+                                                       RotParam r, int frames, int accumulate) {
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int iy = blockIdx.y * 8 + threadIdx.y;
+  const int z0 = blockIdx.z * kShearZChunk;
+  if (c >= r.nxp || iy >= r.ny) return;
   const long long nvox = (long long)r.nx * r.ny * r.nz;
   const long long per_in = (long long)r.nzr * r.ny * r.nxp;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nvox * frames;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)(idx / nvox);
-    long long rem = idx - (long long)f * nvox;
-    const int ix = (int)(rem % r.nx);
-    rem /= r.nx;
-    const int iy = (int)(rem % r.ny);
-    const int iz = (int)(rem / r.ny);
-    int jz, jx;   // inverse of perm_index
-    switch (r.nq) {
-      case 1: jx = r.nz - 1 - iz; jz = ix; break;
-      case 2: jz = r.nz - 1 - iz; jx = r.nx - 1 - ix; break;
-      case 3: jx = iz; jz = r.nx - 1 - ix; break;
-      default: jz = iz; jx = ix; break;
+  const long long zstride = (long long)r.ny * r.nxp;
+  float w[NW];   // w[k] weights the k-th value of the window (ascending i)
+#pragma unroll
+  for (int k = 0; k < NW; ++k) w[k] = __ldg(r.tz + (long long)c * NW + (NW - 1 - k));
+  const int J = __ldg(r.jz + c);
+  const int zend = min(z0 + kShearZChunk, r.nzp);
+  for (int f = 0; f < frames; ++f) {
+    const float* gf = grz + (long long)f * per_in + (long long)iy * r.nxp + c;
+    float* xf = x + (long long)f * nvox;
+    const int ib = z0 + r.pz - J - (NW - 1);   // first output row of source z0
+    float v[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const int i = ib + k;
+      v[k] = (i >= 0 && i < r.nzr) ? __ldg(gf + (long long)i * zstride) : 0.0f;
     }
-    const float sh = column_shift(r.bz, jx, r.nxp);
-    const int i0 = (int)floorf((float)(jz + r.pz) - sh - 1.0f - 0.5f * r.betaz) - 1;
-    const float* gf = grz + (long long)f * per_in;
-    float acc = 0.0f;
-    for (int q = 0; q < r.wz; ++q) {
-      const int i = i0 + q;
-      if (i < 0 || i >= r.nzr) continue;
-      const float w = hat_avg(shear_u(i, jz, r.pz, sh), r.betaz);
-      if (w != 0.0f) acc = fmaf(w, __ldg(gf + ((long long)i * r.ny + iy) * r.nxp + jx), acc);
+    for (int jz = z0; jz < zend; ++jz) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NW; ++k) acc = fmaf(w[k], v[k], acc);
+      const long long o = perm_index<NQ>(r, jz, iy, c);
+      xf[o] = accumulate ? xf[o] + acc : acc;
+#pragma unroll
+      for (int k = 0; k < NW - 1; ++k) v[k] = v[k + 1];
+      const int i = jz + 1 + r.pz - J;
+      v[NW - 1] = (i >= 0 && i < r.nzr) ? __ldg(gf + (long long)i * zstride) : 0.0f;
     }
-    x[idx] = accumulate ? x[idx] + acc : acc;
   }
 }
 
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 32); }
 
+__global__ void add_inplace_kernel(float* __restrict__ x, const float* __restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += y[i];
+}
+
+template <int NW>
+void launch_z_forward_nw(dim3 g, dim3 b, cudaStream_t st, const float* x, float* rz, const RotParam& r, int frames) {
+  switch (r.nq) {
+    case 1: shear_z_forward<NW, 1><<<g, b, 0, st>>>(x, rz, r, frames); break;
+    case 2: shear_z_forward<NW, 2><<<g, b, 0, st>>>(x, rz, r, frames); break;
+    case 3: shear_z_forward<NW, 3><<<g, b, 0, st>>>(x, rz, r, frames); break;
+    default: shear_z_forward<NW, 0><<<g, b, 0, st>>>(x, rz, r, frames); break;
+  }
+}
+void launch_z_forward(dim3 g, dim3 b, cudaStream_t st, const float* x, float* rz, const RotParam& r, int frames) {
+  if (r.nwz == 8) launch_z_forward_nw<8>(g, b, st, x, rz, r, frames);
+  else launch_z_forward_nw<16>(g, b, st, x, rz, r, frames);
+}
+template <int NW>
+void launch_z_adjoint_nw(dim3 g, dim3 b, cudaStream_t st, const float* grz, float* x, const RotParam& r, int frames,
+                         int acc) {
+  switch (r.nq) {
+    case 1: shear_z_adjoint<NW, 1><<<g, b, 0, st>>>(grz, x, r, frames, acc); break;
+    case 2: shear_z_adjoint<NW, 2><<<g, b, 0, st>>>(grz, x, r, frames, acc); break;
+    case 3: shear_z_adjoint<NW, 3><<<g, b, 0, st>>>(grz, x, r, frames, acc); break;
+    default: shear_z_adjoint<NW, 0><<<g, b, 0, st>>>(grz, x, r, frames, acc); break;
+  }
+}
+void launch_z_adjoint(dim3 g, dim3 b, cudaStream_t st, const float* grz, float* x, const RotParam& r, int frames,
+                      int acc) {
+  if (r.nwz == 8) launch_z_adjoint_nw<8>(g, b, st, grz, x, r, frames, acc);
+  else launch_z_adjoint_nw<16>(g, b, st, grz, x, r, frames, acc);
+}
+
 }  // namespace
+
+cudaError_t launch_add_inplace(float* x, const float* y, long long n, cudaStream_t st) {
+  if (n > 0) add_inplace_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shear_tables(const RotParam& r, cudaStream_t st) {
+  const int n = r.nxp + r.nzr;
+  shear_tables_kernel<<<(n + 127) / 128, 128, 0, st>>>(r);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rotate_forward(const float* x, float* rz, float* xr, const RotParam& r, int frames,
                                   cudaStream_t st) {
-  const long long nrz = (long long)r.nzr * r.ny * r.nxp * frames;
-  const long long nxr = (long long)r.nzr * r.ny * r.nxr * frames;
-  shear_z_forward<<<grid_for(nrz), 256, 0, st>>>(x, rz, r, frames);
-  shear_x_forward<<<grid_for(nxr), 256, 0, st>>>(rz, xr, r, frames);
+  const dim3 blk(32, 8);
+  const dim3 gz((r.nxp + 31) / 32, (r.ny + 7) / 8, (r.nzr + kShearZChunk - 1) / kShearZChunk);
+  launch_z_forward(gz, blk, st, x, rz, r, frames);
+  shear_x_forward<<<dim3((r.nxr + 31) / 32, (r.ny + 7) / 8, r.nzr), blk, 0, st>>>(rz, xr, r, frames);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rotate_adjoint(const float* g_xr, float* rz, float* x, const RotParam& r, int frames,
                                   int accumulate, cudaStream_t st) {
-  const long long nrz = (long long)r.nzr * r.ny * r.nxp * frames;
-  const long long nvox = (long long)r.nx * r.ny * r.nz * frames;
-  shear_x_adjoint<<<grid_for(nrz), 256, 0, st>>>(g_xr, rz, r, frames);
-  shear_z_adjoint<<<grid_for(nvox), 256, 0, st>>>(rz, x, r, frames, accumulate);
+  const dim3 blk(32, 8);
+  shear_x_adjoint<<<dim3((r.nxp + 31) / 32, (r.ny + 7) / 8, r.nzr), blk, 0, st>>>(g_xr, rz, r, frames);
+  const dim3 gz((r.nxp + 31) / 32, (r.ny + 7) / 8, (r.nzp + kShearZChunk - 1) / kShearZChunk);
+  launch_z_adjoint(gz, blk, st, rz, x, r, frames, accumulate);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,9 @@ _SIGS = {
     "lt_adjoint_camera": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     "lt_forward_camera_noalloc": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_camera_cells": (c_int32, [c_void_p, c_int32, POINTER(c_int32)]),
+    "lt_camera_grid": (c_int32, [c_void_p, c_int32, POINTER(lt_volume_desc)]),
+    "lt_rotate_volume": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "lt_rotate_volume_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     "lt_plenoptic_stage1": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_plenoptic_stage1_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     "lt_plenoptic_stage2": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -176,6 +179,20 @@ def lt_camera_cells(plan, cam: int) -> int:
     k = c_int32()
     _check(lib().lt_camera_cells(plan, cam, byref(k)))
     return k.value
+
+
+def lt_camera_grid(plan, cam: int) -> lt_volume_desc:
+    g = lt_volume_desc()
+    _check(lib().lt_camera_grid(plan, cam, byref(g)))
+    return g
+
+
+def lt_rotate_volume(plan, cam, x_ptr, xc_ptr, stream=0):
+    _check(lib().lt_rotate_volume(plan, cam, x_ptr, xc_ptr, stream))
+
+
+def lt_rotate_volume_adjoint(plan, cam, xc_ptr, x_ptr, accumulate=0, stream=0):
+    _check(lib().lt_rotate_volume_adjoint(plan, cam, xc_ptr, x_ptr, accumulate, stream))
 
 
 def lt_plenoptic_stage1(plan, cam, x_ptr, fa_ptr, stream=0):
@@ -345,6 +362,29 @@ class Plan:
 
     def stats(self, cam):
         return lt_camera_stats_get(self.handle, cam)
+
+    def camera_grid(self, cam):
+        """(nz, ny, nx) and (dz, dy, dx) of camera cam's rotated grid."""
+        g = lt_camera_grid(self.handle, cam)
+        return (g.nz, g.ny, g.nx), (g.dz, g.dy, g.dx)
+
+    def rotate(self, cam, x, xc=None):
+        """x_c = E^x E^z P x on camera cam's grid (Sec. III-A)."""
+        import torch
+        shp, _ = self.camera_grid(cam)
+        n = int(np.prod(shp))
+        xc = torch.empty(self.frames, n, device="cuda", dtype=torch.float32) if xc is None else xc
+        lt_rotate_volume(self.handle, cam, _dev_f32(x, self.frames * self.nvox, "x"),
+                         _dev_f32(xc, self.frames * n, "xc"), _stream())
+        return xc
+
+    def rotate_adjoint(self, cam, xc, x=None, accumulate=False):
+        shp, _ = self.camera_grid(cam)
+        n = int(np.prod(shp))
+        x = self.new_x() if x is None else x
+        lt_rotate_volume_adjoint(self.handle, cam, _dev_f32(xc, self.frames * n, "xc"),
+                                 _dev_f32(x, self.frames * self.nvox, "x"), int(accumulate), _stream())
+        return x
 
     def array_shape(self, cam):
         c = self.cams[cam]
