@@ -120,13 +120,13 @@ __device__ __forceinline__ void group_barrier(int id) {
 }
 
 template <int W, int SB, int G>
-__global__ void __launch_bounds__(G * FT_GTHREADS)
+__global__ void __launch_bounds__(G * FT_GTHREADS, 1024 / (G * FT_GTHREADS))
 beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict__ items, int n_items,
                      int* __restrict__ counter) {
   __shared__ float sw[G][SB][W][FT_S];
   __shared__ int sx[G][SB][W][FT_S];
-  __shared__ float tw[G][SB][W][FT_T];
   __shared__ int ty[G][SB][W][FT_T];
+  __shared__ float2 tp[G][SB][W][FT_T];  // (t-weight x slice scale, byte offset of its T row)
   __shared__ float red[G > 1 ? G - 1 : 1][FT_T][FT_S + 1];
   __shared__ float T[G][SB][FT_TR][FT_S];
   __shared__ int s_item;
@@ -193,7 +193,7 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
               sw[grp][sl][a][rr] = w;
               sx[grp][sl][a][rr] = jj;
             } else {
-              tw[grp][sl][a][rr] = w;
+              tp[grp][sl][a][rr].x = __fmul_rn(w, p->scale);
               ty[grp][sl][a][rr] = jj;   // voxel row
             }
           }
@@ -214,6 +214,15 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
           }
         }
         if (nrows_max <= FT_TR) {
+          // B2's operands: t-weight and the byte offset of its (clamped) T row
+          for (int e = gt; e < nsl * W * FT_T; e += FT_GTHREADS) {
+            const int sl = e / (W * FT_T);
+            const int b = (e / FT_T) % W;
+            const int row = e % FT_T;
+            const int lo = min(ty[grp][sl][0][0], ty[grp][sl][0][FT_T - 1]);   // r_lo of slice sl
+            const int tr = min(max(ty[grp][sl][b][row] - lo, 0), nrows_max - 1);
+            tp[grp][sl][b][row].y = __int_as_float((sl * FT_TR + tr) * FT_S * 4);
+          }
           // B1: s-contraction T[sl][r][col] = sum_a ws[col][a] x[n][r_lo + r][sx_a(col)]
           for (int sl = 0; sl < nsl; ++sl) {
             const float* xs = xf + (long long)(nb + sl) * ny * nx + (long long)r_lo[sl] * nx;
@@ -236,26 +245,22 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
           }
           group_barrier(1 + grp);
           // B2: t-contraction per pixel from shared memory
+          const char* Tl = reinterpret_cast<const char*>(&T[grp][0][0][0]) + lane * 4;
           for (int sl = 0; sl < nsl; ++sl) {
-            const float scale = pk[nb + sl].scale;
-            const int base = r_lo[sl];
 #pragma unroll
             for (int r = 0; r < FT_ROWS; ++r) {
               const int row = warp + 4 * r;
-              float v = 0.0f;
 #pragma unroll
               for (int b = 0; b < W; ++b) {
-                const int tr = min(max(ty[grp][sl][b][row] - base, 0), nrows_max - 1);
-                v = fmaf(tw[grp][sl][b][row], T[grp][sl][tr][lane], v);
+                const float2 q = tp[grp][sl][b][row];
+                acc[r] = fmaf(q.x, *reinterpret_cast<const float*>(Tl + __float_as_int(q.y)), acc[r]);
               }
-              acc[r] = fmaf(scale, v, acc[r]);
             }
           }
         } else {
           // direct gather (footprints spanning many voxel rows)
           for (int sl = 0; sl < nsl; ++sl) {
             const int n = nb + sl;
-            const float scale = pk[n].scale;
             const float* xs = xf + (long long)n * ny * nx;
             float wsr[W];
             int sxr[W];
@@ -274,9 +279,9 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
                 float u = 0.0f;
 #pragma unroll
                 for (int a = 0; a < W; ++a) u = fmaf(wsr[a], __ldg(xr + sxr[a]), u);
-                v = fmaf(tw[grp][sl][b][row], u, v);
+                v = fmaf(tp[grp][sl][b][row].x, u, v);
               }
-              acc[r] = fmaf(scale, v, acc[r]);
+              acc[r] = __fadd_rn(acc[r], v);
             }
           }
         }
@@ -610,29 +615,37 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
 
 int window_class(int w) { return w <= 2 ? 2 : w <= 3 ? 3 : w <= 4 ? 4 : 8; }
 
+struct FwConfig {
+  const void* fn;
+  int threads;
+};
+
 template <int W, int SB, int G>
-static const void* fw_kernel() {
-  return (const void*)beam_forward_batched<W, SB, G>;
+static FwConfig fw_kernel() {
+  return {(const void*)beam_forward_batched<W, SB, G>, G * FT_GTHREADS};
 }
 
 // Variants (slices per batch SB, warp groups G): {4,2} {4,1} {2,2} {2,4} {8,1};
-// windows of 8 use SB = 2 so that shared memory stays within 48 KB.
+// wider windows use smaller batches so that shared memory stays within 48 KB
+// (the kernel and its thread count come from the same instantiation).
 template <int W>
-static const void* fw_select(int variant) {
+static FwConfig fw_select(int variant) {
   if constexpr (W >= 8) {
     return variant == 1 ? fw_kernel<W, 2, 1>() : fw_kernel<W, 2, 2>();
   } else {
     switch (variant) {
       case 1: return fw_kernel<W, 4, 1>();
       case 2: return fw_kernel<W, 2, 2>();
-      case 3: return fw_kernel<W, 2, 4>();
+      case 3:
+        if constexpr (W >= 4) return fw_kernel<W, 2, 2>();
+        else return fw_kernel<W, 2, 4>();
       case 4: return fw_kernel<W, 8, 1>();
       default: return fw_kernel<W, 4, 2>();
     }
   }
 }
 
-static const void* fw_select_class(int wclass, int variant) {
+static FwConfig fw_select_class(int wclass, int variant) {
   switch (wclass) {
     case 2: return fw_select<2>(variant);
     case 3: return fw_select<3>(variant);
@@ -641,15 +654,10 @@ static const void* fw_select_class(int wclass, int variant) {
   }
 }
 
-static int fw_threads(int wclass, int variant) {
-  if (wclass >= 8) return (variant == 1 ? 1 : 2) * FT_GTHREADS;
-  return kForwardVariantTable[variant < 0 || variant >= kForwardVariants ? 0 : variant].groups * FT_GTHREADS;
-}
-
 int beam_forward_occupancy(int wclass, int variant) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fw_select_class(wclass, variant), fw_threads(wclass, variant), 0) !=
-      cudaSuccess)
+  const FwConfig cfg = fw_select_class(wclass, variant);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cfg.fn, cfg.threads, 0) != cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
@@ -663,7 +671,8 @@ cudaError_t launch_beam_forward_batched(const BeamBatch& b, const int4* items, i
   const long long total = (long long)n_items * b.frames;
   const int grid = (int)std::min<long long>(ctas, total);
   void* args[] = {(void*)&b, (void*)&items, (void*)&n_items, (void*)&counter};
-  return cudaLaunchKernel(fw_select_class(wclass, variant), dim3(grid), dim3(fw_threads(wclass, variant)), args, 0, st);
+  const FwConfig cfg = fw_select_class(wclass, variant);
+  return cudaLaunchKernel(cfg.fn, dim3(grid), dim3(cfg.threads), args, 0, st);
 }
 
 cudaError_t launch_beam_adjoint_batched(const BeamBatch& b, float* x, long long x_fs, int accumulate,
