@@ -53,6 +53,12 @@ def lens_cells(cam):
     return cells
 
 
+def _active(ci, cells):
+    """Cell ci takes part (all cells when `cells` is None): the angular-plane
+    subsets of the view-subset approximation (Sec. V, eq. subset)."""
+    return cells is None or ci in cells
+
+
 def slice_distances(vol, cam):
     return cam.d_obj + centers(vol.nz, vol.dz)
 
@@ -95,11 +101,13 @@ def slice_operators(vol, cam, n, cell, d_img, tgt_ns, tgt_nt, tgt_ps, tgt_pt):
 # single-lens camera (Sec. II-F1, Sec. III)
 # ---------------------------------------------------------------------------
 
-def single_forward(vol, cam, x):
-    """y = sum_k sum_n B^{dn}_k (dz x^n), image [nt][ns]."""
+def single_forward(vol, cam, x, cells=None):
+    """y = sum_k sum_n B^{dn}_k (dz x^n), image [nt][ns] (k over `cells`)."""
     X = np.asarray(x, dtype=np.float64).reshape(vol.shape)
     y = np.zeros((cam.det_nt, cam.det_ns))
-    for cell in lens_cells(cam):
+    for ci, cell in enumerate(lens_cells(cam)):
+        if not _active(ci, cells):
+            continue
         for n in range(vol.nz):
             Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_det,
                                      cam.det_ns, cam.det_nt, cam.det_ps, cam.det_pt)
@@ -107,11 +115,13 @@ def single_forward(vol, cam, x):
     return y
 
 
-def single_adjoint(vol, cam, y):
+def single_adjoint(vol, cam, y, cells=None):
     """x = A^T y = sum_k sum_n dz (B^{dn}_k)^T y  (Sec. IV-A: B^{pq} = (B^{qp})^T)."""
     Y = np.asarray(y, dtype=np.float64).reshape(cam.det_nt, cam.det_ns)
     x = np.zeros(vol.shape)
-    for cell in lens_cells(cam):
+    for ci, cell in enumerate(lens_cells(cam)):
+        if not _active(ci, cells):
+            continue
         for n in range(vol.nz):
             Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_det,
                                      cam.det_ns, cam.det_nt, cam.det_ps, cam.det_pt)
@@ -228,12 +238,14 @@ def plenoptic_array_field(vol, cam, x, cell):
     return np.where(lenslet_owner(cam) >= 0, Fa, 0.0)
 
 
-def plenoptic_stage2(cam, fields, st=None):
+def plenoptic_stage2(cam, fields, st=None, cells=None):
     """y = sum_k sum_mu B^{d mu}_k fa_k for given (masked) array-plane fields
-    [K][arr_nt][arr_ns]."""
+    [K][arr_nt][arr_ns] (k over `cells`)."""
     st = _StageTwo(cam) if st is None else st
     y = np.zeros((cam.det_nt, cam.det_ns))
     for ci, cell in enumerate(lens_cells(cam)):
+        if not _active(ci, cells):
+            continue
         Fa = np.asarray(fields[ci], dtype=np.float64)
         for mt in range(cam.mla_nt):
             for ms in range(cam.mla_ns):
@@ -249,13 +261,17 @@ def plenoptic_stage2(cam, fields, st=None):
     return y
 
 
-def plenoptic_stage2_adjoint(cam, y, st=None):
-    """M sum_mu (B^{d mu}_k)^T y for every cell: fields [K][arr_nt][arr_ns]."""
+def plenoptic_stage2_adjoint(cam, y, st=None, cells=None):
+    """M sum_mu (B^{d mu}_k)^T y for every cell: fields [K][arr_nt][arr_ns]
+    (zero for cells outside `cells`)."""
     st = _StageTwo(cam) if st is None else st
     Y = np.asarray(y, dtype=np.float64).reshape(cam.det_nt, cam.det_ns)
     out = []
     for ci, cell in enumerate(lens_cells(cam)):
         Ga = np.zeros((cam.arr_nt, cam.arr_ns))
+        if not _active(ci, cells):
+            out.append(Ga)
+            continue
         for mt in range(cam.mla_nt):
             for ms in range(cam.mla_ns):
                 mu = mt * cam.mla_ns + ms
@@ -272,10 +288,12 @@ def plenoptic_stage2_adjoint(cam, y, st=None):
     return np.stack(out)
 
 
-def plenoptic_stage1_adjoint(vol, cam, fields):
+def plenoptic_stage1_adjoint(vol, cam, fields, cells=None):
     """sum_k sum_n dz (B^{an}_k)^T (1/V^a) g_k for given fields g."""
     x = np.zeros(vol.shape)
     for ci, cell in enumerate(lens_cells(cam)):
+        if not _active(ci, cells):
+            continue
         Ga = np.asarray(fields[ci], dtype=np.float64) / array_basis_volume(cam, cell)
         for n in range(vol.nz):
             Bs, Bt = slice_operators(vol, cam, n, cell, cam.d_lens_mla,
@@ -284,19 +302,20 @@ def plenoptic_stage1_adjoint(vol, cam, fields):
     return x
 
 
-def plenoptic_forward(vol, cam, x, return_array=False):
+def plenoptic_forward(vol, cam, x, return_array=False, cells=None):
     """y = sum_k sum_mu B^{d mu}_k M_mu (1/V^a) sum_n B^{an}_k w^n."""
-    fields = np.stack([plenoptic_array_field(vol, cam, x, cell) for cell in lens_cells(cam)])
-    y = plenoptic_stage2(cam, fields)
+    fields = np.stack([plenoptic_array_field(vol, cam, x, cell) if _active(ci, cells)
+                       else np.zeros((cam.arr_nt, cam.arr_ns)) for ci, cell in enumerate(lens_cells(cam))])
+    y = plenoptic_stage2(cam, fields, cells=cells)
     if return_array:
         return y, fields
     return y
 
 
-def plenoptic_adjoint(vol, cam, y, return_array=False):
+def plenoptic_adjoint(vol, cam, y, return_array=False, cells=None):
     """x = sum_k sum_n dz (B^{an}_k)^T (1/V^a) M sum_mu (B^{d mu}_k)^T y."""
-    fields = plenoptic_stage2_adjoint(cam, y)
-    x = plenoptic_stage1_adjoint(vol, cam, fields)
+    fields = plenoptic_stage2_adjoint(cam, y, cells=cells)
+    x = plenoptic_stage1_adjoint(vol, cam, fields, cells=cells)
     if return_array:
         return x, fields
     return x
@@ -376,33 +395,34 @@ def rotated_volume(vol, cam, x):
     return g, Xr
 
 
-def _aligned_forward(vol, cam, x):
+def _aligned_forward(vol, cam, x, cells=None):
     if cam.kind == 1:
-        return plenoptic_forward(vol, cam, x)
-    return single_forward(vol, cam, x)
+        return plenoptic_forward(vol, cam, x, cells=cells)
+    return single_forward(vol, cam, x, cells=cells)
 
 
-def _aligned_adjoint(vol, cam, y):
+def _aligned_adjoint(vol, cam, y, cells=None):
     if cam.kind == 1:
-        return plenoptic_adjoint(vol, cam, y)
-    return single_adjoint(vol, cam, y)
+        return plenoptic_adjoint(vol, cam, y, cells=cells)
+    return single_adjoint(vol, cam, y, cells=cells)
 
 
-def forward(vol, cam, x):
+def forward(vol, cam, x, cells=None):
+    """A x, or sum_{k in cells} A_k x (angular-plane subset, Sec. V)."""
     if cam.yaw != 0.0:
         g, Xr = rotated_volume(vol, cam, x)
-        return _aligned_forward(g, _Aligned(cam), Xr)
-    return _aligned_forward(vol, cam, x)
+        return _aligned_forward(g, _Aligned(cam), Xr, cells)
+    return _aligned_forward(vol, cam, x, cells)
 
 
-def adjoint(vol, cam, y):
+def adjoint(vol, cam, y, cells=None):
     if cam.yaw != 0.0:
         from . import rotation
         shape_r, sr, _ = rotation.rotated_grid(vol.shape, (vol.dx, vol.dy, vol.dz), cam.yaw)
         g = Grid(shape_r[2], shape_r[1], shape_r[0], sr[0], sr[1], sr[2])
-        Gr = _aligned_adjoint(g, _Aligned(cam), y)
+        Gr = _aligned_adjoint(g, _Aligned(cam), y, cells)
         return rotation.rotate_adjoint(Gr, vol.shape, (vol.dx, vol.dy, vol.dz), cam.yaw)
-    return _aligned_adjoint(vol, cam, y)
+    return _aligned_adjoint(vol, cam, y, cells)
 
 
 def system_matrix(vol, cam):

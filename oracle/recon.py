@@ -89,11 +89,25 @@ def objective(ops, ys, weights, gains, x, shape, beta, nu, psi=0, delta=1.0):
     return val + nu * float(np.sum(np.abs(x))) + R_value(x, shape, beta, psi, delta)
 
 
+def subset_cells(n_cells, n_subset, it):
+    """Cells of the angular-plane subset used at iteration `it` (0-based):
+    every n_subset-th cell in lexicographic order, k = it mod n_subset,
+    it mod n_subset + n_subset, ... (Sec. V, view-subset acceleration)."""
+    return [k for k in range(n_cells) if k % n_subset == it % n_subset]
+
+
 def fista(ops, ys, weights, shape, n_iter, beta=0.0, nu=0.0, psi=0, delta=1.0,
-          reg_scale=26.0, x0=None, estimate_gains=True, history=False):
+          reg_scale=26.0, x0=None, estimate_gains=True, history=False, n_subset=1, n_cells=None):
     """Table V.  ops: list of (A_c, A_c^T) callables on flat float64 vectors;
     ys / weights: flat measurement and weight vectors.  Returns a dict with
-    x, z, gains, t, D (and the per-iteration data-fit at z if history)."""
+    x, z, gains, t, D (and the per-iteration data-fit at z if history).
+
+    With n_subset > 1 (eq. subset) the callables also take cells=[k, ...] and
+    n_cells[c] gives camera c's K; iteration `it` uses S = subset_cells(K,
+    n_subset, it) and a = K / |S|: p = a sum_{k in S} A_ck z, the gain from p,
+    r = p - gamma y and g_c = a sum_{k in S} A_ck^T W r.  A camera whose subset
+    is empty contributes no gradient (a = 0).  The majoriser D stays the full
+    one (all cells)."""
     n = int(np.prod(shape))
     ys = [np.asarray(y, dtype=np.float64).reshape(-1) for y in ys]
     weights = [np.ones_like(y) if w is None else np.asarray(w, dtype=np.float64).reshape(-1)
@@ -109,12 +123,21 @@ def fista(ops, ys, weights, shape, n_iter, beta=0.0, nu=0.0, psi=0, delta=1.0,
         g = np.zeros(n)
         fit = 0.0
         for c, ((A, At), y, w) in enumerate(zip(ops, ys, weights)):
-            p = A(z)
+            if n_subset > 1:
+                S = subset_cells(n_cells[c], n_subset, len(fits))
+                a = n_cells[c] / len(S) if S else 0.0
+                p = a * A(z, cells=S) if S else np.zeros_like(y)
+            else:
+                p = A(z)
             if c > 0 and estimate_gains:
                 gains[c] = optimal_gain(y, p, w)
             r = p - gains[c] * y
             fit += 0.5 * float(np.sum(w * r * r))
-            g += At(w * r)
+            if n_subset > 1:
+                if S:
+                    g += a * At(w * r, cells=S)
+            else:
+                g += At(w * r)
         fits.append(fit)
         t_new = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
         step = g + grad_R(z, shape, beta, psi, delta)
