@@ -112,6 +112,17 @@ LT_API lt_status lt_forward(lt_plan* plan, const float* x, float* y, void* strea
  * per voxel (one writer per output, no atomics).  x is overwritten. */
 LT_API lt_status lt_adjoint(lt_plan* plan, const float* y, float* x, void* stream);
 
+/* Angular-plane subset operators (Sec. V, eq. subset): sum over the cells k
+ * of every camera with k % n_subset == subset (cells in lexicographic order,
+ * s index fastest), without the K/|S| factor.  lt_forward_subset writes y;
+ * lt_adjoint_subset overwrites x.  The subsets s = 0 .. n_subset - 1 of a
+ * partition sum to lt_forward / lt_adjoint.  LT_EINVAL for n_subset < 1 or
+ * subset outside [0, n_subset). */
+LT_API lt_status lt_forward_subset(lt_plan* plan, const float* x, float* y, int32_t n_subset, int32_t subset,
+                                   void* stream);
+LT_API lt_status lt_adjoint_subset(lt_plan* plan, const float* y, float* x, int32_t n_subset, int32_t subset,
+                                   void* stream);
+
 /* Per-camera forward / adjoint.  y_cam: device [F][M_c] (the camera's own
  * image).  lt_adjoint_camera writes x (accumulate = 0) or adds to it
  * (accumulate = 1). */
@@ -216,6 +227,13 @@ typedef struct {
   double psi_delta;       /* delta of the hyperbola                             */
   double reg_scale;       /* curvature bound: 26 (as printed) or 36 (exact)     */
   int32_t estimate_gains; /* 1: gamma_c (c > 0) per Table V step 1b; 0: all 1   */
+  int32_t n_subset;       /* view subsets (Sec. V, eq. subset); 0 or 1 = none.
+                           * Iteration i (0-based) uses the cells k with
+                           * k % n_subset == i % n_subset of every camera c and
+                           * a_c = K_c / |S_c|: p_c = a_c sum_{k in S} A_ck z,
+                           * the gain from p_c, g_c = a_c sum_{k in S} A_ck^T
+                           * W (p_c - gamma_c y_c); D stays the full majoriser.
+                           * A camera with an empty subset adds no gradient. */
 } lt_recon_params;
 
 /* Copies y (device [F][M]) and the optional weights w (device [F][M], NULL =

@@ -64,10 +64,18 @@ lt_status set_error(lt_status s, const char* fmt, ...);
 lt_status cuda_error(cudaError_t e, const char* where);
 void clear_error();
 
+// Angular-plane subset of a projection (Sec. V, eq. subset): the cells k with
+// k % n == s take part; n <= 1 selects every cell.
+struct SubsetSel {
+  int n = 1;
+  int s = 0;
+};
+
 lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long long y_fs,
-                         cudaStream_t st);
+                         cudaStream_t st, SubsetSel sel = SubsetSel{});
 lt_status camera_adjoint(lt_plan* p, int cam, const float* y, long long y_fs, float* x,
-                         int accumulate, cudaStream_t st);
+                         int accumulate, cudaStream_t st, SubsetSel sel = SubsetSel{});
+
 
 }  // namespace lt
 
@@ -88,6 +96,6 @@ struct lt_plan {
 
 namespace lt {
 // Plan-level operators over every camera (one batched launch per stage).
-lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st);
-lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st);
+lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, SubsetSel sel = SubsetSel{});
+lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st, SubsetSel sel = SubsetSel{});
 }  // namespace lt

@@ -63,6 +63,7 @@ struct StageTwo {
   const int2* cand_all_t;     // [det_nt]
   float* zbuf;                // scratch [F][mla_nt*mla_ns][kStage2Window^2]: per-lenslet sub-images
   int32_t full_cover;         // 1 if every array pixel lies in some lenslet block
+  int32_t sub_n, sub_s;       // angular-plane subset (cell_on); 1, 0 for all cells
 };
 
 // Largest detector window (per axis) of one lenslet's sub-image.
@@ -114,7 +115,13 @@ struct BeamCam {
   long long x_fs, out_fs;  // frame strides
   int32_t nx, ny, nz, ns, nt, K, per_cell, tiles_s, tiles_t;
   int32_t wis, wit;        // adjoint windows (max over cells and slices)
+  int32_t sub_n, sub_s;    // angular-plane subset: cells k with k % sub_n == sub_s (all if sub_n <= 1)
 };
+
+// Cell k takes part in the current angular-plane subset (Sec. V, eq. subset).
+__host__ __device__ __forceinline__ bool cell_on(int sub_n, int sub_s, int k) {
+  return sub_n <= 1 || k % sub_n == sub_s;
+}
 struct BeamBatch {
   BeamCam cam[kMaxBatchCams];
   int32_t n_cams;

@@ -153,12 +153,17 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
     const int k_begin = item.y >= 0 ? item.y : 0;
     const int k_end = item.y >= 0 ? item.y + 1 : C.K;
     const float* xf = C.x + (long long)frame * C.x_fs;
+    if (item.y >= 0 && !cell_on(C.sub_n, C.sub_s, item.y)) {   // cell outside the subset: its plane is not written
+      __syncthreads();   // s_item is rewritten by the next take
+      continue;
+    }
 
     float acc[FT_ROWS];
 #pragma unroll
     for (int r = 0; r < FT_ROWS; ++r) acc[r] = 0.0f;
 
     for (int k = k_begin; k < k_end; ++k) {
+      if (!cell_on(C.sub_n, C.sub_s, k)) continue;   // uniform over the CTA
       const int2 rs = C.srange[k * C.tiles_s + tile_s];
       const int2 rt = C.trange[k * C.tiles_t + tile_t];
       const int n0 = max(rs.x, rt.x);
@@ -362,6 +367,7 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
     const int ns = C.ns, nt = C.nt;
     const float* inf = C.in + (long long)frame * C.out_fs;
     for (int k = 0; k < C.K; ++k) {
+      if (!cell_on(C.sub_n, C.sub_s, k)) continue;   // uniform over the CTA
       const SliceParam* p = C.prm + (long long)k * nz + n;
       const int wis = p->wis;
       const int wit = p->wit;
@@ -502,6 +508,7 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
   for (int o = threadIdx.x; o < L2_W * L2_W; o += blockDim.x) Z[o] = 0.0f;
   if (nc > 0 && nr > 0 && nsu > 0 && ntu > 0) {
     for (int k = 0; k < s2.K; ++k) {
+      if (!cell_on(s2.sub_n, s2.sub_s, k)) continue;   // uniform
       const LensletParam* L = s2.lens + (long long)k * nmu + mu;
       const int4 dr = s2.det_range[(long long)k * nmu + mu];
       const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
@@ -576,6 +583,7 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
   const long long Na = (long long)s2.arr_ns * s2.arr_nt;
   const float* yf = y + (long long)frame * y_fs;
   for (int k = 0; k < s2.K; ++k) {
+    if (!cell_on(s2.sub_n, s2.sub_s, k)) continue;   // uniform: plane k is left unwritten
     const LensletParam* L = s2.lens + (long long)k * nmu + mu;
     const int4 dr = s2.det_range[(long long)k * nmu + mu];
     const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;

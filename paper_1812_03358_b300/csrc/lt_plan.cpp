@@ -541,6 +541,8 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   s2.cand_all_t = c.d_cand_all_t;
   s2.zbuf = c.d_zbuf;
   s2.full_cover = full_cover;
+  s2.sub_n = 1;
+  s2.sub_s = 0;
   return LT_OK;
 }
 
@@ -862,7 +864,8 @@ static lt_status to_camera_grid(lt_plan* p, CameraPlan& c, const float* x, const
 // Description of camera c's slice -> plane transport for a batched launch:
 // camera-grid volume xc, forward output `out` / adjoint input `in`, both with
 // frame stride out_fs.
-static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const float* in, long long out_fs) {
+static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const float* in, long long out_fs,
+                        SubsetSel sel = SubsetSel{}) {
   const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
   BeamCam b{};
   b.x = xc;
@@ -885,6 +888,8 @@ static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const 
   b.tiles_t = c.tiles_t;
   b.wis = c.wimax_s;
   b.wit = c.wimax_t;
+  b.sub_n = sel.n;
+  b.sub_s = sel.s;
   return b;
 }
 
@@ -900,11 +905,11 @@ static int cam_class(const CameraPlan& c) { return window_class(std::max(c.wmax_
 // Adjoint of one camera's slice -> plane transport from `in` back to x
 // (through the transposed rotation for rotated cameras).
 static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* in, long long in_fs, float* x,
-                                        int accumulate, cudaStream_t st) {
+                                        int accumulate, cudaStream_t st, SubsetSel sel = SubsetSel{}) {
   BeamBatch b{};
   b.n_cams = 1;
   b.frames = p->frames;
-  b.cam[0] = beam_cam(c, nullptr, nullptr, in, in_fs);
+  b.cam[0] = beam_cam(c, nullptr, nullptr, in, in_fs, sel);
   float* dst = c.rotated ? c.d_xr : x;
   cudaError_t e = launch_beam_adjoint_batched(b, dst, c.nvox_c, c.rotated ? 0 : accumulate, st);
   if (e != cudaSuccess) return cuda_error(e, "beam adjoint");
@@ -916,50 +921,57 @@ static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* 
 }
 
 lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, long long fa_fs,
-                         cudaStream_t st) {
+                         cudaStream_t st, SubsetSel sel = SubsetSel{}) {
   const float* xc = nullptr;
   lt_status s = to_camera_grid(p, c, x, &xc, st);
   if (s != LT_OK) return s;
   BeamBatch b{};
   b.n_cams = 1;
   b.frames = p->frames;
-  b.cam[0] = beam_cam(c, xc, fa, nullptr, fa_fs);
+  b.cam[0] = beam_cam(c, xc, fa, nullptr, fa_fs, sel);
   return run_forward(p, b, c.d_items, c.n_items, cam_class(c), st);
 }
 
 lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
-                         int accumulate, cudaStream_t st) {
-  return beam_adjoint_to_volume(p, c, fa, fa_fs, x, accumulate, st);
+                         int accumulate, cudaStream_t st, SubsetSel sel = SubsetSel{}) {
+  return beam_adjoint_to_volume(p, c, fa, fa_fs, x, accumulate, st, sel);
+}
+
+static StageTwo stage_two(const CameraPlan& c, SubsetSel sel) {
+  StageTwo s2 = c.s2;
+  s2.sub_n = sel.n;
+  s2.sub_s = sel.s;
+  return s2;
 }
 
 lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long long y_fs,
-                         cudaStream_t st) {
+                         cudaStream_t st, SubsetSel sel) {
   CameraPlan& c = p->cams[cam];
-  if (c.desc.kind == LT_CAM_SINGLE) return stage1_forward(p, c, x, y, y_fs, st);
+  if (c.desc.kind == LT_CAM_SINGLE) return stage1_forward(p, c, x, y, y_fs, st, sel);
   const long long fa_fs = (long long)c.K * c.Na;
-  lt_status s = stage1_forward(p, c, x, c.d_fa, fa_fs, st);
+  lt_status s = stage1_forward(p, c, x, c.d_fa, fa_fs, st, sel);
   if (s != LT_OK) return s;
-  cudaError_t e = launch_stage2_forward(c.d_fa, y, c.s2, p->frames, fa_fs, y_fs, c.d_zbuf, st);
+  cudaError_t e = launch_stage2_forward(c.d_fa, y, stage_two(c, sel), p->frames, fa_fs, y_fs, c.d_zbuf, st);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "plenoptic stage 2");
 }
 
 lt_status camera_adjoint(lt_plan* p, int cam, const float* y, long long y_fs, float* x,
-                         int accumulate, cudaStream_t st) {
+                         int accumulate, cudaStream_t st, SubsetSel sel) {
   CameraPlan& c = p->cams[cam];
-  if (c.desc.kind == LT_CAM_SINGLE) return beam_adjoint_to_volume(p, c, y, y_fs, x, accumulate, st);
+  if (c.desc.kind == LT_CAM_SINGLE) return beam_adjoint_to_volume(p, c, y, y_fs, x, accumulate, st, sel);
   const long long fa_fs = (long long)c.K * c.Na;
-  cudaError_t e = launch_stage2_adjoint(y, c.d_fa, c.s2, p->frames, y_fs, fa_fs, st);
+  cudaError_t e = launch_stage2_adjoint(y, c.d_fa, stage_two(c, sel), p->frames, y_fs, fa_fs, st);
   if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2 adjoint");
-  return stage1_adjoint(p, c, c.d_fa, fa_fs, x, accumulate, st);
+  return stage1_adjoint(p, c, c.d_fa, fa_fs, x, accumulate, st, sel);
 }
 
 // Every camera at once: rotated views, ONE persistent beam launch over all
 // cameras' work items (longest first), then the plenoptic microlens stages.
-lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st) {
+lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, SubsetSel sel) {
   const int nc = (int)p->cams.size();
   if (nc > kMaxBatchCams) {
     for (int c = 0; c < nc; ++c) {
-      lt_status s = camera_forward(p, c, x, y + p->cams[c].offset, p->m_total, st);
+      lt_status s = camera_forward(p, c, x, y + p->cams[c].offset, p->m_total, st, sel);
       if (s != LT_OK) return s;
     }
     return LT_OK;
@@ -973,15 +985,15 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st) {
     lt_status s = to_camera_grid(p, c, x, &xc, st);
     if (s != LT_OK) return s;
     const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
-    b.cam[i] = beam_cam(c, xc, plen ? c.d_fa : y + c.offset, nullptr, plen ? (long long)c.K * c.Na : p->m_total);
+    b.cam[i] = beam_cam(c, xc, plen ? c.d_fa : y + c.offset, nullptr, plen ? (long long)c.K * c.Na : p->m_total, sel);
   }
   lt_status s = run_forward(p, b, p->d_items, p->n_items, p->wclass, st);
   if (s != LT_OK) return s;
   for (int i = 0; i < nc; ++i) {
     CameraPlan& c = p->cams[i];
     if (c.desc.kind != LT_CAM_PLENOPTIC) continue;
-    cudaError_t e = launch_stage2_forward(c.d_fa, y + c.offset, c.s2, p->frames, (long long)c.K * c.Na, p->m_total,
-                                          c.d_zbuf, st);
+    cudaError_t e = launch_stage2_forward(c.d_fa, y + c.offset, stage_two(c, sel), p->frames, (long long)c.K * c.Na,
+                                          p->m_total, c.d_zbuf, st);
     if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2");
   }
   return LT_OK;
@@ -990,13 +1002,13 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st) {
 // x = sum_c A_c^T y_c: microlens-stage adjoints, ONE gather launch over all
 // cameras that see the volume unrotated (one writer per voxel), then each
 // rotated camera through its own grid and the transposed rotation.
-lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st) {
+lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st, SubsetSel sel) {
   const int nc = (int)p->cams.size();
   for (int i = 0; i < nc; ++i) {
     CameraPlan& c = p->cams[i];
     if (c.desc.kind != LT_CAM_PLENOPTIC) continue;
-    cudaError_t e = launch_stage2_adjoint(y + c.offset, c.d_fa, c.s2, p->frames, p->m_total, (long long)c.K * c.Na,
-                                          st);
+    cudaError_t e = launch_stage2_adjoint(y + c.offset, c.d_fa, stage_two(c, sel), p->frames, p->m_total,
+                                          (long long)c.K * c.Na, st);
     if (e != cudaSuccess) return cuda_error(e, "plenoptic stage 2 adjoint");
   }
   BeamBatch b{};
@@ -1015,14 +1027,14 @@ lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st) {
     if (c.rotated) continue;
     const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
     b.cam[b.n_cams++] = beam_cam(c, nullptr, nullptr, plen ? c.d_fa : y + c.offset,
-                                 plen ? (long long)c.K * c.Na : p->m_total);
+                                 plen ? (long long)c.K * c.Na : p->m_total, sel);
   }
   for (int i = 0; i < nc; ++i) {
     CameraPlan& c = p->cams[i];
     if (!c.rotated) continue;
     const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
     lt_status s = beam_adjoint_to_volume(p, c, plen ? c.d_fa : y + c.offset,
-                                         plen ? (long long)c.K * c.Na : p->m_total, x, written, st);
+                                         plen ? (long long)c.K * c.Na : p->m_total, x, written, st, sel);
     if (s != LT_OK) return s;
     written = 1;
   }
@@ -1055,6 +1067,24 @@ extern "C" lt_status lt_adjoint(lt_plan* plan, const float* y, float* x, void* s
   clear_error();
   if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
   return plan_adjoint(plan, y, x, (cudaStream_t)stream);
+}
+
+extern "C" lt_status lt_forward_subset(lt_plan* plan, const float* x, float* y, int32_t n_subset, int32_t subset,
+                                       void* stream) {
+  clear_error();
+  if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
+  if (n_subset < 1 || subset < 0 || subset >= n_subset)
+    return set_error(LT_EINVAL, "subset %d of %d", subset, n_subset);
+  return plan_forward(plan, x, y, (cudaStream_t)stream, SubsetSel{n_subset, subset});
+}
+
+extern "C" lt_status lt_adjoint_subset(lt_plan* plan, const float* y, float* x, int32_t n_subset, int32_t subset,
+                                       void* stream) {
+  clear_error();
+  if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
+  if (n_subset < 1 || subset < 0 || subset >= n_subset)
+    return set_error(LT_EINVAL, "subset %d of %d", subset, n_subset);
+  return plan_adjoint(plan, y, x, (cudaStream_t)stream, SubsetSel{n_subset, subset});
 }
 
 extern "C" lt_status lt_forward_camera(lt_plan* plan, int32_t cam, const float* x, float* y_cam,

@@ -41,7 +41,8 @@ __device__ double block_sum(double v, double* sh) {
 // pixels of w * a * b (w = 1 if NULL).  grid = (RED_BLOCKS, F).
 __global__ void __launch_bounds__(RED_THREADS)
 dot_partials(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ w,
-             long long off, long long len, long long m_total, int C, int c, double* __restrict__ part) {
+             long long off, long long len, long long m_total, int C, int c, double* __restrict__ part,
+             double scale) {
   __shared__ double sh[32];
   const long long base = (long long)blockIdx.y * m_total + off;
   double acc = 0.0;
@@ -51,7 +52,7 @@ dot_partials(const float* __restrict__ a, const float* __restrict__ b, const flo
     acc += wi * (double)a[base + i] * (double)b[base + i];
   }
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[((long long)blockIdx.y * C + c) * RED_BLOCKS + blockIdx.x] = acc;
+  if (threadIdx.x == 0) part[((long long)blockIdx.y * C + c) * RED_BLOCKS + blockIdx.x] = scale * acc;
 }
 
 // Table V step 1b (gamma_c = y^T W p / y^T W y, c > 0) and the FISTA scalars
@@ -78,21 +79,22 @@ __global__ void finalize_gains(const double* __restrict__ part, const double* __
   }
 }
 
-// r = W (p - gamma_c y) over camera c's pixels; fit partials of
-// 1/2 sum W (p - gamma y)^2.  grid = (RED_BLOCKS, F).
+// d = a p - gamma_c y over camera c's pixels, r = a W d (a = K_c / |S_c| of
+// the view subset, 1 without subsets); fit partials of 1/2 sum W d^2.
+// grid = (RED_BLOCKS, F).
 __global__ void __launch_bounds__(RED_THREADS)
 residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const float* __restrict__ p,
                 float* __restrict__ r, const double* __restrict__ gains, long long off, long long len,
-                long long m_total, int C, int c, double* __restrict__ fit_part) {
+                long long m_total, int C, int c, double* __restrict__ fit_part, float alpha) {
   __shared__ double sh[32];
   const long long base = (long long)blockIdx.y * m_total + off;
   const float g = (float)gains[blockIdx.y * C + c];
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (long long)gridDim.x * blockDim.x) {
-    const float d = p[base + i] - g * y[base + i];
+    const float d = alpha * p[base + i] - g * y[base + i];
     const float wi = w ? w[base + i] : 1.0f;
-    r[base + i] = wi * d;
+    r[base + i] = (alpha * wi) * d;
     acc += (double)wi * (double)d * (double)d;
   }
   acc = block_sum(acc, sh);
@@ -218,14 +220,15 @@ struct lt_recon {
   int64_t iters = 0;
   bool captured = false;
   int kernels_per_iter = 0;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int n_sub = 1;                                   // view subsets (graphs per subset)
+  std::vector<cudaGraphExec_t> exec;               // [2 * n_sub]: (z parity, subset)
   cudaStream_t cap = nullptr;
 };
 
 static void recon_free(lt_recon* R) {
   if (!R) return;
-  for (int i = 0; i < 2; ++i)
-    if (R->exec[i]) cudaGraphExecDestroy(R->exec[i]);
+  for (cudaGraphExec_t g : R->exec)
+    if (g) cudaGraphExecDestroy(g);
   if (R->cap) cudaStreamDestroy(R->cap);
   void* bufs[] = {R->y, R->w, R->p, R->r, R->g, R->D, R->x, R->z[0], R->z[1],
                   R->ywy, R->gains, R->part, R->fit_part, R->sc};
@@ -245,22 +248,33 @@ static lt_status dalloc(T** p, size_t n, const char* what) {
 
 static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 16); }
 
-// One iteration of Table V from z[sel] to z[1-sel].
-static lt_status recon_step(lt_recon* R, int sel, cudaStream_t st) {
+// K_c / |S_c| of camera c for view subset `sub` (0 when the subset is empty).
+static double subset_scale(const lt_recon* R, int c, int sub) {
+  if (R->n_sub <= 1) return 1.0;
+  const int K = R->plan->cams[c].K;
+  int n = 0;
+  for (int k = 0; k < K; ++k) n += k % R->n_sub == sub;
+  return n > 0 ? (double)K / n : 0.0;
+}
+
+// One iteration of Table V from z[sel] to z[1-sel], using view subset `sub`.
+static lt_status recon_step(lt_recon* R, int sel, int sub, cudaStream_t st) {
   lt_plan* P = R->plan;
   const float* z = R->z[sel];
-  lt_status s = plan_forward(P, z, R->p, st);  // step 1a: p_c = A_c z for every camera
+  const SubsetSel ss{R->n_sub, sub};
+  lt_status s = plan_forward(P, z, R->p, st, ss);  // step 1a: p_c = A_c z for every camera
   if (s != LT_OK) return s;
   const int est = R->prm.estimate_gains && R->C > 1;
-  if (est)  // step 1b inner products
+  if (est)  // step 1b inner products (of the scaled subset projection)
     for (int c = 1; c < R->C; ++c)
       dot_partials<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
-          R->y, R->p, R->w, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->part);
+          R->y, R->p, R->w, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->part, subset_scale(R, c, sub));
   finalize_gains<<<1, 256, 0, st>>>(R->part, R->ywy, R->gains, R->F, R->C, est, R->sc);
-  for (int c = 0; c < R->C; ++c)  // W (p - gamma y)
+  for (int c = 0; c < R->C; ++c)  // a W (a p - gamma y)
     residual_kernel<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
-        R->y, R->w, R->p, R->r, R->gains, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->fit_part);
-  s = plan_adjoint(P, R->r, R->g, st);  // step 1c + 2: g = sum_c A_c^T r_c
+        R->y, R->w, R->p, R->r, R->gains, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->fit_part,
+        (float)subset_scale(R, c, sub));
+  s = plan_adjoint(P, R->r, R->g, st, ss);  // step 1c + 2: g = sum_c A_c^T r_c
   if (s != LT_OK) return s;
   const lt_volume_desc& v = P->vol;
   dim3 grid((v.nx + UPD_TX - 1) / UPD_TX, (v.ny + UPD_TY - 1) / UPD_TY,
@@ -291,7 +305,7 @@ static lt_status load_data(lt_recon* R, const float* y, const float* w, bool new
   }
   for (int c = 0; c < R->C; ++c)
     dot_partials<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(R->y, R->y, R->w, P->cams[c].offset,
-                                                                 P->cams[c].M, R->M, R->C, c, R->part);
+                                                                 P->cams[c].M, R->M, R->C, c, R->part, 1.0);
   finalize_dots<<<1, 256, 0, st>>>(R->part, R->ywy, R->F * R->C);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LT_OK : cuda_error(e, "loading measurements");
@@ -310,11 +324,14 @@ extern "C" lt_status lt_recon_create(lt_plan* plan, const float* y, const float*
   if (q.psi != 0 && q.psi != 1) return set_error(LT_EINVAL, "psi must be 0 (quadratic) or 1 (hyperbola)");
   if (q.psi == 1 && !(q.psi_delta > 0.0)) return set_error(LT_EINVAL, "psi_delta must be positive");
   if (!(q.reg_scale >= 0.0)) return set_error(LT_EINVAL, "reg_scale must be non-negative");
+  if (q.n_subset < 0 || q.n_subset > 64) return set_error(LT_EINVAL, "n_subset must be in [0, 64]");
   cudaStream_t st = (cudaStream_t)stream;
   lt_recon* R = new (std::nothrow) lt_recon();
   if (!R) return set_error(LT_ENOMEM, "host allocation failed");
   R->plan = plan;
   R->prm = q;
+  R->n_sub = q.n_subset > 1 ? q.n_subset : 1;
+  R->exec.assign(2 * (size_t)R->n_sub, nullptr);
   R->F = plan->frames;
   R->C = (int)plan->cams.size();
   R->N = plan->nvox;
@@ -364,11 +381,12 @@ extern "C" lt_status lt_recon_create(lt_plan* plan, const float* y, const float*
 static lt_status capture(lt_recon* R) {
   cudaError_t e = cudaStreamCreateWithFlags(&R->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_error(e, "capture stream");
-  for (int sel = 0; sel < 2; ++sel) {
+  for (int gi = 0; gi < 2 * R->n_sub; ++gi) {
+    const int sel = gi & 1, sub = gi >> 1;
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(R->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_error(e, "begin capture");
-    lt_status s = recon_step(R, sel, R->cap);
+    lt_status s = recon_step(R, sel, sub, R->cap);
     e = cudaStreamEndCapture(R->cap, &graph);
     if (s != LT_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -385,7 +403,7 @@ static lt_status capture(lt_recon* R) {
       if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
     }
     R->kernels_per_iter = nk;
-    e = cudaGraphInstantiate(&R->exec[sel], graph, 0);
+    e = cudaGraphInstantiate(&R->exec[gi], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_error(e, "graph instantiate");
   }
@@ -403,7 +421,7 @@ extern "C" lt_status lt_recon_iterate(lt_recon* R, int32_t n_iter, void* stream)
   }
   cudaStream_t st = (cudaStream_t)stream;
   for (int i = 0; i < n_iter; ++i) {
-    cudaError_t e = cudaGraphLaunch(R->exec[R->zsel], st);
+    cudaError_t e = cudaGraphLaunch(R->exec[2 * (size_t)(R->iters % R->n_sub) + R->zsel], st);
     if (e != cudaSuccess) return cuda_error(e, "graph launch");
     R->zsel = 1 - R->zsel;
     R->iters++;

@@ -38,7 +38,7 @@ class lt_camera_desc(ctypes.Structure):
 
 class lt_recon_params(ctypes.Structure):
     _fields_ = [("beta", c_double), ("nu", c_double), ("psi", c_int32), ("psi_delta", c_double),
-                ("reg_scale", c_double), ("estimate_gains", c_int32)]
+                ("reg_scale", c_double), ("estimate_gains", c_int32), ("n_subset", c_int32)]
 
 
 class lt_camera_stats(ctypes.Structure):
@@ -67,6 +67,8 @@ _SIGS = {
     "lt_forward_camera_noalloc": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_camera_cells": (c_int32, [c_void_p, c_int32, POINTER(c_int32)]),
     "lt_camera_grid": (c_int32, [c_void_p, c_int32, POINTER(lt_volume_desc)]),
+    "lt_forward_subset": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
+    "lt_adjoint_subset": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
     "lt_rotate_volume": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "lt_rotate_volume_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     "lt_plenoptic_stage1": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -179,6 +181,14 @@ def lt_camera_cells(plan, cam: int) -> int:
     k = c_int32()
     _check(lib().lt_camera_cells(plan, cam, byref(k)))
     return k.value
+
+
+def lt_forward_subset(plan, x_ptr, y_ptr, n_subset, subset, stream=0):
+    _check(lib().lt_forward_subset(plan, x_ptr, y_ptr, n_subset, subset, stream))
+
+
+def lt_adjoint_subset(plan, y_ptr, x_ptr, n_subset, subset, stream=0):
+    _check(lib().lt_adjoint_subset(plan, y_ptr, x_ptr, n_subset, subset, stream))
 
 
 def lt_camera_grid(plan, cam: int) -> lt_volume_desc:
@@ -341,6 +351,19 @@ class Plan:
                    _dev_f32(x, self.frames * self.nvox, "x"), _stream())
         return x
 
+    def forward_subset(self, x, n_subset, subset, y=None):
+        """sum over the cells k % n_subset == subset of every camera (Sec. V)."""
+        y = self.new_y() if y is None else y
+        lt_forward_subset(self.handle, _dev_f32(x, self.frames * self.nvox, "x"),
+                          _dev_f32(y, self.frames * self.m_total, "y"), n_subset, subset, _stream())
+        return y
+
+    def adjoint_subset(self, y, n_subset, subset, x=None):
+        x = self.new_x() if x is None else x
+        lt_adjoint_subset(self.handle, _dev_f32(y, self.frames * self.m_total, "y"),
+                          _dev_f32(x, self.frames * self.nvox, "x"), n_subset, subset, _stream())
+        return x
+
     def forward_camera(self, cam, x, y=None):
         import torch
         m = self.offsets[cam + 1] - self.offsets[cam]
@@ -428,11 +451,11 @@ class Recon:
     """Owner of an lt_recon handle (Table V solver) for a Plan and measurements y."""
 
     def __init__(self, plan: Plan, y, w=None, beta=0.0, nu=0.0, psi=0, psi_delta=1.0,
-                 reg_scale=26.0, estimate_gains=True, x0=None):
+                 reg_scale=26.0, estimate_gains=True, x0=None, n_subset=1):
         self.plan = plan
         n = plan.frames * plan.m_total
         prm = lt_recon_params(float(beta), float(nu), int(psi), float(psi_delta), float(reg_scale),
-                              int(bool(estimate_gains)))
+                              int(bool(estimate_gains)), int(n_subset))
         self.handle = lt_recon_create(plan.handle, _dev_f32(y, n, "y"),
                                       _dev_f32(w, n, "w") if w is not None else 0, prm,
                                       _dev_f32(x0, plan.frames * plan.nvox, "x0") if x0 is not None else 0,
