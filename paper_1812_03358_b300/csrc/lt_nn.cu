@@ -18,10 +18,8 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int CV_M = 64;        // output voxels per CTA
-constexpr int CV_K = 16;        // input channels per k step
-constexpr int CV_LD = 24;       // bf16 leading dimension of the staged tiles (multiple of 8)
-constexpr int CV_THREADS = 128; // 4 warps, warp w owns voxel rows 16w .. 16w+15
+constexpr int CV_LD = 24;       // bf16 leading dimension of the weight-gradient tiles (multiple of 8)
+constexpr int CV_THREADS = 128; // weight gradient: 4 warps
 
 __device__ __forceinline__ void tap_offset(int tap, int& dz, int& dy, int& dx) {
   dz = tap / 9 - 1;
@@ -29,79 +27,104 @@ __device__ __forceinline__ void tap_offset(int tap, int& dz, int& dy, int& dx) {
   dx = tap % 3 - 1;
 }
 
-// Implicit GEMM: M = voxels, N = Co (NB columns per CTA), K = 27 x Ci.
-// A tile (64 voxels x 16 channels of one tap) and B tile (16 k x NB) are
-// staged in shared memory with bounds-checked 16-byte loads (zero padding).
+// Halo-tile implicit GEMM (the convolution used by lt_nn_conv3d).  A CTA owns
+// a 16 (x) x 4 (y) x 2 (z) block of output voxels -- eight M tiles of 16
+// consecutive x voxels, two per warp -- and NB output channels.  Per chunk of
+// 16 input channels it stages, once, the (16+2) x (4+2) x (2+2) input halo
+// and the 27 x NB x 16 weights in shared memory; then every tap's A tile is
+// a plain 16-row window of the halo (rows 32 bytes apart), so the 27 taps run
+// back to back without block barriers.  Out-of-volume halo voxels are zero
+// (padding 1); outputs outside the volume are computed and discarded.
+constexpr int CT_X = 16, CT_Y = 4, CT_Z = 2;
+constexpr int CT_HX = CT_X + 2, CT_HY = CT_Y + 2, CT_HZ = CT_Z + 2;
+constexpr int CT_HALO = CT_HX * CT_HY * CT_HZ;   // halo voxels
+constexpr int CT_THREADS = 128;                   // 4 warps, 2 M tiles each
+constexpr int CT_MT = CT_Y * CT_Z;                // 8 M tiles
+
 template <int NB>
-__global__ void __launch_bounds__(CV_THREADS)
-conv3d_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
-              bf16* __restrict__ out_bf, float* __restrict__ out_f, int D, int H, int W, int Ci, int Co,
-              int o_stride, int o_off, int relu) {
-  __shared__ __align__(128) bf16 As[CV_M][CV_LD];
-  __shared__ __align__(128) bf16 Bs[NB][CV_LD];
-  __shared__ __align__(128) float Cs[4][16][NB + 4];
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const long long V = (long long)D * H * W;
-  const long long m0 = (long long)blockIdx.x * CV_M;
+constexpr int ct_smem_bytes() {
+  return (CT_HALO * 16 + 27 * NB * 16) * 2 > CT_MT * 16 * NB * 4 ? (CT_HALO * 16 + 27 * NB * 16) * 2
+                                                                    : CT_MT * 16 * NB * 4;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(CT_THREADS)
+conv3d_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
+                   bf16* __restrict__ out_bf, float* __restrict__ out_f, int D, int H, int W, int Ci, int Co,
+                   int o_stride, int o_off, int relu, int tiles_x, int tiles_y) {
+  extern __shared__ __align__(128) unsigned char ct_smem[];
+  bf16* halo = reinterpret_cast<bf16*>(ct_smem);          // [CT_HALO][16]
+  bf16* wts = halo + CT_HALO * 16;                        // [27][NB][16]
+  float* stage = reinterpret_cast<float*>(ct_smem);       // epilogue [CT_MT * 16][NB], after the last chunk
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bx = blockIdx.x % tiles_x;
+  const int rest = blockIdx.x / tiles_x;
+  const int by = rest % tiles_y, bz = rest / tiles_y;
+  const int x0 = bx * CT_X, y0 = by * CT_Y, z0 = bz * CT_Z;
   const int n0 = blockIdx.y * NB;
   const int b = blockIdx.z;
+  const long long V = (long long)D * H * W;
   const bf16* inb = in + (long long)b * V * Ci;
 
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[NB / 16];
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][NB / 16];
 #pragma unroll
-  for (int j = 0; j < NB / 16; ++j) wmma::fill_fragment(acc[j], 0.0f);
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < NB / 16; ++j) wmma::fill_fragment(acc[m][j], 0.0f);
 
-  // this thread's A row (voxel) and half (8 channels)
-  const int arow = tid >> 1, ahalf = tid & 1;
-  const long long av = m0 + arow;
-  int az = 0, ay = 0, ax = 0;
-  if (av < V) {
-    az = (int)(av / ((long long)H * W));
-    const int rem = (int)(av - (long long)az * H * W);
-    ay = rem / W;
-    ax = rem - ay * W;
-  }
-  const long long K = 27LL * Ci;
-  for (int tap = 0; tap < 27; ++tap) {
-    int dz, dy, dx;
-    tap_offset(tap, dz, dy, dx);
-    const int zz = az + dz, yy = ay + dy, xx = ax + dx;
-    const bool ain = av < V && zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
-    const long long aoff = ain ? (((long long)zz * H + yy) * W + xx) * Ci + ahalf * 8 : 0;
-    for (int c0 = 0; c0 < Ci; c0 += CV_K) {
-      uint4 av4 = make_uint4(0, 0, 0, 0);
-      if (ain) av4 = *reinterpret_cast<const uint4*>(inb + aoff + c0);
-      *reinterpret_cast<uint4*>(&As[arow][ahalf * 8]) = av4;
-      for (int t = tid; t < NB * 2; t += CV_THREADS) {
-        const int n = t >> 1, h = t & 1;
-        uint4 bv = make_uint4(0, 0, 0, 0);
-        if (n0 + n < Co) bv = *reinterpret_cast<const uint4*>(w + (long long)(n0 + n) * K + (long long)tap * Ci + c0 + h * 8);
-        *reinterpret_cast<uint4*>(&Bs[n][h * 8]) = bv;
-      }
-      __syncthreads();
-      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
-      wmma::load_matrix_sync(a, &As[warp * 16][0], CV_LD);
+  for (int c0 = 0; c0 < Ci; c0 += 16) {
+    __syncthreads();   // the previous chunk's tiles are no longer read
+    for (int t = tid; t < CT_HALO * 2; t += CT_THREADS) {
+      const int v = t >> 1, h = t & 1;
+      const int hx = v % CT_HX, hy = (v / CT_HX) % CT_HY, hz = v / (CT_HX * CT_HY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
+        val = *reinterpret_cast<const uint4*>(inb + (((long long)gz * H + gy) * W + gx) * Ci + c0 + h * 8);
+      *reinterpret_cast<uint4*>(halo + v * 16 + h * 8) = val;
+    }
+    for (int t = tid; t < 27 * NB * 2; t += CT_THREADS) {
+      const int h = t & 1, r = t >> 1;
+      const int co = r % NB, tap = r / NB;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (n0 + co < Co) val = *reinterpret_cast<const uint4*>(w + ((long long)(n0 + co) * 27 + tap) * Ci + c0 + h * 8);
+      *reinterpret_cast<uint4*>(wts + (tap * NB + co) * 16 + h * 8) = val;
+    }
+    __syncthreads();
+    for (int tap = 0; tap < 27; ++tap) {
+      int dz, dy, dx;
+      tap_offset(tap, dz, dy, dx);
+      wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> bfr[NB / 16];
 #pragma unroll
-      for (int j = 0; j < NB / 16; ++j) {
-        wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> bfr;
-        wmma::load_matrix_sync(bfr, &Bs[j * 16][0], CV_LD);
-        wmma::mma_sync(acc[j], a, bfr, acc[j]);
+      for (int j = 0; j < NB / 16; ++j) wmma::load_matrix_sync(bfr[j], wts + (tap * NB + 16 * j) * 16, 16);
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int mt = warp * 2 + m;
+        const int ty = mt % CT_Y, tz = mt / CT_Y;
+        const bf16* ap = halo + (((tz + dz + 1) * CT_HY + (ty + dy + 1)) * CT_HX + (dx + 1)) * 16;
+        wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
+        wmma::load_matrix_sync(a, ap, 16);
+#pragma unroll
+        for (int j = 0; j < NB / 16; ++j) wmma::mma_sync(acc[m][j], a, bfr[j], acc[m][j]);
       }
-      __syncthreads();
     }
   }
+  __syncthreads();   // halo and weights are dead; the region becomes the epilogue stage
 #pragma unroll
-  for (int j = 0; j < NB / 16; ++j) wmma::store_matrix_sync(&Cs[warp][0][j * 16], acc[j], NB + 4, wmma::mem_row_major);
-  __syncwarp();
-  for (int e = lane; e < 16 * NB; e += 32) {
-    const int r = e / NB, c = e - r * NB;
-    const long long v = m0 + warp * 16 + r;
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < NB / 16; ++j)
+      wmma::store_matrix_sync(stage + ((warp * 2 + m) * 16) * NB + 16 * j, acc[m][j], NB, wmma::mem_row_major);
+  __syncwarp();   // each warp reads back only its own 32 rows
+  for (int e = lane; e < 32 * NB; e += 32) {
+    const int row = e / NB, c = e - row * NB;
+    const int mt = warp * 2 + (row >> 4), xr = row & 15;
+    const int gx = x0 + xr, gy = y0 + mt % CT_Y, gz = z0 + mt / CT_Y;
     const int co = n0 + c;
-    if (v < V && co < Co) {
-      float val = Cs[warp][r][c] + (bias ? bias[co] : 0.0f);
+    if (gx < W && gy < H && gz < D && co < Co) {
+      float val = stage[(warp * 32 + row) * NB + c] + (bias ? bias[co] : 0.0f);
       if (relu) val = fmaxf(val, 0.0f);
-      const long long o = ((long long)b * V + v) * o_stride + o_off + co;
+      const long long o = ((long long)b * V + ((long long)gz * H + gy) * W + gx) * o_stride + o_off + co;
       if (out_bf) out_bf[o] = __float2bfloat16_rn(val);
       if (out_f) out_f[o] = val;
     }
@@ -365,16 +388,31 @@ extern "C" lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const f
   if (!in || !w || (!out_bf && !out_f) || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 ||
       Ci % 16 || Co % 16 || o_off < 0 || o_stride < o_off + Co)
     return set_error(LT_EINVAL, "conv3d: bad arguments (channels must be multiples of 16)");
-  const long long V = (long long)D * H * W;
   const int nb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
-  dim3 grid((unsigned)((V + CV_M - 1) / CV_M), Co / nb, batch);
+  const int tx = (W + CT_X - 1) / CT_X, ty = (H + CT_Y - 1) / CT_Y, tz = (D + CT_Z - 1) / CT_Z;
+  const long long tiles = (long long)tx * ty * tz;
+  if (tiles > 0x7fffffffLL) return set_error(LT_EINVAL, "conv3d: volume too large");
+  dim3 grid((unsigned)tiles, Co / nb, batch);
   cudaStream_t st = (cudaStream_t)stream;
   const bf16* i_ = reinterpret_cast<const bf16*>(in);
   const bf16* w_ = reinterpret_cast<const bf16*>(w);
   bf16* o_ = reinterpret_cast<bf16*>(out_bf);
-  if (nb == 64) conv3d_kernel<64><<<grid, CV_THREADS, 0, st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride, o_off, relu);
-  else if (nb == 32) conv3d_kernel<32><<<grid, CV_THREADS, 0, st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride, o_off, relu);
-  else conv3d_kernel<16><<<grid, CV_THREADS, 0, st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride, o_off, relu);
+  static bool attr_set = false;   // the 64-channel variant needs more than 48 KB of shared memory
+  if (!attr_set) {
+    cudaFuncSetAttribute(conv3d_tile_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, ct_smem_bytes<64>());
+    cudaFuncSetAttribute(conv3d_tile_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, ct_smem_bytes<32>());
+    cudaFuncSetAttribute(conv3d_tile_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, ct_smem_bytes<16>());
+    attr_set = true;
+  }
+  if (nb == 64)
+    conv3d_tile_kernel<64><<<grid, CT_THREADS, ct_smem_bytes<64>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride,
+                                                                         o_off, relu, tx, ty);
+  else if (nb == 32)
+    conv3d_tile_kernel<32><<<grid, CT_THREADS, ct_smem_bytes<32>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride,
+                                                                         o_off, relu, tx, ty);
+  else
+    conv3d_tile_kernel<16><<<grid, CT_THREADS, ct_smem_bytes<16>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co, o_stride,
+                                                                         o_off, relu, tx, ty);
   return launched("conv3d");
 }
 

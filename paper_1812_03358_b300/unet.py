@@ -191,6 +191,22 @@ class UNet:
         self.head = Conv(c1, 16, gen)
         self.step = 0
 
+    def flops(self, dims):
+        """Multiply-add flops (2 per MAC) of one forward pass on a D x H x W
+        input: 2 * voxels * 27 * Ci * Co per convolution."""
+        D, H, W = dims
+        total = 0
+        for l, (ca, cb) in enumerate(self.enc):
+            v = (D >> l) * (H >> l) * (W >> l)
+            total += 2 * v * 27 * (ca.ci * ca.co + cb.ci * cb.co)
+        v = (D >> 3) * (H >> 3) * (W >> 3)
+        total += 2 * v * 27 * sum(c.ci * c.co for c in self.bott)
+        for i, (ca, cb) in enumerate(self.dec):
+            l = 2 - i
+            v = (D >> l) * (H >> l) * (W >> l)
+            total += 2 * v * 27 * (ca.ci * ca.co + cb.ci * cb.co)
+        return total + 2 * D * H * W * 27 * self.head.ci * self.head.co
+
     def convs(self):
         out = []
         for a, b in self.enc:

@@ -118,7 +118,10 @@ def evaluate(plan: lt.Plan, ws: WarmStart, y, x_true=None, n_plain: int = 200, b
     t_plain_first = timed(lambda: run_plain(k_plain))
     t_warm = timed(run_warm) if k_warm is not None else None
     t_unet = timed(lambda: ws.infer(bp))
+    v = plan.vol
+    unet_flops = ws.net.flops((v.nz, v.ny, v.nx))
     return {"n_plain": n_plain, "beta_scale": beta_scale, "target_fit": target,
+            "unet_gflop": unet_flops / 1e9, "unet_tflops": unet_flops / (t_unet * 1e-3) / 1e12,
             "plain_ms": t_plain, "plain_first_cross_iters": k_plain, "plain_first_cross_ms": t_plain_first,
             "warm_iters": k_warm, "warm_ms": t_warm, "unet_ms": t_unet,
             "fit_warm_x0_iter1": f_warm[0], "fit_plain_iter1": f_plain[0],
