@@ -18,8 +18,6 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int CV_LD = 24;       // bf16 leading dimension of the weight-gradient tiles (multiple of 8)
-constexpr int CV_THREADS = 128; // weight gradient: 4 warps
 
 __device__ __forceinline__ void tap_offset(int tap, int& dz, int& dy, int& dx) {
   dz = tap / 9 - 1;
@@ -131,74 +129,100 @@ conv3d_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, cons
   }
 }
 
-// Weight gradient: for one tap and 16 input channels, dW[co][tap][ci] =
-// sum over a chunk of voxels of g[v][co] in[v + tap][ci]; M = Co (64 per
-// CTA), N = 16, K = voxels (16 per step).  Partial sums are added with float
-// atomics (order-dependent rounding only).
-constexpr int WG_STEPS = 128;   // k steps (of 16 voxels) per CTA
-
-__global__ void __launch_bounds__(CV_THREADS)
-conv3d_wgrad_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ dw, int D, int H,
-                    int W, int Ci, int Co, int batch) {
-  __shared__ __align__(128) bf16 As[64][CV_LD];   // (co, v)
-  __shared__ __align__(128) bf16 Bs[16][CV_LD];   // (v, ci)
-  __shared__ __align__(128) float Cs[4][16][20];
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int tap = blockIdx.x / (Ci / 16);
-  const int c0 = (blockIdx.x - tap * (Ci / 16)) * 16;
-  const int n0 = blockIdx.y * 64;
+// Weight gradient on halo tiles: dW[co][tap][ci] += sum_v g[v][co] in[v + tap][ci].
+// A CTA owns MB output channels, 16 input channels and the 9 taps of one dz,
+// and walks a range of 16x4x2 voxel blocks (all frames of the batch laid end
+// to end).  Per block it stages the gradient tile g[128 voxels][MB] and the
+// input halo once; for each tap and each 16-voxel x run the MMA is
+// g_run^T (MB x 16 voxels) times the shifted halo window (16 voxels x 16 ci).
+// Warps split the MB/16 channel tiles and, when there are fewer than four,
+// the eight runs; the partial sums are combined in shared memory and added to
+// dw once per CTA (float atomics: the summation order over CTAs varies).
+template <int MB>
+__global__ void __launch_bounds__(CT_THREADS)
+conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ dw, int D,
+                         int H, int W, int Ci, int Co, int tiles_x, int tiles_y, int tiles_z, long long n_tiles,
+                         int tiles_per_cta) {
+  constexpr int MT = MB / 16;            // channel tiles
+  constexpr int RS = 4 / MT;             // warps sharing one channel tile (they split the runs)
+  __shared__ __align__(128) bf16 Gs[CT_MT * 16][MB];      // [voxel of the block][co]
+  __shared__ __align__(128) bf16 halo[CT_HALO * 16];
+  __shared__ __align__(128) float red[4][16][16];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = warp % MT, rsel = warp / MT;
+  const int n_ci = Ci / 16, n_co = Co / MB;
+  const int tg = blockIdx.y % 3;                 // dz = tg - 1
+  const int cc = (blockIdx.y / 3) % n_ci;
+  const int nc = blockIdx.y / (3 * n_ci);
+  const int c0 = cc * 16, n0 = nc * MB;
   const long long V = (long long)D * H * W;
-  const long long vtot = V * batch;
-  int dz, dy, dx;
-  tap_offset(tap, dz, dy, dx);
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
-  wmma::fill_fragment(acc, 0.0f);
-  const long long vbeg = (long long)blockIdx.z * WG_STEPS * 16;
-  for (int step = 0; step < WG_STEPS; ++step) {
-    const long long v0 = vbeg + (long long)step * 16;
-    if (v0 >= vtot) break;   // uniform
-    // A: g[v0 + k][n0 + m] -> As[m][k]; 16 voxels x 64 channels, 8 per thread
-    {
-      const int k = tid >> 3, mc = (tid & 7) * 8;
-      const long long v = v0 + k;
-      uint4 gv = make_uint4(0, 0, 0, 0);
-      if (v < vtot && n0 + mc < Co) gv = *reinterpret_cast<const uint4*>(g + v * Co + n0 + mc);
-      const bf16* e = reinterpret_cast<const bf16*>(&gv);
+  const long long t_begin = (long long)blockIdx.x * tiles_per_cta;
+  const long long t_end = t_begin + tiles_per_cta < n_tiles ? t_begin + tiles_per_cta : n_tiles;
+  (void)n_co;
+
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[9];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) As[mc + i][k] = e[i];
+  for (int t = 0; t < 9; ++t) wmma::fill_fragment(acc[t], 0.0f);
+
+  for (long long tile = t_begin; tile < t_end; ++tile) {
+    long long r = tile;
+    const int bx = (int)(r % tiles_x);
+    r /= tiles_x;
+    const int by = (int)(r % tiles_y);
+    r /= tiles_y;
+    const int bz = (int)(r % tiles_z);
+    const int b = (int)(r / tiles_z);
+    const int x0 = bx * CT_X, y0 = by * CT_Y, z0 = bz * CT_Z;
+    const bf16* inb = in + (long long)b * V * Ci;
+    const bf16* gb = g + (long long)b * V * Co;
+    __syncthreads();
+    for (int t = tid; t < CT_MT * 16 * (MB / 8); t += CT_THREADS) {
+      const int v = t / (MB / 8), q = t - v * (MB / 8);
+      const int m = v >> 4, xr = v & 15;
+      const int gx = x0 + xr, gy = y0 + m % CT_Y, gz = z0 + m / CT_Y;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (gx < W && gy < H && gz < D)
+        val = *reinterpret_cast<const uint4*>(gb + (((long long)gz * H + gy) * W + gx) * Co + n0 + q * 8);
+      *reinterpret_cast<uint4*>(&Gs[v][q * 8]) = val;
     }
-    // B: in[v0 + k shifted by tap][c0 + n] -> Bs[k][n]; 16 voxels x 16 channels
-    if (tid < 32) {
-      const int k = tid >> 1, h = tid & 1;
-      const long long v = v0 + k;
-      uint4 iv = make_uint4(0, 0, 0, 0);
-      if (v < vtot) {
-        const long long bb = v / V;
-        const long long vv = v - bb * V;
-        const int z = (int)(vv / ((long long)H * W));
-        const int rem = (int)(vv - (long long)z * H * W);
-        const int y = rem / W, x = rem - (rem / W) * W;
-        const int zz = z + dz, yy = y + dy, xx = x + dx;
-        if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
-          iv = *reinterpret_cast<const uint4*>(in + ((bb * V) + ((long long)zz * H + yy) * W + xx) * Ci + c0 + h * 8);
+    for (int t = tid; t < CT_HALO * 2; t += CT_THREADS) {
+      const int v = t >> 1, h = t & 1;
+      const int hx = v % CT_HX, hy = (v / CT_HX) % CT_HY, hz = v / (CT_HX * CT_HY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
+        val = *reinterpret_cast<const uint4*>(inb + (((long long)gz * H + gy) * W + gx) * Ci + c0 + h * 8);
+      *reinterpret_cast<uint4*>(halo + v * 16 + h * 8) = val;
+    }
+    __syncthreads();
+    for (int run = rsel; run < CT_MT; run += RS) {
+      const int ty = run % CT_Y, tz = run / CT_Y;
+      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> a;
+      wmma::load_matrix_sync(a, &Gs[run * 16][mt * 16], MB);
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int dy = t / 3 - 1, dx = t % 3 - 1, dz = tg - 1;
+        const bf16* bp = halo + (((tz + dz + 1) * CT_HY + (ty + dy + 1)) * CT_HX + (dx + 1)) * 16;
+        wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bfr;
+        wmma::load_matrix_sync(bfr, bp, 16);
+        wmma::mma_sync(acc[t], a, bfr, acc[t]);
       }
-      *reinterpret_cast<uint4*>(&Bs[k][h * 8]) = iv;
     }
-    __syncthreads();
-    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
-    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bfr;
-    wmma::load_matrix_sync(a, &As[warp * 16][0], CV_LD);
-    wmma::load_matrix_sync(bfr, &Bs[0][0], CV_LD);
-    wmma::mma_sync(acc, a, bfr, acc);
-    __syncthreads();
   }
-  wmma::store_matrix_sync(&Cs[warp][0][0], acc, 20, wmma::mem_row_major);
-  __syncwarp();
-  for (int e = lane; e < 256; e += 32) {
-    const int r = e >> 4, c = e & 15;
-    const int co = n0 + warp * 16 + r;
-    if (co < Co) atomicAdd(dw + ((long long)co * 27 + tap) * Ci + c0 + c, Cs[warp][r][c]);
+  // combine the warps that shared a channel tile, then one atomic add per entry
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    __syncthreads();
+    wmma::store_matrix_sync(&red[warp][0][0], acc[t], 16, wmma::mem_row_major);
+    __syncthreads();
+    const int tap = tg * 9 + t;
+    for (int e = tid; e < MT * 256; e += CT_THREADS) {
+      const int m = e >> 8, i = (e >> 4) & 15, j = e & 15;
+      float v = 0.0f;
+#pragma unroll
+      for (int s2 = 0; s2 < RS; ++s2) v += red[m + s2 * MT][i][j];
+      atomicAdd(dw + ((long long)(n0 + m * 16 + i) * 27 + tap) * Ci + c0 + j, v);
+    }
   }
 }
 
@@ -422,11 +446,25 @@ extern "C" lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, f
   if (!in || !g || !dw || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 || Ci % 16 || Co % 16)
     return set_error(LT_EINVAL, "conv3d_wgrad: bad arguments (channels must be multiples of 16)");
   const long long vtot = (long long)D * H * W * batch;
-  const long long chunks = (vtot + 16LL * WG_STEPS - 1) / (16LL * WG_STEPS);
   cudaStream_t st = (cudaStream_t)stream;
-  dim3 grid(27 * (Ci / 16), (Co + 63) / 64, (unsigned)chunks);
-  conv3d_wgrad_kernel<<<grid, CV_THREADS, 0, st>>>(reinterpret_cast<const bf16*>(in), reinterpret_cast<const bf16*>(g),
-                                                    dw, D, H, W, Ci, Co, batch);
+  const int mb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
+  const int tx = (W + CT_X - 1) / CT_X, ty = (H + CT_Y - 1) / CT_Y, tz = (D + CT_Z - 1) / CT_Z;
+  const long long n_tiles = (long long)tx * ty * tz * batch;
+  const long long groups = 3LL * (Ci / 16) * (Co / mb);
+  if (groups > 65535) return set_error(LT_EINVAL, "conv3d_wgrad: too many channel groups");
+  // about four waves of CTAs over the 148 SMs, each walking a run of voxel blocks
+  const long long want = std::max<long long>(1, (148LL * 4 + groups - 1) / groups);
+  const int per = (int)std::max<long long>(1, (n_tiles + want - 1) / want);
+  const unsigned gx = (unsigned)((n_tiles + per - 1) / per);
+  dim3 grid(gx, (unsigned)groups);
+  const bf16* i_ = reinterpret_cast<const bf16*>(in);
+  const bf16* g_ = reinterpret_cast<const bf16*>(g);
+  if (mb == 64)
+    conv3d_wgrad_tile_kernel<64><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+  else if (mb == 32)
+    conv3d_wgrad_tile_kernel<32><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+  else
+    conv3d_wgrad_tile_kernel<16><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
   if (db) {
     dim3 gb((Co + 31) / 32, (unsigned)std::min<long long>(1024, (vtot + 7) / 8));
     bias_grad_kernel<<<gb, 256, 0, st>>>(reinterpret_cast<const bf16*>(g), db, vtot, Co);
