@@ -381,16 +381,31 @@ class _Aligned:
     def __init__(self, cam):
         self.__dict__.update(cam.__dict__)
         self.yaw = 0.0
+        self.pitch = 0.0
+        self.roll = 0.0
 
     @property
     def m(self):
         return self.det_ns * self.det_nt
 
 
+def _general(cam):
+    """The camera has a pitch or roll: the three-shear rotation applies."""
+    return getattr(cam, "pitch", 0.0) != 0.0 or getattr(cam, "roll", 0.0) != 0.0
+
+
+def _rotated(cam):
+    return cam.yaw != 0.0 or _general(cam)
+
+
 def rotated_volume(vol, cam, x):
     from . import rotation
-    Xr, sr = rotation.rotate(np.asarray(x, dtype=np.float64).reshape(vol.shape),
-                             (vol.dx, vol.dy, vol.dz), cam.yaw)
+    X = np.asarray(x, dtype=np.float64).reshape(vol.shape)
+    sizes = (vol.dx, vol.dy, vol.dz)
+    if _general(cam):
+        Xr, sr = rotation.rotate_general(X, sizes, rotation.camera_rotation(cam.yaw, cam.pitch, cam.roll))
+    else:
+        Xr, sr = rotation.rotate(X, sizes, cam.yaw)
     g = Grid(Xr.shape[2], Xr.shape[1], Xr.shape[0], sr[0], sr[1], sr[2])
     return g, Xr
 
@@ -409,19 +424,27 @@ def _aligned_adjoint(vol, cam, y, cells=None):
 
 def forward(vol, cam, x, cells=None):
     """A x, or sum_{k in cells} A_k x (angular-plane subset, Sec. V)."""
-    if cam.yaw != 0.0:
+    if _rotated(cam):
         g, Xr = rotated_volume(vol, cam, x)
         return _aligned_forward(g, _Aligned(cam), Xr, cells)
     return _aligned_forward(vol, cam, x, cells)
 
 
 def adjoint(vol, cam, y, cells=None):
-    if cam.yaw != 0.0:
+    if _rotated(cam):
         from . import rotation
-        shape_r, sr, _ = rotation.rotated_grid(vol.shape, (vol.dx, vol.dy, vol.dz), cam.yaw)
+        sizes = (vol.dx, vol.dy, vol.dz)
+        if _general(cam):
+            T = rotation.camera_rotation(cam.yaw, cam.pitch, cam.roll)
+            Xr, sr = rotation.rotate_general(np.zeros(vol.shape), sizes, T)   # grid only
+            shape_r = Xr.shape
+        else:
+            shape_r, sr, _ = rotation.rotated_grid(vol.shape, sizes, cam.yaw)
         g = Grid(shape_r[2], shape_r[1], shape_r[0], sr[0], sr[1], sr[2])
         Gr = _aligned_adjoint(g, _Aligned(cam), y, cells)
-        return rotation.rotate_adjoint(Gr, vol.shape, (vol.dx, vol.dy, vol.dz), cam.yaw)
+        if _general(cam):
+            return rotation.rotate_general_adjoint(Gr, vol.shape, sizes, T)
+        return rotation.rotate_adjoint(Gr, vol.shape, sizes, cam.yaw)
     return _aligned_adjoint(vol, cam, y, cells)
 
 

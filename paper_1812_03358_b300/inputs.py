@@ -45,14 +45,18 @@ class Volume:
 @dataclass
 class Camera:
     """One camera (Sec. II-F).  The optical axis passes through the volume
-    centre; the main lens sits ``d_obj`` in front of it.  ``yaw`` rotates the
-    camera about the volume's y axis (Sec. III-A)."""
+    centre; the main lens sits ``d_obj`` in front of it.  The camera is turned
+    by the angles ``yaw`` (about the volume's y axis), ``pitch`` (about x) and
+    ``roll`` (about z, the optical axis), radians: Theta = R_y(yaw) R_x(pitch)
+    R_z(roll), p = Theta p^r (Sec. III-A)."""
     kind: int = CAM_SINGLE
     basis: int = BASIS_PILLBOX
     f_main: float = 30.0
     r_main: float = 5.0
     d_obj: float = 722.3
     yaw: float = 0.0
+    pitch: float = 0.0      # rotation angle about x (not a pixel pitch)
+    roll: float = 0.0
     det_ns: int = 64
     det_nt: int = 64
     det_ps: float = 0.08
