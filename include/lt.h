@@ -63,14 +63,18 @@ typedef struct {
 /* One camera (Sec. II-F).  The optical axis passes through the volume centre;
  * the main lens is d_obj in front of it.  The angular plane is the main lens,
  * divided into ks x kt cells tiling [-r_main, r_main]^2 (cells whose centre is
- * inside the aperture disc are kept).  yaw rotates the camera about the
- * volume's y axis (Sec. III-A). */
+ * inside the aperture disc are kept).  The camera is turned by yaw (about
+ * the volume's y axis), pitch (about x) and roll (about z, the optical axis):
+ * Theta = R_y(yaw) R_x(pitch) R_z(roll), p = Theta p^r (Sec. III-A).  A yaw
+ * alone uses quarter turns and two shears; with pitch or roll the rotation
+ * is split into a signed permutation and D S_z S_x S_y (three shears). */
 typedef struct {
   int32_t kind;            /* LT_CAM_SINGLE or LT_CAM_PLENOPTIC                  */
   int32_t basis;           /* LT_BASIS_PILLBOX or LT_BASIS_DIRAC                 */
   double f_main, r_main;   /* main-lens focal length and aperture radius         */
   double d_obj;            /* main lens -> volume centre                         */
   double yaw;              /* radians                                            */
+  double pitch, roll;      /* radians (rotation angles, not pixel pitches)       */
   int32_t det_ns, det_nt;  /* detector pixels                                    */
   double det_ps, det_pt;   /* detector pitch                                     */
   double d_lens_det;       /* single lens: main lens -> detector (D)             */

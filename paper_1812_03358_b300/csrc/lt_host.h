@@ -28,6 +28,11 @@ struct CameraPlan {
   // the grid this camera sees: the object volume, or its rotated view
   bool rotated = false;
   RotParam rot{};
+  bool general = false;            // pitch or roll: permutation + three shears (GenRot)
+  GenRot grot{};
+  float* d_gb[3] = {nullptr, nullptr, nullptr};   // scratch: permuted, after z, after x
+  float* d_gtab[3] = {nullptr, nullptr, nullptr};
+  int32_t* d_gjo[3] = {nullptr, nullptr, nullptr};
   lt_volume_desc vol_c{};
   int64_t nvox_c = 0;
   float* d_rz = nullptr;           // scratch [F][nzr][ny][nxp] (rotated cameras)

@@ -96,7 +96,26 @@ struct RotParam {
   int32_t* jx;
 };
 
-// Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.
+// General orientation (yaw with pitch and/or roll, Sec. III-A): a signed
+// permutation of the grid, then up to three least-squares shear passes
+// (z, x, y), each along one axis with a shift linear in the other two.
+struct ShearPass {
+  int32_t axis;            // 0 = x, 1 = y, 2 = z (the sheared axis)
+  int32_t n0, n1, n2;      // input dims (x, y, z); the output pads `axis` by 2 pad
+  int32_t pad, nw;         // padding, taps per output
+  int32_t nu, nv;          // column dims: the other two axes in increasing order
+  const float* tab;        // [nv][nu][nw] entries, tab[(v nu + u) nw + q] = E(i, i - pad + J + q)
+  const int32_t* jo;       // [nv][nu] window offsets J
+  int32_t active;          // 0: the identity (both coefficients zero), skipped
+};
+struct GenRot {
+  int32_t nx, ny, nz;      // source volume
+  int32_t km[3], sg[3];    // source axis m reads permuted axis km[m], flipped when sg[m] < 0
+  int32_t np[3];           // permuted dims (x, y, z)
+  ShearPass pass[3];       // z, x, y
+};
+
+// Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.// Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.
 // The planner computes, per (cell, tile column) and (cell, tile row), the
 // slice interval [x, y) outside of which the tile's footprints miss the volume.
 constexpr int kBeamTileS = 32;
@@ -172,6 +191,16 @@ cudaError_t launch_rotate_adjoint(const float* g_xr, float* rz, float* x, const 
 
 // Fills r.tz/jz/tx/jx (device arrays of nxp*nwz, nxp, nzr*wx, nzr entries).
 cudaError_t launch_shear_tables(const RotParam& r, cudaStream_t st);
+
+// General rotations: tables of one pass (built in FP64, stored FP32), and
+// the rotation / its transpose through scratch buffers b0 (permuted), b1
+// (after z), b2 (after x) of the plan (each large enough for its stage).
+cudaError_t launch_shear_pass_table(const ShearPass& ps, double s1, double s2, double du_dt, double dv_dt,
+                                    float* tab, int32_t* jo, cudaStream_t st);
+cudaError_t launch_grot_forward(const float* x, float* b0, float* b1, float* b2, float* xr, const GenRot& g,
+                                int frames, cudaStream_t st);
+cudaError_t launch_grot_adjoint(const float* g_xr, float* b0, float* b1, float* b2, float* x, const GenRot& g,
+                                int frames, int accumulate, cudaStream_t st);
 
 // x[i] += y[i], i < n.
 cudaError_t launch_add_inplace(float* x, const float* y, long long n, cudaStream_t st);

@@ -166,14 +166,17 @@ static lt_status validate_camera(const lt_volume_desc* v, const lt_camera_desc* 
     return set_error(LT_EINVAL, "camera %d: unknown basis %d", idx, c->basis);
   if (!pos(c->f_main) || !pos(c->r_main) || !pos(c->d_obj))
     return set_error(LT_EINVAL, "camera %d: f_main, r_main, d_obj must be positive", idx);
-  if (!std::isfinite(c->yaw)) return set_error(LT_EINVAL, "camera %d: yaw not finite", idx);
+  if (!std::isfinite(c->yaw) || !std::isfinite(c->pitch) || !std::isfinite(c->roll))
+    return set_error(LT_EINVAL, "camera %d: yaw/pitch/roll not finite", idx);
   if (c->det_ns <= 0 || c->det_nt <= 0 || !pos(c->det_ps) || !pos(c->det_pt))
     return set_error(LT_EINVAL, "camera %d: detector sizes/pitches must be positive", idx);
   if (c->ks <= 0 || c->kt <= 0 || c->ks > 256 || c->kt > 256)
     return set_error(LT_EINVAL, "camera %d: angular cells ks, kt must be in [1, 256]", idx);
   // the rotated view's z extent is at most the volume's diagonal in (x, z)
-  const double half = 0.5 * std::sqrt((double)v->nz * v->dz * v->nz * v->dz + (double)v->nx * v->dx * v->nx * v->dx);
-  const double dmin = c->d_obj - (c->yaw != 0.0 ? 2.0 * half : 0.5 * v->nz * v->dz);
+  const double half = 0.5 * std::sqrt((double)v->nz * v->dz * v->nz * v->dz + (double)v->nx * v->dx * v->nx * v->dx +
+                                      (c->pitch != 0.0 || c->roll != 0.0 ? (double)v->ny * v->dy * v->ny * v->dy : 0.0));
+  const bool turned = c->yaw != 0.0 || c->pitch != 0.0 || c->roll != 0.0;
+  const double dmin = c->d_obj - (turned ? 2.0 * half : 0.5 * v->nz * v->dz);
   if (!(dmin > 0.0))
     return set_error(LT_EINVAL, "camera %d: the volume reaches the main lens (nearest slice at %g)", idx, dmin);
   if (c->kind == LT_CAM_SINGLE) {
@@ -220,6 +223,11 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.rot.jz);
   cudaFree(c.rot.tx);
   cudaFree(c.rot.jx);
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(c.d_gb[k]);
+    cudaFree(c.d_gtab[k]);
+    cudaFree(c.d_gjo[k]);
+  }
   cudaFree(c.d_srange);
   cudaFree(c.d_trange);
   cudaFree(c.d_lens);
@@ -605,14 +613,145 @@ static lt_status plan_rotation(const lt_volume_desc& v, CameraPlan& c, int frame
   return LT_OK;
 }
 
+// General orientation (pitch and/or roll, Sec. III-A, eq. rot,decomp):
+// Theta = R_y(yaw) R_x(pitch) R_z(roll) = P Theta_r with P the proper signed
+// permutation of largest trace(P^T Theta) (first of a fixed enumeration on
+// ties; residue below 1e-12 zeroed), Theta_r = D S_z S_x S_y by elimination,
+// voxel sizes s / D on the permuted grid, then one shear pass per axis
+// (z: a x + b y, x: c y + d z, y: e x + f z), each padding its axis by
+// ceil((|s1| n_u du + |s2| n_v dv) / 2 / dt) + 1 (none for a zero pass).
+static lt_status plan_rotation_general(const lt_volume_desc& v, CameraPlan& c, int frames, int idx) {
+  const lt_camera_desc& d = c.desc;
+  auto mul = [](const double A[3][3], const double B[3][3], double C[3][3]) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k) acc += A[i][k] * B[k][j];
+        C[i][j] = acc;
+      }
+  };
+  const double cy = std::cos(d.yaw), sy = std::sin(d.yaw), cp = std::cos(d.pitch), sp = std::sin(d.pitch);
+  const double cr = std::cos(d.roll), sr = std::sin(d.roll);
+  const double Ry[3][3] = {{cy, 0, sy}, {0, 1, 0}, {-sy, 0, cy}};
+  const double Rx[3][3] = {{1, 0, 0}, {0, cp, -sp}, {0, sp, cp}};
+  const double Rz[3][3] = {{cr, -sr, 0}, {sr, cr, 0}, {0, 0, 1}};
+  double T1[3][3], T[3][3];
+  mul(Ry, Rx, T1);
+  mul(T1, Rz, T);
+  static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  double best = -1e300;
+  int bp = 0, bs[3] = {1, 1, 1};
+  for (int pi = 0; pi < 6; ++pi)
+    for (int sx = 1; sx >= -1; sx -= 2)
+      for (int syy = 1; syy >= -1; syy -= 2)
+        for (int sz = 1; sz >= -1; sz -= 2) {
+          const int sg[3] = {sx, syy, sz};
+          double P[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+          for (int m = 0; m < 3; ++m) P[m][perms[pi][m]] = sg[m];
+          const double det = P[0][0] * (P[1][1] * P[2][2] - P[1][2] * P[2][1]) -
+                             P[0][1] * (P[1][0] * P[2][2] - P[1][2] * P[2][0]) +
+                             P[0][2] * (P[1][0] * P[2][1] - P[1][1] * P[2][0]);
+          if (det < 0.5) continue;
+          double tr = 0.0;   // trace(P^T T) = sum_m P[m][k_m] T[m][k_m]
+          for (int m = 0; m < 3; ++m) tr += sg[m] * T[m][perms[pi][m]];
+          if (tr > best + 1e-12) {
+            best = tr;
+            bp = pi;
+            for (int m = 0; m < 3; ++m) bs[m] = sg[m];
+          }
+        }
+  // Tr = P^T T: row k of Tr = sum_m P[m][k] T[m][.] -> the m with k_m = k
+  double Tr[3][3];
+  for (int m = 0; m < 3; ++m)
+    for (int j = 0; j < 3; ++j) Tr[perms[bp][m]][j] = bs[m] * T[m][j];
+  for (auto& row : Tr)
+    for (double& e : row)
+      if (std::fabs(e) < 1e-12) e = 0.0;
+  const double Dy = Tr[1][1], e_ = Tr[1][0] / Dy, f_ = Tr[1][2] / Dy;
+  const double Dx = Tr[0][0] - Tr[0][1] * e_, c_ = Tr[0][1] / Dx, d_ = Tr[0][2] / Dx - c_ * f_;
+  const double u_ = Tr[2][0] - Tr[2][1] * e_, w_ = Tr[2][1] - u_ * c_;
+  const double Dz = Tr[2][2] - u_ * (d_ + c_ * f_) - w_ * f_;
+  const double a_ = u_ / Dz, b_ = w_ / Dz;
+  if (!(Dx > 0 && Dy > 0 && Dz > 0))
+    return set_error(LT_EINVAL, "camera %d: rotation factorisation failed", idx);
+  GenRot& g = c.grot;
+  g.nx = v.nx;
+  g.ny = v.ny;
+  g.nz = v.nz;
+  const int n_src[3] = {v.nx, v.ny, v.nz};
+  const double s_src[3] = {v.dx, v.dy, v.dz};
+  double s_new[3];
+  for (int m = 0; m < 3; ++m) {
+    g.km[m] = perms[bp][m];
+    g.sg[m] = bs[m];
+    g.np[g.km[m]] = n_src[m];
+    s_new[g.km[m]] = s_src[m];
+  }
+  const double Dg[3] = {Dx, Dy, Dz};
+  double srr[3];
+  for (int k = 0; k < 3; ++k) srr[k] = s_new[k] / Dg[k];
+  const double coef[3][2] = {{a_, b_}, {c_, d_}, {e_, f_}};
+  const int axes[3] = {2, 0, 1};   // z, x, y passes
+  int dims[3] = {g.np[0], g.np[1], g.np[2]};
+  size_t bytes[3];
+  for (int k = 0; k < 3; ++k) {
+    ShearPass& ps = g.pass[k];
+    ps.axis = axes[k];
+    ps.n0 = dims[0];
+    ps.n1 = dims[1];
+    ps.n2 = dims[2];
+    bytes[k] = (size_t)frames * dims[0] * dims[1] * dims[2] * sizeof(float);   // this pass's input
+    const int ua = ps.axis == 0 ? 1 : 0, va = ps.axis == 2 ? 1 : 2;
+    ps.nu = dims[ua];
+    ps.nv = dims[va];
+    const double s1 = coef[k][0], s2 = coef[k][1];
+    ps.active = !(s1 == 0.0 && s2 == 0.0);
+    const double dt = srr[ps.axis], du = srr[ua], dv = srr[va];
+    if (ps.active) {
+      ps.pad = (int)std::ceil((std::fabs(s1) * ps.nu * du + std::fabs(s2) * ps.nv * dv) / 2.0 / dt) + 1;
+      ps.nw = (int)std::floor(2.0 + std::fabs(s1) * du / dt + std::fabs(s2) * dv / dt) + 4;
+      if (ps.nw > 64) return set_error(LT_EUNSUPPORTED, "camera %d: shear window %d too wide", idx, ps.nw);
+      const size_t ncol = (size_t)ps.nu * ps.nv;
+      if (cudaMalloc((void**)&c.d_gtab[k], ncol * ps.nw * sizeof(float)) != cudaSuccess ||
+          cudaMalloc((void**)&c.d_gjo[k], ncol * sizeof(int32_t)) != cudaSuccess)
+        return set_error(LT_ENOMEM, "camera %d: shear tables", idx);
+      ps.tab = c.d_gtab[k];
+      ps.jo = c.d_gjo[k];
+      cudaError_t e = launch_shear_pass_table(ps, s1, s2, du / dt, dv / dt, c.d_gtab[k], c.d_gjo[k], 0);
+      if (e != cudaSuccess) return cuda_error(e, "shear tables");
+      dims[ps.axis] += 2 * ps.pad;
+    } else {
+      ps.pad = 0;
+      ps.nw = 0;
+    }
+  }
+  for (int k = 0; k < 3; ++k)
+    if (cudaMalloc((void**)&c.d_gb[k], bytes[k]) != cudaSuccess)
+      return set_error(LT_ENOMEM, "camera %d: rotated-view scratch", idx);
+  c.vol_c.nx = dims[0];
+  c.vol_c.ny = dims[1];
+  c.vol_c.nz = dims[2];
+  c.vol_c.dx = srr[0];
+  c.vol_c.dy = srr[1];
+  c.vol_c.dz = srr[2];
+  c.nvox_c = (int64_t)dims[0] * dims[1] * dims[2];
+  if (d.d_obj - 0.5 * dims[2] * srr[2] <= 0.0)
+    return set_error(LT_EINVAL, "camera %d: the rotated volume reaches the main lens", idx);
+  if (cudaMalloc((void**)&c.d_xr, (size_t)frames * c.nvox_c * sizeof(float)) != cudaSuccess)
+    return set_error(LT_ENOMEM, "camera %d: rotated-view scratch", idx);
+  cudaError_t e = cudaStreamSynchronize(0);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "shear tables");
+}
+
 static lt_status plan_camera(const lt_volume_desc& v0, const lt_camera_desc& src, int frames,
                              CameraPlan& c, int idx) {
   c.desc = src;
   c.vol_c = v0;
   c.nvox_c = (int64_t)v0.nx * v0.ny * v0.nz;
-  c.rotated = src.yaw != 0.0;
+  c.general = src.pitch != 0.0 || src.roll != 0.0;
+  c.rotated = src.yaw != 0.0 || c.general;
   if (c.rotated) {
-    lt_status s = plan_rotation(v0, c, frames, idx);
+    lt_status s = c.general ? plan_rotation_general(v0, c, frames, idx) : plan_rotation(v0, c, frames, idx);
     if (s != LT_OK) return s;
   }
   const lt_volume_desc& v = c.vol_c;
@@ -734,9 +873,10 @@ extern "C" lt_status lt_rotate_volume(lt_plan* plan, int32_t cam, const float* x
     return set_error(LT_EINVAL, "bad plan/camera/pointer argument");
   CameraPlan& c = plan->cams[cam];
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = c.rotated ? launch_rotate_forward(x, c.d_rz, xc, c.rot, plan->frames, st)
-                            : cudaMemcpyAsync(xc, x, (size_t)plan->frames * plan->nvox * sizeof(float),
-                                              cudaMemcpyDeviceToDevice, st);
+  cudaError_t e = !c.rotated ? cudaMemcpyAsync(xc, x, (size_t)plan->frames * plan->nvox * sizeof(float),
+                                               cudaMemcpyDeviceToDevice, st)
+                  : c.general ? launch_grot_forward(x, c.d_gb[0], c.d_gb[1], c.d_gb[2], xc, c.grot, plan->frames, st)
+                              : launch_rotate_forward(x, c.d_rz, xc, c.rot, plan->frames, st);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "rotate volume");
 }
 
@@ -748,7 +888,9 @@ extern "C" lt_status lt_rotate_volume_adjoint(lt_plan* plan, int32_t cam, const 
   CameraPlan& c = plan->cams[cam];
   cudaStream_t st = (cudaStream_t)stream;
   if (c.rotated) {
-    cudaError_t e = launch_rotate_adjoint(xc, c.d_rz, x, c.rot, plan->frames, accumulate, st);
+    cudaError_t e = c.general ? launch_grot_adjoint(xc, c.d_gb[0], c.d_gb[1], c.d_gb[2], x, c.grot, plan->frames,
+                                                    accumulate, st)
+                              : launch_rotate_adjoint(xc, c.d_rz, x, c.rot, plan->frames, accumulate, st);
     return e == cudaSuccess ? LT_OK : cuda_error(e, "rotate volume adjoint");
   }
   const long long n = (long long)plan->frames * plan->nvox;
@@ -849,13 +991,24 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
 
 namespace lt {
 
+static cudaError_t rotate_fwd(const CameraPlan& c, const float* x, float* xr, int frames, cudaStream_t st) {
+  return c.general ? launch_grot_forward(x, c.d_gb[0], c.d_gb[1], c.d_gb[2], xr, c.grot, frames, st)
+                   : launch_rotate_forward(x, c.d_rz, xr, c.rot, frames, st);
+}
+
+static cudaError_t rotate_adj(const CameraPlan& c, const float* g_xr, float* x, int frames, int accumulate,
+                              cudaStream_t st) {
+  return c.general ? launch_grot_adjoint(g_xr, c.d_gb[0], c.d_gb[1], c.d_gb[2], x, c.grot, frames, accumulate, st)
+                   : launch_rotate_adjoint(g_xr, c.d_rz, x, c.rot, frames, accumulate, st);
+}
+
 // The grid this camera sees: x itself, or its rotated view (into c.d_xr).
 static lt_status to_camera_grid(lt_plan* p, CameraPlan& c, const float* x, const float** xc, cudaStream_t st) {
   if (!c.rotated) {
     *xc = x;
     return LT_OK;
   }
-  cudaError_t e = launch_rotate_forward(x, c.d_rz, c.d_xr, c.rot, p->frames, st);
+  cudaError_t e = rotate_fwd(c, x, c.d_xr, p->frames, st);
   if (e != cudaSuccess) return cuda_error(e, "rotated view");
   *xc = c.d_xr;
   return LT_OK;
@@ -914,7 +1067,7 @@ static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* 
   cudaError_t e = launch_beam_adjoint_batched(b, dst, c.nvox_c, c.rotated ? 0 : accumulate, st);
   if (e != cudaSuccess) return cuda_error(e, "beam adjoint");
   if (c.rotated) {
-    e = launch_rotate_adjoint(c.d_xr, c.d_rz, x, c.rot, p->frames, accumulate, st);
+    e = rotate_adj(c, c.d_xr, x, p->frames, accumulate, st);
     if (e != cudaSuccess) return cuda_error(e, "rotated view adjoint");
   }
   return LT_OK;

@@ -239,6 +239,165 @@ void launch_z_adjoint(dim3 g, dim3 b, cudaStream_t st, const float* grz, float* 
   else launch_z_adjoint_nw<16>(g, b, st, grz, x, r, frames, acc);
 }
 
+// ---- general orientations -------------------------------------------------
+
+__device__ double d_hat(double t) { return fmax(0.0, 1.0 - fabs(t)); }
+
+// E[hat(c + U1 + U2)], U1, U2 uniform of widths al, be (>= 0): the density of
+// U1 + U2 is a trapezoid on [-h, h] with plateau [-g, g]; the integrand is
+// piecewise quadratic between the merged kinks, integrated by two-point
+// Gauss-Legendre per piece (exact for cubics).
+__device__ double hat_avg2_d(double c, double al, double be) {
+  al = fabs(al);
+  be = fabs(be);
+  if (al < be) {
+    const double t = al;
+    al = be;
+    be = t;
+  }
+  if (al == 0.0) return d_hat(c);
+  const double h = 0.5 * (al + be), g = 0.5 * (al - be);
+  double k[7] = {-h, -g, g, h, -c - 1.0, -c, -c + 1.0};
+  for (int i = 1; i < 7; ++i)   // insertion sort
+    for (int j = i; j > 0 && k[j - 1] > k[j]; --j) {
+      const double t = k[j];
+      k[j] = k[j - 1];
+      k[j - 1] = t;
+    }
+  const double r3 = 0.5773502691896257645;   // 1 / sqrt(3)
+  double total = 0.0;
+  for (int i = 0; i < 6; ++i) {
+    const double lo = fmax(k[i], -h), hi = fmin(k[i + 1], h);
+    if (!(hi > lo)) continue;
+    const double m = 0.5 * (lo + hi), rr = 0.5 * (hi - lo) * r3;
+    double f = 0.0;
+    for (int e = -1; e <= 1; e += 2) {
+      const double sv = m + e * rr, a = fabs(sv);
+      const double pdf = a >= h ? 0.0 : ((a <= g || be == 0.0) ? 1.0 / al : (h - a) / (al * be));
+      f += d_hat(c + sv) * pdf;
+    }
+    total += 0.5 * (hi - lo) * f;
+  }
+  return total;
+}
+
+// Table of one pass: column (u, v) -> window offset J and nw entries.
+__global__ void shear_pass_table_kernel(ShearPass ps, double s1, double s2, double du_dt, double dv_dt,
+                                        float* __restrict__ tab, int32_t* __restrict__ jo) {
+  const int n = ps.nu * ps.nv;
+  const double al = fabs(s1) * du_dt, be = fabs(s2) * dv_dt;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int u = t % ps.nu, v = t / ps.nu;
+    const double sh = s1 * du_dt * (u - 0.5 * (ps.nu - 1)) + s2 * dv_dt * (v - 0.5 * (ps.nv - 1));
+    const int J = (int)floor(sh - 1.0 - 0.5 * (al + be)) - 1;
+    jo[t] = J;
+    for (int q = 0; q < ps.nw; ++q) tab[(long long)t * ps.nw + q] = (float)hat_avg2_d(-J - q + sh, al, be);
+  }
+}
+
+__device__ __forceinline__ void pass_dims(const ShearPass& ps, int out, int& m0, int& m1, int& m2) {
+  m0 = ps.n0 + (ps.axis == 0 && out ? 2 * ps.pad : 0);
+  m1 = ps.n1 + (ps.axis == 1 && out ? 2 * ps.pad : 0);
+  m2 = ps.n2 + (ps.axis == 2 && out ? 2 * ps.pad : 0);
+}
+
+// Forward pass (gather per output): out[..i..] = sum_q tab[col][q] in[..i - pad + J + q..].
+__global__ void __launch_bounds__(256) shear_pass_forward(const float* __restrict__ in, float* __restrict__ out,
+                                                          ShearPass ps, int frames) {
+  int o0n, o1n, o2n;
+  pass_dims(ps, 1, o0n, o1n, o2n);
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  if (x >= o0n || y >= o1n || z >= o2n) return;
+  const int c[3] = {x, y, z};
+  const int i = c[ps.axis];
+  const int u = ps.axis == 0 ? y : x;
+  const int v = ps.axis == 2 ? y : z;
+  const int col = v * ps.nu + u;
+  const float* tb = ps.tab + (long long)col * ps.nw;
+  const int jb = i - ps.pad + __ldg(ps.jo + col);
+  const int n_ax = ps.axis == 0 ? ps.n0 : ps.axis == 1 ? ps.n1 : ps.n2;
+  const long long stride = ps.axis == 0 ? 1 : ps.axis == 1 ? (long long)ps.n0 : (long long)ps.n0 * ps.n1;
+  const long long base = ((long long)(ps.axis == 2 ? 0 : z) * ps.n1 + (ps.axis == 1 ? 0 : y)) * ps.n0 +
+                         (ps.axis == 0 ? 0 : x);
+  const long long in_fs = (long long)ps.n0 * ps.n1 * ps.n2, out_fs = (long long)o0n * o1n * o2n;
+  const long long o = ((long long)z * o1n + y) * o0n + x;
+  for (int f = 0; f < frames; ++f) {
+    const float* src = in + f * in_fs + base;
+    float acc = 0.0f;
+    for (int q = 0; q < ps.nw; ++q) {
+      const int j = jb + q;
+      if (j >= 0 && j < n_ax) acc = fmaf(__ldg(tb + q), __ldg(src + j * stride), acc);
+    }
+    out[f * out_fs + o] = acc;
+  }
+}
+
+// Transposed pass (gather per source): g_in[..j..] = sum_q tab[col][q] g_out[..j + pad - J - q..].
+__global__ void __launch_bounds__(256) shear_pass_adjoint(const float* __restrict__ gout, float* __restrict__ gin,
+                                                          ShearPass ps, int frames) {
+  int o0n, o1n, o2n;
+  pass_dims(ps, 1, o0n, o1n, o2n);
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  if (x >= ps.n0 || y >= ps.n1 || z >= ps.n2) return;
+  const int c[3] = {x, y, z};
+  const int j = c[ps.axis];
+  const int u = ps.axis == 0 ? y : x;
+  const int v = ps.axis == 2 ? y : z;
+  const int col = v * ps.nu + u;
+  const float* tb = ps.tab + (long long)col * ps.nw;
+  const int ib = j + ps.pad - __ldg(ps.jo + col);
+  const int n_ax = ps.axis == 0 ? o0n : ps.axis == 1 ? o1n : o2n;
+  const long long stride = ps.axis == 0 ? 1 : ps.axis == 1 ? (long long)o0n : (long long)o0n * o1n;
+  const long long base = ((long long)(ps.axis == 2 ? 0 : z) * o1n + (ps.axis == 1 ? 0 : y)) * o0n +
+                         (ps.axis == 0 ? 0 : x);
+  const long long in_fs = (long long)ps.n0 * ps.n1 * ps.n2, out_fs = (long long)o0n * o1n * o2n;
+  const long long o = ((long long)z * ps.n1 + y) * ps.n0 + x;
+  for (int f = 0; f < frames; ++f) {
+    const float* src = gout + f * out_fs + base;
+    float acc = 0.0f;
+    for (int q = ps.nw - 1; q >= 0; --q) {
+      const int i = ib - q;
+      if (i >= 0 && i < n_ax) acc = fmaf(__ldg(tb + q), __ldg(src + i * stride), acc);
+    }
+    gin[f * in_fs + o] = acc;
+  }
+}
+
+// Signed permutation: permuted voxel p -> source voxel s, s_m = p[km[m]] or
+// n_m - 1 - p[km[m]].  Forward gathers from x; the transpose gathers back.
+__global__ void __launch_bounds__(256) grot_permute(const float* __restrict__ x, float* __restrict__ xp, GenRot g,
+                                                    int frames) {
+  const int p0 = blockIdx.x * 32 + threadIdx.x, p1 = blockIdx.y * 8 + threadIdx.y, p2 = blockIdx.z;
+  if (p0 >= g.np[0] || p1 >= g.np[1] || p2 >= g.np[2]) return;
+  const int p[3] = {p0, p1, p2};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  int sidx[3];
+  for (int m = 0; m < 3; ++m) sidx[m] = g.sg[m] > 0 ? p[g.km[m]] : n[m] - 1 - p[g.km[m]];
+  const long long fs = (long long)g.nx * g.ny * g.nz;
+  const long long src = ((long long)sidx[2] * g.ny + sidx[1]) * g.nx + sidx[0];
+  const long long dst = ((long long)p2 * g.np[1] + p1) * g.np[0] + p0;
+  for (int f = 0; f < frames; ++f) xp[f * fs + dst] = __ldg(x + f * fs + src);
+}
+
+__global__ void __launch_bounds__(256) grot_permute_adjoint(const float* __restrict__ xp, float* __restrict__ x,
+                                                            GenRot g, int frames, int accumulate) {
+  const int s0 = blockIdx.x * 32 + threadIdx.x, s1 = blockIdx.y * 8 + threadIdx.y, s2 = blockIdx.z;
+  if (s0 >= g.nx || s1 >= g.ny || s2 >= g.nz) return;
+  const int sv[3] = {s0, s1, s2};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  int p[3];
+  for (int m = 0; m < 3; ++m) p[g.km[m]] = g.sg[m] > 0 ? sv[m] : n[m] - 1 - sv[m];
+  const long long fs = (long long)g.nx * g.ny * g.nz;
+  const long long dst = ((long long)s2 * g.ny + s1) * g.nx + s0;
+  const long long src = ((long long)p[2] * g.np[1] + p[1]) * g.np[0] + p[0];
+  for (int f = 0; f < frames; ++f) {
+    const float v = __ldg(xp + f * fs + src);
+    x[f * fs + dst] = accumulate ? x[f * fs + dst] + v : v;
+  }
+}
+
+inline dim3 grid3(int n0, int n1, int n2) { return dim3((n0 + 31) / 32, (n1 + 7) / 8, n2); }
+
 }  // namespace
 
 cudaError_t launch_add_inplace(float* x, const float* y, long long n, cudaStream_t st) {
@@ -267,6 +426,55 @@ cudaError_t launch_rotate_adjoint(const float* g_xr, float* rz, float* x, const 
   shear_x_adjoint<<<dim3((r.nxp + 31) / 32, (r.ny + 7) / 8, r.nzr), blk, 0, st>>>(g_xr, rz, r, frames);
   const dim3 gz((r.nxp + 31) / 32, (r.ny + 7) / 8, (r.nzp + kShearZChunk - 1) / kShearZChunk);
   launch_z_adjoint(gz, blk, st, rz, x, r, frames, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shear_pass_table(const ShearPass& ps, double s1, double s2, double du_dt, double dv_dt,
+                                    float* tab, int32_t* jo, cudaStream_t st) {
+  const int n = ps.nu * ps.nv;
+  shear_pass_table_kernel<<<(n + 127) / 128, 128, 0, st>>>(ps, s1, s2, du_dt, dv_dt, tab, jo);
+  return cudaGetLastError();
+}
+
+static void pass_out_dims(const ShearPass& ps, int& m0, int& m1, int& m2) {
+  m0 = ps.n0 + (ps.axis == 0 ? 2 * ps.pad : 0);
+  m1 = ps.n1 + (ps.axis == 1 ? 2 * ps.pad : 0);
+  m2 = ps.n2 + (ps.axis == 2 ? 2 * ps.pad : 0);
+}
+
+cudaError_t launch_grot_forward(const float* x, float* b0, float* b1, float* b2, float* xr, const GenRot& g,
+                                int frames, cudaStream_t st) {
+  const dim3 blk(32, 8);
+  int last = -1;
+  for (int k = 0; k < 3; ++k)
+    if (g.pass[k].active) last = k;
+  float* scratch[3] = {b1, b2, nullptr};
+  float* cur = last < 0 ? xr : b0;
+  grot_permute<<<grid3(g.np[0], g.np[1], g.np[2]), blk, 0, st>>>(x, cur, g, frames);
+  for (int k = 0; k < 3; ++k) {
+    const ShearPass& ps = g.pass[k];
+    if (!ps.active) continue;
+    float* out = k == last ? xr : scratch[k];
+    int m0, m1, m2;
+    pass_out_dims(ps, m0, m1, m2);
+    shear_pass_forward<<<grid3(m0, m1, m2), blk, 0, st>>>(cur, out, ps, frames);
+    cur = out;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grot_adjoint(const float* g_xr, float* b0, float* b1, float* b2, float* x, const GenRot& g,
+                                int frames, int accumulate, cudaStream_t st) {
+  const dim3 blk(32, 8);
+  float* in_buf[3] = {b0, b1, b2};   // input of pass k (its transpose writes there)
+  const float* cur = g_xr;
+  for (int k = 2; k >= 0; --k) {
+    const ShearPass& ps = g.pass[k];
+    if (!ps.active) continue;
+    shear_pass_adjoint<<<grid3(ps.n0, ps.n1, ps.n2), blk, 0, st>>>(cur, in_buf[k], ps, frames);
+    cur = in_buf[k];
+  }
+  grot_permute_adjoint<<<grid3(g.nx, g.ny, g.nz), blk, 0, st>>>(cur, x, g, frames, accumulate);
   return cudaGetLastError();
 }
 

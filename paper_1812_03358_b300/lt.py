@@ -28,6 +28,7 @@ class lt_volume_desc(ctypes.Structure):
 class lt_camera_desc(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("basis", c_int32),
                 ("f_main", c_double), ("r_main", c_double), ("d_obj", c_double), ("yaw", c_double),
+                ("pitch", c_double), ("roll", c_double),
                 ("det_ns", c_int32), ("det_nt", c_int32), ("det_ps", c_double), ("det_pt", c_double),
                 ("d_lens_det", c_double), ("ks", c_int32), ("kt", c_int32),
                 ("d_lens_mla", c_double), ("d_mla_det", c_double),

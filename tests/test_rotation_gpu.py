@@ -122,3 +122,48 @@ def test_rotate_volume_and_adjoint_match_oracle(yaw):
     # adjoint identity <R x, g> = <x, R^T g>
     lhs, rhs = float(np.vdot(xc, g)), float(np.vdot(x, xa))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+GENERAL = [(0.0, 0.35, 0.0), (0.0, 0.0, -0.5), (0.4, -0.3, 0.2), (2.5, 0.6, -1.1), (0.0, math.pi / 2, 0.0),
+           (1.0, 0.0, math.pi / 2)]
+
+
+@pytest.mark.parametrize("angles", GENERAL)
+def test_general_rotation_matches_oracle(angles):
+    """Pitch and roll (signed permutation + three shear passes) against the
+    oracle's rotate_general and its transpose, elementwise, ragged grid."""
+    from oracle import rotation as OR_
+    vol = I.Volume(9, 7, 8, 4.0, 4.5, 5.0)
+    cam = I.table_single_lens(28, 0.3, yaw=angles[0])
+    cam.pitch, cam.roll = angles[1], angles[2]
+    plan = lt.Plan(vol, [cam])
+    x = I.gaussian_blobs(vol, seed=1013).reshape(vol.shape) + 0.1 * I.uniform_random(vol.shape, seed=35)
+    T = OR_.camera_rotation(*angles)
+    ref, (sx, sy, sz) = OR_.rotate_general(x, (vol.dx, vol.dy, vol.dz), T)
+    shp, sizes = plan.camera_grid(0)
+    assert tuple(shp) == ref.shape
+    assert np.allclose(sizes, (sz, sy, sx), rtol=1e-12)
+    xc = host(plan.rotate(0, dev(x).reshape(1, -1))).reshape(shp)
+    assert np.abs(xc - ref).max() <= 1e-5 * np.abs(ref).max(), np.abs(xc - ref).max()
+    g = I.uniform_random(int(np.prod(shp)), seed=36).reshape(shp)
+    gref = OR_.rotate_general_adjoint(g, vol.shape, (vol.dx, vol.dy, vol.dz), T)
+    xa = host(plan.rotate_adjoint(0, dev(g).reshape(1, -1))).reshape(vol.shape)
+    assert np.abs(xa - gref).max() <= 1e-5 * np.abs(gref).max()
+
+
+def test_pitched_and_rolled_cameras_match_oracle():
+    vol = I.Volume(10, 9, 8, 4.0, 4.5, 5.0)
+    cam = I.table_single_lens(28, 0.3, yaw=0.3, ks=2, kt=2)
+    cam.pitch, cam.roll = 0.25, -0.35
+    x = I.gaussian_blobs(vol, seed=1014)
+    y = I.uniform_random(cam.m, seed=37)
+    plan = lt.Plan(vol, [cam])
+    assert rel_l2(host(plan.forward(dev(x).reshape(1, -1))), O.forward(vol, cam, x)) < TOL
+    assert rel_l2(host(plan.adjoint(dev(y).reshape(1, -1))), O.adjoint(vol, cam, y)) < TOL
+    pvol, pcam = I.tiny_plenoptic()
+    pcam.pitch, pcam.roll = -0.2, 0.3
+    px = I.gaussian_blobs(pvol, seed=1015)
+    py = I.uniform_random(pcam.m, seed=38)
+    pplan = lt.Plan(pvol, [pcam])
+    assert rel_l2(host(pplan.forward(dev(px).reshape(1, -1))), O.forward(pvol, pcam, px)) < TOL
+    assert rel_l2(host(pplan.adjoint(dev(py).reshape(1, -1))), O.adjoint(pvol, pcam, py)) < TOL
