@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--warm-samples", type=int, default=1200,
+                    help="training volumes for the warm-start time-to-residual measurement (0: skip)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default forward variant (fixed launch sequence, e.g. for profiling)")
     return ap.parse_args()
@@ -217,6 +219,29 @@ def shear_passes(flush, stream, reps=20):
     return out
 
 
+def time_to_residual(plan, n_samples, n_plain=200):
+    """Warm start vs plain solver on the bench workload: the U-Net is trained
+    here for n_samples volumes made by the projector (seeds 1e6 + i), then both
+    arms run on a held-out volume (seed 2e6): wall time (CUDA events) until the
+    data fit reaches the plain solver's n_plain-iteration value, the warm arm
+    including back-projection and U-Net inference (not training)."""
+    import time as _t
+    from paper_1812_03358_b300 import unet, warmstart
+    t0 = _t.time()
+    ws, losses = warmstart.train(plan, unet.UNet(seed=1), n_samples, lr=1e-3)
+    t_train = _t.time() - t0
+    x, _, y = warmstart.training_pair(plan, seed=2_000_000)
+    r = warmstart.evaluate(plan, ws, y, x, n_plain=n_plain)
+    out = {"definition": "wall time until the data fit reaches the plain solver's value after n_plain iterations",
+           "n_plain": n_plain, "plain_ms": r["plain_ms"], "plain_first_cross_iters": r["plain_first_cross_iters"],
+           "warm_ms": r["warm_ms"], "warm_iters": r["warm_iters"], "unet_ms": r["unet_ms"],
+           "unet_tflops": r["unet_tflops"], "gain": (r["plain_ms"] / r["warm_ms"]) if r["warm_ms"] else None,
+           "volume_error_plain": r["err_plain"], "volume_error_warm_x0": r["err_x0"],
+           "train_samples": n_samples, "train_s": round(t_train, 1), "beta": "1e-3 * mean(D)",
+           "held_out_seed": 2_000_000}
+    return out
+
+
 def cpu_baseline_sample(vol, cam, x):
     """The FP64 oracle, as it stands, on one projector + adjoint pass of the
     full workload (its BLAS threads on the host cores)."""
@@ -336,6 +361,9 @@ def run_ours(args):
     # --- a2: the rotation passes of a yawed camera (HBM-bound streams) ---
     shear = shear_passes(flush, stream)
 
+    # --- time-to-residual, warm start vs plain (rank 0 only, outside the timed region) ---
+    ttr = time_to_residual(plan, args.warm_samples) if rank == 0 and args.warm_samples > 0 else None
+
     # --- end to end through the public API: pinned host y in, data fit out ---
     y_pin = torch.from_numpy(y_host.reshape(1, -1)).pin_memory()
     y_stage = torch.empty_like(y_dev)
@@ -384,6 +412,7 @@ def run_ours(args):
             "stages_ms": stage_ms,
             "roofline": roofline,
             "shear_passes": shear,
+            "time_to_residual": ttr,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "e2e": e2e,
