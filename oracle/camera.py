@@ -158,9 +158,38 @@ def lenslet_centers(cam):
     return centers(cam.mla_ns, cam.mla_pitch), centers(cam.mla_nt, cam.mla_pitch)
 
 
+def lenslet_centres_2d(cam):
+    """Centres (s_mu, t_mu), mu = mt * mla_ns + ms: the square grid, or the
+    hexagonal lattice (rows mla_pitch * sqrt(3)/2 apart, odd rows shifted by
+    half a pitch, the lattice centred on the axis: column offset -1/4 pitch)."""
+    ms = np.arange(cam.mla_ns)
+    mt = np.arange(cam.mla_nt)
+    if getattr(cam, "mla_layout", 0) == 1:
+        t = (mt - (cam.mla_nt - 1) / 2.0) * cam.mla_pitch * np.sqrt(3.0) / 2.0
+        S = (ms[None, :] - (cam.mla_ns - 1) / 2.0 + 0.5 * (mt[:, None] % 2) - 0.25) * cam.mla_pitch
+        T = np.broadcast_to(t[:, None], S.shape)
+    else:
+        cs, ct = lenslet_centers(cam)
+        S = np.broadcast_to(cs[None, :], (cam.mla_nt, cam.mla_ns))
+        T = np.broadcast_to(ct[:, None], (cam.mla_nt, cam.mla_ns))
+    return np.array(S, dtype=np.float64).ravel(), np.array(T, dtype=np.float64).ravel()
+
+
+def transmission(cam):
+    """The diagonal of the occlusion mask M (Sec. II-D, eq. occlusion) on the
+    array grid: the microlens apertures (pixels owned by a lenslet) times an
+    optional coded-mask transmission in [0, 1]."""
+    m = (lenslet_owner(cam) >= 0).astype(np.float64)
+    if getattr(cam, "arr_mask", None) is not None:
+        m = m * np.asarray(cam.arr_mask, dtype=np.float64).reshape(cam.arr_nt, cam.arr_ns)
+    return m
+
+
 def lenslet_owner(cam):
     """owner[jt, js] = mt * mla_ns + ms of the lenslet whose disc strictly
     contains the array-pixel centre, -1 where the mask M blocks (Sec. II-D)."""
+    if getattr(cam, "mla_layout", 0) == 1:
+        return _hex_owner(cam)
     s = centers(cam.arr_ns, cam.arr_ps)
     t = centers(cam.arr_nt, cam.arr_pt)
     cs, ct = lenslet_centers(cam)
@@ -177,6 +206,30 @@ def lenslet_owner(cam):
     return np.where(inside, mtc[:, None] * cam.mla_ns + msc[None, :], -1)
 
 
+def _hex_owner(cam):
+    """Hexagonal lattice: the nearest centre among the lenslets of the three
+    nearest rows, kept when its disc strictly contains the pixel centre."""
+    s = centers(cam.arr_ns, cam.arr_ps)[None, :]
+    t = centers(cam.arr_nt, cam.arr_pt)[:, None]
+    S, T = lenslet_centres_2d(cam)
+    S = S.reshape(cam.mla_nt, cam.mla_ns)
+    T = T.reshape(cam.mla_nt, cam.mla_ns)
+    rowh = cam.mla_pitch * np.sqrt(3.0) / 2.0
+    owner = np.full((cam.arr_nt, cam.arr_ns), -1, dtype=np.int64)
+    mt0 = np.rint(t / rowh + (cam.mla_nt - 1) / 2.0).astype(np.int64)
+    for dm in (-1, 0, 1):
+        mt = mt0 + dm
+        okt = (mt >= 0) & (mt < cam.mla_nt)
+        mtc = np.clip(mt, 0, cam.mla_nt - 1)
+        ms = np.rint(s / cam.mla_pitch + (cam.mla_ns - 1) / 2.0 - 0.5 * (mtc % 2) + 0.25).astype(np.int64)
+        oks = (ms >= 0) & (ms < cam.mla_ns)
+        msc = np.clip(ms, 0, cam.mla_ns - 1)
+        d2 = (s - S[mtc, msc]) ** 2 + (t - T[mtc, msc]) ** 2
+        inside = okt & oks & (d2 < cam.mla_radius ** 2)
+        owner = np.where(inside, mtc * cam.mla_ns + msc, owner)
+    return owner
+
+
 def lenslet_maps(cam, f_mu, c_mu):
     """Array plane -> detector through lenslet mu (T_{D_mud} o R_{f_mu, c_mu})
     and array plane -> main lens (propagation back by D_mum)."""
@@ -186,41 +239,48 @@ def lenslet_maps(cam, f_mu, c_mu):
 
 
 class _StageTwo:
-    """Per-lenslet 1-D matrices of the array -> detector transport, memoised by
-    (axis, lenslet column/row, focal length, cell)."""
+    """Per-lenslet 1-D matrices of the array -> detector transport over the
+    lenslet's block (the bounding rows / columns of the pixels it owns),
+    memoised by (axis, centre, focal length, block, cell)."""
 
     def __init__(self, cam):
         self.cam = cam
         self.owner = lenslet_owner(cam)
-        self.cs, self.ct = lenslet_centers(cam)
+        self.trans = transmission(cam)
+        self.S, self.T = lenslet_centres_2d(cam)
         self.arr_s = centers(cam.arr_ns, cam.arr_ps)
         self.arr_t = centers(cam.arr_nt, cam.arr_pt)
         self.det_s = centers(cam.det_ns, cam.det_ps)
         self.det_t = centers(cam.det_nt, cam.det_pt)
         self.cache = {}
-        # array columns / rows holding each lenslet's pixels
-        self.cols = {}
-        self.rows = {}
-        for ms in range(cam.mla_ns):
-            sel = np.nonzero(np.any((self.owner >= 0) & (self.owner % cam.mla_ns == ms), axis=0))[0]
-            self.cols[ms] = sel
-        for mt in range(cam.mla_nt):
-            sel = np.nonzero(np.any((self.owner >= 0) & (self.owner // cam.mla_ns == mt), axis=1))[0]
-            self.rows[mt] = sel
+        nmu = cam.mla_ns * cam.mla_nt
+        jt, js = np.nonzero(self.owner >= 0)
+        mu = self.owner[jt, js]
+        lo_c = np.full(nmu, cam.arr_ns); hi_c = np.full(nmu, -1)
+        lo_r = np.full(nmu, cam.arr_nt); hi_r = np.full(nmu, -1)
+        np.minimum.at(lo_c, mu, js); np.maximum.at(hi_c, mu, js)
+        np.minimum.at(lo_r, mu, jt); np.maximum.at(hi_r, mu, jt)
+        self.cols = [np.arange(lo_c[m], hi_c[m] + 1) for m in range(nmu)]
+        self.rows = [np.arange(lo_r[m], hi_r[m] + 1) for m in range(nmu)]
 
-    def mat(self, axis, m, f_mu, cell_idx, cell):
-        key = (axis, m, float(f_mu), cell_idx)
+    def mat(self, axis, mu, f_mu, cell_idx, cell):
+        cam = self.cam
+        sk, tk, d0s, d0t = cell
+        if axis == 0:
+            key = (0, float(self.S[mu]), float(f_mu), int(self.cols[mu][0]) if len(self.cols[mu]) else -1,
+                   len(self.cols[mu]), cell_idx)
+        else:
+            key = (1, float(self.T[mu]), float(f_mu), int(self.rows[mu][0]) if len(self.rows[mu]) else -1,
+                   len(self.rows[mu]), cell_idx)
         if key not in self.cache:
-            cam = self.cam
-            sk, tk, d0s, d0t = cell
             if axis == 0:
-                Xdq, X0q = lenslet_maps(cam, f_mu, self.cs[m])
+                Xdq, X0q = lenslet_maps(cam, f_mu, self.S[mu])
                 B = matrix_1d(cam, Xdq, X0q, self.det_s, cam.det_ps, sk, d0s,
-                              self.arr_s[self.cols[m]], cam.arr_ps)
+                              self.arr_s[self.cols[mu]], cam.arr_ps)
             else:
-                Xdq, X0q = lenslet_maps(cam, f_mu, self.ct[m])
+                Xdq, X0q = lenslet_maps(cam, f_mu, self.T[mu])
                 B = matrix_1d(cam, Xdq, X0q, self.det_t, cam.det_pt, tk, d0t,
-                              self.arr_t[self.rows[m]], cam.arr_pt)
+                              self.arr_t[self.rows[mu]], cam.arr_pt)
             nz = np.nonzero(np.any(B != 0.0, axis=1))[0]
             self.cache[key] = (nz, B[nz])
         return self.cache[key]
@@ -235,7 +295,7 @@ def plenoptic_array_field(vol, cam, x, cell):
                                  cam.arr_ns, cam.arr_nt, cam.arr_ps, cam.arr_pt)
         Fa += vol.dz * (Bt @ X[n] @ Bs.T)
     Fa /= array_basis_volume(cam, cell)
-    return np.where(lenslet_owner(cam) >= 0, Fa, 0.0)
+    return transmission(cam) * Fa
 
 
 def plenoptic_stage2(cam, fields, st=None, cells=None):
@@ -250,12 +310,14 @@ def plenoptic_stage2(cam, fields, st=None, cells=None):
         for mt in range(cam.mla_nt):
             for ms in range(cam.mla_ns):
                 mu = mt * cam.mla_ns + ms
+                rows, cols = st.rows[mu], st.cols[mu]
+                if len(rows) == 0 or len(cols) == 0:
+                    continue
                 f_mu = cam.mla_focal[mt, ms]
-                rs, Bs = st.mat(0, ms, f_mu, ci, cell)
-                rt, Bt = st.mat(1, mt, f_mu, ci, cell)
+                rs, Bs = st.mat(0, mu, f_mu, ci, cell)
+                rt, Bt = st.mat(1, mu, f_mu, ci, cell)
                 if len(rs) == 0 or len(rt) == 0:
                     continue
-                rows, cols = st.rows[mt], st.cols[ms]
                 sub = Fa[np.ix_(rows, cols)] * (st.owner[np.ix_(rows, cols)] == mu)
                 y[np.ix_(rt, rs)] += Bt @ sub @ Bs.T
     return y
@@ -275,15 +337,17 @@ def plenoptic_stage2_adjoint(cam, y, st=None, cells=None):
         for mt in range(cam.mla_nt):
             for ms in range(cam.mla_ns):
                 mu = mt * cam.mla_ns + ms
+                rows, cols = st.rows[mu], st.cols[mu]
+                if len(rows) == 0 or len(cols) == 0:
+                    continue
                 f_mu = cam.mla_focal[mt, ms]
-                rs, Bs = st.mat(0, ms, f_mu, ci, cell)
-                rt, Bt = st.mat(1, mt, f_mu, ci, cell)
+                rs, Bs = st.mat(0, mu, f_mu, ci, cell)
+                rt, Bt = st.mat(1, mu, f_mu, ci, cell)
                 if len(rs) == 0 or len(rt) == 0:
                     continue
-                rows, cols = st.rows[mt], st.cols[ms]
                 g = Bt.T @ Y[np.ix_(rt, rs)] @ Bs
                 own = st.owner[np.ix_(rows, cols)] == mu
-                Ga[np.ix_(rows, cols)] += np.where(own, g, 0.0)
+                Ga[np.ix_(rows, cols)] += np.where(own, g * st.trans[np.ix_(rows, cols)], 0.0)
         out.append(Ga)
     return np.stack(out)
 
@@ -325,7 +389,7 @@ def plenoptic_matrix(vol, cam):
     """Explicit A for tiny plenoptic cameras, built term by term from the
     factorised model (eq. plenoptic,factor)."""
     owner = lenslet_owner(cam)
-    cs, ct = lenslet_centers(cam)
+    S_mu, T_mu = lenslet_centres_2d(cam)
     arr_s = centers(cam.arr_ns, cam.arr_ps)
     arr_t = centers(cam.arr_nt, cam.arr_pt)
     det_s = centers(cam.det_ns, cam.det_ps)
@@ -345,13 +409,13 @@ def plenoptic_matrix(vol, cam):
             for ms in range(cam.mla_ns):
                 mu = mt * cam.mla_ns + ms
                 f_mu = cam.mla_focal[mt, ms]
-                Xs, X0 = lenslet_maps(cam, f_mu, cs[ms])
-                Xt, _ = lenslet_maps(cam, f_mu, ct[mt])
+                Xs, X0 = lenslet_maps(cam, f_mu, S_mu[mu])
+                Xt, _ = lenslet_maps(cam, f_mu, T_mu[mu])
                 Bs = matrix_1d(cam, Xs, X0, det_s, cam.det_ps, sk, d0s, arr_s, cam.arr_ps)
                 Bt = matrix_1d(cam, Xt, X0, det_t, cam.det_pt, tk, d0t, arr_t, cam.arr_pt)
                 own = (owner.reshape(-1) == mu).astype(np.float64)
                 S2 += np.kron(Bt, Bs) * own[None, :]
-        mask = (owner.reshape(-1) >= 0).astype(np.float64)
+        mask = transmission(cam).reshape(-1)
         A += S2 @ (mask[:, None] * S1) / array_basis_volume(cam, cell)
     return A
 

@@ -21,6 +21,8 @@ CAM_SINGLE = 0
 CAM_PLENOPTIC = 1
 BASIS_PILLBOX = 0
 BASIS_DIRAC = 1
+MLA_SQUARE = 0
+MLA_HEX = 1
 
 
 @dataclass
@@ -76,6 +78,8 @@ class Camera:
     arr_nt: int = 0
     arr_ps: float = 0.0
     arr_pt: float = 0.0
+    mla_layout: int = 0                      # MLA_SQUARE or MLA_HEX
+    arr_mask: Optional[np.ndarray] = None    # [arr_nt, arr_ns] transmission in [0, 1] (coded mask), None = 1
 
     @property
     def m(self) -> int:
@@ -86,6 +90,28 @@ def in_focus_distance(f: float, d_image: float) -> float:
     """Object distance conjugate to an image distance for a thin lens
     (the lens law; used only to place synthetic volumes in focus)."""
     return 1.0 / (1.0 / f - 1.0 / d_image)
+
+
+def hex_mla_focal(mla_nt: int, mla_ns: int, focals=(2.8, 3.0, 3.2)) -> np.ndarray:
+    """Three focal lengths on the hexagonal (odd rows shifted) lattice with no
+    two neighbours alike: type (q - r) mod 3 of the axial coordinates
+    q = col - (row - (row & 1)) / 2, r = row."""
+    r, c = np.meshgrid(np.arange(mla_nt), np.arange(mla_ns), indexing="ij")
+    q = c - (r - (r & 1)) // 2
+    return np.asarray(focals, dtype=np.float64)[(q - r) % 3]
+
+
+def hex_plenoptic_camera(n_cols: int = 40, n_rows: int = 46, n_px: int = 400, pitch_px: float = 0.02,
+                         ks: int = 2, kt: int = 2) -> Camera:
+    """The plenoptic camera with the paper's hexagonal three-focal MLA (rows
+    pitch * sqrt(3)/2 apart, odd rows shifted by half a pitch), 200 um
+    pitch, radius 100 um, over an n_px^2 detector / array plane."""
+    cam = plenoptic_camera(n_lenslets=1, px_per_lenslet=n_px, pitch_px=pitch_px, ks=ks, kt=kt)
+    cam.mla_ns, cam.mla_nt = n_cols, n_rows
+    cam.mla_pitch, cam.mla_radius = 0.2, 0.1
+    cam.mla_layout = MLA_HEX
+    cam.mla_focal = hex_mla_focal(n_rows, n_cols)
+    return cam
 
 
 def square_mla_focal(mla_nt: int, mla_ns: int, focals=(2.8, 3.0, 3.2)) -> np.ndarray:
@@ -158,6 +184,17 @@ def tiny_plenoptic(n_lenslets=4, px_per_lenslet=6, ks=2, kt=2) -> (Volume, Camer
     """A plenoptic camera small enough for an explicit system matrix."""
     cam = plenoptic_camera(n_lenslets=n_lenslets, px_per_lenslet=px_per_lenslet,
                            pitch_px=0.2 / px_per_lenslet, ks=ks, kt=kt)
+    return Volume(8, 8, 6, 0.9, 0.9, 4.0), cam
+
+
+def tiny_hex_plenoptic(n_cols=4, n_rows=5, n_px=24, ks=2, kt=2) -> (Volume, Camera):
+    """A hexagonal-MLA plenoptic camera small enough for an explicit matrix
+    (n_px^2 array / detector pixels over the lattice)."""
+    cam = plenoptic_camera(n_lenslets=1, px_per_lenslet=n_px, pitch_px=0.8 / n_px, ks=ks, kt=kt)
+    cam.mla_ns, cam.mla_nt = n_cols, n_rows
+    cam.mla_pitch, cam.mla_radius = 0.2, 0.1
+    cam.mla_layout = MLA_HEX
+    cam.mla_focal = hex_mla_focal(n_rows, n_cols)
     return Volume(8, 8, 6, 0.9, 0.9, 4.0), cam
 
 
