@@ -52,6 +52,7 @@ typedef enum {
 } lt_status;
 
 enum { LT_BASIS_PILLBOX = 0, LT_BASIS_DIRAC = 1 };    /* angular basis a(.), Sec. II-B */
+enum { LT_MLA_SQUARE = 0, LT_MLA_HEX = 1 };           /* microlens lattice              */
 enum { LT_CAM_SINGLE = 0, LT_CAM_PLENOPTIC = 1 };     /* Sec. II-F                     */
 
 /* Pillbox voxel grid (Sec. III, eq. voxel), centred on the object origin. */
@@ -82,12 +83,19 @@ typedef struct {
   /* plenoptic only (Sec. II-F2) */
   double d_lens_mla;       /* D_mu_m: main lens -> microlens array               */
   double d_mla_det;        /* D_mu_d: microlens array -> detector                */
-  int32_t mla_ns, mla_nt;  /* square lenslet grid                                */
+  int32_t mla_ns, mla_nt;  /* lenslet columns and rows (see mla_layout)          */
   double mla_pitch;        /* lenslet centre spacing                             */
   double mla_radius;       /* lenslet disc radius (<= mla_pitch / 2)             */
   const double* mla_focal; /* host [mla_nt*mla_ns] focal lengths, copied         */
   int32_t arr_ns, arr_nt;  /* array-plane (mask) grid, Sec. II-D                */
   double arr_ps, arr_pt;
+  int32_t mla_layout;      /* LT_MLA_SQUARE, or LT_MLA_HEX: rows mla_pitch sqrt(3)/2
+                            * apart, odd rows shifted by half a pitch, the
+                            * lattice centred on the axis (column offset
+                            * -pitch/4); lenslet (mt, ms) = mla_focal[mt][ms]   */
+  const float* arr_mask;   /* host [arr_nt*arr_ns] coded-mask transmission in
+                            * [0, 1] multiplying the aperture mask M (Sec. II-D,
+                            * eq. occlusion), or NULL (= 1); copied            */
 } lt_camera_desc;
 
 typedef struct lt_plan lt_plan;

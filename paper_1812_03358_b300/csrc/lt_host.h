@@ -49,13 +49,10 @@ struct CameraPlan {
   // plenoptic
   int64_t Na = 0;
   LensletParam* d_lens = nullptr;
-  int2* d_cand_s = nullptr;
-  int2* d_cand_t = nullptr;
-  int2* d_cols = nullptr;
+  int2* d_cols = nullptr;          // [N_mu] block columns / rows of each lenslet
   int2* d_rows = nullptr;
-  int32_t* d_col_owner = nullptr;
-  int32_t* d_row_owner = nullptr;
-  uint8_t* d_mask = nullptr;
+  int32_t* d_owner = nullptr;      // [arr_nt * arr_ns] owning lenslet or -1
+  float* d_mask = nullptr;         // [arr_nt * arr_ns] diagonal of M
   int4* d_det_range = nullptr;
   int4* d_det_union = nullptr;
   int2* d_cand_all_s = nullptr;

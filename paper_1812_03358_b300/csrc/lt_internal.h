@@ -44,13 +44,11 @@ struct LensletParam {
 // Device tables of one plenoptic camera's array -> detector stage.
 struct StageTwo {
   const LensletParam* lens;   // [K][mla_nt*mla_ns]
-  const int2* cand_s;         // [K][det_ns]: lenslet columns that can reach detector column
-  const int2* cand_t;         // [K][det_nt]
-  const int2* cols;           // [mla_ns]: array columns [x, y) of lenslet column
-  const int2* rows;           // [mla_nt]
-  const int32_t* col_owner;   // [arr_ns]: lenslet column of an array column, -1 if none
-  const int32_t* row_owner;   // [arr_nt]
-  const uint8_t* mask;        // [arr_nt*arr_ns] 1 if the pixel centre is inside its lenslet disc
+  const int2* cols;           // [mla_nt*mla_ns]: array columns [x, y) of lenslet mu's block
+  const int2* rows;           // [mla_nt*mla_ns]: array rows [x, y)
+  const int32_t* owner;       // [arr_nt*arr_ns]: lenslet whose disc holds the pixel centre, -1 if none
+  const float* mask;          // [arr_nt*arr_ns]: the diagonal of M (aperture x coded transmission)
+  int32_t overlap;            // 1 if lenslet blocks overlap (hexagonal lattice): write owned pixels only
   int32_t mla_ns, mla_nt;
   int32_t arr_ns, arr_nt;
   int32_t det_ns, det_nt;
@@ -128,7 +126,7 @@ struct BeamCam {
   float* out;              // forward output: [F][K][nt][ns] if per_cell, else [F][..][nt][ns]
   const float* in;         // adjoint input, same layout as out
   const SliceParam* prm;   // [K][nz]
-  const uint8_t* mask;     // per-pixel output mask (plenoptic array plane) or null
+  const float* mask;       // per-pixel output mask M (plenoptic array plane, diagonal) or null
   const int2* srange;      // [K][tiles_s]
   const int2* trange;      // [K][tiles_t]
   long long x_fs, out_fs;  // frame strides

@@ -312,7 +312,7 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
             float v = acc[r];
 #pragma unroll
             for (int g = 1; g < G; ++g) v += red[g - 1][row][lane];
-            if (C.mask && !C.mask[(long long)itp * C.ns + is]) v = 0.0f;
+            if (C.mask) v *= C.mask[(long long)itp * C.ns + is];   // M (Sec. II-D)
             o[(long long)itp * C.ns + is] = v;
           }
         }
@@ -498,8 +498,7 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
   const int mu = blockIdx.x;
   const int frame = blockIdx.y;
   const int nmu = s2.mla_ns * s2.mla_nt;
-  const int ms = mu % s2.mla_ns, mt = mu / s2.mla_ns;
-  const int2 cc = s2.cols[ms], rr = s2.rows[mt];
+  const int2 cc = s2.cols[mu], rr = s2.rows[mu];
   const int nc = cc.y - cc.x, nr = rr.y - rr.x;
   const int4 du = s2.det_union[mu];
   const int nsu = du.y - du.x + 1, ntu = du.w - du.z + 1;
@@ -517,7 +516,8 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
       const float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
       for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
         const int r = o / nc, c = o - r * nc;
-        F[r][c] = __ldg(fk + (long long)(rr.x + r) * s2.arr_ns + cc.x + c);
+        const long long px = (long long)(rr.x + r) * s2.arr_ns + cc.x + c;
+        F[r][c] = __ldg(s2.owner + px) == mu ? __ldg(fk + px) : 0.0f;   // this lenslet's own pixels
       }
       __syncthreads();
       // W[r][q] = sum_c Bs[c][q] F[r][c]
@@ -576,8 +576,7 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
   const int mu = blockIdx.x;
   const int frame = blockIdx.y;
   const int nmu = s2.mla_ns * s2.mla_nt;
-  const int ms = mu % s2.mla_ns, mt = mu / s2.mla_ns;
-  const int2 cc = s2.cols[ms], rr = s2.rows[mt];
+  const int2 cc = s2.cols[mu], rr = s2.rows[mu];
   const int nc = cc.y - cc.x, nr = rr.y - rr.x;
   if (nc <= 0 || nr <= 0) return;   // uniform
   const long long Na = (long long)s2.arr_ns * s2.arr_nt;
@@ -589,8 +588,11 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
     const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
     float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
     if (nds <= 0 || ndt <= 0) {
-      for (int o = threadIdx.x; o < nr * nc; o += blockDim.x)
-        fk[(long long)(rr.x + o / nc) * s2.arr_ns + cc.x + o % nc] = 0.0f;
+      for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
+        const long long px = (long long)(rr.x + o / nc) * s2.arr_ns + cc.x + o % nc;
+        const int own = __ldg(s2.owner + px);
+        if (own == mu || (!s2.overlap && own < 0)) fk[px] = 0.0f;
+      }
       continue;   // uniform
     }
     lenslet_weights(L, dr, cc, rr, Bs, Bt);
@@ -613,7 +615,12 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
       const int jt = rr.x + r, js = cc.x + c;
       float g = 0.0f;
       for (int q = 0; q < nds; ++q) g = fmaf(Bs[c][q], U[r][q], g);
-      fk[(long long)jt * s2.arr_ns + js] = s2.mask[(long long)jt * s2.arr_ns + js] ? scale * g : 0.0f;
+      const long long px = (long long)jt * s2.arr_ns + js;
+      const int own = __ldg(s2.owner + px);
+      // M (its diagonal) on this lenslet's own pixels; blocks that tile the
+      // plane also clear their unowned pixels, overlapping blocks leave them
+      if (own == mu) fk[px] = __ldg(s2.mask + px) * (scale * g);
+      else if (!s2.overlap && own < 0) fk[px] = 0.0f;
     }
     __syncthreads();
   }

@@ -186,6 +186,8 @@ static lt_status validate_camera(const lt_volume_desc* v, const lt_camera_desc* 
       return set_error(LT_EINVAL, "camera %d: d_lens_mla, d_mla_det must be positive", idx);
     if (c->mla_ns <= 0 || c->mla_nt <= 0 || !pos(c->mla_pitch) || !pos(c->mla_radius))
       return set_error(LT_EINVAL, "camera %d: lenslet grid must be non-empty with positive pitch/radius", idx);
+    if (c->mla_layout != LT_MLA_SQUARE && c->mla_layout != LT_MLA_HEX)
+      return set_error(LT_EINVAL, "camera %d: unknown mla_layout %d", idx, c->mla_layout);
     if (c->mla_radius > 0.5 * c->mla_pitch * (1.0 + 1e-12))
       return set_error(LT_EINVAL, "camera %d: lenslet radius exceeds half the pitch (discs overlap)", idx);
     if (!c->mla_focal) return set_error(LT_EINVAL, "camera %d: mla_focal is NULL", idx);
@@ -231,12 +233,9 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.d_srange);
   cudaFree(c.d_trange);
   cudaFree(c.d_lens);
-  cudaFree(c.d_cand_s);
-  cudaFree(c.d_cand_t);
   cudaFree(c.d_cols);
   cudaFree(c.d_rows);
-  cudaFree(c.d_col_owner);
-  cudaFree(c.d_row_owner);
+  cudaFree(c.d_owner);
   cudaFree(c.d_mask);
   cudaFree(c.d_det_range);
   cudaFree(c.d_det_union);
@@ -348,67 +347,117 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   const lt_camera_desc& d = c.desc;
   const int mns = d.mla_ns, mnt = d.mla_nt;
   const int nmu = mns * mnt;
-  // Lenslet grid cells [c - pitch/2, c + pitch/2) own the array columns/rows
-  // whose centres fall inside them.
-  std::vector<int32_t> col_owner(d.arr_ns, -1), row_owner(d.arr_nt, -1);
-  std::vector<int2> cols(mns, make_int2(0, 0)), rows(mnt, make_int2(0, 0));
-  for (int m = 0; m < mns; ++m) cols[m] = make_int2(INT32_MAX, -1);
-  for (int m = 0; m < mnt; ++m) rows[m] = make_int2(INT32_MAX, -1);
-  const double edge_s = centre(0, mns, d.mla_pitch) - 0.5 * d.mla_pitch;
-  const double edge_t = centre(0, mnt, d.mla_pitch) - 0.5 * d.mla_pitch;
-  for (int j = 0; j < d.arr_ns; ++j) {
-    const double m = std::floor((centre(j, d.arr_ns, d.arr_ps) - edge_s) / d.mla_pitch);
-    if (m >= 0 && m < mns) {
-      col_owner[j] = (int)m;
-      cols[(int)m].x = std::min(cols[(int)m].x, j);
-      cols[(int)m].y = std::max(cols[(int)m].y, j + 1);
+  const bool hex = d.mla_layout == LT_MLA_HEX;
+  // Lenslet centres: the square grid, or the hexagonal lattice (rows
+  // pitch sqrt(3)/2 apart, odd rows shifted by half a pitch, centred on the
+  // axis with a column offset of -pitch/4).
+  const double rowh = hex ? d.mla_pitch * std::sqrt(3.0) / 2.0 : d.mla_pitch;
+  std::vector<double> S(nmu), T(nmu);
+  for (int mt = 0; mt < mnt; ++mt)
+    for (int ms = 0; ms < mns; ++ms) {
+      const int mu = mt * mns + ms;
+      S[mu] = hex ? (ms - 0.5 * (mns - 1) + 0.5 * (mt & 1) - 0.25) * d.mla_pitch : centre(ms, mns, d.mla_pitch);
+      T[mu] = hex ? (mt - 0.5 * (mnt - 1)) * rowh : centre(mt, mnt, d.mla_pitch);
+    }
+  // Ownership: the lenslet whose disc strictly contains the pixel centre
+  // (discs are disjoint, radius <= pitch / 2), searched among the nearest
+  // rows / columns.  M = apertures x the coded transmission (Sec. II-D).
+  const size_t npix = (size_t)d.arr_ns * d.arr_nt;
+  std::vector<int32_t> owner(npix, -1);
+  std::vector<float> mask(npix, 0.0f);
+  const double r2 = d.mla_radius * d.mla_radius;
+  for (int jt = 0; jt < d.arr_nt; ++jt) {
+    const double t = centre(jt, d.arr_nt, d.arr_pt);
+    const int mt0 = (int)std::nearbyint(t / rowh + 0.5 * (mnt - 1));
+    for (int js = 0; js < d.arr_ns; ++js) {
+      const double sv = centre(js, d.arr_ns, d.arr_ps);
+      int own = -1;
+      for (int dm = hex ? -1 : 0; dm <= (hex ? 1 : 0) && own < 0; ++dm) {
+        const int mt = mt0 + dm;
+        if (mt < 0 || mt >= mnt) continue;
+        const int ms = (int)std::nearbyint(sv / d.mla_pitch + 0.5 * (mns - 1) - (hex ? 0.5 * (mt & 1) - 0.25 : 0.0));
+        if (ms < 0 || ms >= mns) continue;
+        const int mu = mt * mns + ms;
+        const double ds = sv - S[mu], dt = t - T[mu];
+        if (ds * ds + dt * dt < r2) own = mu;
+      }
+      owner[(size_t)jt * d.arr_ns + js] = own;
+      if (own >= 0) {
+        float m = 1.0f;
+        if (d.arr_mask) m = std::min(1.0f, std::max(0.0f, d.arr_mask[(size_t)jt * d.arr_ns + js]));
+        mask[(size_t)jt * d.arr_ns + js] = m;
+      }
     }
   }
-  for (int j = 0; j < d.arr_nt; ++j) {
-    const double m = std::floor((centre(j, d.arr_nt, d.arr_pt) - edge_t) / d.mla_pitch);
-    if (m >= 0 && m < mnt) {
-      row_owner[j] = (int)m;
-      rows[(int)m].x = std::min(rows[(int)m].x, j);
-      rows[(int)m].y = std::max(rows[(int)m].y, j + 1);
+  // Lenslet blocks.  Square grid: the lenslet's cell [c - pitch/2, c + pitch/2)
+  // (blocks tile the plane; unowned pixels inside a block are written as 0).
+  // Hexagonal lattice: the bounding rows / columns of the owned pixels
+  // (blocks overlap; each lenslet writes only its own pixels).
+  std::vector<int2> cols(nmu, make_int2(INT32_MAX, -1)), rows(nmu, make_int2(INT32_MAX, -1));
+  int full_cover = 1;
+  if (!hex) {
+    const double edge_s = centre(0, mns, d.mla_pitch) - 0.5 * d.mla_pitch;
+    const double edge_t = centre(0, mnt, d.mla_pitch) - 0.5 * d.mla_pitch;
+    std::vector<int2> cs(mns, make_int2(INT32_MAX, -1)), rs(mnt, make_int2(INT32_MAX, -1));
+    for (int j = 0; j < d.arr_ns; ++j) {
+      const double m = std::floor((centre(j, d.arr_ns, d.arr_ps) - edge_s) / d.mla_pitch);
+      if (m >= 0 && m < mns) {
+        cs[(int)m].x = std::min(cs[(int)m].x, j);
+        cs[(int)m].y = std::max(cs[(int)m].y, j + 1);
+      } else {
+        full_cover = 0;
+      }
     }
+    for (int j = 0; j < d.arr_nt; ++j) {
+      const double m = std::floor((centre(j, d.arr_nt, d.arr_pt) - edge_t) / d.mla_pitch);
+      if (m >= 0 && m < mnt) {
+        rs[(int)m].x = std::min(rs[(int)m].x, j);
+        rs[(int)m].y = std::max(rs[(int)m].y, j + 1);
+      } else {
+        full_cover = 0;
+      }
+    }
+    for (int mt = 0; mt < mnt; ++mt)
+      for (int ms = 0; ms < mns; ++ms) {
+        cols[(size_t)mt * mns + ms] = cs[ms];
+        rows[(size_t)mt * mns + ms] = rs[mt];
+      }
+  } else {
+    full_cover = 0;
+    for (int jt = 0; jt < d.arr_nt; ++jt)
+      for (int js = 0; js < d.arr_ns; ++js) {
+        const int mu = owner[(size_t)jt * d.arr_ns + js];
+        if (mu < 0) continue;
+        cols[mu].x = std::min(cols[mu].x, js);
+        cols[mu].y = std::max(cols[mu].y, js + 1);
+        rows[mu].x = std::min(rows[mu].x, jt);
+        rows[mu].y = std::max(rows[mu].y, jt + 1);
+      }
   }
   int max_cols = 0, max_rows = 0;
-  for (auto& r : cols) {
-    if (r.y < 0) r = make_int2(0, 0);
-    max_cols = std::max(max_cols, r.y - r.x);
-  }
-  for (auto& r : rows) {
-    if (r.y < 0) r = make_int2(0, 0);
-    max_rows = std::max(max_rows, r.y - r.x);
+  for (int mu = 0; mu < nmu; ++mu) {
+    if (cols[mu].y < 0 || rows[mu].y < 0) {
+      cols[mu] = make_int2(0, 0);
+      rows[mu] = make_int2(0, 0);
+    }
+    max_cols = std::max(max_cols, cols[mu].y - cols[mu].x);
+    max_rows = std::max(max_rows, rows[mu].y - rows[mu].x);
   }
   if (max_cols > kMaxLensletPixels || max_rows > kMaxLensletPixels)
     return set_error(LT_EUNSUPPORTED, "camera %d: %d x %d array pixels per lenslet (kernel limit %d)",
                      idx, max_cols, max_rows, kMaxLensletPixels);
-  // Binary mask M: array-pixel centre strictly inside its lenslet's disc.
-  std::vector<uint8_t> mask((size_t)d.arr_ns * d.arr_nt, 0);
-  const double r2 = d.mla_radius * d.mla_radius;
-  for (int jt = 0; jt < d.arr_nt; ++jt) {
-    if (row_owner[jt] < 0) continue;
-    const double dt = centre(jt, d.arr_nt, d.arr_pt) - centre(row_owner[jt], mnt, d.mla_pitch);
-    for (int js = 0; js < d.arr_ns; ++js) {
-      if (col_owner[js] < 0) continue;
-      const double ds = centre(js, d.arr_ns, d.arr_ps) - centre(col_owner[js], mns, d.mla_pitch);
-      mask[(size_t)jt * d.arr_ns + js] = (ds * ds + dt * dt < r2) ? 1 : 0;
-    }
-  }
   // Per (cell, lenslet) footprints of detector pixels on the array plane.
   std::vector<LensletParam> lens((size_t)c.K * nmu);
-  std::vector<int2> cand_s((size_t)c.K * d.det_ns, make_int2(INT32_MAX, -1));
-  std::vector<int2> cand_t((size_t)c.K * d.det_nt, make_int2(INT32_MAX, -1));
   std::vector<int4> det_range((size_t)c.K * nmu, make_int4(0, -1, 0, -1));
   int wis = 0, wit = 0;
   for (int k = 0; k < c.K; ++k) {
     for (int mt = 0; mt < mnt; ++mt) {
       for (int ms = 0; ms < mns; ++ms) {
-        const double f = c.focal[(size_t)mt * mns + ms];
+        const int mu = mt * mns + ms;
+        const double f = c.focal[(size_t)mu];
         Row Ps, Ls, Pt, Lt;
-        lenslet_rows(d.d_mla_det, d.d_lens_mla, f, centre(ms, mns, d.mla_pitch), &Ps, &Ls);
-        lenslet_rows(d.d_mla_det, d.d_lens_mla, f, centre(mt, mnt, d.mla_pitch), &Pt, &Lt);
+        lenslet_rows(d.d_mla_det, d.d_lens_mla, f, S[mu], &Ps, &Ls);
+        lenslet_rows(d.d_mla_det, d.d_lens_mla, f, T[mu], &Pt, &Lt);
         Footprint fs, ft;
         if (!footprint(Ls, Ps, c.cells[k].sk, c.cells[k].d0s, centre(0, d.det_ns, d.det_ps), d.det_ps,
                        centre(0, d.arr_ns, d.arr_ps), d.arr_ps, d.basis, &fs) ||
@@ -422,42 +471,26 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
         L.scale = (float)(fs.H * d.arr_ps * ft.H * d.arr_pt);
         wis = std::max(wis, adj_window(L.s.Q, fs.C1));
         wit = std::max(wit, adj_window(L.t.Q, ft.C1));
-        // detector columns whose footprints can reach this lenslet's columns
-        if (cols[ms].y > cols[ms].x) {
-          const double lo = cols[ms].x - 0.5 - fs.Q, hi = cols[ms].y - 0.5 + fs.Q;
-          double a = (lo - fs.C0) / fs.C1, b = (hi - fs.C0) / fs.C1;
-          if (a > b) std::swap(a, b);
-          const long long i0 = std::max<long long>(0, (long long)std::floor(a) - 1);
-          const long long i1 = std::min<long long>(d.det_ns - 1, (long long)std::ceil(b) + 1);
-          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].x = (int)i0;
-          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].y = (int)i1;
-          for (long long i = i0; i <= i1; ++i) {
-            int2& cs = cand_s[(size_t)k * d.det_ns + i];
-            cs.x = std::min(cs.x, ms);
-            cs.y = std::max(cs.y, ms);
+        // detector columns / rows whose footprints can reach this lenslet's block
+        if (cols[mu].y > cols[mu].x && rows[mu].y > rows[mu].x) {
+          {
+            const double lo = cols[mu].x - 0.5 - fs.Q, hi = cols[mu].y - 0.5 + fs.Q;
+            double a = (lo - fs.C0) / fs.C1, b = (hi - fs.C0) / fs.C1;
+            if (a > b) std::swap(a, b);
+            det_range[(size_t)k * nmu + mu].x = (int)std::max<long long>(0, (long long)std::floor(a) - 1);
+            det_range[(size_t)k * nmu + mu].y = (int)std::min<long long>(d.det_ns - 1, (long long)std::ceil(b) + 1);
           }
-        }
-        if (rows[mt].y > rows[mt].x) {
-          const double lo = rows[mt].x - 0.5 - ft.Q, hi = rows[mt].y - 0.5 + ft.Q;
-          double a = (lo - ft.C0) / ft.C1, b = (hi - ft.C0) / ft.C1;
-          if (a > b) std::swap(a, b);
-          const long long i0 = std::max<long long>(0, (long long)std::floor(a) - 1);
-          const long long i1 = std::min<long long>(d.det_nt - 1, (long long)std::ceil(b) + 1);
-          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].z = (int)i0;
-          det_range[(size_t)k * nmu + (size_t)mt * mns + ms].w = (int)i1;
-          for (long long i = i0; i <= i1; ++i) {
-            int2& ct = cand_t[(size_t)k * d.det_nt + i];
-            ct.x = std::min(ct.x, mt);
-            ct.y = std::max(ct.y, mt);
+          {
+            const double lo = rows[mu].x - 0.5 - ft.Q, hi = rows[mu].y - 0.5 + ft.Q;
+            double a = (lo - ft.C0) / ft.C1, b = (hi - ft.C0) / ft.C1;
+            if (a > b) std::swap(a, b);
+            det_range[(size_t)k * nmu + mu].z = (int)std::max<long long>(0, (long long)std::floor(a) - 1);
+            det_range[(size_t)k * nmu + mu].w = (int)std::min<long long>(d.det_nt - 1, (long long)std::ceil(b) + 1);
           }
         }
       }
     }
   }
-  for (auto& r : cand_s)
-    if (r.y < 0) r = make_int2(0, -1);
-  for (auto& r : cand_t)
-    if (r.y < 0) r = make_int2(0, -1);
   // union over cells of each lenslet's detector window, and the lenslets
   // whose union window covers each detector column / row
   std::vector<int4> det_union(nmu, make_int4(INT32_MAX, -1, INT32_MAX, -1));
@@ -489,20 +522,14 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
     if (r.y < 0) r = make_int2(0, -1);
   for (auto& r : cand_all_t)
     if (r.y < 0) r = make_int2(0, -1);
-  int full_cover = 1;
-  for (int j = 0; j < d.arr_ns; ++j) full_cover &= col_owner[j] >= 0;
-  for (int j = 0; j < d.arr_nt; ++j) full_cover &= row_owner[j] >= 0;
   if (wis > kMaxAdjointWindow || wit > kMaxAdjointWindow)
     return set_error(LT_EUNSUPPORTED, "camera %d: an array pixel is covered by %d x %d detector footprints (kernel limit %d)",
                      idx, wis, wit, kMaxAdjointWindow);
   lt_status s;
   if ((s = upload(lens, &c.d_lens, "lenslet parameters")) != LT_OK) return s;
-  if ((s = upload(cand_s, &c.d_cand_s, "candidate columns")) != LT_OK) return s;
-  if ((s = upload(cand_t, &c.d_cand_t, "candidate rows")) != LT_OK) return s;
   if ((s = upload(cols, &c.d_cols, "lenslet columns")) != LT_OK) return s;
   if ((s = upload(rows, &c.d_rows, "lenslet rows")) != LT_OK) return s;
-  if ((s = upload(col_owner, &c.d_col_owner, "column owners")) != LT_OK) return s;
-  if ((s = upload(row_owner, &c.d_row_owner, "row owners")) != LT_OK) return s;
+  if ((s = upload(owner, &c.d_owner, "pixel owners")) != LT_OK) return s;
   if ((s = upload(mask, &c.d_mask, "mask")) != LT_OK) return s;
   if ((s = upload(det_range, &c.d_det_range, "lenslet detector ranges")) != LT_OK) return s;
   if ((s = upload(det_union, &c.d_det_union, "lenslet detector windows")) != LT_OK) return s;
@@ -525,13 +552,11 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   }
   lt::StageTwo& s2 = c.s2;
   s2.lens = c.d_lens;
-  s2.cand_s = c.d_cand_s;
-  s2.cand_t = c.d_cand_t;
   s2.cols = c.d_cols;
   s2.rows = c.d_rows;
-  s2.col_owner = c.d_col_owner;
-  s2.row_owner = c.d_row_owner;
+  s2.owner = c.d_owner;
   s2.mask = c.d_mask;
+  s2.overlap = hex ? 1 : 0;
   s2.mla_ns = mns;
   s2.mla_nt = mnt;
   s2.arr_ns = d.arr_ns;
@@ -777,7 +802,9 @@ static lt_status plan_camera(const lt_volume_desc& v0, const lt_camera_desc& src
   lt_status s = plan_slices(v, c, src.d_lens_mla, src.arr_ns, src.arr_nt, src.arr_ps, src.arr_pt,
                             1.0 / va, idx);
   if (s != LT_OK) return s;
-  return plan_stage_two(c, frames, idx);
+  s = plan_stage_two(c, frames, idx);
+  c.desc.arr_mask = nullptr;   // copied into the plan; the caller's array is not kept
+  return s;
 }
 
 extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_desc* cams,

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, byref, c_char_p, c_double, c_int32, c_int64, c_void_p
+from ctypes import c_float, POINTER, byref, c_char_p, c_double, c_int32, c_int64, c_void_p
 
 import numpy as np
 
@@ -34,7 +34,8 @@ class lt_camera_desc(ctypes.Structure):
                 ("d_lens_mla", c_double), ("d_mla_det", c_double),
                 ("mla_ns", c_int32), ("mla_nt", c_int32), ("mla_pitch", c_double),
                 ("mla_radius", c_double), ("mla_focal", POINTER(c_double)),
-                ("arr_ns", c_int32), ("arr_nt", c_int32), ("arr_ps", c_double), ("arr_pt", c_double)]
+                ("arr_ns", c_int32), ("arr_nt", c_int32), ("arr_ps", c_double), ("arr_pt", c_double),
+                ("mla_layout", c_int32), ("arr_mask", POINTER(c_float))]
 
 
 class lt_recon_params(ctypes.Structure):
@@ -127,13 +128,17 @@ def volume_desc(vol: inputs.Volume) -> lt_volume_desc:
 def camera_desc(cam: inputs.Camera, keep: list) -> lt_camera_desc:
     d = lt_camera_desc()
     for name, _ in lt_camera_desc._fields_:
-        if name == "mla_focal":
+        if name in ("mla_focal", "arr_mask"):
             continue
         setattr(d, name, getattr(cam, name))
     if cam.mla_focal is not None:
         arr = np.ascontiguousarray(cam.mla_focal, dtype=np.float64)
         keep.append(arr)
         d.mla_focal = arr.ctypes.data_as(POINTER(c_double))
+    if getattr(cam, "arr_mask", None) is not None:
+        m = np.ascontiguousarray(cam.arr_mask, dtype=np.float32).reshape(-1)
+        keep.append(m)
+        d.arr_mask = m.ctypes.data_as(POINTER(c_float))
     return d
 
 
