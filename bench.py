@@ -54,6 +54,28 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, device):
+    """The largest x over all ranks (every rank gets it); x itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def frame_seed(rank):
+    """Seed of the frame rank `rank` reconstructs (ranks solve independent
+    problems: no data-path collective, weak scaling)."""
+    return 2000 + rank
+
+
+def job_rate(units_per_rank_step, steps, world, t_max):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time."""
+    return world * units_per_rank_step * steps / t_max
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -271,7 +293,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     vol, cam = I.config_plenoptic()
-    x_true = I.plume_field(vol, seed=2000 + rank)
+    x_true = I.plume_field(vol, seed=frame_seed(rank))
     plan = lt.Plan(vol, [cam])
     if args.no_autotune:
         tuned, tune_ms = 0, None
@@ -313,12 +335,9 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     t_dev = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3
-    t = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = max_over_ranks(t_dev, "cuda")
     samples_step = 2 * stats["ray_samples"]
-    value = world * samples_step * args.steps / t_max
+    value = job_rate(samples_step, args.steps, world, t_max)
 
     # --- per-stage device times (same stream, CUDA events, L2 flushed) ---
     fa = plan.stage1(0, xt)
@@ -384,10 +403,7 @@ def run_ours(args):
         lt.lt_recon_get(rec.handle, 0, nfr, ncam, lt._stream())   # syncs; reads gains + data fit
     torch.cuda.synchronize()
     te = time.perf_counter() - e0
-    te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * samples_step * args.e2e_steps / float(te_t.item()), "unit": UNIT,
+    e2e = {"value": job_rate(samples_step, args.e2e_steps, world, max_over_ranks(te, "cuda")), "unit": UNIT,
            "h2d_bytes_per_step": int(y_pin.numel() * 4), "d2h_bytes_per_step": int(8 * nfr * (ncam + 1)),
            "steps": args.e2e_steps,
            "path": "pinned host y -> device copy, lt_recon_set_data, lt_recon_iterate(1), lt_recon_get(gains, data fit)"}

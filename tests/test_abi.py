@@ -66,3 +66,17 @@ def test_invalid_descriptors_rejected_on_host(library):
     with pytest.raises(lt.LtError) as e:
         lt.lt_plan_sizes(None, 1)
     assert e.value.status == lt.LT_EINVAL
+
+
+def test_orientation_and_mla_fields_validated_on_host(library):
+    vol, cam = I.config_single_small()
+    nan_pitch = I.Camera(**{**cam.__dict__, "pitch": float("nan")})
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_create(vol, [nan_pitch])
+    assert e.value.status == lt.LT_EINVAL and "pitch" in str(e.value)
+    _, pc = I.config_plenoptic()
+    bad_layout = I.Camera(**{**pc.__dict__, "mla_layout": 7})
+    with pytest.raises(lt.LtError) as e:
+        lt.lt_plan_create(vol, [bad_layout])
+    assert e.value.status == lt.LT_EINVAL and "mla_layout" in str(e.value)
+
