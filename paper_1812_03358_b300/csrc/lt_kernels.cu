@@ -457,6 +457,16 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
 // per detector column/row, consecutive cells sharing their common edge), and
 // contract in two steps (the O(S+T) scheme of Sec. IV-B).
 // ---------------------------------------------------------------------------
+// Exact n / d for small operands (n * d < 2^32, d >= 2) by one multiply-high
+// with m = ceil(2^32 / d) = floor((2^32 - 1) / d) + 1: n m / 2^32 exceeds
+// n / d by less than n / 2^32 < 1 / d, which never reaches the next integer.
+// m = 2^32 does not fit for d = 1, which takes the select.
+struct SmallDiv {
+  uint32_t m, d;
+};
+__device__ __forceinline__ SmallDiv small_div(uint32_t d) { return {d > 1u ? 0xFFFFFFFFu / d + 1u : 0u, d}; }
+__device__ __forceinline__ uint32_t div_of(SmallDiv f, uint32_t n) { return f.d > 1u ? __umulhi(n, f.m) : n; }
+
 constexpr int L2_THREADS = 128;
 constexpr int L2_W = kStage2Window;
 
@@ -514,15 +524,16 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
       if (nds <= 0 || ndt <= 0) continue;   // uniform
       lenslet_weights(L, dr, cc, rr, Bs, Bt);
       const float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
+      const SmallDiv dc = small_div(nc), dd = small_div(nds), du_ = small_div(nsu);
       for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
-        const int r = o / nc, c = o - r * nc;
+        const int r = div_of(dc, o), c = o - r * nc;
         const long long px = (long long)(rr.x + r) * s2.arr_ns + cc.x + c;
         F[r][c] = __ldg(s2.owner + px) == mu ? __ldg(fk + px) : 0.0f;   // this lenslet's own pixels
       }
       __syncthreads();
       // W[r][q] = sum_c Bs[c][q] F[r][c]
       for (int o = threadIdx.x; o < nr * nds; o += blockDim.x) {
-        const int r = o / nds, q = o - r * nds;
+        const int r = div_of(dd, o), q = o - r * nds;
         float w = 0.0f;
         for (int c = 0; c < nc; ++c) w = fmaf(Bs[c][q], F[r][c], w);
         W[r][q] = w;
@@ -531,7 +542,8 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
       // Z[it][is] += scale * sum_r Bt[r][b] W[r][q]  (entries owned by one thread)
       const float scale = L->scale;
       for (int o = threadIdx.x; o < ntu * nsu; o += blockDim.x) {
-        const int b = o / nsu + du.z - dr.z, q = o % nsu + du.x - dr.x;
+        const int ob = div_of(du_, o);
+        const int b = ob + du.z - dr.z, q = o - ob * nsu + du.x - dr.x;
         if (b < 0 || b >= ndt || q < 0 || q >= nds) continue;
         float z = 0.0f;
         for (int r = 0; r < nr; ++r) z = fmaf(Bt[r][b], W[r][q], z);
@@ -596,14 +608,15 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
       continue;   // uniform
     }
     lenslet_weights(L, dr, cc, rr, Bs, Bt);
+    const SmallDiv dd = small_div(nds), dc = small_div(nc);
     for (int o = threadIdx.x; o < ndt * nds; o += blockDim.x) {
-      const int b = o / nds, q = o - b * nds;
+      const int b = div_of(dd, o), q = o - b * nds;
       Y[b][q] = __ldg(yf + (long long)(dr.z + b) * s2.det_ns + dr.x + q);
     }
     __syncthreads();
     // U[r][q] = sum_b Bt[r][b] Y[b][q]
     for (int o = threadIdx.x; o < nr * nds; o += blockDim.x) {
-      const int r = o / nds, q = o - r * nds;
+      const int r = div_of(dd, o), q = o - r * nds;
       float u = 0.0f;
       for (int b = 0; b < ndt; ++b) u = fmaf(Bt[r][b], Y[b][q], u);
       U[r][q] = u;
@@ -611,7 +624,7 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
     __syncthreads();
     const float scale = L->scale;
     for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
-      const int r = o / nc, c = o - r * nc;
+      const int r = div_of(dc, o), c = o - r * nc;
       const int jt = rr.x + r, js = cc.x + c;
       float g = 0.0f;
       for (int q = 0; q < nds; ++q) g = fmaf(Bs[c][q], U[r][q], g);
