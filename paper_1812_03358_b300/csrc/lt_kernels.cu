@@ -334,6 +334,27 @@ constexpr int AT_T = 8;
 constexpr int AT_THREADS = 256;
 constexpr int AT_UCOLS = 256;   // pixel columns of the t-contracted rows kept in shared memory
 
+// t-contraction of one voxel row (one warp): U[c] = sum_b w_b g[off_b + c_lo + c]
+// for c < ncols, lane + 32 j holding column c in a register; the (weight,
+// row offset) pair of image row b is one shared-memory broadcast.
+template <int NJ>
+__device__ __forceinline__ void adjoint_t_rows(const float* __restrict__ g, const float2* twi_row, int wit,
+                                               int ncols, float* Urow, int lane) {
+  float u[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) u[j] = 0.0f;
+  for (int b = 0; b < wit; ++b) {
+    const float2 wo = twi_row[b * AT_T];
+    const float* gr = g + __float_as_int(wo.y) + lane;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+      if (j < NJ - 1 || lane + 32 * j < ncols) u[j] = fmaf(wo.x, __ldg(gr + 32 * j), u[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < NJ; ++j)
+    if (j < NJ - 1 || lane + 32 * j < ncols) Urow[lane + 32 * j] = u[j];
+}
+
 // Gather adjoint of the batched beam integration over cameras sharing one
 // grid.  CTA = 32 x 8 voxels of one slice and frame (lane = voxel column,
 // warp = voxel row).  Per (camera, cell): all threads evaluate the windows of
@@ -347,9 +368,7 @@ __global__ void __launch_bounds__(AT_THREADS)
 beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x, long long x_fs,
                      int accumulate, int tiles_x) {
   __shared__ float sw[WIMAX][AT_S];
-  __shared__ int si[WIMAX][AT_S];
-  __shared__ float tw[WIMAX][AT_T];
-  __shared__ int ti[WIMAX][AT_T];
+  __shared__ float2 twi[WIMAX][AT_T];   // (t-weight, element offset of its image row)
   __shared__ float U[AT_T][AT_UCOLS];
 
   const int lane = threadIdx.x & 31;
@@ -358,6 +377,7 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
   const int jx0 = (blockIdx.x % tiles_x) * AT_S;
   const int jy0 = (blockIdx.x / tiles_x) * AT_T;
   const int jx1 = min(jx0 + AT_S, nx) - 1;
+  const int jx = jx0 + lane;
   const int n = blockIdx.y;
   const int frame = blockIdx.z;
 
@@ -377,25 +397,22 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
       const int c_lo = max(min(a0, a1), 0), c_hi = min(max(a0, a1) + wis - 1, ns - 1);
       const int ncols = c_hi - c_lo + 1;
       const bool sep = ncols > 0 && ncols <= AT_UCOLS;
+      const int col_off = sep ? c_lo : 0;   // image column of U / the gather's column 0
+      // first pixel column of this voxel column's window; entry q reads column i0 + q
+      const int i0 = window_start(p->s, jx);
       int flag_s = 0, flag_t = 0;
       // s windows: lane = voxel column, warp r takes window entries r, r+8, ...
-      {
-        const int jx = jx0 + lane;
-        const int i0 = window_start(p->s, jx);
-        for (int q = row; q < wis; q += AT_T) {
-          const int i = i0 + q;
-          float w = 0.0f;
-          if (i >= 0 && i < ns && jx < nx) {
-            int jc;
-            float fr;
-            footprint_centre(p->s, i, jc, fr);
-            w = cell_weight(jx - jc, fr, p->s);
-          }
-          const int ic = min(max(i, 0), ns - 1);
-          sw[q][lane] = w;
-          si[q][lane] = sep ? min(max(ic - c_lo, 0), ncols - 1) : ic;
-          flag_s |= (w != 0.0f);
+      for (int q = row; q < wis; q += AT_T) {
+        const int i = i0 + q;
+        float w = 0.0f;
+        if (i >= 0 && i < ns && jx < nx) {
+          int jc;
+          float fr;
+          footprint_centre(p->s, i, jc, fr);
+          w = cell_weight(jx - jc, fr, p->s);
         }
+        sw[q][lane] = w;
+        flag_s |= (w != 0.0f);
       }
       // t windows: thread t -> voxel row t & 7, entry t >> 3
       for (int tt = threadIdx.x; tt < AT_T * wit; tt += AT_THREADS) {
@@ -409,30 +426,37 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
           footprint_centre(p->t, i, jc, fr);
           w = cell_weight(jy - jc, fr, p->t);
         }
-        tw[q][r] = w;
-        ti[q][r] = min(max(i, 0), nt - 1) * ns;
+        twi[q][r] = make_float2(w, __int_as_float(min(max(i, 0), nt - 1) * ns + col_off));
         flag_t |= (w != 0.0f);
       }
       const int any_s = __syncthreads_or(flag_s);
       const int any_t = __syncthreads_or(flag_t);
       if (any_s && any_t) {
+        // a zero weight may pair with a clamped index; every index stays in range
         if (sep) {
-          for (int c = lane; c < ncols; c += 32) {
-            float u = 0.0f;
-            for (int b = 0; b < wit; ++b) u = fmaf(tw[b][row], __ldg(g + ti[b][row] + c_lo + c), u);
-            U[row][c] = u;
+          switch ((ncols + 31) >> 5) {
+            case 1: adjoint_t_rows<1>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            case 2: adjoint_t_rows<2>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            case 3: adjoint_t_rows<3>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            case 4: adjoint_t_rows<4>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            case 5: adjoint_t_rows<5>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            case 6: adjoint_t_rows<6>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            case 7: adjoint_t_rows<7>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            default: adjoint_t_rows<8>(g, &twi[0][row], wit, ncols, U[row], lane); break;
           }
           __syncwarp();
+          const int u0 = i0 - c_lo;
           float v = 0.0f;
-          for (int q = 0; q < wis; ++q) v = fmaf(sw[q][lane], U[row][si[q][lane]], v);
+          for (int q = 0; q < wis; ++q) v = fmaf(sw[q][lane], U[row][min(max(u0 + q, 0), ncols - 1)], v);
           acc = fmaf(p->scale, v, acc);
         } else {
           float v = 0.0f;
           for (int b = 0; b < wit; ++b) {
-            const float* gr = g + ti[b][row];
+            const float2 wo = twi[b][row];
+            const float* gr = g + __float_as_int(wo.y);
             float u = 0.0f;
-            for (int q = 0; q < wis; ++q) u = fmaf(sw[q][lane], __ldg(gr + si[q][lane]), u);
-            v = fmaf(tw[b][row], u, v);
+            for (int q = 0; q < wis; ++q) u = fmaf(sw[q][lane], __ldg(gr + min(max(i0 + q, 0), ns - 1)), u);
+            v = fmaf(wo.x, u, v);
           }
           acc = fmaf(p->scale, v, acc);
         }
@@ -440,7 +464,6 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
       __syncthreads();
     }
   }
-  const int jx = jx0 + lane;
   const int jy = jy0 + row;
   if (jx < nx && jy < ny) {
     float* o = x + (long long)frame * x_fs + ((long long)n * ny + jy) * nx + jx;
