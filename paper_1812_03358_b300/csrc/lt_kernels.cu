@@ -170,8 +170,13 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
       const int n1 = min(rs.y, rt.y);
       const SliceParam* pk = C.prm + (long long)k * nz;
       for (int nb = n0 + grp * SB; nb < n1; nb += G * SB) {
-        // phase A: weights of SB slices x (32 columns + 32 rows)
-        for (int task = gt; task < SB * (FT_S + FT_T); task += FT_GTHREADS) {
+        // phase A: weights of SB slices x (32 columns + 32 rows); a thread's
+        // tasks are independent and unrolled so that their dependent
+        // footprint arithmetic interleaves
+        static_assert(SB * (FT_S + FT_T) % FT_GTHREADS == 0, "phase A tasks per thread");
+#pragma unroll
+        for (int ta = 0; ta < SB * (FT_S + FT_T) / FT_GTHREADS; ++ta) {
+          const int task = gt + ta * FT_GTHREADS;
           const int sl = task / (FT_S + FT_T);
           const int q = task - sl * (FT_S + FT_T);
           const int n = nb + sl;
@@ -238,15 +243,24 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
               wsr[a] = sw[grp][sl][a][lane];
               sxr[a] = sx[grp][sl][a][lane];
             }
-            // rows past the volume are never referenced by B2 (clamped indices)
+            // rows past the volume are never referenced by B2 (clamped
+            // indices); the warp's rows are unrolled so that all its gathers
+            // are in flight together
             const int r_end = min(nrows_max, ny - r_lo[sl]);
-            for (int r = warp; r < r_end; r += 4) {
-              const float* xr = xs + r * nx;
-              float u = 0.0f;
+            float u[FT_TR / 4];
 #pragma unroll
-              for (int a = 0; a < W; ++a) u = fmaf(wsr[a], __ldg(xr + sxr[a]), u);
-              T[grp][sl][r][lane] = u;
+            for (int i = 0; i < FT_TR / 4; ++i) {
+              const int r = warp + 4 * i;
+              u[i] = 0.0f;
+              if (r < r_end) {
+                const float* xr = xs + r * nx;
+#pragma unroll
+                for (int a = 0; a < W; ++a) u[i] = fmaf(wsr[a], __ldg(xr + sxr[a]), u[i]);
+              }
             }
+#pragma unroll
+            for (int i = 0; i < FT_TR / 4; ++i)
+              if (warp + 4 * i < r_end) T[grp][sl][warp + 4 * i][lane] = u[i];
           }
           group_barrier(1 + grp);
           // B2: t-contraction per pixel from shared memory
