@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--warm-samples", type=int, default=1200,
                     help="training volumes for the warm-start time-to-residual measurement (0: skip)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default forward variant (fixed launch sequence, e.g. for profiling)")
+                    help="pin --forward-variant instead of tuning (fixed launch sequence, e.g. for profiling)")
+    ap.add_argument("--forward-variant", type=int, default=2,
+                    help="forward kernel variant pinned by --no-autotune (the plan's default is 2)")
     return ap.parse_args()
 
 
@@ -296,7 +298,8 @@ def run_ours(args):
     x_true = I.plume_field(vol, seed=frame_seed(rank))
     plan = lt.Plan(vol, [cam])
     if args.no_autotune:
-        tuned, tune_ms = 0, None
+        lt.lt_plan_set_forward_variant(plan.handle, args.forward_variant)
+        tuned, tune_ms = args.forward_variant, None
     else:
         tuned, tune_ms = plan.autotune()
     stats = plan.stats(0)

@@ -202,7 +202,8 @@ LT_API lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, const f
 LT_API int32_t lt_autotune_variants(void);
 LT_API lt_status lt_plan_autotune(lt_plan* plan, void* stream, double* times_ms, int32_t* chosen);
 /* Pins the forward variant (0 .. lt_autotune_variants()-1) instead of tuning;
- * every variant computes the same operator (summation order differs). */
+ * every variant computes the same operator (summation order differs).  A new
+ * plan uses variant 2 (two slices per weight batch, two warp groups). */
 LT_API lt_status lt_plan_set_forward_variant(lt_plan* plan, int32_t variant);
 
 /* Analytic work counts of one camera for one frame, computed on the host in

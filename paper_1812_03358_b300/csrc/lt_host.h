@@ -93,7 +93,7 @@ struct lt_plan {
   int n_items = 0;
   int* d_counter = nullptr;        // persistent-launch work counter
   int wclass = 2;                  // forward window class of the whole plan
-  int fwd_variant = 0;             // forward kernel variant (autotuned)
+  int fwd_variant = 2;             // forward kernel variant (autotuned; {2 slices, 2 groups} until then)
 };
 
 namespace lt {

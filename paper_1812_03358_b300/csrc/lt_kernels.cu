@@ -347,6 +347,7 @@ constexpr int AT_S = 32;
 constexpr int AT_T = 8;
 constexpr int AT_THREADS = 256;
 constexpr int AT_UCOLS = 256;   // pixel columns of the t-contracted rows kept in shared memory
+constexpr int AT_SN = 2;        // slices per CTA
 
 // t-contraction of one voxel row (one warp): U[c] = sum_b w_b g[off_b + c_lo + c]
 // for c < ncols, lane + 32 j holding column c in a register; the (weight,
@@ -392,96 +393,99 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
   const int jy0 = (blockIdx.x / tiles_x) * AT_T;
   const int jx1 = min(jx0 + AT_S, nx) - 1;
   const int jx = jx0 + lane;
-  const int n = blockIdx.y;
   const int frame = blockIdx.z;
-
-  float acc = 0.0f;
-  for (int cam = 0; cam < B.n_cams; ++cam) {
-    const BeamCam& C = B.cam[cam];
-    const int ns = C.ns, nt = C.nt;
-    const float* inf = C.in + (long long)frame * C.out_fs;
-    for (int k = 0; k < C.K; ++k) {
-      if (!cell_on(C.sub_n, C.sub_s, k)) continue;   // uniform over the CTA
-      const SliceParam* p = C.prm + (long long)k * nz + n;
-      const int wis = p->wis;
-      const int wit = p->wit;
-      const float* g = inf + (C.per_cell ? (long long)k * ns * nt : 0);
-      // pixel columns covering every voxel column's window (monotone in the voxel index)
-      const int a0 = window_start(p->s, jx0), a1 = window_start(p->s, jx1);
-      const int c_lo = max(min(a0, a1), 0), c_hi = min(max(a0, a1) + wis - 1, ns - 1);
-      const int ncols = c_hi - c_lo + 1;
-      const bool sep = ncols > 0 && ncols <= AT_UCOLS;
-      const int col_off = sep ? c_lo : 0;   // image column of U / the gather's column 0
-      // first pixel column of this voxel column's window; entry q reads column i0 + q
-      const int i0 = window_start(p->s, jx);
-      int flag_s = 0, flag_t = 0;
-      // s windows: lane = voxel column, warp r takes window entries r, r+8, ...
-      for (int q = row; q < wis; q += AT_T) {
-        const int i = i0 + q;
-        float w = 0.0f;
-        if (i >= 0 && i < ns && jx < nx) {
-          int jc;
-          float fr;
-          footprint_centre(p->s, i, jc, fr);
-          w = cell_weight(jx - jc, fr, p->s);
-        }
-        sw[q][lane] = w;
-        flag_s |= (w != 0.0f);
-      }
-      // t windows: thread t -> voxel row t & 7, entry t >> 3
-      for (int tt = threadIdx.x; tt < AT_T * wit; tt += AT_THREADS) {
-        const int r = tt & (AT_T - 1), q = tt >> 3;
-        const int jy = jy0 + r;
-        const int i = window_start(p->t, jy) + q;
-        float w = 0.0f;
-        if (i >= 0 && i < nt && jy < ny) {
-          int jc;
-          float fr;
-          footprint_centre(p->t, i, jc, fr);
-          w = cell_weight(jy - jc, fr, p->t);
-        }
-        twi[q][r] = make_float2(w, __int_as_float(min(max(i, 0), nt - 1) * ns + col_off));
-        flag_t |= (w != 0.0f);
-      }
-      const int any_s = __syncthreads_or(flag_s);
-      const int any_t = __syncthreads_or(flag_t);
-      if (any_s && any_t) {
-        // a zero weight may pair with a clamped index; every index stays in range
-        if (sep) {
-          switch ((ncols + 31) >> 5) {
-            case 1: adjoint_t_rows<1>(g, &twi[0][row], wit, ncols, U[row], lane); break;
-            case 2: adjoint_t_rows<2>(g, &twi[0][row], wit, ncols, U[row], lane); break;
-            case 3: adjoint_t_rows<3>(g, &twi[0][row], wit, ncols, U[row], lane); break;
-            case 4: adjoint_t_rows<4>(g, &twi[0][row], wit, ncols, U[row], lane); break;
-            case 5: adjoint_t_rows<5>(g, &twi[0][row], wit, ncols, U[row], lane); break;
-            case 6: adjoint_t_rows<6>(g, &twi[0][row], wit, ncols, U[row], lane); break;
-            case 7: adjoint_t_rows<7>(g, &twi[0][row], wit, ncols, U[row], lane); break;
-            default: adjoint_t_rows<8>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+  // AT_SN adjacent slices in turn: their footprints cover nearly the same
+  // image pixels, so the later slices find them in L1
+  const int n_end = min((int)blockIdx.y * AT_SN + AT_SN, nz);
+  for (int n = blockIdx.y * AT_SN; n < n_end; ++n) {
+    float acc = 0.0f;
+    for (int cam = 0; cam < B.n_cams; ++cam) {
+      const BeamCam& C = B.cam[cam];
+      const int ns = C.ns, nt = C.nt;
+      const float* inf = C.in + (long long)frame * C.out_fs;
+      for (int k = 0; k < C.K; ++k) {
+        if (!cell_on(C.sub_n, C.sub_s, k)) continue;   // uniform over the CTA
+        const SliceParam* p = C.prm + (long long)k * nz + n;
+        const int wis = p->wis;
+        const int wit = p->wit;
+        const float* g = inf + (C.per_cell ? (long long)k * ns * nt : 0);
+        // pixel columns covering every voxel column's window (monotone in the voxel index)
+        const int a0 = window_start(p->s, jx0), a1 = window_start(p->s, jx1);
+        const int c_lo = max(min(a0, a1), 0), c_hi = min(max(a0, a1) + wis - 1, ns - 1);
+        const int ncols = c_hi - c_lo + 1;
+        const bool sep = ncols > 0 && ncols <= AT_UCOLS;
+        const int col_off = sep ? c_lo : 0;   // image column of U / the gather's column 0
+        // first pixel column of this voxel column's window; entry q reads column i0 + q
+        const int i0 = window_start(p->s, jx);
+        int flag_s = 0, flag_t = 0;
+        // s windows: lane = voxel column, warp r takes window entries r, r+8, ...
+        for (int q = row; q < wis; q += AT_T) {
+          const int i = i0 + q;
+          float w = 0.0f;
+          if (i >= 0 && i < ns && jx < nx) {
+            int jc;
+            float fr;
+            footprint_centre(p->s, i, jc, fr);
+            w = cell_weight(jx - jc, fr, p->s);
           }
-          __syncwarp();
-          const int u0 = i0 - c_lo;
-          float v = 0.0f;
-          for (int q = 0; q < wis; ++q) v = fmaf(sw[q][lane], U[row][min(max(u0 + q, 0), ncols - 1)], v);
-          acc = fmaf(p->scale, v, acc);
-        } else {
-          float v = 0.0f;
-          for (int b = 0; b < wit; ++b) {
-            const float2 wo = twi[b][row];
-            const float* gr = g + __float_as_int(wo.y);
-            float u = 0.0f;
-            for (int q = 0; q < wis; ++q) u = fmaf(sw[q][lane], __ldg(gr + min(max(i0 + q, 0), ns - 1)), u);
-            v = fmaf(wo.x, u, v);
-          }
-          acc = fmaf(p->scale, v, acc);
+          sw[q][lane] = w;
+          flag_s |= (w != 0.0f);
         }
+        // t windows: thread t -> voxel row t & 7, entry t >> 3
+        for (int tt = threadIdx.x; tt < AT_T * wit; tt += AT_THREADS) {
+          const int r = tt & (AT_T - 1), q = tt >> 3;
+          const int jy = jy0 + r;
+          const int i = window_start(p->t, jy) + q;
+          float w = 0.0f;
+          if (i >= 0 && i < nt && jy < ny) {
+            int jc;
+            float fr;
+            footprint_centre(p->t, i, jc, fr);
+            w = cell_weight(jy - jc, fr, p->t);
+          }
+          twi[q][r] = make_float2(w, __int_as_float(min(max(i, 0), nt - 1) * ns + col_off));
+          flag_t |= (w != 0.0f);
+        }
+        const int any_s = __syncthreads_or(flag_s);
+        const int any_t = __syncthreads_or(flag_t);
+        if (any_s && any_t) {
+          // a zero weight may pair with a clamped index; every index stays in range
+          if (sep) {
+            switch ((ncols + 31) >> 5) {
+              case 1: adjoint_t_rows<1>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+              case 2: adjoint_t_rows<2>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+              case 3: adjoint_t_rows<3>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+              case 4: adjoint_t_rows<4>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+              case 5: adjoint_t_rows<5>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+              case 6: adjoint_t_rows<6>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+              case 7: adjoint_t_rows<7>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+              default: adjoint_t_rows<8>(g, &twi[0][row], wit, ncols, U[row], lane); break;
+            }
+            __syncwarp();
+            const int u0 = i0 - c_lo;
+            float v = 0.0f;
+            for (int q = 0; q < wis; ++q) v = fmaf(sw[q][lane], U[row][min(max(u0 + q, 0), ncols - 1)], v);
+            acc = fmaf(p->scale, v, acc);
+          } else {
+            float v = 0.0f;
+            for (int b = 0; b < wit; ++b) {
+              const float2 wo = twi[b][row];
+              const float* gr = g + __float_as_int(wo.y);
+              float u = 0.0f;
+              for (int q = 0; q < wis; ++q) u = fmaf(sw[q][lane], __ldg(gr + min(max(i0 + q, 0), ns - 1)), u);
+              v = fmaf(wo.x, u, v);
+            }
+            acc = fmaf(p->scale, v, acc);
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
-  }
-  const int jy = jy0 + row;
-  if (jx < nx && jy < ny) {
-    float* o = x + (long long)frame * x_fs + ((long long)n * ny + jy) * nx + jx;
-    *o = accumulate ? *o + acc : acc;
+    const int jy = jy0 + row;
+    if (jx < nx && jy < ny) {
+      float* o = x + (long long)frame * x_fs + ((long long)n * ny + jy) * nx + jx;
+      *o = accumulate ? *o + acc : acc;
+    }
   }
 }
 
@@ -747,7 +751,7 @@ cudaError_t launch_beam_adjoint_batched(const BeamBatch& b, float* x, long long 
   const int nx = b.cam[0].nx, ny = b.cam[0].ny, nz = b.cam[0].nz;
   const int tiles_x = (nx + AT_S - 1) / AT_S;
   const int tiles_y = (ny + AT_T - 1) / AT_T;
-  dim3 grid(tiles_x * tiles_y, nz, b.frames);
+  dim3 grid(tiles_x * tiles_y, (nz + AT_SN - 1) / AT_SN, b.frames);
   beam_adjoint_batched<<<grid, AT_THREADS, 0, st>>>(b, x, x_fs, accumulate, tiles_x);
   return cudaGetLastError();
 }
