@@ -30,6 +30,22 @@ LT_API lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const float
                               float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
                               int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, void* stream);
 
+/* lt_nn_conv3d with an explicit kernel: LT_CONV_AUTO picks one, LT_CONV_WARP_MMA
+ * is the warp-level MMA kernel (every shape), LT_CONV_TCGEN05 the tcgen05
+ * kernel (operands in shared memory, accumulators in tensor memory), which
+ * needs W a multiple of 128, H and D even and 16-byte aligned in, w and
+ * out_bf; other shapes give LT_EUNSUPPORTED on that path. */
+enum { LT_CONV_AUTO = 0, LT_CONV_WARP_MMA = 1, LT_CONV_TCGEN05 = 2 };
+LT_API lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
+                                 float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
+                                 int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, int32_t path,
+                                 void* stream);
+
+/* Synchronises the stream, then reports and clears the device status of the
+ * tcgen05 kernels: LT_OK, or LT_ETIMEOUT if a bounded wait on the tensor core
+ * gave up (that CTA's outputs were not written). */
+LT_API lt_status lt_nn_device_status(void* stream);
+
 /* Weight gradient: dw[co][tap][ci] += sum_v g[v][co] in[v + tap][ci] (float32
  * accumulate, dw must be zeroed by the caller) and db[co] += sum_v g[v][co]
  * (db may be NULL).  g has Co channels per voxel. */

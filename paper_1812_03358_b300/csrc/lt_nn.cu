@@ -10,6 +10,7 @@
 #include "lt.h"
 #include "lt_host.h"
 #include "lt_nn.h"
+#include "lt_nn_tc.h"
 
 using namespace nvcuda;
 
@@ -148,7 +149,7 @@ conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g
   __shared__ __align__(128) bf16 Gs[CT_MT * 16][MB];      // [voxel of the block][co]
   __shared__ __align__(128) bf16 halo[CT_HALO * 16];
   __shared__ __align__(128) float red[4][16][16];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int mt = warp % MT, rsel = warp / MT;
   const int n_ci = Ci / 16, n_co = Co / MB;
   const int tg = blockIdx.y % 3;                 // dz = tg - 1
@@ -408,10 +409,35 @@ static lt_status launched(const char* what) {
 extern "C" lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
                                   float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
                                   int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, void* stream) {
+  return lt_nn_conv3d_ex(in, w, b, out_bf, out_f, batch, D, H, W, Ci, Co, o_stride, o_off, relu, LT_CONV_AUTO,
+                         stream);
+}
+
+extern "C" lt_status lt_nn_device_status(void* stream) {
+  clear_error();
+  int st = 0;
+  cudaError_t e = take_tc_status(&st, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "device status");
+  if (st != 0) return set_error(LT_ETIMEOUT, "a tcgen05 convolution gave up waiting for the tensor core");
+  return LT_OK;
+}
+
+extern "C" lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
+                                     float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
+                                     int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, int32_t path,
+                                     void* stream) {
   clear_error();
   if (!in || !w || (!out_bf && !out_f) || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 ||
-      Ci % 16 || Co % 16 || o_off < 0 || o_stride < o_off + Co)
+      Ci % 16 || Co % 16 || o_off < 0 || o_stride < o_off + Co || path < LT_CONV_AUTO || path > LT_CONV_TCGEN05)
     return set_error(LT_EINVAL, "conv3d: bad arguments (channels must be multiples of 16)");
+  const bool tc_ok = conv3d_tc_supported(in, w, out_bf, D, H, W, Ci, Co);
+  if (path == LT_CONV_TCGEN05) {
+    if (!tc_ok)
+      return set_error(LT_EUNSUPPORTED, "conv3d: the tcgen05 kernel needs W %% 128 == 0, even H and D, aligned pointers");
+    const cudaError_t e = launch_conv3d_tc(in, w, b, out_bf, out_f, batch, D, H, W, Ci, Co, o_stride, o_off, relu,
+                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? LT_OK : cuda_error(e, "conv3d (tcgen05)");
+  }
   const int nb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
   const int tx = (W + CT_X - 1) / CT_X, ty = (H + CT_Y - 1) / CT_Y, tz = (D + CT_Z - 1) / CT_Z;
   const long long tiles = (long long)tx * ty * tz;

@@ -1,0 +1,307 @@
+// 3x3x3 convolution of the warm-start U-Net on the fifth-generation tensor
+// cores (tcgen05): bfloat16 operands in shared memory, float32 accumulators
+// in tensor memory (TMEM).  Used for volumes whose x extent is a multiple of
+// 128 (the full-resolution level of the network), the warp-level MMA kernel
+// of lt_nn.cu for the rest.
+//
+// A CTA owns a 128 (x) x 2 (y) x 2 (z) block of output voxels -- four
+// M = 128 tiles, one x run each -- and N = 16 or 32 output channels.  Per
+// chunk of 16 input channels it stages the input halo (130 x 4 x 4 voxels)
+// and the 27 taps' weights in shared memory, in the canonical K-major layout
+// without swizzle: 8 (voxels or output channels) x 8 channels of 16 bytes
+// form one 128-byte core matrix, consecutive x voxels are 16 bytes apart.  A
+// tap (dz, dy, dx) of a tile is then a descriptor whose start moves by whole
+// voxels, and one thread issues the 4 x 27 MMAs (M 128, N, K 16) of a chunk
+// back to back into the tile's TMEM columns; a commit to an mbarrier tells the
+// CTA when the tensor core is done with the staged data.  The epilogue reads
+// the accumulators with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e.
+// x voxels 32w..32w+31 of every tile), adds the bias, applies ReLU and stores.
+//
+// Every wait on the mbarrier is bounded; a wait that gives up records
+// LT_ETIMEOUT in a device status word (lt_nn_device_status), skips the rest
+// of the CTA's work and still frees its TMEM.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "lt.h"
+#include "lt_host.h"
+#include "lt_nn.h"
+#include "lt_nn_tc.h"
+
+namespace lt {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int TC_M = 128;                  // x voxels per tile (MMA rows)
+constexpr int TC_RY = 2, TC_RZ = 2;        // output rows per CTA
+constexpr int TC_TILES = TC_RY * TC_RZ;
+constexpr int TC_HX = TC_M + 2, TC_HY = TC_RY + 2, TC_HZ = TC_RZ + 2;
+constexpr int TC_THREADS = 128;            // 4 warps = the 128 TMEM lanes
+constexpr int TC_ROW = TC_HX * 16;         // bytes of one (hz, hy, channel group) halo row
+constexpr int TC_HALO = TC_HZ * TC_HY * 2 * TC_ROW;
+// Guard bytes after the halo and the weights: with them, a descriptor read
+// under either assignment of the two byte offsets stays inside the
+// allocation.
+constexpr int TC_GUARD_A = 32768, TC_GUARD_B = 8192;
+constexpr long long kWaitLimit = 1LL << 24;   // mbarrier polls (with 64 ns back-off) before giving up
+
+template <int N>
+__host__ __device__ constexpr int tc_weight_bytes() { return 27 * 2 * N * 16; }
+template <int N>
+__host__ __device__ constexpr int tc_smem_bytes() { return TC_HALO + TC_GUARD_A + tc_weight_bytes<N>() + TC_GUARD_B + 16; }
+
+__device__ int g_tc_status;   // LT_ETIMEOUT after a bounded wait gave up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading (K)
+// byte offset between core matrices, stride (M/N) byte offset between 8-row
+// groups, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(lbo >> 4) << 16) |
+         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: float32 accumulator, bfloat16 A and B,
+// both K-major, N >> 3 and M >> 4 in their fields.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for phase `parity` of the mbarrier.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// D[tmem] (+)= A[smem] x B[smem]^T, one M x N x 16 bfloat16 step.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// The mbarrier completes a phase once every MMA this thread issued is done.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// 16 consecutive float32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int N>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
+                 bf16* __restrict__ out_bf, float* __restrict__ out_f, int D, int H, int W, int Ci, int Co,
+                 int o_stride, int o_off, int relu, int tiles_x, int tiles_y, int vec_store) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* halo = tc_smem;                                   // [hz][hy][cg][hx][8] bf16
+  unsigned char* wts = tc_smem + TC_HALO + TC_GUARD_A;             // [tap][cg][co][8] bf16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(wts + tc_weight_bytes<N>() + TC_GUARD_B);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  constexpr uint32_t kCols = TC_TILES * N;   // 64 or 128 TMEM columns: a power of two >= 32
+  constexpr uint32_t kIdesc = mma_idesc(TC_M, N);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bx = blockIdx.x % tiles_x;
+  const int rest = blockIdx.x / tiles_x;
+  const int by = rest % tiles_y, bz = rest / tiles_y;
+  const int x0 = bx * TC_M, y0 = by * TC_RY, z0 = bz * TC_RZ;
+  const int n0 = blockIdx.y * N;
+  const int b = blockIdx.z;
+  const long long V = (long long)D * H * W;
+  const bf16* inb = in + (long long)b * V * Ci;
+  const uint32_t bar = smem_u32(mbar);
+
+  if (warp == 0) tmem_alloc(smem_u32(tslot), kCols);
+  if (tid == 0) mbar_init(bar);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  const int chunks = Ci / 16;
+  bool ok = true;
+  for (int c = 0; c < chunks && ok; ++c) {
+    if (c > 0) {   // the tensor core has finished reading the previous chunk's tiles
+      ok = __syncthreads_and(mbar_wait(bar, (c - 1) & 1));
+      if (!ok) break;
+    }
+    for (int t = tid; t < TC_HZ * TC_HY * TC_HX * 2; t += TC_THREADS) {
+      const int cg = t & 1, v = t >> 1;
+      const int hx = v % TC_HX, r = v / TC_HX;
+      const int hy = r % TC_HY, hz = r / TC_HY;
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
+        val = *reinterpret_cast<const uint4*>(inb + (((long long)gz * H + gy) * W + gx) * Ci + c * 16 + cg * 8);
+      *reinterpret_cast<uint4*>(halo + ((hz * TC_HY + hy) * 2 + cg) * TC_ROW + hx * 16) = val;
+    }
+    for (int t = tid; t < 27 * 2 * N; t += TC_THREADS) {
+      const int co = t % N, r = t / N;
+      const int cg = r & 1, tap = r >> 1;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (n0 + co < Co)
+        val = *reinterpret_cast<const uint4*>(w + ((long long)(n0 + co) * 27 + tap) * Ci + c * 16 + cg * 8);
+      *reinterpret_cast<uint4*>(wts + ((tap * 2 + cg) * N + co) * 16) = val;
+    }
+    fence_async_smem();   // make these generic-proxy writes visible to the tensor core
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t h0 = smem_u32(halo), w0 = smem_u32(wts);
+      for (int m = 0; m < TC_TILES; ++m) {
+        const int ry = m % TC_RY, rz = m / TC_RY;
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+          const uint32_t a = h0 + ((rz + dz + 1) * TC_HY + (ry + dy + 1)) * 2 * TC_ROW + (dx + 1) * 16;
+          const uint32_t bw = w0 + tap * 2 * N * 16;
+          mma_bf16(tbase + m * N, smem_desc(a, TC_ROW, 128), smem_desc(bw, N * 16, 128), kIdesc,
+                   (c > 0 || tap > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(bar);
+    }
+  }
+  if (ok) ok = __syncthreads_and(mbar_wait(bar, (chunks - 1) & 1));
+  tc_fence_after();
+  if (ok) {
+    for (int m = 0; m < TC_TILES; ++m) {
+      const int ry = m % TC_RY, rz = m / TC_RY;
+      const int gx = x0 + warp * 32 + lane, gy = y0 + ry, gz = z0 + rz;
+      const long long o = ((long long)b * V + ((long long)gz * H + gy) * W + gx) * o_stride + o_off + n0;
+#pragma unroll
+      for (int j = 0; j < N / 16; ++j) {
+        float v[16];
+        tmem_ld16(tbase + (static_cast<uint32_t>(warp * 32) << 16) + m * N + j * 16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          v[i] += bias ? __ldg(bias + n0 + j * 16 + i) : 0.0f;
+          if (relu) v[i] = fmaxf(v[i], 0.0f);
+        }
+        if (out_bf) {
+          if (vec_store) {
+            uint4 p[2];
+            __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(p);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            uint4* dst = reinterpret_cast<uint4*>(out_bf + o + j * 16);
+            dst[0] = p[0];
+            dst[1] = p[1];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) out_bf[o + j * 16 + i] = __float2bfloat16_rn(v[i]);
+          }
+        }
+        if (out_f) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) out_f[o + j * 16 + i] = v[i];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_tc_status, (int)LT_ETIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, kCols);
+}
+
+}  // namespace
+
+bool conv3d_tc_supported(const void* in, const void* w, const void* out_bf, int D, int H, int W, int Ci, int Co) {
+  const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  return W > 0 && W % TC_M == 0 && H > 0 && H % TC_RY == 0 && D > 0 && D % TC_RZ == 0 && Ci > 0 && Ci % 16 == 0 &&
+         Co > 0 && Co % 16 == 0 && al16(in) && al16(w) && al16(out_bf);
+}
+
+cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf, float* out_f,
+                             int batch, int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu,
+                             cudaStream_t st) {
+  const int nb = Co % 32 == 0 ? 32 : 16;
+  const int tx = W / TC_M, ty = H / TC_RY, tz = D / TC_RZ;
+  const long long tiles = (long long)tx * ty * tz;
+  if (tiles > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc_smem_bytes<32>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(conv3d_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc_smem_bytes<16>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  // 16-byte bfloat16 stores need every voxel's channel run on a 16-byte boundary
+  const int vec = (o_stride % 8 == 0 && o_off % 8 == 0) ? 1 : 0;
+  dim3 grid((unsigned)tiles, Co / nb, batch);
+  const bf16* i_ = reinterpret_cast<const bf16*>(in);
+  const bf16* w_ = reinterpret_cast<const bf16*>(w);
+  bf16* o_ = reinterpret_cast<bf16*>(out_bf);
+  if (nb == 32)
+    conv3d_tc_kernel<32><<<grid, TC_THREADS, tc_smem_bytes<32>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co,
+                                                                         o_stride, o_off, relu, tx, ty, vec);
+  else
+    conv3d_tc_kernel<16><<<grid, TC_THREADS, tc_smem_bytes<16>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co,
+                                                                         o_stride, o_off, relu, tx, ty, vec);
+  return cudaGetLastError();
+}
+
+cudaError_t take_tc_status(int* status, cudaStream_t st) {
+  const int zero = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(status, g_tc_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int));
+  return e;
+}
+
+}  // namespace lt

@@ -1,0 +1,22 @@
+// Host entry points of the tcgen05 convolution (lt_nn_tc.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lt {
+
+// Shapes (and 16-byte aligned pointers) the tcgen05 kernel tiles exactly:
+// W a multiple of 128, H and D even, channel counts multiples of 16.
+bool conv3d_tc_supported(const void* in, const void* w, const void* out_bf, int D, int H, int W, int Ci, int Co);
+
+// Same operation and layouts as lt_nn_conv3d.
+cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf, float* out_f,
+                             int batch, int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu,
+                             cudaStream_t st);
+
+// Reads and clears the device status word of the tcgen05 kernels (0, or
+// LT_ETIMEOUT after a bounded wait gave up); synchronises the stream.
+cudaError_t take_tc_status(int* status, cudaStream_t st);
+
+}  // namespace lt

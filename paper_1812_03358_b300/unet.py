@@ -25,6 +25,9 @@ from . import lt
 _SIGS = {
     "lt_nn_conv3d": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
                      c_int32, c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_conv3d_ex": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
+                        c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_device_status": [c_void_p],
     "lt_nn_conv3d_wgrad": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
                            c_void_p],
     "lt_nn_conv3d_flip": [c_void_p, c_void_p, c_int32, c_int32, c_void_p],
@@ -117,7 +120,17 @@ def _need(t, n, what):
         raise ValueError(f"{what}: {t.numel()} elements, the layer needs {n}")
 
 
-def conv3d(inp, w, b, out_bf=None, out_f=None, *, Ci, Co, dims, o_stride=None, o_off=0, relu=True):
+CONV_AUTO, CONV_WARP_MMA, CONV_TCGEN05 = 0, 1, 2   # lt_nn_conv3d_ex kernel choice
+
+
+def device_status():
+    """Raises LtError if a tcgen05 kernel gave up waiting for the tensor core
+    (synchronises the stream; clears the status)."""
+    _call("lt_nn_device_status", _s())
+
+
+def conv3d(inp, w, b, out_bf=None, out_f=None, *, Ci, Co, dims, o_stride=None, o_off=0, relu=True,
+           path=CONV_AUTO):
     D, H, W = dims
     V = D * H * W
     _need(inp, V * Ci, "conv3d input")
@@ -127,8 +140,8 @@ def conv3d(inp, w, b, out_bf=None, out_f=None, *, Ci, Co, dims, o_stride=None, o
     _need(out_f, V * (o_stride or Co), "conv3d output")
     if inp.numel() != V * Ci:
         raise ValueError("conv3d input shape does not match dims x Ci")
-    _call("lt_nn_conv3d", _p(inp), _p(w), _p(b), _p(out_bf), _p(out_f), 1, D, H, W, Ci, Co,
-          o_stride or Co, o_off, int(relu), _s())
+    _call("lt_nn_conv3d_ex", _p(inp), _p(w), _p(b), _p(out_bf), _p(out_f), 1, D, H, W, Ci, Co,
+          o_stride or Co, o_off, int(relu), int(path), _s())
 
 
 def conv3d_wgrad(inp, g, dw, db, *, Ci, Co, dims):

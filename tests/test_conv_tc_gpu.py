@@ -1,0 +1,90 @@
+"""tcgen05 convolution (operands in shared memory, accumulators in tensor
+memory) against a float64 PyTorch convolution of the same bfloat16 operands
+on the host, and against the warp-level MMA kernel.
+
+The reference is the plain definition of the layer: a 3x3x3 cross-correlation
+with zero padding 1, out[v][co] = b[co] + sum_{tap, ci} w[co][tap][ci]
+in[v + tap][ci], tap = (dz+1)*9 + (dy+1)*3 + (dx+1).  bfloat16 products are
+exact in float32, so the only difference is the float32 summation order of
+27 Ci terms: relative L2 error below 1e-5 on the float32 output, and the
+bfloat16 output within one bfloat16 rounding (2^-8 relative) of it.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1812_03358_b300 import lt
+from paper_1812_03358_b300 import unet as U
+
+pytestmark = pytest.mark.gpu
+
+
+def _operands(D, H, W, Ci, Co, seed):
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn(D * H * W * Ci, generator=g).to(torch.bfloat16)
+    w = (0.1 * torch.randn(Co * 27 * Ci, generator=g)).to(torch.bfloat16)
+    b = 0.1 * torch.randn(Co, generator=g)
+    return x, w, b
+
+
+def _reference(x, w, b, D, H, W, Ci, Co, relu):
+    xt = x.double().reshape(1, D, H, W, Ci).permute(0, 4, 1, 2, 3)
+    wt = w.double().reshape(Co, 3, 3, 3, Ci).permute(0, 4, 1, 2, 3)
+    y = torch.nn.functional.conv3d(xt, wt, b.double(), padding=1)
+    if relu:
+        y = torch.relu(y)
+    return y.permute(0, 2, 3, 4, 1).reshape(D * H * W, Co)
+
+
+def _run(path, x, w, b, D, H, W, Ci, Co, relu, o_stride=None, o_off=0):
+    V = D * H * W
+    os_ = o_stride or Co
+    out_f = torch.full((V * os_,), 7.0, device="cuda")
+    out_b = torch.full((V * os_,), 7.0, device="cuda", dtype=torch.bfloat16)
+    U.conv3d(x.cuda(), w.cuda(), b.cuda(), out_b, out_f, Ci=Ci, Co=Co, dims=(D, H, W), o_stride=o_stride,
+             o_off=o_off, relu=relu, path=path)
+    U.device_status()
+    return out_f.reshape(V, os_).cpu(), out_b.reshape(V, os_).float().cpu()
+
+
+CASES = [  # (D, H, W, Ci, Co, relu)
+    (2, 2, 128, 16, 16, False),
+    (4, 6, 128, 32, 16, True),
+    (2, 4, 256, 16, 32, False),
+    (6, 2, 128, 48, 64, True),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[:5])) + ("-relu" if c[5] else ""))
+def test_tcgen05_conv_matches_reference(case):
+    D, H, W, Ci, Co, relu = case
+    x, w, b = _operands(D, H, W, Ci, Co, seed=D * 100 + Ci)
+    ref = _reference(x, w, b, D, H, W, Ci, Co, relu)
+    yf, yb = _run(U.CONV_TCGEN05, x, w, b, D, H, W, Ci, Co, relu)
+    err = float((yf.double() - ref).norm() / ref.norm())
+    assert err < 1e-5, err
+    assert torch.all((yb.double() - yf.double()).abs() <= 2.0 ** -8 * yf.double().abs() + 1e-30)
+
+
+def test_tcgen05_conv_writes_only_its_channel_slice():
+    D, H, W, Ci, Co = 2, 2, 128, 16, 16
+    x, w, b = _operands(D, H, W, Ci, Co, seed=5)
+    ref = _reference(x, w, b, D, H, W, Ci, Co, True)
+    yf, yb = _run(U.CONV_TCGEN05, x, w, b, D, H, W, Ci, Co, True, o_stride=48, o_off=16)
+    assert torch.all(yf[:, :16] == 7.0) and torch.all(yf[:, 32:] == 7.0)
+    assert torch.all(yb[:, :16] == 7.0) and torch.all(yb[:, 32:] == 7.0)
+    assert float((yf[:, 16:32].double() - ref).norm() / ref.norm()) < 1e-5
+
+
+def test_tcgen05_and_warp_mma_kernels_agree():
+    D, H, W, Ci, Co = 2, 4, 128, 32, 32
+    x, w, b = _operands(D, H, W, Ci, Co, seed=9)
+    a, _ = _run(U.CONV_TCGEN05, x, w, b, D, H, W, Ci, Co, True)
+    c, _ = _run(U.CONV_WARP_MMA, x, w, b, D, H, W, Ci, Co, True)
+    assert float((a - c).norm() / c.norm()) < 1e-5
+
+
+def test_tcgen05_conv_rejects_shapes_it_cannot_tile():
+    x, w, b = _operands(2, 2, 64, 16, 16, seed=3)
+    with pytest.raises(lt.LtError):
+        _run(U.CONV_TCGEN05, x, w, b, 2, 2, 64, 16, 16, False)

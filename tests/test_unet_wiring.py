@@ -19,7 +19,7 @@ def test_forward_backward_shapes(monkeypatch):
     gi = net.backward(torch.zeros_like(out))
     assert gi.shape == (16, 16, 16, 16)
     # one forward conv per layer, one weight gradient and one data gradient each
-    assert calls.count("lt_nn_conv3d") == 2 * 15 and calls.count("lt_nn_conv3d_wgrad") == 15
+    assert calls.count("lt_nn_conv3d_ex") == 2 * 15 and calls.count("lt_nn_conv3d_wgrad") == 15
     with pytest.raises(ValueError):
         unet.conv3d(torch.zeros(10, dtype=torch.bfloat16), net.head.wb, None, torch.zeros(10, dtype=torch.bfloat16),
                     Ci=16, Co=16, dims=(2, 2, 2))
