@@ -30,7 +30,8 @@ LT_API lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const float
                               float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
                               int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, void* stream);
 
-/* lt_nn_conv3d with an explicit kernel: LT_CONV_AUTO picks one, LT_CONV_WARP_MMA
+/* lt_nn_conv3d with an explicit kernel: LT_CONV_AUTO takes the tcgen05 kernel
+ * wherever it applies and the warp-level MMA kernel elsewhere, LT_CONV_WARP_MMA
  * is the warp-level MMA kernel (every shape), LT_CONV_TCGEN05 the tcgen05
  * kernel (operands in shared memory, accumulators in tensor memory), which
  * needs W a multiple of 128, H and D even and 16-byte aligned in, w and

@@ -5,7 +5,7 @@
 // of lt_nn.cu for the rest.
 //
 // A CTA owns a 128 (x) x 2 (y) x 2 (z) block of output voxels -- four
-// M = 128 tiles, one x run each -- and N = 16 or 32 output channels.  Per
+// M = 128 tiles, one x run each -- and N = 16, 32 or 48 output channels.  Per
 // chunk of 16 input channels it stages the input halo (130 x 4 x 4 voxels)
 // and the 27 taps' weights in shared memory, in the canonical K-major layout
 // without swizzle: 8 (voxels or output channels) x 8 channels of 16 bytes
@@ -41,10 +41,9 @@ constexpr int TC_HX = TC_M + 2, TC_HY = TC_RY + 2, TC_HZ = TC_RZ + 2;
 constexpr int TC_THREADS = 128;            // 4 warps = the 128 TMEM lanes
 constexpr int TC_ROW = TC_HX * 16;         // bytes of one (hz, hy, channel group) halo row
 constexpr int TC_HALO = TC_HZ * TC_HY * 2 * TC_ROW;
-// Guard bytes after the halo and the weights: with them, a descriptor read
-// under either assignment of the two byte offsets stays inside the
-// allocation.
-constexpr int TC_GUARD_A = 32768, TC_GUARD_B = 8192;
+// Guard bytes after the halo and the weights (none: every descriptor read
+// ends inside its buffer, the halo's exactly at its last byte).
+constexpr int TC_GUARD_A = 0, TC_GUARD_B = 0;
 constexpr long long kWaitLimit = 1LL << 24;   // mbarrier polls (with 64 ns back-off) before giving up
 
 template <int N>
@@ -124,6 +123,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+// 16-byte global -> shared copy that does not pass through registers; with
+// valid == false it writes zeros and reads nothing (src must still be a
+// mapped address).  All of a thread's copies are in flight together until
+// cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // 16 consecutive float32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -148,7 +157,9 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
   unsigned char* wts = tc_smem + TC_HALO + TC_GUARD_A;             // [tap][cg][co][8] bf16
   uint64_t* mbar = reinterpret_cast<uint64_t*>(wts + tc_weight_bytes<N>() + TC_GUARD_B);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  constexpr uint32_t kCols = TC_TILES * N;   // 64 or 128 TMEM columns: a power of two >= 32
+  // TMEM columns: TC_TILES x N rounded up to a power of two (64, 128, 256)
+  constexpr uint32_t kCols = TC_TILES * N <= 64 ? 64 : TC_TILES * N <= 128 ? 128 : 256;
+  static_assert(N % 16 == 0 && N <= 64 && TC_TILES * N <= 256, "tcgen05 tile width");
   constexpr uint32_t kIdesc = mma_idesc(TC_M, N);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -176,37 +187,44 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
       ok = __syncthreads_and(mbar_wait(bar, (c - 1) & 1));
       if (!ok) break;
     }
+    // halo (zero outside the volume) and weights of this chunk, all copies in flight at once
     for (int t = tid; t < TC_HZ * TC_HY * TC_HX * 2; t += TC_THREADS) {
       const int cg = t & 1, v = t >> 1;
       const int hx = v % TC_HX, r = v / TC_HX;
       const int hy = r % TC_HY, hz = r / TC_HY;
       const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
-        val = *reinterpret_cast<const uint4*>(inb + (((long long)gz * H + gy) * W + gx) * Ci + c * 16 + cg * 8);
-      *reinterpret_cast<uint4*>(halo + ((hz * TC_HY + hy) * 2 + cg) * TC_ROW + hx * 16) = val;
+      const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
+      const bf16* src = inside ? inb + (((long long)gz * H + gy) * W + gx) * Ci + c * 16 + cg * 8 : inb;
+      cp_async16(smem_u32(halo + ((hz * TC_HY + hy) * 2 + cg) * TC_ROW + hx * 16), src, inside);
     }
     for (int t = tid; t < 27 * 2 * N; t += TC_THREADS) {
       const int co = t % N, r = t / N;
       const int cg = r & 1, tap = r >> 1;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (n0 + co < Co)
-        val = *reinterpret_cast<const uint4*>(w + ((long long)(n0 + co) * 27 + tap) * Ci + c * 16 + cg * 8);
-      *reinterpret_cast<uint4*>(wts + ((tap * 2 + cg) * N + co) * 16) = val;
+      const bool inside = n0 + co < Co;
+      const bf16* src = inside ? w + ((long long)(n0 + co) * 27 + tap) * Ci + c * 16 + cg * 8 : w;
+      cp_async16(smem_u32(wts + ((tap * 2 + cg) * N + co) * 16), src, inside);
     }
-    fence_async_smem();   // make these generic-proxy writes visible to the tensor core
+    cp_async_wait_all();
+    fence_async_smem();   // make these writes visible to the tensor core (async proxy)
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t h0 = smem_u32(halo), w0 = smem_u32(wts);
-      for (int m = 0; m < TC_TILES; ++m) {
-        const int ry = m % TC_RY, rz = m / TC_RY;
-        for (int tap = 0; tap < 27; ++tap) {
+      // Descriptors differ only in the start-address field (bits 0-13, in
+      // 16-byte units; every address here is below 256 KB), so each MMA's is
+      // a base descriptor plus a compile-time offset.
+      const uint64_t a0 = smem_desc(smem_u32(halo), TC_ROW, 128);
+      const uint64_t b0 = smem_desc(smem_u32(wts), N * 16, 128);
+      // taps outer, tiles inner: consecutive MMAs go to different
+      // accumulators and do not wait for one another's results
+#pragma unroll
+      for (int tap = 0; tap < 27; ++tap) {
+#pragma unroll
+        for (int m = 0; m < TC_TILES; ++m) {
+          const int ry = m % TC_RY, rz = m / TC_RY;
           const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-          const uint32_t a = h0 + ((rz + dz + 1) * TC_HY + (ry + dy + 1)) * 2 * TC_ROW + (dx + 1) * 16;
-          const uint32_t bw = w0 + tap * 2 * N * 16;
-          mma_bf16(tbase + m * N, smem_desc(a, TC_ROW, 128), smem_desc(bw, N * 16, 128), kIdesc,
-                   (c > 0 || tap > 0) ? 1u : 0u);
+          const uint32_t a_off = ((rz + dz + 1) * TC_HY + (ry + dy + 1)) * 2 * TC_ROW + (dx + 1) * 16;
+          const uint32_t b_off = tap * 2 * N * 16;
+          mma_bf16(tbase + m * N, a0 + (a_off >> 4), b0 + (b_off >> 4), kIdesc, (c > 0 || tap > 0) ? 1u : 0u);
         }
       }
       mma_commit(bar);
@@ -267,14 +285,19 @@ bool conv3d_tc_supported(const void* in, const void* w, const void* out_bf, int 
 cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf, float* out_f,
                              int batch, int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu,
                              cudaStream_t st) {
-  const int nb = Co % 32 == 0 ? 32 : 16;
+  // the widest N that divides Co: the MMA count per output tile does not
+  // depend on N (each MMA's time is set by reading its 128 x 16 A tile)
+  const int nb = Co % 48 == 0 ? 48 : Co % 32 == 0 ? 32 : 16;
   const int tx = W / TC_M, ty = H / TC_RY, tz = D / TC_RZ;
   const long long tiles = (long long)tx * ty * tz;
   if (tiles > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc_smem_bytes<32>());
+    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc_smem_bytes<48>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(conv3d_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc_smem_bytes<32>());
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(conv3d_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                tc_smem_bytes<16>());
@@ -287,7 +310,10 @@ cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float*
   const bf16* i_ = reinterpret_cast<const bf16*>(in);
   const bf16* w_ = reinterpret_cast<const bf16*>(w);
   bf16* o_ = reinterpret_cast<bf16*>(out_bf);
-  if (nb == 32)
+  if (nb == 48)
+    conv3d_tc_kernel<48><<<grid, TC_THREADS, tc_smem_bytes<48>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co,
+                                                                         o_stride, o_off, relu, tx, ty, vec);
+  else if (nb == 32)
     conv3d_tc_kernel<32><<<grid, TC_THREADS, tc_smem_bytes<32>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co,
                                                                          o_stride, o_off, relu, tx, ty, vec);
   else

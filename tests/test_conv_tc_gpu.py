@@ -52,6 +52,8 @@ CASES = [  # (D, H, W, Ci, Co, relu)
     (4, 6, 128, 32, 16, True),
     (2, 4, 256, 16, 32, False),
     (6, 2, 128, 48, 64, True),
+    (2, 2, 128, 16, 48, False),
+    (4, 2, 128, 32, 96, True),
 ]
 
 
