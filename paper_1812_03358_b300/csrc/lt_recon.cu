@@ -24,7 +24,7 @@ struct Scalars {
 };
 
 constexpr int RED_BLOCKS = 148;
-constexpr int RED_THREADS = 256;
+constexpr int RED_THREADS = 1024;   // 32 warps per SM: the reductions are latency-bound
 
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -108,28 +108,32 @@ residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const 
 // values slide through three shared-memory planes of (8 + 2) x (32 + 2)
 // (one-voxel halo, zero outside the volume), so each z value is read from
 // memory about 1.7 times instead of 27; neighbours outside the volume drop
-// out of the sum through per-axis validity masks (no branches).
+// out of the sum through per-axis validity masks (no branches).  The walk is
+// software-pipelined: while slice k is computed, the plane of slice k + 2
+// and the voxel's D, g, x of slice k + 1 are already on their way into
+// registers, so memory latency overlaps the 26-neighbour arithmetic.
 constexpr int UPD_TX = 32, UPD_TY = 8, UPD_ZB = 8;
 constexpr int UPD_PX = UPD_TX + 2, UPD_PY = UPD_TY + 2;
+constexpr int UPD_PLANE = UPD_PX * UPD_PY;            // 340 values
+constexpr int UPD_THREADS = UPD_TX * UPD_TY;          // 256: at most two plane values per thread
+static_assert(UPD_PLANE <= 2 * UPD_THREADS, "plane slots per thread");
 
-__device__ __forceinline__ void load_plane(float* __restrict__ dst, const float* __restrict__ zf, int kz, int x0,
-                                           int y0, int nx, int ny, int nz, int tid) {
-  for (int i = tid; i < UPD_PX * UPD_PY; i += UPD_TX * UPD_TY) {
-    const int ly = i / UPD_PX, lx = i - ly * UPD_PX;
-    const int gy = y0 + ly - 1, gx = x0 + lx - 1;
-    float v = 0.0f;
-    if (kz >= 0 && kz < nz && gy >= 0 && gy < ny && gx >= 0 && gx < nx)
-      v = zf[((long long)kz * ny + gy) * nx + gx];
-    dst[i] = v;
-  }
+// Plane value i (0 <= i < UPD_PLANE) of slice kz: z at the halo position, 0 outside the volume.
+__device__ __forceinline__ float plane_value(const float* __restrict__ zf, int i, int kz, int x0, int y0, int nx,
+                                             int ny, int nz) {
+  const int ly = i / UPD_PX, lx = i - ly * UPD_PX;
+  const int gy = y0 + ly - 1, gx = x0 + lx - 1;
+  if (i < UPD_PLANE && kz >= 0 && kz < nz && gy >= 0 && gy < ny && gx >= 0 && gx < nx)
+    return __ldg(zf + ((long long)kz * ny + gy) * nx + gx);
+  return 0.0f;
 }
 
-__global__ void __launch_bounds__(UPD_TX * UPD_TY)
+__global__ void __launch_bounds__(UPD_THREADS)
 update_kernel(float* __restrict__ x, const float* __restrict__ z, float* __restrict__ zn,
               const float* __restrict__ g, const float* __restrict__ D, int nx, int ny, int nz,
               long long nvox, float beta, float nu, int psi, float inv_delta, float sbeta,
               const Scalars* __restrict__ sc) {
-  __shared__ float pl[3][UPD_PY * UPD_PX];
+  __shared__ float pl[3][UPD_PLANE];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * UPD_TX + tx;
   const int nzb = (nz + UPD_ZB - 1) / UPD_ZB;
   const int f = blockIdx.z / nzb;
@@ -142,22 +146,48 @@ update_kernel(float* __restrict__ x, const float* __restrict__ z, float* __restr
   const bool vy[3] = {iy > 0, true, iy + 1 < ny};
   const bool vx[3] = {ix > 0, true, ix + 1 < nx};
   const float mom = (float)sc->mom;
-  if (reg_on) {
-    load_plane(pl[0], zf, z0 - 1, x0, y0, nx, ny, nz, tid);
-    load_plane(pl[1], zf, z0, x0, y0, nx, ny, nz, tid);
+  const int kend = min(UPD_ZB, nz - z0);   // slices of this CTA (>= 1)
+  const int i0 = tid, i1 = tid + UPD_THREADS;
+  // voxel (ix, iy, z0 + k): index, and its D, g, x loaded one slice ahead
+  const auto vidx = [&](int k) { return (long long)f * nvox + ((long long)(z0 + k) * ny + iy) * nx + ix; };
+  float dn = 0.0f, gn = 0.0f, xn_ = 0.0f, zcn = 0.0f;
+  if (inside) {
+    const long long jf = vidx(0);
+    dn = __ldg(D + jf);
+    gn = __ldg(g + jf);
+    xn_ = x[jf];
+    if (!reg_on) zcn = __ldg(z + jf);
   }
-  for (int k = 0; k < UPD_ZB; ++k) {
+  float q0 = 0.0f, q1 = 0.0f;   // plane of slice z0 + k + 1, staged for the next store
+  if (reg_on) {
+    pl[0][i0] = plane_value(zf, i0, z0 - 1, x0, y0, nx, ny, nz);
+    if (i1 < UPD_PLANE) pl[0][i1] = plane_value(zf, i1, z0 - 1, x0, y0, nx, ny, nz);
+    pl[1][i0] = plane_value(zf, i0, z0, x0, y0, nx, ny, nz);
+    if (i1 < UPD_PLANE) pl[1][i1] = plane_value(zf, i1, z0, x0, y0, nx, ny, nz);
+    q0 = plane_value(zf, i0, z0 + 1, x0, y0, nx, ny, nz);
+    q1 = plane_value(zf, i1, z0 + 1, x0, y0, nx, ny, nz);
+  }
+  for (int k = 0; k < kend; ++k) {
     const int iz = z0 + k;
-    if (iz >= nz) break;   // uniform over the CTA
+    const float dv = dn, gv = gn, xv = xn_, zv = zcn;
     if (reg_on) {
-      load_plane(pl[(k + 2) % 3], zf, iz + 1, x0, y0, nx, ny, nz, tid);
-      __syncthreads();
+      pl[(k + 2) % 3][i0] = q0;   // plane iz + 1
+      if (i1 < UPD_PLANE) pl[(k + 2) % 3][i1] = q1;
+      q0 = plane_value(zf, i0, iz + 2, x0, y0, nx, ny, nz);
+      q1 = plane_value(zf, i1, iz + 2, x0, y0, nx, ny, nz);
     }
+    if (inside && k + 1 < kend) {   // next slice's operands
+      const long long jn = vidx(k + 1);
+      dn = __ldg(D + jn);
+      gn = __ldg(g + jn);
+      xn_ = x[jn];
+      if (!reg_on) zcn = __ldg(z + jn);
+    }
+    if (reg_on) __syncthreads();
     if (inside) {
-      const long long j = ((long long)iz * ny + iy) * nx + ix;
-      const long long jf = (long long)f * nvox + j;
+      const long long jf = vidx(k);
       const float* p3[3] = {pl[k % 3], pl[(k + 1) % 3], pl[(k + 2) % 3]};
-      const float zc = reg_on ? p3[1][(ty + 1) * UPD_PX + tx + 1] : zf[j];
+      const float zc = reg_on ? p3[1][(ty + 1) * UPD_PX + tx + 1] : zv;
       float reg = 0.0f;
       if (reg_on) {
         const bool vz[3] = {iz > 0, true, iz + 1 < nz};
@@ -174,10 +204,10 @@ update_kernel(float* __restrict__ x, const float* __restrict__ z, float* __restr
             }
         reg *= beta;
       }
-      const float den = D[jf] + sbeta;
-      const float wv = den > 0.0f ? fmaxf(zc - (g[jf] + reg) / den, 0.0f) : 0.0f;
+      const float den = dv + sbeta;
+      const float wv = den > 0.0f ? fmaxf(zc - (gv + reg) / den, 0.0f) : 0.0f;
       const float xn = fmaxf(wv - nu, 0.0f);
-      zn[jf] = xn + mom * (xn - x[jf]);
+      zn[jf] = xn + mom * (xn - xv);
       x[jf] = xn;
     }
     if (reg_on) __syncthreads();   // plane k % 3 is overwritten next
