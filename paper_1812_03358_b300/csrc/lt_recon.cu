@@ -214,6 +214,20 @@ update_kernel(float* __restrict__ x, const float* __restrict__ z, float* __restr
   }
 }
 
+// res[f] = sum over cameras and blocks of the fit partials of frame f,
+// res[F + f * C + c] = gains[f * C + c].  grid = F, one block per frame.
+__global__ void __launch_bounds__(256)
+finalize_result(const double* __restrict__ fit_part, const double* __restrict__ gains, double* __restrict__ res,
+                int F, int C) {
+  __shared__ double sh[32];
+  const int f = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < C * RED_BLOCKS; i += blockDim.x) acc += fit_part[(long long)f * C * RED_BLOCKS + i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) res[f] = acc;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) res[F + f * C + c] = gains[f * C + c];
+}
+
 __global__ void finalize_dots(const double* __restrict__ part, double* __restrict__ out, int n) {
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     double acc = 0.0;
@@ -245,6 +259,7 @@ struct lt_recon {
   float *y = nullptr, *w = nullptr, *p = nullptr, *r = nullptr, *g = nullptr, *D = nullptr, *x = nullptr;
   float* z[2] = {nullptr, nullptr};
   double *ywy = nullptr, *gains = nullptr, *part = nullptr, *fit_part = nullptr;
+  double* res = nullptr;                           // [F] data fit, [F][C] gains (lt_recon_get_async)
   Scalars* sc = nullptr;
   int zsel = 0;
   int64_t iters = 0;
@@ -261,7 +276,7 @@ static void recon_free(lt_recon* R) {
     if (g) cudaGraphExecDestroy(g);
   if (R->cap) cudaStreamDestroy(R->cap);
   void* bufs[] = {R->y, R->w, R->p, R->r, R->g, R->D, R->x, R->z[0], R->z[1],
-                  R->ywy, R->gains, R->part, R->fit_part, R->sc};
+                  R->ywy, R->gains, R->part, R->fit_part, R->res, R->sc};
   for (void* b : bufs) cudaFree(b);
   delete R;
 }
@@ -374,6 +389,7 @@ extern "C" lt_status lt_recon_create(lt_plan* plan, const float* y, const float*
       (s = dalloc(&R->ywy, (size_t)R->F * R->C, "ywy")) || (s = dalloc(&R->gains, (size_t)R->F * R->C, "gains")) ||
       (s = dalloc(&R->part, (size_t)R->F * R->C * RED_BLOCKS, "partials")) ||
       (s = dalloc(&R->fit_part, (size_t)R->F * R->C * RED_BLOCKS, "fit partials")) ||
+      (s = dalloc(&R->res, (size_t)R->F * (R->C + 1), "results")) ||
       (s = dalloc(&R->sc, 1, "scalars"))) {
     recon_free(R);
     return s;
@@ -482,6 +498,17 @@ extern "C" lt_status lt_recon_get(lt_recon* R, float* x, double* gains, double* 
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LT_OK : cuda_error(e, "lt_recon_get");
+}
+
+extern "C" lt_status lt_recon_get_async(lt_recon* R, double* host_out, void* stream) {
+  clear_error();
+  if (!R || !host_out) return set_error(LT_EINVAL, "recon and host_out are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  finalize_result<<<R->F, 256, 0, st>>>(R->fit_part, R->gains, R->res, R->F, R->C);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host_out, R->res, (size_t)R->F * (R->C + 1) * sizeof(double), cudaMemcpyDeviceToHost, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "lt_recon_get_async");
 }
 
 extern "C" lt_status lt_recon_iterations(const lt_recon* R, int64_t* n_iter) {

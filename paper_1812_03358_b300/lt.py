@@ -81,6 +81,7 @@ _SIGS = {
                                   c_void_p, POINTER(c_void_p)]),
     "lt_recon_iterate": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lt_recon_get": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "lt_recon_get_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "lt_recon_iterations": (c_int32, [c_void_p, POINTER(c_int64)]),
     "lt_recon_state_size": (c_int32, [c_void_p, POINTER(c_int64)]),
     "lt_recon_get_state": (c_int32, [c_void_p, c_void_p]),
@@ -271,6 +272,12 @@ def lt_recon_get(rec, x_ptr: int, n_frames: int, n_cams: int, stream: int = 0):
     fit = (c_double * n_frames)()
     _check(lib().lt_recon_get(rec, x_ptr or None, gains, fit, stream))
     return np.array(gains).reshape(n_frames, n_cams), np.array(fit)
+
+
+def lt_recon_get_async(rec, host_ptr: int, stream: int = 0) -> None:
+    """Enqueues the data fit [F] and gains [F][n_cams] into the (page-locked)
+    host buffer at host_ptr; valid once the stream has passed this point."""
+    _check(lib().lt_recon_get_async(rec, host_ptr, stream))
 
 
 def lt_recon_iterations(rec) -> int:
@@ -483,6 +490,16 @@ class Recon:
         gains, fit = lt_recon_get(self.handle, _dev_f32(x, self.plan.frames * self.plan.nvox, "x"),
                                   self.plan.frames, len(self.plan.cams), _stream())
         return x, gains, fit
+
+    def get_async(self, out):
+        """Enqueues [data_fit[F], gains[F][n_cams]] into `out`, a page-locked
+        float64 host tensor of F * (n_cams + 1) values, on the current stream
+        (read it after an event or a synchronise)."""
+        import torch
+        n = self.plan.frames * (len(self.plan.cams) + 1)
+        if out.device.type != "cpu" or out.dtype != torch.float64 or out.numel() < n or not out.is_pinned():
+            raise ValueError(f"get_async needs a pinned float64 host tensor of {n} values")
+        lt_recon_get_async(self.handle, out.data_ptr(), _stream())
 
     @property
     def iterations(self):

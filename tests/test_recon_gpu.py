@@ -135,3 +135,24 @@ def test_frames_are_independent_problems():
     for f, y in enumerate([y0, y1]):
         xf, _, _, _, _ = run_gpu(vol, [cam], [y], 12)
         assert np.array_equal(x2[f], xf)
+
+
+def test_async_result_read_matches_synchronous_read():
+    vol = I.Volume(16, 16, 16, 5.0, 5.0, 5.0)
+    cams = [I.table_single_lens(36, 0.25), I.table_single_lens(30, 0.3, ks=2, kt=2)]
+    ys = measure(vol, cams, I.gaussian_blobs(vol, seed=1004), scales=[1.0, 2.5])
+    plan = lt.Plan(vol, cams)
+    rec = lt.Recon(plan, dev(np.concatenate([np.ravel(y) for y in ys])), estimate_gains=True)
+    out = torch.empty(1 * (len(cams) + 1), dtype=torch.float64).pin_memory()
+    rec.get_async(out)                       # before any iteration: fit 0, the initial gains
+    _, gains0, fit0 = rec.get()
+    torch.cuda.synchronize()
+    assert out[0].item() == fit0[0] == 0.0 and np.array_equal(out[1:].numpy(), np.ravel(gains0))
+    rec.iterate(7)
+    rec.get_async(out)
+    _, gains, fit = rec.get()
+    torch.cuda.synchronize()
+    assert abs(out[0].item() - fit[0]) <= 1e-12 * abs(fit[0])
+    assert np.array_equal(out[1:].numpy(), np.ravel(gains))
+    with pytest.raises(ValueError):
+        rec.get_async(torch.empty(3, dtype=torch.float64))   # not page-locked
