@@ -90,3 +90,37 @@ def test_tcgen05_conv_rejects_shapes_it_cannot_tile():
     x, w, b = _operands(2, 2, 64, 16, 16, seed=3)
     with pytest.raises(lt.LtError):
         _run(U.CONV_TCGEN05, x, w, b, 2, 2, 64, 16, 16, False)
+
+
+def test_unet_at_full_resolution_is_unchanged_by_the_tcgen05_layers(monkeypatch):
+    """The whole network at 128^3 (where the full-resolution layers take the
+    tcgen05 kernel by default) against the same network with every layer
+    forced onto the warp-level MMA kernel: forward output and input gradient."""
+    n = 128
+    net = U.UNet(seed=3)
+    g = torch.Generator().manual_seed(11)
+    x = torch.zeros(n, n, n, 16)
+    x[..., 0] = torch.rand(n, n, n, generator=g)
+    xb = x.bfloat16().cuda()
+    gout = (0.01 * torch.randn(n, n, n, 16, generator=g)).bfloat16().cuda()
+
+    def run():
+        out = net.forward(xb, keep=True).float().clone()
+        gin = net.backward(gout).float().clone()
+        torch.cuda.synchronize()
+        return out, gin
+
+    out_tc, gin_tc = run()
+    U.device_status()
+    calls = U._call
+
+    def warp_only(name, *args):
+        if name == "lt_nn_conv3d_ex":
+            args = list(args)
+            args[-2] = U.CONV_WARP_MMA
+        return calls(name, *args)
+
+    monkeypatch.setattr(U, "_call", warp_only)
+    out_w, gin_w = run()
+    assert float((out_tc - out_w).norm() / out_w.norm()) < 1e-5
+    assert float((gin_tc - gin_w).norm() / gin_w.norm()) < 1e-5
