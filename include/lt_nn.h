@@ -34,7 +34,7 @@ LT_API lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const float
  * wherever it applies and the warp-level MMA kernel elsewhere, LT_CONV_WARP_MMA
  * is the warp-level MMA kernel (every shape), LT_CONV_TCGEN05 the tcgen05
  * kernel (operands in shared memory, accumulators in tensor memory), which
- * needs W a multiple of 128, H and D even and 16-byte aligned in, w and
+ * needs W a multiple of 64, H and D even and 16-byte aligned in, w and
  * out_bf; other shapes give LT_EUNSUPPORTED on that path. */
 enum { LT_CONV_AUTO = 0, LT_CONV_WARP_MMA = 1, LT_CONV_TCGEN05 = 2 };
 LT_API lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,

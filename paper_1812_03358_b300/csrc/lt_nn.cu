@@ -433,7 +433,7 @@ extern "C" lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, cons
   const bool tc_ok = conv3d_tc_supported(in, w, out_bf, D, H, W, Ci, Co);
   if (path == LT_CONV_TCGEN05 || (path == LT_CONV_AUTO && tc_ok)) {
     if (!tc_ok)
-      return set_error(LT_EUNSUPPORTED, "conv3d: the tcgen05 kernel needs W %% 128 == 0, even H and D, aligned pointers");
+      return set_error(LT_EUNSUPPORTED, "conv3d: the tcgen05 kernel needs W %% 64 == 0, even H and D, aligned pointers");
     const cudaError_t e = launch_conv3d_tc(in, w, b, out_bf, out_f, batch, D, H, W, Ci, Co, o_stride, o_off, relu,
                                            (cudaStream_t)stream);
     return e == cudaSuccess ? LT_OK : cuda_error(e, "conv3d (tcgen05)");

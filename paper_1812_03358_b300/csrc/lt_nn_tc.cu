@@ -1,11 +1,12 @@
 // 3x3x3 convolution of the warm-start U-Net on the fifth-generation tensor
 // cores (tcgen05): bfloat16 operands in shared memory, float32 accumulators
 // in tensor memory (TMEM).  Used for volumes whose x extent is a multiple of
-// 128 (the full-resolution level of the network), the warp-level MMA kernel
-// of lt_nn.cu for the rest.
+// 64 (the full- and half-resolution levels of the network), the warp-level
+// MMA kernel of lt_nn.cu for the rest.
 //
-// A CTA owns a 128 (x) x 2 (y) x 2 (z) block of output voxels -- four
-// M = 128 tiles, one x run each -- and N = 16, 32 or 48 output channels.  Per
+// A CTA owns a TM (x) x 2 (y) x 2 (z) block of output voxels -- four tiles,
+// one x run of TM = 128 (or 64) voxels each, one M = 128 MMA row per voxel
+// (rows past TM unused) -- and N = 16, 32 or 48 output channels.  Per
 // chunk of 16 input channels it stages the input halo (130 x 4 x 4 voxels)
 // and the 27 taps' weights in shared memory, in the canonical K-major layout
 // without swizzle: 8 (voxels or output channels) x 8 channels of 16 bytes
@@ -34,22 +35,35 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int TC_M = 128;                  // x voxels per tile (MMA rows)
+constexpr int TC_MMA_M = 128;              // rows of every MMA (TMEM lanes)
 constexpr int TC_RY = 2, TC_RZ = 2;        // output rows per CTA
 constexpr int TC_TILES = TC_RY * TC_RZ;
-constexpr int TC_HX = TC_M + 2, TC_HY = TC_RY + 2, TC_HZ = TC_RZ + 2;
+constexpr int TC_HY = TC_RY + 2, TC_HZ = TC_RZ + 2;
 constexpr int TC_THREADS = 128;            // 4 warps = the 128 TMEM lanes
-constexpr int TC_ROW = TC_HX * 16;         // bytes of one (hz, hy, channel group) halo row
-constexpr int TC_HALO = TC_HZ * TC_HY * 2 * TC_ROW;
-// Guard bytes after the halo and the weights (none: every descriptor read
-// ends inside its buffer, the halo's exactly at its last byte).
-constexpr int TC_GUARD_A = 0, TC_GUARD_B = 0;
 constexpr long long kWaitLimit = 1LL << 24;   // mbarrier polls (with 64 ns back-off) before giving up
+
+// Halo geometry for x runs of TM voxels (128, or 64 for the half-resolution
+// level).  An MMA always reads 128 rows of A: with TM = 64 the upper 64 rows
+// run on into the next halo row (their accumulator rows are never stored,
+// and row m of the product depends on row m of A alone), and past the last
+// row into TAIL bytes kept inside the allocation.  The last A start is two
+// voxels into the last (hz, hy, channel group 0) row, so the furthest byte
+// read is HALO - ROW + 2 * 16 + 128 * 16 - 1 = HALO + TAIL - 1.
+template <int TM>
+struct TcGeom {
+  static constexpr int HX = TM + 2;
+  static constexpr int ROW = HX * 16;               // bytes of one (hz, hy, channel group) halo row
+  static constexpr int HALO = TC_HZ * TC_HY * 2 * ROW;
+  static constexpr int TAIL = (TC_MMA_M - TM) * 16;
+  static_assert(TM == 128 || TM == 64, "x run");
+};
 
 template <int N>
 __host__ __device__ constexpr int tc_weight_bytes() { return 27 * 2 * N * 16; }
-template <int N>
-__host__ __device__ constexpr int tc_smem_bytes() { return TC_HALO + TC_GUARD_A + tc_weight_bytes<N>() + TC_GUARD_B + 16; }
+template <int TM, int N>
+__host__ __device__ constexpr int tc_smem_bytes() {
+  return TcGeom<TM>::HALO + TcGeom<TM>::TAIL + tc_weight_bytes<N>() + 16;
+}
 
 __device__ int g_tc_status;   // LT_ETIMEOUT after a bounded wait gave up
 
@@ -147,26 +161,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int N>
+template <int TM, int N>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
                  bf16* __restrict__ out_bf, float* __restrict__ out_f, int D, int H, int W, int Ci, int Co,
                  int o_stride, int o_off, int relu, int tiles_x, int tiles_y, int vec_store) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* halo = tc_smem;                                   // [hz][hy][cg][hx][8] bf16
-  unsigned char* wts = tc_smem + TC_HALO + TC_GUARD_A;             // [tap][cg][co][8] bf16
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(wts + tc_weight_bytes<N>() + TC_GUARD_B);
+  using G = TcGeom<TM>;
+  unsigned char* wts = tc_smem + G::HALO + G::TAIL;               // [tap][cg][co][8] bf16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(wts + tc_weight_bytes<N>());
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   // TMEM columns: TC_TILES x N rounded up to a power of two (64, 128, 256)
   constexpr uint32_t kCols = TC_TILES * N <= 64 ? 64 : TC_TILES * N <= 128 ? 128 : 256;
   static_assert(N % 16 == 0 && N <= 64 && TC_TILES * N <= 256, "tcgen05 tile width");
-  constexpr uint32_t kIdesc = mma_idesc(TC_M, N);
+  constexpr uint32_t kIdesc = mma_idesc(TC_MMA_M, N);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int bx = blockIdx.x % tiles_x;
   const int rest = blockIdx.x / tiles_x;
   const int by = rest % tiles_y, bz = rest / tiles_y;
-  const int x0 = bx * TC_M, y0 = by * TC_RY, z0 = bz * TC_RZ;
+  const int x0 = bx * TM, y0 = by * TC_RY, z0 = bz * TC_RZ;
   const int n0 = blockIdx.y * N;
   const int b = blockIdx.z;
   const long long V = (long long)D * H * W;
@@ -188,14 +203,14 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
       if (!ok) break;
     }
     // halo (zero outside the volume) and weights of this chunk, all copies in flight at once
-    for (int t = tid; t < TC_HZ * TC_HY * TC_HX * 2; t += TC_THREADS) {
+    for (int t = tid; t < TC_HZ * TC_HY * G::HX * 2; t += TC_THREADS) {
       const int cg = t & 1, v = t >> 1;
-      const int hx = v % TC_HX, r = v / TC_HX;
+      const int hx = v % G::HX, r = v / G::HX;
       const int hy = r % TC_HY, hz = r / TC_HY;
       const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
       const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
       const bf16* src = inside ? inb + (((long long)gz * H + gy) * W + gx) * Ci + c * 16 + cg * 8 : inb;
-      cp_async16(smem_u32(halo + ((hz * TC_HY + hy) * 2 + cg) * TC_ROW + hx * 16), src, inside);
+      cp_async16(smem_u32(halo + ((hz * TC_HY + hy) * 2 + cg) * G::ROW + hx * 16), src, inside);
     }
     for (int t = tid; t < 27 * 2 * N; t += TC_THREADS) {
       const int co = t % N, r = t / N;
@@ -212,7 +227,7 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
       // Descriptors differ only in the start-address field (bits 0-13, in
       // 16-byte units; every address here is below 256 KB), so each MMA's is
       // a base descriptor plus a compile-time offset.
-      const uint64_t a0 = smem_desc(smem_u32(halo), TC_ROW, 128);
+      const uint64_t a0 = smem_desc(smem_u32(halo), G::ROW, 128);
       const uint64_t b0 = smem_desc(smem_u32(wts), N * 16, 128);
       // taps outer, tiles inner: consecutive MMAs go to different
       // accumulators and do not wait for one another's results
@@ -222,7 +237,7 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
         for (int m = 0; m < TC_TILES; ++m) {
           const int ry = m % TC_RY, rz = m / TC_RY;
           const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-          const uint32_t a_off = ((rz + dz + 1) * TC_HY + (ry + dy + 1)) * 2 * TC_ROW + (dx + 1) * 16;
+          const uint32_t a_off = ((rz + dz + 1) * TC_HY + (ry + dy + 1)) * 2 * G::ROW + (dx + 1) * 16;
           const uint32_t b_off = tap * 2 * N * 16;
           mma_bf16(tbase + m * N, a0 + (a_off >> 4), b0 + (b_off >> 4), kIdesc, (c > 0 || tap > 0) ? 1u : 0u);
         }
@@ -232,7 +247,7 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
   }
   if (ok) ok = __syncthreads_and(mbar_wait(bar, (chunks - 1) & 1));
   tc_fence_after();
-  if (ok) {
+  if (ok && warp * 32 < TM) {   // warps past TM hold the unused accumulator rows
     for (int m = 0; m < TC_TILES; ++m) {
       const int ry = m % TC_RY, rz = m / TC_RY;
       const int gx = x0 + warp * 32 + lane, gy = y0 + ry, gz = z0 + rz;
@@ -266,7 +281,8 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
         }
       }
     }
-  } else if (tid == 0) {
+  }
+  if (!ok && tid == 0) {
     atomicExch(&g_tc_status, (int)LT_ETIMEOUT);
   }
   tc_fence_before();
@@ -278,9 +294,36 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
 
 bool conv3d_tc_supported(const void* in, const void* w, const void* out_bf, int D, int H, int W, int Ci, int Co) {
   const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-  return W > 0 && W % TC_M == 0 && H > 0 && H % TC_RY == 0 && D > 0 && D % TC_RZ == 0 && Ci > 0 && Ci % 16 == 0 &&
+  return W > 0 && W % 64 == 0 && H > 0 && H % TC_RY == 0 && D > 0 && D % TC_RZ == 0 && Ci > 0 && Ci % 16 == 0 &&
          Co > 0 && Co % 16 == 0 && al16(in) && al16(w) && al16(out_bf);
 }
+
+namespace {
+template <int TM, int N>
+cudaError_t launch_tc(const bf16* in, const bf16* w, const float* b, bf16* out_bf, float* out_f, dim3 grid, int D,
+                      int H, int W, int Ci, int Co, int o_stride, int o_off, int relu, int tx, int ty, int vec,
+                      cudaStream_t st) {
+  static bool attr_set = false;   // more than 48 KB of dynamic shared memory
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<TM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               tc_smem_bytes<TM, N>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  conv3d_tc_kernel<TM, N><<<grid, TC_THREADS, tc_smem_bytes<TM, N>(), st>>>(in, w, b, out_bf, out_f, D, H, W, Ci,
+                                                                            Co, o_stride, o_off, relu, tx, ty, vec);
+  return cudaGetLastError();
+}
+
+template <int TM>
+cudaError_t launch_tm(int nb, const bf16* in, const bf16* w, const float* b, bf16* out_bf, float* out_f, dim3 grid,
+                      int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu, int tx, int ty, int vec,
+                      cudaStream_t st) {
+  if (nb == 48) return launch_tc<TM, 48>(in, w, b, out_bf, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
+  if (nb == 32) return launch_tc<TM, 32>(in, w, b, out_bf, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
+  return launch_tc<TM, 16>(in, w, b, out_bf, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
+}
+}  // namespace
 
 cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf, float* out_f,
                              int batch, int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu,
@@ -288,38 +331,18 @@ cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float*
   // the widest N that divides Co: the MMA count per output tile does not
   // depend on N (each MMA's time is set by reading its 128 x 16 A tile)
   const int nb = Co % 48 == 0 ? 48 : Co % 32 == 0 ? 32 : 16;
-  const int tx = W / TC_M, ty = H / TC_RY, tz = D / TC_RZ;
+  const int tm = W % 128 == 0 ? 128 : 64;
+  const int tx = W / tm, ty = H / TC_RY, tz = D / TC_RZ;
   const long long tiles = (long long)tx * ty * tz;
   if (tiles > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc_smem_bytes<48>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(conv3d_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               tc_smem_bytes<32>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(conv3d_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               tc_smem_bytes<16>());
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   // 16-byte bfloat16 stores need every voxel's channel run on a 16-byte boundary
   const int vec = (o_stride % 8 == 0 && o_off % 8 == 0) ? 1 : 0;
   dim3 grid((unsigned)tiles, Co / nb, batch);
   const bf16* i_ = reinterpret_cast<const bf16*>(in);
   const bf16* w_ = reinterpret_cast<const bf16*>(w);
   bf16* o_ = reinterpret_cast<bf16*>(out_bf);
-  if (nb == 48)
-    conv3d_tc_kernel<48><<<grid, TC_THREADS, tc_smem_bytes<48>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co,
-                                                                         o_stride, o_off, relu, tx, ty, vec);
-  else if (nb == 32)
-    conv3d_tc_kernel<32><<<grid, TC_THREADS, tc_smem_bytes<32>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co,
-                                                                         o_stride, o_off, relu, tx, ty, vec);
-  else
-    conv3d_tc_kernel<16><<<grid, TC_THREADS, tc_smem_bytes<16>(), st>>>(i_, w_, b, o_, out_f, D, H, W, Ci, Co,
-                                                                         o_stride, o_off, relu, tx, ty, vec);
-  return cudaGetLastError();
+  if (tm == 128) return launch_tm<128>(nb, i_, w_, b, o_, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
+  return launch_tm<64>(nb, i_, w_, b, o_, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
 }
 
 cudaError_t take_tc_status(int* status, cudaStream_t st) {

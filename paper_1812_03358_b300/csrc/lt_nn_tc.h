@@ -7,7 +7,7 @@
 namespace lt {
 
 // Shapes (and 16-byte aligned pointers) the tcgen05 kernel tiles exactly:
-// W a multiple of 128, H and D even, channel counts multiples of 16.
+// W a multiple of 64, H and D even, channel counts multiples of 16.
 bool conv3d_tc_supported(const void* in, const void* w, const void* out_bf, int D, int H, int W, int Ci, int Co);
 
 // Same operation and layouts as lt_nn_conv3d.

@@ -54,6 +54,10 @@ CASES = [  # (D, H, W, Ci, Co, relu)
     (6, 2, 128, 48, 64, True),
     (2, 2, 128, 16, 48, False),
     (4, 2, 128, 32, 96, True),
+    (2, 2, 64, 16, 16, False),      # 64-voxel x runs: half of every MMA's rows unused
+    (4, 2, 64, 32, 32, True),
+    (2, 4, 192, 96, 32, False),
+    (2, 2, 64, 16, 48, True),
 ]
 
 
@@ -87,9 +91,10 @@ def test_tcgen05_and_warp_mma_kernels_agree():
 
 
 def test_tcgen05_conv_rejects_shapes_it_cannot_tile():
-    x, w, b = _operands(2, 2, 64, 16, 16, seed=3)
-    with pytest.raises(lt.LtError):
-        _run(U.CONV_TCGEN05, x, w, b, 2, 2, 64, 16, 16, False)
+    for D, H, W in ((2, 2, 32), (3, 2, 64), (2, 2, 96)):
+        x, w, b = _operands(D, H, W, 16, 16, seed=3)
+        with pytest.raises(lt.LtError):
+            _run(U.CONV_TCGEN05, x, w, b, D, H, W, 16, 16, False)
 
 
 def test_unet_at_full_resolution_is_unchanged_by_the_tcgen05_layers(monkeypatch):
