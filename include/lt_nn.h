@@ -30,13 +30,23 @@ LT_API lt_status lt_nn_conv3d(const uint16_t* in, const uint16_t* w, const float
                               float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
                               int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, void* stream);
 
-/* lt_nn_conv3d with an explicit kernel: LT_CONV_AUTO takes the tcgen05 kernel
- * wherever it applies and the warp-level MMA kernel elsewhere, LT_CONV_WARP_MMA
- * is the warp-level MMA kernel (every shape), LT_CONV_TCGEN05 the tcgen05
- * kernel (operands in shared memory, accumulators in tensor memory), which
- * needs W a multiple of 64, H and D even and 16-byte aligned in, w and
- * out_bf; other shapes give LT_EUNSUPPORTED on that path. */
-enum { LT_CONV_AUTO = 0, LT_CONV_WARP_MMA = 1, LT_CONV_TCGEN05 = 2 };
+/* lt_nn_conv3d with an explicit kernel: LT_CONV_AUTO takes a tcgen05 kernel
+ * wherever one applies and the warp-level MMA kernel elsewhere, LT_CONV_WARP_MMA
+ * is the warp-level MMA kernel (every shape), LT_CONV_TCGEN05 the faster of
+ * the two tcgen05 kernels (operands in shared memory, accumulators in tensor
+ * memory), LT_CONV_TCGEN05_CHUNKED and LT_CONV_TCGEN05_ZWALK one of them.
+ * Both need W a multiple of 64 and 16-byte aligned in, w and out_bf; the
+ * chunked kernel (CTA = 2 x 2 output rows, input channels in chunks of 16)
+ * needs H and D even, the z-walking kernel (CTA = 4 output rows walking 8
+ * slices, a ring of input planes) Ci == 16, H a multiple of 4 and Co not a
+ * multiple of 48.  Other shapes give LT_EUNSUPPORTED on those paths. */
+enum {
+  LT_CONV_AUTO = 0,
+  LT_CONV_WARP_MMA = 1,
+  LT_CONV_TCGEN05 = 2,
+  LT_CONV_TCGEN05_CHUNKED = 3,
+  LT_CONV_TCGEN05_ZWALK = 4
+};
 LT_API lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
                                  float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
                                  int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, int32_t path,

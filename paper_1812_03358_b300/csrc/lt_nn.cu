@@ -428,14 +428,16 @@ extern "C" lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, cons
                                      void* stream) {
   clear_error();
   if (!in || !w || (!out_bf && !out_f) || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 ||
-      Ci % 16 || Co % 16 || o_off < 0 || o_stride < o_off + Co || path < LT_CONV_AUTO || path > LT_CONV_TCGEN05)
+      Ci % 16 || Co % 16 || o_off < 0 || o_stride < o_off + Co || path < LT_CONV_AUTO || path > LT_CONV_TCGEN05_ZWALK)
     return set_error(LT_EINVAL, "conv3d: bad arguments (channels must be multiples of 16)");
   const bool tc_ok = conv3d_tc_supported(in, w, out_bf, D, H, W, Ci, Co);
-  if (path == LT_CONV_TCGEN05 || (path == LT_CONV_AUTO && tc_ok)) {
-    if (!tc_ok)
-      return set_error(LT_EUNSUPPORTED, "conv3d: the tcgen05 kernel needs W %% 64 == 0, even H and D, aligned pointers");
+  if (path >= LT_CONV_TCGEN05 || (path == LT_CONV_AUTO && tc_ok)) {
+    const int variant = path == LT_CONV_TCGEN05_CHUNKED ? kTcChunked : path == LT_CONV_TCGEN05_ZWALK ? kTcZWalk : kTcBest;
+    if (!tc_ok || !conv3d_tc_variant_supported(variant, D, H, Ci, Co))
+      return set_error(LT_EUNSUPPORTED, "conv3d: this tcgen05 kernel does not tile the shape (W %% 64, aligned pointers; "
+                                        "chunked: even H and D; z-walking: Ci == 16, H %% 4 == 0, Co %% 48 != 0)");
     const cudaError_t e = launch_conv3d_tc(in, w, b, out_bf, out_f, batch, D, H, W, Ci, Co, o_stride, o_off, relu,
-                                           (cudaStream_t)stream);
+                                           variant, (cudaStream_t)stream);
     return e == cudaSuccess ? LT_OK : cuda_error(e, "conv3d (tcgen05)");
   }
   const int nb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;

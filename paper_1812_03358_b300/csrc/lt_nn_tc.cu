@@ -290,12 +290,191 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
   if (warp == 0) tmem_dealloc(tbase, kCols);
 }
 
+// z-walking variant for 16 input channels (one channel chunk).  A CTA owns a
+// TM (x) x 4 (y) column of output rows and walks ZW_SLICES slices in z.  The
+// input halo lives in a ring of three planes of 6 (y) rows in shared memory;
+// output slice z needs planes z - 1, z, z + 1.  Per slice: wait for its MMAs,
+// load plane z + 2 into the slot of plane z - 1 (now unread) while the
+// epilogue drains the accumulators, then issue the next slice's MMAs.  Each
+// input plane is staged once per CTA, 6 rows for 4 output rows (1.9x over
+// ZW_SLICES = 8 slices, against 4x for the chunked kernel), and two CTAs per
+// SM overlap one's staging and epilogue with the other's MMAs.
+constexpr int ZW_RY = 4, ZW_HY = ZW_RY + 2;
+constexpr int ZW_SLICES = 8;
+
+template <int TM>
+struct ZwGeom {
+  static constexpr int HX = TM + 2;
+  static constexpr int ROW = HX * 16;                   // one (hy, channel group) row of a plane
+  static constexpr int PLANE = ZW_HY * 2 * ROW;
+  static constexpr int RING = 3 * PLANE;
+  // the last A start is two voxels into the last plane's last (hy, cg 0) row:
+  // furthest byte RING - ROW + 32 + 2048 - 1 = RING + TAIL - 1
+  static constexpr int TAIL = (TC_MMA_M - TM) * 16;
+};
+template <int TM, int N>
+__host__ __device__ constexpr int zw_smem_bytes() {
+  return ZwGeom<TM>::RING + ZwGeom<TM>::TAIL + tc_weight_bytes<N>() + 16;
+}
+
+template <int TM, int N>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+conv3d_tc_zwalk_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
+                       bf16* __restrict__ out_bf, float* __restrict__ out_f, int D, int H, int W, int Co,
+                       int o_stride, int o_off, int relu, int tiles_x, int tiles_y, int vec_store) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  using G = ZwGeom<TM>;
+  unsigned char* ring = tc_smem;                                     // [slot][hy][cg][hx][8] bf16
+  unsigned char* wts = tc_smem + G::RING + G::TAIL;                  // [tap][cg][co][8] bf16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(wts + tc_weight_bytes<N>());
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  constexpr uint32_t kCols = ZW_RY * N <= 64 ? 64 : ZW_RY * N <= 128 ? 128 : 256;
+  static_assert(N % 16 == 0 && ZW_RY * N <= 256, "tcgen05 tile width");
+  constexpr uint32_t kIdesc = mma_idesc(TC_MMA_M, N);
+  constexpr int Ci = 16;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bx = blockIdx.x % tiles_x;
+  const int rest = blockIdx.x / tiles_x;
+  const int by = rest % tiles_y, bz = rest / tiles_y;
+  const int x0 = bx * TM, y0 = by * ZW_RY, z0 = bz * ZW_SLICES;
+  const int nsl = min(ZW_SLICES, D - z0);
+  const int n0 = blockIdx.y * N;
+  const int b = blockIdx.z;
+  const long long V = (long long)D * H * W;
+  const bf16* inb = in + (long long)b * V * Ci;
+  const uint32_t bar = smem_u32(mbar);
+
+  // plane of slice kz (zero outside the volume) into ring slot `slot`
+  const auto stage_plane = [&](int kz, int slot) {
+    unsigned char* dst = ring + slot * G::PLANE;
+    for (int t = tid; t < ZW_HY * G::HX * 2; t += TC_THREADS) {
+      const int cg = t & 1, v = t >> 1;
+      const int hx = v % G::HX, hy = v / G::HX;
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1;
+      const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H && kz >= 0 && kz < D;
+      const bf16* src = inside ? inb + (((long long)kz * H + gy) * W + gx) * Ci + cg * 8 : inb;
+      cp_async16(smem_u32(dst + (hy * 2 + cg) * G::ROW + hx * 16), src, inside);
+    }
+  };
+  // ring slot of plane kz: planes z0 - 1, z0, z0 + 1, ... take slots 0, 1, 2, 0, ...
+  const auto slot_of = [&](int kz) { return (kz - z0 + 1) % 3; };
+
+  if (warp == 0) tmem_alloc(smem_u32(tslot), kCols);
+  if (tid == 0) mbar_init(bar);
+  for (int t = tid; t < 27 * 2 * N; t += TC_THREADS) {
+    const int co = t % N, r = t / N;
+    const int cg = r & 1, tap = r >> 1;
+    const bool inside = n0 + co < Co;
+    const bf16* src = inside ? w + ((long long)(n0 + co) * 27 + tap) * Ci + cg * 8 : w;
+    cp_async16(smem_u32(wts + ((tap * 2 + cg) * N + co) * 16), src, inside);
+  }
+  stage_plane(z0 - 1, 0);
+  stage_plane(z0, 1);
+  stage_plane(z0 + 1, 2);
+  cp_async_wait_all();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  // issue the 27 x ZW_RY MMAs of slice kz (one thread) and commit them
+  const auto issue = [&](int kz) {
+    const uint64_t a0 = smem_desc(smem_u32(ring), G::ROW, 128);
+    const uint64_t b0 = smem_desc(smem_u32(wts), N * 16, 128);
+    const uint32_t s0 = slot_of(kz - 1) * G::PLANE, s1 = slot_of(kz) * G::PLANE, s2 = slot_of(kz + 1) * G::PLANE;
+#pragma unroll
+    for (int tap = 0; tap < 27; ++tap) {
+#pragma unroll
+      for (int ry = 0; ry < ZW_RY; ++ry) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const uint32_t sb = dz < 0 ? s0 : dz == 0 ? s1 : s2;
+        const uint32_t a_off = sb + ((ry + dy + 1) * 2) * G::ROW + (dx + 1) * 16;
+        const uint32_t b_off = tap * 2 * N * 16;
+        mma_bf16(tbase + ry * N, a0 + (a_off >> 4), b0 + (b_off >> 4), kIdesc, tap > 0 ? 1u : 0u);
+      }
+    }
+    mma_commit(bar);
+  };
+  if (tid == 0) issue(z0);
+
+  bool ok = true;
+  for (int s = 0; s < nsl; ++s) {
+    const int z = z0 + s;
+    ok = __syncthreads_and(mbar_wait(bar, s & 1));   // slice z's MMAs are done
+    if (!ok) break;
+    tc_fence_after();
+    if (s + 1 < nsl) stage_plane(z + 2, slot_of(z + 2));   // the slot of plane z - 1, no longer read
+    if (warp * 32 < TM) {   // warps past TM hold the unused accumulator rows
+      for (int ry = 0; ry < ZW_RY; ++ry) {
+        const int gx = x0 + warp * 32 + lane, gy = y0 + ry;
+        const long long o = ((long long)b * V + ((long long)z * H + gy) * W + gx) * o_stride + o_off + n0;
+#pragma unroll
+        for (int j = 0; j < N / 16; ++j) {
+          float v[16];
+          tmem_ld16(tbase + (static_cast<uint32_t>(warp * 32) << 16) + ry * N + j * 16, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            v[i] += bias ? __ldg(bias + n0 + j * 16 + i) : 0.0f;
+            if (relu) v[i] = fmaxf(v[i], 0.0f);
+          }
+          if (out_bf) {
+            if (vec_store) {
+              uint4 p[2];
+              __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(p);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+              uint4* dst = reinterpret_cast<uint4*>(out_bf + o + j * 16);
+              dst[0] = p[0];
+              dst[1] = p[1];
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) out_bf[o + j * 16 + i] = __float2bfloat16_rn(v[i]);
+            }
+          }
+          if (out_f) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) out_f[o + j * 16 + i] = v[i];
+          }
+        }
+      }
+    }
+    if (s + 1 < nsl) {
+      cp_async_wait_all();
+      fence_async_smem();   // plane z + 2 visible to the tensor core
+      tc_fence_before();    // this slice's tcgen05.ld are complete before the accumulators are rewritten
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        issue(z + 1);
+      }
+    }
+  }
+  if (!ok && tid == 0) atomicExch(&g_tc_status, (int)LT_ETIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, kCols);
+}
+
 }  // namespace
+
+// The z-walking kernel takes one channel chunk (Ci == 16) and any D; the
+// chunked kernel needs even H and D.
+static bool zwalk_applies(int H, int Ci, int Co) { return Ci == 16 && H % ZW_RY == 0 && Co % 48 != 0; }
 
 bool conv3d_tc_supported(const void* in, const void* w, const void* out_bf, int D, int H, int W, int Ci, int Co) {
   const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-  return W > 0 && W % 64 == 0 && H > 0 && H % TC_RY == 0 && D > 0 && D % TC_RZ == 0 && Ci > 0 && Ci % 16 == 0 &&
-         Co > 0 && Co % 16 == 0 && al16(in) && al16(w) && al16(out_bf);
+  if (!(W > 0 && W % 64 == 0 && H > 0 && D > 0 && Ci > 0 && Ci % 16 == 0 && Co > 0 && Co % 16 == 0 && al16(in) &&
+        al16(w) && al16(out_bf)))
+    return false;
+  return zwalk_applies(H, Ci, Co) || (H % TC_RY == 0 && D % TC_RZ == 0);
+}
+
+bool conv3d_tc_variant_supported(int variant, int D, int H, int Ci, int Co) {
+  if (variant == kTcZWalk) return zwalk_applies(H, Ci, Co);
+  if (variant == kTcChunked) return H % TC_RY == 0 && D % TC_RZ == 0;
+  return true;
 }
 
 namespace {
@@ -325,18 +504,59 @@ cudaError_t launch_tm(int nb, const bf16* in, const bf16* w, const float* b, bf1
 }
 }  // namespace
 
+namespace {
+template <int TM, int N>
+cudaError_t launch_zw(const bf16* in, const bf16* w, const float* b, bf16* out_bf, float* out_f, int batch, int D,
+                      int H, int W, int Co, int o_stride, int o_off, int relu, int vec, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(conv3d_tc_zwalk_kernel<TM, N>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, zw_smem_bytes<TM, N>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int tx = W / TM, ty = H / ZW_RY, tz = (D + ZW_SLICES - 1) / ZW_SLICES;
+  dim3 grid((unsigned)((long long)tx * ty * tz), Co / N, batch);
+  conv3d_tc_zwalk_kernel<TM, N><<<grid, TC_THREADS, zw_smem_bytes<TM, N>(), st>>>(
+      in, w, b, out_bf, out_f, D, H, W, Co, o_stride, o_off, relu, tx, ty, vec);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf, float* out_f,
                              int batch, int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu,
-                             cudaStream_t st) {
+                             int variant, cudaStream_t st) {
+  const int tm = W % 128 == 0 ? 128 : 64;
+  if ((long long)(W / tm) * H * D > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
+  // 16-byte bfloat16 stores need every voxel's channel run on a 16-byte boundary
+  const int vec = (o_stride % 8 == 0 && o_off % 8 == 0) ? 1 : 0;
+  // One channel chunk: the z-walking kernel, when its grid (a CTA per
+  // 4-row column and 8 slices) still gives every SM two CTAs; the chunked
+  // kernel's grid is 4x larger and fills small volumes better.
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 148;
+  const long long zw_ctas = (long long)(W / tm) * (H / ZW_RY) * ((D + ZW_SLICES - 1) / ZW_SLICES) * batch;
+  const bool zw_ok = zwalk_applies(H, Ci, Co), chunked_ok = H % TC_RY == 0 && D % TC_RZ == 0;
+  bool zwalk = zw_ok && (zw_ctas >= 2LL * sms || !chunked_ok);
+  if (variant == kTcChunked) zwalk = false;
+  if (variant == kTcZWalk) zwalk = true;
+  if ((zwalk && !zw_ok) || (!zwalk && !chunked_ok)) return cudaErrorInvalidValue;
+  if (zwalk) {
+    const bf16* i_ = reinterpret_cast<const bf16*>(in);
+    const bf16* w_ = reinterpret_cast<const bf16*>(w);
+    bf16* o_ = reinterpret_cast<bf16*>(out_bf);
+    if (Co % 32 == 0)
+      return tm == 128 ? launch_zw<128, 32>(i_, w_, b, o_, out_f, batch, D, H, W, Co, o_stride, o_off, relu, vec, st)
+                       : launch_zw<64, 32>(i_, w_, b, o_, out_f, batch, D, H, W, Co, o_stride, o_off, relu, vec, st);
+    return tm == 128 ? launch_zw<128, 16>(i_, w_, b, o_, out_f, batch, D, H, W, Co, o_stride, o_off, relu, vec, st)
+                     : launch_zw<64, 16>(i_, w_, b, o_, out_f, batch, D, H, W, Co, o_stride, o_off, relu, vec, st);
+  }
   // the widest N that divides Co: the MMA count per output tile does not
   // depend on N (each MMA's time is set by reading its 128 x 16 A tile)
   const int nb = Co % 48 == 0 ? 48 : Co % 32 == 0 ? 32 : 16;
-  const int tm = W % 128 == 0 ? 128 : 64;
   const int tx = W / tm, ty = H / TC_RY, tz = D / TC_RZ;
   const long long tiles = (long long)tx * ty * tz;
-  if (tiles > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
-  // 16-byte bfloat16 stores need every voxel's channel run on a 16-byte boundary
-  const int vec = (o_stride % 8 == 0 && o_off % 8 == 0) ? 1 : 0;
   dim3 grid((unsigned)tiles, Co / nb, batch);
   const bf16* i_ = reinterpret_cast<const bf16*>(in);
   const bf16* w_ = reinterpret_cast<const bf16*>(w);

@@ -7,13 +7,19 @@
 namespace lt {
 
 // Shapes (and 16-byte aligned pointers) the tcgen05 kernel tiles exactly:
-// W a multiple of 64, H and D even, channel counts multiples of 16.
+// W a multiple of 64, channel counts multiples of 16, and Ci == 16 with H a
+// multiple of 4 (z-walking kernel) or H and D even (chunked kernel).
 bool conv3d_tc_supported(const void* in, const void* w, const void* out_bf, int D, int H, int W, int Ci, int Co);
 
-// Same operation and layouts as lt_nn_conv3d.
+// Which tcgen05 kernel: the faster one for the shape, or one of the two.
+enum { kTcBest = 0, kTcChunked = 1, kTcZWalk = 2 };
+bool conv3d_tc_variant_supported(int variant, int D, int H, int Ci, int Co);
+
+// Same operation and layouts as lt_nn_conv3d (shape already checked with
+// conv3d_tc_supported / conv3d_tc_variant_supported).
 cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf, float* out_f,
                              int batch, int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu,
-                             cudaStream_t st);
+                             int variant, cudaStream_t st);
 
 // Reads and clears the device status word of the tcgen05 kernels (0, or
 // LT_ETIMEOUT after a bounded wait gave up); synchronises the stream.

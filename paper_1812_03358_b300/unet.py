@@ -120,7 +120,8 @@ def _need(t, n, what):
         raise ValueError(f"{what}: {t.numel()} elements, the layer needs {n}")
 
 
-CONV_AUTO, CONV_WARP_MMA, CONV_TCGEN05 = 0, 1, 2   # lt_nn_conv3d_ex kernel choice
+# lt_nn_conv3d_ex kernel choice
+CONV_AUTO, CONV_WARP_MMA, CONV_TCGEN05, CONV_TCGEN05_CHUNKED, CONV_TCGEN05_ZWALK = 0, 1, 2, 3, 4
 
 
 def device_status():

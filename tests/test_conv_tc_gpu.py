@@ -58,7 +58,20 @@ CASES = [  # (D, H, W, Ci, Co, relu)
     (4, 2, 64, 32, 32, True),
     (2, 4, 192, 96, 32, False),
     (2, 2, 64, 16, 48, True),
+    (10, 4, 128, 16, 16, True),     # 16 input channels, H % 4 == 0: the z-walking kernel (ragged last z block)
+    (3, 8, 64, 16, 32, False),
+    (16, 4, 128, 16, 32, False),
 ]
+
+
+def _kernels(D, H, Ci, Co):
+    """The tcgen05 kernels that tile this shape."""
+    out = []
+    if H % 2 == 0 and D % 2 == 0:
+        out.append(U.CONV_TCGEN05_CHUNKED)
+    if Ci == 16 and H % 4 == 0 and Co % 48:
+        out.append(U.CONV_TCGEN05_ZWALK)
+    return out
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[:5])) + ("-relu" if c[5] else ""))
@@ -66,17 +79,21 @@ def test_tcgen05_conv_matches_reference(case):
     D, H, W, Ci, Co, relu = case
     x, w, b = _operands(D, H, W, Ci, Co, seed=D * 100 + Ci)
     ref = _reference(x, w, b, D, H, W, Ci, Co, relu)
-    yf, yb = _run(U.CONV_TCGEN05, x, w, b, D, H, W, Ci, Co, relu)
-    err = float((yf.double() - ref).norm() / ref.norm())
-    assert err < 1e-5, err
-    assert torch.all((yb.double() - yf.double()).abs() <= 2.0 ** -8 * yf.double().abs() + 1e-30)
+    kernels = _kernels(D, H, Ci, Co)
+    assert kernels
+    for path in kernels + [U.CONV_TCGEN05]:
+        yf, yb = _run(path, x, w, b, D, H, W, Ci, Co, relu)
+        err = float((yf.double() - ref).norm() / ref.norm())
+        assert err < 1e-5, (path, err)
+        assert torch.all((yb.double() - yf.double()).abs() <= 2.0 ** -8 * yf.double().abs() + 1e-30)
 
 
-def test_tcgen05_conv_writes_only_its_channel_slice():
-    D, H, W, Ci, Co = 2, 2, 128, 16, 16
+@pytest.mark.parametrize("path", [U.CONV_TCGEN05_CHUNKED, U.CONV_TCGEN05_ZWALK], ids=["chunked", "z-walking"])
+def test_tcgen05_conv_writes_only_its_channel_slice(path):
+    D, H, W, Ci, Co = 2, 4, 128, 16, 16
     x, w, b = _operands(D, H, W, Ci, Co, seed=5)
     ref = _reference(x, w, b, D, H, W, Ci, Co, True)
-    yf, yb = _run(U.CONV_TCGEN05, x, w, b, D, H, W, Ci, Co, True, o_stride=48, o_off=16)
+    yf, yb = _run(path, x, w, b, D, H, W, Ci, Co, True, o_stride=48, o_off=16)
     assert torch.all(yf[:, :16] == 7.0) and torch.all(yf[:, 32:] == 7.0)
     assert torch.all(yb[:, :16] == 7.0) and torch.all(yb[:, 32:] == 7.0)
     assert float((yf[:, 16:32].double() - ref).norm() / ref.norm()) < 1e-5
@@ -91,10 +108,16 @@ def test_tcgen05_and_warp_mma_kernels_agree():
 
 
 def test_tcgen05_conv_rejects_shapes_it_cannot_tile():
-    for D, H, W in ((2, 2, 32), (3, 2, 64), (2, 2, 96)):
+    for D, H, W in ((2, 2, 32), (3, 2, 64), (2, 2, 96), (3, 6, 64)):
         x, w, b = _operands(D, H, W, 16, 16, seed=3)
         with pytest.raises(lt.LtError):
             _run(U.CONV_TCGEN05, x, w, b, D, H, W, 16, 16, False)
+    x, w, b = _operands(3, 4, 64, 16, 16, seed=4)      # odd D: the chunked kernel alone cannot
+    with pytest.raises(lt.LtError):
+        _run(U.CONV_TCGEN05_CHUNKED, x, w, b, 3, 4, 64, 16, 16, False)
+    x, w, b = _operands(2, 2, 64, 32, 16, seed=4)      # 32 input channels: not the z-walking kernel
+    with pytest.raises(lt.LtError):
+        _run(U.CONV_TCGEN05_ZWALK, x, w, b, 2, 2, 64, 32, 16, False)
 
 
 def test_unet_at_full_resolution_is_unchanged_by_the_tcgen05_layers(monkeypatch):
