@@ -95,7 +95,7 @@ residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const 
     const float d = alpha * p[base + i] - g * y[base + i];
     const float wi = w ? w[base + i] : 1.0f;
     r[base + i] = (alpha * wi) * d;
-    acc += (double)wi * (double)d * (double)d;
+    acc += (double)(wi * d * d);   // the term in float32 (FP64 units are scarce), the sum in float64
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) fit_part[((long long)blockIdx.y * C + c) * RED_BLOCKS + blockIdx.x] = 0.5 * acc;
