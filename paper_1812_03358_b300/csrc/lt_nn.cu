@@ -11,6 +11,7 @@
 #include "lt_host.h"
 #include "lt_nn.h"
 #include "lt_nn_tc.h"
+#include "lt_async.cuh"
 
 using namespace nvcuda;
 
@@ -73,22 +74,23 @@ conv3d_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, cons
 
   for (int c0 = 0; c0 < Ci; c0 += 16) {
     __syncthreads();   // the previous chunk's tiles are no longer read
+    // halo (zero outside the volume) and weights: all copies in flight at once
     for (int t = tid; t < CT_HALO * 2; t += CT_THREADS) {
       const int v = t >> 1, h = t & 1;
       const int hx = v % CT_HX, hy = (v / CT_HX) % CT_HY, hz = v / (CT_HX * CT_HY);
       const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
-        val = *reinterpret_cast<const uint4*>(inb + (((long long)gz * H + gy) * W + gx) * Ci + c0 + h * 8);
-      *reinterpret_cast<uint4*>(halo + v * 16 + h * 8) = val;
+      const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
+      const bf16* src = inside ? inb + (((long long)gz * H + gy) * W + gx) * Ci + c0 + h * 8 : inb;
+      cp_async16(smem_addr(halo + v * 16 + h * 8), src, inside);
     }
     for (int t = tid; t < 27 * NB * 2; t += CT_THREADS) {
       const int h = t & 1, r = t >> 1;
       const int co = r % NB, tap = r / NB;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (n0 + co < Co) val = *reinterpret_cast<const uint4*>(w + ((long long)(n0 + co) * 27 + tap) * Ci + c0 + h * 8);
-      *reinterpret_cast<uint4*>(wts + (tap * NB + co) * 16 + h * 8) = val;
+      const bool inside = n0 + co < Co;
+      const bf16* src = inside ? w + ((long long)(n0 + co) * 27 + tap) * Ci + c0 + h * 8 : w;
+      cp_async16(smem_addr(wts + (tap * NB + co) * 16 + h * 8), src, inside);
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int tap = 0; tap < 27; ++tap) {
       int dz, dy, dx;
@@ -177,24 +179,24 @@ conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g
     const bf16* inb = in + (long long)b * V * Ci;
     const bf16* gb = g + (long long)b * V * Co;
     __syncthreads();
+    // gradient tile and input halo (zero outside the volume): all copies in flight at once
     for (int t = tid; t < CT_MT * 16 * (MB / 8); t += CT_THREADS) {
       const int v = t / (MB / 8), q = t - v * (MB / 8);
       const int m = v >> 4, xr = v & 15;
       const int gx = x0 + xr, gy = y0 + m % CT_Y, gz = z0 + m / CT_Y;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (gx < W && gy < H && gz < D)
-        val = *reinterpret_cast<const uint4*>(gb + (((long long)gz * H + gy) * W + gx) * Co + n0 + q * 8);
-      *reinterpret_cast<uint4*>(&Gs[v][q * 8]) = val;
+      const bool inside = gx < W && gy < H && gz < D;
+      const bf16* src = inside ? gb + (((long long)gz * H + gy) * W + gx) * Co + n0 + q * 8 : gb;
+      cp_async16(smem_addr(&Gs[v][q * 8]), src, inside);
     }
     for (int t = tid; t < CT_HALO * 2; t += CT_THREADS) {
       const int v = t >> 1, h = t & 1;
       const int hx = v % CT_HX, hy = (v / CT_HX) % CT_HY, hz = v / (CT_HX * CT_HY);
       const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
-        val = *reinterpret_cast<const uint4*>(inb + (((long long)gz * H + gy) * W + gx) * Ci + c0 + h * 8);
-      *reinterpret_cast<uint4*>(halo + v * 16 + h * 8) = val;
+      const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
+      const bf16* src = inside ? inb + (((long long)gz * H + gy) * W + gx) * Ci + c0 + h * 8 : inb;
+      cp_async16(smem_addr(halo + v * 16 + h * 8), src, inside);
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int run = rsel; run < CT_MT; run += RS) {
       const int ty = run % CT_Y, tz = run / CT_Y;

@@ -29,6 +29,7 @@
 #include "lt_host.h"
 #include "lt_nn.h"
 #include "lt_nn_tc.h"
+#include "lt_async.cuh"
 
 namespace lt {
 namespace {
@@ -136,16 +137,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
 }
-
-// 16-byte global -> shared copy that does not pass through registers; with
-// valid == false it writes zeros and reads nothing (src must still be a
-// mapped address).  All of a thread's copies are in flight together until
-// cp_async_wait_all.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // 16 consecutive float32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
