@@ -6,6 +6,7 @@
 #include <mma.h>
 
 #include <algorithm>
+#include <initializer_list>
 
 #include "lt.h"
 #include "lt_host.h"
@@ -342,6 +343,143 @@ __global__ void copy_channels_kernel(const bf16* src, bf16* dst, long long voxel
     dst[v * ds + dof + c] = src[v * ss + so + c];
   }
 }
+// Vectorised forms of the pooling, upsampling and channel-copy kernels: one
+// thread per (coarse voxel, group of 8 channels), 16-byte loads and stores
+// and 32-bit index arithmetic, for channel counts, strides and offsets that
+// are multiples of 8 on 16-byte aligned buffers (every use in the network).
+// Per element they compute exactly what the scalar kernels above compute,
+// summing the eight fine voxels in the same order.
+struct V8 {
+  float v[8];
+};
+__device__ __forceinline__ V8 load8(const bf16* p) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+  V8 r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(h[i]);
+    r.v[2 * i] = f.x;
+    r.v[2 * i + 1] = f.y;
+  }
+  return r;
+}
+__device__ __forceinline__ void store8(bf16* p, const V8& r) {
+  uint4 u;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(r.v[2 * i], r.v[2 * i + 1]);
+  *reinterpret_cast<uint4*>(p) = u;
+}
+// thread index i over (batch, z, y, x, channel group) of a d x h x w grid
+__device__ __forceinline__ void coarse_index(unsigned i, int C8, int w, int h, int d, int& g, long long& vox, int& x,
+                                             int& y, int& z, int& b) {
+  g = (int)(i % C8);
+  unsigned u = i / C8;
+  vox = u;
+  x = (int)(u % w);
+  u /= w;
+  y = (int)(u % h);
+  u /= h;
+  z = (int)(u % d);
+  b = (int)(u / d);
+}
+// fine voxel k (0..7, z-major as in the scalar kernels) of coarse voxel (x, y, z)
+__device__ __forceinline__ long long fine_voxel(int k, int b, int z, int y, int x, int D, int H, int W) {
+  const int zz = 2 * z + (k >> 2), yy = 2 * y + ((k >> 1) & 1), xx = 2 * x + (k & 1);
+  return (((long long)b * D + zz) * H + yy) * W + xx;
+}
+
+__global__ void avgpool_vec_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, int batch, int D, int H,
+                                   int W, int C, int is, int io) {
+  const int d = D / 2, h = H / 2, w = W / 2, C8 = C / 8;
+  const unsigned n = (unsigned)batch * d * h * w * C8;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int g, x, y, z, b;
+    long long vox;
+    coarse_index(i, C8, w, h, d, g, vox, x, y, z, b);
+    V8 s;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s.v[c] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const V8 a = load8(in + fine_voxel(k, b, z, y, x, D, H, W) * is + io + 8 * g);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) s.v[c] += a.v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s.v[c] *= 0.125f;
+    store8(out + vox * C + 8 * g, s);
+  }
+}
+__global__ void avgpool_bwd_vec_kernel(const bf16* __restrict__ gout, bf16* __restrict__ gin, int batch, int D, int H,
+                                       int W, int C, int is, int io) {
+  const int d = D / 2, h = H / 2, w = W / 2, C8 = C / 8;
+  const unsigned n = (unsigned)batch * d * h * w * C8;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int g, x, y, z, b;
+    long long vox;
+    coarse_index(i, C8, w, h, d, g, vox, x, y, z, b);
+    V8 v = load8(gout + vox * C + 8 * g);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v.v[c] *= 0.125f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) store8(gin + fine_voxel(k, b, z, y, x, D, H, W) * is + io + 8 * g, v);
+  }
+}
+__global__ void upsample_vec_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, int batch, int d, int h,
+                                    int w, int C, int os, int oo) {
+  const int C8 = C / 8;
+  const unsigned n = (unsigned)batch * d * h * w * C8;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int g, x, y, z, b;
+    long long vox;
+    coarse_index(i, C8, w, h, d, g, vox, x, y, z, b);
+    const uint4 u = *reinterpret_cast<const uint4*>(in + vox * C + 8 * g);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      *reinterpret_cast<uint4*>(out + fine_voxel(k, b, z, y, x, 2 * d, 2 * h, 2 * w) * os + oo + 8 * g) = u;
+  }
+}
+__global__ void upsample_bwd_vec_kernel(const bf16* __restrict__ gout, bf16* __restrict__ gin, int batch, int d,
+                                        int h, int w, int C, int os, int oo) {
+  const int C8 = C / 8;
+  const unsigned n = (unsigned)batch * d * h * w * C8;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int g, x, y, z, b;
+    long long vox;
+    coarse_index(i, C8, w, h, d, g, vox, x, y, z, b);
+    V8 s;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s.v[c] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const V8 a = load8(gout + fine_voxel(k, b, z, y, x, 2 * d, 2 * h, 2 * w) * os + oo + 8 * g);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) s.v[c] += a.v[c];
+    }
+    store8(gin + vox * C + 8 * g, s);
+  }
+}
+__global__ void copy_channels_vec_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, unsigned n, int C8,
+                                         int ss, int so, int ds, int dof) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned v = i / C8;
+    const int g = (int)(i - v * C8);
+    *reinterpret_cast<uint4*>(dst + (long long)v * ds + dof + 8 * g) =
+        *reinterpret_cast<const uint4*>(src + (long long)v * ss + so + 8 * g);
+  }
+}
+
+// The vectorised kernels apply: channel counts, strides and offsets multiples
+// of 8, buffers 16-byte aligned, and fewer than 2^31 thread items.
+static bool vec8_ok(const void* a, const void* b, long long items, std::initializer_list<int> mult8) {
+  const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  for (int m : mult8)
+    if (m % 8) return false;
+  return al(a) && al(b) && items < (1LL << 31);
+}
+
 __global__ void adam_kernel(float* p, bf16* pb, const float* g, float* m, float* v, long long n, float lr, float b1,
                             float b2, float eps, float c1, float c2) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -538,8 +676,13 @@ extern "C" lt_status lt_nn_avgpool2(const uint16_t* in, uint16_t* out, int32_t b
       i_stride < i_off + C || i_off < 0)
     return set_error(LT_EINVAL, "avgpool2: bad arguments");
   const long long n = (long long)batch * (D / 2) * (H / 2) * (W / 2) * C;
-  avgpool_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(in), reinterpret_cast<bf16*>(out),
-                                                               batch, D, H, W, C, i_stride, i_off);
+  if (vec8_ok(in, out, n / 8, {C, i_stride, i_off}))
+    avgpool_vec_kernel<<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(in), reinterpret_cast<bf16*>(out), batch, D, H, W, C, i_stride, i_off);
+  else
+    avgpool_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(in),
+                                                                 reinterpret_cast<bf16*>(out), batch, D, H, W, C,
+                                                                 i_stride, i_off);
   return launched("avgpool2");
 }
 
@@ -550,9 +693,13 @@ extern "C" lt_status lt_nn_avgpool2_backward(const uint16_t* gout, uint16_t* gin
       i_stride < i_off + C || i_off < 0)
     return set_error(LT_EINVAL, "avgpool2_backward: bad arguments");
   const long long n = (long long)batch * D * H * W * C;
-  avgpool_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(gout),
-                                                                   reinterpret_cast<bf16*>(gin), batch, D, H, W, C,
-                                                                   i_stride, i_off);
+  if (vec8_ok(gout, gin, n / 64, {C, i_stride, i_off}))
+    avgpool_bwd_vec_kernel<<<grid1d(n / 64), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(gout), reinterpret_cast<bf16*>(gin), batch, D, H, W, C, i_stride, i_off);
+  else
+    avgpool_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(gout),
+                                                                     reinterpret_cast<bf16*>(gin), batch, D, H, W, C,
+                                                                     i_stride, i_off);
   return launched("avgpool2_backward");
 }
 
@@ -562,8 +709,13 @@ extern "C" lt_status lt_nn_upsample2(const uint16_t* in, uint16_t* out, int32_t 
   if (!in || !out || batch <= 0 || d <= 0 || h <= 0 || w <= 0 || C <= 0 || o_stride < o_off + C || o_off < 0)
     return set_error(LT_EINVAL, "upsample2: bad arguments");
   const long long n = (long long)batch * 8 * d * h * w * C;
-  upsample_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(in), reinterpret_cast<bf16*>(out),
-                                                                batch, d, h, w, C, o_stride, o_off);
+  if (vec8_ok(in, out, n / 64, {C, o_stride, o_off}))
+    upsample_vec_kernel<<<grid1d(n / 64), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(in), reinterpret_cast<bf16*>(out), batch, d, h, w, C, o_stride, o_off);
+  else
+    upsample_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(in),
+                                                                  reinterpret_cast<bf16*>(out), batch, d, h, w, C,
+                                                                  o_stride, o_off);
   return launched("upsample2");
 }
 
@@ -573,9 +725,13 @@ extern "C" lt_status lt_nn_upsample2_backward(const uint16_t* gout, uint16_t* gi
   if (!gout || !gin || batch <= 0 || d <= 0 || h <= 0 || w <= 0 || C <= 0 || o_stride < o_off + C || o_off < 0)
     return set_error(LT_EINVAL, "upsample2_backward: bad arguments");
   const long long n = (long long)batch * d * h * w * C;
-  upsample_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(gout),
-                                                                    reinterpret_cast<bf16*>(gin), batch, d, h, w, C,
-                                                                    o_stride, o_off);
+  if (vec8_ok(gout, gin, n / 8, {C, o_stride, o_off}))
+    upsample_bwd_vec_kernel<<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(gout), reinterpret_cast<bf16*>(gin), batch, d, h, w, C, o_stride, o_off);
+  else
+    upsample_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(gout),
+                                                                      reinterpret_cast<bf16*>(gin), batch, d, h, w, C,
+                                                                      o_stride, o_off);
   return launched("upsample2_backward");
 }
 
@@ -584,7 +740,11 @@ extern "C" lt_status lt_nn_copy_channels(const uint16_t* src, uint16_t* dst, int
   clear_error();
   if (!src || !dst || voxels < 0 || C <= 0 || s_stride < s_off + C || d_stride < d_off + C || s_off < 0 || d_off < 0)
     return set_error(LT_EINVAL, "copy_channels: bad arguments");
-  if (voxels)
+  if (voxels && vec8_ok(src, dst, voxels * C / 8, {C, s_stride, s_off, d_stride, d_off}))
+    copy_channels_vec_kernel<<<grid1d(voxels * C / 8), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(src), reinterpret_cast<bf16*>(dst), (unsigned)(voxels * C / 8), C / 8, s_stride,
+        s_off, d_stride, d_off);
+  else if (voxels)
     copy_channels_kernel<<<grid1d(voxels * C), 256, 0, (cudaStream_t)stream>>>(
         reinterpret_cast<const bf16*>(src), reinterpret_cast<bf16*>(dst), voxels, C, s_stride, s_off, d_stride, d_off);
   return launched("copy_channels");
