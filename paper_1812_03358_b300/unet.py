@@ -71,35 +71,58 @@ def pool(s, p, d, C):
     _need(s, int(np.prod(d)) * C, "avgpool input")
     if p.numel() != int(np.prod(d)) * C // 8:
         raise ValueError("avgpool output shape")
-    _call("lt_nn_avgpool2", _p(s), _p(p), 1, *d, C, C, 0, _s())
+    _call("lt_nn_avgpool2", _pb(s), _pb(p), 1, *d, C, C, 0, _s())
 
 
 def pool_back(g, gs, d, C):
     if g.numel() != int(np.prod(d)) * C // 8 or gs.numel() != int(np.prod(d)) * C:
         raise ValueError("avgpool backward shapes")
-    _call("lt_nn_avgpool2_backward", _p(g), _p(gs), 1, *d, C, C, 0, _s())
+    _call("lt_nn_avgpool2_backward", _pb(g), _pb(gs), 1, *d, C, C, 0, _s())
 
 
 def upsample(x, cat, dsmall, cx, ctot):
     if x.numel() != int(np.prod(dsmall)) * cx or cat.numel() != 8 * int(np.prod(dsmall)) * ctot:
         raise ValueError("upsample shapes")
-    _call("lt_nn_upsample2", _p(x), _p(cat), 1, *dsmall, cx, ctot, 0, _s())
+    _call("lt_nn_upsample2", _pb(x), _pb(cat), 1, *dsmall, cx, ctot, 0, _s())
 
 
 def upsample_back(g, gx, dsmall, cx, ctot):
     if gx.numel() != int(np.prod(dsmall)) * cx or g.numel() != 8 * int(np.prod(dsmall)) * ctot:
         raise ValueError("upsample backward shapes")
-    _call("lt_nn_upsample2_backward", _p(g), _p(gx), 1, *dsmall, cx, ctot, 0, _s())
+    _call("lt_nn_upsample2_backward", _pb(g), _pb(gx), 1, *dsmall, cx, ctot, 0, _s())
 
 
 def copy_channels(src, dst, voxels, C, s_stride, s_off, d_stride, d_off):
     if src.numel() != voxels * s_stride or dst.numel() != voxels * d_stride:
         raise ValueError("copy_channels shapes")
-    _call("lt_nn_copy_channels", _p(src), _p(dst), voxels, C, s_stride, s_off, d_stride, d_off, _s())
+    _call("lt_nn_copy_channels", _pb(src), _pb(dst), voxels, C, s_stride, s_off, d_stride, d_off, _s())
 
 
 def _p(t):
     return t.data_ptr() if t is not None else None
+
+
+def _ptr(t, dtype, what):
+    """Device pointer of a contiguous tensor of the element type the kernel
+    reads or writes (a tensor of another type would make it run past the
+    buffer); None passes through."""
+    if t is None:
+        return None
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: the tensor must be contiguous")
+    if t.device.type != torch.device(DEVICE).type:
+        raise ValueError(f"{what}: expected a {DEVICE} tensor, got {t.device}")
+    return t.data_ptr()
+
+
+def _pb(t, what="bfloat16 operand"):
+    return _ptr(t, torch.bfloat16, what)
+
+
+def _pf(t, what="float32 operand"):
+    return _ptr(t, torch.float32, what)
 
 
 def _s():
@@ -141,7 +164,8 @@ def conv3d(inp, w, b, out_bf=None, out_f=None, *, Ci, Co, dims, o_stride=None, o
     _need(out_f, V * (o_stride or Co), "conv3d output")
     if inp.numel() != V * Ci:
         raise ValueError("conv3d input shape does not match dims x Ci")
-    _call("lt_nn_conv3d_ex", _p(inp), _p(w), _p(b), _p(out_bf), _p(out_f), 1, D, H, W, Ci, Co,
+    _call("lt_nn_conv3d_ex", _pb(inp, "conv3d input"), _pb(w, "conv3d weights"), _pf(b, "conv3d bias"),
+          _pb(out_bf, "conv3d output"), _pf(out_f, "conv3d output"), 1, D, H, W, Ci, Co,
           o_stride or Co, o_off, int(relu), int(path), _s())
 
 
@@ -152,7 +176,8 @@ def conv3d_wgrad(inp, g, dw, db, *, Ci, Co, dims):
         raise ValueError("conv3d_wgrad: input / gradient shapes do not match dims")
     _need(dw, 27 * Ci * Co, "conv3d_wgrad dw")
     _need(db, Co, "conv3d_wgrad db")
-    _call("lt_nn_conv3d_wgrad", _p(inp), _p(g), _p(dw), _p(db), 1, D, H, W, Ci, Co, _s())
+    _call("lt_nn_conv3d_wgrad", _pb(inp, "wgrad input"), _pb(g, "wgrad gradient"), _pf(dw, "wgrad dw"),
+          _pf(db, "wgrad db"), 1, D, H, W, Ci, Co, _s())
 
 
 class Conv:
@@ -173,19 +198,19 @@ class Conv:
         self.sync_bf16()
 
     def sync_bf16(self):
-        _call("lt_nn_f32_to_bf16", _p(self.w), _p(self.wb), self.w.numel(), _s())
+        _call("lt_nn_f32_to_bf16", _pf(self.w), _pb(self.wb), self.w.numel(), _s())
 
     def flip(self):
-        _call("lt_nn_conv3d_flip", _p(self.wb), _p(self.wt), self.ci, self.co, _s())
+        _call("lt_nn_conv3d_flip", _pb(self.wb), _pb(self.wt), self.ci, self.co, _s())
 
     def zero_grad(self):
         self.gw.zero_()
         self.gb.zero_()
 
     def adam(self, lr, step):
-        _call("lt_nn_adam", _p(self.w), _p(self.wb), _p(self.gw), _p(self.mw), _p(self.vw), self.w.numel(),
+        _call("lt_nn_adam", _pf(self.w), _pb(self.wb), _pf(self.gw), _pf(self.mw), _pf(self.vw), self.w.numel(),
               lr, 0.9, 0.999, 1e-8, step, _s())
-        _call("lt_nn_adam", _p(self.b), None, _p(self.gb), _p(self.mb), _p(self.vb), self.b.numel(),
+        _call("lt_nn_adam", _pf(self.b), None, _pf(self.gb), _pf(self.mb), _pf(self.vb), self.b.numel(),
               lr, 0.9, 0.999, 1e-8, step, _s())
 
 
@@ -288,7 +313,7 @@ class UNet:
         if relu:
             if out_act.numel() != g.numel():
                 raise ValueError("relu backward shapes")
-            _call("lt_nn_relu_backward", _p(out_act), _p(g), g.numel(), _s())
+            _call("lt_nn_relu_backward", _pb(out_act), _pb(g), g.numel(), _s())
         conv3d_wgrad(inp, g, conv.gw, conv.gb, Ci=conv.ci, Co=conv.co, dims=dims)
         conv.flip()
         gi = bf16(*dims, conv.ci)
@@ -298,10 +323,13 @@ class UNet:
     def backward(self, g_out):
         """g_out: float32 gradient w.r.t. the output [D][H][W][16]."""
         acts, dims = self._acts, self._dims
+        if g_out.dtype != torch.float32 or tuple(g_out.shape) != (*dims[0], 16):
+            raise TypeError(f"backward: expected a float32 {(*dims[0], 16)} gradient, got {g_out.dtype} "
+                            f"{tuple(g_out.shape)}")
         for c in self.convs():
             c.zero_grad()
         g = bf16(*g_out.shape)
-        _call("lt_nn_f32_to_bf16", _p(g_out), _p(g), g_out.numel(), _s())
+        _call("lt_nn_f32_to_bf16", _pf(g_out, "output gradient (float32)"), _pb(g), g_out.numel(), _s())
         (x,) = acts["head"]
         g = self._conv_back(self.head, x, None, g, dims[0], relu=False)
         skip_grads = [None, None, None]
@@ -330,7 +358,7 @@ class UNet:
             pool_back(g, gs, d, cb.co)
             if skip_grads[l].numel() != gs.numel():
                 raise ValueError("skip gradient shape")
-            _call("lt_nn_add", _p(gs), _p(skip_grads[l]), _p(gs), gs.numel(), _s())
+            _call("lt_nn_add", _pb(gs), _pb(skip_grads[l]), _pb(gs), gs.numel(), _s())
             g = self._conv_back(cb, a, s, gs, d)
             g = self._conv_back(ca, x, a, g, d)
         return g
@@ -359,21 +387,23 @@ class WarmStart:
         self.u = bf16(*self.dims, 16)
 
     def prepare(self, bp):
-        _call("lt_nn_prepare_input", _p(bp), _p(self.D), _p(self.r), _p(self.m), _p(self.u), self.r.numel(), _s())
+        _call("lt_nn_prepare_input", _pf(bp, "back-projection"), _pf(self.D), _pf(self.r), _pf(self.m), _pb(self.u),
+              self.r.numel(), _s())
         return self.u
 
     def infer(self, bp):
         """x0 (float32 [n_vox]) from a back-projection A^T y."""
         out = self.net.forward(self.prepare(bp))
         x0 = torch.empty(self.r.numel(), device="cuda")
-        _call("lt_nn_unpack_output", _p(out), _p(self.m), _p(x0), x0.numel(), _s())
+        _call("lt_nn_unpack_output", _pf(out), _pf(self.m), _pf(x0), x0.numel(), _s())
         return x0
 
     def train_step(self, bp, x_true, lr):
         out = self.net.forward(self.prepare(bp), keep=True)
         g = torch.empty_like(out)
         self.loss.zero_()
-        _call("lt_nn_mse", _p(out), _p(x_true), _p(self.m), _p(g), _p(self.loss), x_true.numel(), _s())
+        _call("lt_nn_mse", _pf(out), _pf(x_true, "target volume"), _pf(self.m), _pf(g), _pf(self.loss), x_true.numel(),
+              _s())
         self.net.backward(g)
         self.net.adam_step(lr)
         return self.loss

@@ -130,7 +130,7 @@ def test_unet_at_full_resolution_is_unchanged_by_the_tcgen05_layers(monkeypatch)
     x = torch.zeros(n, n, n, 16)
     x[..., 0] = torch.rand(n, n, n, generator=g)
     xb = x.bfloat16().cuda()
-    gout = (0.01 * torch.randn(n, n, n, 16, generator=g)).bfloat16().cuda()
+    gout = (0.01 * torch.randn(n, n, n, 16, generator=g)).cuda()   # float32, as backward expects
 
     def run():
         out = net.forward(xb, keep=True).float().clone()

@@ -23,3 +23,28 @@ def test_forward_backward_shapes(monkeypatch):
     with pytest.raises(ValueError):
         unet.conv3d(torch.zeros(10, dtype=torch.bfloat16), net.head.wb, None, torch.zeros(10, dtype=torch.bfloat16),
                     Ci=16, Co=16, dims=(2, 2, 2))
+
+
+def test_layer_calls_reject_wrong_element_types(monkeypatch):
+    """A tensor of the wrong element type would make a kernel read or write
+    past its buffer (a bfloat16 gradient read as float32 is twice as long):
+    the binding refuses it before anything is launched."""
+    calls = []
+    monkeypatch.setattr(unet, "DEVICE", "cpu")
+    monkeypatch.setattr(unet, "_call", lambda name, *a: calls.append(name))
+    monkeypatch.setattr(unet, "_s", lambda: 0)
+    net = unet.UNet(seed=0)
+    x = torch.zeros(16, 16, 16, 16, dtype=torch.bfloat16)
+    out = net.forward(x, keep=True)
+    n = len(calls)
+    with pytest.raises(TypeError):
+        net.backward(torch.zeros_like(out).bfloat16())
+    with pytest.raises(TypeError):
+        net.backward(torch.zeros(8, 8, 8, 16))              # wrong shape
+    with pytest.raises(TypeError):
+        unet.conv3d(torch.zeros(2 * 2 * 2 * 16), net.head.wb, None, torch.zeros(2 * 2 * 2 * 16, dtype=torch.bfloat16),
+                    Ci=16, Co=16, dims=(2, 2, 2))            # float32 input where bfloat16 is read
+    with pytest.raises(TypeError):
+        unet.conv3d(torch.zeros(8 * 16, dtype=torch.bfloat16), net.head.wb, None, None,
+                    torch.zeros(8 * 16, dtype=torch.bfloat16), Ci=16, Co=16, dims=(2, 2, 2))   # bf16 out_f
+    assert len(calls) == n                                   # nothing reached the library
