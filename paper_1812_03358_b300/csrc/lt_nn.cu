@@ -230,6 +230,95 @@ conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g
   }
 }
 
+// Weight gradient for 16 output channels (one channel tile) with all 27 taps
+// in one CTA: warp w owns taps 7w .. 7w + 6 (the last warp six), each a
+// 16 x 16 accumulator, and runs all eight 16-voxel x runs of every staged
+// block against them.  Staged once per block for all taps (the kernel above
+// stages each block once per dz: three times), and each warp issues 56 MMAs
+// per staged block instead of 18.  One float atomic add per weight entry per
+// CTA, as above.
+__global__ void __launch_bounds__(CT_THREADS)
+conv3d_wgrad27_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ dw, int D, int H,
+                      int W, int Ci, int Co, int tiles_x, int tiles_y, int tiles_z, long long n_tiles,
+                      int tiles_per_cta) {
+  constexpr int TPW = 7;   // taps per warp: 4 x 7 >= 27
+  __shared__ __align__(128) bf16 Gs[CT_MT * 16][16];      // [voxel of the block][co]
+  __shared__ __align__(128) bf16 halo[CT_HALO * 16];
+  __shared__ __align__(128) float red[4][16][16];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_ci = Ci / 16;
+  const int cc = blockIdx.y % n_ci, nc = blockIdx.y / n_ci;
+  const int c0 = cc * 16, n0 = nc * 16;
+  const long long V = (long long)D * H * W;
+  const long long t_begin = (long long)blockIdx.x * tiles_per_cta;
+  const long long t_end = t_begin + tiles_per_cta < n_tiles ? t_begin + tiles_per_cta : n_tiles;
+
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[TPW];
+#pragma unroll
+  for (int j = 0; j < TPW; ++j) wmma::fill_fragment(acc[j], 0.0f);
+
+  for (long long tile = t_begin; tile < t_end; ++tile) {
+    long long r = tile;
+    const int bx = (int)(r % tiles_x);
+    r /= tiles_x;
+    const int by = (int)(r % tiles_y);
+    r /= tiles_y;
+    const int bz = (int)(r % tiles_z);
+    const int b = (int)(r / tiles_z);
+    const int x0 = bx * CT_X, y0 = by * CT_Y, z0 = bz * CT_Z;
+    const bf16* inb = in + (long long)b * V * Ci;
+    const bf16* gb = g + (long long)b * V * Co;
+    __syncthreads();   // the previous block's tiles are no longer read
+    for (int t = tid; t < CT_MT * 16 * 2; t += CT_THREADS) {
+      const int v = t >> 1, q = t & 1;
+      const int m = v >> 4, xr = v & 15;
+      const int gx = x0 + xr, gy = y0 + m % CT_Y, gz = z0 + m / CT_Y;
+      const bool inside = gx < W && gy < H && gz < D;
+      const bf16* src = inside ? gb + (((long long)gz * H + gy) * W + gx) * Co + n0 + q * 8 : gb;
+      cp_async16(smem_addr(&Gs[v][q * 8]), src, inside);
+    }
+    for (int t = tid; t < CT_HALO * 2; t += CT_THREADS) {
+      const int v = t >> 1, h = t & 1;
+      const int hx = v % CT_HX, hy = (v / CT_HX) % CT_HY, hz = v / (CT_HX * CT_HY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+      const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
+      const bf16* src = inside ? inb + (((long long)gz * H + gy) * W + gx) * Ci + c0 + h * 8 : inb;
+      cp_async16(smem_addr(halo + v * 16 + h * 8), src, inside);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int run = 0; run < CT_MT; ++run) {
+      const int ty = run % CT_Y, tz = run / CT_Y;
+      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> a;
+      wmma::load_matrix_sync(a, &Gs[run * 16][0], 16);
+#pragma unroll
+      for (int j = 0; j < TPW; ++j) {
+        const int tap = warp * TPW + j;
+        if (tap < 27) {   // uniform over the warp
+          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+          const bf16* bp = halo + (((tz + dz + 1) * CT_HY + (ty + dy + 1)) * CT_HX + (dx + 1)) * 16;
+          wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bfr;
+          wmma::load_matrix_sync(bfr, bp, 16);
+          wmma::mma_sync(acc[j], a, bfr, acc[j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < TPW; ++j) {
+    const int tap = warp * TPW + j;
+    if (tap < 27) {
+      wmma::store_matrix_sync(&red[warp][0][0], acc[j], 16, wmma::mem_row_major);
+      __syncwarp();
+      for (int e = lane; e < 256; e += 32) {
+        const int i = e >> 4, c = e & 15;
+        atomicAdd(dw + ((long long)(n0 + i) * 27 + tap) * Ci + c0 + c, red[warp][i][c]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
 __global__ void bias_grad_kernel(const bf16* __restrict__ g, float* __restrict__ db, long long vtot, int Co) {
   // one block per output channel chunk of 32; threads stride over voxels
   const int co = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -618,7 +707,8 @@ extern "C" lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, f
   const int mb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
   const int tx = (W + CT_X - 1) / CT_X, ty = (H + CT_Y - 1) / CT_Y, tz = (D + CT_Z - 1) / CT_Z;
   const long long n_tiles = (long long)tx * ty * tz * batch;
-  const long long groups = 3LL * (Ci / 16) * (Co / mb);
+  const bool all_taps = mb == 16;   // one channel tile: every tap in one CTA
+  const long long groups = (all_taps ? 1LL : 3LL) * (Ci / 16) * (Co / mb);
   if (groups > 65535) return set_error(LT_EINVAL, "conv3d_wgrad: too many channel groups");
   // about four waves of CTAs over the 148 SMs, each walking a run of voxel blocks
   const long long want = std::max<long long>(1, (148LL * 4 + groups - 1) / groups);
@@ -627,7 +717,9 @@ extern "C" lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, f
   dim3 grid(gx, (unsigned)groups);
   const bf16* i_ = reinterpret_cast<const bf16*>(in);
   const bf16* g_ = reinterpret_cast<const bf16*>(g);
-  if (mb == 64)
+  if (all_taps)
+    conv3d_wgrad27_kernel<<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+  else if (mb == 64)
     conv3d_wgrad_tile_kernel<64><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
   else if (mb == 32)
     conv3d_wgrad_tile_kernel<32><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
