@@ -565,7 +565,7 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
       if (nds <= 0 || ndt <= 0) continue;   // uniform
       lenslet_weights(L, dr, cc, rr, Bs, Bt);
       const float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
-      const SmallDiv dc = small_div(nc), dd = small_div(nds), du_ = small_div(nsu);
+      const SmallDiv dc = small_div(nc), dd = small_div(nds);
       for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
         const int r = div_of(dc, o), c = o - r * nc;
         const long long px = (long long)(rr.x + r) * s2.arr_ns + cc.x + c;
@@ -580,15 +580,16 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
         W[r][q] = w;
       }
       __syncthreads();
-      // Z[it][is] += scale * sum_r Bt[r][b] W[r][q]  (entries owned by one thread)
+      // Z[it][is] += scale * sum_r Bt[r][b] W[r][q] over the cell's own
+      // window inside the union (entries owned by one thread)
       const float scale = L->scale;
-      for (int o = threadIdx.x; o < ntu * nsu; o += blockDim.x) {
-        const int ob = div_of(du_, o);
-        const int b = ob + du.z - dr.z, q = o - ob * nsu + du.x - dr.x;
-        if (b < 0 || b >= ndt || q < 0 || q >= nds) continue;
+      const int zoff = (dr.z - du.z) * nsu + (dr.x - du.x);
+      for (int o = threadIdx.x; o < ndt * nds; o += blockDim.x) {
+        const int b = div_of(dd, o), q = o - b * nds;
+        const int zi = zoff + b * nsu + q;
         float z = 0.0f;
         for (int r = 0; r < nr; ++r) z = fmaf(Bt[r][b], W[r][q], z);
-        Z[o] = fmaf(scale, z, Z[o]);
+        Z[zi] = fmaf(scale, z, Z[zi]);
       }
       __syncthreads();
     }
