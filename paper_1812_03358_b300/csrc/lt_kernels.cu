@@ -557,6 +557,24 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
   const long long Na = (long long)s2.arr_ns * s2.arr_nt;
   for (int o = threadIdx.x; o < L2_W * L2_W; o += blockDim.x) Z[o] = 0.0f;
   if (nc > 0 && nr > 0 && nsu > 0 && ntu > 0) {
+    // this thread's block pixels (at most MAXC^2 = 2 x L2_THREADS): array
+    // index, -1 where another lenslet (or none) owns the pixel, and the
+    // position in F; the same for every cell
+    static_assert(MAXC * MAXC <= 2 * L2_THREADS, "two block pixels per thread");
+    const SmallDiv dc = small_div(nc);
+    int pix[2], fix[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int o = threadIdx.x + e * L2_THREADS;
+      pix[e] = -1;
+      fix[e] = -1;
+      if (o < nr * nc) {
+        const int r = div_of(dc, o), c = o - r * nc;
+        const int px = (rr.x + r) * s2.arr_ns + cc.x + c;
+        pix[e] = __ldg(s2.owner + px) == mu ? px : -1;
+        fix[e] = r * (MAXC + 1) + c;
+      }
+    }
     for (int k = 0; k < s2.K; ++k) {
       if (!cell_on(s2.sub_n, s2.sub_s, k)) continue;   // uniform
       const LensletParam* L = s2.lens + (long long)k * nmu + mu;
@@ -565,12 +583,10 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
       if (nds <= 0 || ndt <= 0) continue;   // uniform
       lenslet_weights(L, dr, cc, rr, Bs, Bt);
       const float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
-      const SmallDiv dc = small_div(nc), dd = small_div(nds);
-      for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
-        const int r = div_of(dc, o), c = o - r * nc;
-        const long long px = (long long)(rr.x + r) * s2.arr_ns + cc.x + c;
-        F[r][c] = __ldg(s2.owner + px) == mu ? __ldg(fk + px) : 0.0f;   // this lenslet's own pixels
-      }
+      const SmallDiv dd = small_div(nds);
+#pragma unroll
+      for (int e = 0; e < 2; ++e)   // this lenslet's own pixels, zero elsewhere
+        if (fix[e] >= 0) (&F[0][0])[fix[e]] = pix[e] >= 0 ? __ldg(fk + pix[e]) : 0.0f;
       __syncthreads();
       // W[r][q] = sum_c Bs[c][q] F[r][c]
       for (int o = threadIdx.x; o < nr * nds; o += blockDim.x) {
@@ -620,7 +636,7 @@ stage2_gather(const float* __restrict__ zbuf, float* __restrict__ y, StageTwo s2
 
 // Adjoint: fa_k[jt][js] = M * scale * sum_b sum_q Bt[r][b] Bs[c][q] y[dr.z+b][dr.x+q]
 // for the lenslet's own block (a gather: every array pixel has one lenslet).
-__global__ void __launch_bounds__(L2_THREADS)
+__global__ void __launch_bounds__(L2_THREADS, 16)
 stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, StageTwo s2, long long y_fs,
                        long long fa_fs) {
   __shared__ float Bs[MAXC][L2_W + 1];
@@ -635,22 +651,47 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
   if (nc <= 0 || nr <= 0) return;   // uniform
   const long long Na = (long long)s2.arr_ns * s2.arr_nt;
   const float* yf = y + (long long)frame * y_fs;
+  // This thread's block pixels (at most MAXC^2 = 2 x L2_THREADS) and what is
+  // written there, the same for every cell: M g on the lenslet's own pixels
+  // (wpx = index, mv = M), zero on unowned pixels of blocks that tile the
+  // plane (wpx = -(index + 2)), nothing elsewhere (wpx = -1); rcx = (r, c).
+  static_assert(MAXC * MAXC <= 2 * L2_THREADS, "two block pixels per thread");
+  const SmallDiv dc = small_div(nc);
+  int wpx[2], rcx[2];
+  float mv[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int o = threadIdx.x + e * L2_THREADS;
+    wpx[e] = -1;
+    rcx[e] = -1;
+    mv[e] = 0.0f;
+    if (o < nr * nc) {
+      const int r = div_of(dc, o), c = o - r * nc;
+      const int px = (rr.x + r) * s2.arr_ns + cc.x + c;
+      const int own = __ldg(s2.owner + px);
+      rcx[e] = (r << 8) | c;
+      if (own == mu) {
+        wpx[e] = px;
+        mv[e] = __ldg(s2.mask + px);
+      } else if (!s2.overlap && own < 0) {
+        wpx[e] = -(px + 2);
+      }
+    }
+  }
   for (int k = 0; k < s2.K; ++k) {
     if (!cell_on(s2.sub_n, s2.sub_s, k)) continue;   // uniform: plane k is left unwritten
     const LensletParam* L = s2.lens + (long long)k * nmu + mu;
     const int4 dr = s2.det_range[(long long)k * nmu + mu];
     const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
     float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
-    if (nds <= 0 || ndt <= 0) {
-      for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
-        const long long px = (long long)(rr.x + o / nc) * s2.arr_ns + cc.x + o % nc;
-        const int own = __ldg(s2.owner + px);
-        if (own == mu || (!s2.overlap && own < 0)) fk[px] = 0.0f;
-      }
+    if (nds <= 0 || ndt <= 0) {   // no detector pixel: the block's written pixels are zero
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        if (wpx[e] != -1) fk[wpx[e] >= 0 ? wpx[e] : -(wpx[e] + 2)] = 0.0f;
       continue;   // uniform
     }
     lenslet_weights(L, dr, cc, rr, Bs, Bt);
-    const SmallDiv dd = small_div(nds), dc = small_div(nc);
+    const SmallDiv dd = small_div(nds);
     for (int o = threadIdx.x; o < ndt * nds; o += blockDim.x) {
       const int b = div_of(dd, o), q = o - b * nds;
       Y[b][q] = __ldg(yf + (long long)(dr.z + b) * s2.det_ns + dr.x + q);
@@ -665,17 +706,18 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
     }
     __syncthreads();
     const float scale = L->scale;
-    for (int o = threadIdx.x; o < nr * nc; o += blockDim.x) {
-      const int r = div_of(dc, o), c = o - r * nc;
-      const int jt = rr.x + r, js = cc.x + c;
-      float g = 0.0f;
-      for (int q = 0; q < nds; ++q) g = fmaf(Bs[c][q], U[r][q], g);
-      const long long px = (long long)jt * s2.arr_ns + js;
-      const int own = __ldg(s2.owner + px);
-      // M (its diagonal) on this lenslet's own pixels; blocks that tile the
-      // plane also clear their unowned pixels, overlapping blocks leave them
-      if (own == mu) fk[px] = __ldg(s2.mask + px) * (scale * g);
-      else if (!s2.overlap && own < 0) fk[px] = 0.0f;
+    // M (its diagonal) on this lenslet's own pixels; blocks that tile the
+    // plane also clear their unowned pixels, overlapping blocks leave them
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (wpx[e] >= 0) {
+        const int r = rcx[e] >> 8, c = rcx[e] & 255;
+        float g = 0.0f;
+        for (int q = 0; q < nds; ++q) g = fmaf(Bs[c][q], U[r][q], g);
+        fk[wpx[e]] = mv[e] * (scale * g);
+      } else if (wpx[e] != -1) {
+        fk[-(wpx[e] + 2)] = 0.0f;
+      }
     }
     __syncthreads();
   }

@@ -347,6 +347,9 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   const lt_camera_desc& d = c.desc;
   const int mns = d.mla_ns, mnt = d.mla_nt;
   const int nmu = mns * mnt;
+  if ((long long)d.arr_ns * d.arr_nt >= (1LL << 31))   // the stage-2 kernels index one array plane in 32 bits
+    return set_error(LT_EUNSUPPORTED, "camera %d: array plane of %d x %d pixels (limit 2^31 pixels)", idx, d.arr_ns,
+                     d.arr_nt);
   const bool hex = d.mla_layout == LT_MLA_HEX;
   // Lenslet centres: the square grid, or the hexagonal lattice (rows
   // pitch sqrt(3)/2 apart, odd rows shifted by half a pitch, centred on the
