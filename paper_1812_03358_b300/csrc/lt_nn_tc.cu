@@ -4,7 +4,7 @@
 // 64 (the full- and half-resolution levels of the network), the warp-level
 // MMA kernel of lt_nn.cu for the rest.
 //
-// A CTA owns a TM (x) x 2 (y) x 2 (z) block of output voxels -- four tiles,
+// Chunked kernel: a CTA owns a TM (x) x 2 (y) x 2 (z) block of output voxels -- four tiles,
 // one x run of TM = 128 (or 64) voxels each, one M = 128 MMA row per voxel
 // (rows past TM unused) -- and N = 16, 32 or 48 output channels.  Per
 // chunk of 16 input channels it stages the input halo (130 x 4 x 4 voxels)
@@ -17,6 +17,10 @@
 // CTA when the tensor core is done with the staged data.  The epilogue reads
 // the accumulators with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e.
 // x voxels 32w..32w+31 of every tile), adds the bias, applies ReLU and stores.
+// That is the chunked kernel; layers with 16 input channels and large grids
+// take the z-walking kernel below (a CTA walks 8 slices in z over a ring of
+// three input planes, so each plane is staged once per CTA and staging
+// overlaps the other CTA's MMAs).
 //
 // Every wait on the mbarrier is bounded; a wait that gives up records
 // LT_ETIMEOUT in a device status word (lt_nn_device_status), skips the rest
