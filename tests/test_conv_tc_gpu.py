@@ -152,3 +152,28 @@ def test_unet_at_full_resolution_is_unchanged_by_the_tcgen05_layers(monkeypatch)
     out_w, gin_w = run()
     assert float((out_tc - out_w).norm() / out_w.norm()) < 1e-5
     assert float((gin_tc - gin_w).norm() / gin_w.norm()) < 1e-5
+
+
+@pytest.mark.parametrize("path", [U.CONV_TCGEN05_CHUNKED, U.CONV_TCGEN05_ZWALK, U.CONV_WARP_MMA],
+                         ids=["chunked", "z-walking", "warp-mma"])
+def test_batched_frames_are_independent(path):
+    """Two frames in one call (the ABI's batch argument): each equals the
+    reference convolution of its own frame."""
+    D, H, W, Ci, Co = 2, 4, 128, 16, 16
+    xs, refs = [], []
+    w = b = None
+    for f in range(2):
+        x, w_, b_ = _operands(D, H, W, Ci, Co, seed=40)
+        x = (x.float() * (1.0 + f)).to(torch.bfloat16)         # a different frame, same weights
+        w, b = w_, b_
+        xs.append(x)
+        refs.append(_reference(x, w, b, D, H, W, Ci, Co, True))
+    V = D * H * W
+    xin, wd, bd = torch.cat(xs).cuda(), w.cuda(), b.cuda()   # alive until the kernel has run
+    out_f = torch.full((2 * V * Co,), 7.0, device="cuda")
+    U._call("lt_nn_conv3d_ex", xin.data_ptr(), wd.data_ptr(), bd.data_ptr(), None, out_f.data_ptr(),
+            2, D, H, W, Ci, Co, Co, 0, 1, path, U._s())
+    U.device_status()
+    y = out_f.reshape(2, V, Co).cpu().double()
+    for f in range(2):
+        assert float((y[f] - refs[f]).norm() / refs[f].norm()) < 1e-5, f
