@@ -560,6 +560,67 @@ __global__ void copy_channels_vec_kernel(const bf16* __restrict__ src, bf16* __r
   }
 }
 
+// Elementwise kernels on 8 values per thread (16-byte accesses).
+__global__ void relu_bwd_vec_kernel(const bf16* __restrict__ y, bf16* __restrict__ g, unsigned n8) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += gridDim.x * blockDim.x) {
+    const V8 a = load8(y + 8LL * i);
+    V8 b = load8(g + 8LL * i);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (!(a.v[c] > 0.0f)) b.v[c] = 0.0f;
+    store8(g + 8LL * i, b);
+  }
+}
+__global__ void add_vec_kernel(const bf16* __restrict__ a, const bf16* __restrict__ b, bf16* __restrict__ out,
+                               unsigned n8) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += gridDim.x * blockDim.x) {
+    V8 x = load8(a + 8LL * i);
+    const V8 y = load8(b + 8LL * i);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x.v[c] += y.v[c];
+    store8(out + 8LL * i, x);
+  }
+}
+__global__ void f2b_vec_kernel(const float* __restrict__ x, bf16* __restrict__ y, unsigned n8) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += gridDim.x * blockDim.x) {
+    const float4 p = *reinterpret_cast<const float4*>(x + 8LL * i);
+    const float4 q = *reinterpret_cast<const float4*>(x + 8LL * i + 4);
+    const V8 v{{p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w}};
+    store8(y + 8LL * i, v);
+  }
+}
+// db[co] += sum_v g[v][co] with 8 channels per lane: Co / 8 = C8 divides 32,
+// so lane l always holds channel group l % C8; lanes of one group are summed
+// by xor shuffles at multiples of C8, warps in shared memory, and each block
+// adds one value per channel.
+constexpr int kBiasMaxC = 256;
+__global__ void __launch_bounds__(256)
+bias_grad_vec_kernel(const bf16* __restrict__ g, float* __restrict__ db, long long vtot, int Co) {
+  __shared__ float sh[8][kBiasMaxC];
+  const int C8 = Co / 8, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane % C8, vpw = 32 / C8;
+  V8 acc;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc.v[c] = 0.0f;
+  for (long long v = ((long long)blockIdx.x * 8 + warp) * vpw + lane / C8; v < vtot; v += (long long)gridDim.x * 8 * vpw) {
+    const V8 a = load8(g + v * Co + 8 * grp);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc.v[c] += a.v[c];
+  }
+  for (int off = C8; off < 32; off <<= 1)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc.v[c] += __shfl_xor_sync(0xffffffffu, acc.v[c], off);
+  if (lane < C8)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sh[warp][8 * grp + c] = acc.v[c];
+  __syncthreads();
+  for (int ch = threadIdx.x; ch < Co; ch += blockDim.x) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += sh[w][ch];
+    atomicAdd(db + ch, t);
+  }
+}
+
 // The vectorised kernels apply: channel counts, strides and offsets multiples
 // of 8, buffers 16-byte aligned, and fewer than 2^31 thread items.
 static bool vec8_ok(const void* a, const void* b, long long items, std::initializer_list<int> mult8) {
@@ -726,8 +787,15 @@ extern "C" lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, f
   else
     conv3d_wgrad_tile_kernel<16><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
   if (db) {
-    dim3 gb((Co + 31) / 32, (unsigned)std::min<long long>(1024, (vtot + 7) / 8));
-    bias_grad_kernel<<<gb, 256, 0, st>>>(reinterpret_cast<const bf16*>(g), db, vtot, Co);
+    const int c8 = Co / 8;
+    if (Co % 8 == 0 && Co <= kBiasMaxC && 32 % c8 == 0 && (reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
+      const long long per_block = 8LL * (32 / c8);   // voxels a block reads per sweep
+      const unsigned nb = (unsigned)std::min<long long>(148LL * 8, (vtot + per_block - 1) / per_block);
+      bias_grad_vec_kernel<<<nb, 256, 0, st>>>(reinterpret_cast<const bf16*>(g), db, vtot, Co);
+    } else {
+      dim3 gb((Co + 31) / 32, (unsigned)std::min<long long>(1024, (vtot + 7) / 8));
+      bias_grad_kernel<<<gb, 256, 0, st>>>(reinterpret_cast<const bf16*>(g), db, vtot, Co);
+    }
   }
   return launched("conv3d_wgrad");
 }
@@ -743,7 +811,10 @@ extern "C" lt_status lt_nn_conv3d_flip(const uint16_t* w, uint16_t* wt, int32_t 
 extern "C" lt_status lt_nn_f32_to_bf16(const float* x, uint16_t* y, int64_t n, void* stream) {
   clear_error();
   if (!x || !y || n < 0) return set_error(LT_EINVAL, "f32_to_bf16: bad arguments");
-  if (n) f2b_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(x, reinterpret_cast<bf16*>(y), n);
+  if (n && vec8_ok(x, y, n / 8, {(int)(n % 8)}))
+    f2b_vec_kernel<<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(x, reinterpret_cast<bf16*>(y), (unsigned)(n / 8));
+  else if (n)
+    f2b_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(x, reinterpret_cast<bf16*>(y), n);
   return launched("f32_to_bf16");
 }
 
@@ -757,7 +828,12 @@ extern "C" lt_status lt_nn_bf16_to_f32(const uint16_t* x, float* y, int64_t n, v
 extern "C" lt_status lt_nn_relu_backward(const uint16_t* y, uint16_t* g, int64_t n, void* stream) {
   clear_error();
   if (!y || !g || n < 0) return set_error(LT_EINVAL, "relu_backward: bad arguments");
-  if (n) relu_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(y), reinterpret_cast<bf16*>(g), n);
+  if (n && vec8_ok(y, g, n / 8, {(int)(n % 8)}))
+    relu_bwd_vec_kernel<<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(y), reinterpret_cast<bf16*>(g), (unsigned)(n / 8));
+  else if (n)
+    relu_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(y),
+                                                                  reinterpret_cast<bf16*>(g), n);
   return launched("relu_backward");
 }
 
@@ -856,7 +932,11 @@ extern "C" lt_status lt_nn_adam(float* p, uint16_t* pb, const float* g, float* m
 extern "C" lt_status lt_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, int64_t n, void* stream) {
   clear_error();
   if (!a || !b || !out || n < 0) return set_error(LT_EINVAL, "add: bad arguments");
-  if (n)
+  if (n && vec8_ok(a, b, n / 8, {(int)(n % 8)}) && (reinterpret_cast<uintptr_t>(out) & 15u) == 0)
+    add_vec_kernel<<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const bf16*>(a), reinterpret_cast<const bf16*>(b), reinterpret_cast<bf16*>(out),
+        (unsigned)(n / 8));
+  else if (n)
     add_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const bf16*>(a), reinterpret_cast<const bf16*>(b),
                                                              reinterpret_cast<bf16*>(out), n);
   return launched("add");
