@@ -9,6 +9,19 @@
 
 namespace lt {
 
+// Every device allocation of the library goes through here, so that a test
+// can make the n-th one fail (lt_test_fail_allocation_after).
+cudaError_t device_alloc(void** p, size_t bytes);
+
+// NVTX range around a host entry point (visible to profilers; a no-op
+// without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Kernel window limits (must match lt_kernels.cu).
 constexpr int kMaxForwardWindow = 8;
 constexpr int kMaxAdjointWindow = 16;

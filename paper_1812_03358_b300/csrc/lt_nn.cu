@@ -712,11 +712,18 @@ extern "C" lt_status lt_nn_device_status(void* stream) {
   return LT_OK;
 }
 
+extern "C" lt_status lt_nn_test_stall_tensor_core(int32_t on, void* stream) {
+  clear_error();
+  const cudaError_t e = set_tc_stall(on, (cudaStream_t)stream);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "tensor-core stall hook");
+}
+
 extern "C" lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
                                      float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
                                      int32_t Co, int32_t o_stride, int32_t o_off, int32_t relu, int32_t path,
                                      void* stream) {
   clear_error();
+  NvtxRange range("lt_nn_conv3d");
   if (!in || !w || (!out_bf && !out_f) || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 ||
       Ci % 16 || Co % 16 || o_off < 0 || o_stride < o_off + Co || path < LT_CONV_AUTO || path > LT_CONV_TCGEN05_ZWALK)
     return set_error(LT_EINVAL, "conv3d: bad arguments (channels must be multiples of 16)");

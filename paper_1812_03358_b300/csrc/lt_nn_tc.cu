@@ -71,6 +71,10 @@ __host__ __device__ constexpr int tc_smem_bytes() {
 }
 
 __device__ int g_tc_status;   // LT_ETIMEOUT after a bounded wait gave up
+// Test hook (lt_nn_test_stall_tensor_core): no MMA is issued, so every wait
+// runs out, after g_tc_wait_limit polls.
+__device__ int g_tc_stall = 0;
+__device__ long long g_tc_wait_limit = kWaitLimit;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -120,7 +124,8 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait for phase `parity` of the mbarrier.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
+  const long long limit = g_tc_wait_limit;
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_test(bar, parity)) return true;
     __nanosleep(64);
   }
@@ -191,6 +196,7 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
   const uint32_t tbase = *tslot;
 
   const int chunks = Ci / 16;
+  const bool stall = g_tc_stall != 0;
   bool ok = true;
   for (int c = 0; c < chunks && ok; ++c) {
     if (c > 0) {   // the tensor core has finished reading the previous chunk's tiles
@@ -217,7 +223,7 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
     cp_async_wait_all();
     fence_async_smem();   // make these writes visible to the tensor core (async proxy)
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !stall) {
       tc_fence_after();
       // Descriptors differ only in the start-address field (bits 0-13, in
       // 16-byte units; every address here is below 256 KB), so each MMA's is
@@ -392,7 +398,8 @@ conv3d_tc_zwalk_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, 
     }
     mma_commit(bar);
   };
-  if (tid == 0) issue(z0);
+  const bool stall = g_tc_stall != 0;
+  if (tid == 0 && !stall) issue(z0);
 
   bool ok = true;
   for (int s = 0; s < nsl; ++s) {
@@ -440,7 +447,7 @@ conv3d_tc_zwalk_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, 
       fence_async_smem();   // plane z + 2 visible to the tensor core
       tc_fence_before();    // this slice's tcgen05.ld are complete before the accumulators are rewritten
       __syncthreads();
-      if (tid == 0) {
+      if (tid == 0 && !stall) {
         tc_fence_after();
         issue(z + 1);
       }
@@ -558,6 +565,15 @@ cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float*
   bf16* o_ = reinterpret_cast<bf16*>(out_bf);
   if (tm == 128) return launch_tm<128>(nb, i_, w_, b, o_, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
   return launch_tm<64>(nb, i_, w_, b, o_, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
+}
+
+cudaError_t set_tc_stall(int on, cudaStream_t st) {
+  const int v = on ? 1 : 0;
+  const long long limit = on ? (1LL << 12) : kWaitLimit;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_stall, &v, sizeof(v));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_wait_limit, &limit, sizeof(limit));
+  return e;
 }
 
 cudaError_t take_tc_status(int* status, cudaStream_t st) {

@@ -21,6 +21,10 @@ cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float*
                              int batch, int D, int H, int W, int Ci, int Co, int o_stride, int o_off, int relu,
                              int variant, cudaStream_t st);
 
+// Test hook: with on != 0 the kernels issue no MMA (their waits run out after
+// 4096 polls); on == 0 restores normal operation.  Synchronises the stream.
+cudaError_t set_tc_stall(int on, cudaStream_t st);
+
 // Reads and clears the device status word of the tcgen05 kernels (0, or
 // LT_ETIMEOUT after a bounded wait gave up); synchronises the stream.
 cudaError_t take_tc_status(int* status, cudaStream_t st);

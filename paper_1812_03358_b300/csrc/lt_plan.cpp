@@ -5,7 +5,10 @@
 #include "lt_internal.h"
 #include "lt_host.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <atomic>
 #define _USE_MATH_DEFINES
 #include <cmath>
 #include <cstdarg>
@@ -25,6 +28,27 @@ thread_local std::string g_last_error;
 }  // namespace
 
 namespace lt {
+
+namespace {
+std::atomic<int> g_fail_alloc_in{0};   // > 0: the allocation that brings it to 0 fails
+}  // namespace
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+  int n = g_fail_alloc_in.load();
+  while (n > 0) {
+    if (g_fail_alloc_in.compare_exchange_weak(n, n - 1)) {
+      if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 lt_status set_error(lt_status s, const char* fmt, ...) {
   char buf[512];
@@ -205,7 +229,7 @@ static lt_status upload(const std::vector<T>& h, T** d, const char* what) {
     *d = nullptr;
     return LT_OK;
   }
-  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+  cudaError_t e = device_alloc((void**)d, h.size() * sizeof(T));
   if (e != cudaSuccess) {
     *d = nullptr;
     return set_error(LT_ENOMEM, "cudaMalloc(%s, %zu bytes): %s", what, h.size() * sizeof(T),
@@ -540,7 +564,7 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   if ((s = upload(cand_all_t, &c.d_cand_all_t, "candidate rows")) != LT_OK) return s;
   {
     const size_t zb = (size_t)frames * nmu * kStage2Window * kStage2Window * sizeof(float);
-    cudaError_t ez = cudaMalloc((void**)&c.d_zbuf, zb);
+    cudaError_t ez = device_alloc((void**)&c.d_zbuf, zb);
     if (ez != cudaSuccess) {
       c.d_zbuf = nullptr;
       return set_error(LT_ENOMEM, "cudaMalloc(lenslet sub-images, %zu bytes): %s", zb, cudaGetErrorString(ez));
@@ -548,7 +572,7 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   }
   c.Na = (int64_t)d.arr_ns * d.arr_nt;
   const size_t fa_bytes = (size_t)frames * c.K * c.Na * sizeof(float);
-  cudaError_t e = cudaMalloc((void**)&c.d_fa, fa_bytes);
+  cudaError_t e = device_alloc((void**)&c.d_fa, fa_bytes);
   if (e != cudaSuccess) {
     c.d_fa = nullptr;
     return set_error(LT_ENOMEM, "cudaMalloc(array plane, %zu bytes): %s", fa_bytes, cudaGetErrorString(e));
@@ -624,16 +648,16 @@ static lt_status plan_rotation(const lt_volume_desc& v, CameraPlan& c, int frame
     return set_error(LT_EINVAL, "camera %d: the rotated volume reaches the main lens", idx);
   const size_t brz = (size_t)frames * r.nzr * v.ny * r.nxp * sizeof(float);
   const size_t bxr = (size_t)frames * c.nvox_c * sizeof(float);
-  if (cudaMalloc((void**)&c.d_rz, brz) != cudaSuccess || cudaMalloc((void**)&c.d_xr, bxr) != cudaSuccess)
+  if (device_alloc((void**)&c.d_rz, brz) != cudaSuccess || device_alloc((void**)&c.d_xr, bxr) != cudaSuccess)
     return set_error(LT_ENOMEM, "camera %d: rotated-view scratch (%zu + %zu bytes)", idx, brz, bxr);
   if (r.wz > 16 || r.wx > 64)
     return set_error(LT_EUNSUPPORTED, "camera %d: voxel aspect ratio too large for the shear passes "
                      "(windows %d, %d)", idx, r.wz, r.wx);
   r.nwz = r.wz <= 8 ? 8 : 16;
-  if (cudaMalloc((void**)&r.tz, (size_t)r.nxp * r.nwz * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&r.jz, (size_t)r.nxp * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc((void**)&r.tx, (size_t)r.nzr * r.wx * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&r.jx, (size_t)r.nzr * sizeof(int32_t)) != cudaSuccess)
+  if (device_alloc((void**)&r.tz, (size_t)r.nxp * r.nwz * sizeof(float)) != cudaSuccess ||
+      device_alloc((void**)&r.jz, (size_t)r.nxp * sizeof(int32_t)) != cudaSuccess ||
+      device_alloc((void**)&r.tx, (size_t)r.nzr * r.wx * sizeof(float)) != cudaSuccess ||
+      device_alloc((void**)&r.jx, (size_t)r.nzr * sizeof(int32_t)) != cudaSuccess)
     return set_error(LT_ENOMEM, "camera %d: shear tables", idx);
   cudaError_t e = launch_shear_tables(r, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(0);
@@ -740,8 +764,8 @@ static lt_status plan_rotation_general(const lt_volume_desc& v, CameraPlan& c, i
       ps.nw = (int)std::floor(2.0 + std::fabs(s1) * du / dt + std::fabs(s2) * dv / dt) + 4;
       if (ps.nw > 64) return set_error(LT_EUNSUPPORTED, "camera %d: shear window %d too wide", idx, ps.nw);
       const size_t ncol = (size_t)ps.nu * ps.nv;
-      if (cudaMalloc((void**)&c.d_gtab[k], ncol * ps.nw * sizeof(float)) != cudaSuccess ||
-          cudaMalloc((void**)&c.d_gjo[k], ncol * sizeof(int32_t)) != cudaSuccess)
+      if (device_alloc((void**)&c.d_gtab[k], ncol * ps.nw * sizeof(float)) != cudaSuccess ||
+          device_alloc((void**)&c.d_gjo[k], ncol * sizeof(int32_t)) != cudaSuccess)
         return set_error(LT_ENOMEM, "camera %d: shear tables", idx);
       ps.tab = c.d_gtab[k];
       ps.jo = c.d_gjo[k];
@@ -754,7 +778,7 @@ static lt_status plan_rotation_general(const lt_volume_desc& v, CameraPlan& c, i
     }
   }
   for (int k = 0; k < 3; ++k)
-    if (cudaMalloc((void**)&c.d_gb[k], bytes[k]) != cudaSuccess)
+    if (device_alloc((void**)&c.d_gb[k], bytes[k]) != cudaSuccess)
       return set_error(LT_ENOMEM, "camera %d: rotated-view scratch", idx);
   c.vol_c.nx = dims[0];
   c.vol_c.ny = dims[1];
@@ -765,7 +789,7 @@ static lt_status plan_rotation_general(const lt_volume_desc& v, CameraPlan& c, i
   c.nvox_c = (int64_t)dims[0] * dims[1] * dims[2];
   if (d.d_obj - 0.5 * dims[2] * srr[2] <= 0.0)
     return set_error(LT_EINVAL, "camera %d: the rotated volume reaches the main lens", idx);
-  if (cudaMalloc((void**)&c.d_xr, (size_t)frames * c.nvox_c * sizeof(float)) != cudaSuccess)
+  if (device_alloc((void**)&c.d_xr, (size_t)frames * c.nvox_c * sizeof(float)) != cudaSuccess)
     return set_error(LT_ENOMEM, "camera %d: rotated-view scratch", idx);
   cudaError_t e = cudaStreamSynchronize(0);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "shear tables");
@@ -848,7 +872,7 @@ extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_d
     std::stable_sort(all.begin(), all.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
     p->n_items = (int)all.size();
     s = upload(all, &p->d_items, "forward work items");
-    if (s == LT_OK && cudaMalloc((void**)&p->d_counter, sizeof(int)) != cudaSuccess)
+    if (s == LT_OK && device_alloc((void**)&p->d_counter, sizeof(int)) != cudaSuccess)
       s = set_error(LT_ENOMEM, "cudaMalloc(work counter)");
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
     if (s != LT_OK) {
@@ -1240,15 +1264,19 @@ static lt_status check_plenoptic(const lt_plan* p, int cam) {
   return LT_OK;
 }
 
+extern "C" void lt_test_fail_allocation_after(int32_t n) { g_fail_alloc_in.store(n > 0 ? n : 0); }
+
 extern "C" lt_status lt_forward(lt_plan* plan, const float* x, float* y, void* stream) {
   clear_error();
   if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
+  NvtxRange range("lt_forward");
   return plan_forward(plan, x, y, (cudaStream_t)stream);
 }
 
 extern "C" lt_status lt_adjoint(lt_plan* plan, const float* y, float* x, void* stream) {
   clear_error();
   if (!plan || !x || !y) return set_error(LT_EINVAL, "NULL argument");
+  NvtxRange range("lt_adjoint");
   return plan_adjoint(plan, y, x, (cudaStream_t)stream);
 }
 
@@ -1342,8 +1370,8 @@ extern "C" lt_status lt_plan_autotune(lt_plan* plan, void* stream, double* times
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nx = (size_t)plan->frames * plan->nvox, ny = (size_t)plan->frames * plan->m_total;
   float *x = nullptr, *y = nullptr;
-  if (cudaMalloc((void**)&x, nx * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&y, ny * sizeof(float)) != cudaSuccess) {
+  if (device_alloc((void**)&x, nx * sizeof(float)) != cudaSuccess ||
+      device_alloc((void**)&y, ny * sizeof(float)) != cudaSuccess) {
     cudaFree(x);
     return set_error(LT_ENOMEM, "autotune buffers");
   }

@@ -283,7 +283,7 @@ static void recon_free(lt_recon* R) {
 
 template <typename T>
 static lt_status dalloc(T** p, size_t n, const char* what) {
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  cudaError_t e = device_alloc((void**)p, n * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
     return set_error(LT_ENOMEM, "cudaMalloc(%s, %zu bytes): %s", what, n * sizeof(T), cudaGetErrorString(e));
@@ -466,6 +466,7 @@ extern "C" lt_status lt_recon_iterate(lt_recon* R, int32_t n_iter, void* stream)
     if (s != LT_OK) return s;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  NvtxRange range("lt_recon_iterate");
   for (int i = 0; i < n_iter; ++i) {
     cudaError_t e = cudaGraphLaunch(R->exec[2 * (size_t)(R->iters % R->n_sub) + R->zsel], st);
     if (e != cudaSuccess) return cuda_error(e, "graph launch");

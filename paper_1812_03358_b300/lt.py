@@ -93,6 +93,7 @@ _SIGS = {
     "lt_autotune_variants": (c_int32, []),
     "lt_plan_autotune": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
     "lt_plan_set_forward_variant": (c_int32, [c_void_p, c_int32]),
+    "lt_test_fail_allocation_after": (None, [c_int32]),
     "lt_last_error": (c_char_p, []),
 }
 
@@ -234,6 +235,12 @@ def lt_plan_autotune(plan, stream: int = 0):
     chosen = c_int32()
     _check(lib().lt_plan_autotune(plan, stream, times, byref(chosen)))
     return chosen.value, list(times)
+
+
+def lt_test_fail_allocation_after(n: int) -> None:
+    """Fault injection for tests: the n-th device allocation from now on fails
+    (LT_ENOMEM); n <= 0 turns it off."""
+    lib().lt_test_fail_allocation_after(int(n))
 
 
 def lt_plan_set_forward_variant(plan, variant: int) -> None:

@@ -28,6 +28,7 @@ _SIGS = {
     "lt_nn_conv3d_ex": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
                         c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
     "lt_nn_device_status": [c_void_p],
+    "lt_nn_test_stall_tensor_core": [c_int32, c_void_p],
     "lt_nn_conv3d_wgrad": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
                            c_void_p],
     "lt_nn_conv3d_flip": [c_void_p, c_void_p, c_int32, c_int32, c_void_p],
