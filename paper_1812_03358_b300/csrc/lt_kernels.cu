@@ -344,10 +344,8 @@ beam_forward_batched(const __grid_constant__ BeamBatch B, const int4* __restrict
 // thread gathers its voxel.
 // ---------------------------------------------------------------------------
 constexpr int AT_S = 32;
-constexpr int AT_T = 8;                    // voxel rows per CTA (one warp each); a power of two
-constexpr int AT_T_LOG2 = AT_T == 16 ? 4 : 3;
-constexpr int AT_THREADS = 32 * AT_T;
-static_assert(AT_T == (1 << AT_T_LOG2), "AT_T");
+constexpr int AT_T = 8;
+constexpr int AT_THREADS = 256;
 constexpr int AT_UCOLS = 256;   // pixel columns of the t-contracted rows kept in shared memory
 constexpr int AT_SN = 2;        // slices per CTA
 
@@ -433,9 +431,9 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
           sw[q][lane] = w;
           flag_s |= (w != 0.0f);
         }
-        // t windows: thread t -> voxel row t % AT_T, entry t / AT_T
+        // t windows: thread t -> voxel row t & 7, entry t >> 3
         for (int tt = threadIdx.x; tt < AT_T * wit; tt += AT_THREADS) {
-          const int r = tt & (AT_T - 1), q = tt >> AT_T_LOG2;
+          const int r = tt & (AT_T - 1), q = tt >> 3;
           const int jy = jy0 + r;
           const int i = window_start(p->t, jy) + q;
           float w = 0.0f;
