@@ -737,10 +737,15 @@ extern "C" lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, cons
                                            variant, (cudaStream_t)stream);
     return e == cudaSuccess ? LT_OK : cuda_error(e, "conv3d (tcgen05)");
   }
-  const int nb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
   const int tx = (W + CT_X - 1) / CT_X, ty = (H + CT_Y - 1) / CT_Y, tz = (D + CT_Z - 1) / CT_Z;
   const long long tiles = (long long)tx * ty * tz;
   if (tiles > 0x7fffffffLL) return set_error(LT_EINVAL, "conv3d: volume too large");
+  constexpr long long kNbMinCtasPerSm = 1;
+  // the widest channel block that still gives kNbMinCtasPerSm CTAs per SM: a
+  // wider block stages its halo once for more output channels, a narrower
+  // one keeps small volumes (32^3, 16^3) from leaving SMs idle
+  int nb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
+  while (nb > 16 && tiles * (Co / nb) * batch < 148LL * kNbMinCtasPerSm) nb /= 2;
   dim3 grid((unsigned)tiles, Co / nb, batch);
   cudaStream_t st = (cudaStream_t)stream;
   const bf16* i_ = reinterpret_cast<const bf16*>(in);
