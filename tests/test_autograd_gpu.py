@@ -100,5 +100,5 @@ def test_tv_regularised_nonnegative_fit_decreases_objective(setup):
         opt.step()
         with torch.no_grad():
             x.clamp_(min=0.0)
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert losses[-1] < 0.2 * losses[0]
