@@ -52,6 +52,13 @@ __device__ __forceinline__ long long perm_index(const RotParam& r, int jz, int i
   return ((long long)iz * r.ny + iy) * r.nx + ix;
 }
 
+// perm_index is affine in jz: voxel (jz, iy, c) sits at off0 + jz * sj.
+template <int NQ>
+__device__ __forceinline__ void perm_line(const RotParam& r, int iy, int c, long long& off0, long long& sj) {
+  off0 = perm_index<NQ>(r, 0, iy, c);
+  sj = perm_index<NQ>(r, 1, iy, c) - off0;
+}
+
 // Entries of a shear pass depend on the output/source offset and the
 // column's shift only, so each column's band is tabulated once (plan time):
 // window offset J = floor(sh - 1 - beta/2) - 1 and, for q = 0..nw-1, the entry
@@ -76,8 +83,11 @@ __global__ void shear_tables_kernel(RotParam r) {
 constexpr int kShearZChunk = 16;   // outputs along the sheared axis per thread
 
 // rz[f][izr][iy][c] = sum_q tz[c][q] xp[f][izr - pz + jz[c] + q][iy][c], xp the
-// quarter-turned volume.  Thread = (iy, c) column; the NW source values slide
-// through registers along izr, one load per output.
+// quarter-turned volume.  Thread = (iy, c) column and kShearZChunk outputs
+// along izr; the chunk's whole source window (kShearZChunk + NW - 1 values)
+// is loaded before any output is formed, so that every load of the chunk is
+// in flight at once (one dependent load per output left the pass
+// latency-bound at a fifth of the HBM rate).
 template <int NW, int NQ>
 __global__ void __launch_bounds__(256) shear_z_forward(const float* __restrict__ x, float* __restrict__ rz,
                                                        RotParam r, int frames) {
@@ -92,31 +102,86 @@ __global__ void __launch_bounds__(256) shear_z_forward(const float* __restrict__
 #pragma unroll
   for (int q = 0; q < NW; ++q) w[q] = __ldg(r.tz + (long long)c * NW + q);
   const int J = __ldg(r.jz + c);
-  const int zend = min(z0 + kShearZChunk, r.nzr);
+  const int nout = min(kShearZChunk, r.nzr - z0);
+  long long off0, sj;
+  perm_line<NQ>(r, iy, c, off0, sj);
   for (int f = 0; f < frames; ++f) {
-    const float* xf = x + (long long)f * nvox;
     float* out = rz + (long long)f * per + (long long)iy * r.nxp + c;
     const int jb = z0 - r.pz + J;   // first source of output z0
-    float v[NW];
+    // source jb + q at ps + q * sj (formed only where it is in the volume)
+    const float* ps = x + (long long)f * nvox + off0 + (long long)jb * sj;
+    float v[kShearZChunk + NW - 1];
+    if (jb >= 0 && jb + kShearZChunk + NW - 1 <= r.nzp) {   // window inside the volume
 #pragma unroll
-    for (int q = 0; q < NW; ++q) {
-      const int j = jb + q;
-      v[q] = (j >= 0 && j < r.nzp) ? __ldg(xf + perm_index<NQ>(r, j, iy, c)) : 0.0f;
+      for (int q = 0; q < kShearZChunk + NW - 1; ++q) v[q] = __ldg(ps + q * sj);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kShearZChunk + NW - 1; ++q)
+        v[q] = (unsigned)(jb + q) < (unsigned)r.nzp ? __ldg(ps + q * sj) : 0.0f;
     }
-    for (int izr = z0; izr < zend; ++izr) {
-      float acc = 0.0f;
 #pragma unroll
-      for (int q = 0; q < NW; ++q) acc = fmaf(w[q], v[q], acc);
-      out[(long long)izr * zstride] = acc;
+    for (int t = 0; t < kShearZChunk; ++t) {
+      if (t < nout) {
+        float acc = 0.0f;
 #pragma unroll
-      for (int q = 0; q < NW - 1; ++q) v[q] = v[q + 1];
-      const int j = izr + 1 - r.pz + J + NW - 1;
-      v[NW - 1] = (j >= 0 && j < r.nzp) ? __ldg(xf + perm_index<NQ>(r, j, iy, c)) : 0.0f;
+        for (int q = 0; q < NW; ++q) acc = fmaf(w[q], v[t + q], acc);
+        out[(long long)(z0 + t) * zstride] = acc;
+      }
     }
   }
 }
 
-// xr[f][izr][iy][ixr] = sum_q tx[izr][q] rz[f][izr][iy][ixr - px + jx[izr] + q]
+constexpr int kShearXWarps = 8;   // rows (one per warp) per CTA of the staged x passes
+constexpr int kShearXSmemMax = 48 * 1024;
+
+// xr[f][izr][iy][ixr] = sum_q tx[izr][q] rz[f][izr][iy][ixr - px + jx[izr] + q].
+// Warp = one row (izr, iy): the row's nxp inputs are staged in the warp's
+// shared-memory slice between WX zeros, so that a window overlapping the row
+// reads inputs or zeros with no bounds test per tap; lane = outputs lane +
+// 32 k.  The taps run in ascending q with zero weights past wx, which gives
+// the generic loop's values bit for bit (a tap outside the row adds w * 0).
+template <int WX>
+__global__ void __launch_bounds__(32 * kShearXWarps) shear_x_forward_rows(const float* __restrict__ rz,
+                                                                          float* __restrict__ xr, RotParam r,
+                                                                          int frames) {
+  extern __shared__ float smem_rows[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int iy = blockIdx.x * kShearXWarps + wid;
+  const int izr = blockIdx.y;
+  if (iy >= r.ny) return;   // warp-uniform; no block barrier below
+  const int L = r.nxp + 2 * WX;
+  float* Rw = smem_rows + wid * L;
+  if (lane < WX) {
+    Rw[lane] = 0.0f;
+    Rw[WX + r.nxp + lane] = 0.0f;
+  }
+  const long long per_in = (long long)r.nzr * r.ny * r.nxp;
+  const long long per = (long long)r.nzr * r.ny * r.nxr;
+  const float* tab = r.tx + (long long)izr * r.wx;
+  float w[WX];
+#pragma unroll
+  for (int q = 0; q < WX; ++q) w[q] = q < r.wx ? __ldg(tab + q) : 0.0f;
+  const int off = __ldg(r.jx + izr) - r.px;   // output ixr's first source is ixr + off
+  for (int f = 0; f < frames; ++f) {
+    const float* row = rz + (long long)f * per_in + ((long long)izr * r.ny + iy) * r.nxp;
+    __syncwarp();   // the previous frame's reads are done
+    for (int j = lane; j < r.nxp; j += 32) Rw[WX + j] = __ldg(row + j);
+    __syncwarp();
+    float* o = xr + (long long)f * per + ((long long)izr * r.ny + iy) * r.nxr;
+    for (int ixr = lane; ixr < r.nxr; ixr += 32) {
+      const int jb = ixr + off;
+      float acc = 0.0f;
+      if (jb > -WX && jb < r.nxp) {   // else every tap lies outside the row
+        const float* src = Rw + WX + jb;
+#pragma unroll
+        for (int q = 0; q < WX; ++q) acc = fmaf(w[q], src[q], acc);
+      }
+      o[ixr] = acc;
+    }
+  }
+}
+
+// Generic x pass (windows wider than 16): one output per thread.
 __global__ void __launch_bounds__(256) shear_x_forward(const float* __restrict__ rz, float* __restrict__ xr,
                                                        RotParam r, int frames) {
   const int ixr = blockIdx.x * 32 + threadIdx.x;
@@ -139,7 +204,51 @@ __global__ void __launch_bounds__(256) shear_x_forward(const float* __restrict__
 }
 
 // grz[f][izr][iy][j] = sum_ixr E^x(ixr, j; izr) g[f][izr][iy][ixr]: outputs
-// i = j + px - jx[izr] - q, visited in ascending i.
+// i = j + px - jx[izr] - q, visited in ascending i.  Warp = one row, its nxr
+// values of g staged between WX zeros (as shear_x_forward_rows); lane =
+// sources lane + 32 k.
+template <int WX>
+__global__ void __launch_bounds__(32 * kShearXWarps) shear_x_adjoint_rows(const float* __restrict__ g,
+                                                                          float* __restrict__ grz, RotParam r,
+                                                                          int frames) {
+  extern __shared__ float smem_rows[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int iy = blockIdx.x * kShearXWarps + wid;
+  const int izr = blockIdx.y;
+  if (iy >= r.ny) return;   // warp-uniform; no block barrier below
+  const int L = r.nxr + 2 * WX;
+  float* Gw = smem_rows + wid * L;
+  if (lane < WX) {
+    Gw[lane] = 0.0f;
+    Gw[WX + r.nxr + lane] = 0.0f;
+  }
+  const long long per_in = (long long)r.nzr * r.ny * r.nxr;
+  const long long per = (long long)r.nzr * r.ny * r.nxp;
+  const float* tab = r.tx + (long long)izr * r.wx;
+  float w[WX];
+#pragma unroll
+  for (int q = 0; q < WX; ++q) w[q] = q < r.wx ? __ldg(tab + q) : 0.0f;
+  const int off = r.px - __ldg(r.jx + izr);   // source j's last tap is output j + off
+  for (int f = 0; f < frames; ++f) {
+    const float* row = g + (long long)f * per_in + ((long long)izr * r.ny + iy) * r.nxr;
+    __syncwarp();
+    for (int i = lane; i < r.nxr; i += 32) Gw[WX + i] = __ldg(row + i);
+    __syncwarp();
+    float* o = grz + (long long)f * per + ((long long)izr * r.ny + iy) * r.nxp;
+    for (int j = lane; j < r.nxp; j += 32) {
+      const int ib = j + off;
+      float acc = 0.0f;
+      if (ib >= 0 && ib - (WX - 1) < r.nxr) {   // else every tap lies outside the row
+        const float* src = Gw + WX + ib;
+#pragma unroll
+        for (int q = WX - 1; q >= 0; --q) acc = fmaf(w[q], src[-q], acc);
+      }
+      o[j] = acc;
+    }
+  }
+}
+
+// Generic transposed x pass (windows wider than 16): one source per thread.
 __global__ void __launch_bounds__(256) shear_x_adjoint(const float* __restrict__ g, float* __restrict__ grz,
                                                        RotParam r, int frames) {
   const int j = blockIdx.x * 32 + threadIdx.x;
@@ -162,8 +271,9 @@ __global__ void __launch_bounds__(256) shear_x_adjoint(const float* __restrict__
 }
 
 // x[f][perm(jz, iy, c)] (= or +=) sum_i E^z(i, jz; c) grz[f][i][iy][c]:
-// outputs i = jz + pz - jz_tab[c] - q in ascending order; the NW values of
-// grz slide through registers along jz.
+// outputs i = jz + pz - jz_tab[c] - q in ascending order.  Thread = (iy, c)
+// column and kShearZChunk sources along jz, the chunk's whole window of grz
+// loaded first (as in shear_z_forward).
 template <int NW, int NQ>
 __global__ void __launch_bounds__(256) shear_z_adjoint(const float* __restrict__ grz, float* __restrict__ x,
                                                        RotParam r, int frames, int accumulate) {
@@ -178,28 +288,39 @@ __global__ void __launch_bounds__(256) shear_z_adjoint(const float* __restrict__
 #pragma unroll
   for (int k = 0; k < NW; ++k) w[k] = __ldg(r.tz + (long long)c * NW + (NW - 1 - k));
   const int J = __ldg(r.jz + c);
-  const int zend = min(z0 + kShearZChunk, r.nzp);
+  const int nout = min(kShearZChunk, r.nzp - z0);
+  long long off0, sj;
+  perm_line<NQ>(r, iy, c, off0, sj);
   for (int f = 0; f < frames; ++f) {
-    const float* gf = grz + (long long)f * per_in + (long long)iy * r.nxp + c;
-    float* xf = x + (long long)f * nvox;
     const int ib = z0 + r.pz - J - (NW - 1);   // first output row of source z0
-    float v[NW];
+    // row ib + k at gi + k * zstride (formed only where it is in the grid)
+    const float* gi = grz + (long long)f * per_in + (long long)iy * r.nxp + c + (long long)ib * zstride;
+    float* xo = x + (long long)f * nvox + off0 + (long long)z0 * sj;   // source z0 + t at xo + t * sj
+    float v[kShearZChunk + NW - 1];
+    if (ib >= 0 && ib + kShearZChunk + NW - 1 <= r.nzr) {   // window inside the grid
 #pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      const int i = ib + k;
-      v[k] = (i >= 0 && i < r.nzr) ? __ldg(gf + (long long)i * zstride) : 0.0f;
+      for (int k = 0; k < kShearZChunk + NW - 1; ++k) v[k] = __ldg(gi + k * zstride);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kShearZChunk + NW - 1; ++k)
+        v[k] = (unsigned)(ib + k) < (unsigned)r.nzr ? __ldg(gi + k * zstride) : 0.0f;
     }
-    for (int jz = z0; jz < zend; ++jz) {
+    float res[kShearZChunk];
+#pragma unroll
+    for (int t = 0; t < kShearZChunk; ++t) {
       float acc = 0.0f;
 #pragma unroll
-      for (int k = 0; k < NW; ++k) acc = fmaf(w[k], v[k], acc);
-      const long long o = perm_index<NQ>(r, jz, iy, c);
-      xf[o] = accumulate ? xf[o] + acc : acc;
-#pragma unroll
-      for (int k = 0; k < NW - 1; ++k) v[k] = v[k + 1];
-      const int i = jz + 1 + r.pz - J;
-      v[NW - 1] = (i >= 0 && i < r.nzr) ? __ldg(gf + (long long)i * zstride) : 0.0f;
+      for (int k = 0; k < NW; ++k) acc = fmaf(w[k], v[t + k], acc);
+      res[t] = acc;
     }
+    if (accumulate) {   // every old value read before any is written
+#pragma unroll
+      for (int t = 0; t < kShearZChunk; ++t)
+        if (t < nout) res[t] += xo[t * sj];
+    }
+#pragma unroll
+    for (int t = 0; t < kShearZChunk; ++t)
+      if (t < nout) xo[t * sj] = res[t];
   }
 }
 
@@ -416,14 +537,26 @@ cudaError_t launch_rotate_forward(const float* x, float* rz, float* xr, const Ro
   const dim3 blk(32, 8);
   const dim3 gz((r.nxp + 31) / 32, (r.ny + 7) / 8, (r.nzr + kShearZChunk - 1) / kShearZChunk);
   launch_z_forward(gz, blk, st, x, rz, r, frames);
-  shear_x_forward<<<dim3((r.nxr + 31) / 32, (r.ny + 7) / 8, r.nzr), blk, 0, st>>>(rz, xr, r, frames);
+  const int WX = r.wx <= 8 ? 8 : 16;
+  const size_t sm = (size_t)kShearXWarps * (r.nxp + 2 * WX) * sizeof(float);
+  const dim3 gx((r.ny + kShearXWarps - 1) / kShearXWarps, r.nzr);
+  if (r.wx <= 16 && sm <= (size_t)kShearXSmemMax) {
+    if (WX == 8) shear_x_forward_rows<8><<<gx, 32 * kShearXWarps, sm, st>>>(rz, xr, r, frames);
+    else shear_x_forward_rows<16><<<gx, 32 * kShearXWarps, sm, st>>>(rz, xr, r, frames);
+  } else shear_x_forward<<<dim3((r.nxr + 31) / 32, (r.ny + 7) / 8, r.nzr), blk, 0, st>>>(rz, xr, r, frames);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rotate_adjoint(const float* g_xr, float* rz, float* x, const RotParam& r, int frames,
                                   int accumulate, cudaStream_t st) {
   const dim3 blk(32, 8);
-  shear_x_adjoint<<<dim3((r.nxp + 31) / 32, (r.ny + 7) / 8, r.nzr), blk, 0, st>>>(g_xr, rz, r, frames);
+  const int WX = r.wx <= 8 ? 8 : 16;
+  const size_t sm = (size_t)kShearXWarps * (r.nxr + 2 * WX) * sizeof(float);
+  const dim3 gx((r.ny + kShearXWarps - 1) / kShearXWarps, r.nzr);
+  if (r.wx <= 16 && sm <= (size_t)kShearXSmemMax) {
+    if (WX == 8) shear_x_adjoint_rows<8><<<gx, 32 * kShearXWarps, sm, st>>>(g_xr, rz, r, frames);
+    else shear_x_adjoint_rows<16><<<gx, 32 * kShearXWarps, sm, st>>>(g_xr, rz, r, frames);
+  } else shear_x_adjoint<<<dim3((r.nxp + 31) / 32, (r.ny + 7) / 8, r.nzr), blk, 0, st>>>(g_xr, rz, r, frames);
   const dim3 gz((r.nxp + 31) / 32, (r.ny + 7) / 8, (r.nzp + kShearZChunk - 1) / kShearZChunk);
   launch_z_adjoint(gz, blk, st, rz, x, r, frames, accumulate);
   return cudaGetLastError();
