@@ -148,6 +148,39 @@ def rotate(X, sizes, theta):
     return R, sr
 
 
+def rotate_voxels(X, sizes, theta, idx):
+    """Values of rotate(X, sizes, theta) at the output voxels idx (rows
+    (izr, iy, ixr)), each formed from its own entries: the x shear's entries
+    of row izr times the z-sheared values of that row, each of those the z
+    shear's entries of its column times the quarter-turned volume.  The same
+    shear_entry terms as shear_z and shear_x, for spot checks of volumes too
+    large for `rotate`."""
+    n, tr = split_angle(theta)
+    Xp, sp = quarter_turn(np.asarray(X, dtype=np.float64), n, sizes)
+    Dg, a, b = shear_factors(tr)
+    dx, dy, dz = sp[0] / Dg[0], sp[1], sp[2] / Dg[2]
+    nz, ny, nx = Xp.shape
+    pz = int(math.ceil(abs(b) * nx * dx / 2 / dz)) + 1
+    nzo = nz + 2 * pz
+    px = int(math.ceil(abs(a) * nzo * dz / 2 / dx)) + 1
+    zs, zo = _centres(nz, dz), _centres(nzo, dz)
+    xs, xo = _centres(nx, dx), _centres(nx + 2 * px, dx)
+    out = np.zeros(len(idx))
+    for m, (iz, iy, ix) in enumerate(idx):
+        for j in range(nx):   # source column j of the z-sheared row iz
+            if not abs(xo[ix] - (xs[j] - a * zo[iz])) < dx + abs(a) * dz / 2 + 1e-12:
+                continue
+            ex = shear_entry(xo[ix], xs[j], dx, zo[iz], dz, a)
+            if ex == 0.0:
+                continue
+            zval = 0.0
+            for k in range(nz):
+                if abs(zo[iz] - (zs[k] - b * xs[j])) < dz + abs(b) * dx / 2 + 1e-12:
+                    zval += shear_entry(zo[iz], zs[k], dz, xs[j], dx, b) * Xp[k, iy, j]
+            out[m] += ex * zval
+    return out
+
+
 def rotation_matrix(shape, sizes, theta):
     """Explicit matrix of `rotate` (columns = rotated unit voxels), tiny grids."""
     N = int(np.prod(shape))

@@ -24,7 +24,8 @@ struct NvtxRange {
 
 // Kernel window limits (must match lt_kernels.cu).
 constexpr int kMaxForwardWindow = 8;
-constexpr int kMaxAdjointWindow = 16;
+constexpr int kFwdClasses[4] = {8, 4, 3, 2};   // the forward kernels' window classes (window_class)
+constexpr int kMaxAdjointWindow = 32;
 constexpr int kMaxLensletPixels = 16;
 
 struct Cell {
@@ -102,10 +103,15 @@ struct lt_plan {
   int device = 0;
   int sms = 148;
   std::vector<lt::CameraPlan> cams;
-  int4* d_items = nullptr;         // every camera's forward items, longest first
+  // every camera's forward items, grouped by the camera's forward window
+  // class (kFwdClasses order), longest first within a group: the batched
+  // forward makes one persistent launch per class present, so that a camera
+  // runs the same kernel instantiation as in a launch of its own
+  int4* d_items = nullptr;
   int n_items = 0;
+  int class_begin[4] = {0, 0, 0, 0};
+  int class_count[4] = {0, 0, 0, 0};
   int* d_counter = nullptr;        // persistent-launch work counter
-  int wclass = 2;                  // forward window class of the whole plan
   int fwd_variant = 2;             // forward kernel variant (autotuned; {2 slices, 2 groups} until then)
 };
 

@@ -22,7 +22,7 @@ namespace lt {
 namespace {
 
 constexpr int WMAX = 8;      // forward window cap: source cells per target pixel per axis
-constexpr int WIMAX = 16;    // adjoint window cap: target pixels per source cell per axis
+constexpr int WIMAX = 32;    // adjoint window cap: target pixels per source cell per axis
 constexpr int MAXC = 16;     // array pixels per lenslet per axis (stage two)
 
 // ---------------------------------------------------------------------------

@@ -865,11 +865,15 @@ extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_d
   p->m_total = off;
   {
     std::vector<int4> all;
-    for (auto& c : p->cams) {
-      all.insert(all.end(), c.h_items.begin(), c.h_items.end());
-      p->wclass = std::max(p->wclass, window_class(std::max(c.wmax_s, c.wmax_t)));
+    for (int g = 0; g < 4; ++g) {
+      const size_t start = all.size();
+      for (auto& c : p->cams)
+        if (window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g])
+          all.insert(all.end(), c.h_items.begin(), c.h_items.end());
+      std::stable_sort(all.begin() + start, all.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+      p->class_begin[g] = (int)start;
+      p->class_count[g] = (int)(all.size() - start);
     }
-    std::stable_sort(all.begin(), all.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
     p->n_items = (int)all.size();
     s = upload(all, &p->d_items, "forward work items");
     if (s == LT_OK && device_alloc((void**)&p->d_counter, sizeof(int)) != cudaSuccess)
@@ -1194,8 +1198,11 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, Su
     const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
     b.cam[i] = beam_cam(c, xc, plen ? c.d_fa : y + c.offset, nullptr, plen ? (long long)c.K * c.Na : p->m_total, sel);
   }
-  lt_status s = run_forward(p, b, p->d_items, p->n_items, p->wclass, st);
-  if (s != LT_OK) return s;
+  for (int g = 0; g < 4; ++g) {   // one persistent launch per window class present
+    if (p->class_count[g] == 0) continue;
+    lt_status s = run_forward(p, b, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g], st);
+    if (s != LT_OK) return s;
+  }
   for (int i = 0; i < nc; ++i) {
     CameraPlan& c = p->cams[i];
     if (c.desc.kind != LT_CAM_PLENOPTIC) continue;

@@ -265,14 +265,16 @@ def uniform_random(shape, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.nda
     return rng.uniform(lo, hi, size=shape).astype(np.float32)
 
 
-def plume_field_torch(vol: Volume, seed: int, n_plumes: int = 20, turbulence: float = 0.3, device="cuda"):
+def plume_field_torch(vol: Volume, seed: int, n_plumes: int = 20, turbulence: float = 0.3, device="cuda",
+                      drift_voxels: float = 0.0):
     """The plume distribution of ``plume_field`` evaluated on the GPU with
-    torch (for generating many training volumes); parameters drawn from the
-    same PCG64 recipe, turbulence from a seeded torch generator."""
+    torch (for generating many training volumes and full-size frames);
+    parameters drawn from the same PCG64 recipe, turbulence from a seeded
+    torch generator, ``drift_voxels`` as in ``plume_field``."""
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
     z = (torch.arange(vol.nz, device=device, dtype=torch.float32) + 0.5) / vol.nz
-    y = (torch.arange(vol.ny, device=device, dtype=torch.float32) + 0.5) / vol.ny
+    y = (torch.arange(vol.ny, device=device, dtype=torch.float32) + 0.5) / vol.ny - drift_voxels / vol.ny
     x = (torch.arange(vol.nx, device=device, dtype=torch.float32) + 0.5) / vol.nx
     Z, Y, X = torch.meshgrid(z, y, x, indexing="ij")
     out = torch.zeros(vol.shape, device=device, dtype=torch.float32)

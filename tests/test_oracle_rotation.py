@@ -2,8 +2,9 @@
 decomposition reproduces the rotation matrix, zero angle is the identity,
 quarter turns equal numpy's rot90, every shear conserves mass, the shear
 entries equal an independent closed form (average of the box-overlap hat over
-the sheared cell), and a smooth blob rotates into the analytically rotated
-blob up to resampling error."""
+the sheared cell), a smooth blob rotates into the analytically rotated
+blob up to resampling error, and the per-voxel spot check equals the whole
+rotation at every voxel."""
 import math
 
 import numpy as np
@@ -113,3 +114,15 @@ def test_rotated_blob_matches_analytic_rotation():
     wrong = f(T[0, 0] * Xr - T[0, 2] * Zr, Yr, -T[2, 0] * Xr + T[2, 2] * Zr)
     err_wrong = np.linalg.norm(Rv - wrong) / np.linalg.norm(wrong)
     assert err < 0.05 and err_wrong > 5 * err, (err, err_wrong)
+
+
+@pytest.mark.parametrize("theta", [0.3, -0.7, 0.785, 1.9, 3.0, -2.2])
+def test_rotate_voxels_equals_rotate_everywhere(theta):
+    rng = np.random.default_rng(7)
+    X = rng.random((5, 3, 6))
+    sizes = (1.0, 1.2, 0.8)
+    full, _ = R.rotate(X, sizes, theta)
+    idx = [(i, j, k) for i in range(full.shape[0]) for j in range(full.shape[1])
+           for k in range(full.shape[2])]
+    got = R.rotate_voxels(X, sizes, theta, idx)
+    assert np.abs(got - full.ravel()).max() <= 1e-13 * np.abs(full).max()
