@@ -508,33 +508,91 @@ struct SmallDiv {
 __device__ __forceinline__ SmallDiv small_div(uint32_t d) { return {d > 1u ? 0xFFFFFFFFu / d + 1u : 0u, d}; }
 __device__ __forceinline__ uint32_t div_of(SmallDiv f, uint32_t n) { return f.d > 1u ? __umulhi(n, f.m) : n; }
 
-constexpr int L2_THREADS = 128;
 constexpr int L2_W = kStage2Window;
+constexpr int S2_THREADS = 256;
+constexpr int S2_KB = 4;   // cells per pass of the lenslet adjoint
+static_assert(MAXC * MAXC <= S2_THREADS, "one block pixel per thread");
+static_assert(S2_KB * 64 <= S2_THREADS && 2 * L2_W <= 64, "one footprint task per thread");
+
+// Entries of one detector column or row of a (lenslet, cell): task < nds is
+// column dr.x + task, Bs[c][task] = entry (column, array column cc.x + c);
+// otherwise row dr.z + task - nds into Bt likewise.  Consecutive array cells
+// share their common edge value.
+__device__ __forceinline__ void lenslet_weight_task(const LensletParam* L, int4 dr, int2 cc, int2 rr, int task,
+                                                    float (*Bs)[L2_W + 1], float (*Bt)[L2_W + 1]) {
+  const int nds = dr.y - dr.x + 1;
+  const bool s_axis = task < nds;
+  const AxisParam& a = s_axis ? L->s : L->t;
+  const int q = s_axis ? task : task - nds;
+  const int i = s_axis ? dr.x + q : dr.z + q;
+  const int j0 = s_axis ? cc.x : rr.x;
+  const int n = s_axis ? cc.y - cc.x : rr.y - rr.x;
+  int jc;
+  float fr;
+  footprint_centre(a, i, jc, fr);
+  float Flo = edge_F(j0 - jc, fr, a);
+  for (int c = 0; c < n; ++c) {
+    const float Fhi = edge_F(j0 + c + 1 - jc, fr, a);
+    const float w = __fsub_rn(Fhi, Flo);
+    Flo = Fhi;
+    if (s_axis) Bs[c][q] = w; else Bt[c][q] = w;
+  }
+}
+
+// One cell of a pass of the lenslet adjoint (shared memory).
+struct S2Cell {
+  int4 dr;         // detector window (s0, s1, t0, t1), inclusive
+  int nds, ndt;
+  int dz, dx;      // offset of the window inside the lenslet's union window
+  float scale;
+  SmallDiv dd;     // division by nds
+  int sub;         // cell in the angular subset
+  int on;          // in the subset and with a non-empty window
+  int cnt;         // nr * nds contraction outputs, 0 when off
+};
+
+// Cell table of the pass starting at cell k0 (threads 0 .. S2_KB - 1).
+__device__ __forceinline__ void s2_cell_table(const StageTwo& s2, int mu, int nmu, int k0, int4 du, int nr,
+                                              S2Cell* cell) {
+  const int kk = threadIdx.x;
+  if (kk >= S2_KB) return;
+  S2Cell cl{};
+  const int k = k0 + kk;
+  if (k < s2.K) {
+    cl.dr = s2.det_range[(long long)k * nmu + mu];
+    cl.nds = cl.dr.y - cl.dr.x + 1;
+    cl.ndt = cl.dr.w - cl.dr.z + 1;
+    cl.sub = cell_on(s2.sub_n, s2.sub_s, k);
+    cl.on = cl.sub && cl.nds > 0 && cl.ndt > 0;
+    cl.dz = cl.dr.z - du.z;
+    cl.dx = cl.dr.x - du.x;
+    cl.scale = s2.lens[(long long)k * nmu + mu].scale;
+    cl.dd = small_div(cl.on ? cl.nds : 1);
+    cl.cnt = cl.on ? nr * cl.nds : 0;
+  }
+  cell[kk] = cl;
+}
+
+// The cell and local index of flat contraction task e (e < the pass's total).
+__device__ __forceinline__ int s2_task_cell(const S2Cell* cell, int& o) {
+  int kk = 0;
+#pragma unroll
+  for (int t = 0; t < S2_KB - 1; ++t)
+    if (kk == t && o >= cell[t].cnt) {
+      o -= cell[t].cnt;
+      kk = t + 1;
+    }
+  return kk;
+}
+
+constexpr int L2_THREADS = 128;
 
 // Bs[c][q] = entry (detector column dr.x + q, array column cc.x + c) and
 // Bt[r][b] likewise; one task per detector column / row.
 __device__ __forceinline__ void lenslet_weights(const LensletParam* L, int4 dr, int2 cc, int2 rr,
                                                 float (*Bs)[L2_W + 1], float (*Bt)[L2_W + 1]) {
   const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
-  const int nc = cc.y - cc.x, nr = rr.y - rr.x;
-  for (int task = threadIdx.x; task < nds + ndt; task += blockDim.x) {
-    const bool s_axis = task < nds;
-    const AxisParam& a = s_axis ? L->s : L->t;
-    const int q = s_axis ? task : task - nds;
-    const int i = s_axis ? dr.x + q : dr.z + q;
-    const int j0 = s_axis ? cc.x : rr.x;
-    const int n = s_axis ? nc : nr;
-    int jc;
-    float fr;
-    footprint_centre(a, i, jc, fr);
-    float Flo = edge_F(j0 - jc, fr, a);
-    for (int c = 0; c < n; ++c) {
-      const float Fhi = edge_F(j0 + c + 1 - jc, fr, a);
-      const float w = __fsub_rn(Fhi, Flo);
-      Flo = Fhi;
-      if (s_axis) Bs[c][q] = w; else Bt[c][q] = w;
-    }
-  }
+  for (int task = threadIdx.x; task < nds + ndt; task += blockDim.x) lenslet_weight_task(L, dr, cc, rr, task, Bs, Bt);
 }
 
 // Forward, pass 1: each lenslet's contribution sum_k Bt (x) Bs fa_k on the
@@ -636,90 +694,92 @@ stage2_gather(const float* __restrict__ zbuf, float* __restrict__ y, StageTwo s2
 
 // Adjoint: fa_k[jt][js] = M * scale * sum_b sum_q Bt[r][b] Bs[c][q] y[dr.z+b][dr.x+q]
 // for the lenslet's own block (a gather: every array pixel has one lenslet).
-__global__ void __launch_bounds__(L2_THREADS, 16)
+// The lenslet's union window of y is staged once; the cells go S2_KB at a
+// time through three phases (footprint entries; U = Bt^T Y for every cell;
+// each thread's block pixel for every cell), one block barrier per phase.
+__global__ void __launch_bounds__(S2_THREADS, 8)
 stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, StageTwo s2, long long y_fs,
                        long long fa_fs) {
-  __shared__ float Bs[MAXC][L2_W + 1];
-  __shared__ float Bt[MAXC][L2_W + 1];
+  __shared__ float Bs[S2_KB][MAXC][L2_W + 1];
+  __shared__ float Bt[S2_KB][MAXC][L2_W + 1];
   __shared__ float Y[L2_W][L2_W + 1];
-  __shared__ float U[MAXC][L2_W + 1];
+  __shared__ float U[S2_KB][MAXC][L2_W + 1];
+  __shared__ S2Cell cell[S2_KB];
   const int mu = blockIdx.x;
   const int frame = blockIdx.y;
   const int nmu = s2.mla_ns * s2.mla_nt;
   const int2 cc = s2.cols[mu], rr = s2.rows[mu];
   const int nc = cc.y - cc.x, nr = rr.y - rr.x;
   if (nc <= 0 || nr <= 0) return;   // uniform
+  const int4 du = s2.det_union[mu];
+  const int nsu = du.y - du.x + 1, ntu = du.w - du.z + 1;
   const long long Na = (long long)s2.arr_ns * s2.arr_nt;
   const float* yf = y + (long long)frame * y_fs;
-  // This thread's block pixels (at most MAXC^2 = 2 x L2_THREADS) and what is
-  // written there, the same for every cell: M g on the lenslet's own pixels
-  // (wpx = index, mv = M), zero on unowned pixels of blocks that tile the
-  // plane (wpx = -(index + 2)), nothing elsewhere (wpx = -1); rcx = (r, c).
-  static_assert(MAXC * MAXC <= 2 * L2_THREADS, "two block pixels per thread");
-  const SmallDiv dc = small_div(nc);
-  int wpx[2], rcx[2];
-  float mv[2];
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int o = threadIdx.x + e * L2_THREADS;
-    wpx[e] = -1;
-    rcx[e] = -1;
-    mv[e] = 0.0f;
-    if (o < nr * nc) {
-      const int r = div_of(dc, o), c = o - r * nc;
-      const int px = (rr.x + r) * s2.arr_ns + cc.x + c;
-      const int own = __ldg(s2.owner + px);
-      rcx[e] = (r << 8) | c;
-      if (own == mu) {
-        wpx[e] = px;
-        mv[e] = __ldg(s2.mask + px);
-      } else if (!s2.overlap && own < 0) {
-        wpx[e] = -(px + 2);
-      }
+  // This thread's block pixel and what is written there, the same for every
+  // cell: M g on the lenslet's own pixels (wpx = index, mv = M), zero on
+  // unowned pixels of blocks that tile the plane (wpx = -(index + 2)),
+  // nothing elsewhere (wpx = -1).
+  int wpx = -1, pr = 0, pc = 0;
+  float mv = 0.0f;
+  if ((int)threadIdx.x < nr * nc) {
+    pr = div_of(small_div(nc), threadIdx.x);
+    pc = threadIdx.x - pr * nc;
+    const int px = (rr.x + pr) * s2.arr_ns + cc.x + pc;
+    const int own = __ldg(s2.owner + px);
+    if (own == mu) {
+      wpx = px;
+      mv = __ldg(s2.mask + px);
+    } else if (!s2.overlap && own < 0) {
+      wpx = -(px + 2);
     }
   }
-  for (int k = 0; k < s2.K; ++k) {
-    if (!cell_on(s2.sub_n, s2.sub_s, k)) continue;   // uniform: plane k is left unwritten
-    const LensletParam* L = s2.lens + (long long)k * nmu + mu;
-    const int4 dr = s2.det_range[(long long)k * nmu + mu];
-    const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
-    float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
-    if (nds <= 0 || ndt <= 0) {   // no detector pixel: the block's written pixels are zero
-#pragma unroll
-      for (int e = 0; e < 2; ++e)
-        if (wpx[e] != -1) fk[wpx[e] >= 0 ? wpx[e] : -(wpx[e] + 2)] = 0.0f;
-      continue;   // uniform
+  if (nsu > 0 && ntu > 0) {   // the union window of y, shared by every cell
+    const SmallDiv du_div = small_div(nsu);
+    for (int e = threadIdx.x; e < ntu * nsu; e += S2_THREADS) {
+      const int bu = div_of(du_div, e), qu = e - bu * nsu;
+      Y[bu][qu] = __ldg(yf + (long long)(du.z + bu) * s2.det_ns + du.x + qu);
     }
-    lenslet_weights(L, dr, cc, rr, Bs, Bt);
-    const SmallDiv dd = small_div(nds);
-    for (int o = threadIdx.x; o < ndt * nds; o += blockDim.x) {
-      const int b = div_of(dd, o), q = o - b * nds;
-      Y[b][q] = __ldg(yf + (long long)(dr.z + b) * s2.det_ns + dr.x + q);
+  }
+  float* faf = fa + (long long)frame * fa_fs;
+  for (int k0 = 0; k0 < s2.K; k0 += S2_KB) {
+    s2_cell_table(s2, mu, nmu, k0, du, nr, cell);
+    __syncthreads();
+    {
+      const int kk = threadIdx.x >> 6, task = threadIdx.x & 63;
+      if (cell[kk].on && task < cell[kk].nds + cell[kk].ndt)
+        lenslet_weight_task(s2.lens + (long long)(k0 + kk) * nmu + mu, cell[kk].dr, cc, rr, task, Bs[kk], Bt[kk]);
     }
     __syncthreads();
-    // U[r][q] = sum_b Bt[r][b] Y[b][q]
-    for (int o = threadIdx.x; o < nr * nds; o += blockDim.x) {
-      const int r = div_of(dd, o), q = o - r * nds;
+    // U[kk][r][q] = sum_b Bt[kk][r][b] y[dr.z + b][dr.x + q]
+    const int tot = cell[0].cnt + cell[1].cnt + cell[2].cnt + cell[3].cnt;
+    for (int e = threadIdx.x; e < tot; e += S2_THREADS) {
+      int o = e;
+      const int kk = s2_task_cell(cell, o);
+      const int r = div_of(cell[kk].dd, o), q = o - r * cell[kk].nds;
+      const int dz = cell[kk].dz, qx = cell[kk].dx + q;
       float u = 0.0f;
-      for (int b = 0; b < ndt; ++b) u = fmaf(Bt[r][b], Y[b][q], u);
-      U[r][q] = u;
+      for (int b = 0; b < cell[kk].ndt; ++b) u = fmaf(Bt[kk][r][b], Y[dz + b][qx], u);
+      U[kk][r][q] = u;
     }
     __syncthreads();
-    const float scale = L->scale;
     // M (its diagonal) on this lenslet's own pixels; blocks that tile the
-    // plane also clear their unowned pixels, overlapping blocks leave them
+    // plane also clear their unowned pixels, overlapping blocks leave them.
+    // A cell outside the subset leaves its plane unwritten.
+    if (wpx != -1) {
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      if (wpx[e] >= 0) {
-        const int r = rcx[e] >> 8, c = rcx[e] & 255;
-        float g = 0.0f;
-        for (int q = 0; q < nds; ++q) g = fmaf(Bs[c][q], U[r][q], g);
-        fk[wpx[e]] = mv[e] * (scale * g);
-      } else if (wpx[e] != -1) {
-        fk[-(wpx[e] + 2)] = 0.0f;
+      for (int kk = 0; kk < S2_KB; ++kk) {
+        if (!cell[kk].sub) continue;
+        float* fk = faf + (long long)(k0 + kk) * Na;
+        if (wpx >= 0 && cell[kk].on) {
+          float g = 0.0f;
+          for (int q = 0; q < cell[kk].nds; ++q) g = fmaf(Bs[kk][pc][q], U[kk][pr][q], g);
+          fk[wpx] = mv * (cell[kk].scale * g);
+        } else {
+          fk[wpx >= 0 ? wpx : -(wpx + 2)] = 0.0f;
+        }
       }
     }
-    __syncthreads();
+    if (k0 + S2_KB < s2.K) __syncthreads();
   }
 }
 
@@ -821,7 +881,7 @@ cudaError_t launch_stage2_adjoint(const float* y, float* fa, StageTwo s2, int fr
                       (size_t)s2.K * s2.arr_ns * s2.arr_nt * sizeof(float), st);
   }
   dim3 g(s2.mla_ns * s2.mla_nt, frames);
-  stage2_lenslet_adjoint<<<g, L2_THREADS, 0, st>>>(y, fa, s2, y_frame_stride, fa_frame_stride);
+  stage2_lenslet_adjoint<<<g, S2_THREADS, 0, st>>>(y, fa, s2, y_frame_stride, fa_frame_stride);
   return cudaGetLastError();
 }
 
