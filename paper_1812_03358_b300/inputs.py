@@ -180,6 +180,15 @@ def config_multiview(seed: int = 3000, n_views: int = 4, n_px: int = 2048,
     return Volume(256, 256, 256, 0.5, 0.5, 0.5), cams
 
 
+def config_differentiable(n_views: int = 4, n_px: int = 1024, pitch: float = 0.01):
+    """Differentiable-reconstruction workload: four single-lens 1024 x 1024
+    cameras (2 x 2 cells) at yaw 0, 45, 90 and 135 degrees around a 256^3
+    volume at 0.5 mm."""
+    yaws = np.deg2rad(np.arange(n_views) * 180.0 / n_views)
+    cams = [table_single_lens(n_px, pitch, float(y), 2, 2) for y in yaws]
+    return Volume(256, 256, 256, 0.5, 0.5, 0.5), cams
+
+
 def tiny_plenoptic(n_lenslets=4, px_per_lenslet=6, ks=2, kt=2) -> (Volume, Camera):
     """A plenoptic camera small enough for an explicit system matrix."""
     cam = plenoptic_camera(n_lenslets=n_lenslets, px_per_lenslet=px_per_lenslet,
