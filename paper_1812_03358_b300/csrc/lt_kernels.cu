@@ -680,15 +680,41 @@ stage2_gather(const float* __restrict__ zbuf, float* __restrict__ y, StageTwo s2
   if (is >= s2.det_ns || it >= s2.det_nt) return;
   const int nmu = s2.mla_ns * s2.mla_nt;
   const int2 cs = s2.cand_all_s[is], ct = s2.cand_all_t[it];
+  const float* zf = zbuf + (long long)frame * nmu * (L2_W * L2_W);
   float acc = 0.0f;
-  for (int mt = ct.x; mt <= ct.y; ++mt)
-    for (int ms = cs.x; ms <= cs.y; ++ms) {
-      const int mu = mt * s2.mla_ns + ms;
-      const int4 du = s2.det_union[mu];
-      if (is < du.x || is > du.y || it < du.z || it > du.w) continue;
-      const int nsu = du.y - du.x + 1;
-      acc += __ldg(zbuf + ((long long)frame * nmu + mu) * (L2_W * L2_W) + (it - du.z) * nsu + (is - du.x));
+  if (cs.y - cs.x < 2 && ct.y - ct.x < 2) {
+    // at most 2 x 2 candidates (the usual case): their windows, then their
+    // sub-image values, each set of loads in flight together; summed in the
+    // same (mt, ms) order as the general loop below
+    int4 du[4];
+    float v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int mt = ct.x + (c >> 1), ms = cs.x + (c & 1);
+      du[c] = make_int4(1, 0, 1, 0);   // covers nothing
+      if (mt <= ct.y && ms <= cs.y) du[c] = __ldg(s2.det_union + mt * s2.mla_ns + ms);
     }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int mu = (ct.x + (c >> 1)) * s2.mla_ns + cs.x + (c & 1);
+      const bool in = is >= du[c].x && is <= du[c].y && it >= du[c].z && it <= du[c].w;
+      v[c] = in ? __ldg(zf + (long long)mu * (L2_W * L2_W) + (it - du[c].z) * (du[c].y - du[c].x + 1) + (is - du[c].x))
+                : 0.0f;
+      du[c].x = in;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (du[c].x) acc += v[c];
+  } else {
+    for (int mt = ct.x; mt <= ct.y; ++mt)
+      for (int ms = cs.x; ms <= cs.y; ++ms) {
+        const int mu = mt * s2.mla_ns + ms;
+        const int4 du = s2.det_union[mu];
+        if (is < du.x || is > du.y || it < du.z || it > du.w) continue;
+        const int nsu = du.y - du.x + 1;
+        acc += __ldg(zf + (long long)mu * (L2_W * L2_W) + (it - du.z) * nsu + (is - du.x));
+      }
+  }
   y[(long long)frame * y_fs + (long long)it * s2.det_ns + is] = acc;
 }
 
