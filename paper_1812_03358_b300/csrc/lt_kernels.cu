@@ -597,7 +597,7 @@ __device__ __forceinline__ void lenslet_weights(const LensletParam* L, int4 dr, 
 
 // Forward, pass 1: each lenslet's contribution sum_k Bt (x) Bs fa_k on the
 // union over cells of its detector windows, written to zbuf (no overlap).
-__global__ void __launch_bounds__(L2_THREADS)
+__global__ void __launch_bounds__(L2_THREADS, 16)
 stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_fs, float* __restrict__ zbuf) {
   __shared__ float Bs[MAXC][L2_W + 1];
   __shared__ float Bt[MAXC][L2_W + 1];
@@ -639,12 +639,17 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
       const int4 dr = s2.det_range[(long long)k * nmu + mu];
       const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
       if (nds <= 0 || ndt <= 0) continue;   // uniform
-      lenslet_weights(L, dr, cc, rr, Bs, Bt);
+      // this lenslet's own pixels, zero elsewhere: loaded before the
+      // footprint entries are evaluated so that the two overlap
       const float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
+      float fv[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) fv[e] = pix[e] >= 0 ? __ldg(fk + pix[e]) : 0.0f;
+      lenslet_weights(L, dr, cc, rr, Bs, Bt);
       const SmallDiv dd = small_div(nds);
 #pragma unroll
-      for (int e = 0; e < 2; ++e)   // this lenslet's own pixels, zero elsewhere
-        if (fix[e] >= 0) (&F[0][0])[fix[e]] = pix[e] >= 0 ? __ldg(fk + pix[e]) : 0.0f;
+      for (int e = 0; e < 2; ++e)
+        if (fix[e] >= 0) (&F[0][0])[fix[e]] = fv[e];
       __syncthreads();
       // W[r][q] = sum_c Bs[c][q] F[r][c]
       for (int o = threadIdx.x; o < nr * nds; o += blockDim.x) {
