@@ -207,7 +207,8 @@ def shear_passes(flush, stream, reps=20):
     """The rotation passes of a yawed camera (quarter turn + z shear + x shear,
     and the transposed passes) on a 128^3 volume: CUDA-event time per call, L2
     flushed before each, against the HBM roofline.  Algorithmic bytes per
-    pass = 4 (N_in + N_out)."""
+    pass = 4 (N_in + N_out).  Also timed: a pitched and rolled camera's
+    signed permutation and three shear passes (general_*_ms)."""
     import math
     import torch
     from paper_1812_03358_b300 import inputs as I
@@ -239,6 +240,24 @@ def shear_passes(flush, stream, reps=20):
         out[name + "_ms"] = ms
         out[name + "_GBps"] = nbytes / (ms * 1e-3) / 1e9
         out[name + "_frac"] = out[name + "_GBps"] / peak
+    plan.close()
+    # a pitched and rolled camera: signed permutation + three shear passes
+    cam = I.table_single_lens(64, 0.08, yaw=0.5)
+    cam.pitch, cam.roll = 0.3, -0.2
+    plan = lt.Plan(vol, [cam])
+    (gz, gy, gx), _ = plan.camera_grid(0)
+    xg = plan.rotate(0, x)
+    xga = plan.rotate_adjoint(0, xg)
+    out["general_workload"] = f"128^3 volume (1 mm), yaw 0.5, pitch 0.3, roll -0.2 rad -> camera grid {gz}x{gy}x{gx}"
+    for name, fn in (("forward", lambda: plan.rotate(0, x, xg)), ("adjoint", lambda: plan.rotate_adjoint(0, xg, xga))):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        out["general_" + name + "_ms"] = sum(a.elapsed_time(b) for a, b in ev) / reps
     plan.close()
     return out
 

@@ -484,6 +484,108 @@ __global__ void __launch_bounds__(256) shear_pass_adjoint(const float* __restric
   }
 }
 
+// Passes along y (AX = 1) or z (AX = 2), column-walking: thread = column
+// (x, other axis) and kShearZChunk outputs along the sheared axis, whose
+// whole source window (kShearZChunk + NW - 1 values, NW >= nw with zero
+// weights past nw) is loaded before any output is formed; each output's taps
+// in ascending q, so every value equals shear_pass_forward's bit for bit.
+// Outputs along these axes share most of their window, which the
+// one-output-per-thread kernel read again for every output.
+template <int NW, int AX>
+__global__ void __launch_bounds__(256) shear_pass_col_forward(const float* __restrict__ in, float* __restrict__ out,
+                                                              ShearPass ps, int frames) {
+  static_assert(AX == 1 || AX == 2, "column passes run along y or z");
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int w2 = blockIdx.y * 8 + threadIdx.y;   // y (AX = 2) or z (AX = 1)
+  const int i0 = blockIdx.z * kShearZChunk;      // first output along the axis
+  if (x >= ps.n0 || w2 >= (AX == 2 ? ps.n1 : ps.n2)) return;
+  const int n_ax = AX == 2 ? ps.n2 : ps.n1;
+  const int n_out = n_ax + 2 * ps.pad;
+  const int nout = min(kShearZChunk, n_out - i0);
+  const int col = w2 * ps.nu + x;               // u = x, v = the other axis
+  float w[NW];
+#pragma unroll
+  for (int q = 0; q < NW; ++q) w[q] = q < ps.nw ? __ldg(ps.tab + (long long)col * ps.nw + q) : 0.0f;
+  const int jb = i0 - ps.pad + __ldg(ps.jo + col);   // first source of output i0
+  const long long s_in = AX == 2 ? (long long)ps.n0 * ps.n1 : ps.n0;
+  const long long b_in = AX == 2 ? (long long)w2 * ps.n0 + x : (long long)w2 * ps.n1 * ps.n0 + x;
+  const long long s_out = s_in;
+  const long long b_out = AX == 2 ? b_in : (long long)w2 * n_out * ps.n0 + x;
+  const long long in_fs = (long long)ps.n0 * ps.n1 * ps.n2, out_fs = in_fs / n_ax * n_out;
+  for (int f = 0; f < frames; ++f) {
+    const float* src = in + f * in_fs + b_in + (long long)jb * s_in;   // source jb + q at src + q s_in
+    float v[kShearZChunk + NW - 1];
+    if (jb >= 0 && jb + kShearZChunk + NW - 1 <= n_ax) {
+#pragma unroll
+      for (int q = 0; q < kShearZChunk + NW - 1; ++q) v[q] = __ldg(src + q * s_in);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kShearZChunk + NW - 1; ++q)
+        v[q] = (unsigned)(jb + q) < (unsigned)n_ax ? __ldg(src + q * s_in) : 0.0f;
+    }
+    float* o = out + f * out_fs + b_out;
+#pragma unroll
+    for (int t = 0; t < kShearZChunk; ++t) {
+      if (t < nout) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc = fmaf(w[q], v[t + q], acc);
+        o[(long long)(i0 + t) * s_out] = acc;
+      }
+    }
+  }
+}
+
+// Transposed column pass: thread = column and kShearZChunk sources along the
+// axis, the window of outputs they gather from loaded first; taps in
+// descending q as in shear_pass_adjoint, bit for bit.
+template <int NW, int AX>
+__global__ void __launch_bounds__(256) shear_pass_col_adjoint(const float* __restrict__ gout,
+                                                              float* __restrict__ gin, ShearPass ps, int frames) {
+  static_assert(AX == 1 || AX == 2, "column passes run along y or z");
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int w2 = blockIdx.y * 8 + threadIdx.y;
+  const int j0 = blockIdx.z * kShearZChunk;      // first source along the axis
+  if (x >= ps.n0 || w2 >= (AX == 2 ? ps.n1 : ps.n2)) return;
+  const int n_ax = AX == 2 ? ps.n2 : ps.n1;
+  const int n_out = n_ax + 2 * ps.pad;
+  const int nsrc = min(kShearZChunk, n_ax - j0);
+  const int col = w2 * ps.nu + x;
+  float w[NW];   // w[k] weights the k-th value of the window (ascending output index)
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const int q = NW - 1 - k;
+    w[k] = q < ps.nw ? __ldg(ps.tab + (long long)col * ps.nw + q) : 0.0f;
+  }
+  const int ib = j0 + ps.pad - __ldg(ps.jo + col) - (NW - 1);   // first output of source j0's window
+  const long long s_in = AX == 2 ? (long long)ps.n0 * ps.n1 : ps.n0;
+  const long long b_in = AX == 2 ? (long long)w2 * ps.n0 + x : (long long)w2 * ps.n1 * ps.n0 + x;
+  const long long b_out = AX == 2 ? b_in : (long long)w2 * n_out * ps.n0 + x;
+  const long long in_fs = (long long)ps.n0 * ps.n1 * ps.n2, out_fs = in_fs / n_ax * n_out;
+  for (int f = 0; f < frames; ++f) {
+    const float* g = gout + f * out_fs + b_out + (long long)ib * s_in;   // output ib + k at g + k s_in
+    float v[kShearZChunk + NW - 1];
+    if (ib >= 0 && ib + kShearZChunk + NW - 1 <= n_out) {
+#pragma unroll
+      for (int k = 0; k < kShearZChunk + NW - 1; ++k) v[k] = __ldg(g + k * s_in);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kShearZChunk + NW - 1; ++k)
+        v[k] = (unsigned)(ib + k) < (unsigned)n_out ? __ldg(g + k * s_in) : 0.0f;
+    }
+    float* o = gin + f * in_fs + b_in;
+#pragma unroll
+    for (int t = 0; t < kShearZChunk; ++t) {
+      if (t < nsrc) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) acc = fmaf(w[k], v[t + k], acc);
+        o[(long long)(j0 + t) * s_in] = acc;
+      }
+    }
+  }
+}
+
 // Signed permutation: permuted voxel p -> source voxel s, s_m = p[km[m]] or
 // n_m - 1 - p[km[m]].  Forward gathers from x; the transpose gathers back.
 __global__ void __launch_bounds__(256) grot_permute(const float* __restrict__ x, float* __restrict__ xp, GenRot g,
@@ -590,7 +692,20 @@ cudaError_t launch_grot_forward(const float* x, float* b0, float* b1, float* b2,
     float* out = k == last ? xr : scratch[k];
     int m0, m1, m2;
     pass_out_dims(ps, m0, m1, m2);
-    shear_pass_forward<<<grid3(m0, m1, m2), blk, 0, st>>>(cur, out, ps, frames);
+    if (ps.axis != 0 && ps.nw <= 16) {
+      const int n_oth = ps.axis == 2 ? ps.n1 : ps.n2;
+      const int n_out = (ps.axis == 2 ? ps.n2 : ps.n1) + 2 * ps.pad;
+      const dim3 g((ps.n0 + 31) / 32, (n_oth + 7) / 8, (n_out + kShearZChunk - 1) / kShearZChunk);
+      if (ps.axis == 2) {
+        if (ps.nw <= 8) shear_pass_col_forward<8, 2><<<g, blk, 0, st>>>(cur, out, ps, frames);
+        else shear_pass_col_forward<16, 2><<<g, blk, 0, st>>>(cur, out, ps, frames);
+      } else {
+        if (ps.nw <= 8) shear_pass_col_forward<8, 1><<<g, blk, 0, st>>>(cur, out, ps, frames);
+        else shear_pass_col_forward<16, 1><<<g, blk, 0, st>>>(cur, out, ps, frames);
+      }
+    } else {
+      shear_pass_forward<<<grid3(m0, m1, m2), blk, 0, st>>>(cur, out, ps, frames);
+    }
     cur = out;
   }
   return cudaGetLastError();
@@ -604,7 +719,20 @@ cudaError_t launch_grot_adjoint(const float* g_xr, float* b0, float* b1, float* 
   for (int k = 2; k >= 0; --k) {
     const ShearPass& ps = g.pass[k];
     if (!ps.active) continue;
-    shear_pass_adjoint<<<grid3(ps.n0, ps.n1, ps.n2), blk, 0, st>>>(cur, in_buf[k], ps, frames);
+    if (ps.axis != 0 && ps.nw <= 16) {
+      const int n_oth = ps.axis == 2 ? ps.n1 : ps.n2;
+      const int n_ax = ps.axis == 2 ? ps.n2 : ps.n1;
+      const dim3 g((ps.n0 + 31) / 32, (n_oth + 7) / 8, (n_ax + kShearZChunk - 1) / kShearZChunk);
+      if (ps.axis == 2) {
+        if (ps.nw <= 8) shear_pass_col_adjoint<8, 2><<<g, blk, 0, st>>>(cur, in_buf[k], ps, frames);
+        else shear_pass_col_adjoint<16, 2><<<g, blk, 0, st>>>(cur, in_buf[k], ps, frames);
+      } else {
+        if (ps.nw <= 8) shear_pass_col_adjoint<8, 1><<<g, blk, 0, st>>>(cur, in_buf[k], ps, frames);
+        else shear_pass_col_adjoint<16, 1><<<g, blk, 0, st>>>(cur, in_buf[k], ps, frames);
+      }
+    } else {
+      shear_pass_adjoint<<<grid3(ps.n0, ps.n1, ps.n2), blk, 0, st>>>(cur, in_buf[k], ps, frames);
+    }
     cur = in_buf[k];
   }
   grot_permute_adjoint<<<grid3(g.nx, g.ny, g.nz), blk, 0, st>>>(cur, x, g, frames, accumulate);
