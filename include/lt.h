@@ -105,8 +105,13 @@ typedef struct lt_plan lt_plan;
  * every transport parameter (Tables II/III) in float64 on the host and
  * uploads them.  Uses the current CUDA device.
  * Errors: LT_EINVAL for non-positive sizes/pitches/focal lengths, a slice at
- * or behind the lens, a lenslet radius above half the pitch, footprints
- * wider than the kernels' windows (LT_EUNSUPPORTED); LT_ENOMEM. */
+ * or behind the lens, a lenslet radius above half the pitch; LT_EUNSUPPORTED
+ * for footprints wider than the kernels' windows (a pixel's footprint over
+ * more than 8 voxels per axis, a voxel covered by more than 32 pixels per
+ * axis, more than 16 array pixels per lenslet per axis, a lenslet sub-image
+ * wider than 24 detector pixels per axis); LT_ENOMEM.
+ * The forward makes one persistent launch per forward window class (2, 3,
+ * 4, 8 voxels) present among the cameras. */
 LT_API lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_desc* cams,
                          int32_t n_cams, int32_t n_frames, lt_plan** out);
 
