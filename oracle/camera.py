@@ -298,6 +298,25 @@ def plenoptic_array_field(vol, cam, x, cell):
     return transmission(cam) * Fa
 
 
+def plenoptic_array_block(vol, cam, x, cell, rows, cols):
+    """Entries [rows][cols] of plenoptic_array_field: the same sum with each
+    axis' transport matrix restricted to those array rows and columns (spot
+    checks of planes too large for the whole field)."""
+    X = np.asarray(x, dtype=np.float64).reshape(vol.shape)
+    rows, cols = np.asarray(rows), np.asarray(cols)
+    sk, tk, d0s, d0t = cell
+    ts = centers(cam.arr_ns, cam.arr_ps)[cols]
+    tt = centers(cam.arr_nt, cam.arr_pt)[rows]
+    Fa = np.zeros((len(rows), len(cols)))
+    for n in range(vol.nz):
+        Xpq, X0q = slice_maps(cam, slice_distances(vol, cam)[n], cam.d_lens_mla)
+        Bs = matrix_1d(cam, Xpq, X0q, ts, cam.arr_ps, sk, d0s, centers(vol.nx, vol.dx), vol.dx)
+        Bt = matrix_1d(cam, Xpq, X0q, tt, cam.arr_pt, tk, d0t, centers(vol.ny, vol.dy), vol.dy)
+        Fa += vol.dz * (Bt @ X[n] @ Bs.T)
+    Fa /= array_basis_volume(cam, cell)
+    return transmission(cam)[np.ix_(rows, cols)] * Fa
+
+
 def plenoptic_stage2(cam, fields, st=None, cells=None):
     """y = sum_k sum_mu B^{d mu}_k fa_k for given (masked) array-plane fields
     [K][arr_nt][arr_ns] (k over `cells`)."""

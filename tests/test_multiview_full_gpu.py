@@ -5,12 +5,15 @@ a drifting plume field, every camera x frame in one persistent launch.
 Checked at this size: the batched launch equals per-camera launches bit for
 bit; the adjoint identity <A x, y> = <x, A^T y>; every rotation conserves the
 voxel sum; sampled rotated voxels of the first and last frames equal the
-oracle's; a CUDA graph of the autotuned plan replays the eager result."""
+oracle's; sampled blocks of the plenoptic camera's array plane (every cell,
+first and last frames) equal the oracle's; a CUDA graph of the autotuned
+plan replays the eager result."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import camera as O
 from oracle import rotation as OR_
 from paper_1812_03358_b300 import build, inputs as I, lt
 
@@ -72,6 +75,26 @@ def test_rotations_conserve_sum_and_match_oracle_samples(multiview):
             scale = float(np.abs(xf).max())
             assert np.all(np.abs(got - ref) <= 1e-5 * scale + 1e-6 * np.abs(ref))
         del xc
+
+
+def test_plenoptic_array_blocks_match_oracle(multiview):
+    vol, cams, plan, x = multiview
+    c = next(i for i, cam in enumerate(cams) if cam.kind == I.CAM_PLENOPTIC)
+    cam = cams[c]
+    fa = plan.stage1(c, x)   # [frames][cells][arr_nt][arr_ns]
+    rng = np.random.default_rng(29)
+    for f in (0, FRAMES - 1):
+        xf = x[f].cpu().numpy().reshape(vol.shape)
+        for ci, cell in enumerate(O.lens_cells(cam)):
+            rows = np.sort(rng.choice(np.arange(cam.arr_nt // 4, 3 * cam.arr_nt // 4), 3, replace=False))
+            cols = np.sort(rng.choice(np.arange(cam.arr_ns // 4, 3 * cam.arr_ns // 4), 48, replace=False))
+            ref = O.plenoptic_array_block(vol, cam, xf, cell, rows, cols)
+            r_t = torch.as_tensor(rows, device="cuda")
+            c_t = torch.as_tensor(cols, device="cuda")
+            got = fa[f, ci].index_select(0, r_t).index_select(1, c_t).cpu().numpy().astype(np.float64)
+            scale = float(np.abs(ref).max())
+            assert scale > 0
+            assert np.all(np.abs(got - ref) <= 1e-5 * scale + 1e-6 * np.abs(ref))
 
 
 def test_graph_replay_of_autotuned_plan(multiview):

@@ -181,3 +181,17 @@ def test_plenoptic_total_flux_equals_masked_array_flux():
     img = camera.single_forward(vol, single, x)
     expect = img[camera.lenslet_owner(cam) >= 0].sum()
     assert abs(y.sum() - expect) < 1e-12 * expect
+
+
+def test_array_block_equals_whole_array_field():
+    vol, cam = I.tiny_plenoptic()
+    x = I.gaussian_blobs(vol, seed=1300)
+    rng = np.random.default_rng(3)
+    for cell in camera.lens_cells(cam):
+        full = camera.plenoptic_array_field(vol, cam, x, cell)
+        rows = np.sort(rng.choice(cam.arr_nt, size=5, replace=False))
+        cols = np.sort(rng.choice(cam.arr_ns, size=7, replace=False))
+        blk = camera.plenoptic_array_block(vol, cam, x, cell, rows, cols)
+        assert np.abs(blk - full[np.ix_(rows, cols)]).max() <= 1e-13 * np.abs(full).max()
+        allb = camera.plenoptic_array_block(vol, cam, x, cell, np.arange(cam.arr_nt), np.arange(cam.arr_ns))
+        assert np.abs(allb - full).max() <= 1e-13 * np.abs(full).max()
