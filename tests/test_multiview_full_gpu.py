@@ -5,7 +5,8 @@ a drifting plume field, every camera x frame in one persistent launch.
 Checked at this size: the batched launch equals per-camera launches bit for
 bit; the adjoint identity <A x, y> = <x, A^T y>; every rotation conserves the
 voxel sum; sampled rotated voxels of the first and last frames equal the
-oracle's; sampled blocks of the plenoptic camera's array plane (every cell,
+oracle's; a yawed camera's image equals the unrotated camera's image of the
+rotated volume; sampled blocks of the plenoptic camera's array plane (every cell,
 first and last frames) equal the oracle's; a CUDA graph of the autotuned
 plan replays the eager result."""
 import numpy as np
@@ -75,6 +76,25 @@ def test_rotations_conserve_sum_and_match_oracle_samples(multiview):
             scale = float(np.abs(xf).max())
             assert np.all(np.abs(got - ref) <= 1e-5 * scale + 1e-6 * np.abs(ref))
         del xc
+
+
+def test_rotated_camera_is_unrotated_camera_on_rotated_grid(multiview):
+    """A yawed camera's image equals the image of the same camera at yaw 0
+    looking at the rotated volume on the camera grid (the projection of
+    an unrotated camera being pinned against the oracle elementwise)."""
+    import dataclasses
+    vol, cams, plan, x = multiview
+    for c in (0, 2):
+        (nz, ny, nx), (dz, dy, dx) = plan.camera_grid(c)
+        plan_r = lt.Plan(I.Volume(nx, ny, nz, dx, dy, dz), [dataclasses.replace(cams[c], yaw=0.0)], FRAMES)
+        xr = plan.rotate(c, x)
+        y_r = plan_r.forward(xr)
+        y_c = plan.forward_camera(c, x)
+        scale = float(y_c.abs().max())
+        assert scale > 0
+        assert float((y_r - y_c).abs().max()) <= 1e-6 * scale
+        plan_r.close()
+        del xr, y_r, y_c
 
 
 def test_plenoptic_array_blocks_match_oracle(multiview):
