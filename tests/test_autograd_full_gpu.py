@@ -108,4 +108,4 @@ def test_projected_tv_fit_lowers_objective(fit):
         losses.append(float(loss.detach()))
     assert all(b <= a * (1 + 1e-6) for a, b in zip(losses, losses[1:]))
     assert losses[-1] < 0.7 * losses[0]
-    assert float(x.min()) >= 0.0 and bool(torch.isfinite(x).all())
+    assert float(x.detach().min()) >= 0.0 and bool(torch.isfinite(x.detach()).all())
