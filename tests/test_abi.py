@@ -80,3 +80,13 @@ def test_orientation_and_mla_fields_validated_on_host(library):
         lt.lt_plan_create(vol, [bad_layout])
     assert e.value.status == lt.LT_EINVAL and "mla_layout" in str(e.value)
 
+
+
+def test_binding_refuses_to_run_without_the_library(monkeypatch):
+    """No CPU fallback: with the library absent, the first call raises."""
+    from paper_1812_03358_b300 import inputs as I
+    from paper_1812_03358_b300 import lt as LT
+    monkeypatch.setattr(LT, "_lib", None)
+    monkeypatch.setattr(LT, "LIB_PATH", "/nonexistent/liblt.so")
+    with pytest.raises(RuntimeError, match="missing"):
+        LT.Plan(I.Volume(4, 4, 4, 1.0, 1.0, 1.0), [I.table_single_lens(8, 0.1)])
