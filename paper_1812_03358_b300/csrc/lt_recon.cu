@@ -57,6 +57,17 @@ dot_partials(const float* __restrict__ a, const float* __restrict__ b, const flo
 
 // Table V step 1b (gamma_c = y^T W p / y^T W y, c > 0) and the FISTA scalars
 // t^{(n+1)} = (1 + sqrt(1 + 4 t^2)) / 2, mom = (t^{(n)} - 1) / t^{(n+1)}.
+// FISTA step (Table V): t <- (1 + sqrt(1 + 4 t^2)) / 2 and the momentum
+// weight (t_old - 1) / t_new of the coming update; one thread, once per
+// iteration.
+__device__ __forceinline__ void fista_advance(Scalars* sc) {
+  const double t = sc->t;
+  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+  sc->mom = (t - 1.0) / tn;
+  sc->t = tn;
+  sc->iter += 1;
+}
+
 __global__ void finalize_gains(const double* __restrict__ part, const double* __restrict__ ywy,
                                double* __restrict__ gains, int F, int C, int estimate,
                                Scalars* __restrict__ sc) {
@@ -70,13 +81,7 @@ __global__ void finalize_gains(const double* __restrict__ part, const double* __
     for (int b = 0; b < RED_BLOCKS; ++b) s += part[(long long)idx * RED_BLOCKS + b];
     gains[idx] = ywy[idx] > 0.0 ? s / ywy[idx] : 0.0;
   }
-  if (threadIdx.x == 0) {
-    const double t = sc->t;
-    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    sc->mom = (t - 1.0) / tn;
-    sc->t = tn;
-    sc->iter += 1;
-  }
+  if (threadIdx.x == 0) fista_advance(sc);
 }
 
 // d = a p - gamma_c y over camera c's pixels, r = a W d (a = K_c / |S_c| of
@@ -85,8 +90,10 @@ __global__ void finalize_gains(const double* __restrict__ part, const double* __
 __global__ void __launch_bounds__(RED_THREADS)
 residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const float* __restrict__ p,
                 float* __restrict__ r, const double* __restrict__ gains, long long off, long long len,
-                long long m_total, int C, int c, double* __restrict__ fit_part, float alpha) {
+                long long m_total, int C, int c, double* __restrict__ fit_part, float alpha,
+                Scalars* __restrict__ sc) {
   __shared__ double sh[32];
+  if (sc && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) fista_advance(sc);
   const long long base = (long long)blockIdx.y * m_total + off;
   const float g = (float)gains[blockIdx.y * C + c];
   double acc = 0.0;
@@ -314,11 +321,13 @@ static lt_status recon_step(lt_recon* R, int sel, int sub, cudaStream_t st) {
     for (int c = 1; c < R->C; ++c)
       dot_partials<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
           R->y, R->p, R->w, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->part, subset_scale(R, c, sub));
-  finalize_gains<<<1, 256, 0, st>>>(R->part, R->ywy, R->gains, R->F, R->C, est, R->sc);
+  // without estimation the gains keep their initial values (1), and the
+  // FISTA scalars advance in the first residual block instead
+  if (est) finalize_gains<<<1, 256, 0, st>>>(R->part, R->ywy, R->gains, R->F, R->C, est, R->sc);
   for (int c = 0; c < R->C; ++c)  // a W (a p - gamma y)
     residual_kernel<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
         R->y, R->w, R->p, R->r, R->gains, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->fit_part,
-        (float)subset_scale(R, c, sub));
+        (float)subset_scale(R, c, sub), !est && c == 0 ? R->sc : nullptr);
   s = plan_adjoint(P, R->r, R->g, st, ss);  // step 1c + 2: g = sum_c A_c^T r_c
   if (s != LT_OK) return s;
   const lt_volume_desc& v = P->vol;
