@@ -484,6 +484,91 @@ __global__ void __launch_bounds__(256) shear_pass_adjoint(const float* __restric
   }
 }
 
+// Passes along x, row-staged: warp = one (y, z) row, whose n0 inputs (or, for
+// the transpose, n0 + 2 pad outputs) sit in the warp's shared-memory slice
+// between WX zeros; the row's WX (>= nw, zero-padded) weights in registers.
+// Taps in ascending (forward) or descending (transpose) q, as in
+// shear_pass_forward / shear_pass_adjoint, whose values they give bit for bit.
+template <int WX>
+__global__ void __launch_bounds__(32 * kShearXWarps) shear_pass_row_forward(const float* __restrict__ in,
+                                                                            float* __restrict__ out, ShearPass ps,
+                                                                            int frames) {
+  extern __shared__ float smem_rows[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long row = (long long)blockIdx.x * kShearXWarps + wid;   // z * n1 + y
+  if (row >= (long long)ps.n1 * ps.n2) return;   // warp-uniform; no block barrier below
+  const int n_out = ps.n0 + 2 * ps.pad;
+  const int L = ps.n0 + 2 * WX;
+  float* Rw = smem_rows + wid * L;
+  if (lane < WX) {
+    Rw[lane] = 0.0f;
+    Rw[WX + ps.n0 + lane] = 0.0f;
+  }
+  const int col = (int)row;   // u = y, v = z: col = z * nu + y with nu = n1
+  float w[WX];
+#pragma unroll
+  for (int q = 0; q < WX; ++q) w[q] = q < ps.nw ? __ldg(ps.tab + (long long)col * ps.nw + q) : 0.0f;
+  const int off = __ldg(ps.jo + col) - ps.pad;   // output i's first source is i + off
+  const long long in_fs = (long long)ps.n0 * ps.n1 * ps.n2, out_fs = (long long)n_out * ps.n1 * ps.n2;
+  for (int f = 0; f < frames; ++f) {
+    const float* src = in + f * in_fs + row * ps.n0;
+    __syncwarp();
+    for (int j = lane; j < ps.n0; j += 32) Rw[WX + j] = __ldg(src + j);
+    __syncwarp();
+    float* o = out + f * out_fs + row * n_out;
+    for (int i = lane; i < n_out; i += 32) {
+      const int jb = i + off;
+      float acc = 0.0f;
+      if (jb > -WX && jb < ps.n0) {   // else every tap lies outside the row
+        const float* sp = Rw + WX + jb;
+#pragma unroll
+        for (int q = 0; q < WX; ++q) acc = fmaf(w[q], sp[q], acc);
+      }
+      o[i] = acc;
+    }
+  }
+}
+
+template <int WX>
+__global__ void __launch_bounds__(32 * kShearXWarps) shear_pass_row_adjoint(const float* __restrict__ gout,
+                                                                            float* __restrict__ gin, ShearPass ps,
+                                                                            int frames) {
+  extern __shared__ float smem_rows[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long row = (long long)blockIdx.x * kShearXWarps + wid;
+  if (row >= (long long)ps.n1 * ps.n2) return;
+  const int n_out = ps.n0 + 2 * ps.pad;
+  const int L = n_out + 2 * WX;
+  float* Gw = smem_rows + wid * L;
+  if (lane < WX) {
+    Gw[lane] = 0.0f;
+    Gw[WX + n_out + lane] = 0.0f;
+  }
+  const int col = (int)row;
+  float w[WX];
+#pragma unroll
+  for (int q = 0; q < WX; ++q) w[q] = q < ps.nw ? __ldg(ps.tab + (long long)col * ps.nw + q) : 0.0f;
+  const int off = ps.pad - __ldg(ps.jo + col);   // source j's last tap is output j + off
+  const long long in_fs = (long long)ps.n0 * ps.n1 * ps.n2, out_fs = (long long)n_out * ps.n1 * ps.n2;
+  for (int f = 0; f < frames; ++f) {
+    const float* g = gout + f * out_fs + row * n_out;
+    __syncwarp();
+    for (int i = lane; i < n_out; i += 32) Gw[WX + i] = __ldg(g + i);
+    __syncwarp();
+    float* o = gin + f * in_fs + row * ps.n0;
+    for (int j = lane; j < ps.n0; j += 32) {
+      const int ib = j + off;
+      float acc = 0.0f;
+      if (ib >= 0 && ib - (WX - 1) < n_out) {   // else every tap lies outside the row
+        const float* sp = Gw + WX + ib;
+#pragma unroll
+        for (int q = WX - 1; q >= 0; --q) acc = fmaf(w[q], sp[-q], acc);
+      }
+      o[j] = acc;
+    }
+  }
+}
+
 // Passes along y (AX = 1) or z (AX = 2), column-walking: thread = column
 // (x, other axis) and kShearZChunk outputs along the sheared axis, whose
 // whole source window (kShearZChunk + NW - 1 values, NW >= nw with zero
@@ -703,6 +788,16 @@ cudaError_t launch_grot_forward(const float* x, float* b0, float* b1, float* b2,
         if (ps.nw <= 8) shear_pass_col_forward<8, 1><<<g, blk, 0, st>>>(cur, out, ps, frames);
         else shear_pass_col_forward<16, 1><<<g, blk, 0, st>>>(cur, out, ps, frames);
       }
+    } else if (ps.axis == 0 && ps.nw <= 16 &&
+               (size_t)kShearXWarps * (ps.n0 + 32) * sizeof(float) <= (size_t)kShearXSmemMax) {
+      const long long rows = (long long)ps.n1 * ps.n2;
+      const dim3 g((unsigned)((rows + kShearXWarps - 1) / kShearXWarps));
+      if (ps.nw <= 8)
+        shear_pass_row_forward<8><<<g, 32 * kShearXWarps, kShearXWarps * (ps.n0 + 16) * sizeof(float), st>>>(
+            cur, out, ps, frames);
+      else
+        shear_pass_row_forward<16><<<g, 32 * kShearXWarps, kShearXWarps * (ps.n0 + 32) * sizeof(float), st>>>(
+            cur, out, ps, frames);
     } else {
       shear_pass_forward<<<grid3(m0, m1, m2), blk, 0, st>>>(cur, out, ps, frames);
     }
@@ -730,6 +825,17 @@ cudaError_t launch_grot_adjoint(const float* g_xr, float* b0, float* b1, float* 
         if (ps.nw <= 8) shear_pass_col_adjoint<8, 1><<<g, blk, 0, st>>>(cur, in_buf[k], ps, frames);
         else shear_pass_col_adjoint<16, 1><<<g, blk, 0, st>>>(cur, in_buf[k], ps, frames);
       }
+    } else if (ps.axis == 0 && ps.nw <= 16 &&
+               (size_t)kShearXWarps * (ps.n0 + 2 * ps.pad + 32) * sizeof(float) <= (size_t)kShearXSmemMax) {
+      const long long rows = (long long)ps.n1 * ps.n2;
+      const dim3 g((unsigned)((rows + kShearXWarps - 1) / kShearXWarps));
+      const int n_out = ps.n0 + 2 * ps.pad;
+      if (ps.nw <= 8)
+        shear_pass_row_adjoint<8><<<g, 32 * kShearXWarps, kShearXWarps * (n_out + 16) * sizeof(float), st>>>(
+            cur, in_buf[k], ps, frames);
+      else
+        shear_pass_row_adjoint<16><<<g, 32 * kShearXWarps, kShearXWarps * (n_out + 32) * sizeof(float), st>>>(
+            cur, in_buf[k], ps, frames);
     } else {
       shear_pass_adjoint<<<grid3(ps.n0, ps.n1, ps.n2), blk, 0, st>>>(cur, in_buf[k], ps, frames);
     }
