@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--warm-samples", type=int, default=6000,
                     help="training volumes for the warm-start time-to-residual measurement (0: skip)")
     ap.add_argument("--no-autotune", action="store_true",
