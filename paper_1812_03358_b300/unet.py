@@ -2,7 +2,7 @@
 
 The network maps a normalised back-projection to an initial volume for the
 Table V reconstruction (which then refines it; the plain solver stays the
-fallback and the judge of the result).  Four levels, 16-128 channels, 3x3x3
+fallback and the reference the result is measured against).  Four levels, 16-128 channels, 3x3x3
 convolutions with ReLU, 2x2x2 average pooling, nearest upsampling and
 channel-concatenated skips; bfloat16 activations and weights, float32
 accumulation, float32 master weights updated by Adam.  Every layer runs in the

@@ -5,7 +5,7 @@ Training pairs come from the forward model itself: a seeded plume volume x
 with Poisson noise, and the network input prepared from A^T y (the CUDA
 back-projector).  Reconstruction then starts from the network's estimate
 instead of 0 (Table V initialises x and z at 0; only the initial point
-changes).  The plain solver stays both the fallback and the judge:
+changes).  The plain solver stays both the fallback and the yardstick:
 
 * time-to-residual: wall time until the data fit (1/2) sum_c ||A_c x -
   gamma_c y_c||^2 reaches the value the plain solver has after n_plain
