@@ -308,6 +308,9 @@ LT_API lt_status lt_recon_state_size(const lt_recon* rec, int64_t* bytes);
 LT_API lt_status lt_recon_get_state(lt_recon* rec, void* host_buf);
 LT_API lt_status lt_recon_set_state(lt_recon* rec, const void* host_buf);
 
+/* Frees the solver's device state (D, x, z, scratch, captured graphs) after
+ * synchronising the device; the plan it was created on is not freed.
+ * NULL is accepted and ignored. */
 LT_API lt_status lt_recon_destroy(lt_recon* rec);
 
 /* Description of the last error on the calling thread ("" if none). */
