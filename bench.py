@@ -36,7 +36,6 @@ METRIC = "projector+adjoint ray-samples/s"
 UNIT = "ray-samples/s"
 WORKLOAD = ("plenoptic camera, 100x100 lenslets x 10x10 px (1000^2 detector), K=2x2 pillbox, "
             "128^3 FP32 plume volume (1 mm voxels), Poisson peak 1e4; one Table V FISTA iteration per step")
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
 def parse():
@@ -87,6 +86,54 @@ def dist_env():
 # clocks during the timed region (NVML reads only)
 # ---------------------------------------------------------------------------
 
+class _PyNvml:
+    name = "nvml (pynvml)"
+
+    def __init__(self, mod, h):
+        self.m, self.h = mod, h
+
+    def sm(self):
+        return self.m.nvmlDeviceGetClockInfo(self.h, self.m.NVML_CLOCK_SM)
+
+    def reasons(self):
+        return self.m.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+
+
+class _CtypesNvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (clock and
+    clock-event reasons of one device); nothing is set."""
+    name = "nvml (ctypes)"
+
+    def __init__(self, bus):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        self._ok(self.lib.nvmlInit_v2())
+        self.h = ctypes.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.h)))
+
+    @staticmethod
+    def _ok(rc):
+        if rc != 0:
+            raise RuntimeError(f"NVML error {rc}")
+
+    def _clock(self, fn):
+        v = self.ct.c_uint()
+        self._ok(fn(self.h, 1, self.ct.byref(v)))   # NVML_CLOCK_SM = 1
+        return int(v.value)
+
+    def max_sm(self):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def sm(self):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def reasons(self):
+        v = self.ct.c_ulonglong()
+        self._ok(self.lib.nvmlDeviceGetCurrentClocksEventReasons(self.h, self.ct.byref(v)))
+        return int(v.value)
+
+
 class ClockSampler:
     """Samples the SM clock and clock-event reasons of the benchmarked GPU
     while the timed region runs (NVML reads; nvidia-smi as a fallback)."""
@@ -96,7 +143,7 @@ class ClockSampler:
         "hw_power_brake_slowdown": 0x80,
     }
 
-    def __init__(self, device, period=0.02):
+    def __init__(self, device, period=0.001):
         import torch
         self.period = period
         self.samples = []
@@ -114,21 +161,27 @@ class ClockSampler:
             pynvml.nvmlInit()
             self.h = pynvml.nvmlDeviceGetHandleByPciBusId(self.bus)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            self.nvml = pynvml
-        except Exception as e:  # fall back to nvidia-smi
-            self.errors.append("nvml: " + repr(e))
+            self.nvml = _PyNvml(pynvml, self.h)
+        except Exception as e:  # the driver's NVML through ctypes, then nvidia-smi
+            self.errors.append("pynvml: " + repr(e)[:200])
+            try:
+                self.nvml = _CtypesNvml(self.bus)
+                self.max_mhz = self.nvml.max_sm()
+            except Exception as e2:
+                self.nvml = None
+                self.errors.append("libnvidia-ml: " + repr(e2)[:200])
 
     def _run_nvml(self):
-        nv = self.nvml
         while not self._stop.is_set():
             try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
-                mask = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                self.samples.append(self.nvml.sm())
+                mask = self.nvml.reasons()
                 for name, bit in self.REASONS.items():
                     if mask & bit:
                         self.reasons.add(name)
             except Exception as e:
-                self.errors.append(repr(e))
+                if len(self.errors) < 8:
+                    self.errors.append(repr(e)[:200])
             time.sleep(self.period)
 
     def __enter__(self):
@@ -168,7 +221,7 @@ class ClockSampler:
     def summary(self):
         out = {"sm_mhz": float(np.median(self.samples)) if self.samples else None,
                "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
-               "samples": len(self.samples), "source": "nvml" if self.nvml else "nvidia-smi"}
+               "samples": len(self.samples), "source": self.nvml.name if self.nvml else "nvidia-smi"}
         if not self.samples:
             out["errors"] = self.errors[:3]
         return out
@@ -201,6 +254,55 @@ def hbm_peak():
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+def measure_peaks(stream, reps=5):
+    """Roofline denominators of the on-chip levels, measured here by the
+    library's own microbenchmarks (include/lt_peaks.h): shared-memory read
+    and L2 read bandwidth (GB/s) and the FP32 FMA rate (TFLOP/s), each the
+    best of `reps` CUDA-event-timed launches on the launching stream.  HBM is
+    the measured copy bandwidth."""
+    import torch
+    from paper_1812_03358_b300 import lt
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.float32, device="cuda")
+    l2buf = torch.ones(32 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 32 MB: L2-resident
+    h = stream.cuda_stream
+
+    def best(fn):
+        fn()
+        rate = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            work = fn()
+            b.record(stream)
+            b.synchronize()
+            rate = max(rate, work / (a.elapsed_time(b) * 1e-3))
+        return rate
+
+    smem = best(lambda: lt.lt_peak_smem_read(sink.data_ptr(), sms * 4, 4096, h)) / 1e9
+    l2 = best(lambda: lt.lt_peak_l2_read(l2buf.data_ptr(), l2buf.numel() // 4, sink.data_ptr(), sms * 8, 256, h)) / 1e9
+    fp32 = best(lambda: lt.lt_peak_fp32_fma(sink.data_ptr(), sms * 8, 32768, h)) / 1e12
+    hbm, src = hbm_peak()
+    return {"smem_GBps": smem, "l2_GBps": l2, "fp32_TFLOPs": fp32, "hbm_GBps": hbm,
+            "hbm_source": src + " (MEASURED_PEAKS.json copy bandwidth)" if src == "measured" else src,
+            "how": "library microbenchmarks: conflict-free 16 B shared loads (32 KiB per CTA, 4 CTAs/SM), "
+                   "L1-bypassing 16 B loads over a 32 MB buffer, 8 independent FMA chains per thread; "
+                   "best of 5 CUDA-event-timed launches"}
+
+
+def level_roofline(ms, dram_b, l2_b, smem_b, flops, peaks):
+    """Time bound of every level for one kernel launch (algorithmic bytes or
+    flops / that level's measured peak), the level that binds, and the
+    memory roofline fraction = the largest memory-level bound / the measured
+    time."""
+    t = {"dram": dram_b / (peaks["hbm_GBps"] * 1e9), "l2": l2_b / (peaks["l2_GBps"] * 1e9),
+         "smem": smem_b / (peaks["smem_GBps"] * 1e9), "fp32": flops / (peaks["fp32_TFLOPs"] * 1e12)}
+    mem = max(("dram", "l2", "smem"), key=lambda k: t[k])
+    return {"ms": ms, "bytes": {"dram": dram_b, "l2": l2_b, "smem": smem_b}, "flops": flops,
+            "bound_us": {k: v * 1e6 for k, v in t.items()}, "binding": max(t, key=t.get),
+            "memory_level": mem, "memory_frac": t[mem] / (ms * 1e-3), "fp32_frac": t["fp32"] / (ms * 1e-3)}
 
 
 def shear_passes(flush, stream, reps=20):
@@ -396,20 +498,36 @@ def run_ours(args):
             b.record(stream)
         torch.cuda.synchronize()
         stage_ms[name] = sum(a.elapsed_time(b) for a, b in ev) / reps
-    nnz = {"beam_forward (stage 1, slices->array)": stats["stage1_nnz"],
-           "stage2_forward (array->detector)": stats["stage2_nnz"],
-           "stage2_adjoint (detector->array)": stats["stage2_nnz"],
-           "beam_adjoint (stage 1^T, array->voxels)": stats["stage1_nnz"]}
+    # --- per-level rooflines of every stage (algorithmic bytes and flops) ---
+    peaks = measure_peaks(stream)
+    N, Na, K, M = vol.n, cam.arr_ns * cam.arr_nt, stats["n_cells"], cam.m
+    b1, b2 = stats["stage1_nnz"], stats["stage2_nnz"]
+    tile_b = 4 * stats["stage1_tile_voxels"] + 4 * K * Na
+    work = {   # (dram, l2, smem bytes, flops) per launch
+        "beam_forward (stage 1, slices->array)": (4 * (N + K * Na + Na), tile_b, 4 * b1, 2 * b1),
+        "stage2_forward (array->detector)": (4 * (K * Na + M + Na), 4 * (K * Na + M + Na), 4 * b2, 2 * b2),
+        "stage2_adjoint (detector->array)": (4 * (M + K * Na + 2 * Na), 4 * (M + K * Na + 2 * Na), 4 * b2, 2 * b2),
+        "beam_adjoint (stage 1^T, array->voxels)": (4 * (K * Na + N), tile_b, 4 * b1, 2 * b1),
+    }
+    levels = {name: level_roofline(stage_ms[name], *work[name], peaks) for name in stage_ms}
     dom = max(stage_ms, key=stage_ms.get)
-    achieved = 2.0 * nnz[dom] / (stage_ms[dom] * 1e-3) / 1e12
     kname = {"beam_forward (stage 1, slices->array)": "beam_forward_batched",
              "stage2_forward (array->detector)": "stage2_lenslet_forward",
              "stage2_adjoint (detector->array)": "stage2_lenslet_adjoint",
              "beam_adjoint (stage 1^T, array->voxels)": "beam_adjoint_batched"}[dom]
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for(kname),
-                "work": "2 flop (one FMA) per nonzero (pixel, cell, voxel) entry evaluated",
-                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts and max clock)"}
+    lv = levels[dom]
+    mem = lv["memory_level"]
+    peak = {"dram": peaks["hbm_GBps"], "l2": peaks["l2_GBps"], "smem": peaks["smem_GBps"]}[mem]
+    achieved = lv["bytes"][mem] / (stage_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": {"dram": "hbm"}.get(mem, mem), "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(kname),
+                "work": {"dram": "compulsory: every input read once, every output written once",
+                         "l2": "per 32 x 32 target tile, cell and slice the voxel rectangle its footprints "
+                               "touch, plus the array plane once",
+                         "smem": "4 B of operand per nonzero (pixel, cell, voxel) entry",
+                         "fp32": "one FMA per nonzero entry"}[mem],
+                "peak_source": "measured by the library's microbenchmark in this run (of measured)",
+                "binding_level": lv["binding"], "fp32_frac": lv["fp32_frac"]}
 
     # --- a2: the rotation passes of a yawed camera (HBM-bound streams) ---
     shear = shear_passes(flush, stream)
@@ -417,24 +535,31 @@ def run_ours(args):
     # --- time-to-residual, warm start vs plain (rank 0 only, outside the timed region) ---
     ttr = time_to_residual(plan, args.warm_samples) if rank == 0 and args.warm_samples > 0 else None
 
-    # --- end to end through the public API: pinned host y in, data fit out ---
+    # --- end to end through the public API: pinned host y in, volume and data fit out ---
     # Streaming use of the API: step i + 1's measurements are copied from
     # pinned host memory on a copy stream (double buffer) while step i
-    # iterates, and step i's data fit and gains come back asynchronously into
-    # pinned memory and are read on the host one step later.  Every step's
-    # copy in and result read happen inside the timed region.
+    # iterates; after step i the reconstructed volume is copied into a device
+    # staging buffer (lt_recon_get, no synchronisation) and from there into
+    # pinned host memory on the copy stream, and the data fit and gains come
+    # back asynchronously into pinned memory; the host reads step i's fit
+    # and volume one step later.  Every step's copy in and result reads
+    # happen inside the timed region.
     y_pin = torch.from_numpy(y_host.reshape(1, -1)).pin_memory()
     nfr, ncam = plan.frames, len(plan.cams)
     y_stage = [torch.empty_like(y_dev) for _ in range(2)]
+    x_stage = [torch.empty(nfr, plan.nvox, dtype=torch.float32, device="cuda") for _ in range(2)]
+    x_host = [torch.empty(nfr, plan.nvox, dtype=torch.float32).pin_memory() for _ in range(2)]
     res = [torch.empty(nfr * (ncam + 1), dtype=torch.float64).pin_memory() for _ in range(2)]
     copy_stream = torch.cuda.Stream()
     comp = torch.cuda.current_stream()
     h2d_done = [torch.cuda.Event() for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
     step_done = [torch.cuda.Event() for _ in range(2)]
+    x_staged = [torch.cuda.Event() for _ in range(2)]
+    x_home = [torch.cuda.Event() for _ in range(2)]
 
     def e2e_run(n):
-        fits = []
+        fits, vol_sums = [], []
         with torch.cuda.stream(copy_stream):
             y_stage[0].copy_(y_pin, non_blocking=True)
             h2d_done[0].record(copy_stream)
@@ -449,30 +574,44 @@ def run_ours(args):
                     y_stage[nxt].copy_(y_pin, non_blocking=True)
                     h2d_done[nxt].record(copy_stream)
             rec.iterate(1)
+            if i >= 2:
+                comp.wait_event(x_home[cur])               # step i - 2's volume has left x_stage[cur]
+            rec.copy_x(x_stage[cur])
+            x_staged[cur].record(comp)
             rec.get_async(res[cur])
             step_done[cur].record(comp)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(x_staged[cur])
+                x_host[cur].copy_(x_stage[cur], non_blocking=True)
+                x_home[cur].record(copy_stream)
             if i >= 1:
-                step_done[nxt].synchronize()               # step i - 1's result is on the host
+                step_done[nxt].synchronize()               # step i - 1's results are on the host
+                x_home[nxt].synchronize()
                 fits.append(float(res[nxt][0]))
+                vol_sums.append(float(x_host[nxt][0, :: 4096].sum()))
         step_done[(n - 1) % 2].synchronize()
+        x_home[(n - 1) % 2].synchronize()
         fits.append(float(res[(n - 1) % 2][0]))
-        return fits
+        vol_sums.append(float(x_host[(n - 1) % 2][0, :: 4096].sum()))
+        return fits, vol_sums
 
     e2e_run(3)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     e0 = time.perf_counter()
-    fits = e2e_run(args.e2e_steps)
+    fits, vol_sums = e2e_run(args.e2e_steps)
     torch.cuda.synchronize()
     te = time.perf_counter() - e0
-    assert len(fits) == args.e2e_steps and all(np.isfinite(fits))
+    assert len(fits) == args.e2e_steps and all(np.isfinite(fits)) and all(np.isfinite(vol_sums))
     e2e = {"value": job_rate(samples_step, args.e2e_steps, world, max_over_ranks(te, "cuda")), "unit": UNIT,
-           "h2d_bytes_per_step": int(y_pin.numel() * 4), "d2h_bytes_per_step": int(8 * nfr * (ncam + 1)),
+           "h2d_bytes_per_step": int(y_pin.numel() * 4),
+           "d2h_bytes_per_step": int(8 * nfr * (ncam + 1) + 4 * nfr * plan.nvox),
            "steps": args.e2e_steps,
            "path": "pinned host y -> device copy (copy stream, double buffered, overlapping the previous step), "
-                   "lt_recon_set_data, lt_recon_iterate(1), lt_recon_get_async(data fit, gains) into pinned "
-                   "memory, read on the host one step later"}
+                   "lt_recon_set_data, lt_recon_iterate(1), lt_recon_get(x) into a device staging buffer, "
+                   "volume -> pinned host memory on the copy stream, lt_recon_get_async(data fit, gains) into "
+                   "pinned memory; both read on the host one step later"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -493,6 +632,8 @@ def run_ours(args):
                        "forward_variant": tuned, "autotune_ms": tune_ms},
             "stages_ms": stage_ms,
             "roofline": roofline,
+            "peaks": peaks,
+            "levels": levels,
             "shear_passes": shear,
             "time_to_residual": ttr,
             "cpu_baseline": cpu,

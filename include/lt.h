@@ -157,7 +157,12 @@ LT_API lt_status lt_adjoint_camera(lt_plan* plan, int32_t cam, const float* y_ca
  * plan's buffer, and the call allocates and frees nothing.
  *   - frames x cells x array pixels must be <= 4,194,304 floats, else
  *     LT_EINVAL with a message; non-plenoptic cameras give LT_EINVAL.
- *   - Every GPU that loads the library reserves the array until exit.
+ *     Rotated cameras are served (their rotated view goes to the scratch
+ *     the plan allocated when it was created).
+ *   - Every GPU that uses the array holds it until exit.  With CUDA's lazy
+ *     module loading (the default since CUDA 12.2) the array is reserved
+ *     by the first call on each device, which may also synchronise; later
+ *     calls reserve nothing.
  *   - All calls share the array and it keeps the last call's contents; every
  *     element a call reads is first written by that call, but calls that
  *     overlap in time on the GPU (any plan, any stream) race on it.
@@ -233,6 +238,10 @@ typedef struct {
   int64_t hit_samples;      /* stage-1 samples whose footprint meets the volume */
   int64_t stage1_nnz;       /* nonzero (pixel, cell, voxel) entries of stage 1 */
   int64_t stage2_nnz;       /* nonzero (pixel, cell, array pixel) entries      */
+  int64_t stage1_tile_voxels; /* sum over 32 x 32 target-pixel tiles, cells and
+                             * slices of the voxels the tile's footprints
+                             * touch: what a tiled stage 1 must bring on chip
+                             * once per (tile, cell, slice)                   */
 } lt_camera_stats;
 
 LT_API lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_camera_stats* out);

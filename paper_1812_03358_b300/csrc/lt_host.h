@@ -91,6 +91,10 @@ lt_status camera_forward(lt_plan* p, int cam, const float* x, float* y, long lon
                          cudaStream_t st, SubsetSel sel = SubsetSel{});
 lt_status camera_adjoint(lt_plan* p, int cam, const float* y, long long y_fs, float* x,
                          int accumulate, cudaStream_t st, SubsetSel sel = SubsetSel{});
+// Slice -> plane beam integration of camera c (through its rotated view when
+// it is rotated, in the plan's scratch) into fa [F][..] with frame stride fa_fs.
+lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, long long fa_fs,
+                         cudaStream_t st, SubsetSel sel = SubsetSel{});
 
 
 }  // namespace lt

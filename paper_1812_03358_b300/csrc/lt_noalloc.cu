@@ -19,8 +19,11 @@
 //     different plans on one device) race on it;
 //   * the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture.
-#include <algorithm>
+//     before any stream capture.  Under CUDA's lazy module loading (the
+//     default since CUDA 12.2) that lookup is also what loads this file's
+//     module on the device, so the 16 MiB are reserved, and the call may
+//     synchronise, at that first call rather than when the library loads;
+//     later calls reserve nothing.
 #include <mutex>
 
 #include "lt.h"
@@ -66,8 +69,6 @@ extern "C" lt_status lt_forward_camera_noalloc(lt_plan* plan, int32_t cam, const
   lt::CameraPlan& c = plan->cams[cam];
   if (c.desc.kind != LT_CAM_PLENOPTIC)
     return lt::set_error(LT_EINVAL, "camera %d is not plenoptic (the allocation-free path stages the array plane)", cam);
-  if (c.rotated)
-    return lt::set_error(LT_EUNSUPPORTED, "camera %d is rotated; the allocation-free path takes aligned cameras only", cam);
   const long long need = (long long)plan->frames * c.K * c.Na;
   if (need > kNoAllocScratchFloats)
     return lt::set_error(LT_EINVAL,
@@ -79,31 +80,10 @@ extern "C" lt_status lt_forward_camera_noalloc(lt_plan* plan, int32_t cam, const
   if (s != LT_OK) return s;
   const long long fa_fs = (long long)c.K * c.Na;
   cudaStream_t st = (cudaStream_t)stream;
-  lt::BeamBatch b{};
-  b.n_cams = 1;
-  b.frames = plan->frames;
-  b.cam[0].x = x;
-  b.cam[0].out = fa;
-  b.cam[0].prm = c.d_slice;
-  b.cam[0].mask = c.d_mask;
-  b.cam[0].srange = c.d_srange;
-  b.cam[0].trange = c.d_trange;
-  b.cam[0].x_fs = c.nvox_c;
-  b.cam[0].out_fs = fa_fs;
-  b.cam[0].nx = c.vol_c.nx;
-  b.cam[0].ny = c.vol_c.ny;
-  b.cam[0].nz = c.vol_c.nz;
-  b.cam[0].ns = c.desc.arr_ns;
-  b.cam[0].nt = c.desc.arr_nt;
-  b.cam[0].K = c.K;
-  b.cam[0].per_cell = 1;
-  b.cam[0].tiles_s = c.tiles_s;
-  b.cam[0].tiles_t = c.tiles_t;
-  const int wclass = lt::window_class(std::max(c.wmax_s, c.wmax_t));
-  const int ctas = plan->sms * lt::beam_forward_occupancy(wclass, plan->fwd_variant);
-  cudaError_t e = lt::launch_beam_forward_batched(b, c.d_items, c.n_items, plan->d_counter, wclass,
-                                                  plan->fwd_variant, ctas, st);
-  if (e != cudaSuccess) return lt::cuda_error(e, "allocation-free stage 1");
-  e = lt::launch_stage2_forward(fa, y_cam, c.s2, plan->frames, fa_fs, c.M, c.d_zbuf, st);
+  // the same stage-one call as lt_forward_camera (rotated cameras through the
+  // plan's own rotation scratch), with the static array as its output
+  s = lt::stage1_forward(plan, c, x, fa, fa_fs, st);
+  if (s != LT_OK) return s;
+  cudaError_t e = lt::launch_stage2_forward(fa, y_cam, c.s2, plan->frames, fa_fs, c.M, c.d_zbuf, st);
   return e == cudaSuccess ? LT_OK : lt::cuda_error(e, "allocation-free stage 2");
 }

@@ -8,6 +8,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #define _USE_MATH_DEFINES
 #include <cmath>
@@ -967,10 +968,16 @@ extern "C" lt_status lt_rotate_volume_adjoint(lt_plan* plan, int32_t cam, const 
 // For target pixels [i0, i1] of a footprint, the number of source cells in
 // [0, n_src) each footprint overlaps (open interval (xi - Q, xi + Q)),
 // summed (nnz) and the number of pixels with at least one (hits).
+// With `tile` > 0, *span also receives the sum over consecutive blocks of
+// `tile` target pixels of the number of source cells the block's footprints
+// touch together.
 static void count_cells(const lt::Footprint& f, long long i0, long long i1, long long c_lo,
-                        long long c_hi, long long* nnz, long long* hits) {
+                        long long c_hi, long long* nnz, long long* hits, int tile = 0,
+                        long long* span = nullptr) {
   *nnz = 0;
   *hits = 0;
+  if (span) *span = 0;
+  long long blo = LLONG_MAX, bhi = LLONG_MIN;
   for (long long i = i0; i <= i1; ++i) {
     const double xi = f.C0 + f.C1 * (double)i;
     long long jl = (long long)std::floor(xi - f.Q - 0.5) + 1;
@@ -980,6 +987,13 @@ static void count_cells(const lt::Footprint& f, long long i0, long long i1, long
     if (jh >= jl) {
       *nnz += jh - jl + 1;
       *hits += 1;
+      blo = std::min(blo, jl);
+      bhi = std::max(bhi, jh);
+    }
+    if (span && (i == i1 || (i - i0 + 1) % tile == 0)) {
+      if (bhi >= blo) *span += bhi - blo + 1;
+      blo = LLONG_MAX;
+      bhi = LLONG_MIN;
     }
   }
 }
@@ -1007,11 +1021,12 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
                 d.basis, &fs);
       footprint(L, P, c.cells[k].tk, c.cells[k].d0t, centre(0, tnt, tpt), tpt, centre(0, v.ny, v.dy), v.dy,
                 d.basis, &ft);
-      long long ns_, hs, nt_, ht;
-      count_cells(fs, 0, tns - 1, 0, v.nx - 1, &ns_, &hs);
-      count_cells(ft, 0, tnt - 1, 0, v.ny - 1, &nt_, &ht);
+      long long ns_, hs, nt_, ht, span_s, span_t;
+      count_cells(fs, 0, tns - 1, 0, v.nx - 1, &ns_, &hs, kBeamTileS, &span_s);
+      count_cells(ft, 0, tnt - 1, 0, v.ny - 1, &nt_, &ht, kBeamTileT, &span_t);
       st.stage1_nnz += ns_ * nt_;
       st.hit_samples += hs * ht;
+      st.stage1_tile_voxels += span_s * span_t;
     }
   if (plen) {
     st.stage2_samples = (int64_t)d.det_ns * d.det_nt * c.K;
@@ -1132,7 +1147,7 @@ static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* 
 }
 
 lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, long long fa_fs,
-                         cudaStream_t st, SubsetSel sel = SubsetSel{}) {
+                         cudaStream_t st, SubsetSel sel) {
   const float* xc = nullptr;
   lt_status s = to_camera_grid(p, c, x, &xc, st);
   if (s != LT_OK) return s;

@@ -46,7 +46,7 @@ class lt_recon_params(ctypes.Structure):
 class lt_camera_stats(ctypes.Structure):
     _fields_ = [("n_cells", c_int64), ("stage1_samples", c_int64), ("stage2_samples", c_int64),
                 ("ray_samples", c_int64), ("hit_samples", c_int64), ("stage1_nnz", c_int64),
-                ("stage2_nnz", c_int64)]
+                ("stage2_nnz", c_int64), ("stage1_tile_voxels", c_int64)]
 
 
 class LtError(RuntimeError):
@@ -95,6 +95,9 @@ _SIGS = {
     "lt_plan_set_forward_variant": (c_int32, [c_void_p, c_int32]),
     "lt_test_fail_allocation_after": (None, [c_int32]),
     "lt_last_error": (c_char_p, []),
+    "lt_peak_smem_read": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
+    "lt_peak_l2_read": (c_int32, [c_void_p, c_int64, c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
+    "lt_peak_fp32_fma": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
 }
 
 
@@ -281,6 +284,12 @@ def lt_recon_get(rec, x_ptr: int, n_frames: int, n_cams: int, stream: int = 0):
     return np.array(gains).reshape(n_frames, n_cams), np.array(fit)
 
 
+def lt_recon_get_x(rec, x_ptr: int, stream: int = 0) -> None:
+    """Enqueues a device-to-device copy of x into x_ptr (lt_recon_get with
+    NULL gains and data fit: no synchronisation)."""
+    _check(lib().lt_recon_get(rec, x_ptr, None, None, stream))
+
+
 def lt_recon_get_async(rec, host_ptr: int, stream: int = 0) -> None:
     """Enqueues the data fit [F] and gains [F][n_cams] into the (page-locked)
     host buffer at host_ptr; valid once the stream has passed this point."""
@@ -308,6 +317,29 @@ def lt_recon_set_state(rec, state: bytes) -> None:
 
 def lt_recon_destroy(rec) -> None:
     _check(lib().lt_recon_destroy(rec))
+
+
+def lt_peak_smem_read(sink_ptr: int, ctas: int, reps: int, stream: int = 0) -> float:
+    """Launches the shared-memory read microbenchmark (include/lt_peaks.h);
+    returns the bytes it reads."""
+    b = c_double()
+    _check(lib().lt_peak_smem_read(sink_ptr, ctas, reps, stream, byref(b)))
+    return b.value
+
+
+def lt_peak_l2_read(buf_ptr: int, n16: int, sink_ptr: int, ctas: int, reps: int, stream: int = 0) -> float:
+    """Launches the L2 read microbenchmark over buf[n16] 16-byte words;
+    returns the bytes it reads."""
+    b = c_double()
+    _check(lib().lt_peak_l2_read(buf_ptr, n16, sink_ptr, ctas, reps, stream, byref(b)))
+    return b.value
+
+
+def lt_peak_fp32_fma(sink_ptr: int, ctas: int, reps: int, stream: int = 0) -> float:
+    """Launches the FP32 FMA microbenchmark; returns its flops."""
+    f = c_double()
+    _check(lib().lt_peak_fp32_fma(sink_ptr, ctas, reps, stream, byref(f)))
+    return f.value
 
 
 # ---------------------------------------------------------------------------
@@ -497,6 +529,11 @@ class Recon:
         gains, fit = lt_recon_get(self.handle, _dev_f32(x, self.plan.frames * self.plan.nvox, "x"),
                                   self.plan.frames, len(self.plan.cams), _stream())
         return x, gains, fit
+
+    def copy_x(self, x):
+        """Enqueues a copy of the current x into the device tensor x on the
+        current stream (no synchronisation)."""
+        lt_recon_get_x(self.handle, _dev_f32(x, self.plan.frames * self.plan.nvox, "x"), _stream())
 
     def get_async(self, out):
         """Enqueues [data_fit[F], gains[F][n_cams]] into `out`, a page-locked
