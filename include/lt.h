@@ -203,8 +203,13 @@ LT_API lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, const f
                                       void* stream);
 
 /* Autotuner (no counterpart in the paper): times each forward kernel variant
- * (slices per weight batch x warp groups per work item) on this plan's own
- * cameras and frames and keeps the fastest for later calls.  Allocates and
+ * on this plan's own cameras and frames and keeps the fastest for later
+ * calls.  Variants 0-4 are the direct beam kernel's shapes (slices per
+ * weight batch x warp groups per work item); variant 5, the default of a new
+ * plan, is the brick-staged kernel (volume bricks brought to shared memory
+ * by TMA, one warp per slice), which cameras whose bricks the planner could
+ * not size, or whose source rows are not a multiple of 4 floats, replace by
+ * variant 2.  Allocates and
  * frees temporary device buffers and synchronises the stream; call it once
  * after lt_plan_create and before capturing graphs.  times_ms (host array of
  * lt_autotune_variants() entries, may be NULL) receives each variant's best
@@ -215,6 +220,14 @@ LT_API lt_status lt_plan_autotune(lt_plan* plan, void* stream, double* times_ms,
  * every variant computes the same operator (summation order differs).  A new
  * plan uses variant 2 (two slices per weight batch, two warp groups). */
 LT_API lt_status lt_plan_set_forward_variant(lt_plan* plan, int32_t variant);
+
+/* Device-side status word of the projector kernels (no counterpart in the
+ * paper): bit 0 = a brick or band of the brick-staged forward did not fit
+ * its planned size (that slice's weights were zeroed; the planner sizes
+ * them so that this does not happen), bit 1 = a bounded wait for a TMA load
+ * gave up (the kernel stopped taking work).  0 after correct runs.  Reading
+ * synchronises the device; clear != 0 resets the word. */
+LT_API lt_status lt_projector_status(int32_t* flags, int32_t clear);
 
 /* Fault injection for tests (no counterpart in the paper): the n-th device
  * allocation the library makes from now on fails as if the device were out
@@ -242,6 +255,9 @@ typedef struct {
                              * slices of the voxels the tile's footprints
                              * touch: what a tiled stage 1 must bring on chip
                              * once per (tile, cell, slice)                   */
+  int64_t forward_brick;    /* floats per brick of the brick-staged forward
+                             * (box columns x rows), 0 if the camera takes the
+                             * direct kernel                                   */
 } lt_camera_stats;
 
 LT_API lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_camera_stats* out);

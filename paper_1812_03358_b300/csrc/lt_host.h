@@ -60,6 +60,9 @@ struct CameraPlan {
   int2* d_srange = nullptr;        // [K][tiles_s] slice interval per forward tile column
   int2* d_trange = nullptr;        // [K][tiles_t] slice interval per forward tile row
   int wmax_s = 0, wmax_t = 0, wimax_s = 0, wimax_t = 0;
+  // brick-staged (TMA) forward: brick box and band rows sized at plan time
+  // for every (cell, slice, tile); tma_nb = 0 when the camera does not fit it
+  int tma_bx = 0, tma_by = 0, tma_nb = 0;
   // plenoptic
   int64_t Na = 0;
   LensletParam* d_lens = nullptr;
@@ -116,7 +119,7 @@ struct lt_plan {
   int class_begin[4] = {0, 0, 0, 0};
   int class_count[4] = {0, 0, 0, 0};
   int* d_counter = nullptr;        // persistent-launch work counter
-  int fwd_variant = 2;             // forward kernel variant (autotuned; {2 slices, 2 groups} until then)
+  int fwd_variant = lt::kTmaVariant;   // forward kernel variant (autotuned; the brick-staged kernel until then)
 };
 
 namespace lt {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace lt {
@@ -145,13 +146,29 @@ struct BeamBatch {
   int32_t frames;
 };
 
+// TMA view of each camera's source volume for the brick-staged forward
+// (lt_beam_tma.cu): a 3-D tensor map over [F * nz][ny][nx] float32 and the
+// brick box (bx columns, a multiple of 4, by rows) the planner sized for the
+// camera's 32 x 32 tiles.
+struct TmaBatch {
+  CUtensorMap map[kMaxBatchCams];
+  int32_t bx[kMaxBatchCams];
+  int32_t by[kMaxBatchCams];
+};
+
 // Forward kernel variants chosen by the autotuner: slices per weight batch
 // and warp groups (128 threads each) splitting a tile's slices.
-constexpr int kForwardVariants = 5;
+// Variants 0-4 are the direct kernel's shapes; variant kTmaVariant is the
+// brick-staged TMA kernel (cameras that do not fit it run
+// kDefaultDirectVariant).
+constexpr int kDirectVariants = 5;
+constexpr int kTmaVariant = 5;
+constexpr int kForwardVariants = 6;
+constexpr int kDefaultDirectVariant = 2;
 struct ForwardVariant {
   int32_t sb, groups;
 };
-constexpr ForwardVariant kForwardVariantTable[kForwardVariants] = {{4, 2}, {4, 1}, {2, 2}, {2, 4}, {8, 1}};
+constexpr ForwardVariant kForwardVariantTable[kDirectVariants] = {{4, 2}, {4, 1}, {2, 2}, {2, 4}, {8, 1}};
 
 // ---- kernel launchers (lt_kernels.cu) -------------------------------------
 
@@ -164,6 +181,21 @@ cudaError_t launch_beam_forward_batched(const BeamBatch& b, const int4* items, i
 // CTAs per SM of a forward variant (for the persistent grid).
 int beam_forward_occupancy(int wclass, int variant);
 int window_class(int w);
+
+// Brick-staged forward (lt_beam_tma.cu): W = forward window class (2..4),
+// nb = band rows per group of four pixel rows (4 or 8), bxy = floats per
+// brick stage (tma_forward_bxy of the largest bx * by in the launch).
+bool tma_forward_available();
+bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, int bx, int by);
+int tma_forward_bxy(int max_brick);
+size_t tma_forward_smem(int w, int nb, int bxy);
+int tma_forward_occupancy(int w, int nb, int bxy);
+cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
+                                    int* counter, int w, int nb, int bxy, int ctas, cudaStream_t st);
+// Device status word of the projector kernels: bit 0 a brick or band that
+// did not fit (its weights were zeroed), bit 1 a TMA wait that gave up.
+// Read (and optionally cleared) synchronously.
+cudaError_t projector_status(int* flags, bool clear);
 
 // Batched gather adjoint over cameras that share one grid (cam[0]'s dims):
 // x[F][nz][ny][nx] (= or +=) sum over cameras and cells.

@@ -271,6 +271,51 @@ static void free_camera(CameraPlan& c) {
   c = CameraPlan();
 }
 
+// Brick box and band rows of the brick-staged forward for camera c.  For a
+// tile of 32 target pixels along an axis the first taps floor(xi(i) - Q + 1/2)
+// range over [lo, hi] (evaluated at the tile's two ends, widened by 1e-3 so
+// that float evaluation on the device stays inside); the kernel's brick
+// starts at the tile's smallest first tap (columns rounded down to a
+// multiple of 4) and must hold W taps past the largest, and a group of four
+// pixel rows must fit its taps in NB band rows.  Cameras whose window class
+// exceeds 4 or whose bricks exceed 1024 floats keep the direct kernels.
+static void plan_bricks(CameraPlan& c, const std::vector<Footprint>& fps, const std::vector<Footprint>& fpt,
+                        int tiles_s, int tiles_t) {
+  c.tma_bx = c.tma_by = c.tma_nb = 0;
+  const int W = window_class(std::max(c.wmax_s, c.wmax_t));
+  if (W > 4) return;
+  auto tap_range = [](const Footprint& f, int i0, int i1, long long& lo, long long& hi) {
+    const double a = f.C0 + f.C1 * i0 - (double)f.a.Q + 0.5, b = f.C0 + f.C1 * i1 - (double)f.a.Q + 0.5;
+    lo = (long long)std::floor(std::min(a, b) - 1e-3);
+    hi = (long long)std::floor(std::max(a, b) + 1e-3);
+  };
+  long long need_bx = 0, span_t = 0, need_nb = 0;
+  for (size_t q = 0; q < fps.size(); ++q) {
+    for (int ts = 0; ts < tiles_s; ++ts) {
+      long long lo, hi;
+      tap_range(fps[q], ts * kBeamTileS, ts * kBeamTileS + kBeamTileS - 1, lo, hi);
+      need_bx = std::max(need_bx, hi + W - 1 - (lo & ~3LL) + 1);
+    }
+    for (int tt = 0; tt < tiles_t; ++tt) {
+      long long lo, hi;
+      tap_range(fpt[q], tt * kBeamTileT, tt * kBeamTileT + kBeamTileT - 1, lo, hi);
+      span_t = std::max(span_t, hi - lo);
+      for (int g = 0; g < kBeamTileT / 4; ++g) {
+        const int r0 = tt * kBeamTileT + 4 * g;
+        tap_range(fpt[q], r0, r0 + 3, lo, hi);
+        need_nb = std::max(need_nb, hi - lo + W);
+      }
+    }
+  }
+  const int nb = need_nb <= 4 ? 4 : need_nb <= 8 ? 8 : 0;
+  if (nb == 0) return;
+  const long long bx = (need_bx + 3) / 4 * 4, by = span_t + nb;
+  if (bx > 256 || by > 256 || bx * by > 1024) return;
+  c.tma_bx = (int)bx;
+  c.tma_by = (int)by;
+  c.tma_nb = nb;
+}
+
 // Per (cell, slice) parameters of the slice -> image-plane transport.
 static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_img, int tgt_ns,
                              int tgt_nt, double tgt_ps, double tgt_pt, double extra_scale, int idx) {
@@ -295,12 +340,14 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
       }
     }
   };
+  std::vector<Footprint> fps((size_t)c.K * v.nz), fpt((size_t)c.K * v.nz);
   for (int k = 0; k < c.K; ++k) {
     for (int n = 0; n < v.nz; ++n) {
       const double dist = d.d_obj + centre(n, v.nz, v.dz);
       Row P, L;
       slice_rows(dist, d_img, d.f_main, &P, &L);
-      Footprint fs, ft;
+      Footprint& fs = fps[(size_t)k * v.nz + n];
+      Footprint& ft = fpt[(size_t)k * v.nz + n];
       if (!footprint(L, P, c.cells[k].sk, c.cells[k].d0s, centre(0, tgt_ns, tgt_ps), tgt_ps,
                      centre(0, v.nx, v.dx), v.dx, d.basis, &fs) ||
           !footprint(L, P, c.cells[k].tk, c.cells[k].d0t, centre(0, tgt_nt, tgt_pt), tgt_pt,
@@ -331,6 +378,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
     return set_error(LT_EUNSUPPORTED,
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
+  plan_bricks(c, fps, fpt, tiles_s, tiles_t);
   for (auto& r : srange)
     if (r.y < 0) r = make_int2(0, 0);
   for (auto& r : trange)
@@ -1054,6 +1102,7 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
         }
   }
   st.ray_samples = st.stage1_samples + st.stage2_samples;
+  st.forward_brick = (int64_t)c.tma_bx * c.tma_by;
   *out = st;
   return LT_OK;
 }
@@ -1119,10 +1168,44 @@ static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const 
   return b;
 }
 
-static lt_status run_forward(lt_plan* p, const BeamBatch& b, const int4* items, int n_items, int wclass,
-                             cudaStream_t st) {
-  const int ctas = p->sms * beam_forward_occupancy(wclass, p->fwd_variant);
-  cudaError_t e = launch_beam_forward_batched(b, items, n_items, p->d_counter, wclass, p->fwd_variant, ctas, st);
+// One persistent forward launch over `items` of the cameras in b (cps[i] is
+// the plan of b.cam[i]).  The brick-staged TMA kernel runs when the plan's
+// variant selects it and every camera of the launch fits it (planner-sized
+// bricks, a 16-byte aligned source whose rows are a multiple of 4 floats);
+// otherwise the direct kernel of the variant (variant kTmaVariant falls back
+// to the default direct variant).
+static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* cps, const int4* items,
+                             int n_items, int wclass, cudaStream_t st) {
+  if (p->fwd_variant == kTmaVariant && wclass <= 4 && tma_forward_available()) {
+    static_assert(sizeof(TmaBatch) % 64 == 0, "tensor maps stay 64-byte aligned");
+    TmaBatch tb;
+    std::memset(&tb, 0, sizeof(tb));
+    bool ok = true;
+    int nb = 4, brick = 0;
+    for (int i = 0; i < b.n_cams && ok; ++i) {
+      const CameraPlan& c = *cps[i];
+      const BeamCam& bc = b.cam[i];
+      ok = c.tma_nb > 0 && bc.x_fs == (long long)bc.nx * bc.ny * bc.nz &&
+           tma_encode_volume(&tb.map[i], bc.x, bc.nx, bc.ny, bc.nz * b.frames, c.tma_bx, c.tma_by);
+      if (!ok) break;
+      tb.bx[i] = c.tma_bx;
+      tb.by[i] = c.tma_by;
+      nb = std::max(nb, c.tma_nb);
+      brick = std::max(brick, c.tma_bx * c.tma_by);
+    }
+    if (ok) {
+      const int bxy = tma_forward_bxy(brick);
+      const int occ = tma_forward_occupancy(wclass, nb, bxy);
+      if (occ > 0) {
+        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, p->d_counter, wclass, nb, bxy, p->sms * occ,
+                                                st);
+        return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward (TMA bricks)");
+      }
+    }
+  }
+  const int variant = p->fwd_variant == kTmaVariant ? kDefaultDirectVariant : p->fwd_variant;
+  const int ctas = p->sms * beam_forward_occupancy(wclass, variant);
+  cudaError_t e = launch_beam_forward_batched(b, items, n_items, p->d_counter, wclass, variant, ctas, st);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward");
 }
 
@@ -1155,7 +1238,8 @@ lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, l
   b.n_cams = 1;
   b.frames = p->frames;
   b.cam[0] = beam_cam(c, xc, fa, nullptr, fa_fs, sel);
-  return run_forward(p, b, c.d_items, c.n_items, cam_class(c), st);
+  CameraPlan* cps[1] = {&c};
+  return run_forward(p, b, cps, c.d_items, c.n_items, cam_class(c), st);
 }
 
 lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
@@ -1205,8 +1289,10 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, Su
   BeamBatch b{};
   b.n_cams = nc;
   b.frames = p->frames;
+  CameraPlan* cps[kMaxBatchCams];
   for (int i = 0; i < nc; ++i) {
     CameraPlan& c = p->cams[i];
+    cps[i] = &c;
     const float* xc = nullptr;
     lt_status s = to_camera_grid(p, c, x, &xc, st);
     if (s != LT_OK) return s;
@@ -1215,7 +1301,7 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, Su
   }
   for (int g = 0; g < 4; ++g) {   // one persistent launch per window class present
     if (p->class_count[g] == 0) continue;
-    lt_status s = run_forward(p, b, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g], st);
+    lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g], st);
     if (s != LT_OK) return s;
   }
   for (int i = 0; i < nc; ++i) {
@@ -1385,6 +1471,16 @@ extern "C" lt_status lt_plenoptic_stage2_adjoint(lt_plan* plan, int32_t cam, con
 extern "C" const char* lt_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int32_t lt_autotune_variants(void) { return kForwardVariants; }
+
+extern "C" lt_status lt_projector_status(int32_t* flags, int32_t clear) {
+  clear_error();
+  if (!flags) return set_error(LT_EINVAL, "flags is NULL");
+  int f = 0;
+  cudaError_t e = projector_status(&f, clear != 0);
+  if (e != cudaSuccess) return cuda_error(e, "projector status");
+  *flags = f;
+  return LT_OK;
+}
 
 extern "C" lt_status lt_plan_autotune(lt_plan* plan, void* stream, double* times_ms, int32_t* chosen) {
   clear_error();

@@ -46,7 +46,8 @@ class lt_recon_params(ctypes.Structure):
 class lt_camera_stats(ctypes.Structure):
     _fields_ = [("n_cells", c_int64), ("stage1_samples", c_int64), ("stage2_samples", c_int64),
                 ("ray_samples", c_int64), ("hit_samples", c_int64), ("stage1_nnz", c_int64),
-                ("stage2_nnz", c_int64), ("stage1_tile_voxels", c_int64)]
+                ("stage2_nnz", c_int64), ("stage1_tile_voxels", c_int64),
+                ("forward_brick", c_int64)]
 
 
 class LtError(RuntimeError):
@@ -93,6 +94,7 @@ _SIGS = {
     "lt_autotune_variants": (c_int32, []),
     "lt_plan_autotune": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
     "lt_plan_set_forward_variant": (c_int32, [c_void_p, c_int32]),
+    "lt_projector_status": (c_int32, [POINTER(c_int32), c_int32]),
     "lt_test_fail_allocation_after": (None, [c_int32]),
     "lt_last_error": (c_char_p, []),
     "lt_peak_smem_read": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
@@ -244,6 +246,14 @@ def lt_test_fail_allocation_after(n: int) -> None:
     """Fault injection for tests: the n-th device allocation from now on fails
     (LT_ENOMEM); n <= 0 turns it off."""
     lib().lt_test_fail_allocation_after(int(n))
+
+
+def lt_projector_status(clear: bool = False) -> int:
+    """Device status word of the projector kernels (0 after correct runs);
+    synchronises the device."""
+    f = c_int32()
+    _check(lib().lt_projector_status(byref(f), int(clear)))
+    return f.value
 
 
 def lt_plan_set_forward_variant(plan, variant: int) -> None:
