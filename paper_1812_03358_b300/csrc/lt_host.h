@@ -25,6 +25,8 @@ struct NvtxRange {
 // Kernel window limits (must match lt_kernels.cu).
 constexpr int kMaxForwardWindow = 8;
 constexpr int kFwdClasses[4] = {8, 4, 3, 2};   // the forward kernels' window classes (window_class)
+// forward item groups: (window class kFwdClasses[g / 2], brick-staged if g is even)
+constexpr int kForwardGroups = 8;
 constexpr int kMaxAdjointWindow = 32;
 constexpr int kMaxLensletPixels = 16;
 
@@ -111,13 +113,14 @@ struct lt_plan {
   int sms = 148;
   std::vector<lt::CameraPlan> cams;
   // every camera's forward items, grouped by the camera's forward window
-  // class (kFwdClasses order), longest first within a group: the batched
-  // forward makes one persistent launch per class present, so that a camera
-  // runs the same kernel instantiation as in a launch of its own
+  // class (kFwdClasses order) and by whether the brick-staged kernel serves
+  // it, longest first within a group: the batched forward makes one
+  // persistent launch per group present, so that a camera runs the same
+  // kernel instantiation as in a launch of its own
   int4* d_items = nullptr;
   int n_items = 0;
-  int class_begin[4] = {0, 0, 0, 0};
-  int class_count[4] = {0, 0, 0, 0};
+  int class_begin[lt::kForwardGroups] = {};
+  int class_count[lt::kForwardGroups] = {};
   int* d_counter = nullptr;        // persistent-launch work counter
   int fwd_variant = lt::kTmaVariant;   // forward kernel variant (autotuned; the brick-staged kernel until then)
 };

@@ -278,12 +278,13 @@ static void free_camera(CameraPlan& c) {
 // starts at the tile's smallest first tap (columns rounded down to a
 // multiple of 4) and must hold W taps past the largest, and a group of four
 // pixel rows must fit its taps in NB band rows.  Cameras whose window class
-// exceeds 4 or whose bricks exceed 1024 floats keep the direct kernels.
-static void plan_bricks(CameraPlan& c, const std::vector<Footprint>& fps, const std::vector<Footprint>& fpt,
-                        int tiles_s, int tiles_t) {
+// exceeds 4, whose bricks exceed 1024 floats or whose grid rows are not a
+// multiple of 4 floats keep the direct kernels.
+static void plan_bricks(CameraPlan& c, int grid_nx, const std::vector<Footprint>& fps,
+                        const std::vector<Footprint>& fpt, int tiles_s, int tiles_t) {
   c.tma_bx = c.tma_by = c.tma_nb = 0;
   const int W = window_class(std::max(c.wmax_s, c.wmax_t));
-  if (W > 4) return;
+  if (W > 4 || grid_nx % 4 != 0) return;   // a TMA row stride is a multiple of 16 bytes
   auto tap_range = [](const Footprint& f, int i0, int i1, long long& lo, long long& hi) {
     const double a = f.C0 + f.C1 * i0 - (double)f.a.Q + 0.5, b = f.C0 + f.C1 * i1 - (double)f.a.Q + 0.5;
     lo = (long long)std::floor(std::min(a, b) - 1e-3);
@@ -378,7 +379,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
     return set_error(LT_EUNSUPPORTED,
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
-  plan_bricks(c, fps, fpt, tiles_s, tiles_t);
+  plan_bricks(c, v.nx, fps, fpt, tiles_s, tiles_t);
   for (auto& r : srange)
     if (r.y < 0) r = make_int2(0, 0);
   for (auto& r : trange)
@@ -914,10 +915,10 @@ extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_d
   p->m_total = off;
   {
     std::vector<int4> all;
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < kForwardGroups; ++g) {
       const size_t start = all.size();
       for (auto& c : p->cams)
-        if (window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g])
+        if (window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g / 2] && (c.tma_nb > 0) == (g % 2 == 0))
           all.insert(all.end(), c.h_items.begin(), c.h_items.end());
       std::stable_sort(all.begin() + start, all.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
       p->class_begin[g] = (int)start;
@@ -1169,14 +1170,14 @@ static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const 
 }
 
 // One persistent forward launch over `items` of the cameras in b (cps[i] is
-// the plan of b.cam[i]).  The brick-staged TMA kernel runs when the plan's
-// variant selects it and every camera of the launch fits it (planner-sized
-// bricks, a 16-byte aligned source whose rows are a multiple of 4 floats);
-// otherwise the direct kernel of the variant (variant kTmaVariant falls back
-// to the default direct variant).
+// the plan of b.cam[i]).  The brick-staged TMA kernel runs when the items
+// belong to cameras the planner sized bricks for (`staged`), the plan's
+// variant selects it and every source is 16-byte aligned; otherwise the
+// direct kernel of the variant (variant kTmaVariant falls back to the
+// default direct variant).
 static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* cps, const int4* items,
-                             int n_items, int wclass, cudaStream_t st) {
-  if (p->fwd_variant == kTmaVariant && wclass <= 4 && tma_forward_available()) {
+                             int n_items, int wclass, bool staged, cudaStream_t st) {
+  if (staged && p->fwd_variant == kTmaVariant && wclass <= 4 && tma_forward_available()) {
     static_assert(sizeof(TmaBatch) % 64 == 0, "tensor maps stay 64-byte aligned");
     TmaBatch tb;
     std::memset(&tb, 0, sizeof(tb));
@@ -1185,7 +1186,9 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
     for (int i = 0; i < b.n_cams && ok; ++i) {
       const CameraPlan& c = *cps[i];
       const BeamCam& bc = b.cam[i];
-      ok = c.tma_nb > 0 && bc.x_fs == (long long)bc.nx * bc.ny * bc.nz &&
+      if (c.tma_nb == 0 || window_class(std::max(c.wmax_s, c.wmax_t)) != wclass)
+        continue;   // none of its items are in this launch
+      ok = bc.x_fs == (long long)bc.nx * bc.ny * bc.nz &&
            tma_encode_volume(&tb.map[i], bc.x, bc.nx, bc.ny, bc.nz * b.frames, c.tma_bx, c.tma_by);
       if (!ok) break;
       tb.bx[i] = c.tma_bx;
@@ -1239,7 +1242,7 @@ lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, l
   b.frames = p->frames;
   b.cam[0] = beam_cam(c, xc, fa, nullptr, fa_fs, sel);
   CameraPlan* cps[1] = {&c};
-  return run_forward(p, b, cps, c.d_items, c.n_items, cam_class(c), st);
+  return run_forward(p, b, cps, c.d_items, c.n_items, cam_class(c), c.tma_nb > 0, st);
 }
 
 lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
@@ -1299,9 +1302,10 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, Su
     const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
     b.cam[i] = beam_cam(c, xc, plen ? c.d_fa : y + c.offset, nullptr, plen ? (long long)c.K * c.Na : p->m_total, sel);
   }
-  for (int g = 0; g < 4; ++g) {   // one persistent launch per window class present
+  for (int g = 0; g < kForwardGroups; ++g) {   // one persistent launch per window class and kernel present
     if (p->class_count[g] == 0) continue;
-    lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g], st);
+    lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g / 2],
+                              g % 2 == 0, st);
     if (s != LT_OK) return s;
   }
   for (int i = 0; i < nc; ++i) {

@@ -81,7 +81,7 @@ def test_brick_forward_matches_oracle(case):
 
 def test_brick_forward_frames_are_independent():
     vol = I.Volume(20, 16, 12, 4.0, 4.0, 5.0)
-    cams = [I.table_single_lens(36, 0.2), I.table_single_lens(28, 0.3, ks=2, kt=2)]
+    cams = [I.table_single_lens(36, 0.09), I.table_single_lens(28, 0.11, ks=2, kt=2)]
     frames = 3
     xs = np.stack([I.gaussian_blobs(vol, seed=1200 + f).ravel() for f in range(frames)])
     plan = lt.Plan(vol, cams, frames)
