@@ -25,8 +25,10 @@ struct NvtxRange {
 // Kernel window limits (must match lt_kernels.cu).
 constexpr int kMaxForwardWindow = 8;
 constexpr int kFwdClasses[4] = {8, 4, 3, 2};   // the forward kernels' window classes (window_class)
-// forward item groups: (window class kFwdClasses[g / 2], brick-staged if g is even)
-constexpr int kForwardGroups = 8;
+// forward item groups g: window class kFwdClasses[g / 3]; g % 3 = 0, 1: the
+// brick-staged kernel with 4 or 8 band rows, 2: the direct kernel
+constexpr int kForwardGroups = 12;
+inline int forward_group_kind(int tma_nb) { return tma_nb == 4 ? 0 : tma_nb == 8 ? 1 : 2; }
 constexpr int kMaxAdjointWindow = 32;
 constexpr int kMaxLensletPixels = 16;
 

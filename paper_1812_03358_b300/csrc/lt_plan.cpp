@@ -918,7 +918,7 @@ extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_d
     for (int g = 0; g < kForwardGroups; ++g) {
       const size_t start = all.size();
       for (auto& c : p->cams)
-        if (window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g / 2] && (c.tma_nb > 0) == (g % 2 == 0))
+        if (window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g / 3] && forward_group_kind(c.tma_nb) == g % 3)
           all.insert(all.end(), c.h_items.begin(), c.h_items.end());
       std::stable_sort(all.begin() + start, all.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
       p->class_begin[g] = (int)start;
@@ -1171,29 +1171,29 @@ static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const 
 
 // One persistent forward launch over `items` of the cameras in b (cps[i] is
 // the plan of b.cam[i]).  The brick-staged TMA kernel runs when the items
-// belong to cameras the planner sized bricks for (`staged`), the plan's
-// variant selects it and every source is 16-byte aligned; otherwise the
-// direct kernel of the variant (variant kTmaVariant falls back to the
-// default direct variant).
+// belong to cameras the planner sized bricks of `staged_nb` band rows for
+// (0: none), the plan's variant selects it and every source is 16-byte
+// aligned; otherwise the direct kernel of the variant (variant kTmaVariant
+// falls back to the default direct variant).
 static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* cps, const int4* items,
-                             int n_items, int wclass, bool staged, cudaStream_t st) {
-  if (staged && p->fwd_variant == kTmaVariant && wclass <= 4 && tma_forward_available()) {
+                             int n_items, int wclass, int staged_nb, cudaStream_t st) {
+  if (staged_nb > 0 && p->fwd_variant == kTmaVariant && wclass <= 4 && tma_forward_available()) {
     static_assert(sizeof(TmaBatch) % 64 == 0, "tensor maps stay 64-byte aligned");
     TmaBatch tb;
     std::memset(&tb, 0, sizeof(tb));
     bool ok = true;
-    int nb = 4, brick = 0;
+    const int nb = staged_nb;
+    int brick = 0;
     for (int i = 0; i < b.n_cams && ok; ++i) {
       const CameraPlan& c = *cps[i];
       const BeamCam& bc = b.cam[i];
-      if (c.tma_nb == 0 || window_class(std::max(c.wmax_s, c.wmax_t)) != wclass)
+      if (c.tma_nb != staged_nb || window_class(std::max(c.wmax_s, c.wmax_t)) != wclass)
         continue;   // none of its items are in this launch
       ok = bc.x_fs == (long long)bc.nx * bc.ny * bc.nz &&
            tma_encode_volume(&tb.map[i], bc.x, bc.nx, bc.ny, bc.nz * b.frames, c.tma_bx, c.tma_by);
       if (!ok) break;
       tb.bx[i] = c.tma_bx;
       tb.by[i] = c.tma_by;
-      nb = std::max(nb, c.tma_nb);
       brick = std::max(brick, c.tma_bx * c.tma_by);
     }
     if (ok) {
@@ -1242,7 +1242,7 @@ lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, l
   b.frames = p->frames;
   b.cam[0] = beam_cam(c, xc, fa, nullptr, fa_fs, sel);
   CameraPlan* cps[1] = {&c};
-  return run_forward(p, b, cps, c.d_items, c.n_items, cam_class(c), c.tma_nb > 0, st);
+  return run_forward(p, b, cps, c.d_items, c.n_items, cam_class(c), c.tma_nb, st);
 }
 
 lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
@@ -1304,8 +1304,8 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, Su
   }
   for (int g = 0; g < kForwardGroups; ++g) {   // one persistent launch per window class and kernel present
     if (p->class_count[g] == 0) continue;
-    lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g / 2],
-                              g % 2 == 0, st);
+    lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g / 3],
+                              g % 3 == 2 ? 0 : 4 << (g % 3), st);
     if (s != LT_OK) return s;
   }
   for (int i = 0; i < nc; ++i) {
