@@ -10,18 +10,21 @@
 //   * a persistent CTA of four warps takes a work item (camera, cell or all
 //     cells, tile, frame) from a counter; its warps take every fourth
 //     (cell, slice) pair of the item;
-//   * three slices ahead of the one it contracts, a warp evaluates the
-//     slice's footprint weights (lane = pixel column for s, lane = pixel
-//     row for t) into a weight stage in shared memory, derives the brick's
-//     origin from them, and lane 0 issues one cp.async.bulk.tensor load of
-//     the brick into a ring of four stages guarded by mbarriers, so the
-//     volume reaches shared memory through TMA while the warp computes;
-//   * the contraction keeps the tile column of every lane in registers: a
-//     window of NB s-contracted voxel rows T[k][col] (each computed from the
-//     brick once, as the window rolls down the tile) and 32 accumulators,
-//     one per pixel row; pixel rows come in groups of four whose taps fall
-//     in one band of NB voxel rows, so a group is 4 x NB FMAs against
-//     broadcast band weights with no data-dependent register index;
+//   * the footprint weights of every (cell, slice, tile column) and
+//     (cell, slice, tile row) are evaluated once per plan into tables
+//     (lane = pixel column for s, lane = pixel row for t), together with the
+//     brick's origin;
+//   * three slices ahead of the one it contracts, lane 0 of a warp fills a
+//     stage of a four-stage ring: one cp.async.bulk.tensor load of the
+//     brick and two bulk copies of the slice's table entries, all completing
+//     one mbarrier, so volume and weights reach shared memory through TMA
+//     while the warp computes;
+//   * the contraction keeps the tile column of every lane: the s-contracted
+//     voxel rows T[k][col] of the brick (each computed once, into the lane's
+//     own column of shared memory) and 32 accumulators in registers, one per
+//     pixel row; pixel rows come in groups of four whose taps fall in one
+//     band of NB voxel rows, so a group is 4 x NB FMAs against broadcast
+//     band weights, with every load address known up front;
 //   * at the end of an item the four warps' partial tiles are summed in a
 //     fixed order and written with the mask M (Sec. II-D).
 //
@@ -30,9 +33,10 @@
 // exact transposes up to float32 summation order.  Outside the volume the
 // TMA load fills zeros, which contribute exact zeros.  Every mbarrier wait is
 // bounded: a wait that gives up records bit 1 of the projector status word
-// and the CTA stops taking work; a weight stage that would not fit its brick
-// or band (the planner sizes both so that this cannot happen) is zeroed and
-// records bit 0.
+// and the CTA stops taking work.  A table entry whose taps would not fit
+// its brick or band is zeroed and reported when the tables are built (the
+// planner sizes both so that this cannot happen, and a plan whose tables
+// report it keeps the direct kernel).
 #include <cuda.h>
 
 #include <algorithm>
@@ -50,18 +54,28 @@ __device__ int g_projector_status;
 
 constexpr int TM_WARPS = 4;
 constexpr int TM_STAGES = 4;
-constexpr int TM_AHEAD = TM_STAGES - 1;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long kTmaWaitPolls = 1LL << 22;   // polls (with back-off) before a wait gives up
 
-template <int W, int NB>
-struct __align__(16) WeightStage {
-  float wl[32][NB];   // band weights of each pixel row (t-weight x slice scale at its taps), NB per row
-  float ws[W][32];    // s-weights of each pixel column
-  int sx[32];         // first tap column of each pixel column, relative to the brick
-  int base[8];        // first band row of each group of four pixel rows, relative to the brick
-  int up;             // 1: band rows ascend with the row group, 0: they descend
-  int pad[3];
+// Weights of one (cell, slice) for a column of 32-pixel tiles (s) and a row
+// of 32-pixel tiles (t), built once per plan (beam_weight_tables) in exactly
+// the layout the kernel stages in shared memory, so that a bulk copy brings
+// them next to the brick.
+template <int W>
+struct __align__(16) SPart {
+  float ws[W][32];   // s-weights of each pixel column
+  int sx[32];        // first tap column of each pixel column, relative to the brick
+  int x0;            // brick's first column (a multiple of 4)
+  int ok;            // 0: the taps did not fit the planned brick (weights zeroed)
+  int pad[2];
+};
+template <int NB>
+struct __align__(16) TPart {
+  float wl[32][NB];  // band weights of each pixel row (t-weight x slice scale at its taps)
+  int base[8];       // first band row of each group of four pixel rows, relative to the brick
+  int y0;            // brick's first row
+  int ok;
+  int pad[2];
 };
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -115,30 +129,35 @@ __device__ __forceinline__ int taps(const AxisParam& ap, int i, float (&w)[W]) {
   return jc + mlo;
 }
 
-// Weights of slice n, cell k for the tile (is0, it0) into stage S; returns the
-// brick origin (x0, y0).  Lane = pixel column for s, pixel row for t.
-template <int W, int NB>
-__device__ __forceinline__ void stage_weights(const SliceParam* p, int is0, int it0, int lane, int bx, int by,
-                                              WeightStage<W, NB>& S, int& x0, int& y0) {
-  float ws[W], tw[W];
-  const int sx0 = taps<W>(p->s, is0 + lane, ws);
-  const int ty0 = taps<W>(p->t, it0 + lane, tw);
+// s-part of one (cell, slice, tile column): lane = pixel column.
+template <int W>
+__device__ __forceinline__ void build_spart(const SliceParam& p, int is0, int lane, int bx, SPart<W>& S, int* bad) {
+  float ws[W];
+  const int sx0 = taps<W>(p.s, is0 + lane, ws);
   const int smin = __reduce_min_sync(FULL, sx0), smax = __reduce_max_sync(FULL, sx0);
-  const int tmin = __reduce_min_sync(FULL, ty0), tmax = __reduce_max_sync(FULL, ty0);
-  x0 = smin & ~3;   // floor to a multiple of 4 columns: a TMA box starts on 16 bytes
-  y0 = tmin;
-  int gb = min(ty0, __shfl_xor_sync(FULL, ty0, 1));
-  gb = min(gb, __shfl_xor_sync(FULL, gb, 2));   // band start of this lane's group of four rows
-  const bool up = __shfl_sync(FULL, ty0, 31) >= __shfl_sync(FULL, ty0, 0);
-  const int g_next = __shfl_down_sync(FULL, gb, 4);
-  bool ok = smax + W - 1 - x0 < bx && tmax - tmin + NB <= by && ty0 + W - 1 - gb < NB;
-  if (lane < 28) ok = ok && (up ? g_next >= gb : g_next <= gb);
-  ok = __all_sync(FULL, ok);
-  if (!ok && lane == 0) atomicOr(&g_projector_status, 1);
-  const float scale = p->scale;
+  const int x0 = smin & ~3;   // floor to a multiple of 4 columns: a TMA box starts on 16 bytes
+  const bool ok = smax + W - 1 - x0 < bx;
 #pragma unroll
   for (int a = 0; a < W; ++a) S.ws[a][lane] = ok ? ws[a] : 0.0f;
   S.sx[lane] = ok ? sx0 - x0 : 0;
+  if (lane == 0) {
+    S.x0 = x0;
+    S.ok = ok;
+    S.pad[0] = S.pad[1] = 0;
+    if (!ok) atomicOr(bad, 1);
+  }
+}
+
+// t-part of one (cell, slice, tile row): lane = pixel row.  A group of four
+// rows keeps its taps in NB band rows from its smallest first tap.
+template <int W, int NB>
+__device__ __forceinline__ void build_tpart(const SliceParam& p, int it0, int lane, int by, TPart<NB>& T, int* bad) {
+  float tw[W];
+  const int ty0 = taps<W>(p.t, it0 + lane, tw);
+  const int tmin = __reduce_min_sync(FULL, ty0), tmax = __reduce_max_sync(FULL, ty0);
+  int gb = min(ty0, __shfl_xor_sync(FULL, ty0, 1));
+  gb = min(gb, __shfl_xor_sync(FULL, gb, 2));
+  const bool ok = __all_sync(FULL, tmax - tmin + NB <= by && ty0 + W - 1 - gb < NB);
   float wl[NB];
 #pragma unroll
   for (int m = 0; m < NB; ++m) wl[m] = 0.0f;
@@ -146,20 +165,39 @@ __device__ __forceinline__ void stage_weights(const SliceParam* p, int is0, int 
 #pragma unroll
     for (int b = 0; b < W; ++b) {
       const int m = ty0 + b - gb;
-      const float v = __fmul_rn(tw[b], scale);
+      const float v = __fmul_rn(tw[b], p.scale);
 #pragma unroll
       for (int mm = 0; mm < NB; ++mm)
         if (m == mm) wl[mm] = v;
     }
   }
 #pragma unroll
-  for (int q = 0; q < NB / 4; ++q)
-    reinterpret_cast<float4*>(S.wl[lane])[q] = make_float4(wl[4 * q], wl[4 * q + 1], wl[4 * q + 2], wl[4 * q + 3]);
-  if ((lane & 3) == 0) S.base[lane >> 2] = ok ? gb - y0 : 0;
-  if (lane == 0) S.up = ok ? (int)up : 1;
+  for (int m = 0; m < NB; ++m) T.wl[lane][m] = wl[m];
+  if ((lane & 3) == 0) T.base[lane >> 2] = ok ? gb - tmin : 0;
+  if (lane == 0) {
+    T.y0 = tmin;
+    T.ok = ok;
+    T.pad[0] = T.pad[1] = 0;
+    if (!ok) atomicOr(bad, 1);
+  }
 }
 
-// s-contraction of brick row `row` for this lane's pixel column.
+// Plan-time tables: block (tile, slice, cell); warp 0 the s-part of tile
+// column blockIdx.x, warp 1 the t-part of tile row blockIdx.x.
+template <int W, int NB>
+__global__ void __launch_bounds__(64) beam_weight_tables(const SliceParam* __restrict__ prm, int nz, int tiles_s,
+                                                         int tiles_t, int bx, int by, SPart<W>* __restrict__ stab,
+                                                         TPart<NB>* __restrict__ ttab, int* __restrict__ bad) {
+  const int tile = blockIdx.x, n = blockIdx.y, k = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const SliceParam p = prm[(long long)k * nz + n];
+  if (warp == 0 && tile < tiles_s)
+    build_spart<W>(p, tile * kBeamTileS, lane, bx, stab[((long long)k * nz + n) * tiles_s + tile], bad);
+  if (warp == 1 && tile < tiles_t)
+    build_tpart<W, NB>(p, tile * kBeamTileT, lane, by, ttab[((long long)k * nz + n) * tiles_t + tile], bad);
+}
+
+// s-contraction of brick row `off` (a row start) for this lane's pixel column.
 template <int W>
 __device__ __forceinline__ float trow(const float* bc, int off, const float (&ws)[W]) {
   float u = 0.0f;
@@ -168,28 +206,29 @@ __device__ __forceinline__ float trow(const float* bc, int off, const float (&ws
   return u;
 }
 
-// t-contraction of one slice into the 32 row accumulators, rolling a window
-// of NB s-contracted brick rows down (UP) or up the tile's row groups.
-template <int W, int NB, bool UP>
-__device__ __forceinline__ void band_rows(const WeightStage<W, NB>& S, const float* bc, int bx, const float (&ws)[W],
-                                          float (&acc)[32]) {
-  float R[NB];
-  int cur = S.base[UP ? 0 : 7];
+// One slice of one tile column (this lane's): the s-contraction of every
+// brick row into the lane's own column of Tw, then each group of four pixel
+// rows against its NB band rows.  Every load's address is known before any
+// of them is needed, so the loads of all groups overlap.
+template <int W, int NB>
+__device__ __forceinline__ void contract_slice(const SPart<W>& S, const TPart<NB>& T, const float* brick, int bx,
+                                               int by, float* Tw, int lane, float (&acc)[32]) {
+  float ws[W];
 #pragma unroll
-  for (int m = 0; m < NB; ++m) R[m] = trow<W>(bc, (cur + m) * bx, ws);
+  for (int a = 0; a < W; ++a) ws[a] = S.ws[a][lane];
+  const float* bc = brick + S.sx[lane];
+#pragma unroll 2
+  for (int k = 0; k < by; ++k) Tw[k * 32] = trow<W>(bc, k * bx, ws);
 #pragma unroll
-  for (int gg = 0; gg < 8; ++gg) {
-    const int g = UP ? gg : 7 - gg;
-    for (int d = S.base[g] - cur; d > 0; --d) {   // uniform across the warp
+  for (int g = 0; g < 8; ++g) {
+    const int b = T.base[g];
+    float R[NB];
 #pragma unroll
-      for (int m = 0; m < NB - 1; ++m) R[m] = R[m + 1];
-      ++cur;
-      R[NB - 1] = trow<W>(bc, (cur + NB - 1) * bx, ws);
-    }
+    for (int m = 0; m < NB; ++m) R[m] = Tw[(b + m) * 32];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int row = 4 * g + i;
-      const float4* wr = reinterpret_cast<const float4*>(S.wl[row]);
+      const float4* wr = reinterpret_cast<const float4*>(T.wl[row]);
       float a = acc[row];
 #pragma unroll
       for (int q = 0; q < NB / 4; ++q) {
@@ -241,39 +280,54 @@ __device__ __forceinline__ void cursor_advance(const BeamCam& C, int ts, int tt,
   }
 }
 
-// Weights of the cursor's (cell, slice) pair into the warp's next stage, and
-// the TMA load of its brick (lane 0); then the cursor moves to the warp's
-// next pair.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Shared-memory layout of the brick-staged forward, per warp: TM_STAGES
+// stages of {brick, SPart, TPart}, the lane columns of the s-contracted rows
+// (Tw, by_max x 32 floats), and one mbarrier per stage.
 template <int W, int NB>
-__device__ __forceinline__ void issue_pair(const BeamCam& C, const CUtensorMap* map, PairCursor& pf, int is0,
-                                           int it0, int lane, int warp, int bx, int by, uint32_t brick_bytes,
-                                           int frame, float* bricks, WeightStage<W, NB>* wst, uint64_t* bars,
-                                           int bxy, uint32_t& n_issued, int& inflight) {
-  const int st = (int)(n_issued % TM_STAGES);
-  int x0, y0;
-  stage_weights<W, NB>(C.prm + (long long)pf.k * C.nz + pf.n, is0, it0, lane, bx, by, wst[warp * TM_STAGES + st],
-                       x0, y0);
-  if (lane == 0) {
-    const uint32_t bar = smem_addr(bars + warp * TM_STAGES + st);
-    fence_proxy_async();   // this stage's earlier generic reads precede the new async-proxy write
-    mbar_expect_tx(bar, brick_bytes);
-    tma_load_3d(smem_addr(bricks + (size_t)(warp * TM_STAGES + st) * bxy), map, x0, y0, frame * C.nz + pf.n, bar);
+struct StageLayout {
+  static constexpr size_t parts = sizeof(SPart<W>) + sizeof(TPart<NB>);
+  // 128-byte multiples: every stage's brick starts where a TMA box may land
+  __host__ __device__ static size_t stage_bytes(int bxy) {
+    return ((size_t)bxy * sizeof(float) + parts + 127) / 128 * 128;
   }
-  ++n_issued;
-  ++inflight;
-  cursor_advance(C, is0 / kBeamTileS, it0 / kBeamTileT, pf, TM_WARPS);
+  static size_t bytes(int bxy, int tsz) {
+    return (size_t)TM_WARPS * (TM_STAGES * stage_bytes(bxy) + (size_t)tsz * sizeof(float)) +
+           (size_t)TM_WARPS * TM_STAGES * sizeof(uint64_t);
+  }
+};
+
+// Stage fill for the cursor's (cell, slice) pair by lane 0: the pair's table
+// parts and its brick, all completing one mbarrier.  (x0, y0), the brick's
+// origin, were read from the tables one pair earlier (px, py).
+template <int W, int NB>
+__device__ __forceinline__ void issue_stage(const CUtensorMap* map, const SPart<W>* S, const TPart<NB>* T,
+                                            unsigned char* stage, int bxy, uint32_t brick_bytes, uint32_t bar,
+                                            int x0, int y0, int z) {
+  fence_proxy_async();   // this stage's earlier generic reads precede the new async-proxy writes
+  mbar_expect_tx(bar, brick_bytes + (uint32_t)(sizeof(SPart<W>) + sizeof(TPart<NB>)));
+  const uint32_t dst = smem_addr(stage);
+  tma_load_3d(dst, map, x0, y0, z, bar);
+  bulk_copy(dst + (uint32_t)bxy * 4, S, (uint32_t)sizeof(SPart<W>), bar);
+  bulk_copy(dst + (uint32_t)bxy * 4 + (uint32_t)sizeof(SPart<W>), T, (uint32_t)sizeof(TPart<NB>), bar);
 }
 
 template <int W, int NB>
 __global__ void __launch_bounds__(TM_WARPS * 32)
 beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ TmaBatch TB,
-                 const int4* __restrict__ items, int n_items, int* __restrict__ counter, int bxy) {
-  using WS = WeightStage<W, NB>;
+                 const int4* __restrict__ items, int n_items, int* __restrict__ counter, int bxy, int tsz) {
+  using L = StageLayout<W, NB>;
   extern __shared__ __align__(128) unsigned char dsm[];
-  float* bricks = reinterpret_cast<float*>(dsm);                                   // [warp][stage][bxy]
-  WS* wst = reinterpret_cast<WS*>(dsm + (size_t)TM_WARPS * TM_STAGES * bxy * sizeof(float));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(wst + TM_WARPS * TM_STAGES);        // [warp][stage]
-  float(*red)[32][33] = reinterpret_cast<float(*)[32][33]>(dsm);                    // aliases the bricks
+  const size_t stage_bytes = L::stage_bytes(bxy);
+  unsigned char* stages = dsm;                                                       // [warp][stage]
+  float* tws = reinterpret_cast<float*>(dsm + (size_t)TM_WARPS * TM_STAGES * stage_bytes);   // [warp][tsz]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tws + (size_t)TM_WARPS * tsz);      // [warp][stage]
+  float(*red)[32][33] = reinterpret_cast<float(*)[32][33]>(dsm);                    // aliases the stages
   __shared__ int s_item;
   __shared__ int s_fail;
 
@@ -284,7 +338,9 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
 
-  uint32_t n_issued = 0, n_done = 0;   // this warp's brick loads (stage = count % S, phase = count / S)
+  unsigned char* my_stages = stages + (size_t)warp * TM_STAGES * stage_bytes;
+  float* Tw = tws + (size_t)warp * tsz + lane;
+  uint32_t n_issued = 0, n_done = 0;   // this warp's stage fills (stage = count % S, phase = count / S)
   bool failed = false;
   const long long total = (long long)n_items * B.frames;
 
@@ -297,6 +353,8 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
     const int frame = (int)(it % B.frames);
     const BeamCam& C = B.cam[item.x];
     const CUtensorMap* map = &TB.map[item.x];
+    const SPart<W>* stab = static_cast<const SPart<W>*>(TB.stab[item.x]);
+    const TPart<NB>* ttab = static_cast<const TPart<NB>*>(TB.ttab[item.x]);
     const int bx = TB.bx[item.x], by = TB.by[item.x];
     const uint32_t brick_bytes = (uint32_t)(bx * by * sizeof(float));
     const int tile_s = item.z % C.tiles_s;
@@ -314,22 +372,48 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
 #pragma unroll
     for (int r = 0; r < 32; ++r) acc[r] = 0.0f;
 
+    // this warp's pairs: every TM_WARPS-th (cell, slice) of the item
     PairCursor pf{k_begin, 0, 0, k_end, false};
     cursor_range(C, tile_s, tile_t, pf);
     cursor_advance(C, tile_s, tile_t, pf, warp);
+    // the cursor's table parts and brick origin (lane 0 reads the origin one
+    // pair before it issues the pair's stage fill)
+    const SPart<W>* sp = stab;
+    const TPart<NB>* tp = ttab;
+    int px = 0, py = 0;
+    if (pf.valid) {
+      const long long kn = (long long)pf.k * C.nz + pf.n;
+      sp = stab + kn * C.tiles_s + tile_s;
+      tp = ttab + kn * C.tiles_t + tile_t;
+      if (lane == 0) {
+        px = __ldg(&sp->x0);
+        py = __ldg(&tp->y0);
+      }
+    }
     int inflight = 0;
-
     if (!failed) {
-      for (int d = 0; d < TM_AHEAD && pf.valid; ++d)
-        issue_pair<W, NB>(C, map, pf, is0, it0, lane, warp, bx, by, brick_bytes, frame, bricks, wst, bars, bxy,
-                          n_issued, inflight);
-      while (inflight > 0) {
-        if (pf.valid)
-          issue_pair<W, NB>(C, map, pf, is0, it0, lane, warp, bx, by, brick_bytes, frame, bricks, wst, bars, bxy,
-                            n_issued, inflight);
+      for (;;) {
+        while (pf.valid && inflight < TM_STAGES) {
+          const int st = (int)(n_issued % TM_STAGES);
+          if (lane == 0)
+            issue_stage<W, NB>(map, sp, tp, my_stages + st * stage_bytes, bxy, brick_bytes,
+                               smem_addr(bars + warp * TM_STAGES + st), px, py, frame * C.nz + pf.n);
+          ++n_issued;
+          ++inflight;
+          cursor_advance(C, tile_s, tile_t, pf, TM_WARPS);
+          if (pf.valid) {
+            const long long kn = (long long)pf.k * C.nz + pf.n;
+            sp = stab + kn * C.tiles_s + tile_s;
+            tp = ttab + kn * C.tiles_t + tile_t;
+            if (lane == 0) {
+              px = __ldg(&sp->x0);
+              py = __ldg(&tp->y0);
+            }
+          }
+        }
+        if (inflight == 0) break;
         const int st = (int)(n_done % TM_STAGES);
-        const bool ready = mbar_wait_bounded(smem_addr(bars + warp * TM_STAGES + st), (n_done / TM_STAGES) & 1);
-        if (!ready) {
+        if (!mbar_wait_bounded(smem_addr(bars + warp * TM_STAGES + st), (n_done / TM_STAGES) & 1)) {
           failed = true;
           if (lane == 0) {
             atomicOr(&g_projector_status, 2);
@@ -337,15 +421,10 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
           }
           break;
         }
-        const WS& S = wst[warp * TM_STAGES + st];
-        float wsr[W];
-#pragma unroll
-        for (int a = 0; a < W; ++a) wsr[a] = S.ws[a][lane];
-        const float* bc = bricks + (size_t)(warp * TM_STAGES + st) * bxy + S.sx[lane];
-        if (S.up)
-          band_rows<W, NB, true>(S, bc, bx, wsr, acc);
-        else
-          band_rows<W, NB, false>(S, bc, bx, wsr, acc);
+        const unsigned char* stg = my_stages + st * stage_bytes;
+        contract_slice<W, NB>(*reinterpret_cast<const SPart<W>*>(stg + (size_t)bxy * 4),
+                              *reinterpret_cast<const TPart<NB>*>(stg + (size_t)bxy * 4 + sizeof(SPart<W>)),
+                              reinterpret_cast<const float*>(stg), bx, by, Tw, lane, acc);
         ++n_done;
         --inflight;
         __syncwarp();
@@ -382,7 +461,7 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
   }
 
   // a warp that gave up leaves nothing in flight behind it: wait (bounded)
-  // for the loads it issued and did not consume
+  // for the fills it issued and did not consume
   if (failed) {
     for (uint32_t q = n_done; q < n_issued; ++q)
       mbar_wait_bounded(smem_addr(bars + warp * TM_STAGES + (q % TM_STAGES)), (q / TM_STAGES) & 1);
@@ -409,9 +488,12 @@ const void* tma_select(int w, int nb) {
   }
 }
 
-size_t weight_stage_bytes(int w, int nb) {
-  if (nb <= 4) return w == 2 ? sizeof(WeightStage<2, 4>) : w == 3 ? sizeof(WeightStage<3, 4>) : sizeof(WeightStage<4, 4>);
-  return w == 2 ? sizeof(WeightStage<2, 8>) : w == 3 ? sizeof(WeightStage<3, 8>) : sizeof(WeightStage<4, 8>);
+size_t layout_bytes(int w, int nb, int bxy, int tsz) {
+  if (nb <= 4)
+    return w == 2 ? StageLayout<2, 4>::bytes(bxy, tsz) : w == 3 ? StageLayout<3, 4>::bytes(bxy, tsz)
+                                                                : StageLayout<4, 4>::bytes(bxy, tsz);
+  return w == 2 ? StageLayout<2, 8>::bytes(bxy, tsz) : w == 3 ? StageLayout<3, 8>::bytes(bxy, tsz)
+                                                              : StageLayout<4, 8>::bytes(bxy, tsz);
 }
 
 // cuTensorMapEncodeTiled from the driver, found once through the runtime.
@@ -460,22 +542,43 @@ bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t tma_forward_smem(int w, int nb, int bxy) {
-  return (size_t)TM_WARPS * TM_STAGES * ((size_t)bxy * sizeof(float) + weight_stage_bytes(w, nb)) +
-         (size_t)TM_WARPS * TM_STAGES * sizeof(uint64_t);
+size_t tma_table_bytes(int w, int nb, int K, int nz, int tiles_s, int tiles_t) {
+  const size_t sp = w == 2 ? sizeof(SPart<2>) : w == 3 ? sizeof(SPart<3>) : sizeof(SPart<4>);
+  const size_t tp = nb <= 4 ? sizeof(TPart<4>) : sizeof(TPart<8>);
+  return (size_t)K * nz * ((size_t)tiles_s * sp + (size_t)tiles_t * tp);
 }
 
-int tma_forward_bxy(int max_brick) {
-  // the reduction buffer of three warps' tiles aliases the bricks
-  const int red = (TM_WARPS - 1) * 32 * 33;
+cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int nb, int bx,
+                               int by, void* stab, void* ttab, int* bad, cudaStream_t st) {
+  const dim3 grid(std::max(tiles_s, tiles_t), nz, K);
+#define LT_TABLES(WW, NN)                                                                                    \
+  beam_weight_tables<WW, NN><<<grid, 64, 0, st>>>(prm, nz, tiles_s, tiles_t, bx, by,                           \
+                                                  static_cast<SPart<WW>*>(stab), static_cast<TPart<NN>*>(ttab), bad)
+  if (nb <= 4) {
+    if (w == 2) LT_TABLES(2, 4);
+    else if (w == 3) LT_TABLES(3, 4);
+    else LT_TABLES(4, 4);
+  } else {
+    if (w == 2) LT_TABLES(2, 8);
+    else if (w == 3) LT_TABLES(3, 8);
+    else LT_TABLES(4, 8);
+  }
+#undef LT_TABLES
+  return cudaGetLastError();
+}
+
+int tma_forward_bxy(int max_brick, int w, int nb) {
+  // the reduction buffer of three warps' tiles aliases the stages
+  const size_t red = (size_t)(TM_WARPS - 1) * 32 * 33 * sizeof(float);
   int bxy = (max_brick + 31) / 32 * 32;
-  while ((long long)TM_WARPS * TM_STAGES * bxy < red) bxy += 32;
+  const size_t parts = layout_bytes(w, nb, 0, 0) / TM_WARPS / TM_STAGES;   // stage bytes with bxy = 0 (+ bars)
+  while ((size_t)TM_WARPS * TM_STAGES * ((size_t)bxy * sizeof(float) + parts) < red) bxy += 32;
   return bxy;
 }
 
-int tma_forward_occupancy(int w, int nb, int bxy) {
+int tma_forward_occupancy(int w, int nb, int bxy, int tsz) {
   const void* fn = tma_select(w, nb);
-  const size_t smem = tma_forward_smem(w, nb, bxy);
+  const size_t smem = layout_bytes(w, nb, bxy, tsz);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb_ctas = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_ctas, fn, TM_WARPS * 32, smem) != cudaSuccess) return 0;
@@ -483,18 +586,18 @@ int tma_forward_occupancy(int w, int nb, int bxy) {
 }
 
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int* counter, int w, int nb, int bxy, int ctas, cudaStream_t st) {
+                                    int* counter, int w, int nb, int bxy, int tsz, int ctas, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (w < 2 || w > 4) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   const void* fn = tma_select(w, nb);
-  const size_t smem = tma_forward_smem(w, nb, bxy);
+  const size_t smem = layout_bytes(w, nb, bxy, tsz);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_items * b.frames;
   const int grid = (int)std::min<long long>(ctas, total);
-  void* args[] = {(void*)&b, (void*)&tb, (void*)&items, (void*)&n_items, (void*)&counter, (void*)&bxy};
+  void* args[] = {(void*)&b, (void*)&tb, (void*)&items, (void*)&n_items, (void*)&counter, (void*)&bxy, (void*)&tsz};
   return cudaLaunchKernel(fn, dim3(grid), dim3(TM_WARPS * 32), args, smem, st);
 }
 

@@ -67,6 +67,8 @@ struct CameraPlan {
   // brick-staged (TMA) forward: brick box and band rows sized at plan time
   // for every (cell, slice, tile); tma_nb = 0 when the camera does not fit it
   int tma_bx = 0, tma_by = 0, tma_nb = 0;
+  void* d_stab = nullptr;          // its footprint-weight tables (lt_beam_tma.cu layout)
+  void* d_ttab = nullptr;
   // plenoptic
   int64_t Na = 0;
   LensletParam* d_lens = nullptr;

@@ -147,11 +147,13 @@ struct BeamBatch {
 };
 
 // TMA view of each camera's source volume for the brick-staged forward
-// (lt_beam_tma.cu): a 3-D tensor map over [F * nz][ny][nx] float32 and the
+// (lt_beam_tma.cu): a 3-D tensor map over [F * nz][ny][nx] float32, the
 // brick box (bx columns, a multiple of 4, by rows) the planner sized for the
-// camera's 32 x 32 tiles.
+// camera's 32 x 32 tiles, and the camera's footprint-weight tables.
 struct TmaBatch {
   CUtensorMap map[kMaxBatchCams];
+  const void* stab[kMaxBatchCams];   // per-(cell, slice, tile column) s-weights (plan-built tables)
+  const void* ttab[kMaxBatchCams];   // per-(cell, slice, tile row) t band weights
   int32_t bx[kMaxBatchCams];
   int32_t by[kMaxBatchCams];
 };
@@ -185,13 +187,18 @@ int window_class(int w);
 // Brick-staged forward (lt_beam_tma.cu): W = forward window class (2..4),
 // nb = band rows per group of four pixel rows (4 or 8), bxy = floats per
 // brick stage (tma_forward_bxy of the largest bx * by in the launch).
+// tsz = floats of a warp's s-contracted rows (32 x the largest by).  Tables:
+// tma_table_bytes for one camera; launch_beam_tables fills them from the
+// camera's SliceParam table and sets *bad if a brick or band did not fit.
 bool tma_forward_available();
 bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, int bx, int by);
-int tma_forward_bxy(int max_brick);
-size_t tma_forward_smem(int w, int nb, int bxy);
-int tma_forward_occupancy(int w, int nb, int bxy);
+size_t tma_table_bytes(int w, int nb, int K, int nz, int tiles_s, int tiles_t);
+cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int nb, int bx,
+                               int by, void* stab, void* ttab, int* bad, cudaStream_t st);
+int tma_forward_bxy(int max_brick, int w, int nb);
+int tma_forward_occupancy(int w, int nb, int bxy, int tsz);
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int* counter, int w, int nb, int bxy, int ctas, cudaStream_t st);
+                                    int* counter, int w, int nb, int bxy, int tsz, int ctas, cudaStream_t st);
 // Device status word of the projector kernels: bit 0 a brick or band that
 // did not fit (its weights were zeroed), bit 1 a TMA wait that gave up.
 // Read (and optionally cleared) synchronously.

@@ -268,6 +268,8 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.d_cand_all_t);
   cudaFree(c.d_zbuf);
   cudaFree(c.d_fa);
+  cudaFree(c.d_stab);
+  cudaFree(c.d_ttab);
   c = CameraPlan();
 }
 
@@ -315,6 +317,48 @@ static void plan_bricks(CameraPlan& c, int grid_nx, const std::vector<Footprint>
   c.tma_bx = (int)bx;
   c.tma_by = (int)by;
   c.tma_nb = nb;
+}
+
+// Footprint-weight tables of the brick-staged forward (one entry per
+// (cell, slice, tile column) and (cell, slice, tile row)), built on the
+// device from the slice parameters.  A camera whose tables would exceed
+// kMaxTableBytes, or whose build reports a brick or band that does not fit,
+// keeps the direct kernel; only a failed allocation is an error.
+static lt_status plan_weight_tables(CameraPlan& c, int nz, int idx) {
+  constexpr size_t kMaxTableBytes = (size_t)512 << 20;
+  if (c.tma_nb == 0 || !tma_forward_available()) {
+    c.tma_nb = 0;
+    return LT_OK;
+  }
+  const int W = window_class(std::max(c.wmax_s, c.wmax_t));
+  const size_t bytes = tma_table_bytes(W, c.tma_nb, c.K, nz, c.tiles_s, c.tiles_t);
+  if (bytes > kMaxTableBytes) {
+    c.tma_nb = 0;
+    return LT_OK;
+  }
+  const size_t s_bytes = tma_table_bytes(W, c.tma_nb, c.K, nz, c.tiles_s, 0);
+  int* d_bad = nullptr;
+  if (device_alloc(&c.d_stab, s_bytes) != cudaSuccess ||
+      device_alloc(&c.d_ttab, bytes - s_bytes) != cudaSuccess ||
+      device_alloc((void**)&d_bad, sizeof(int)) != cudaSuccess) {
+    cudaFree(d_bad);
+    return set_error(LT_ENOMEM, "camera %d: cudaMalloc(forward weight tables, %zu bytes)", idx, bytes);
+  }
+  int bad = 0;
+  cudaError_t e = cudaMemset(d_bad, 0, sizeof(int));
+  if (e == cudaSuccess)
+    e = launch_beam_tables(c.d_slice, c.K, nz, c.tiles_s, c.tiles_t, W, c.tma_nb, c.tma_bx, c.tma_by, c.d_stab,
+                           c.d_ttab, d_bad, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_bad);
+  if (e != cudaSuccess) return cuda_error(e, "forward weight tables");
+  if (bad) {   // a brick or band the planner sized too small: the direct kernel serves this camera
+    cudaFree(c.d_stab);
+    cudaFree(c.d_ttab);
+    c.d_stab = c.d_ttab = nullptr;
+    c.tma_nb = 0;
+  }
+  return LT_OK;
 }
 
 // Per (cell, slice) parameters of the slice -> image-plane transport.
@@ -413,7 +457,9 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
   s = upload(srange, &c.d_srange, "tile slice ranges");
   if (s == LT_OK) s = upload(trange, &c.d_trange, "tile slice ranges");
   if (s != LT_OK) return s;
-  return upload(sp, &c.d_slice, "slice parameters");
+  s = upload(sp, &c.d_slice, "slice parameters");
+  if (s != LT_OK) return s;
+  return plan_weight_tables(c, v.nz, idx);
 }
 
 // Array -> detector stage of a plenoptic camera (Sec. II-D, II-F2).
@@ -1183,7 +1229,7 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
     std::memset(&tb, 0, sizeof(tb));
     bool ok = true;
     const int nb = staged_nb;
-    int brick = 0;
+    int brick = 0, tsz = 0;
     for (int i = 0; i < b.n_cams && ok; ++i) {
       const CameraPlan& c = *cps[i];
       const BeamCam& bc = b.cam[i];
@@ -1192,16 +1238,19 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       ok = bc.x_fs == (long long)bc.nx * bc.ny * bc.nz &&
            tma_encode_volume(&tb.map[i], bc.x, bc.nx, bc.ny, bc.nz * b.frames, c.tma_bx, c.tma_by);
       if (!ok) break;
+      tb.stab[i] = c.d_stab;
+      tb.ttab[i] = c.d_ttab;
       tb.bx[i] = c.tma_bx;
       tb.by[i] = c.tma_by;
       brick = std::max(brick, c.tma_bx * c.tma_by);
+      tsz = std::max(tsz, 32 * c.tma_by);
     }
     if (ok) {
-      const int bxy = tma_forward_bxy(brick);
-      const int occ = tma_forward_occupancy(wclass, nb, bxy);
+      const int bxy = tma_forward_bxy(brick, wclass, nb);
+      const int occ = tma_forward_occupancy(wclass, nb, bxy, tsz);
       if (occ > 0) {
-        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, p->d_counter, wclass, nb, bxy, p->sms * occ,
-                                                st);
+        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, p->d_counter, wclass, nb, bxy, tsz,
+                                                p->sms * occ, st);
         return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward (TMA bricks)");
       }
     }
