@@ -53,7 +53,8 @@ namespace {
 __device__ int g_projector_status;
 
 constexpr int TM_WARPS = 4;
-constexpr int TM_STAGES = 4;
+constexpr int TM_STAGES = 3;
+constexpr int TM_EMPTY_BATCH = 16;   // empty tiles zeroed per work ticket
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long kTmaWaitPolls = 1LL << 22;   // polls (with back-off) before a wait gives up
 
@@ -317,10 +318,15 @@ __device__ __forceinline__ void issue_stage(const CUtensorMap* map, const SPart<
   bulk_copy(dst + (uint32_t)bxy * 4 + (uint32_t)sizeof(SPart<W>), T, (uint32_t)sizeof(TPart<NB>), bar);
 }
 
+// Work tickets from *counter: ticket t < n_real * F is (item t / F, frame
+// t % F) of the first n_real items (those whose tile meets the volume, listed
+// first); the tickets after it each zero TM_EMPTY_BATCH (item, frame) tiles
+// of the remaining items, which no slice reaches.
 template <int W, int NB>
-__global__ void __launch_bounds__(TM_WARPS * 32)
+__global__ void __launch_bounds__(TM_WARPS * 32, 7)
 beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ TmaBatch TB,
-                 const int4* __restrict__ items, int n_items, int* __restrict__ counter, int bxy, int tsz) {
+                 const int4* __restrict__ items, int n_items, int n_real, int* __restrict__ counter, int bxy,
+                 int tsz) {
   using L = StageLayout<W, NB>;
   extern __shared__ __align__(128) unsigned char dsm[];
   const size_t stage_bytes = L::stage_bytes(bxy);
@@ -342,13 +348,32 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
   float* Tw = tws + (size_t)warp * tsz + lane;
   uint32_t n_issued = 0, n_done = 0;   // this warp's stage fills (stage = count % S, phase = count / S)
   bool failed = false;
-  const long long total = (long long)n_items * B.frames;
+  const long long real = (long long)n_real * B.frames;
+  const long long empty = (long long)(n_items - n_real) * B.frames;
+  const long long total = real + (empty + TM_EMPTY_BATCH - 1) / TM_EMPTY_BATCH;
 
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
     const long long it = s_item;
     if (it >= total || s_fail) break;
+    if (it >= real) {   // a batch of tiles no slice reaches: zeros
+      const long long e0 = (it - real) * TM_EMPTY_BATCH;
+      for (long long e = e0; e < e0 + TM_EMPTY_BATCH && e < empty; ++e) {
+        const int4 item = items[n_real + e / B.frames];
+        const int frame = (int)(e % B.frames);
+        const BeamCam& C = B.cam[item.x];
+        if (item.y >= 0 && !cell_on(C.sub_n, C.sub_s, item.y)) continue;
+        const int is0 = (item.z % C.tiles_s) * kBeamTileS, it0 = (item.z / C.tiles_s) * kBeamTileT;
+        float* o = C.out + (long long)frame * C.out_fs + (C.per_cell ? (long long)item.y * C.ns * C.nt : 0);
+        for (int q = threadIdx.x; q < kBeamTileS * kBeamTileT; q += TM_WARPS * 32) {
+          const int r = it0 + q / kBeamTileS, c = is0 + q % kBeamTileS;
+          if (r < C.nt && c < C.ns) o[(long long)r * C.ns + c] = 0.0f;
+        }
+      }
+      __syncthreads();   // s_item is rewritten by the next take
+      continue;
+    }
     const int4 item = items[it / B.frames];
     const int frame = (int)(it % B.frames);
     const BeamCam& C = B.cam[item.x];
@@ -586,7 +611,8 @@ int tma_forward_occupancy(int w, int nb, int bxy, int tsz) {
 }
 
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int* counter, int w, int nb, int bxy, int tsz, int ctas, cudaStream_t st) {
+                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int ctas,
+                                    cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (w < 2 || w > 4) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
@@ -595,9 +621,11 @@ cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, cons
   const size_t smem = layout_bytes(w, nb, bxy, tsz);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long total = (long long)n_items * b.frames;
+  const long long total = (long long)n_real * b.frames +
+                         ((long long)(n_items - n_real) * b.frames + TM_EMPTY_BATCH - 1) / TM_EMPTY_BATCH;
   const int grid = (int)std::min<long long>(ctas, total);
-  void* args[] = {(void*)&b, (void*)&tb, (void*)&items, (void*)&n_items, (void*)&counter, (void*)&bxy, (void*)&tsz};
+  void* args[] = {(void*)&b,       (void*)&tb,   (void*)&items, (void*)&n_items, (void*)&n_real,
+                  (void*)&counter, (void*)&bxy, (void*)&tsz};
   return cudaLaunchKernel(fn, dim3(grid), dim3(TM_WARPS * 32), args, smem, st);
 }
 

@@ -61,6 +61,7 @@ struct CameraPlan {
   std::vector<int4> h_items;              // forward work items {cam, k or -1, tile, cost}
   int4* d_items = nullptr;                // this camera's items, longest first
   int n_items = 0;
+  int n_real_items = 0;                   // leading items of positive cost (the rest meet no slice)
   int2* d_srange = nullptr;        // [K][tiles_s] slice interval per forward tile column
   int2* d_trange = nullptr;        // [K][tiles_t] slice interval per forward tile row
   int wmax_s = 0, wmax_t = 0, wimax_s = 0, wimax_t = 0;
@@ -125,6 +126,7 @@ struct lt_plan {
   int n_items = 0;
   int class_begin[lt::kForwardGroups] = {};
   int class_count[lt::kForwardGroups] = {};
+  int class_real[lt::kForwardGroups] = {};   // leading items of positive cost in each group
   int* d_counter = nullptr;        // persistent-launch work counter
   int fwd_variant = lt::kTmaVariant;   // forward kernel variant (autotuned; the brick-staged kernel until then)
 };

@@ -197,8 +197,11 @@ cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s
                                int by, void* stab, void* ttab, int* bad, cudaStream_t st);
 int tma_forward_bxy(int max_brick, int w, int nb);
 int tma_forward_occupancy(int w, int nb, int bxy, int tsz);
+// items: the launch's work items, those of positive cost (the first n_real)
+// before those whose tile no slice reaches.
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int* counter, int w, int nb, int bxy, int tsz, int ctas, cudaStream_t st);
+                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int ctas,
+                                    cudaStream_t st);
 // Device status word of the projector kernels: bit 0 a brick or band that
 // did not fit (its weights were zeroed), bit 1 a TMA wait that gave up.
 // Read (and optionally cleared) synchronously.

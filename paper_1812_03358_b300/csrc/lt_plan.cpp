@@ -452,6 +452,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
   std::vector<int4> local = c.h_items;
   for (auto& it : local) it.x = 0;   // a single-camera batch names this camera 0
   c.n_items = (int)local.size();
+  c.n_real_items = (int)std::count_if(local.begin(), local.end(), [](const int4& a) { return a.w > 0; });
   lt_status s = upload(local, &c.d_items, "forward work items");
   if (s != LT_OK) return s;
   s = upload(srange, &c.d_srange, "tile slice ranges");
@@ -969,6 +970,7 @@ extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_d
       std::stable_sort(all.begin() + start, all.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
       p->class_begin[g] = (int)start;
       p->class_count[g] = (int)(all.size() - start);
+      p->class_real[g] = (int)std::count_if(all.begin() + start, all.end(), [](const int4& a) { return a.w > 0; });
     }
     p->n_items = (int)all.size();
     s = upload(all, &p->d_items, "forward work items");
@@ -1222,7 +1224,7 @@ static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const 
 // aligned; otherwise the direct kernel of the variant (variant kTmaVariant
 // falls back to the default direct variant).
 static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* cps, const int4* items,
-                             int n_items, int wclass, int staged_nb, cudaStream_t st) {
+                             int n_items, int n_real, int wclass, int staged_nb, cudaStream_t st) {
   if (staged_nb > 0 && p->fwd_variant == kTmaVariant && wclass <= 4 && tma_forward_available()) {
     static_assert(sizeof(TmaBatch) % 64 == 0, "tensor maps stay 64-byte aligned");
     TmaBatch tb;
@@ -1249,7 +1251,7 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       const int bxy = tma_forward_bxy(brick, wclass, nb);
       const int occ = tma_forward_occupancy(wclass, nb, bxy, tsz);
       if (occ > 0) {
-        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, p->d_counter, wclass, nb, bxy, tsz,
+        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, n_real, p->d_counter, wclass, nb, bxy, tsz,
                                                 p->sms * occ, st);
         return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward (TMA bricks)");
       }
@@ -1291,7 +1293,7 @@ lt_status stage1_forward(lt_plan* p, CameraPlan& c, const float* x, float* fa, l
   b.frames = p->frames;
   b.cam[0] = beam_cam(c, xc, fa, nullptr, fa_fs, sel);
   CameraPlan* cps[1] = {&c};
-  return run_forward(p, b, cps, c.d_items, c.n_items, cam_class(c), c.tma_nb, st);
+  return run_forward(p, b, cps, c.d_items, c.n_items, c.n_real_items, cam_class(c), c.tma_nb, st);
 }
 
 lt_status stage1_adjoint(lt_plan* p, CameraPlan& c, const float* fa, long long fa_fs, float* x,
@@ -1353,8 +1355,8 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, Su
   }
   for (int g = 0; g < kForwardGroups; ++g) {   // one persistent launch per window class and kernel present
     if (p->class_count[g] == 0) continue;
-    lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], kFwdClasses[g / 3],
-                              g % 3 == 2 ? 0 : 4 << (g % 3), st);
+    lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], p->class_real[g],
+                              kFwdClasses[g / 3], g % 3 == 2 ? 0 : 4 << (g % 3), st);
     if (s != LT_OK) return s;
   }
   for (int i = 0; i < nc; ++i) {
