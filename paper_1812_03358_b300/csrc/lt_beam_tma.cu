@@ -318,15 +318,24 @@ __device__ __forceinline__ void issue_stage(const CUtensorMap* map, const SPart<
   bulk_copy(dst + (uint32_t)bxy * 4 + (uint32_t)sizeof(SPart<W>), T, (uint32_t)sizeof(TPart<NB>), bar);
 }
 
-// Work tickets from *counter: ticket t < n_real * F is (item t / F, frame
-// t % F) of the first n_real items (those whose tile meets the volume, listed
-// first); the tickets after it each zero TM_EMPTY_BATCH (item, frame) tiles
-// of the remaining items, which no slice reaches.
+// Work tickets from *counter: ticket t < n_real * F * chunks is chunk
+// t % chunks of unit u = t / chunks, i.e. of (item u / F, frame u % F) among
+// the first n_real items (those whose tile meets the volume, listed first);
+// the tickets after those each zero TM_EMPTY_BATCH (item, frame) tiles of
+// the remaining items, which no slice reaches.
+//
+// Chunks split an item's (cell, slice) sequence into TB.chunks[camera]
+// consecutive parts (at most `chunks`) processed by different CTAs, so that
+// a workload with few tiles still spreads evenly over the SMs.  Each chunk's
+// partial tile goes to scratch[u][chunk]; the CTA that completes a unit's
+// last chunk (a per-unit ticket count, reset by that CTA) sums the partials
+// in chunk order and writes the tile, so the result does not depend on which
+// CTA ran what.
 template <int W, int NB>
 __global__ void __launch_bounds__(TM_WARPS * 32, 7)
 beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ TmaBatch TB,
                  const int4* __restrict__ items, int n_items, int n_real, int* __restrict__ counter, int bxy,
-                 int tsz) {
+                 int tsz, int chunks, float* __restrict__ scratch, int* __restrict__ unit_count) {
   using L = StageLayout<W, NB>;
   extern __shared__ __align__(128) unsigned char dsm[];
   const size_t stage_bytes = L::stage_bytes(bxy);
@@ -336,6 +345,7 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
   float(*red)[32][33] = reinterpret_cast<float(*)[32][33]>(dsm);                    // aliases the stages
   __shared__ int s_item;
   __shared__ int s_fail;
+  __shared__ int s_last;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -348,7 +358,7 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
   float* Tw = tws + (size_t)warp * tsz + lane;
   uint32_t n_issued = 0, n_done = 0;   // this warp's stage fills (stage = count % S, phase = count / S)
   bool failed = false;
-  const long long real = (long long)n_real * B.frames;
+  const long long real = (long long)n_real * B.frames * chunks;
   const long long empty = (long long)(n_items - n_real) * B.frames;
   const long long total = real + (empty + TM_EMPTY_BATCH - 1) / TM_EMPTY_BATCH;
 
@@ -374,9 +384,16 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
       __syncthreads();   // s_item is rewritten by the next take
       continue;
     }
-    const int4 item = items[it / B.frames];
-    const int frame = (int)(it % B.frames);
+    const long long unit = it / chunks;
+    const int chunk = (int)(it % chunks);
+    const int4 item = items[unit / B.frames];
+    const int frame = (int)(unit % B.frames);
     const BeamCam& C = B.cam[item.x];
+    const int cc = TB.chunks[item.x];
+    if (chunk >= cc) {   // this camera splits its items into fewer chunks
+      __syncthreads();
+      continue;
+    }
     const CUtensorMap* map = &TB.map[item.x];
     const SPart<W>* stab = static_cast<const SPart<W>*>(TB.stab[item.x]);
     const TPart<NB>* ttab = static_cast<const TPart<NB>*>(TB.ttab[item.x]);
@@ -398,9 +415,20 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
     for (int r = 0; r < 32; ++r) acc[r] = 0.0f;
 
     // this warp's pairs: every TM_WARPS-th (cell, slice) of the item
+    // this warp's pairs: every TM_WARPS-th (cell, slice) pair of the chunk,
+    // pairs [j_lo, j_hi) of the item's sequence of L pairs
     PairCursor pf{k_begin, 0, 0, k_end, false};
     cursor_range(C, tile_s, tile_t, pf);
-    cursor_advance(C, tile_s, tile_t, pf, warp);
+    int j_hi = 0x7fffffff, pj = warp;
+    if (cc > 1) {
+      int L = 0;
+      for (PairCursor q = pf; q.valid; ++q.k, cursor_range(C, tile_s, tile_t, q)) L += q.n1 - q.n;
+      const int j_lo = (int)((long long)L * chunk / cc);
+      j_hi = (int)((long long)L * (chunk + 1) / cc);
+      pj = j_lo + warp;
+    }
+    cursor_advance(C, tile_s, tile_t, pf, pj);
+    if (pj >= j_hi) pf.valid = false;
     // the cursor's table parts and brick origin (lane 0 reads the origin one
     // pair before it issues the pair's stage fill)
     const SPart<W>* sp = stab;
@@ -426,6 +454,8 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
           ++n_issued;
           ++inflight;
           cursor_advance(C, tile_s, tile_t, pf, TM_WARPS);
+          pj += TM_WARPS;
+          if (pj >= j_hi) pf.valid = false;
           if (pf.valid) {
             const long long kn = (long long)pf.k * C.nz + pf.n;
             sp = stab + kn * C.tiles_s + tile_s;
@@ -456,7 +486,9 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
       }
     }
 
-    // the four warps' partial tiles, summed in warp order, masked and written
+    // the four warps' partial tiles, summed in warp order; then either the
+    // tile (one chunk) or this chunk's partial, the unit's last chunk summing
+    // every partial in chunk order; masked and written
     __syncthreads();
     if (!s_fail) {
       if (warp > 0) {
@@ -465,6 +497,39 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
       }
       __syncthreads();
       if (warp == 0) {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+#pragma unroll
+          for (int g = 0; g < TM_WARPS - 1; ++g) acc[r] += red[g][r][lane];
+        }
+      }
+      bool write = true;
+      float* part = scratch + unit * (long long)chunks * 1024;
+      if (cc > 1) {
+        if (warp == 0) {
+#pragma unroll
+          for (int r = 0; r < 32; ++r) part[chunk * 1024 + r * 32 + lane] = acc[r];
+          __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const int done = atomicAdd(&unit_count[unit], 1);
+          s_last = done == cc - 1;
+          if (s_last) unit_count[unit] = 0;   // ready for the next launch
+        }
+        __syncthreads();
+        write = s_last;
+        if (write && warp == 0) {
+          __threadfence();
+#pragma unroll
+          for (int r = 0; r < 32; ++r) {
+            float v = __ldcg(part + r * 32 + lane);
+            for (int c = 1; c < cc; ++c) v += __ldcg(part + c * 1024 + r * 32 + lane);
+            acc[r] = v;
+          }
+        }
+      }
+      if (write && warp == 0) {
         const int is = is0 + lane;
         if (is < C.ns) {
           float* o = C.out + (long long)frame * C.out_fs + (C.per_cell ? (long long)k_begin * C.ns * C.nt : 0);
@@ -473,8 +538,6 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
             const int itp = it0 + r;
             if (itp < C.nt) {
               float v = acc[r];
-#pragma unroll
-              for (int g = 0; g < TM_WARPS - 1; ++g) v += red[g][r][lane];
               if (C.mask) v *= C.mask[(long long)itp * C.ns + is];   // M (Sec. II-D)
               o[(long long)itp * C.ns + is] = v;
             }
@@ -611,8 +674,8 @@ int tma_forward_occupancy(int w, int nb, int bxy, int tsz) {
 }
 
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int ctas,
-                                    cudaStream_t st) {
+                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int chunks,
+                                    float* scratch, int* unit_count, int ctas, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (w < 2 || w > 4) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
@@ -621,11 +684,12 @@ cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, cons
   const size_t smem = layout_bytes(w, nb, bxy, tsz);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long total = (long long)n_real * b.frames +
+  if (chunks < 1 || (chunks > 1 && (!scratch || !unit_count))) return cudaErrorInvalidValue;
+  const long long total = (long long)n_real * b.frames * chunks +
                          ((long long)(n_items - n_real) * b.frames + TM_EMPTY_BATCH - 1) / TM_EMPTY_BATCH;
   const int grid = (int)std::min<long long>(ctas, total);
-  void* args[] = {(void*)&b,       (void*)&tb,   (void*)&items, (void*)&n_items, (void*)&n_real,
-                  (void*)&counter, (void*)&bxy, (void*)&tsz};
+  void* args[] = {(void*)&b,   (void*)&tb,  (void*)&items,  (void*)&n_items, (void*)&n_real,  (void*)&counter,
+                  (void*)&bxy, (void*)&tsz, (void*)&chunks, (void*)&scratch, (void*)&unit_count};
   return cudaLaunchKernel(fn, dim3(grid), dim3(TM_WARPS * 32), args, smem, st);
 }
 

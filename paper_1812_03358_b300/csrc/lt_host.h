@@ -68,6 +68,7 @@ struct CameraPlan {
   // brick-staged (TMA) forward: brick box and band rows sized at plan time
   // for every (cell, slice, tile); tma_nb = 0 when the camera does not fit it
   int tma_bx = 0, tma_by = 0, tma_nb = 0;
+  int tma_chunks = 1;              // parts each forward item is split into (few tiles: more CTAs per tile)
   void* d_stab = nullptr;          // its footprint-weight tables (lt_beam_tma.cu layout)
   void* d_ttab = nullptr;
   // plenoptic
@@ -128,6 +129,8 @@ struct lt_plan {
   int class_count[lt::kForwardGroups] = {};
   int class_real[lt::kForwardGroups] = {};   // leading items of positive cost in each group
   int* d_counter = nullptr;        // persistent-launch work counter
+  float* d_chunk_part = nullptr;   // brick-staged forward: partial tiles of chunked items
+  int* d_chunk_count = nullptr;    // and the chunks completed per (item, frame), zero between launches
   int fwd_variant = lt::kTmaVariant;   // forward kernel variant (autotuned; the brick-staged kernel until then)
 };
 

@@ -156,6 +156,7 @@ struct TmaBatch {
   const void* ttab[kMaxBatchCams];   // per-(cell, slice, tile row) t band weights
   int32_t bx[kMaxBatchCams];
   int32_t by[kMaxBatchCams];
+  int32_t chunks[kMaxBatchCams];     // parts each of the camera's items is split into (>= 1)
 };
 
 // Forward kernel variants chosen by the autotuner: slices per weight batch
@@ -198,10 +199,12 @@ cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s
 int tma_forward_bxy(int max_brick, int w, int nb);
 int tma_forward_occupancy(int w, int nb, int bxy, int tsz);
 // items: the launch's work items, those of positive cost (the first n_real)
-// before those whose tile no slice reaches.
+// before those whose tile no slice reaches.  chunks: the largest
+// tb.chunks[] of the launch; with chunks > 1, scratch holds n_real * F *
+// chunks * 1024 floats and unit_count n_real * F ints, zero between launches.
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int ctas,
-                                    cudaStream_t st);
+                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int chunks,
+                                    float* scratch, int* unit_count, int ctas, cudaStream_t st);
 // Device status word of the projector kernels: bit 0 a brick or band that
 // did not fit (its weights were zeroed), bit 1 a TMA wait that gave up.
 // Read (and optionally cleared) synchronously.

@@ -931,6 +931,45 @@ static lt_status plan_camera(const lt_volume_desc& v0, const lt_camera_desc& src
   return s;
 }
 
+// Chunks of the brick-staged forward: a camera whose tiles meeting the
+// volume (times frames) number fewer than twice the CTAs the kernel keeps
+// resident splits each tile's slices into up to 4 parts, so that its work
+// spreads evenly over the SMs; the partial tiles and per-tile counts live in
+// plan scratch sized for the largest launch (a window-class group of the
+// batched forward, or one camera).
+static lt_status plan_chunks(lt_plan* p) {
+  const long long slots = 7LL * p->sms;   // resident CTAs of the brick-staged kernel
+  long long need_part = 0, need_count = 0;
+  for (auto& c : p->cams) {
+    c.tma_chunks = 1;
+    if (c.tma_nb == 0) continue;
+    const long long units = (long long)c.n_real_items * p->frames;
+    if (units > 0 && units < 2 * slots) c.tma_chunks = (int)std::min<long long>(4, (2 * slots + units - 1) / units);
+    if (c.tma_chunks > 1) {
+      need_part = std::max(need_part, units * c.tma_chunks);
+      need_count = std::max(need_count, units);
+    }
+  }
+  for (int g = 0; g < kForwardGroups; ++g) {
+    if (g % 3 == 2 || p->class_count[g] == 0) continue;
+    int cmax = 1;
+    for (auto& c : p->cams)
+      if (c.tma_nb == (4 << (g % 3)) && window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g / 3])
+        cmax = std::max(cmax, c.tma_chunks);
+    if (cmax > 1) {
+      const long long units = (long long)p->class_real[g] * p->frames;
+      need_part = std::max(need_part, units * cmax);
+      need_count = std::max(need_count, units);
+    }
+  }
+  if (need_part == 0) return LT_OK;
+  if (device_alloc((void**)&p->d_chunk_part, (size_t)need_part * 1024 * sizeof(float)) != cudaSuccess ||
+      device_alloc((void**)&p->d_chunk_count, (size_t)need_count * sizeof(int)) != cudaSuccess)
+    return set_error(LT_ENOMEM, "cudaMalloc(forward chunk scratch)");
+  cudaError_t e = cudaMemset(p->d_chunk_count, 0, (size_t)need_count * sizeof(int));
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "forward chunk scratch");
+}
+
 extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_desc* cams,
                                     int32_t n_cams, int32_t n_frames, lt_plan** out) {
   clear_error();
@@ -977,6 +1016,7 @@ extern "C" lt_status lt_plan_create(const lt_volume_desc* vol, const lt_camera_d
     if (s == LT_OK && device_alloc((void**)&p->d_counter, sizeof(int)) != cudaSuccess)
       s = set_error(LT_ENOMEM, "cudaMalloc(work counter)");
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (s == LT_OK) s = plan_chunks(p);
     if (s != LT_OK) {
       lt_plan_destroy(p);
       return s;
@@ -992,6 +1032,8 @@ extern "C" lt_status lt_plan_destroy(lt_plan* plan) {
   for (auto& c : plan->cams) free_camera(c);
   cudaFree(plan->d_items);
   cudaFree(plan->d_counter);
+  cudaFree(plan->d_chunk_part);
+  cudaFree(plan->d_chunk_count);
   delete plan;
   return LT_OK;
 }
@@ -1231,7 +1273,7 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
     std::memset(&tb, 0, sizeof(tb));
     bool ok = true;
     const int nb = staged_nb;
-    int brick = 0, tsz = 0;
+    int brick = 0, tsz = 0, chunks = 1;
     for (int i = 0; i < b.n_cams && ok; ++i) {
       const CameraPlan& c = *cps[i];
       const BeamCam& bc = b.cam[i];
@@ -1242,6 +1284,8 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       if (!ok) break;
       tb.stab[i] = c.d_stab;
       tb.ttab[i] = c.d_ttab;
+      tb.chunks[i] = c.tma_chunks;
+      chunks = std::max(chunks, c.tma_chunks);
       tb.bx[i] = c.tma_bx;
       tb.by[i] = c.tma_by;
       brick = std::max(brick, c.tma_bx * c.tma_by);
@@ -1252,7 +1296,7 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       const int occ = tma_forward_occupancy(wclass, nb, bxy, tsz);
       if (occ > 0) {
         cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, n_real, p->d_counter, wclass, nb, bxy, tsz,
-                                                p->sms * occ, st);
+                                                chunks, p->d_chunk_part, p->d_chunk_count, p->sms * occ, st);
         return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward (TMA bricks)");
       }
     }
