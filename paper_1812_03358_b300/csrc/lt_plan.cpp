@@ -932,11 +932,13 @@ static lt_status plan_camera(const lt_volume_desc& v0, const lt_camera_desc& src
 }
 
 // Chunks of the brick-staged forward: a camera whose tiles meeting the
-// volume (times frames) number fewer than twice the CTAs the kernel keeps
-// resident splits each tile's slices into up to 4 parts, so that its work
-// spreads evenly over the SMs; the partial tiles and per-tile counts live in
-// plan scratch sized for the largest launch (a window-class group of the
-// batched forward, or one camera).
+// volume (times frames) number at most a quarter of the CTAs the kernel
+// keeps resident splits each tile's slices into up to 4 parts, so that more
+// SMs share its work (measured: with about one tile per resident CTA the
+// extra per-chunk start-up and combining cost more than the better balance
+// gains, so larger workloads keep whole tiles); the partial tiles and
+// per-tile counts live in plan scratch sized for the largest launch (a
+// window-class group of the batched forward, or one camera).
 static lt_status plan_chunks(lt_plan* p) {
   const long long slots = 7LL * p->sms;   // resident CTAs of the brick-staged kernel
   long long need_part = 0, need_count = 0;
@@ -944,7 +946,7 @@ static lt_status plan_chunks(lt_plan* p) {
     c.tma_chunks = 1;
     if (c.tma_nb == 0) continue;
     const long long units = (long long)c.n_real_items * p->frames;
-    if (units > 0 && units < 2 * slots) c.tma_chunks = (int)std::min<long long>(4, (2 * slots + units - 1) / units);
+    if (units > 0 && 4 * units <= slots) c.tma_chunks = (int)std::min<long long>(4, slots / units);
     if (c.tma_chunks > 1) {
       need_part = std::max(need_part, units * c.tma_chunks);
       need_count = std::max(need_count, units);
