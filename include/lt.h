@@ -229,6 +229,13 @@ LT_API lt_status lt_plan_set_forward_variant(lt_plan* plan, int32_t variant);
  * synchronises the device; clear != 0 resets the word. */
 LT_API lt_status lt_projector_status(int32_t* flags, int32_t clear);
 
+/* Adjoint kernel choice (no counterpart in the paper): 1 (default) = the
+ * box-staged gather adjoint (each image box a voxel tile reads over a chunk
+ * of slices brought to shared memory once by TMA) where the camera fits it,
+ * 0 = the direct gather adjoint.  Both compute the same operator (summation
+ * order differs).  LT_EINVAL for another value. */
+LT_API lt_status lt_plan_set_adjoint_variant(lt_plan* plan, int32_t variant);
+
 /* Fault injection for tests (no counterpart in the paper): the n-th device
  * allocation the library makes from now on fails as if the device were out
  * of memory (n >= 1); n <= 0 turns the injection off.  The failing call
@@ -258,6 +265,8 @@ typedef struct {
   int64_t forward_brick;    /* floats per brick of the brick-staged forward
                              * (box columns x rows), 0 if the camera takes the
                              * direct kernel                                   */
+  int64_t adjoint_box;      /* floats per image box of the box-staged adjoint,
+                             * 0 if the camera takes the direct adjoint        */
 } lt_camera_stats;
 
 LT_API lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_camera_stats* out);

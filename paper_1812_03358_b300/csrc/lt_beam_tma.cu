@@ -617,12 +617,17 @@ cudaError_t projector_status(int* flags, bool clear) {
 }
 
 bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, int bx, int by) {
+  return tma_encode_planes(map, x, nx, ny, nz_total, (long long)nx * ny, bx, by);
+}
+
+bool tma_encode_planes(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, long long z_stride, int bx,
+                       int by) {
   EncodeTiled enc = encoder();
-  if (!enc || !x || (reinterpret_cast<uintptr_t>(x) & 15) || (nx & 3) || bx <= 0 || by <= 0 || bx > 256 ||
-      by > 256 || (bx & 3))
+  if (!enc || !x || (reinterpret_cast<uintptr_t>(x) & 15) || (nx & 3) || (z_stride & 3) || bx <= 0 || by <= 0 ||
+      bx > 256 || by > 256 || (bx & 3))
     return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz_total};
-  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)z_stride * sizeof(float)};
   const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(x), dims, strides, box, estr,

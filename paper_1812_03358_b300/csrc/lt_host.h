@@ -69,6 +69,7 @@ struct CameraPlan {
   // for every (cell, slice, tile); tma_nb = 0 when the camera does not fit it
   int tma_bx = 0, tma_by = 0, tma_nb = 0;
   int tma_chunks = 1;              // parts each forward item is split into (few tiles: more CTAs per tile)
+  int adj_bx = 0, adj_by = 0;      // box-staged adjoint: image box (0: the direct adjoint serves it)
   void* d_stab = nullptr;          // its footprint-weight tables (lt_beam_tma.cu layout)
   void* d_ttab = nullptr;
   // plenoptic
@@ -132,6 +133,7 @@ struct lt_plan {
   float* d_chunk_part = nullptr;   // brick-staged forward: partial tiles of chunked items
   int* d_chunk_count = nullptr;    // and the chunks completed per (item, frame), zero between launches
   int fwd_variant = lt::kTmaVariant;   // forward kernel variant (autotuned; the brick-staged kernel until then)
+  int adj_variant = 1;             // 1: box-staged adjoint where it fits, 0: the direct gather adjoint
 };
 
 namespace lt {

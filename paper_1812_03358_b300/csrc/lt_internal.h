@@ -193,6 +193,9 @@ int window_class(int w);
 // camera's SliceParam table and sets *bad if a brick or band did not fit.
 bool tma_forward_available();
 bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, int bx, int by);
+// The same for a plane stack whose third-axis stride (floats) is z_stride.
+bool tma_encode_planes(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, long long z_stride, int bx,
+                       int by);
 size_t tma_table_bytes(int w, int nb, int K, int nz, int tiles_s, int tiles_t);
 cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int nb, int bx,
                                int by, void* stab, void* ttab, int* bad, cudaStream_t st);
@@ -209,6 +212,28 @@ cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, cons
 // did not fit (its weights were zeroed), bit 1 a TMA wait that gave up.
 // Read (and optionally cleared) synchronously.
 cudaError_t projector_status(int* flags, bool clear);
+
+// TMA view of each camera's adjoint input (the image plane, or the array
+// plane of every cell) for the box-staged adjoint (lt_beam_adj.cu): a 3-D
+// tensor map over [F * zf][nt][ns] float32 (zf = K per-cell planes or 1),
+// and the image box (bx columns, a multiple of 4, by rows) the planner sized
+// for the camera's voxel tiles and slice chunks.
+struct AdjBatch {
+  CUtensorMap map[kMaxBatchCams];
+  int32_t bx[kMaxBatchCams];
+  int32_t by[kMaxBatchCams];
+  int32_t zf[kMaxBatchCams];
+};
+// Box-staged adjoint: voxel tile adjoint_tile_x() x adjoint_tile_y(),
+// adjoint_chunk() slices per CTA; x[F][nz][ny][nx] (= or +=) the sum over
+// the batch's cameras and cells.
+int adjoint_tile_x();
+int adjoint_tile_y();
+int adjoint_chunk();
+cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, float* x, long long x_fs, int accumulate,
+                                    cudaStream_t st);
+// Status word of the box-staged adjoint (bits as the forward's).
+cudaError_t adjoint_status(int* flags, bool clear);
 
 // Batched gather adjoint over cameras that share one grid (cam[0]'s dims):
 // x[F][nz][ny][nx] (= or +=) sum over cameras and cells.

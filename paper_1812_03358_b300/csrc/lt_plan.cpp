@@ -319,6 +319,56 @@ static void plan_bricks(CameraPlan& c, int grid_nx, const std::vector<Footprint>
   c.tma_nb = nb;
 }
 
+// Image box of the box-staged adjoint for camera c: per (cell, chunk of
+// adjoint_chunk() slices, tile of adjoint_tile_x() x adjoint_tile_y()
+// voxels), the target pixels the tile's windows reach, [first window start,
+// last window start + window - 1] per axis over the chunk's slices (window
+// starts floor(min(lo, hi)) - 1 of (j -+ 1/2 -+ Q - c0) / c1 at the tile's
+// two ends, widened by 1e-3), the columns rounded to a multiple of 4.  The
+// box is the largest span; cameras whose box exceeds 8192 floats keep the
+// direct adjoint.
+static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, const std::vector<Footprint>& fps,
+                             const std::vector<Footprint>& fpt, const std::vector<SliceParam>& sp) {
+  c.adj_bx = c.adj_by = 0;
+  const int TX = adjoint_tile_x(), TY = adjoint_tile_y(), SC = adjoint_chunk();
+  auto start = [](const Footprint& f, int j, double eps) {
+    const double lo = (j - 0.5 - (double)f.a.Q - f.C0) / f.C1, hi = (j + 0.5 + (double)f.a.Q - f.C0) / f.C1;
+    return (long long)std::floor(std::min(lo, hi) + eps) - 1;
+  };
+  long long need_bx = 0, need_by = 0;
+  for (int k = 0; k < c.K; ++k)
+    for (int n0 = 0; n0 < v.nz; n0 += SC) {
+      for (int j0 = 0; j0 < v.nx; j0 += TX) {
+        const int j1 = std::min(j0 + TX, v.nx) - 1;
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        for (int n = n0; n < std::min(n0 + SC, v.nz); ++n) {
+          const size_t q = (size_t)k * v.nz + n;
+          for (int j : {j0, j1}) {
+            lo = std::min(lo, start(fps[q], j, -1e-3));
+            hi = std::max(hi, start(fps[q], j, 1e-3) + sp[q].wis - 1);
+          }
+        }
+        need_bx = std::max(need_bx, hi - (lo & ~3LL) + 1);
+      }
+      for (int j0 = 0; j0 < v.ny; j0 += TY) {
+        const int j1 = std::min(j0 + TY, v.ny) - 1;
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        for (int n = n0; n < std::min(n0 + SC, v.nz); ++n) {
+          const size_t q = (size_t)k * v.nz + n;
+          for (int j : {j0, j1}) {
+            lo = std::min(lo, start(fpt[q], j, -1e-3));
+            hi = std::max(hi, start(fpt[q], j, 1e-3) + sp[q].wit - 1);
+          }
+        }
+        need_by = std::max(need_by, hi - lo + 1);
+      }
+    }
+  const long long bx = (need_bx + 3) / 4 * 4, by = need_by;
+  if (bx < 4 || by < 1 || bx > 256 || by > 256 || bx * by > 8192 || c.wimax_s > 32 || c.wimax_t > 32) return;
+  c.adj_bx = (int)bx;
+  c.adj_by = (int)by;
+}
+
 // Footprint-weight tables of the brick-staged forward (one entry per
 // (cell, slice, tile column) and (cell, slice, tile row)), built on the
 // device from the slice parameters.  A camera whose tables would exceed
@@ -424,6 +474,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
   plan_bricks(c, v.nx, fps, fpt, tiles_s, tiles_t);
+  plan_adjoint_box(c, v, fps, fpt, sp);
   for (auto& r : srange)
     if (r.y < 0) r = make_int2(0, 0);
   for (auto& r : trange)
@@ -1196,6 +1247,7 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
   }
   st.ray_samples = st.stage1_samples + st.stage2_samples;
   st.forward_brick = (int64_t)c.tma_bx * c.tma_by;
+  st.adjoint_box = (int64_t)c.adj_bx * c.adj_by;
   *out = st;
   return LT_OK;
 }
@@ -1311,6 +1363,37 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
 
 static int cam_class(const CameraPlan& c) { return window_class(std::max(c.wmax_s, c.wmax_t)); }
 
+// One gather-adjoint launch over the cameras of b (cps[i] is the plan of
+// b.cam[i], all on one grid): the box-staged kernel when the plan selects
+// it and every camera fits it (planner-sized boxes, 16-byte aligned input
+// whose rows and plane strides are multiples of 4 floats), otherwise the
+// direct gather kernel.
+static lt_status run_adjoint(lt_plan* p, const BeamBatch& b, CameraPlan* const* cps, float* x, long long x_fs,
+                             int accumulate, cudaStream_t st) {
+  if (p->adj_variant == 1 && tma_forward_available()) {
+    AdjBatch a;
+    std::memset(&a, 0, sizeof(a));
+    bool ok = true;
+    for (int i = 0; i < b.n_cams && ok; ++i) {
+      const CameraPlan& c = *cps[i];
+      const BeamCam& bc = b.cam[i];
+      const long long plane = (long long)bc.ns * bc.nt;
+      ok = c.adj_bx > 0 && (!bc.per_cell || bc.out_fs == plane * bc.K) &&
+           tma_encode_planes(&a.map[i], bc.in, bc.ns, bc.nt, b.frames * (bc.per_cell ? bc.K : 1),
+                             bc.per_cell ? plane : bc.out_fs, c.adj_bx, c.adj_by);
+      a.bx[i] = c.adj_bx;
+      a.by[i] = c.adj_by;
+      a.zf[i] = bc.per_cell ? bc.K : 1;
+    }
+    if (ok) {
+      cudaError_t e = launch_beam_adjoint_tma(b, a, x, x_fs, accumulate, st);
+      return e == cudaSuccess ? LT_OK : cuda_error(e, "beam adjoint (TMA boxes)");
+    }
+  }
+  cudaError_t e = launch_beam_adjoint_batched(b, x, x_fs, accumulate, st);
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "beam adjoint");
+}
+
 // Adjoint of one camera's slice -> plane transport from `in` back to x
 // (through the transposed rotation for rotated cameras).
 static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* in, long long in_fs, float* x,
@@ -1320,10 +1403,11 @@ static lt_status beam_adjoint_to_volume(lt_plan* p, CameraPlan& c, const float* 
   b.frames = p->frames;
   b.cam[0] = beam_cam(c, nullptr, nullptr, in, in_fs, sel);
   float* dst = c.rotated ? c.d_xr : x;
-  cudaError_t e = launch_beam_adjoint_batched(b, dst, c.nvox_c, c.rotated ? 0 : accumulate, st);
-  if (e != cudaSuccess) return cuda_error(e, "beam adjoint");
+  CameraPlan* cps[1] = {&c};
+  lt_status s = run_adjoint(p, b, cps, dst, c.nvox_c, c.rotated ? 0 : accumulate, st);
+  if (s != LT_OK) return s;
   if (c.rotated) {
-    e = rotate_adj(c, c.d_xr, x, p->frames, accumulate, st);
+    cudaError_t e = rotate_adj(c, c.d_xr, x, p->frames, accumulate, st);
     if (e != cudaSuccess) return cuda_error(e, "rotated view adjoint");
   }
   return LT_OK;
@@ -1429,12 +1513,13 @@ lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st, Su
   }
   BeamBatch b{};
   b.frames = p->frames;
+  CameraPlan* cps[kMaxBatchCams];
   int written = 0;
   for (int i = 0; i <= nc; ++i) {
     const bool flush = (i == nc && b.n_cams > 0) || b.n_cams == kMaxBatchCams;
     if (flush) {
-      cudaError_t e = launch_beam_adjoint_batched(b, x, p->nvox, written ? 1 : 0, st);
-      if (e != cudaSuccess) return cuda_error(e, "beam adjoint");
+      lt_status s = run_adjoint(p, b, cps, x, p->nvox, written ? 1 : 0, st);
+      if (s != LT_OK) return s;
       written = 1;
       b.n_cams = 0;
     }
@@ -1442,6 +1527,7 @@ lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st, Su
     CameraPlan& c = p->cams[i];
     if (c.rotated) continue;
     const bool plen = c.desc.kind == LT_CAM_PLENOPTIC;
+    cps[b.n_cams] = &c;
     b.cam[b.n_cams++] = beam_cam(c, nullptr, nullptr, plen ? c.d_fa : y + c.offset,
                                  plen ? (long long)c.K * c.Na : p->m_total, sel);
   }
@@ -1576,10 +1662,19 @@ extern "C" int32_t lt_autotune_variants(void) { return kForwardVariants; }
 extern "C" lt_status lt_projector_status(int32_t* flags, int32_t clear) {
   clear_error();
   if (!flags) return set_error(LT_EINVAL, "flags is NULL");
-  int f = 0;
+  int f = 0, g = 0;
   cudaError_t e = projector_status(&f, clear != 0);
+  if (e == cudaSuccess) e = adjoint_status(&g, clear != 0);
   if (e != cudaSuccess) return cuda_error(e, "projector status");
-  *flags = f;
+  *flags = f | g;
+  return LT_OK;
+}
+
+extern "C" lt_status lt_plan_set_adjoint_variant(lt_plan* plan, int32_t variant) {
+  clear_error();
+  if (!plan) return set_error(LT_EINVAL, "plan is NULL");
+  if (variant != 0 && variant != 1) return set_error(LT_EINVAL, "adjoint variant %d is not 0 or 1", variant);
+  plan->adj_variant = variant;
   return LT_OK;
 }
 

@@ -47,7 +47,7 @@ class lt_camera_stats(ctypes.Structure):
     _fields_ = [("n_cells", c_int64), ("stage1_samples", c_int64), ("stage2_samples", c_int64),
                 ("ray_samples", c_int64), ("hit_samples", c_int64), ("stage1_nnz", c_int64),
                 ("stage2_nnz", c_int64), ("stage1_tile_voxels", c_int64),
-                ("forward_brick", c_int64)]
+                ("forward_brick", c_int64), ("adjoint_box", c_int64)]
 
 
 class LtError(RuntimeError):
@@ -95,6 +95,7 @@ _SIGS = {
     "lt_plan_autotune": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
     "lt_plan_set_forward_variant": (c_int32, [c_void_p, c_int32]),
     "lt_projector_status": (c_int32, [POINTER(c_int32), c_int32]),
+    "lt_plan_set_adjoint_variant": (c_int32, [c_void_p, c_int32]),
     "lt_test_fail_allocation_after": (None, [c_int32]),
     "lt_last_error": (c_char_p, []),
     "lt_peak_smem_read": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
@@ -254,6 +255,11 @@ def lt_projector_status(clear: bool = False) -> int:
     f = c_int32()
     _check(lib().lt_projector_status(byref(f), int(clear)))
     return f.value
+
+
+def lt_plan_set_adjoint_variant(plan, variant: int) -> None:
+    """1: box-staged adjoint where the camera fits it (default); 0: direct."""
+    _check(lib().lt_plan_set_adjoint_variant(plan, variant))
 
 
 def lt_plan_set_forward_variant(plan, variant: int) -> None:

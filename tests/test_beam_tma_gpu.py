@@ -132,3 +132,57 @@ def test_brick_forward_is_deterministic_and_status_clean():
     assert np.array_equal(a, b)
     assert lt.lt_projector_status() == 0
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# the box-staged adjoint (image boxes brought to shared memory by TMA once per
+# voxel tile, cell and chunk of slices)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", list(_cases()), ids=lambda c: c[0])
+def test_box_adjoint_matches_oracle(case):
+    _, vol, cam, staged = case
+    plan = lt.Plan(vol, [cam])
+    assert (plan.stats(0)["adjoint_box"] > 0) == staged
+    y = I.uniform_random(cam.m, seed=29)
+    xo = O.single_adjoint(vol, cam, y).ravel()
+    for variant in (1, 0):
+        lt.lt_plan_set_adjoint_variant(plan.handle, variant)
+        xg = host(plan.adjoint(dev(y).reshape(1, -1)))
+        assert rel_l2(xg, xo) < TOL, (variant, rel_l2(xg, xo))
+        assert close_elementwise(xg, xo), variant
+    plan.close()
+
+
+def test_box_adjoint_frames_cameras_and_accumulation():
+    vol = I.Volume(20, 16, 12, 4.0, 4.0, 5.0)
+    cams = [I.table_single_lens(36, 0.09), I.table_single_lens(28, 0.11, ks=2, kt=2)]
+    frames = 3
+    plan = lt.Plan(vol, cams, frames)
+    assert all(plan.stats(c)["adjoint_box"] > 0 for c in range(len(cams)))
+    ys = np.stack([I.uniform_random(plan.m_total, seed=70 + f) for f in range(frames)])
+    xg = host(plan.adjoint(dev(ys)))
+    for f in range(frames):
+        xo = sum(O.single_adjoint(vol, cam, ys[f, plan.offsets[c]:plan.offsets[c + 1]]).ravel()
+                 for c, cam in enumerate(cams))
+        assert rel_l2(xg[f], xo) < TOL and close_elementwise(xg[f], xo)
+    plan.close()
+
+
+def test_box_adjoint_full_size_plenoptic_equals_direct_kernel():
+    vol, cam = I.config_plenoptic()
+    plan = lt.Plan(vol, [cam])
+    assert plan.stats(0)["adjoint_box"] > 0
+    ga = dev(np.random.default_rng(3).random((1, plan.cells[0], cam.arr_nt, cam.arr_ns)))
+    out = {}
+    for variant in (1, 0):
+        lt.lt_plan_set_adjoint_variant(plan.handle, variant)
+        out[variant] = host(plan.stage1_adjoint(0, ga))
+    assert rel_l2(out[1], out[0]) < 1e-6
+    assert close_elementwise(out[1], out[0], 1e-6)
+    y = dev(I.uniform_random(cam.m, seed=31).reshape(1, -1))
+    a = host(plan.adjoint(y))
+    b = host(plan.adjoint(y))
+    assert np.array_equal(a, b)
+    assert lt.lt_projector_status() == 0
+    plan.close()
