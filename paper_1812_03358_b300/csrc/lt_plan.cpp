@@ -326,10 +326,12 @@ static void plan_bricks(CameraPlan& c, int grid_nx, const std::vector<Footprint>
 // starts floor(min(lo, hi)) - 1 of (j -+ 1/2 -+ Q - c0) / c1 at the tile's
 // two ends, widened by 1e-3), the columns rounded to a multiple of 4.  The
 // box is the largest span; cameras whose box exceeds 8192 floats keep the
-// direct adjoint.
-static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, const std::vector<Footprint>& fps,
+// direct adjoint, and so do cameras whose target rows are not a multiple of
+// 4 floats.
+static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns, const std::vector<Footprint>& fps,
                              const std::vector<Footprint>& fpt, const std::vector<SliceParam>& sp) {
   c.adj_bx = c.adj_by = 0;
+  if (tgt_ns % 4 != 0) return;   // a TMA row stride is a multiple of 16 bytes
   const int TX = adjoint_tile_x(), TY = adjoint_tile_y(), SC = adjoint_chunk();
   auto start = [](const Footprint& f, int j, double eps) {
     const double lo = (j - 0.5 - (double)f.a.Q - f.C0) / f.C1, hi = (j + 0.5 + (double)f.a.Q - f.C0) / f.C1;
@@ -474,7 +476,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
   plan_bricks(c, v.nx, fps, fpt, tiles_s, tiles_t);
-  plan_adjoint_box(c, v, fps, fpt, sp);
+  plan_adjoint_box(c, v, tgt_ns, fps, fpt, sp);
   for (auto& r : srange)
     if (r.y < 0) r = make_int2(0, 0);
   for (auto& r : trange)
