@@ -1,22 +1,25 @@
-// Beam integration, gather adjoint, with TMA-staged image boxes (Sec. IV-A,
-// Sec. IV-B).
+// Beam integration, gather adjoint, with TMA-staged image boxes and
+// plan-built window tables (Sec. IV-A, Sec. IV-B).
 //
 // x[n][jy][jx] = sum over cameras, cells k, target pixels (it, is) of
 // Bt[it][jy] Bs[is][jx] g_k[it][is] x scale_kn: the transpose of the beam
 // forward, evaluated as a gather (one writer per voxel, no atomics).  A CTA
 // owns a 32 x 8 voxel tile (thread = voxel) and a chunk of ASC consecutive
 // slices of one frame, and keeps one accumulator per slice of the chunk in
-// registers.  For each (camera, cell) it brings the image box that every
-// slice of the chunk reads (the union of the tile's pixel windows over the
-// chunk) into shared memory with one cp.async.bulk.tensor load, double
-// buffered so that the next cell's box arrives while this one is used; then
-// per slice it evaluates the tile's window entries (the same cell_weight of
-// the same (pixel, cell) pair as the forward), contracts along t (warp =
-// voxel row, lanes over box columns) and then along s from shared memory
-// (the separable scheme of Sec. IV-B).  Each image pixel is read from L2
-// once per (tile, cell, chunk) instead of once per slice.  Outside the image
-// the TMA load fills zeros.  Waits are bounded (status bit 1); a box the
-// planner sized too small zeroes that cell's entries and sets status bit 0.
+// registers.  For each (camera, cell) one thread brings into shared memory,
+// all completing one mbarrier: the image box every slice of the chunk reads
+// (the union of the tile's pixel windows over the chunk; one
+// cp.async.bulk.tensor load), and the chunk's window entries of the tile's
+// columns and rows (two bulk copies of plan-built tables: the same
+// cell_weight of the same (pixel, cell) pair as the forward, the t entries
+// already multiplied by the slice scale as in the forward).  Buffers are
+// double so that the next cell's data arrives while this one is used.  Per
+// slice, warp r contracts along t into its own row of U (lanes over box
+// columns) and then every voxel along s from that row: no CTA barrier
+// inside a chunk.  Each image pixel is read from L2 once per (tile, cell,
+// chunk).  Outside the image the TMA load fills zeros.  Waits are bounded
+// (status bit 1); a box the planner sized too small is reported when the
+// tables are built, and that camera keeps the direct adjoint.
 #include <cuda.h>
 
 #include <algorithm>
@@ -34,6 +37,8 @@ constexpr int AY = 8;           // voxel rows per tile (warps)
 constexpr int ASC = 8;          // slices per chunk (register accumulators)
 constexpr int AWMAX = 32;       // adjoint window cap (target pixels per voxel per axis)
 constexpr long long kAdjWaitPolls = 1LL << 22;
+
+__device__ int g_adjoint_status;
 
 __device__ __forceinline__ void a_mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -65,8 +70,84 @@ __device__ __forceinline__ void a_tma_3d(uint32_t dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void a_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
 
-__device__ int g_adjoint_status;
+// ---------------------------------------------------------------------------
+// Plan-time tables.  S entry (cell k, tile column tx, slice n): float
+// sw[wqs][32] (column c's entries, zero past the slice's window or the
+// volume), int i0[32] (first target pixel of the window).  T entry (k, tile
+// row ty, n): float tw[wqt][8] (x slice scale), int tr[wqt][8] (target rows).
+// Origin entries (k, chunk, tile): int2 {first box column (a multiple of 4)
+// or row, 1 if the chunk's windows fit the planned box}.
+// ---------------------------------------------------------------------------
+__global__ void adj_s_table(const SliceParam* __restrict__ prm, int nz, int nx, int wqs, int tiles_x,
+                            float* __restrict__ tab) {
+  const int tx = blockIdx.x, n = blockIdx.y, k = blockIdx.z, c = threadIdx.x;
+  const SliceParam& p = prm[(long long)k * nz + n];
+  const int jx = tx * AX + c, je = min(jx, nx - 1);
+  float* e = tab + (((long long)k * tiles_x + tx) * nz + n) * (wqs * AX + AX);
+  const int i0 = window_start(p.s, je);
+  for (int q = 0; q < wqs; ++q) {
+    float w = 0.0f;
+    if (q < p.wis && jx < nx) {
+      int jc;
+      float fr;
+      footprint_centre(p.s, i0 + q, jc, fr);
+      w = cell_weight(jx - jc, fr, p.s);
+    }
+    e[q * AX + c] = w;
+  }
+  reinterpret_cast<int*>(e + wqs * AX)[c] = i0;
+}
+
+__global__ void adj_t_table(const SliceParam* __restrict__ prm, int nz, int ny, int wqt, int tiles_y,
+                            float* __restrict__ tab) {
+  const int ty = blockIdx.x, n = blockIdx.y, k = blockIdx.z;
+  const SliceParam& p = prm[(long long)k * nz + n];
+  float* e = tab + (((long long)k * tiles_y + ty) * nz + n) * (wqt * AY * 2);
+  for (int t = threadIdx.x; t < wqt * AY; t += blockDim.x) {
+    const int q = t / AY, r = t % AY;
+    const int jy = ty * AY + r, je = min(jy, ny - 1);
+    const int i = window_start(p.t, je) + q;
+    float w = 0.0f;
+    if (q < p.wit && jy < ny) {
+      int jc;
+      float fr;
+      footprint_centre(p.t, i, jc, fr);
+      w = __fmul_rn(cell_weight(jy - jc, fr, p.t), p.scale);
+    }
+    e[q * AY + r] = w;
+    reinterpret_cast<int*>(e + wqt * AY)[q * AY + r] = i;
+  }
+}
+
+// axis 0: columns (x, s), axis 1: rows (y, t).  Thread = tile; the union of
+// the windows of the tile's two end voxels over the chunk's slices.
+// Every table row holds wq (the camera's largest window) entries, so the box
+// reaches wq pixels past each window start.
+__global__ void adj_origins(const SliceParam* __restrict__ prm, int nz, int nvox, int tile, int tiles, int axis,
+                            int wq, int box, int chunks, int2* __restrict__ out, int* __restrict__ bad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ch = blockIdx.y, k = blockIdx.z;
+  if (t >= tiles) return;
+  const int j0 = t * tile, j1 = min(j0 + tile, nvox) - 1;
+  int lo = 0x7fffffff, hi = -0x7fffffff;
+  for (int n = ch * ASC; n < min(ch * ASC + ASC, nz); ++n) {
+    const SliceParam& p = prm[(long long)k * nz + n];
+    const AxisParam& a = axis == 0 ? p.s : p.t;
+    const int s0 = window_start(a, j0), s1 = window_start(a, j1);
+    lo = min(lo, min(s0, s1));
+    hi = max(hi, max(s0, s1) + wq - 1);
+  }
+  const int o = axis == 0 ? (lo & ~3) : lo;   // a TMA box starts on 16 bytes
+  const int ok = hi - o < box;
+  out[((long long)k * chunks + ch) * tiles + t] = make_int2(o, ok);
+  if (!ok) atomicOr(bad, 1);
+}
 
 // The (camera, cell) pairs a CTA visits, in order: cameras of the batch,
 // cells of the subset.
@@ -88,63 +169,56 @@ __device__ __forceinline__ void unit_next(const BeamBatch& B, UnitCursor& u) {
   unit_first(B, u);
 }
 
-// Origin of the image box of (camera, cell) for slices [n0, n0 + ns) of the
-// tile (columns [jx0, jx1], rows [jy0, jy1]), by warp 0 (lane = slice), and
-// its TMA load by lane 0.  Returns through shared memory: origin and fit.
-__device__ __forceinline__ void box_issue(const BeamCam& C, const AdjBatch& A, int cam, int k, int n0, int n_cnt,
-                                          int jx0, int jx1, int jy0, int jy1, int frame, int lane, float* box,
-                                          uint32_t bar, int* org) {
-  int sx_lo = 0x7fffffff, sx_hi = -0x7fffffff, ty_lo = 0x7fffffff, ty_hi = -0x7fffffff;
-  if (lane < n_cnt) {
-    const SliceParam& p = C.prm[(long long)k * C.nz + n0 + lane];
-    const int a0 = window_start(p.s, jx0), a1 = window_start(p.s, jx1);
-    const int b0 = window_start(p.t, jy0), b1 = window_start(p.t, jy1);
-    sx_lo = min(a0, a1);
-    sx_hi = max(a0, a1) + p.wis - 1;
-    ty_lo = min(b0, b1);
-    ty_hi = max(b0, b1) + p.wit - 1;
+// Shared-memory stage of one (camera, cell): the image box, then the
+// chunk's S and T entries (sizes are the launch's largest).
+struct AdjStage {
+  int box_floats, s_bytes, t_bytes;
+  __host__ __device__ size_t bytes() const {
+    return ((size_t)box_floats * 4 + (size_t)ASC * s_bytes + (size_t)ASC * t_bytes + 127) / 128 * 128;
   }
-  sx_lo = __reduce_min_sync(0xffffffffu, sx_lo);
-  sx_hi = __reduce_max_sync(0xffffffffu, sx_hi);
-  ty_lo = __reduce_min_sync(0xffffffffu, ty_lo);
-  ty_hi = __reduce_max_sync(0xffffffffu, ty_hi);
+};
+
+// One thread fills a stage for (camera, cell) and slices [n0, n0 + n_cnt) of
+// the tile (tx, ty); the box origin is returned through `org`.
+__device__ __forceinline__ void adj_issue(const BeamCam& C, const AdjBatch& A, const AdjStage& L, int cam, int k,
+                                          int tx, int ty, int chunk, int n0, int n_cnt, int frame,
+                                          unsigned char* stage, uint32_t bar, int* org) {
+  const int2 ox = __ldg(&A.ox[cam][((long long)k * A.chunks[cam] + chunk) * A.tiles_x[cam] + tx]);
+  const int2 oy = __ldg(&A.oy[cam][((long long)k * A.chunks[cam] + chunk) * A.tiles_y[cam] + ty]);
+  org[0] = ox.x;
+  org[1] = oy.x;
   const int bx = A.bx[cam], by = A.by[cam];
-  const int x0 = sx_lo & ~3;   // a TMA box starts on 16 bytes
-  const bool ok = sx_hi - x0 < bx && ty_hi - ty_lo < by;
-  if (lane == 0) {
-    org[0] = x0;
-    org[1] = ty_lo;
-    org[2] = ok;
-    if (!ok) atomicOr(&g_adjoint_status, 1);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    a_expect_tx(bar, (uint32_t)(bx * by * sizeof(float)));
-    a_tma_3d(smem_addr(box), &A.map[cam], x0, ty_lo, frame * A.zf[cam] + (C.per_cell ? k : 0), bar);
-  }
+  const uint32_t sb = (uint32_t)(A.wqs[cam] * AX + AX) * 4, tb = (uint32_t)(A.wqt[cam] * AY * 2) * 4;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  a_expect_tx(bar, (uint32_t)(bx * by * 4) + n_cnt * (sb + tb));
+  const uint32_t dst = smem_addr(stage);
+  a_tma_3d(dst, &A.map[cam], ox.x, oy.x, frame * A.zf[cam] + (C.per_cell ? k : 0), bar);
+  const char* s_src = reinterpret_cast<const char*>(A.stab[cam]) +
+                      (((long long)k * A.tiles_x[cam] + tx) * C.nz + n0) * (long long)sb;
+  const char* t_src = reinterpret_cast<const char*>(A.ttab[cam]) +
+                      (((long long)k * A.tiles_y[cam] + ty) * C.nz + n0) * (long long)tb;
+  a_bulk(dst + (uint32_t)L.box_floats * 4, s_src, n_cnt * sb, bar);
+  a_bulk(dst + (uint32_t)L.box_floats * 4 + ASC * (uint32_t)L.s_bytes, t_src, n_cnt * tb, bar);
 }
 
-__global__ void __launch_bounds__(AX * AY)
+template <int CI>
+__global__ void __launch_bounds__(AX * AY, 3)
 beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ AdjBatch A, float* __restrict__ x,
-                 long long x_fs, int accumulate, int tiles_x, int box_floats, int ucols) {
+                 long long x_fs, int accumulate, int tiles_x, AdjStage L, int ucols) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  float* boxes = reinterpret_cast<float*>(dsm);                   // [2][box_floats]
-  float* U = boxes + 2 * (size_t)box_floats;                       // [AY][ucols]
-  __shared__ float sw[AWMAX][AX];   // s-window entries of each voxel column
-  __shared__ int si[AX];            // first box column of each voxel column's window
-  __shared__ float tw[AWMAX][AY];   // t-window entries of each voxel row
-  __shared__ int tr[AWMAX][AY];     // their box rows
+  const size_t stage_bytes = L.bytes();
+  float* U = reinterpret_cast<float*>(dsm + 2 * stage_bytes);    // [AY][ucols]
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ int org[2][3];         // box origin (x0, y0) and fit, per buffer
+  __shared__ int org[2][2];         // box origin (x0, y0) per buffer
   __shared__ int s_fail;
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nx = B.cam[0].nx, ny = B.cam[0].ny, nz = B.cam[0].nz;
-  const int jx0 = (blockIdx.x % tiles_x) * AX;
-  const int jy0 = (blockIdx.x / tiles_x) * AY;
-  const int jx1 = min(jx0 + AX, nx) - 1;
-  const int jy1 = min(jy0 + AY, ny) - 1;
-  const int jx = jx0 + lane, jy = jy0 + warp;
-  const int n0 = blockIdx.y * ASC;
+  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+  const int jx = tx * AX + lane, jy = ty * AY + warp;
+  const int chunk = blockIdx.y;
+  const int n0 = chunk * ASC;
   const int n_cnt = min(ASC, nz - n0);
   const int frame = blockIdx.z;
 
@@ -159,81 +233,63 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
 
   UnitCursor cur{0, 0, false};
   unit_first(B, cur);
-  if (cur.valid && warp == 0)
-    box_issue(B.cam[cur.cam], A, cur.cam, cur.k, n0, n_cnt, jx0, jx1, jy0, jy1, frame, lane, boxes,
-              smem_addr(&bars[0]), org[0]);
+  if (cur.valid && threadIdx.x == 0)
+    adj_issue(B.cam[cur.cam], A, L, cur.cam, cur.k, tx, ty, chunk, n0, n_cnt, frame, dsm, smem_addr(&bars[0]),
+              org[0]);
   int u = 0;
-  bool next_issued = false;
   while (cur.valid) {
     const int buf = u & 1;
     UnitCursor nxt = cur;
     unit_next(B, nxt);
-    next_issued = nxt.valid;
-    if (nxt.valid && warp == 0)   // the other buffer was released by the last barrier of unit u - 1
-      box_issue(B.cam[nxt.cam], A, nxt.cam, nxt.k, n0, n_cnt, jx0, jx1, jy0, jy1, frame, lane,
-                boxes + (size_t)(buf ^ 1) * box_floats, smem_addr(&bars[buf ^ 1]), org[buf ^ 1]);
+    if (nxt.valid && threadIdx.x == 0)   // the other buffer was released by the barrier ending unit u - 1
+      adj_issue(B.cam[nxt.cam], A, L, nxt.cam, nxt.k, tx, ty, chunk, n0, n_cnt, frame, dsm + (buf ^ 1) * stage_bytes,
+                smem_addr(&bars[buf ^ 1]), org[buf ^ 1]);
     if (!a_wait(smem_addr(&bars[buf]), (u >> 1) & 1)) {
       if (threadIdx.x == 0) atomicOr(&g_adjoint_status, 2);
       s_fail = 1;
     }
     __syncthreads();
     if (s_fail) {
-      // leave no copy in flight behind: wait (bounded) for the box issued next
-      if (threadIdx.x == 0 && next_issued) a_wait(smem_addr(&bars[buf ^ 1]), ((u + 1) >> 1) & 1);
+      // leave no copy in flight behind: wait (bounded) for the stage issued next
+      if (threadIdx.x == 0 && nxt.valid) a_wait(smem_addr(&bars[buf ^ 1]), ((u + 1) >> 1) & 1);
       break;
     }
-    const BeamCam& C = B.cam[cur.cam];
-    const float* box = boxes + (size_t)buf * box_floats;
-    const int bx = A.bx[cur.cam];
+    const int cam = cur.cam;
+    const unsigned char* stg = dsm + buf * stage_bytes;
+    const float* box = reinterpret_cast<const float*>(stg);
+    const int bx = A.bx[cam], wqs = A.wqs[cam], wqt = A.wqt[cam];
     const int x0 = org[buf][0], y0 = org[buf][1];
-    const bool ok = org[buf][2] != 0;
+    const float* S0 = reinterpret_cast<const float*>(stg + (size_t)L.box_floats * 4);
+    const float* T0 = reinterpret_cast<const float*>(stg + (size_t)L.box_floats * 4 + (size_t)ASC * L.s_bytes);
+    float* Ur = U + warp * ucols;
+#pragma unroll 1
     for (int s = 0; s < n_cnt; ++s) {
-      const SliceParam* p = C.prm + (long long)cur.k * nz + n0 + s;
-      const int wis = min(p->wis, AWMAX), wit = min(p->wit, AWMAX);
-      // window entries: s (column lane, entry q) and t (row r, entry q)
-      for (int task = threadIdx.x; task < AX * wis; task += AX * AY) {
-        const int q = task / AX, c = task % AX;
-        const int j = jx0 + c;
-        const int i0 = window_start(p->s, j);
-        float w = 0.0f;
-        if (ok && j < nx) {
-          int jc;
-          float fr;
-          footprint_centre(p->s, i0 + q, jc, fr);
-          w = cell_weight(j - jc, fr, p->s);
-        }
-        sw[q][c] = w;
-        if (q == 0) si[c] = (ok && j < nx) ? i0 - x0 : 0;
+      // t: this warp's voxel row over every box column
+      const float* T = T0 + s * (wqt * AY * 2);
+      const int* Tr = reinterpret_cast<const int*>(T + wqt * AY);
+      float v[CI];
+#pragma unroll
+      for (int m = 0; m < CI; ++m) v[m] = 0.0f;
+      for (int q = 0; q < wqt; ++q) {
+        const float w = T[q * AY + warp];
+        const float* row = box + (Tr[q * AY + warp] - y0) * bx + lane;
+#pragma unroll
+        for (int m = 0; m < CI; ++m)
+          if (lane + AX * m < bx) v[m] = fmaf(w, row[AX * m], v[m]);
       }
-      for (int task = threadIdx.x; task < AY * wit; task += AX * AY) {
-        const int q = task / AY, r = task % AY;
-        const int j = jy0 + r;
-        const int i = window_start(p->t, j) + q;
-        float w = 0.0f;
-        if (ok && j < ny) {
-          int jc;
-          float fr;
-          footprint_centre(p->t, i, jc, fr);
-          w = cell_weight(j - jc, fr, p->t);
-        }
-        tw[q][r] = w;
-        tr[q][r] = (ok && j < ny) ? i - y0 : 0;
-      }
-      __syncthreads();
-      // t-contraction of this warp's voxel row over every box column
-      for (int c = lane; c < bx; c += AX) {
-        float v = 0.0f;
-        for (int q = 0; q < wit; ++q) v = fmaf(tw[q][warp], box[tr[q][warp] * bx + c], v);
-        U[warp * ucols + c] = v;
-      }
+#pragma unroll
+      for (int m = 0; m < CI; ++m)
+        if (lane + AX * m < bx) Ur[lane + AX * m] = v[m];
       __syncwarp();
-      // s-contraction of this voxel from its row of U
-      const float* Ur = U + warp * ucols + si[lane];
-      float v = 0.0f;
-      for (int q = 0; q < wis; ++q) v = fmaf(sw[q][lane], Ur[q], v);
-      acc[s] = fmaf(p->scale, v, acc[s]);
-      __syncthreads();
+      // s: this voxel from its row of U
+      const float* S = S0 + s * (wqs * AX + AX);
+      const float* Uc = Ur + (reinterpret_cast<const int*>(S + wqs * AX)[lane] - x0);
+      float a = 0.0f;
+      for (int q = 0; q < wqs; ++q) a = fmaf(S[q * AX + lane], Uc[q], a);
+      acc[s] += a;
+      __syncwarp();
     }
+    __syncthreads();   // this buffer may be refilled
     cur = nxt;
     ++u;
   }
@@ -249,8 +305,21 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
   }
 }
 
-size_t adj_smem(int box_floats, int ucols) {
-  return (2 * (size_t)box_floats + (size_t)AY * ucols) * sizeof(float);
+template <int CI>
+const void* adj_kernel() {
+  return (const void*)beam_adjoint_tma<CI>;
+}
+const void* adj_select(int ci) {
+  switch (ci) {
+    case 1: return adj_kernel<1>();
+    case 2: return adj_kernel<2>();
+    case 3: return adj_kernel<3>();
+    case 4: return adj_kernel<4>();
+    case 5: return adj_kernel<5>();
+    case 6: return adj_kernel<6>();
+    case 7: return adj_kernel<7>();
+    default: return adj_kernel<8>();
+  }
 }
 
 }  // namespace
@@ -268,23 +337,51 @@ int adjoint_tile_x() { return AX; }
 int adjoint_tile_y() { return AY; }
 int adjoint_chunk() { return ASC; }
 
+void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, size_t* s_bytes, size_t* t_bytes,
+                         size_t* ox_count, size_t* oy_count) {
+  const long long tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + ASC - 1) / ASC;
+  *s_bytes = (size_t)K * nz * tiles_x * (wqs * AX + AX) * 4;
+  *t_bytes = (size_t)K * nz * tiles_y * (wqt * AY * 2) * 4;
+  *ox_count = (size_t)K * chunks * tiles_x;
+  *oy_count = (size_t)K * chunks * tiles_y;
+}
+
+cudaError_t launch_adjoint_tables(const SliceParam* prm, int K, int nz, int nx, int ny, int wqs, int wqt, int bx,
+                                  int by, float* stab, float* ttab, int2* ox, int2* oy, int* bad, cudaStream_t st) {
+  const int tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + ASC - 1) / ASC;
+  adj_s_table<<<dim3(tiles_x, nz, K), AX, 0, st>>>(prm, nz, nx, wqs, tiles_x, stab);
+  adj_t_table<<<dim3(tiles_y, nz, K), 128, 0, st>>>(prm, nz, ny, wqt, tiles_y, ttab);
+  adj_origins<<<dim3((tiles_x + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, nx, AX, tiles_x, 0, wqs, bx, chunks, ox,
+                                                                   bad);
+  adj_origins<<<dim3((tiles_y + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, ny, AY, tiles_y, 1, wqt, by, chunks, oy,
+                                                                   bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, float* x, long long x_fs, int accumulate,
                                     cudaStream_t st) {
   const int nx = b.cam[0].nx, ny = b.cam[0].ny, nz = b.cam[0].nz;
-  int box = 0, ucols = 32;
+  int box = 0, bxmax = 4, sb = 16, tb = 16;
   for (int c = 0; c < b.n_cams; ++c) {
-    if (b.cam[c].wis > AWMAX || b.cam[c].wit > AWMAX || a.bx[c] <= 0 || a.by[c] <= 0) return cudaErrorInvalidValue;
+    if (a.bx[c] <= 0 || a.by[c] <= 0 || a.wqs[c] > AWMAX || a.wqt[c] > AWMAX) return cudaErrorInvalidValue;
     box = std::max(box, a.bx[c] * a.by[c]);
-    ucols = std::max(ucols, (a.bx[c] + 31) / 32 * 32);
+    bxmax = std::max(bxmax, a.bx[c]);
+    sb = std::max(sb, (a.wqs[c] * AX + AX) * 4);
+    tb = std::max(tb, a.wqt[c] * AY * 2 * 4);
   }
-  const int box_floats = (box + 31) / 32 * 32;
-  const size_t smem = adj_smem(box_floats, ucols);
-  cudaError_t e = cudaFuncSetAttribute(beam_adjoint_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (bxmax > AX * 8) return cudaErrorInvalidValue;
+  AdjStage L{(box + 31) / 32 * 32, sb, tb};
+  int ucols = (bxmax + 31) / 32 * 32;
+  const size_t smem = 2 * L.bytes() + (size_t)AY * ucols * sizeof(float);
+  const void* fn = adj_select((bxmax + AX - 1) / AX);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY;
-  dim3 grid(tiles_x * tiles_y, (nz + ASC - 1) / ASC, b.frames);
-  beam_adjoint_tma<<<grid, AX * AY, smem, st>>>(b, a, x, x_fs, accumulate, tiles_x, box_floats, ucols);
-  return cudaGetLastError();
+  int tiles_x = (nx + AX - 1) / AX;
+  const int tiles_y = (ny + AY - 1) / AY;
+  const dim3 grid(tiles_x * tiles_y, (nz + ASC - 1) / ASC, b.frames);
+  void* args[] = {(void*)&b, (void*)&a, (void*)&x, (void*)&x_fs, (void*)&accumulate, (void*)&tiles_x, (void*)&L,
+                  (void*)&ucols};
+  return cudaLaunchKernel(fn, grid, dim3(AX * AY), args, smem, st);
 }
 
 }  // namespace lt

@@ -70,6 +70,10 @@ struct CameraPlan {
   int tma_bx = 0, tma_by = 0, tma_nb = 0;
   int tma_chunks = 1;              // parts each forward item is split into (few tiles: more CTAs per tile)
   int adj_bx = 0, adj_by = 0;      // box-staged adjoint: image box (0: the direct adjoint serves it)
+  float* d_adj_s = nullptr;        // and its window tables (lt_beam_adj.cu layout)
+  float* d_adj_t = nullptr;
+  int2* d_adj_ox = nullptr;
+  int2* d_adj_oy = nullptr;
   void* d_stab = nullptr;          // its footprint-weight tables (lt_beam_tma.cu layout)
   void* d_ttab = nullptr;
   // plenoptic

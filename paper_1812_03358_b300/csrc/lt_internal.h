@@ -216,20 +216,36 @@ cudaError_t projector_status(int* flags, bool clear);
 // TMA view of each camera's adjoint input (the image plane, or the array
 // plane of every cell) for the box-staged adjoint (lt_beam_adj.cu): a 3-D
 // tensor map over [F * zf][nt][ns] float32 (zf = K per-cell planes or 1),
-// and the image box (bx columns, a multiple of 4, by rows) the planner sized
-// for the camera's voxel tiles and slice chunks.
+// the image box (bx columns, a multiple of 4, by rows) the planner sized for
+// the camera's voxel tiles and slice chunks, and the camera's plan-built
+// window tables (wqs / wqt entries per voxel column / row).
 struct AdjBatch {
   CUtensorMap map[kMaxBatchCams];
+  const float* stab[kMaxBatchCams];
+  const float* ttab[kMaxBatchCams];
+  const int2* ox[kMaxBatchCams];
+  const int2* oy[kMaxBatchCams];
   int32_t bx[kMaxBatchCams];
   int32_t by[kMaxBatchCams];
   int32_t zf[kMaxBatchCams];
+  int32_t wqs[kMaxBatchCams];
+  int32_t wqt[kMaxBatchCams];
+  int32_t tiles_x[kMaxBatchCams];
+  int32_t tiles_y[kMaxBatchCams];
+  int32_t chunks[kMaxBatchCams];
 };
 // Box-staged adjoint: voxel tile adjoint_tile_x() x adjoint_tile_y(),
 // adjoint_chunk() slices per CTA; x[F][nz][ny][nx] (= or +=) the sum over
-// the batch's cameras and cells.
+// the batch's cameras and cells.  Tables: adjoint_table_sizes gives the
+// bytes of the S and T tables and the origin counts of one camera;
+// launch_adjoint_tables fills them and sets *bad if a box does not fit.
 int adjoint_tile_x();
 int adjoint_tile_y();
 int adjoint_chunk();
+void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, size_t* s_bytes, size_t* t_bytes,
+                         size_t* ox_count, size_t* oy_count);
+cudaError_t launch_adjoint_tables(const SliceParam* prm, int K, int nz, int nx, int ny, int wqs, int wqt, int bx,
+                                  int by, float* stab, float* ttab, int2* ox, int2* oy, int* bad, cudaStream_t st);
 cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, float* x, long long x_fs, int accumulate,
                                     cudaStream_t st);
 // Status word of the box-staged adjoint (bits as the forward's).

@@ -270,6 +270,10 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.d_fa);
   cudaFree(c.d_stab);
   cudaFree(c.d_ttab);
+  cudaFree(c.d_adj_s);
+  cudaFree(c.d_adj_t);
+  cudaFree(c.d_adj_ox);
+  cudaFree(c.d_adj_oy);
   c = CameraPlan();
 }
 
@@ -322,14 +326,14 @@ static void plan_bricks(CameraPlan& c, int grid_nx, const std::vector<Footprint>
 // Image box of the box-staged adjoint for camera c: per (cell, chunk of
 // adjoint_chunk() slices, tile of adjoint_tile_x() x adjoint_tile_y()
 // voxels), the target pixels the tile's windows reach, [first window start,
-// last window start + window - 1] per axis over the chunk's slices (window
+// last window start + largest window - 1] per axis over the chunk's slices (window
 // starts floor(min(lo, hi)) - 1 of (j -+ 1/2 -+ Q - c0) / c1 at the tile's
 // two ends, widened by 1e-3), the columns rounded to a multiple of 4.  The
 // box is the largest span; cameras whose box exceeds 8192 floats keep the
 // direct adjoint, and so do cameras whose target rows are not a multiple of
 // 4 floats.
 static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns, const std::vector<Footprint>& fps,
-                             const std::vector<Footprint>& fpt, const std::vector<SliceParam>& sp) {
+                             const std::vector<Footprint>& fpt) {
   c.adj_bx = c.adj_by = 0;
   if (tgt_ns % 4 != 0) return;   // a TMA row stride is a multiple of 16 bytes
   const int TX = adjoint_tile_x(), TY = adjoint_tile_y(), SC = adjoint_chunk();
@@ -347,7 +351,7 @@ static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns,
           const size_t q = (size_t)k * v.nz + n;
           for (int j : {j0, j1}) {
             lo = std::min(lo, start(fps[q], j, -1e-3));
-            hi = std::max(hi, start(fps[q], j, 1e-3) + sp[q].wis - 1);
+            hi = std::max(hi, start(fps[q], j, 1e-3) + c.wimax_s - 1);
           }
         }
         need_bx = std::max(need_bx, hi - (lo & ~3LL) + 1);
@@ -359,7 +363,7 @@ static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns,
           const size_t q = (size_t)k * v.nz + n;
           for (int j : {j0, j1}) {
             lo = std::min(lo, start(fpt[q], j, -1e-3));
-            hi = std::max(hi, start(fpt[q], j, 1e-3) + sp[q].wit - 1);
+            hi = std::max(hi, start(fpt[q], j, 1e-3) + c.wimax_t - 1);
           }
         }
         need_by = std::max(need_by, hi - lo + 1);
@@ -369,6 +373,50 @@ static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns,
   if (bx < 4 || by < 1 || bx > 256 || by > 256 || bx * by > 8192 || c.wimax_s > 32 || c.wimax_t > 32) return;
   c.adj_bx = (int)bx;
   c.adj_by = (int)by;
+}
+
+// Window tables and box origins of the box-staged adjoint, built on the
+// device from the slice parameters; a camera whose tables exceed
+// kMaxTableBytes, or whose boxes do not fit (reported by the build), keeps
+// the direct adjoint.
+static lt_status plan_adjoint_tables(CameraPlan& c, const lt_volume_desc& v, int idx) {
+  constexpr size_t kMaxTableBytes = (size_t)512 << 20;
+  if (c.adj_bx == 0 || !tma_forward_available()) {
+    c.adj_bx = c.adj_by = 0;
+    return LT_OK;
+  }
+  size_t sb, tb, nox, noy;
+  adjoint_table_sizes(c.K, v.nz, v.nx, v.ny, c.wimax_s, c.wimax_t, &sb, &tb, &nox, &noy);
+  if (sb + tb > kMaxTableBytes) {
+    c.adj_bx = c.adj_by = 0;
+    return LT_OK;
+  }
+  int* d_bad = nullptr;
+  if (device_alloc((void**)&c.d_adj_s, sb) != cudaSuccess || device_alloc((void**)&c.d_adj_t, tb) != cudaSuccess ||
+      device_alloc((void**)&c.d_adj_ox, nox * sizeof(int2)) != cudaSuccess ||
+      device_alloc((void**)&c.d_adj_oy, noy * sizeof(int2)) != cudaSuccess ||
+      device_alloc((void**)&d_bad, sizeof(int)) != cudaSuccess) {
+    cudaFree(d_bad);
+    return set_error(LT_ENOMEM, "camera %d: cudaMalloc(adjoint window tables, %zu bytes)", idx, sb + tb);
+  }
+  int bad = 0;
+  cudaError_t e = cudaMemset(d_bad, 0, sizeof(int));
+  if (e == cudaSuccess)
+    e = launch_adjoint_tables(c.d_slice, c.K, v.nz, v.nx, v.ny, c.wimax_s, c.wimax_t, c.adj_bx, c.adj_by, c.d_adj_s,
+                              c.d_adj_t, c.d_adj_ox, c.d_adj_oy, d_bad, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_bad);
+  if (e != cudaSuccess) return cuda_error(e, "adjoint window tables");
+  if (bad) {   // a box the planner sized too small: the direct adjoint serves this camera
+    cudaFree(c.d_adj_s);
+    cudaFree(c.d_adj_t);
+    cudaFree(c.d_adj_ox);
+    cudaFree(c.d_adj_oy);
+    c.d_adj_s = c.d_adj_t = nullptr;
+    c.d_adj_ox = c.d_adj_oy = nullptr;
+    c.adj_bx = c.adj_by = 0;
+  }
+  return LT_OK;
 }
 
 // Footprint-weight tables of the brick-staged forward (one entry per
@@ -476,7 +524,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
   plan_bricks(c, v.nx, fps, fpt, tiles_s, tiles_t);
-  plan_adjoint_box(c, v, tgt_ns, fps, fpt, sp);
+  plan_adjoint_box(c, v, tgt_ns, fps, fpt);
   for (auto& r : srange)
     if (r.y < 0) r = make_int2(0, 0);
   for (auto& r : trange)
@@ -513,7 +561,9 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
   if (s != LT_OK) return s;
   s = upload(sp, &c.d_slice, "slice parameters");
   if (s != LT_OK) return s;
-  return plan_weight_tables(c, v.nz, idx);
+  s = plan_weight_tables(c, v.nz, idx);
+  if (s != LT_OK) return s;
+  return plan_adjoint_tables(c, v, idx);
 }
 
 // Array -> detector stage of a plenoptic camera (Sec. II-D, II-F2).
@@ -1383,9 +1433,18 @@ static lt_status run_adjoint(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       ok = c.adj_bx > 0 && (!bc.per_cell || bc.out_fs == plane * bc.K) &&
            tma_encode_planes(&a.map[i], bc.in, bc.ns, bc.nt, b.frames * (bc.per_cell ? bc.K : 1),
                              bc.per_cell ? plane : bc.out_fs, c.adj_bx, c.adj_by);
+      a.stab[i] = c.d_adj_s;
+      a.ttab[i] = c.d_adj_t;
+      a.ox[i] = c.d_adj_ox;
+      a.oy[i] = c.d_adj_oy;
       a.bx[i] = c.adj_bx;
       a.by[i] = c.adj_by;
       a.zf[i] = bc.per_cell ? bc.K : 1;
+      a.wqs[i] = c.wimax_s;
+      a.wqt[i] = c.wimax_t;
+      a.tiles_x[i] = (bc.nx + adjoint_tile_x() - 1) / adjoint_tile_x();
+      a.tiles_y[i] = (bc.ny + adjoint_tile_y() - 1) / adjoint_tile_y();
+      a.chunks[i] = (bc.nz + adjoint_chunk() - 1) / adjoint_chunk();
     }
     if (ok) {
       cudaError_t e = launch_beam_adjoint_tma(b, a, x, x_fs, accumulate, st);
