@@ -23,8 +23,9 @@ struct Scalars {
   long long iter;  // completed iterations
 };
 
-constexpr int RED_BLOCKS = 148;
-constexpr int RED_THREADS = 1024;   // 32 warps per SM: the reductions are latency-bound
+// Reductions use one block per SM (the plan's SM count, nb below) of
+// RED_THREADS threads: 32 warps per SM, since they are latency-bound.
+constexpr int RED_THREADS = 1024;
 
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -37,8 +38,8 @@ __device__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// part[(f*C + c)*RED_BLOCKS + b] = sum over block b's share of camera c's
-// pixels of w * a * b (w = 1 if NULL).  grid = (RED_BLOCKS, F).
+// part[(f*C + c)*nb + b] = sum over block b's share of camera c's pixels of
+// w * a * b (w = 1 if NULL).  grid = (nb, F).
 __global__ void __launch_bounds__(RED_THREADS)
 dot_partials(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ w,
              long long off, long long len, long long m_total, int C, int c, double* __restrict__ part,
@@ -52,7 +53,7 @@ dot_partials(const float* __restrict__ a, const float* __restrict__ b, const flo
     acc += wi * (double)a[base + i] * (double)b[base + i];
   }
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[((long long)blockIdx.y * C + c) * RED_BLOCKS + blockIdx.x] = scale * acc;
+  if (threadIdx.x == 0) part[((long long)blockIdx.y * C + c) * gridDim.x + blockIdx.x] = scale * acc;
 }
 
 // Table V step 1b (gamma_c = y^T W p / y^T W y, c > 0) and the FISTA scalars
@@ -69,7 +70,7 @@ __device__ __forceinline__ void fista_advance(Scalars* sc) {
 }
 
 __global__ void finalize_gains(const double* __restrict__ part, const double* __restrict__ ywy,
-                               double* __restrict__ gains, int F, int C, int estimate,
+                               double* __restrict__ gains, int F, int C, int estimate, int nb,
                                Scalars* __restrict__ sc) {
   for (int idx = threadIdx.x; idx < F * C; idx += blockDim.x) {
     const int c = idx % C;
@@ -78,7 +79,7 @@ __global__ void finalize_gains(const double* __restrict__ part, const double* __
       continue;
     }
     double s = 0.0;
-    for (int b = 0; b < RED_BLOCKS; ++b) s += part[(long long)idx * RED_BLOCKS + b];
+    for (int b = 0; b < nb; ++b) s += part[(long long)idx * nb + b];
     gains[idx] = ywy[idx] > 0.0 ? s / ywy[idx] : 0.0;
   }
   if (threadIdx.x == 0) fista_advance(sc);
@@ -86,7 +87,7 @@ __global__ void finalize_gains(const double* __restrict__ part, const double* __
 
 // d = a p - gamma_c y over camera c's pixels, r = a W d (a = K_c / |S_c| of
 // the view subset, 1 without subsets); fit partials of 1/2 sum W d^2.
-// grid = (RED_BLOCKS, F).
+// grid = (nb, F).
 __global__ void __launch_bounds__(RED_THREADS)
 residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const float* __restrict__ p,
                 float* __restrict__ r, const double* __restrict__ gains, long long off, long long len,
@@ -105,7 +106,7 @@ residual_kernel(const float* __restrict__ y, const float* __restrict__ w, const 
     acc += (double)(wi * d * d);   // the term in float32 (FP64 units are scarce), the sum in float64
   }
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) fit_part[((long long)blockIdx.y * C + c) * RED_BLOCKS + blockIdx.x] = 0.5 * acc;
+  if (threadIdx.x == 0) fit_part[((long long)blockIdx.y * C + c) * gridDim.x + blockIdx.x] = 0.5 * acc;
 }
 
 // Table V step 3: w = [z - (D + s beta)^-1 (g + grad R(z))]_+, x' = [w - nu]_+,
@@ -225,20 +226,20 @@ update_kernel(float* __restrict__ x, const float* __restrict__ z, float* __restr
 // res[F + f * C + c] = gains[f * C + c].  grid = F, one block per frame.
 __global__ void __launch_bounds__(256)
 finalize_result(const double* __restrict__ fit_part, const double* __restrict__ gains, double* __restrict__ res,
-                int F, int C) {
+                int F, int C, int nb) {
   __shared__ double sh[32];
   const int f = blockIdx.x;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < C * RED_BLOCKS; i += blockDim.x) acc += fit_part[(long long)f * C * RED_BLOCKS + i];
+  for (int i = threadIdx.x; i < C * nb; i += blockDim.x) acc += fit_part[(long long)f * C * nb + i];
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) res[f] = acc;
   for (int c = threadIdx.x; c < C; c += blockDim.x) res[F + f * C + c] = gains[f * C + c];
 }
 
-__global__ void finalize_dots(const double* __restrict__ part, double* __restrict__ out, int n) {
+__global__ void finalize_dots(const double* __restrict__ part, double* __restrict__ out, int n, int nb) {
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     double acc = 0.0;
-    for (int b = 0; b < RED_BLOCKS; ++b) acc += part[(long long)idx * RED_BLOCKS + b];
+    for (int b = 0; b < nb; ++b) acc += part[(long long)idx * nb + b];
     out[idx] = acc;
   }
 }
@@ -262,6 +263,7 @@ struct lt_recon {
   lt_plan* plan = nullptr;
   lt_recon_params prm{};
   int F = 0, C = 0;
+  int nb = 1;                                      // reduction blocks: one per SM
   int64_t N = 0, M = 0;
   float *y = nullptr, *w = nullptr, *p = nullptr, *r = nullptr, *g = nullptr, *D = nullptr, *x = nullptr;
   float* z[2] = {nullptr, nullptr};
@@ -319,13 +321,13 @@ static lt_status recon_step(lt_recon* R, int sel, int sub, cudaStream_t st) {
   const int est = R->prm.estimate_gains && R->C > 1;
   if (est)  // step 1b inner products (of the scaled subset projection)
     for (int c = 1; c < R->C; ++c)
-      dot_partials<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
+      dot_partials<<<dim3(R->nb, R->F), RED_THREADS, 0, st>>>(
           R->y, R->p, R->w, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->part, subset_scale(R, c, sub));
   // without estimation the gains keep their initial values (1), and the
   // FISTA scalars advance in the first residual block instead
-  if (est) finalize_gains<<<1, 256, 0, st>>>(R->part, R->ywy, R->gains, R->F, R->C, est, R->sc);
+  if (est) finalize_gains<<<1, 256, 0, st>>>(R->part, R->ywy, R->gains, R->F, R->C, est, R->nb, R->sc);
   for (int c = 0; c < R->C; ++c)  // a W (a p - gamma y)
-    residual_kernel<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(
+    residual_kernel<<<dim3(R->nb, R->F), RED_THREADS, 0, st>>>(
         R->y, R->w, R->p, R->r, R->gains, P->cams[c].offset, P->cams[c].M, R->M, R->C, c, R->fit_part,
         (float)subset_scale(R, c, sub), !est && c == 0 ? R->sc : nullptr);
   s = plan_adjoint(P, R->r, R->g, st, ss);  // step 1c + 2: g = sum_c A_c^T r_c
@@ -358,9 +360,9 @@ static lt_status load_data(lt_recon* R, const float* y, const float* w, bool new
     if (s != LT_OK) return s;
   }
   for (int c = 0; c < R->C; ++c)
-    dot_partials<<<dim3(RED_BLOCKS, R->F), RED_THREADS, 0, st>>>(R->y, R->y, R->w, P->cams[c].offset,
+    dot_partials<<<dim3(R->nb, R->F), RED_THREADS, 0, st>>>(R->y, R->y, R->w, P->cams[c].offset,
                                                                  P->cams[c].M, R->M, R->C, c, R->part, 1.0);
-  finalize_dots<<<1, 256, 0, st>>>(R->part, R->ywy, R->F * R->C);
+  finalize_dots<<<1, 256, 0, st>>>(R->part, R->ywy, R->F * R->C, R->nb);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LT_OK : cuda_error(e, "loading measurements");
 }
@@ -388,6 +390,7 @@ extern "C" lt_status lt_recon_create(lt_plan* plan, const float* y, const float*
   R->exec.assign(2 * (size_t)R->n_sub, nullptr);
   R->F = plan->frames;
   R->C = (int)plan->cams.size();
+  R->nb = plan->sms > 0 ? plan->sms : 1;
   R->N = plan->nvox;
   R->M = plan->m_total;
   const size_t FN = (size_t)R->F * R->N, FM = (size_t)R->F * R->M;
@@ -396,8 +399,8 @@ extern "C" lt_status lt_recon_create(lt_plan* plan, const float* y, const float*
       (s = dalloc(&R->r, FM, "r")) || (s = dalloc(&R->g, FN, "g")) || (s = dalloc(&R->D, FN, "D")) ||
       (s = dalloc(&R->x, FN, "x")) || (s = dalloc(&R->z[0], FN, "z")) || (s = dalloc(&R->z[1], FN, "z")) ||
       (s = dalloc(&R->ywy, (size_t)R->F * R->C, "ywy")) || (s = dalloc(&R->gains, (size_t)R->F * R->C, "gains")) ||
-      (s = dalloc(&R->part, (size_t)R->F * R->C * RED_BLOCKS, "partials")) ||
-      (s = dalloc(&R->fit_part, (size_t)R->F * R->C * RED_BLOCKS, "fit partials")) ||
+      (s = dalloc(&R->part, (size_t)R->F * R->C * R->nb, "partials")) ||
+      (s = dalloc(&R->fit_part, (size_t)R->F * R->C * R->nb, "fit partials")) ||
       (s = dalloc(&R->res, (size_t)R->F * (R->C + 1), "results")) ||
       (s = dalloc(&R->sc, 1, "scalars"))) {
     recon_free(R);
@@ -416,7 +419,7 @@ extern "C" lt_status lt_recon_create(lt_plan* plan, const float* y, const float*
   Scalars sc0{1.0, 0.0, 0};
   cudaMemcpy(R->gains, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(R->sc, &sc0, sizeof(sc0), cudaMemcpyHostToDevice);
-  cudaMemset(R->fit_part, 0, (size_t)R->F * R->C * RED_BLOCKS * sizeof(double));
+  cudaMemset(R->fit_part, 0, (size_t)R->F * R->C * R->nb * sizeof(double));
   if (x0) {
     cudaMemcpy(R->x, x0, FN * sizeof(float), cudaMemcpyDeviceToDevice);
     cudaMemcpy(R->z[0], x0, FN * sizeof(float), cudaMemcpyDeviceToDevice);
@@ -492,7 +495,7 @@ extern "C" lt_status lt_recon_get(lt_recon* R, float* x, double* gains, double* 
   const size_t FN = (size_t)R->F * R->N;
   if (x) cudaMemcpyAsync(x, R->x, FN * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (gains || data_fit) {
-    std::vector<double> g((size_t)R->F * R->C), fp((size_t)R->F * R->C * RED_BLOCKS);
+    std::vector<double> g((size_t)R->F * R->C), fp((size_t)R->F * R->C * R->nb);
     cudaMemcpyAsync(g.data(), R->gains, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(fp.data(), R->fit_part, fp.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
@@ -502,7 +505,7 @@ extern "C" lt_status lt_recon_get(lt_recon* R, float* x, double* gains, double* 
       for (int f = 0; f < R->F; ++f) {
         double acc = 0.0;
         for (int c = 0; c < R->C; ++c)
-          for (int b = 0; b < RED_BLOCKS; ++b) acc += fp[((size_t)f * R->C + c) * RED_BLOCKS + b];
+          for (int b = 0; b < R->nb; ++b) acc += fp[((size_t)f * R->C + c) * R->nb + b];
         data_fit[f] = acc;
       }
   }
@@ -514,7 +517,7 @@ extern "C" lt_status lt_recon_get_async(lt_recon* R, double* host_out, void* str
   clear_error();
   if (!R || !host_out) return set_error(LT_EINVAL, "recon and host_out are required");
   cudaStream_t st = (cudaStream_t)stream;
-  finalize_result<<<R->F, 256, 0, st>>>(R->fit_part, R->gains, R->res, R->F, R->C);
+  finalize_result<<<R->F, 256, 0, st>>>(R->fit_part, R->gains, R->res, R->F, R->C, R->nb);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(host_out, R->res, (size_t)R->F * (R->C + 1) * sizeof(double), cudaMemcpyDeviceToHost, st);
