@@ -234,11 +234,14 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
+KERNEL_SOURCE = {"beam_forward_tma": "lt_beam_tma.cu", "beam_adjoint_tma": "lt_beam_adj.cu"}
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel source has not changed since the counters were taken."""
+    kernel's source file has not changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    src = os.path.join(ROOT, "paper_1812_03358_b300", "csrc", "lt_kernels.cu")
+    src = os.path.join(ROOT, "paper_1812_03358_b300", "csrc", KERNEL_SOURCE.get(kernel, "lt_kernels.cu"))
     try:
         rec = json.load(open(path))
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
@@ -636,10 +639,12 @@ def run_ours(args):
     }
     levels = {name: level_roofline(stage_ms[name], *work[name], peaks) for name in stage_ms}
     dom = max(stage_ms, key=stage_ms.get)
-    kname = {"beam_forward (stage 1, slices->array)": "beam_forward_batched",
+    kname = {"beam_forward (stage 1, slices->array)":
+             "beam_forward_tma" if stats["forward_brick"] > 0 and tuned == 5 else "beam_forward_batched",
              "stage2_forward (array->detector)": "stage2_lenslet_forward",
              "stage2_adjoint (detector->array)": "stage2_lenslet_adjoint",
-             "beam_adjoint (stage 1^T, array->voxels)": "beam_adjoint_batched"}[dom]
+             "beam_adjoint (stage 1^T, array->voxels)":
+             "beam_adjoint_tma" if stats["adjoint_box"] > 0 else "beam_adjoint_batched"}[dom]
     lv = levels[dom]
     mem = lv["memory_level"]
     peak = {"dram": peaks["hbm_GBps"], "l2": peaks["l2_GBps"], "smem": peaks["smem_GBps"]}[mem]
