@@ -236,13 +236,6 @@ LT_API lt_status lt_projector_status(int32_t* flags, int32_t clear);
  * order differs).  LT_EINVAL for another value. */
 LT_API lt_status lt_plan_set_adjoint_variant(lt_plan* plan, int32_t variant);
 
-/* Fault injection for tests (no counterpart in the paper): the n-th device
- * allocation the library makes from now on fails as if the device were out
- * of memory (n >= 1); n <= 0 turns the injection off.  The failing call
- * returns LT_ENOMEM through its normal error path and frees what it had
- * allocated.  Host-side only: nothing faults. */
-LT_API void lt_test_fail_allocation_after(int32_t n);
-
 /* Analytic work counts of one camera for one frame, computed on the host in
  * float64 from the plan's footprints (used for throughput and roofline
  * figures).  A ray-sample is one (beam, slice) pair: a beam is a target pixel

@@ -57,13 +57,6 @@ LT_API lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const fl
  * gave up (that CTA's outputs were not written). */
 LT_API lt_status lt_nn_device_status(void* stream);
 
-/* Fault injection for tests: with on != 0 the tcgen05 convolution kernels
- * issue no tensor-core work, so their bounded mbarrier waits (shortened to
- * 4096 polls) run out; each CTA then records LT_ETIMEOUT for
- * lt_nn_device_status and writes no output.  Nothing is left in flight.
- * on == 0 restores normal operation.  Synchronises the stream. */
-LT_API lt_status lt_nn_test_stall_tensor_core(int32_t on, void* stream);
-
 /* Weight gradient: dw[co][tap][ci] += sum_v g[v][co] in[v + tap][ci] (float32
  * accumulate, dw must be zeroed by the caller) and db[co] += sum_v g[v][co]
  * (db may be NULL).  g has Co channels per voxel. */

@@ -2,7 +2,11 @@
 
     python -m paper_1812_03358_b300.build
 
-produces paper_1812_03358_b300/_lib/liblt.so from csrc/*.cu and csrc/*.cpp.
+produces paper_1812_03358_b300/_lib/liblt.so from csrc/*.cu and csrc/*.cpp,
+and beside it the test build _lib/liblt_testhooks.so (the same sources with
+-DLT_TEST_HOOKS: it adds the fault-injection entry points of
+include/lt_testing.h, which the product library does not carry).  The two
+are compiled concurrently.
 """
 import glob
 import os
@@ -15,6 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "liblt.so")
+TEST_LIB = os.path.join(LIBDIR, "liblt_testhooks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -34,29 +39,42 @@ def headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in sources() + headers() + [__file__])
 
 
+def _command(out, verbose, extra):
+    return [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+            "-Xcompiler", "-fvisibility=hidden", "-Xptxas", "-v" if verbose else "-O3",
+            "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra,
+            *sources(), "-o", out, "-lcudart"]
+
+
 def build(force=False, verbose=False, extra=()):
-    if not force and up_to_date():
-        return LIB
+    """Builds whichever of liblt.so and liblt_testhooks.so is out of date;
+    returns the product library's path."""
     os.makedirs(LIBDIR, exist_ok=True)
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fvisibility=hidden", "-Xptxas", "-v" if verbose else "-O3",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra,
-           *sources(), "-o", tmp, "-lcudart"]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building liblt.so")
-    if verbose:
-        sys.stderr.write(res.stderr)
-    os.replace(tmp, LIB)
+    jobs = []
+    for lib, flags in ((LIB, ()), (TEST_LIB, ("-DLT_TEST_HOOKS",))):
+        if force or not up_to_date(lib):
+            tmp = lib + ".tmp"
+            jobs.append((lib, tmp, subprocess.Popen(_command(tmp, verbose, (*flags, *extra)),
+                                                    stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    failed = None
+    for lib, tmp, proc in jobs:
+        out, err = proc.communicate()
+        if proc.returncode != 0:
+            failed = failed or (lib, out + err)
+            continue
+        if verbose:
+            sys.stderr.write(err)
+        os.replace(tmp, lib)
+    if failed:
+        sys.stderr.write(failed[1])
+        raise RuntimeError(f"nvcc failed building {os.path.basename(failed[0])}")
     return LIB
 
 

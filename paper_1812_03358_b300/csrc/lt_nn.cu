@@ -11,6 +11,7 @@
 #include "lt.h"
 #include "lt_host.h"
 #include "lt_nn.h"
+#include "lt_testing.h"
 #include "lt_nn_tc.h"
 #include "lt_async.cuh"
 
@@ -712,11 +713,13 @@ extern "C" lt_status lt_nn_device_status(void* stream) {
   return LT_OK;
 }
 
+#ifdef LT_TEST_HOOKS
 extern "C" lt_status lt_nn_test_stall_tensor_core(int32_t on, void* stream) {
   clear_error();
   const cudaError_t e = set_tc_stall(on, (cudaStream_t)stream);
   return e == cudaSuccess ? LT_OK : cuda_error(e, "tensor-core stall hook");
 }
+#endif
 
 extern "C" lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const float* b, uint16_t* out_bf,
                                      float* out_f, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,

@@ -71,9 +71,14 @@ __host__ __device__ constexpr int tc_smem_bytes() {
 }
 
 __device__ int g_tc_status;   // LT_ETIMEOUT after a bounded wait gave up
-// Test hook (lt_nn_test_stall_tensor_core): no MMA is issued, so every wait
-// runs out, after g_tc_wait_limit polls.
+// Test hook (lt_nn_test_stall_tensor_core, test builds only): no MMA is
+// issued, so every wait runs out, after g_tc_wait_limit polls.
+#ifdef LT_TEST_HOOKS
 __device__ int g_tc_stall = 0;
+#define LT_TC_STALL (g_tc_stall != 0)
+#else
+#define LT_TC_STALL false
+#endif
 __device__ long long g_tc_wait_limit = kWaitLimit;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -196,7 +201,7 @@ conv3d_tc_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, const 
   const uint32_t tbase = *tslot;
 
   const int chunks = Ci / 16;
-  const bool stall = g_tc_stall != 0;
+  const bool stall = LT_TC_STALL;
   bool ok = true;
   for (int c = 0; c < chunks && ok; ++c) {
     if (c > 0) {   // the tensor core has finished reading the previous chunk's tiles
@@ -398,7 +403,7 @@ conv3d_tc_zwalk_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, 
     }
     mma_commit(bar);
   };
-  const bool stall = g_tc_stall != 0;
+  const bool stall = LT_TC_STALL;
   if (tid == 0 && !stall) issue(z0);
 
   bool ok = true;
@@ -567,6 +572,7 @@ cudaError_t launch_conv3d_tc(const uint16_t* in, const uint16_t* w, const float*
   return launch_tm<64>(nb, i_, w_, b, o_, out_f, grid, D, H, W, Ci, Co, o_stride, o_off, relu, tx, ty, vec, st);
 }
 
+#ifdef LT_TEST_HOOKS
 cudaError_t set_tc_stall(int on, cudaStream_t st) {
   const int v = on ? 1 : 0;
   const long long limit = on ? (1LL << 12) : kWaitLimit;
@@ -575,6 +581,7 @@ cudaError_t set_tc_stall(int on, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_wait_limit, &limit, sizeof(limit));
   return e;
 }
+#endif
 
 cudaError_t take_tc_status(int* status, cudaStream_t st) {
   const int zero = 0;

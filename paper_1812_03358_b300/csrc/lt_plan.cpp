@@ -4,6 +4,7 @@
 #include "lt.h"
 #include "lt_internal.h"
 #include "lt_host.h"
+#include "lt_testing.h"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -30,11 +31,14 @@ thread_local std::string g_last_error;
 
 namespace lt {
 
+#ifdef LT_TEST_HOOKS
 namespace {
 std::atomic<int> g_fail_alloc_in{0};   // > 0: the allocation that brings it to 0 fails
 }  // namespace
+#endif
 
 cudaError_t device_alloc(void** p, size_t bytes) {
+#ifdef LT_TEST_HOOKS
   int n = g_fail_alloc_in.load();
   while (n > 0) {
     if (g_fail_alloc_in.compare_exchange_weak(n, n - 1)) {
@@ -45,6 +49,7 @@ cudaError_t device_alloc(void** p, size_t bytes) {
       break;
     }
   }
+#endif
   return cudaMalloc(p, bytes);
 }
 
@@ -1620,7 +1625,9 @@ static lt_status check_plenoptic(const lt_plan* p, int cam) {
   return LT_OK;
 }
 
+#ifdef LT_TEST_HOOKS
 extern "C" void lt_test_fail_allocation_after(int32_t n) { g_fail_alloc_in.store(n > 0 ? n : 0); }
+#endif
 
 extern "C" lt_status lt_forward(lt_plan* plan, const float* x, float* y, void* stream) {
   clear_error();

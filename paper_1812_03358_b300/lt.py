@@ -15,7 +15,11 @@ import numpy as np
 
 from . import inputs
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblt.so")
+# The product library; with LT_TEST_HOOKS=1 in the environment the test build
+# (the same library plus the fault-injection entry points of
+# include/lt_testing.h) is loaded instead.
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib",
+                        "liblt_testhooks.so" if os.environ.get("LT_TEST_HOOKS") == "1" else "liblt.so")
 
 LT_OK, LT_EINVAL, LT_ENOMEM, LT_ECUDA, LT_EUNSUPPORTED, LT_ETIMEOUT = range(6)
 
@@ -96,7 +100,6 @@ _SIGS = {
     "lt_plan_set_forward_variant": (c_int32, [c_void_p, c_int32]),
     "lt_projector_status": (c_int32, [POINTER(c_int32), c_int32]),
     "lt_plan_set_adjoint_variant": (c_int32, [c_void_p, c_int32]),
-    "lt_test_fail_allocation_after": (None, [c_int32]),
     "lt_last_error": (c_char_p, []),
     "lt_peak_smem_read": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
     "lt_peak_l2_read": (c_int32, [c_void_p, c_int64, c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
@@ -116,6 +119,9 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        if hasattr(L, "lt_test_fail_allocation_after"):   # the test build
+            L.lt_test_fail_allocation_after.restype = None
+            L.lt_test_fail_allocation_after.argtypes = [c_int32]
         _lib = L
     return _lib
 
@@ -244,8 +250,8 @@ def lt_plan_autotune(plan, stream: int = 0):
 
 
 def lt_test_fail_allocation_after(n: int) -> None:
-    """Fault injection for tests: the n-th device allocation from now on fails
-    (LT_ENOMEM); n <= 0 turns it off."""
+    """Fault injection (test build only, LT_TEST_HOOKS=1): the n-th device
+    allocation from now on fails (LT_ENOMEM); n <= 0 turns it off."""
     lib().lt_test_fail_allocation_after(int(n))
 
 

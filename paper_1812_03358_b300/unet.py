@@ -28,7 +28,6 @@ _SIGS = {
     "lt_nn_conv3d_ex": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
                         c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
     "lt_nn_device_status": [c_void_p],
-    "lt_nn_test_stall_tensor_core": [c_int32, c_void_p],
     "lt_nn_conv3d_wgrad": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
                            c_void_p],
     "lt_nn_conv3d_flip": [c_void_p, c_void_p, c_int32, c_int32, c_void_p],
@@ -60,6 +59,9 @@ def nn():
             fn = getattr(L, name)
             fn.restype = c_int32
             fn.argtypes = args
+        if hasattr(L, "lt_nn_test_stall_tensor_core"):   # the test build
+            L.lt_nn_test_stall_tensor_core.restype = c_int32
+            L.lt_nn_test_stall_tensor_core.argtypes = [c_int32, c_void_p]
         _bound = True
     return L
 

@@ -12,9 +12,13 @@ from paper_1812_03358_b300 import build, inputs as I, lt
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
+def declared_symbols(testing=False):
+    """lt_* entry points of include/*.h; the fault-injection header
+    (lt_testing.h) only for the test build."""
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        if os.path.basename(h) == "lt_testing.h" and not testing:
+            continue
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         names.update(re.findall(r"\b(lt_\w+)\s*\(", text))
@@ -34,12 +38,20 @@ def test_every_declared_symbol_is_exported(library):
     assert not missing, missing
 
 
-def test_only_declared_symbols_are_exported(library):
+def _exported(path):
     import subprocess
-    out = subprocess.run(["nm", "-D", "--defined-only", lt.LIB_PATH], capture_output=True, text=True).stdout
-    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
-    ours = {n for n in exported if n.startswith("lt_")}
-    assert ours == set(declared_symbols())
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    return {l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("lt_")}
+
+
+def test_only_declared_symbols_are_exported(library):
+    assert _exported(build.LIB) == set(declared_symbols())
+
+
+def test_test_build_adds_only_the_fault_injection_entry_points(library):
+    testing = set(declared_symbols(testing=True)) - set(declared_symbols())
+    assert testing == {"lt_test_fail_allocation_after", "lt_nn_test_stall_tensor_core"}
+    assert _exported(build.TEST_LIB) == set(declared_symbols(testing=True))
 
 
 def test_invalid_descriptors_rejected_on_host(library):
