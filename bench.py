@@ -764,7 +764,8 @@ def run_ours(args):
                        "ray_samples_per_step": samples_step, "hit_fraction_stage1": stats["hit_samples"] / stats["stage1_samples"],
                        "beta": beta, "l2": "flushed (512 MB write) between timed iterations",
                        "frames_per_rank": 1, "parallelism": f"replicas x{world}" if world > 1 else "single",
-                       "forward_variant": tuned, "autotune_ms": tune_ms},
+                       "forward_variant": tuned, "autotune_ms": tune_ms,
+                       "forward_brick": stats["forward_brick"], "adjoint_box": stats["adjoint_box"]},
             "stages_ms": stage_ms,
             "roofline": roofline,
             "peaks": peaks,
