@@ -382,7 +382,7 @@ def time_to_residual(plan, n_samples, n_plain=200, n_eval=5):
     import time as _t
     from paper_1812_03358_b300 import unet, warmstart
     t0 = _t.time()
-    ws, losses = warmstart.train(plan, unet.UNet(seed=1), n_samples, lr=1e-3)
+    ws, losses = warmstart.train(plan, unet.UNet(seed=1), n_samples, lr=1e-3, max_norm=1.0)
     t_train = _t.time() - t0
     rows = []
     for j in range(n_eval):
@@ -401,7 +401,7 @@ def time_to_residual(plan, n_samples, n_plain=200, n_eval=5):
             "unet_tflops": med("unet_tflops"), "gain": statistics.median(ok) if ok else None,
             "gain_per_volume": gains, "volume_error_plain": med("err_plain"),
             "volume_error_warm_x0": med("err_x0"), "train_samples": n_samples, "train_s": round(t_train, 1),
-            "beta": "1e-3 * mean(D)", "held_out_seeds": [2_000_000 + j for j in range(n_eval)],
+            "beta": "1e-3 * mean(D)", "grad_clip_norm": 1.0, "train_reproducible": True, "held_out_seeds": [2_000_000 + j for j in range(n_eval)],
             "statistic": "median over the held-out volumes"}
 
 

@@ -57,11 +57,22 @@ LT_API lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, const fl
  * gave up (that CTA's outputs were not written). */
 LT_API lt_status lt_nn_device_status(void* stream);
 
-/* Weight gradient: dw[co][tap][ci] += sum_v g[v][co] in[v + tap][ci] (float32
- * accumulate, dw must be zeroed by the caller) and db[co] += sum_v g[v][co]
- * (db may be NULL).  g has Co channels per voxel. */
-LT_API lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, float* dw, float* db, int32_t batch,
-                                    int32_t D, int32_t H, int32_t W, int32_t Ci, int32_t Co, void* stream);
+/* Weight gradient: dw[co][tap][ci] += sum_v g[v][co] in[v + tap][ci] and
+ * db[co] += sum_v g[v][co] (db may be NULL); float32 accumulation, g has Co
+ * channels per voxel.  Deterministic: every CTA stores its partial sums in the
+ * caller's device workspace `work` (work_floats floats, at least what
+ * lt_nn_conv3d_wgrad_workspace reports for the same shape; contents on entry
+ * do not matter, overwritten), and one kernel adds them to dw and db in a fixed
+ * order, so repeated calls on the same inputs give the same bits.  LT_EINVAL
+ * for channel counts not multiples of 16, NULL pointers or a short workspace;
+ * `work` must not be shared with a call in flight on another stream. */
+LT_API lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, float* dw, float* db, float* work,
+                                    int64_t work_floats, int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
+                                    int32_t Co, void* stream);
+/* Workspace (floats) lt_nn_conv3d_wgrad needs for this shape; a few MB to
+ * tens of MB (one row of 27 Co Ci partial sums per CTA column). */
+LT_API lt_status lt_nn_conv3d_wgrad_workspace(int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci, int32_t Co,
+                                              int64_t* floats);
 
 /* wt[ci][tap][co] = w[co][26 - tap][ci]: the weights whose convolution is the
  * data gradient (the transposed convolution) of lt_nn_conv3d. */
@@ -89,10 +100,21 @@ LT_API lt_status lt_nn_upsample2_backward(const uint16_t* gout, uint16_t* gin, i
  * [d_off, d_off+C) of a [v][d_stride] tensor (skip connections). */
 LT_API lt_status lt_nn_copy_channels(const uint16_t* src, uint16_t* dst, int64_t voxels, int32_t C, int32_t s_stride,
                                      int32_t s_off, int32_t d_stride, int32_t d_off, void* stream);
+/* Gradient norm and clipping factor of n float32 gradients g, on the device
+ * and in a fixed order: out[0] = min(1, max_norm / ||g||) (1 when max_norm <=
+ * 0; 0 when ||g|| is not finite), out[1] = ||g||.  work: device scratch of at
+ * least LT_NN_NORM_WORK floats; out: 2 device floats.  Nothing is read back
+ * to the host. */
+#define LT_NN_NORM_WORK 256
+LT_API lt_status lt_nn_grad_norm_clip(const float* g, int64_t n, float max_norm, float* work, float* out,
+                                      void* stream);
 /* Adam step on float32 master weights p (and their bfloat16 copy pb, may be
- * NULL): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr mhat/(sqrt(vhat)+eps). */
-LT_API lt_status lt_nn_adam(float* p, uint16_t* pb, const float* g, float* m, float* v, int64_t n, float lr,
-                            float b1, float b2, float eps, int32_t step, void* stream);
+ * NULL) with gradient s g, s = *g_scale (a device float, e.g. out[0] of
+ * lt_nn_grad_norm_clip; NULL means 1): m = b1 m + (1-b1) s g;
+ * v = b2 v + (1-b2) (s g)^2; p -= lr mhat/(sqrt(vhat)+eps), mhat = m/(1-b1^step),
+ * vhat = v/(1-b2^step). */
+LT_API lt_status lt_nn_adam(float* p, uint16_t* pb, const float* g, const float* g_scale, float* m, float* v,
+                            int64_t n, float lr, float b1, float b2, float eps, int32_t step, void* stream);
 
 /* out[i] = a[i] + b[i] (bfloat16, float32 arithmetic). */
 LT_API lt_status lt_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, int64_t n, void* stream);

@@ -141,11 +141,13 @@ conv3d_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ w, cons
 // input halo once; for each tap and each 16-voxel x run the MMA is
 // g_run^T (MB x 16 voxels) times the shifted halo window (16 voxels x 16 ci).
 // Warps split the MB/16 channel tiles and, when there are fewer than four,
-// the eight runs; the partial sums are combined in shared memory and added to
-// dw once per CTA (float atomics: the summation order over CTAs varies).
+// the eight runs; the partial sums are combined in shared memory and stored
+// once per CTA in row blockIdx.x of the partial-sum array part[gridDim.x][E]
+// (E = 27 Co Ci entries, dw's layout), which sum_parts_kernel then adds to dw
+// in a fixed order: the result does not depend on CTA scheduling.
 template <int MB>
 __global__ void __launch_bounds__(CT_THREADS)
-conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ dw, int D,
+conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ part, int D,
                          int H, int W, int Ci, int Co, int tiles_x, int tiles_y, int tiles_z, long long n_tiles,
                          int tiles_per_cta) {
   constexpr int MT = MB / 16;            // channel tiles
@@ -214,7 +216,8 @@ conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g
       }
     }
   }
-  // combine the warps that shared a channel tile, then one atomic add per entry
+  // combine the warps that shared a channel tile, then one store per entry
+  float* prow = part + (long long)blockIdx.x * 27 * Co * Ci;
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     __syncthreads();
@@ -226,7 +229,7 @@ conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g
       float v = 0.0f;
 #pragma unroll
       for (int s2 = 0; s2 < RS; ++s2) v += red[m + s2 * MT][i][j];
-      atomicAdd(dw + ((long long)(n0 + m * 16 + i) * 27 + tap) * Ci + c0 + j, v);
+      prow[((long long)(n0 + m * 16 + i) * 27 + tap) * Ci + c0 + j] = v;
     }
   }
 }
@@ -236,10 +239,10 @@ conv3d_wgrad_tile_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g
 // 16 x 16 accumulator, and runs all eight 16-voxel x runs of every staged
 // block against them.  Staged once per block for all taps (the kernel above
 // stages each block once per dz: three times), and each warp issues 56 MMAs
-// per staged block instead of 18.  One float atomic add per weight entry per
-// CTA, as above.
+// per staged block instead of 18.  One partial sum per weight entry per CTA,
+// stored in row blockIdx.x of part as above.
 __global__ void __launch_bounds__(CT_THREADS)
-conv3d_wgrad27_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ dw, int D, int H,
+conv3d_wgrad27_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, float* __restrict__ part, int D, int H,
                       int W, int Ci, int Co, int tiles_x, int tiles_y, int tiles_z, long long n_tiles,
                       int tiles_per_cta) {
   constexpr int TPW = 7;   // taps per warp: 4 x 7 >= 27
@@ -305,6 +308,7 @@ conv3d_wgrad27_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, f
       }
     }
   }
+  float* prow = part + (long long)blockIdx.x * 27 * Co * Ci;
 #pragma unroll
   for (int j = 0; j < TPW; ++j) {
     const int tap = warp * TPW + j;
@@ -313,14 +317,44 @@ conv3d_wgrad27_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g, f
       __syncwarp();
       for (int e = lane; e < 256; e += 32) {
         const int i = e >> 4, c = e & 15;
-        atomicAdd(dw + ((long long)(n0 + i) * 27 + tap) * Ci + c0 + c, red[warp][i][c]);
+        prow[((long long)(n0 + i) * 27 + tap) * Ci + c0 + c] = red[warp][i][c];
       }
       __syncwarp();
     }
   }
 }
 
-__global__ void bias_grad_kernel(const bf16* __restrict__ g, float* __restrict__ db, long long vtot, int Co) {
+// out[e] += sum_{p < n_parts} part[p stride + e]: a block owns 32 entries,
+// warp w sums the parts p = w (mod 8) with two accumulators, and warp 0 adds
+// the eight warp sums in order.  Every entry is summed in the same order on
+// every run.
+__global__ void __launch_bounds__(256)
+sum_parts_kernel(const float* __restrict__ part, int n_parts, long long stride, float* __restrict__ out, long long n) {
+  __shared__ float sh[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long e = (long long)blockIdx.x * 32 + lane;
+  float a0 = 0.0f, a1 = 0.0f;
+  if (e < n) {
+    int p = warp;
+    for (; p + 8 < n_parts; p += 16) {
+      a0 += part[(long long)p * stride + e];
+      a1 += part[(long long)(p + 8) * stride + e];
+    }
+    if (p < n_parts) a0 += part[(long long)p * stride + e];
+  }
+  sh[warp][lane] = a0 + a1;
+  __syncthreads();
+  if (warp == 0 && e < n) {
+    float s = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += sh[w][lane];
+    out[e] += s;
+  }
+}
+
+// Bias gradient partial sums, part[blockIdx.y][co] (summed into db by
+// sum_parts_kernel).
+__global__ void bias_grad_kernel(const bf16* __restrict__ g, float* __restrict__ part, long long vtot, int Co) {
   // one block per output channel chunk of 32; threads stride over voxels
   const int co = blockIdx.x * 32 + (threadIdx.x & 31);
   float acc = 0.0f;
@@ -333,7 +367,7 @@ __global__ void bias_grad_kernel(const bf16* __restrict__ g, float* __restrict__
   if (threadIdx.x < 32 && co < Co) {
     float s = 0.0f;
     for (int i = 0; i < 8; ++i) s += sh[i][threadIdx.x];
-    atomicAdd(db + co, s);
+    part[(long long)blockIdx.y * Co + co] = s;
   }
 }
 
@@ -590,13 +624,13 @@ __global__ void f2b_vec_kernel(const float* __restrict__ x, bf16* __restrict__ y
     store8(y + 8LL * i, v);
   }
 }
-// db[co] += sum_v g[v][co] with 8 channels per lane: Co / 8 = C8 divides 32,
-// so lane l always holds channel group l % C8; lanes of one group are summed
-// by xor shuffles at multiples of C8, warps in shared memory, and each block
-// adds one value per channel.
+// Bias gradient partial sums with 8 channels per lane: Co / 8 = C8 divides
+// 32, so lane l always holds channel group l % C8; lanes of one group are
+// summed by xor shuffles at multiples of C8, warps in shared memory, and each
+// block stores one value per channel in part[blockIdx.x][co].
 constexpr int kBiasMaxC = 256;
 __global__ void __launch_bounds__(256)
-bias_grad_vec_kernel(const bf16* __restrict__ g, float* __restrict__ db, long long vtot, int Co) {
+bias_grad_vec_kernel(const bf16* __restrict__ g, float* __restrict__ part, long long vtot, int Co) {
   __shared__ float sh[8][kBiasMaxC];
   const int C8 = Co / 8, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane % C8, vpw = 32 / C8;
@@ -618,7 +652,7 @@ bias_grad_vec_kernel(const bf16* __restrict__ g, float* __restrict__ db, long lo
   for (int ch = threadIdx.x; ch < Co; ch += blockDim.x) {
     float t = 0.0f;
     for (int w = 0; w < 8; ++w) t += sh[w][ch];
-    atomicAdd(db + ch, t);
+    part[(long long)blockIdx.x * Co + ch] = t;
   }
 }
 
@@ -631,10 +665,45 @@ static bool vec8_ok(const void* a, const void* b, long long items, std::initiali
   return al(a) && al(b) && items < (1LL << 31);
 }
 
-__global__ void adam_kernel(float* p, bf16* pb, const float* g, float* m, float* v, long long n, float lr, float b1,
-                            float b2, float eps, float c1, float c2) {
+// Squared gradient norm in a fixed order: block b of a fixed grid of
+// kNormBlocks sums the elements b*256 + t (mod kNormBlocks*256) per thread,
+// then the block's threads in a fixed tree, into part[b]; clip_scale_kernel
+// adds the kNormBlocks partial sums in order and writes {scale, norm}, scale =
+// min(1, max_norm / norm) (1 if max_norm <= 0; 0 if the norm is not finite,
+// so that step's gradient is dropped).
+constexpr int kNormBlocks = 148;
+static_assert(kNormBlocks <= LT_NN_NORM_WORK, "norm scratch too small");
+__global__ void __launch_bounds__(256) sumsq_parts_kernel(const float* __restrict__ g, long long n,
+                                                          float* __restrict__ part) {
+  __shared__ float sh[8];
+  float acc = 0.0f;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)kNormBlocks * 256)
+    acc = fmaf(g[i], g[i], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+__global__ void clip_scale_kernel(const float* __restrict__ part, float max_norm, float* __restrict__ out) {
+  double t = 0.0;
+  for (int b = 0; b < kNormBlocks; ++b) t += (double)part[b];
+  const float norm = (float)sqrt(t);
+  float scale = 1.0f;
+  if (!isfinite(norm)) scale = 0.0f;
+  else if (max_norm > 0.0f && norm > max_norm) scale = max_norm / norm;
+  out[0] = scale;
+  out[1] = norm;
+}
+
+__global__ void adam_kernel(float* p, bf16* pb, const float* g, const float* g_scale, float* m, float* v, long long n,
+                            float lr, float b1, float b2, float eps, float c1, float c2) {
+  const float gs = g_scale ? *g_scale : 1.0f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    const float gi = g[i] * gs;
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
@@ -773,44 +842,88 @@ extern "C" lt_status lt_nn_conv3d_ex(const uint16_t* in, const uint16_t* w, cons
   return launched("conv3d");
 }
 
-extern "C" lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, float* dw, float* db, int32_t batch,
-                                        int32_t D, int32_t H, int32_t W, int32_t Ci, int32_t Co, void* stream) {
+// Launch shape of the weight gradient and the size of its partial-sum array:
+// gx CTAs per channel group, each walking `per` voxel blocks (about four waves
+// over the 148 SMs), one row of E = 27 Co Ci partial sums per CTA column, then
+// the bias partial sums (one row of Co per block of whichever bias kernel the
+// gradient's alignment selects; the array is sized for the larger).
+struct WgradShape {
+  int mb = 0, tx = 0, ty = 0, tz = 0, per = 0;
+  bool all_taps = false;
+  long long vtot = 0, n_tiles = 0, groups = 0, E = 0;
+  unsigned gx = 0, bias_vec_blocks = 0, bias_rows = 0;
+  long long floats = 0;
+};
+
+static bool wgrad_shape(int batch, int D, int H, int W, int Ci, int Co, WgradShape& q) {
+  if (batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 || Ci % 16 || Co % 16) return false;
+  q.vtot = (long long)D * H * W * batch;
+  q.mb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
+  q.tx = (W + CT_X - 1) / CT_X;
+  q.ty = (H + CT_Y - 1) / CT_Y;
+  q.tz = (D + CT_Z - 1) / CT_Z;
+  q.n_tiles = (long long)q.tx * q.ty * q.tz * batch;
+  q.all_taps = q.mb == 16;   // one channel tile: every tap in one CTA
+  q.groups = (q.all_taps ? 1LL : 3LL) * (Ci / 16) * (Co / q.mb);
+  if (q.groups > 65535) return false;
+  const long long want = std::max<long long>(1, (148LL * 4 + q.groups - 1) / q.groups);
+  q.per = (int)std::max<long long>(1, (q.n_tiles + want - 1) / want);
+  q.gx = (unsigned)((q.n_tiles + q.per - 1) / q.per);
+  q.E = 27LL * Co * Ci;
+  const int c8 = Co / 8;
+  const long long per_block = 8LL * (32 / std::max(1, std::min(c8, 32)));   // voxels a vector block reads per sweep
+  q.bias_vec_blocks = (unsigned)std::min<long long>(148LL * 8, (q.vtot + per_block - 1) / per_block);
+  q.bias_rows = (unsigned)std::min<long long>(1024, (q.vtot + 7) / 8);
+  q.floats = (long long)q.gx * q.E + (long long)std::max(q.bias_vec_blocks, q.bias_rows) * Co;
+  return true;
+}
+
+extern "C" lt_status lt_nn_conv3d_wgrad_workspace(int32_t batch, int32_t D, int32_t H, int32_t W, int32_t Ci,
+                                                  int32_t Co, int64_t* floats) {
   clear_error();
-  if (!in || !g || !dw || batch <= 0 || D <= 0 || H <= 0 || W <= 0 || Ci <= 0 || Co <= 0 || Ci % 16 || Co % 16)
+  WgradShape q;
+  if (!floats || !wgrad_shape(batch, D, H, W, Ci, Co, q))
+    return set_error(LT_EINVAL, "conv3d_wgrad_workspace: bad arguments (channels must be multiples of 16)");
+  *floats = q.floats;
+  return LT_OK;
+}
+
+extern "C" lt_status lt_nn_conv3d_wgrad(const uint16_t* in, const uint16_t* g, float* dw, float* db, float* work,
+                                        int64_t work_floats, int32_t batch, int32_t D, int32_t H, int32_t W,
+                                        int32_t Ci, int32_t Co, void* stream) {
+  clear_error();
+  WgradShape q;
+  if (!in || !g || !dw || !work || !wgrad_shape(batch, D, H, W, Ci, Co, q))
     return set_error(LT_EINVAL, "conv3d_wgrad: bad arguments (channels must be multiples of 16)");
-  const long long vtot = (long long)D * H * W * batch;
+  if (work_floats < q.floats) return set_error(LT_EINVAL, "conv3d_wgrad: workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
-  const int mb = Co % 64 == 0 ? 64 : Co % 32 == 0 ? 32 : 16;
-  const int tx = (W + CT_X - 1) / CT_X, ty = (H + CT_Y - 1) / CT_Y, tz = (D + CT_Z - 1) / CT_Z;
-  const long long n_tiles = (long long)tx * ty * tz * batch;
-  const bool all_taps = mb == 16;   // one channel tile: every tap in one CTA
-  const long long groups = (all_taps ? 1LL : 3LL) * (Ci / 16) * (Co / mb);
-  if (groups > 65535) return set_error(LT_EINVAL, "conv3d_wgrad: too many channel groups");
-  // about four waves of CTAs over the 148 SMs, each walking a run of voxel blocks
-  const long long want = std::max<long long>(1, (148LL * 4 + groups - 1) / groups);
-  const int per = (int)std::max<long long>(1, (n_tiles + want - 1) / want);
-  const unsigned gx = (unsigned)((n_tiles + per - 1) / per);
-  dim3 grid(gx, (unsigned)groups);
+  dim3 grid(q.gx, (unsigned)q.groups);
   const bf16* i_ = reinterpret_cast<const bf16*>(in);
   const bf16* g_ = reinterpret_cast<const bf16*>(g);
-  if (all_taps)
-    conv3d_wgrad27_kernel<<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
-  else if (mb == 64)
-    conv3d_wgrad_tile_kernel<64><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
-  else if (mb == 32)
-    conv3d_wgrad_tile_kernel<32><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+  const int tx = q.tx, ty = q.ty, tz = q.tz, per = q.per;
+  const long long n_tiles = q.n_tiles;
+  if (q.all_taps)
+    conv3d_wgrad27_kernel<<<grid, CT_THREADS, 0, st>>>(i_, g_, work, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+  else if (q.mb == 64)
+    conv3d_wgrad_tile_kernel<64><<<grid, CT_THREADS, 0, st>>>(i_, g_, work, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+  else if (q.mb == 32)
+    conv3d_wgrad_tile_kernel<32><<<grid, CT_THREADS, 0, st>>>(i_, g_, work, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
   else
-    conv3d_wgrad_tile_kernel<16><<<grid, CT_THREADS, 0, st>>>(i_, g_, dw, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+    conv3d_wgrad_tile_kernel<16><<<grid, CT_THREADS, 0, st>>>(i_, g_, work, D, H, W, Ci, Co, tx, ty, tz, n_tiles, per);
+  sum_parts_kernel<<<(unsigned)((q.E + 31) / 32), 256, 0, st>>>(work, (int)q.gx, q.E, dw, q.E);
   if (db) {
+    float* bpart = work + (long long)q.gx * q.E;
     const int c8 = Co / 8;
+    unsigned rows;
     if (Co % 8 == 0 && Co <= kBiasMaxC && 32 % c8 == 0 && (reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
-      const long long per_block = 8LL * (32 / c8);   // voxels a block reads per sweep
-      const unsigned nb = (unsigned)std::min<long long>(148LL * 8, (vtot + per_block - 1) / per_block);
-      bias_grad_vec_kernel<<<nb, 256, 0, st>>>(reinterpret_cast<const bf16*>(g), db, vtot, Co);
+      rows = q.bias_vec_blocks;
+      bias_grad_vec_kernel<<<rows, 256, 0, st>>>(g_, bpart, q.vtot, Co);
     } else {
-      dim3 gb((Co + 31) / 32, (unsigned)std::min<long long>(1024, (vtot + 7) / 8));
-      bias_grad_kernel<<<gb, 256, 0, st>>>(reinterpret_cast<const bf16*>(g), db, vtot, Co);
+      rows = q.bias_rows;
+      dim3 gb((Co + 31) / 32, rows);
+      bias_grad_kernel<<<gb, 256, 0, st>>>(g_, bpart, q.vtot, Co);
     }
+    sum_parts_kernel<<<(unsigned)((Co + 31) / 32), 256, 0, st>>>(bpart, (int)rows, Co, db, Co);
   }
   return launched("conv3d_wgrad");
 }
@@ -933,14 +1046,24 @@ extern "C" lt_status lt_nn_copy_channels(const uint16_t* src, uint16_t* dst, int
   return launched("copy_channels");
 }
 
-extern "C" lt_status lt_nn_adam(float* p, uint16_t* pb, const float* g, float* m, float* v, int64_t n, float lr,
-                                float b1, float b2, float eps, int32_t step, void* stream) {
+extern "C" lt_status lt_nn_grad_norm_clip(const float* g, int64_t n, float max_norm, float* work, float* out,
+                                          void* stream) {
+  clear_error();
+  if (!g || !work || !out || n < 0) return set_error(LT_EINVAL, "grad_norm_clip: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  sumsq_parts_kernel<<<kNormBlocks, 256, 0, st>>>(g, n, work);
+  clip_scale_kernel<<<1, 1, 0, st>>>(work, max_norm, out);
+  return launched("grad_norm_clip");
+}
+
+extern "C" lt_status lt_nn_adam(float* p, uint16_t* pb, const float* g, const float* g_scale, float* m, float* v,
+                                int64_t n, float lr, float b1, float b2, float eps, int32_t step, void* stream) {
   clear_error();
   if (!p || !g || !m || !v || n < 0 || step < 1) return set_error(LT_EINVAL, "adam: bad arguments");
   const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
   if (n)
-    adam_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(p, reinterpret_cast<bf16*>(pb), g, m, v, n, lr, b1, b2,
-                                                              eps, c1, c2);
+    adam_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(p, reinterpret_cast<bf16*>(pb), g, g_scale, m, v, n, lr,
+                                                              b1, b2, eps, c1, c2);
   return launched("adam");
 }
 

@@ -28,8 +28,10 @@ _SIGS = {
     "lt_nn_conv3d_ex": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
                         c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
     "lt_nn_device_status": [c_void_p],
-    "lt_nn_conv3d_wgrad": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
-                           c_void_p],
+    "lt_nn_conv3d_wgrad": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int32,
+                           c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_conv3d_wgrad_workspace": [c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p],
+    "lt_nn_grad_norm_clip": [c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p],
     "lt_nn_conv3d_flip": [c_void_p, c_void_p, c_int32, c_int32, c_void_p],
     "lt_nn_f32_to_bf16": [c_void_p, c_void_p, c_int64, c_void_p],
     "lt_nn_bf16_to_f32": [c_void_p, c_void_p, c_int64, c_void_p],
@@ -45,8 +47,8 @@ _SIGS = {
     "lt_nn_prepare_input": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
     "lt_nn_unpack_output": [c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
     "lt_nn_mse": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
-    "lt_nn_adam": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float, c_float,
-                   c_int32, c_void_p],
+    "lt_nn_adam": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float,
+                   c_float, c_int32, c_void_p],
 }
 _bound = False
 
@@ -133,6 +135,7 @@ def _s():
 
 
 DEVICE = "cuda"
+NORM_WORK = 256          # LT_NN_NORM_WORK: scratch floats of lt_nn_grad_norm_clip
 
 
 def bf16(*shape):
@@ -144,6 +147,11 @@ def bf16(*shape):
 def _need(t, n, what):
     if t is not None and t.numel() < n:
         raise ValueError(f"{what}: {t.numel()} elements, the layer needs {n}")
+
+
+def _need_at_least(t, n, what):
+    if t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the call needs {n}")
 
 
 # lt_nn_conv3d_ex kernel choice
@@ -172,20 +180,36 @@ def conv3d(inp, w, b, out_bf=None, out_f=None, *, Ci, Co, dims, o_stride=None, o
           o_stride or Co, o_off, int(relu), int(path), _s())
 
 
-def conv3d_wgrad(inp, g, dw, db, *, Ci, Co, dims):
+def wgrad_workspace_floats(*, Ci, Co, dims):
+    """Floats of device workspace lt_nn_conv3d_wgrad needs for this shape."""
+    n = c_int64(0)
+    _call("lt_nn_conv3d_wgrad_workspace", 1, *dims, Ci, Co, ctypes.byref(n))
+    return int(n.value)
+
+
+def conv3d_wgrad(inp, g, dw, db, *, Ci, Co, dims, work=None):
+    """dw += weight gradient, db += bias gradient (deterministic).  `work`: a
+    float32 device workspace of at least wgrad_workspace_floats() elements
+    (allocated here when None)."""
     D, H, W = dims
     V = D * H * W
     if inp.numel() != V * Ci or g.numel() != V * Co:
         raise ValueError("conv3d_wgrad: input / gradient shapes do not match dims")
     _need(dw, 27 * Ci * Co, "conv3d_wgrad dw")
     _need(db, Co, "conv3d_wgrad db")
+    need = wgrad_workspace_floats(Ci=Ci, Co=Co, dims=dims)
+    if work is None:
+        work = torch.empty(max(need, 1), device=DEVICE)
+    _need_at_least(work, need, "conv3d_wgrad workspace")
     _call("lt_nn_conv3d_wgrad", _pb(inp, "wgrad input"), _pb(g, "wgrad gradient"), _pf(dw, "wgrad dw"),
-          _pf(db, "wgrad db"), 1, D, H, W, Ci, Co, _s())
+          _pf(db, "wgrad db"), _pf(work, "wgrad workspace"), work.numel(), 1, D, H, W, Ci, Co, _s())
 
 
 class Conv:
-    """One 3x3x3 convolution's parameters: float32 master weights [Co][27][Ci],
-    their bfloat16 copy, bias, Adam moments and gradients."""
+    """One 3x3x3 convolution's parameters: float32 master weights [Co][27][Ci]
+    and bias, the weights' bfloat16 copy and the gradients.  The network moves
+    them into its flat parameter buffers (Adam and the gradient norm run once
+    over all of them); these attributes are then views into those buffers."""
 
     def __init__(self, ci, co, gen):
         self.ci, self.co = ci, co
@@ -196,8 +220,6 @@ class Conv:
         self.wt = bf16(ci, 27, co)
         self.gw = torch.zeros_like(self.w)
         self.gb = torch.zeros_like(self.b)
-        self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
-        self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
         self.sync_bf16()
 
     def sync_bf16(self):
@@ -205,16 +227,6 @@ class Conv:
 
     def flip(self):
         _call("lt_nn_conv3d_flip", _pb(self.wb), _pb(self.wt), self.ci, self.co, _s())
-
-    def zero_grad(self):
-        self.gw.zero_()
-        self.gb.zero_()
-
-    def adam(self, lr, step):
-        _call("lt_nn_adam", _pf(self.w), _pb(self.wb), _pf(self.gw), _pf(self.mw), _pf(self.vw), self.w.numel(),
-              lr, 0.9, 0.999, 1e-8, step, _s())
-        _call("lt_nn_adam", _pf(self.b), None, _pf(self.gb), _pf(self.mb), _pf(self.vb), self.b.numel(),
-              lr, 0.9, 0.999, 1e-8, step, _s())
 
 
 class UNet:
@@ -232,6 +244,42 @@ class UNet:
                     (Conv(c2 + c1, c1, gen), Conv(c1, c1, gen))]
         self.head = Conv(c1, 16, gen)
         self.step = 0
+        self._flatten()
+        self.clip = torch.zeros(2, device=DEVICE)                 # {scale, gradient norm} of the last step
+        self._norm_work = torch.empty(NORM_WORK, device=DEVICE)
+        self._wg_work = torch.empty(0, device=DEVICE)
+
+    def _flatten(self):
+        """Parameters, gradients and Adam moments of every layer in four flat
+        float32 buffers (and the bfloat16 weights in a fifth); each weight and
+        bias block starts at a multiple of 64 elements."""
+        segs, off = [], 0
+        for c in self.convs():
+            for name in ("w", "b"):
+                n = getattr(c, name).numel()
+                segs.append((c, name, off, n))
+                off += -(-n // 64) * 64
+        self.n_params = off
+        self.P = torch.zeros(off, device=DEVICE)
+        self.G = torch.zeros(off, device=DEVICE)
+        self.M = torch.zeros(off, device=DEVICE)
+        self.V = torch.zeros(off, device=DEVICE)
+        self.PB = bf16(off)
+        for c, name, o, n in segs:
+            t = getattr(c, name)
+            self.P[o:o + n].copy_(t.reshape(-1))
+            setattr(c, name, self.P[o:o + n].view(t.shape))
+            if name == "w":
+                c.gw = self.G[o:o + n].view(t.shape)
+                c.wb = self.PB[o:o + n].view(t.shape)
+            else:
+                c.gb = self.G[o:o + n].view(t.shape)
+        _call("lt_nn_f32_to_bf16", _pf(self.P), _pb(self.PB), off, _s())
+
+    def _workspace(self, floats):
+        if self._wg_work.numel() < floats:
+            self._wg_work = torch.empty(floats, device=DEVICE)
+        return self._wg_work
 
     def flops(self, dims):
         """Multiply-add flops (2 per MAC) of one forward pass on a D x H x W
@@ -317,7 +365,8 @@ class UNet:
             if out_act.numel() != g.numel():
                 raise ValueError("relu backward shapes")
             _call("lt_nn_relu_backward", _pb(out_act), _pb(g), g.numel(), _s())
-        conv3d_wgrad(inp, g, conv.gw, conv.gb, Ci=conv.ci, Co=conv.co, dims=dims)
+        work = self._workspace(max(1, wgrad_workspace_floats(Ci=conv.ci, Co=conv.co, dims=dims)))
+        conv3d_wgrad(inp, g, conv.gw, conv.gb, Ci=conv.ci, Co=conv.co, dims=dims, work=work)
         conv.flip()
         gi = bf16(*dims, conv.ci)
         conv3d(g, conv.wt, None, gi, Ci=conv.co, Co=conv.ci, dims=dims, relu=False)
@@ -329,8 +378,7 @@ class UNet:
         if g_out.dtype != torch.float32 or tuple(g_out.shape) != (*dims[0], 16):
             raise TypeError(f"backward: expected a float32 {(*dims[0], 16)} gradient, got {g_out.dtype} "
                             f"{tuple(g_out.shape)}")
-        for c in self.convs():
-            c.zero_grad()
+        self.G.zero_()
         g = bf16(*g_out.shape)
         _call("lt_nn_f32_to_bf16", _pf(g_out, "output gradient (float32)"), _pb(g), g_out.numel(), _s())
         (x,) = acts["head"]
@@ -366,10 +414,16 @@ class UNet:
             g = self._conv_back(ca, x, a, g, d)
         return g
 
-    def adam_step(self, lr):
+    def adam_step(self, lr, max_norm=0.0):
+        """One Adam step over every parameter, the gradient first scaled to a
+        global norm of at most max_norm (no clipping when max_norm <= 0; a
+        non-finite gradient is dropped).  self.clip holds {scale, norm} on the
+        device afterwards."""
         self.step += 1
-        for c in self.convs():
-            c.adam(lr, self.step)
+        _call("lt_nn_grad_norm_clip", _pf(self.G), self.n_params, float(max_norm), _pf(self._norm_work),
+              _pf(self.clip), _s())
+        _call("lt_nn_adam", _pf(self.P), _pb(self.PB), _pf(self.G), _pf(self.clip), _pf(self.M), _pf(self.V),
+              self.n_params, lr, 0.9, 0.999, 1e-8, self.step, _s())
 
 
 class WarmStart:
@@ -401,12 +455,12 @@ class WarmStart:
         _call("lt_nn_unpack_output", _pf(out), _pf(self.m), _pf(x0), x0.numel(), _s())
         return x0
 
-    def train_step(self, bp, x_true, lr):
+    def train_step(self, bp, x_true, lr, max_norm=0.0):
         out = self.net.forward(self.prepare(bp), keep=True)
         g = torch.empty_like(out)
         self.loss.zero_()
         _call("lt_nn_mse", _pf(out), _pf(x_true, "target volume"), _pf(self.m), _pf(g), _pf(self.loss), x_true.numel(),
               _s())
         self.net.backward(g)
-        self.net.adam_step(lr)
+        self.net.adam_step(lr, max_norm)
         return self.loss

@@ -44,16 +44,20 @@ def training_pair(plan: lt.Plan, seed: int, peak=1e4):
 
 
 def train(plan: lt.Plan, net: UNet, n_samples: int, seed0: int = 1_000_000, lr: float = 1e-3,
-          log_every: int = 0):
-    """Adam on one fresh (x, A^T y) pair per step, cosine-decayed rate.
-    Returns the WarmStart and [(step, loss)] every log_every steps."""
+          log_every: int = 0, max_norm: float = 1.0):
+    """Adam on one fresh (x, A^T y) pair per step, cosine-decayed rate, the
+    gradient clipped to a global norm of max_norm (none when 0; at the bench's
+    size the norm's median is 0.3-0.5, so 1.0 clips only the first steps and
+    rare spikes).  Training is bit-reproducible (every gradient is summed in a
+    fixed order).  Returns the WarmStart and [(step, loss, gradient norm)]
+    every log_every steps."""
     ws = WarmStart(plan, net)
     losses = []
     for s in range(n_samples):
         x, bp, _ = training_pair(plan, seed0 + s)
-        ws.train_step(bp, x, lr * 0.5 * (1.0 + math.cos(math.pi * s / n_samples)))
+        ws.train_step(bp, x, lr * 0.5 * (1.0 + math.cos(math.pi * s / n_samples)), max_norm)
         if log_every and (s % log_every == 0 or s == n_samples - 1):
-            losses.append((s, float(ws.loss)))
+            losses.append((s, float(ws.loss), float(net.clip[1])))
     torch.cuda.synchronize()
     return ws, losses
 
@@ -137,18 +141,19 @@ def main(argv=None):
     ap.add_argument("--n-plain", type=int, default=200)
     ap.add_argument("--beta-scale", type=float, default=1e-3)
     ap.add_argument("--test-seeds", type=int, default=4)
+    ap.add_argument("--max-norm", type=float, default=1.0, help="gradient clipping norm (0: none)")
     a = ap.parse_args(argv)
     build.build()
     vox = 128.0 / a.n
     plan = lt.Plan(I.Volume(a.n, a.n, a.n, vox, vox, vox), [I.plenoptic_camera()])
     t0 = time.time()
-    ws, losses = train(plan, UNet(seed=1), a.samples, lr=a.lr, log_every=max(1, a.samples // 20))
+    ws, losses = train(plan, UNet(seed=1), a.samples, lr=a.lr, log_every=max(1, a.samples // 20), max_norm=a.max_norm)
     t_train = time.time() - t0
     rows = []
     for s in range(a.test_seeds):
         x, _, y = training_pair(plan, seed=2_000_000 + s)     # held out: disjoint from training seeds
         rows.append(evaluate(plan, ws, y, x, n_plain=a.n_plain, beta_scale=a.beta_scale))
-    print(json.dumps({"workload": f"plenoptic {a.n}^3 warm start", "train_samples": a.samples,
+    print(json.dumps({"workload": f"plenoptic {a.n}^3 warm start", "train_samples": a.samples, "max_norm": a.max_norm,
                       "train_s": round(t_train, 1), "losses": losses, "eval": rows}))
 
 

@@ -204,3 +204,97 @@ def test_unet_forward_and_gradient_match_torch_restatement():
         ref_g = weights[c].grad.permute(0, 2, 3, 4, 1).reshape(c.co, 27, c.ci)
         errs.append((c.ci, c.co, float((c.gw - ref_g).norm()) / max(float(ref_g.norm()), 1e-30)))
     assert all(e < 2e-2 for _, _, e in errs), errs
+
+
+@pytest.mark.parametrize("Ci,Co,dims", [(16, 16, (16, 32, 64)), (32, 64, (8, 16, 16)), (48, 16, (6, 10, 18))])
+def test_weight_gradient_is_deterministic(Ci, Co, dims):
+    """Partial sums per CTA, added in a fixed order: repeated calls give the
+    same bits, and the result accumulates onto dw and db."""
+    u = U()
+    x = rnd(*dims, Ci, seed=11).bfloat16()
+    g = rnd(*dims, Co, seed=12).bfloat16()
+    runs = []
+    for _ in range(3):
+        dw = torch.zeros(Co, 27, Ci, device="cuda")
+        db = torch.zeros(Co, device="cuda")
+        u.conv3d_wgrad(x, g, dw, db, Ci=Ci, Co=Co, dims=dims)
+        runs.append((dw.clone(), db.clone()))
+    torch.cuda.synchronize()
+    for dw, db in runs[1:]:
+        assert torch.equal(dw, runs[0][0]) and torch.equal(db, runs[0][1])
+    dw = runs[0][0].clone()
+    db = runs[0][1].clone()
+    u.conv3d_wgrad(x, g, dw, db, Ci=Ci, Co=Co, dims=dims)      # accumulates
+    torch.cuda.synchronize()
+    assert torch.allclose(dw, 2 * runs[0][0], rtol=1e-6, atol=0) and torch.allclose(db, 2 * runs[0][1], rtol=1e-6)
+    # a workspace smaller than the shape needs is refused before any launch
+    from paper_1812_03358_b300 import lt
+    need = u.wgrad_workspace_floats(Ci=Ci, Co=Co, dims=dims)
+    with pytest.raises(ValueError):
+        u.conv3d_wgrad(x, g, dw, db, Ci=Ci, Co=Co, dims=dims, work=torch.empty(need - 1, device="cuda"))
+    with pytest.raises(lt.LtError):
+        u._call("lt_nn_conv3d_wgrad", x.data_ptr(), g.data_ptr(), dw.data_ptr(), db.data_ptr(),
+                torch.empty(need - 1, device="cuda").data_ptr(), need - 1, 1, *dims, Ci, Co, u._s())
+
+
+@pytest.mark.parametrize("n", [1, 1000, 37_000_001])
+def test_gradient_norm_and_clip_scale(n):
+    u = U()
+    g = rnd(n, seed=13, scale=0.3)
+    work = torch.empty(u.NORM_WORK, device="cuda")
+    out = torch.empty(2, device="cuda")
+    ref = float(g.double().norm())
+    for max_norm, scale in ((0.0, 1.0), (2 * ref, 1.0), (ref / 4, 0.25)):
+        u._call("lt_nn_grad_norm_clip", g.data_ptr(), n, max_norm, work.data_ptr(), out.data_ptr(), u._s())
+        torch.cuda.synchronize()
+        assert abs(float(out[1]) - ref) <= 1e-5 * ref
+        assert abs(float(out[0]) - scale) <= 1e-5
+    a = out.clone()
+    u._call("lt_nn_grad_norm_clip", g.data_ptr(), n, ref / 4, work.data_ptr(), out.data_ptr(), u._s())
+    torch.cuda.synchronize()
+    assert torch.equal(a, out)                                   # same bits every time
+    g[n // 2] = float("inf")
+    u._call("lt_nn_grad_norm_clip", g.data_ptr(), n, 1.0, work.data_ptr(), out.data_ptr(), u._s())
+    torch.cuda.synchronize()
+    assert float(out[0]) == 0.0                                  # a non-finite gradient is dropped
+
+
+def test_adam_with_scaled_gradient_matches_torch():
+    """lt_nn_adam with a device scale s against torch.optim.Adam on s * g
+    (three steps, float32)."""
+    u = U()
+    n = 4099
+    p0 = rnd(n, seed=14)
+    grads = [rnd(n, seed=15 + k) for k in range(3)]
+    p, m, v = p0.clone(), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    pb = torch.empty(n, device="cuda", dtype=torch.bfloat16)
+    s = torch.tensor([0.37], device="cuda")
+    ref = p0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([ref], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    for k, gk in enumerate(grads):
+        u._call("lt_nn_adam", p.data_ptr(), pb.data_ptr(), gk.data_ptr(), s.data_ptr(), m.data_ptr(), v.data_ptr(),
+                n, 1e-2, 0.9, 0.999, 1e-8, k + 1, u._s())
+        opt.zero_grad()
+        ref.grad = 0.37 * gk
+        opt.step()
+    torch.cuda.synchronize()
+    assert (p - ref.detach()).abs().max() <= 1e-5 * ref.detach().abs().max()
+    assert torch.equal(pb, p.bfloat16())
+
+
+def test_unet_training_steps_are_reproducible():
+    """Two networks from the same seed, trained on the same inputs, hold the
+    same bits: every gradient is summed in a fixed order."""
+    u = U()
+    dims = (16, 16, 32)
+    nets = [u.UNet(seed=5), u.UNet(seed=5)]
+    x = rnd(*dims, 16, seed=20).bfloat16()
+    for net in nets:
+        for k in range(3):
+            out = net.forward(x, keep=True)
+            g = rnd(*dims, 16, seed=30 + k) * 1e-3
+            net.backward(g)
+            net.adam_step(1e-3, max_norm=1.0)
+    torch.cuda.synchronize()
+    assert torch.equal(nets[0].P, nets[1].P) and torch.equal(nets[0].M, nets[1].M)
+    assert torch.equal(nets[0].clip, nets[1].clip) and float(nets[0].clip[1]) > 0

@@ -17,7 +17,7 @@ def test_trained_network_beats_plain_solver_on_volume_error():
     from paper_1812_03358_b300 import unet, warmstart as WS
     plan = lt.Plan(I.Volume(64, 64, 64, 2.0, 2.0, 2.0), [I.plenoptic_camera()])
     ws, losses = WS.train(plan, unet.UNet(seed=1), n_samples=800, lr=1e-3, log_every=40)
-    late = [l for s, l in losses if s >= 400]
+    late = [l for s, l, _ in losses if s >= 400]
     assert sum(late) / len(late) < 0.8 * losses[0][1], losses
     x, bp, y = WS.training_pair(plan, seed=2_000_000)
     x0 = ws.infer(bp)
