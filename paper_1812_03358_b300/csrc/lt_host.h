@@ -88,6 +88,10 @@ struct CameraPlan {
   int2* d_cand_all_s = nullptr;
   int2* d_cand_all_t = nullptr;
   float* d_zbuf = nullptr;         // scratch [F][N_mu][window^2]
+  float* d_s2tab = nullptr;        // stage-two transport table (Bs, Bt per lenslet and cell)
+  lt::S2Desc* d_s2desc = nullptr;  // [N_mu][K] stage-two descriptors
+  uint32_t* d_s2bits = nullptr;    // [N_mu][16] block ownership bits
+  int64_t s2tab_floats = 0;
   float* d_fa = nullptr;           // scratch array plane [F][K][Na]
   StageTwo s2{};
 };

@@ -43,6 +43,23 @@ struct LensletParam {
 };
 
 // Device tables of one plenoptic camera's array -> detector stage.
+// One (lenslet, cell) of stage two, 32 bytes (plan-built, read by the
+// stage-two kernels; lenslet-major, cell k of lenslet mu at mu * K + k).
+struct alignas(16) S2Desc {
+  int32_t off;     // offset of its transport table entry (floats, a multiple of 4); -1: empty window
+  int32_t px0;     // array index of the lenslet block's first pixel
+  int32_t y0;      // detector index of the cell window's first pixel
+  int32_t zo;      // index of the cell window's first pixel in the lenslet's union window (rows of nsu)
+  uint32_t dims;   // nc | nr << 8 | nds << 16 | ndt << 24
+  float scale;     // the lenslet's transmission scale for this cell
+  uint32_t win;    // nsu | ntu << 8 | (last cell of the lenslet) << 16 | k << 17
+  int32_t mu;
+};
+static_assert(sizeof(S2Desc) == 32, "S2Desc is 32 bytes");
+
+// Threads per CTA of the stage-two kernels (one lenslet walk per warp).
+constexpr int kStage2Threads = 256;
+
 struct StageTwo {
   const LensletParam* lens;   // [K][mla_nt*mla_ns]
   const int2* cols;           // [mla_nt*mla_ns]: array columns [x, y) of lenslet mu's block
@@ -63,6 +80,16 @@ struct StageTwo {
   float* zbuf;                // scratch [F][mla_nt*mla_ns][kStage2Window^2]: per-lenslet sub-images
   int32_t full_cover;         // 1 if every array pixel lies in some lenslet block
   int32_t sub_n, sub_s;       // angular-plane subset (cell_on); 1, 0 for all cells
+  // The per-(lenslet, cell) form the kernels walk (plan-built):
+  const S2Desc* desc;         // [mla_nt*mla_ns][K]
+  const float* wtab;          // transport table: per (lenslet, cell) Bs [nc][nds rounded up to 4] (zero padded)
+                              // then Bt [nr][ndt], 16-byte aligned
+  const uint32_t* bits;       // [mla_nt*mla_ns][16]: bit r*nc+c of words 0..7 = the lenslet owns block pixel (r, c);
+                              // of words 8..15 = nobody owns it and blocks tile the plane (the adjoint clears it)
+  int32_t tab_max, pix_max, w_max, z_max, y_max;   // largest table entry, block, nr*nds, union window, cell window
+                                                   // (floats, multiples of 4)
+  int32_t fwd_warp_floats, adj_warp_floats;        // shared memory per warp of the two kernels
+  int32_t fwd_per_sm, adj_per_sm, sms;             // resident CTAs per SM of each kernel, SM count
 };
 
 // Largest detector window (per axis) of one lenslet's sub-image.
@@ -114,7 +141,7 @@ struct GenRot {
   ShearPass pass[3];       // z, x, y
 };
 
-// Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.// Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.
+// Forward beam-integration tile: kBeamTileS x kBeamTileT target pixels per CTA.
 // The planner computes, per (cell, tile column) and (cell, tile row), the
 // slice interval [x, y) outside of which the tile's footprints miss the volume.
 constexpr int kBeamTileS = 32;
@@ -258,6 +285,13 @@ cudaError_t launch_beam_adjoint_batched(const BeamBatch& b, float* x, long long 
 
 // zbuf: per-lenslet sub-image scratch [F][N_mu][kStage2Window^2] (the plan's,
 // or any buffer of that size).
+// Plan time: fills s2's transport table wtab (sized by the host from the
+// windows, at the offsets of s2.desc) on stream st; the stage-two kernels'
+// shared memory and resident CTAs per SM (raises their dynamic shared memory
+// limit as needed).
+cudaError_t launch_stage2_tables(StageTwo s2, float* wtab, cudaStream_t st);
+size_t stage2_smem_bytes(const StageTwo& s2, bool adjoint);
+cudaError_t stage2_occupancy(const StageTwo& s2, bool adjoint, int* ctas_per_sm);
 cudaError_t launch_stage2_forward(const float* fa, float* y, StageTwo s2, int frames,
                                   long long fa_frame_stride, long long y_frame_stride,
                                   float* zbuf, cudaStream_t st);

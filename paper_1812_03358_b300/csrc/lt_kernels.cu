@@ -15,6 +15,7 @@
 // exact transposes up to float32 summation order (Sec. IV-A).
 #include <algorithm>
 
+#include "lt_async.cuh"
 #include "lt_beam_math.cuh"
 #include "lt_internal.h"
 
@@ -425,33 +426,35 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
 // Plenoptic stage two.  For one lenslet mu and cell k the transport from the
 // lenslet's array block (nr x nc pixels) to its detector window (ndt x nds)
 // is the separable product Bt (x) Bs of two small dense matrices
-// (eq. xport,sep); both kernels below give one CTA to a (lenslet, frame),
-// evaluate Bs and Bt once per cell into shared memory (one footprint centre
-// per detector column/row, consecutive cells sharing their common edge), and
-// contract in two steps (the O(S+T) scheme of Sec. IV-B).
+// (eq. xport,sep).  Both matrices depend on the geometry alone, so the plan
+// evaluates them once (stage2_table_kernel: one footprint centre per detector
+// column / row, consecutive array cells sharing their common edge) into a
+// table, and describes every (lenslet, cell) by a 32-byte S2Desc.  A table
+// entry is Bs[c][q] (nc rows of nds4 = nds rounded up to 4, zero past nds)
+// then Bt[r][b] (nr rows of ndt), so that every contraction runs on float4
+// rows: a lane computes four adjacent detector columns q at once.
+//
+// A (lenslet, cell) carries a few hundred multiply-adds on a few hundred
+// loaded values, so the kernels are built to keep loads in flight: a
+// persistent grid whose warps each walk their own lenslets (warp w of W takes
+// lenslet-frames w, w + W, ...) cell after cell.  While a warp contracts one
+// cell in two steps (the O(S+T) scheme of Sec. IV-B) in its own shared
+// memory, cp.async already brings the next cell's table entry and pixels into
+// the other half of a double buffer; the descriptors of the next 64 cells sit
+// in a shared-memory ring.  No block barrier anywhere: each warp owns its
+// lenslets' outputs.  Every output is accumulated in the same order as the
+// plain double loop (c, then r; b, then q), so the result does not depend on
+// the blocking.
 // ---------------------------------------------------------------------------
-// Exact n / d for small operands (n * d < 2^32, d >= 2) by one multiply-high
-// with m = ceil(2^32 / d) = floor((2^32 - 1) / d) + 1: n m / 2^32 exceeds
-// n / d by less than n / 2^32 < 1 / d, which never reaches the next integer.
-// m = 2^32 does not fit for d = 1, which takes the select.
-struct SmallDiv {
-  uint32_t m, d;
-};
-__device__ __forceinline__ SmallDiv small_div(uint32_t d) { return {d > 1u ? 0xFFFFFFFFu / d + 1u : 0u, d}; }
-__device__ __forceinline__ uint32_t div_of(SmallDiv f, uint32_t n) { return f.d > 1u ? __umulhi(n, f.m) : n; }
-
 constexpr int L2_W = kStage2Window;
-constexpr int S2_THREADS = 256;
-constexpr int S2_KB = 4;   // cells per pass of the lenslet adjoint
-static_assert(MAXC * MAXC <= S2_THREADS, "one block pixel per thread");
-static_assert(S2_KB * 64 <= S2_THREADS && 2 * L2_W <= 64, "one footprint task per thread");
+static_assert(2 * L2_W <= 64, "one footprint task per thread of the table kernel");
 
 // Entries of one detector column or row of a (lenslet, cell): task < nds is
-// column dr.x + task, Bs[c][task] = entry (column, array column cc.x + c);
-// otherwise row dr.z + task - nds into Bt likewise.  Consecutive array cells
-// share their common edge value.
+// column dr.x + task, Bs[c * lds + task] = entry (column, array column
+// cc.x + c); otherwise row dr.z + task - nds into Bt[r * ldt + (task - nds)]
+// likewise.  Consecutive array cells share their common edge value.
 __device__ __forceinline__ void lenslet_weight_task(const LensletParam* L, int4 dr, int2 cc, int2 rr, int task,
-                                                    float (*Bs)[L2_W + 1], float (*Bt)[L2_W + 1]) {
+                                                    float* Bs, int lds, float* Bt, int ldt) {
   const int nds = dr.y - dr.x + 1;
   const bool s_axis = task < nds;
   const AxisParam& a = s_axis ? L->s : L->t;
@@ -459,153 +462,210 @@ __device__ __forceinline__ void lenslet_weight_task(const LensletParam* L, int4 
   const int i = s_axis ? dr.x + q : dr.z + q;
   const int j0 = s_axis ? cc.x : rr.x;
   const int n = s_axis ? cc.y - cc.x : rr.y - rr.x;
+  float* out = s_axis ? Bs + q : Bt + q;
+  const int ld = s_axis ? lds : ldt;
   int jc;
   float fr;
   footprint_centre(a, i, jc, fr);
   float Flo = edge_F(j0 - jc, fr, a);
   for (int c = 0; c < n; ++c) {
     const float Fhi = edge_F(j0 + c + 1 - jc, fr, a);
-    const float w = __fsub_rn(Fhi, Flo);
+    out[c * ld] = __fsub_rn(Fhi, Flo);
     Flo = Fhi;
-    if (s_axis) Bs[c][q] = w; else Bt[c][q] = w;
   }
 }
 
-// One cell of a pass of the lenslet adjoint (shared memory).
-struct S2Cell {
-  int4 dr;         // detector window (s0, s1, t0, t1), inclusive
-  int nds, ndt;
-  int dz, dx;      // offset of the window inside the lenslet's union window
-  float scale;
-  SmallDiv dd;     // division by nds
-  int sub;         // cell in the angular subset
-  int on;          // in the subset and with a non-empty window
-  int cnt;         // nr * nds contraction outputs, 0 when off
+__device__ __forceinline__ int d_nc(uint32_t v) { return v & 0xff; }
+__device__ __forceinline__ int d_nr(uint32_t v) { return (v >> 8) & 0xff; }
+__device__ __forceinline__ int d_nds(uint32_t v) { return (v >> 16) & 0xff; }
+__device__ __forceinline__ int d_ndt(uint32_t v) { return v >> 24; }
+__device__ __forceinline__ int w_nsu(uint32_t v) { return v & 0xff; }
+__device__ __forceinline__ int w_ntu(uint32_t v) { return (v >> 8) & 0xff; }
+__device__ __forceinline__ bool w_last(uint32_t v) { return (v >> 16) & 1u; }
+__device__ __forceinline__ int up4(int v) { return (v + 3) & ~3; }
+
+// Plan time: the (lenslet, cell) table entries.  Grid (lenslets, cells).
+__global__ void __launch_bounds__(64) stage2_table_kernel(StageTwo s2, float* __restrict__ wtab) {
+  const int mu = blockIdx.x, k = blockIdx.y;
+  const int nmu = s2.mla_ns * s2.mla_nt;
+  const S2Desc dsc = s2.desc[(long long)mu * s2.K + k];
+  if (dsc.off < 0) return;
+  const int4 dr = s2.det_range[(long long)k * nmu + mu];
+  const int2 cc = s2.cols[mu], rr = s2.rows[mu];
+  const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1, nds4 = up4(nds), nc = cc.y - cc.x;
+  float* bs = wtab + dsc.off;
+  float* bt = bs + nc * nds4;
+  for (int task = threadIdx.x; task < nds + ndt; task += blockDim.x)
+    lenslet_weight_task(s2.lens + (long long)k * nmu + mu, dr, cc, rr, task, bs, nds4, bt, ndt);
+  for (int e = threadIdx.x; e < nc * (nds4 - nds); e += blockDim.x) {   // zero padding of the Bs rows
+    const int cix = e / (nds4 - nds);
+    bs[cix * nds4 + nds + (e - cix * (nds4 - nds))] = 0.0f;
+  }
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// floor(o / d) for 0 <= o < 2^12, 1 <= d <= 64 from the float reciprocal:
+// (o + 1/2) / d lies at least 1 / (2d) >= 1/128 from an integer, and the
+// product of o + 1/2 with the rounded reciprocal is off by at most
+// 2^12 * 2^-23 < 1/2000, so truncation gives the exact quotient.
+struct FDiv {
+  float inv;
+};
+__device__ __forceinline__ FDiv fdiv(int d) { return {__frcp_rn((float)d)}; }
+__device__ __forceinline__ int fdiv_of(FDiv f, int o) { return __float2int_rz(((float)o + 0.5f) * f.inv); }
+
+// The warp's cells: item j is cell j % K of lenslet-frame unit
+// w0 + (j / K) * nw (unit = frame * N_mu + mu, fewer than 2^31).  The walk
+// keeps (unit, cell) of the next item to issue and of the item being
+// contracted as counters; descriptors come 32 at a time into a ring of 64 in
+// shared memory (slot j % 64), one per lane.
+struct S2Walk {
+  int w0, nw, n_items, K, nmu;
+  __device__ __forceinline__ void load_chunk(const S2Desc* desc, S2Desc* ring, int chunk, int lane) const {
+    const int j = chunk * 32 + lane;
+    if (j < n_items) {
+      const int u = w0 + (j / K) * nw;
+      ring[j & 63] = desc[(long long)(u % nmu) * K + j % K];
+    }
+  }
+};
+struct S2Pos {
+  int unit, k, frame;
+  __device__ __forceinline__ void next(const S2Walk& w) {
+    if (++k == w.K) {
+      k = 0;
+      unit += w.nw;
+      frame = unit / w.nmu;
+    }
+  }
 };
 
-// Cell table of the pass starting at cell k0 (threads 0 .. S2_KB - 1).
-__device__ __forceinline__ void s2_cell_table(const StageTwo& s2, int mu, int nmu, int k0, int4 du, int nr,
-                                              S2Cell* cell) {
-  const int kk = threadIdx.x;
-  if (kk >= S2_KB) return;
-  S2Cell cl{};
-  const int k = k0 + kk;
-  if (k < s2.K) {
-    cl.dr = s2.det_range[(long long)k * nmu + mu];
-    cl.nds = cl.dr.y - cl.dr.x + 1;
-    cl.ndt = cl.dr.w - cl.dr.z + 1;
-    cl.sub = cell_on(s2.sub_n, s2.sub_s, k);
-    cl.on = cl.sub && cl.nds > 0 && cl.ndt > 0;
-    cl.dz = cl.dr.z - du.z;
-    cl.dx = cl.dr.x - du.x;
-    cl.scale = s2.lens[(long long)k * nmu + mu].scale;
-    cl.dd = small_div(cl.on ? cl.nds : 1);
-    cl.cnt = cl.on ? nr * cl.nds : 0;
-  }
-  cell[kk] = cl;
+// Issue the copies of block pixels (nr rows of nc values starting at src,
+// row stride `stride`) into dst[r * nc + c], two rows per warp pass.
+__device__ __forceinline__ void s2_copy_block(float* dst, const float* src, int nr, int nc, long long stride,
+                                              int lane) {
+  const int c = lane & 15;
+  if (c < nc)
+    for (int r = lane >> 4; r < nr; r += 2) cp_async4(smem_addr(dst + r * nc + c), src + r * stride + c);
 }
 
-// The cell and local index of flat contraction task e (e < the pass's total).
-__device__ __forceinline__ int s2_task_cell(const S2Cell* cell, int& o) {
-  int kk = 0;
-#pragma unroll
-  for (int t = 0; t < S2_KB - 1; ++t)
-    if (kk == t && o >= cell[t].cnt) {
-      o -= cell[t].cnt;
-      kk = t + 1;
-    }
-  return kk;
+__device__ __forceinline__ void fma4(float4& acc, float a, const float4& b) {
+  acc.x = fmaf(a, b.x, acc.x);
+  acc.y = fmaf(a, b.y, acc.y);
+  acc.z = fmaf(a, b.z, acc.z);
+  acc.w = fmaf(a, b.w, acc.w);
 }
 
-constexpr int L2_THREADS = 128;
-
-// Bs[c][q] = entry (detector column dr.x + q, array column cc.x + c) and
-// Bt[r][b] likewise; one task per detector column / row.
-__device__ __forceinline__ void lenslet_weights(const LensletParam* L, int4 dr, int2 cc, int2 rr,
-                                                float (*Bs)[L2_W + 1], float (*Bt)[L2_W + 1]) {
-  const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
-  for (int task = threadIdx.x; task < nds + ndt; task += blockDim.x) lenslet_weight_task(L, dr, cc, rr, task, Bs, Bt);
-}
-
-// Forward, pass 1: each lenslet's contribution sum_k Bt (x) Bs fa_k on the
-// union over cells of its detector windows, written to zbuf (no overlap).
-__global__ void __launch_bounds__(L2_THREADS, 16)
-stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_fs, float* __restrict__ zbuf) {
-  __shared__ float Bs[MAXC][L2_W + 1];
-  __shared__ float Bt[MAXC][L2_W + 1];
-  __shared__ float F[MAXC][MAXC + 1];
-  __shared__ float W[MAXC][L2_W + 1];
-  __shared__ float Z[L2_W * L2_W];
-  const int mu = blockIdx.x;
-  const int frame = blockIdx.y;
-  const int nmu = s2.mla_ns * s2.mla_nt;
-  const int2 cc = s2.cols[mu], rr = s2.rows[mu];
-  const int nc = cc.y - cc.x, nr = rr.y - rr.x;
-  const int4 du = s2.det_union[mu];
-  const int nsu = du.y - du.x + 1, ntu = du.w - du.z + 1;
-  float* zout = zbuf + ((long long)frame * nmu + mu) * (L2_W * L2_W);
+// Forward, pass 1: each lenslet's contribution sum_k scale_k Bt (x) Bs fa_k
+// on the union over cells of its detector windows (cells in order), written
+// to zbuf (no overlap between lenslets).
+__global__ void __launch_bounds__(kStage2Threads)
+stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_fs, int frames,
+                       float* __restrict__ zbuf) {
+  extern __shared__ __align__(16) float s2_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int TB = s2.tab_max, FB = s2.pix_max;
+  float* base = s2_smem + (long long)warp * s2.fwd_warp_floats;
+  S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [64]
+  float* tab = base + 64 * 8;                          // [2][TB]
+  float* fv = tab + 2 * TB;                            // [2][FB]
+  uint32_t* own = reinterpret_cast<uint32_t*>(fv + 2 * FB);   // [2][8]
+  float* wb = reinterpret_cast<float*>(own + 16);      // [w_max]: W[r][q], rows of nds4
+  float* zb = wb + s2.w_max;                           // [z_max]
+  S2Walk wk;
+  wk.K = s2.K;
+  wk.nmu = s2.mla_ns * s2.mla_nt;
+  const int units = frames * wk.nmu;
+  wk.nw = gridDim.x * (kStage2Threads / 32);
+  wk.w0 = blockIdx.x * (kStage2Threads / 32) + warp;
+  if (wk.w0 >= units) return;
+  wk.n_items = ((units - 1 - wk.w0) / wk.nw + 1) * wk.K;
   const long long Na = (long long)s2.arr_ns * s2.arr_nt;
-  for (int o = threadIdx.x; o < L2_W * L2_W; o += blockDim.x) Z[o] = 0.0f;
-  if (nc > 0 && nr > 0 && nsu > 0 && ntu > 0) {
-    // this thread's block pixels (at most MAXC^2 = 2 x L2_THREADS): array
-    // index, -1 where another lenslet (or none) owns the pixel, and the
-    // position in F; the same for every cell
-    static_assert(MAXC * MAXC <= 2 * L2_THREADS, "two block pixels per thread");
-    const SmallDiv dc = small_div(nc);
-    int pix[2], fix[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int o = threadIdx.x + e * L2_THREADS;
-      pix[e] = -1;
-      fix[e] = -1;
-      if (o < nr * nc) {
-        const int r = div_of(dc, o), c = o - r * nc;
-        const int px = (rr.x + r) * s2.arr_ns + cc.x + c;
-        pix[e] = __ldg(s2.owner + px) == mu ? px : -1;
-        fix[e] = r * (MAXC + 1) + c;
+  for (int o = lane; o < s2.z_max; o += 32) zb[o] = 0.0f;
+  wk.load_chunk(s2.desc, ring, 0, lane);
+  wk.load_chunk(s2.desc, ring, 1, lane);
+  __syncwarp();
+  S2Pos cur{wk.w0, 0, wk.w0 / wk.nmu}, nxt = cur;
+
+  auto issue = [&](const S2Pos& p, const S2Desc& d, int buf) {
+    if (d.off >= 0 && cell_on(s2.sub_n, s2.sub_s, p.k)) {
+      const uint32_t dm = d.dims;
+      const int n4 = (d_nc(dm) * up4(d_nds(dm)) + d_nr(dm) * d_ndt(dm) + 3) >> 2;
+      const float* t = s2.wtab + d.off;
+      for (int e = lane; e < n4; e += 32) cp_async16(smem_addr(tab + buf * TB + 4 * e), t + 4 * e, true);
+      s2_copy_block(fv + buf * FB, fa + p.frame * fa_fs + p.k * Na + d.px0, d_nr(dm), d_nc(dm), s2.arr_ns, lane);
+      if (lane < 2) cp_async16(smem_addr(own + buf * 8 + 4 * lane), s2.bits + (long long)d.mu * 16 + 4 * lane, true);
+    }
+    cp_async_commit();
+  };
+
+  issue(nxt, ring[0], 0);
+  nxt.next(wk);
+  for (int j = 0; j < wk.n_items; ++j) {
+    if ((j & 31) == 0 && j > 0) {   // chunk j / 32 starts: bring in chunk j / 32 + 1
+      wk.load_chunk(s2.desc, ring, (j >> 5) + 1, lane);
+      __syncwarp();
+    }
+    const S2Desc d = ring[j & 63];
+    if (j + 1 < wk.n_items) {
+      issue(nxt, ring[(j + 1) & 63], (j + 1) & 1);
+      nxt.next(wk);
+    } else {
+      cp_async_commit();
+    }
+    cp_async_wait_one();
+    __syncwarp();
+    const int buf = j & 1;
+    const uint32_t dm = d.dims, wn = d.win;
+    if (d.off >= 0 && cell_on(s2.sub_n, s2.sub_s, cur.k)) {
+      const int nc = d_nc(dm), nr = d_nr(dm), nds = d_nds(dm), ndt = d_ndt(dm), nsu = w_nsu(wn);
+      const int nds4 = up4(nds), nq4 = nds4 >> 2;
+      float* F = fv + buf * FB;
+      const uint32_t* OW = own + buf * 8;
+      for (int o = lane; o < nr * nc; o += 32)
+        if (!((OW[o >> 5] >> (o & 31)) & 1u)) F[o] = 0.0f;   // another lenslet's pixel
+      __syncwarp();
+      const float* bs = tab + buf * TB;
+      const float* bt = bs + nc * nds4;
+      const FDiv dq = fdiv(nq4);
+      // W[r][q..q+3] = sum_c F[r][c] Bs[c][q..q+3]
+      for (int o = lane; o < nr * nq4; o += 32) {
+        const int r = fdiv_of(dq, o), q = (o - r * nq4) << 2;
+        const float* fr = F + r * nc;
+        float4 w = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int cix = 0; cix < nc; ++cix) fma4(w, fr[cix], *reinterpret_cast<const float4*>(bs + cix * nds4 + q));
+        *reinterpret_cast<float4*>(wb + r * nds4 + q) = w;
+      }
+      __syncwarp();
+      // Z[b][q..q+3] += scale sum_r Bt[r][b] W[r][q..q+3] (columns q < nds)
+      for (int o = lane; o < ndt * nq4; o += 32) {
+        const int bb = fdiv_of(dq, o), q = (o - bb * nq4) << 2;
+        float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int r = 0; r < nr; ++r) fma4(z, bt[r * ndt + bb], *reinterpret_cast<const float4*>(wb + r * nds4 + q));
+        float* zr = zb + d.zo + bb * nsu + q;
+        zr[0] = fmaf(d.scale, z.x, zr[0]);
+        if (q + 1 < nds) zr[1] = fmaf(d.scale, z.y, zr[1]);
+        if (q + 2 < nds) zr[2] = fmaf(d.scale, z.z, zr[2]);
+        if (q + 3 < nds) zr[3] = fmaf(d.scale, z.w, zr[3]);
       }
     }
-    for (int k = 0; k < s2.K; ++k) {
-      if (!cell_on(s2.sub_n, s2.sub_s, k)) continue;   // uniform
-      const LensletParam* L = s2.lens + (long long)k * nmu + mu;
-      const int4 dr = s2.det_range[(long long)k * nmu + mu];
-      const int nds = dr.y - dr.x + 1, ndt = dr.w - dr.z + 1;
-      if (nds <= 0 || ndt <= 0) continue;   // uniform
-      // this lenslet's own pixels, zero elsewhere: loaded before the
-      // footprint entries are evaluated so that the two overlap
-      const float* fk = fa + (long long)frame * fa_fs + (long long)k * Na;
-      float fv[2];
-#pragma unroll
-      for (int e = 0; e < 2; ++e) fv[e] = pix[e] >= 0 ? __ldg(fk + pix[e]) : 0.0f;
-      lenslet_weights(L, dr, cc, rr, Bs, Bt);
-      const SmallDiv dd = small_div(nds);
-#pragma unroll
-      for (int e = 0; e < 2; ++e)
-        if (fix[e] >= 0) (&F[0][0])[fix[e]] = fv[e];
-      __syncthreads();
-      // W[r][q] = sum_c Bs[c][q] F[r][c]
-      for (int o = threadIdx.x; o < nr * nds; o += blockDim.x) {
-        const int r = div_of(dd, o), q = o - r * nds;
-        float w = 0.0f;
-        for (int c = 0; c < nc; ++c) w = fmaf(Bs[c][q], F[r][c], w);
-        W[r][q] = w;
+    if (w_last(wn)) {
+      __syncwarp();
+      const int n = w_nsu(wn) * w_ntu(wn);
+      float* zout = zbuf + (long long)cur.unit * (L2_W * L2_W);
+      for (int o = lane; o < n; o += 32) {
+        zout[o] = zb[o];
+        zb[o] = 0.0f;
       }
-      __syncthreads();
-      // Z[it][is] += scale * sum_r Bt[r][b] W[r][q] over the cell's own
-      // window inside the union (entries owned by one thread)
-      const float scale = L->scale;
-      const int zoff = (dr.z - du.z) * nsu + (dr.x - du.x);
-      for (int o = threadIdx.x; o < ndt * nds; o += blockDim.x) {
-        const int b = div_of(dd, o), q = o - b * nds;
-        const int zi = zoff + b * nsu + q;
-        float z = 0.0f;
-        for (int r = 0; r < nr; ++r) z = fmaf(Bt[r][b], W[r][q], z);
-        Z[zi] = fmaf(scale, z, Z[zi]);
-      }
-      __syncthreads();
     }
+    cur.next(wk);
+    __syncwarp();
   }
-  for (int o = threadIdx.x; o < ntu * nsu; o += blockDim.x) zout[o] = Z[o];
 }
 
 // Forward, pass 2: each detector pixel gathers the sub-images that cover it.
@@ -656,93 +716,137 @@ stage2_gather(const float* __restrict__ zbuf, float* __restrict__ y, StageTwo s2
 }
 
 // Adjoint: fa_k[jt][js] = M * scale * sum_b sum_q Bt[r][b] Bs[c][q] y[dr.z+b][dr.x+q]
-// for the lenslet's own block (a gather: every array pixel has one lenslet).
-// The lenslet's union window of y is staged once; the cells go S2_KB at a
-// time through three phases (footprint entries; U = Bt^T Y for every cell;
-// each thread's block pixel for every cell), one block barrier per phase.
-__global__ void __launch_bounds__(S2_THREADS, 8)
+// for the lenslet's own block (a gather: every array pixel has one lenslet),
+// one cell after another per warp as in the forward: U = Bt^T Y on the
+// cell's window, then every block pixel of the cell, written to that cell's
+// plane (one writer per output).  Blocks that tile the plane also clear
+// their unowned pixels; a cell outside the subset leaves its plane unwritten.
+__global__ void __launch_bounds__(kStage2Threads)
 stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, StageTwo s2, long long y_fs,
-                       long long fa_fs) {
-  __shared__ float Bs[S2_KB][MAXC][L2_W + 1];
-  __shared__ float Bt[S2_KB][MAXC][L2_W + 1];
-  __shared__ float Y[L2_W][L2_W + 1];
-  __shared__ float U[S2_KB][MAXC][L2_W + 1];
-  __shared__ S2Cell cell[S2_KB];
-  const int mu = blockIdx.x;
-  const int frame = blockIdx.y;
-  const int nmu = s2.mla_ns * s2.mla_nt;
-  const int2 cc = s2.cols[mu], rr = s2.rows[mu];
-  const int nc = cc.y - cc.x, nr = rr.y - rr.x;
-  if (nc <= 0 || nr <= 0) return;   // uniform
-  const int4 du = s2.det_union[mu];
-  const int nsu = du.y - du.x + 1, ntu = du.w - du.z + 1;
+                       long long fa_fs, int frames) {
+  extern __shared__ __align__(16) float s2_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int TB = s2.tab_max, FB = s2.pix_max, YB = s2.y_max;
+  float* base = s2_smem + (long long)warp * s2.adj_warp_floats;
+  S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [64]
+  float* tab = base + 64 * 8;                          // [2][TB]
+  float* yw = tab + 2 * TB;                            // [2][YB]: the cell's window of y, rows of nds4 (zero past nds)
+  float* mv = yw + 2 * YB;                             // [2][FB]: M on the block
+  uint32_t* bits = reinterpret_cast<uint32_t*>(mv + 2 * FB);  // [2][16]: own (0..7), clear (8..15)
+  float* ub = reinterpret_cast<float*>(bits + 32);     // [w_max]: U[r][q], rows of nds4
+  S2Walk wk;
+  wk.K = s2.K;
+  wk.nmu = s2.mla_ns * s2.mla_nt;
+  const int units = frames * wk.nmu;
+  wk.nw = gridDim.x * (kStage2Threads / 32);
+  wk.w0 = blockIdx.x * (kStage2Threads / 32) + warp;
+  if (wk.w0 >= units) return;
+  wk.n_items = ((units - 1 - wk.w0) / wk.nw + 1) * wk.K;
   const long long Na = (long long)s2.arr_ns * s2.arr_nt;
-  const float* yf = y + (long long)frame * y_fs;
-  // This thread's block pixel and what is written there, the same for every
-  // cell: M g on the lenslet's own pixels (wpx = index, mv = M), zero on
-  // unowned pixels of blocks that tile the plane (wpx = -(index + 2)),
-  // nothing elsewhere (wpx = -1).
-  int wpx = -1, pr = 0, pc = 0;
-  float mv = 0.0f;
-  if ((int)threadIdx.x < nr * nc) {
-    pr = div_of(small_div(nc), threadIdx.x);
-    pc = threadIdx.x - pr * nc;
-    const int px = (rr.x + pr) * s2.arr_ns + cc.x + pc;
-    const int own = __ldg(s2.owner + px);
-    if (own == mu) {
-      wpx = px;
-      mv = __ldg(s2.mask + px);
-    } else if (!s2.overlap && own < 0) {
-      wpx = -(px + 2);
+  wk.load_chunk(s2.desc, ring, 0, lane);
+  wk.load_chunk(s2.desc, ring, 1, lane);
+  __syncwarp();
+  S2Pos cur{wk.w0, 0, wk.w0 / wk.nmu}, nxt = cur;
+
+  auto issue = [&](const S2Pos& p, const S2Desc& d, int buf) {
+    if (cell_on(s2.sub_n, s2.sub_s, p.k)) {
+      const uint32_t dm = d.dims;
+      if (d.off >= 0) {
+        const int nds = d_nds(dm), ndt = d_ndt(dm), nds4 = up4(nds);
+        const int n4 = (d_nc(dm) * nds4 + d_nr(dm) * ndt + 3) >> 2;
+        const float* t = s2.wtab + d.off;
+        for (int e = lane; e < n4; e += 32) cp_async16(smem_addr(tab + buf * TB + 4 * e), t + 4 * e, true);
+        const float* ys = y + p.frame * y_fs + d.y0;
+        const FDiv dd = fdiv(nds);
+        float* yb = yw + buf * YB;
+        for (int o = lane; o < ndt * nds; o += 32) {
+          const int bb = fdiv_of(dd, o), q = o - bb * nds;
+          cp_async4(smem_addr(yb + bb * nds4 + q), ys + (long long)bb * s2.det_ns + q);
+        }
+        if (nds4 > nds)   // the padding columns are zero (plain stores; the copies never touch them)
+          for (int o = lane; o < ndt * (nds4 - nds); o += 32) {
+            const int bb = o / (nds4 - nds);
+            yb[bb * nds4 + nds + (o - bb * (nds4 - nds))] = 0.0f;
+          }
+        s2_copy_block(mv + buf * FB, s2.mask + d.px0, d_nr(dm), d_nc(dm), s2.arr_ns, lane);
+      }
+      if (lane < 4) cp_async16(smem_addr(bits + buf * 16 + 4 * lane), s2.bits + (long long)d.mu * 16 + 4 * lane, true);
     }
-  }
-  if (nsu > 0 && ntu > 0) {   // the union window of y, shared by every cell
-    const SmallDiv du_div = small_div(nsu);
-    for (int e = threadIdx.x; e < ntu * nsu; e += S2_THREADS) {
-      const int bu = div_of(du_div, e), qu = e - bu * nsu;
-      Y[bu][qu] = __ldg(yf + (long long)(du.z + bu) * s2.det_ns + du.x + qu);
+    cp_async_commit();
+  };
+
+  issue(nxt, ring[0], 0);
+  nxt.next(wk);
+  for (int j = 0; j < wk.n_items; ++j) {
+    if ((j & 31) == 0 && j > 0) {
+      wk.load_chunk(s2.desc, ring, (j >> 5) + 1, lane);
+      __syncwarp();
     }
-  }
-  float* faf = fa + (long long)frame * fa_fs;
-  for (int k0 = 0; k0 < s2.K; k0 += S2_KB) {
-    s2_cell_table(s2, mu, nmu, k0, du, nr, cell);
-    __syncthreads();
-    {
-      const int kk = threadIdx.x >> 6, task = threadIdx.x & 63;
-      if (cell[kk].on && task < cell[kk].nds + cell[kk].ndt)
-        lenslet_weight_task(s2.lens + (long long)(k0 + kk) * nmu + mu, cell[kk].dr, cc, rr, task, Bs[kk], Bt[kk]);
+    const S2Desc d = ring[j & 63];
+    if (j + 1 < wk.n_items) {
+      issue(nxt, ring[(j + 1) & 63], (j + 1) & 1);
+      nxt.next(wk);
+    } else {
+      cp_async_commit();
     }
-    __syncthreads();
-    // U[kk][r][q] = sum_b Bt[kk][r][b] y[dr.z + b][dr.x + q]
-    const int tot = cell[0].cnt + cell[1].cnt + cell[2].cnt + cell[3].cnt;
-    for (int e = threadIdx.x; e < tot; e += S2_THREADS) {
-      int o = e;
-      const int kk = s2_task_cell(cell, o);
-      const int r = div_of(cell[kk].dd, o), q = o - r * cell[kk].nds;
-      const int dz = cell[kk].dz, qx = cell[kk].dx + q;
-      float u = 0.0f;
-      for (int b = 0; b < cell[kk].ndt; ++b) u = fmaf(Bt[kk][r][b], Y[dz + b][qx], u);
-      U[kk][r][q] = u;
-    }
-    __syncthreads();
-    // M (its diagonal) on this lenslet's own pixels; blocks that tile the
-    // plane also clear their unowned pixels, overlapping blocks leave them.
-    // A cell outside the subset leaves its plane unwritten.
-    if (wpx != -1) {
-#pragma unroll
-      for (int kk = 0; kk < S2_KB; ++kk) {
-        if (!cell[kk].sub) continue;
-        float* fk = faf + (long long)(k0 + kk) * Na;
-        if (wpx >= 0 && cell[kk].on) {
-          float g = 0.0f;
-          for (int q = 0; q < cell[kk].nds; ++q) g = fmaf(Bs[kk][pc][q], U[kk][pr][q], g);
-          fk[wpx] = mv * (cell[kk].scale * g);
-        } else {
-          fk[wpx >= 0 ? wpx : -(wpx + 2)] = 0.0f;
+    cp_async_wait_one();
+    __syncwarp();
+    const int buf = j & 1;
+    if (cell_on(s2.sub_n, s2.sub_s, cur.k)) {
+      const uint32_t dm = d.dims;
+      const int nc = d_nc(dm), nr = d_nr(dm), nds = d_nds(dm), ndt = d_ndt(dm);
+      const uint32_t* B = bits + buf * 16;
+      float* fk = fa + cur.frame * fa_fs + cur.k * Na + d.px0;
+      const FDiv dc = fdiv(nc > 0 ? nc : 1);
+      if (d.off < 0) {   // empty window: zeros
+        for (int o = lane; o < nr * nc; o += 32) {
+          const uint32_t bit = 1u << (o & 31);
+          if ((B[o >> 5] | B[8 + (o >> 5)]) & bit) {
+            const int r = fdiv_of(dc, o), cix = o - r * nc;
+            fk[(long long)r * s2.arr_ns + cix] = 0.0f;
+          }
+        }
+      } else {
+        const int nds4 = up4(nds), nq4 = nds4 >> 2;
+        const float* bs = tab + buf * TB;
+        const float* bt = bs + nc * nds4;
+        const float* Y = yw + buf * YB;
+        const FDiv dq = fdiv(nq4);
+        // U[r][q..q+3] = sum_b Bt[r][b] Y[b][q..q+3]
+        for (int o = lane; o < nr * nq4; o += 32) {
+          const int r = fdiv_of(dq, o), q = (o - r * nq4) << 2;
+          float4 u = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          for (int bb = 0; bb < ndt; ++bb) fma4(u, bt[r * ndt + bb], *reinterpret_cast<const float4*>(Y + bb * nds4 + q));
+          *reinterpret_cast<float4*>(ub + r * nds4 + q) = u;
+        }
+        __syncwarp();
+        const float* M = mv + buf * FB;
+        for (int o = lane; o < nr * nc; o += 32) {
+          const uint32_t bit = 1u << (o & 31);
+          const bool mine = B[o >> 5] & bit;
+          if (!mine && !(B[8 + (o >> 5)] & bit)) continue;
+          const int r = fdiv_of(dc, o), cix = o - r * nc;
+          float v = 0.0f;
+          if (mine) {
+            const float* br = bs + cix * nds4;
+            const float* ur = ub + r * nds4;
+            float g = 0.0f;
+            for (int q = 0; q < nds4; q += 4) {
+              const float4 a = *reinterpret_cast<const float4*>(br + q);
+              const float4 b = *reinterpret_cast<const float4*>(ur + q);
+              g = fmaf(a.x, b.x, g);
+              g = fmaf(a.y, b.y, g);
+              g = fmaf(a.z, b.z, g);
+              g = fmaf(a.w, b.w, g);
+            }
+            v = M[o] * (d.scale * g);
+          }
+          fk[(long long)r * s2.arr_ns + cix] = v;
         }
       }
     }
-    if (k0 + S2_KB < s2.K) __syncthreads();
+    cur.next(wk);
+    __syncwarp();
   }
 }
 
@@ -822,12 +926,43 @@ cudaError_t launch_beam_adjoint_batched(const BeamBatch& b, float* x, long long 
   return cudaGetLastError();
 }
 
+size_t stage2_smem_bytes(const StageTwo& s2, bool adjoint) {
+  return (size_t)(kStage2Threads / 32) * (adjoint ? s2.adj_warp_floats : s2.fwd_warp_floats) * sizeof(float);
+}
+
+cudaError_t stage2_occupancy(const StageTwo& s2, bool adjoint, int* ctas_per_sm) {
+  const void* fn = adjoint ? (const void*)stage2_lenslet_adjoint : (const void*)stage2_lenslet_forward;
+  const size_t smem = stage2_smem_bytes(s2, adjoint);
+  // the limit is per kernel and other plans may need more: raise it to the
+  // device's opt-in maximum, never lower it
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess && smem > (size_t)optin) {
+    *ctas_per_sm = 0;
+    return cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, kStage2Threads, smem);
+  return e;
+}
+
+// Persistent grid: every resident CTA, or fewer when there are fewer
+// lenslet-frames than warps.
+static unsigned stage2_ctas(const StageTwo& s2, int per_sm, int frames) {
+  const long long units = (long long)frames * s2.mla_ns * s2.mla_nt;
+  const long long need = (units + kStage2Threads / 32 - 1) / (kStage2Threads / 32);
+  return (unsigned)std::max<long long>(1, std::min<long long>(need, (long long)s2.sms * std::max(1, per_sm)));
+}
+
 cudaError_t launch_stage2_forward(const float* fa, float* y, StageTwo s2, int frames,
                                   long long fa_frame_stride, long long y_frame_stride,
                                   float* zbuf, cudaStream_t st) {
-  if (s2.max_cols > MAXC || s2.max_rows > MAXC) return cudaErrorInvalidValue;
-  dim3 g1(s2.mla_ns * s2.mla_nt, frames);
-  stage2_lenslet_forward<<<g1, L2_THREADS, 0, st>>>(fa, s2, fa_frame_stride, zbuf);
+  if (s2.max_cols > MAXC || s2.max_rows > MAXC || !s2.desc || !s2.wtab || !s2.bits) return cudaErrorInvalidValue;
+  if (frames <= 0) return cudaSuccess;
+  if ((long long)frames * s2.mla_ns * s2.mla_nt >= (1LL << 31)) return cudaErrorInvalidValue;
+  stage2_lenslet_forward<<<stage2_ctas(s2, s2.fwd_per_sm, frames), kStage2Threads, stage2_smem_bytes(s2, false), st>>>(
+      fa, s2, fa_frame_stride, frames, zbuf);
   dim3 g2((s2.det_ns + 31) / 32, (s2.det_nt + 7) / 8, frames);
   stage2_gather<<<g2, 256, 0, st>>>(zbuf, y, s2, y_frame_stride);
   return cudaGetLastError();
@@ -836,15 +971,24 @@ cudaError_t launch_stage2_forward(const float* fa, float* y, StageTwo s2, int fr
 cudaError_t launch_stage2_adjoint(const float* y, float* fa, StageTwo s2, int frames,
                                   long long y_frame_stride, long long fa_frame_stride,
                                   cudaStream_t st) {
-  if (s2.max_cols > MAXC || s2.max_rows > MAXC) return cudaErrorInvalidValue;
+  if (s2.max_cols > MAXC || s2.max_rows > MAXC || !s2.desc || !s2.wtab || !s2.bits) return cudaErrorInvalidValue;
+  if (frames <= 0) return cudaSuccess;
+  if ((long long)frames * s2.mla_ns * s2.mla_nt >= (1LL << 31)) return cudaErrorInvalidValue;
   if (!s2.full_cover) {
-    // array pixels outside every lenslet block are never written by a lenslet CTA
+    // array pixels outside every lenslet block are never written by a lenslet warp
     for (int f = 0; f < frames; ++f)
       cudaMemsetAsync(fa + (long long)f * fa_frame_stride, 0,
                       (size_t)s2.K * s2.arr_ns * s2.arr_nt * sizeof(float), st);
   }
-  dim3 g(s2.mla_ns * s2.mla_nt, frames);
-  stage2_lenslet_adjoint<<<g, S2_THREADS, 0, st>>>(y, fa, s2, y_frame_stride, fa_frame_stride);
+  stage2_lenslet_adjoint<<<stage2_ctas(s2, s2.adj_per_sm, frames), kStage2Threads, stage2_smem_bytes(s2, true), st>>>(
+      y, fa, s2, y_frame_stride, fa_frame_stride, frames);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage2_tables(StageTwo s2, float* wtab, cudaStream_t st) {
+  if (s2.max_cols > MAXC || s2.max_rows > MAXC || !s2.desc) return cudaErrorInvalidValue;
+  dim3 g(s2.mla_ns * s2.mla_nt, s2.K);
+  stage2_table_kernel<<<g, 64, 0, st>>>(s2, wtab);
   return cudaGetLastError();
 }
 

@@ -272,6 +272,9 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.d_cand_all_s);
   cudaFree(c.d_cand_all_t);
   cudaFree(c.d_zbuf);
+  cudaFree(c.d_s2tab);
+  cudaFree(c.d_s2desc);
+  cudaFree(c.d_s2bits);
   cudaFree(c.d_fa);
   cudaFree(c.d_stab);
   cudaFree(c.d_ttab);
@@ -808,6 +811,90 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   s2.full_cover = full_cover;
   s2.sub_n = 1;
   s2.sub_s = 0;
+  // The form the stage-two kernels walk: per (lenslet, cell) a descriptor
+  // and, for a non-empty window, a transport table entry Bs (nc x nds) then
+  // Bt (nr x ndt), padded to 4 floats and evaluated once here on the device;
+  // per lenslet the ownership bits of its block.
+  if (c.K >= (1 << 15)) return set_error(LT_EUNSUPPORTED, "camera %d: %d angular cells (limit 32767)", idx, c.K);
+  std::vector<lt::S2Desc> desc((size_t)nmu * c.K);
+  std::vector<uint32_t> bits((size_t)nmu * 16, 0u);
+  long long tab = 0;
+  int tab_max = 0, pix_max = 0, w_max = 0, z_max = 0, y_max = 0;
+  for (int m = 0; m < nmu; ++m) {
+    const int nc = cols[m].y - cols[m].x, nr = rows[m].y - rows[m].x;
+    const int4 u = det_union[m];
+    const int nsu = u.y - u.x + 1, ntu = u.w - u.z + 1;
+    pix_max = std::max(pix_max, nr * nc);
+    z_max = std::max(z_max, std::max(nsu, 0) * std::max(ntu, 0));
+    for (int r = 0; r < nr; ++r)
+      for (int cix = 0; cix < nc; ++cix) {
+        const int o = r * nc + cix;
+        const int own = owner[(size_t)(rows[m].x + r) * d.arr_ns + cols[m].x + cix];
+        if (own == m) bits[(size_t)m * 16 + (o >> 5)] |= 1u << (o & 31);
+        else if (!hex && own < 0) bits[(size_t)m * 16 + 8 + (o >> 5)] |= 1u << (o & 31);
+      }
+    for (int k = 0; k < c.K; ++k) {
+      const int4 r = det_range[(size_t)k * nmu + m];
+      const int nds = r.y - r.x + 1, ndt = r.w - r.z + 1;
+      lt::S2Desc& e = desc[(size_t)m * c.K + k];
+      e.off = -1;
+      e.px0 = rows[m].x * d.arr_ns + cols[m].x;
+      e.y0 = 0;
+      e.zo = 0;
+      e.dims = (uint32_t)nc | (uint32_t)nr << 8;
+      e.scale = lens[(size_t)k * nmu + m].scale;
+      e.win = (uint32_t)std::max(nsu, 0) | (uint32_t)std::max(ntu, 0) << 8 | (uint32_t)(k == c.K - 1) << 16 |
+              (uint32_t)k << 17;
+      e.mu = m;
+      if (nds <= 0 || ndt <= 0 || nc <= 0 || nr <= 0) continue;
+      e.off = (int32_t)tab;
+      e.y0 = r.z * d.det_ns + r.x;
+      e.zo = (r.z - u.z) * nsu + (r.x - u.x);
+      e.dims |= (uint32_t)nds << 16 | (uint32_t)ndt << 24;
+      const int nds4 = (nds + 3) / 4 * 4;   // Bs rows and the windows' rows are padded to 4 floats
+      const int n = nc * nds4 + nr * ndt, n4 = (n + 3) / 4 * 4;
+      tab += n4;
+      tab_max = std::max(tab_max, n4);
+      w_max = std::max(w_max, nr * nds4);
+      y_max = std::max(y_max, nds4 * ndt);
+      if (tab >= (1LL << 31))
+        return set_error(LT_EUNSUPPORTED, "camera %d: stage-two transport table beyond 2^31 entries", idx);
+    }
+  }
+  auto up4 = [](int v) { return (std::max(v, 1) + 3) / 4 * 4; };
+  s2.tab_max = up4(tab_max);
+  s2.pix_max = up4(pix_max);
+  s2.w_max = up4(w_max);
+  s2.z_max = up4(z_max);
+  s2.y_max = up4(y_max);
+  // per warp: a ring of 64 descriptors (8 floats each), then the buffers
+  s2.fwd_warp_floats = 64 * 8 + 2 * s2.tab_max + 2 * s2.pix_max + 16 + s2.w_max + s2.z_max;
+  s2.adj_warp_floats = 64 * 8 + 2 * s2.tab_max + 2 * s2.y_max + 2 * s2.pix_max + 32 + s2.w_max;
+  if ((s = upload(desc, &c.d_s2desc, "stage-two descriptors")) != LT_OK) return s;
+  if ((s = upload(bits, &c.d_s2bits, "lenslet ownership bits")) != LT_OK) return s;
+  c.s2tab_floats = tab;
+  {
+    const size_t tb = (size_t)std::max<long long>(tab, 4) * sizeof(float);
+    cudaError_t et = device_alloc((void**)&c.d_s2tab, tb);
+    if (et != cudaSuccess) {
+      c.d_s2tab = nullptr;
+      return set_error(LT_ENOMEM, "cudaMalloc(stage-two transport table, %zu bytes): %s", tb, cudaGetErrorString(et));
+    }
+  }
+  s2.desc = c.d_s2desc;
+  s2.bits = c.d_s2bits;
+  s2.wtab = c.d_s2tab;
+  int dev = 0;
+  cudaError_t et = cudaGetDevice(&dev);
+  if (et == cudaSuccess) et = cudaDeviceGetAttribute(&s2.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (et == cudaSuccess) et = lt::stage2_occupancy(s2, false, &s2.fwd_per_sm);
+  if (et == cudaSuccess) et = lt::stage2_occupancy(s2, true, &s2.adj_per_sm);
+  if (et == cudaSuccess && (s2.fwd_per_sm < 1 || s2.adj_per_sm < 1))
+    return set_error(LT_EUNSUPPORTED, "camera %d: stage-two kernels do not fit an SM (%zu / %zu bytes of shared memory)",
+                     idx, lt::stage2_smem_bytes(s2, false), lt::stage2_smem_bytes(s2, true));
+  if (et == cudaSuccess) et = lt::launch_stage2_tables(s2, c.d_s2tab, 0);
+  if (et == cudaSuccess) et = cudaStreamSynchronize(0);
+  if (et != cudaSuccess) return cuda_error(et, "stage-two transport table");
   return LT_OK;
 }
 
