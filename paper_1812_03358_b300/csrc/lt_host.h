@@ -91,6 +91,7 @@ struct CameraPlan {
   float* d_s2tab = nullptr;        // stage-two transport table (Bs, Bt per lenslet and cell)
   lt::S2Desc* d_s2desc = nullptr;  // [N_mu][K] stage-two descriptors
   uint32_t* d_s2bits = nullptr;    // [N_mu][16] block ownership bits
+  uint32_t* d_s2ivals = nullptr;   // [N_mu][8] per-row intervals of the owned pixels
   int64_t s2tab_floats = 0;
   float* d_fa = nullptr;           // scratch array plane [F][K][Na]
   StageTwo s2{};

@@ -86,8 +86,12 @@ struct StageTwo {
                               // then Bt [nr][ndt], 16-byte aligned
   const uint32_t* bits;       // [mla_nt*mla_ns][16]: bit r*nc+c of words 0..7 = the lenslet owns block pixel (r, c);
                               // of words 8..15 = nobody owns it and blocks tile the plane (the adjoint clears it)
-  int32_t tab_max, pix_max, w_max, z_max, y_max;   // largest table entry, block, nr*nds, union window, cell window
-                                                   // (floats, multiples of 4)
+  int32_t tab_max, pix_max, w_max, z_max, y_max;   // largest table entry, block (rows of row_max), nr*nds4, union
+                                                   // window, cell window (floats, multiples of 4)
+  int32_t row_max;                                 // block row in shared memory: nc + 3 rounded up to 4
+  const uint32_t* ivals;      // [mla_nt*mla_ns][8]: per block row r, uint16 c0 | c1 << 8: the lenslet owns
+                              // exactly columns [c0, c1) of the row (valid when iv_ok)
+  int32_t iv_ok;              // every lenslet's own pixels form one interval per row
   int32_t fwd_warp_floats, adj_warp_floats;        // shared memory per warp of the two kernels
   int32_t fwd_per_sm, adj_per_sm, sms;             // resident CTAs per SM of each kernel, SM count
 };

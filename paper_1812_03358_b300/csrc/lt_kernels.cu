@@ -509,15 +509,18 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// floor(o / d) for 0 <= o < 2^12, 1 <= d <= 64 from the float reciprocal:
+// floor(o / d) for 0 <= o < 2^12, 1 <= d <= 64 from the reciprocal RN(1/d):
 // (o + 1/2) / d lies at least 1 / (2d) >= 1/128 from an integer, and the
 // product of o + 1/2 with the rounded reciprocal is off by at most
-// 2^12 * 2^-23 < 1/2000, so truncation gives the exact quotient.
-struct FDiv {
-  float inv;
-};
-__device__ __forceinline__ FDiv fdiv(int d) { return {__frcp_rn((float)d)}; }
-__device__ __forceinline__ int fdiv_of(FDiv f, int o) { return __float2int_rz(((float)o + 0.5f) * f.inv); }
+// 2^12 * 2^-23 < 1/2000, so truncation gives the exact quotient.  The
+// reciprocals are constants rounded by the compiler.
+#define LT_RCP8(b) 1.0f / (b + 0), 1.0f / (b + 1), 1.0f / (b + 2), 1.0f / (b + 3), 1.0f / (b + 4), 1.0f / (b + 5), \
+                   1.0f / (b + 6), 1.0f / (b + 7)
+__constant__ float kRcp[72] = {0.0f, 1.0f, 0.5f, 1.0f / 3, 0.25f, 0.2f, 1.0f / 6, 1.0f / 7,
+                               LT_RCP8(8), LT_RCP8(16), LT_RCP8(24), LT_RCP8(32), LT_RCP8(40),
+                               LT_RCP8(48), LT_RCP8(56), LT_RCP8(64)};
+#undef LT_RCP8
+__device__ __forceinline__ int div_small(int o, int d) { return __float2int_rz(((float)o + 0.5f) * kRcp[d]); }
 
 // The warp's cells: item j is cell j % K of lenslet-frame unit
 // w0 + (j / K) * nw (unit = frame * N_mu + mu, fewer than 2^31).  The walk
@@ -545,13 +548,27 @@ struct S2Pos {
   }
 };
 
-// Issue the copies of block pixels (nr rows of nc values starting at src,
-// row stride `stride`) into dst[r * nc + c], two rows per warp pass.
-__device__ __forceinline__ void s2_copy_block(float* dst, const float* src, int nr, int nc, long long stride,
-                                              int lane) {
-  const int c = lane & 15;
-  if (c < nc)
-    for (int r = lane >> 4; r < nr; r += 2) cp_async4(smem_addr(dst + r * nc + c), src + r * stride + c);
+// Block copies into shared memory: nr rows of n floats starting at src (row
+// stride `stride` floats) into dst rows of stride `dstride`.  Aligned mode
+// (src - shift 16-byte aligned, stride a multiple of 4, shift = the row start
+// mod 4): whole 16-byte chunks covering each row, element c landing at
+// dst[r * dstride + shift + c]; otherwise one float per copy at
+// dst[r * dstride + c] (shift 0).
+__device__ __forceinline__ void s2_copy_rows(float* dst, int dstride, const float* src, int nr, int n,
+                                             long long stride, int shift, bool aligned, int lane) {
+  if (aligned) {
+    const float* s0 = src - shift;
+    const int nch = (shift + n + 3) >> 2;
+    for (int o = lane; o < nr * nch; o += 32) {
+      const int r = div_small(o, nch), ch = o - r * nch;
+      cp_async16(smem_addr(dst + r * dstride + 4 * ch), s0 + r * stride + 4 * ch, true);
+    }
+  } else {
+    for (int o = lane; o < nr * n; o += 32) {
+      const int r = div_small(o, n), cix = o - r * n;
+      cp_async4(smem_addr(dst + r * dstride + cix), src + r * stride + cix);
+    }
+  }
 }
 
 __device__ __forceinline__ void fma4(float4& acc, float a, const float4& b) {
@@ -565,7 +582,7 @@ __device__ __forceinline__ void fma4(float4& acc, float a, const float4& b) {
 // on the union over cells of its detector windows (cells in order), written
 // to zbuf (no overlap between lenslets).
 __global__ void __launch_bounds__(kStage2Threads)
-stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_fs, int frames,
+stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_fs, int frames, int aligned,
                        float* __restrict__ zbuf) {
   extern __shared__ __align__(16) float s2_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -573,8 +590,8 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
   float* base = s2_smem + (long long)warp * s2.fwd_warp_floats;
   S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [64]
   float* tab = base + 64 * 8;                          // [2][TB]
-  float* fv = tab + 2 * TB;                            // [2][FB]
-  uint32_t* own = reinterpret_cast<uint32_t*>(fv + 2 * FB);   // [2][8]
+  float* fv = tab + 2 * TB;                            // [2][FB]: block rows of row_max
+  uint32_t* own = reinterpret_cast<uint32_t*>(fv + 2 * FB);   // [2][8]: row intervals (or ownership bits)
   float* wb = reinterpret_cast<float*>(own + 16);      // [w_max]: W[r][q], rows of nds4
   float* zb = wb + s2.w_max;                           // [z_max]
   S2Walk wk;
@@ -598,8 +615,12 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
       const int n4 = (d_nc(dm) * up4(d_nds(dm)) + d_nr(dm) * d_ndt(dm) + 3) >> 2;
       const float* t = s2.wtab + d.off;
       for (int e = lane; e < n4; e += 32) cp_async16(smem_addr(tab + buf * TB + 4 * e), t + 4 * e, true);
-      s2_copy_block(fv + buf * FB, fa + p.frame * fa_fs + p.k * Na + d.px0, d_nr(dm), d_nc(dm), s2.arr_ns, lane);
-      if (lane < 2) cp_async16(smem_addr(own + buf * 8 + 4 * lane), s2.bits + (long long)d.mu * 16 + 4 * lane, true);
+      s2_copy_rows(fv + buf * FB, s2.row_max, fa + p.frame * fa_fs + p.k * Na + d.px0, d_nr(dm), d_nc(dm), s2.arr_ns,
+                   aligned ? (d.px0 & 3) : 0, aligned, lane);
+      if (lane < 2) {
+        const uint32_t* src = s2.iv_ok ? s2.ivals + (long long)d.mu * 8 : s2.bits + (long long)d.mu * 16;
+        cp_async16(smem_addr(own + buf * 8 + 4 * lane), src + 4 * lane, true);
+      }
     }
     cp_async_commit();
   };
@@ -625,26 +646,34 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
     if (d.off >= 0 && cell_on(s2.sub_n, s2.sub_s, cur.k)) {
       const int nc = d_nc(dm), nr = d_nr(dm), nds = d_nds(dm), ndt = d_ndt(dm), nsu = w_nsu(wn);
       const int nds4 = up4(nds), nq4 = nds4 >> 2;
-      float* F = fv + buf * FB;
+      const float* F = fv + buf * FB + (aligned ? (d.px0 & 3) : 0);
       const uint32_t* OW = own + buf * 8;
-      for (int o = lane; o < nr * nc; o += 32)
-        if (!((OW[o >> 5] >> (o & 31)) & 1u)) F[o] = 0.0f;   // another lenslet's pixel
-      __syncwarp();
       const float* bs = tab + buf * TB;
       const float* bt = bs + nc * nds4;
-      const FDiv dq = fdiv(nq4);
-      // W[r][q..q+3] = sum_c F[r][c] Bs[c][q..q+3]
+      // W[r][q..q+3] = sum_c F[r][c] Bs[c][q..q+3] over the lenslet's own
+      // pixels of row r: the interval [c0, c1) of the row (or, when some row's
+      // are not one interval, every c with its ownership bit)
       for (int o = lane; o < nr * nq4; o += 32) {
-        const int r = fdiv_of(dq, o), q = (o - r * nq4) << 2;
-        const float* fr = F + r * nc;
+        const int r = div_small(o, nq4), q = (o - r * nq4) << 2;
+        const float* fr = F + r * s2.row_max;
         float4 w = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (int cix = 0; cix < nc; ++cix) fma4(w, fr[cix], *reinterpret_cast<const float4*>(bs + cix * nds4 + q));
+        if (s2.iv_ok) {
+          const uint32_t iv = reinterpret_cast<const uint16_t*>(OW)[r];
+          for (int cix = iv & 0xff; cix < (int)(iv >> 8); ++cix)
+            fma4(w, fr[cix], *reinterpret_cast<const float4*>(bs + cix * nds4 + q));
+        } else {
+          for (int cix = 0; cix < nc; ++cix) {
+            const uint32_t bit = r * nc + cix;
+            const float f = (OW[bit >> 5] >> (bit & 31)) & 1u ? fr[cix] : 0.0f;
+            fma4(w, f, *reinterpret_cast<const float4*>(bs + cix * nds4 + q));
+          }
+        }
         *reinterpret_cast<float4*>(wb + r * nds4 + q) = w;
       }
       __syncwarp();
       // Z[b][q..q+3] += scale sum_r Bt[r][b] W[r][q..q+3] (columns q < nds)
       for (int o = lane; o < ndt * nq4; o += 32) {
-        const int bb = fdiv_of(dq, o), q = (o - bb * nq4) << 2;
+        const int bb = div_small(o, nq4), q = (o - bb * nq4) << 2;
         float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         for (int r = 0; r < nr; ++r) fma4(z, bt[r * ndt + bb], *reinterpret_cast<const float4*>(wb + r * nds4 + q));
         float* zr = zb + d.zo + bb * nsu + q;
@@ -723,7 +752,7 @@ stage2_gather(const float* __restrict__ zbuf, float* __restrict__ y, StageTwo s2
 // their unowned pixels; a cell outside the subset leaves its plane unwritten.
 __global__ void __launch_bounds__(kStage2Threads)
 stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, StageTwo s2, long long y_fs,
-                       long long fa_fs, int frames) {
+                       long long fa_fs, int frames, int aligned) {
   extern __shared__ __align__(16) float s2_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int TB = s2.tab_max, FB = s2.pix_max, YB = s2.y_max;
@@ -731,8 +760,8 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
   S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [64]
   float* tab = base + 64 * 8;                          // [2][TB]
   float* yw = tab + 2 * TB;                            // [2][YB]: the cell's window of y, rows of nds4 (zero past nds)
-  float* mv = yw + 2 * YB;                             // [2][FB]: M on the block
-  uint32_t* bits = reinterpret_cast<uint32_t*>(mv + 2 * FB);  // [2][16]: own (0..7), clear (8..15)
+  float* mv = yw + 2 * YB;                             // [2][FB]: M on the block, rows of row_max
+  uint32_t* bits = reinterpret_cast<uint32_t*>(mv + 2 * FB);  // [2][16]: row intervals, or own (0..7), clear (8..15)
   float* ub = reinterpret_cast<float*>(bits + 32);     // [w_max]: U[r][q], rows of nds4
   S2Walk wk;
   wk.K = s2.K;
@@ -757,20 +786,22 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
         const float* t = s2.wtab + d.off;
         for (int e = lane; e < n4; e += 32) cp_async16(smem_addr(tab + buf * TB + 4 * e), t + 4 * e, true);
         const float* ys = y + p.frame * y_fs + d.y0;
-        const FDiv dd = fdiv(nds);
         float* yb = yw + buf * YB;
-        for (int o = lane; o < ndt * nds; o += 32) {
-          const int bb = fdiv_of(dd, o), q = o - bb * nds;
-          cp_async4(smem_addr(yb + bb * nds4 + q), ys + (long long)bb * s2.det_ns + q);
-        }
+        // the window one float per copy, so that its rows start 16-byte aligned
+        s2_copy_rows(yb, nds4, ys, ndt, nds, s2.det_ns, 0, false, lane);
         if (nds4 > nds)   // the padding columns are zero (plain stores; the copies never touch them)
           for (int o = lane; o < ndt * (nds4 - nds); o += 32) {
-            const int bb = o / (nds4 - nds);
+            const int bb = div_small(o, nds4 - nds);
             yb[bb * nds4 + nds + (o - bb * (nds4 - nds))] = 0.0f;
           }
-        s2_copy_block(mv + buf * FB, s2.mask + d.px0, d_nr(dm), d_nc(dm), s2.arr_ns, lane);
+        s2_copy_rows(mv + buf * FB, s2.row_max, s2.mask + d.px0, d_nr(dm), d_nc(dm), s2.arr_ns,
+                     aligned ? (d.px0 & 3) : 0, aligned, lane);
       }
-      if (lane < 4) cp_async16(smem_addr(bits + buf * 16 + 4 * lane), s2.bits + (long long)d.mu * 16 + 4 * lane, true);
+      if (s2.iv_ok) {
+        if (lane < 2) cp_async16(smem_addr(bits + buf * 16 + 4 * lane), s2.ivals + (long long)d.mu * 8 + 4 * lane, true);
+      } else if (lane < 4) {
+        cp_async16(smem_addr(bits + buf * 16 + 4 * lane), s2.bits + (long long)d.mu * 16 + 4 * lane, true);
+      }
     }
     cp_async_commit();
   };
@@ -796,36 +827,44 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
       const uint32_t dm = d.dims;
       const int nc = d_nc(dm), nr = d_nr(dm), nds = d_nds(dm), ndt = d_ndt(dm);
       const uint32_t* B = bits + buf * 16;
+      const uint16_t* IV = reinterpret_cast<const uint16_t*>(B);
+      // pixel (r, c) of the block: the lenslet's own (written with its value),
+      // or nobody's in blocks that tile the plane (written zero)?
+      auto mine_of = [&](int r, int cix, int o) -> bool {
+        if (s2.iv_ok) {
+          const uint32_t iv = IV[r];
+          return cix >= (int)(iv & 0xff) && cix < (int)(iv >> 8);
+        }
+        return (B[o >> 5] >> (o & 31)) & 1u;
+      };
+      auto clear_of = [&](int o) -> bool {
+        if (s2.iv_ok) return !s2.overlap;
+        return (B[8 + (o >> 5)] >> (o & 31)) & 1u;
+      };
       float* fk = fa + cur.frame * fa_fs + cur.k * Na + d.px0;
-      const FDiv dc = fdiv(nc > 0 ? nc : 1);
       if (d.off < 0) {   // empty window: zeros
         for (int o = lane; o < nr * nc; o += 32) {
-          const uint32_t bit = 1u << (o & 31);
-          if ((B[o >> 5] | B[8 + (o >> 5)]) & bit) {
-            const int r = fdiv_of(dc, o), cix = o - r * nc;
-            fk[(long long)r * s2.arr_ns + cix] = 0.0f;
-          }
+          const int r = div_small(o, nc), cix = o - r * nc;
+          if (mine_of(r, cix, o) || clear_of(o)) fk[(long long)r * s2.arr_ns + cix] = 0.0f;
         }
       } else {
         const int nds4 = up4(nds), nq4 = nds4 >> 2;
         const float* bs = tab + buf * TB;
         const float* bt = bs + nc * nds4;
         const float* Y = yw + buf * YB;
-        const FDiv dq = fdiv(nq4);
         // U[r][q..q+3] = sum_b Bt[r][b] Y[b][q..q+3]
         for (int o = lane; o < nr * nq4; o += 32) {
-          const int r = fdiv_of(dq, o), q = (o - r * nq4) << 2;
+          const int r = div_small(o, nq4), q = (o - r * nq4) << 2;
           float4 u = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
           for (int bb = 0; bb < ndt; ++bb) fma4(u, bt[r * ndt + bb], *reinterpret_cast<const float4*>(Y + bb * nds4 + q));
           *reinterpret_cast<float4*>(ub + r * nds4 + q) = u;
         }
         __syncwarp();
-        const float* M = mv + buf * FB;
+        const float* M = mv + buf * FB + (aligned ? (d.px0 & 3) : 0);
         for (int o = lane; o < nr * nc; o += 32) {
-          const uint32_t bit = 1u << (o & 31);
-          const bool mine = B[o >> 5] & bit;
-          if (!mine && !(B[8 + (o >> 5)] & bit)) continue;
-          const int r = fdiv_of(dc, o), cix = o - r * nc;
+          const int r = div_small(o, nc), cix = o - r * nc;
+          const bool mine = mine_of(r, cix, o);
+          if (!mine && !clear_of(o)) continue;
           float v = 0.0f;
           if (mine) {
             const float* br = bs + cix * nds4;
@@ -839,7 +878,7 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
               g = fmaf(a.z, b.z, g);
               g = fmaf(a.w, b.w, g);
             }
-            v = M[o] * (d.scale * g);
+            v = M[r * s2.row_max + cix] * (d.scale * g);
           }
           fk[(long long)r * s2.arr_ns + cix] = v;
         }
@@ -961,8 +1000,10 @@ cudaError_t launch_stage2_forward(const float* fa, float* y, StageTwo s2, int fr
   if (s2.max_cols > MAXC || s2.max_rows > MAXC || !s2.desc || !s2.wtab || !s2.bits) return cudaErrorInvalidValue;
   if (frames <= 0) return cudaSuccess;
   if ((long long)frames * s2.mla_ns * s2.mla_nt >= (1LL << 31)) return cudaErrorInvalidValue;
+  // 16-byte block copies when the rows start 4-aligned up to one shift per block
+  const int aligned = (reinterpret_cast<uintptr_t>(fa) & 15) == 0 && s2.arr_ns % 4 == 0 && fa_frame_stride % 4 == 0;
   stage2_lenslet_forward<<<stage2_ctas(s2, s2.fwd_per_sm, frames), kStage2Threads, stage2_smem_bytes(s2, false), st>>>(
-      fa, s2, fa_frame_stride, frames, zbuf);
+      fa, s2, fa_frame_stride, frames, aligned, zbuf);
   dim3 g2((s2.det_ns + 31) / 32, (s2.det_nt + 7) / 8, frames);
   stage2_gather<<<g2, 256, 0, st>>>(zbuf, y, s2, y_frame_stride);
   return cudaGetLastError();
@@ -980,8 +1021,9 @@ cudaError_t launch_stage2_adjoint(const float* y, float* fa, StageTwo s2, int fr
       cudaMemsetAsync(fa + (long long)f * fa_frame_stride, 0,
                       (size_t)s2.K * s2.arr_ns * s2.arr_nt * sizeof(float), st);
   }
+  const int aligned = (reinterpret_cast<uintptr_t>(s2.mask) & 15) == 0 && s2.arr_ns % 4 == 0;
   stage2_lenslet_adjoint<<<stage2_ctas(s2, s2.adj_per_sm, frames), kStage2Threads, stage2_smem_bytes(s2, true), st>>>(
-      y, fa, s2, y_frame_stride, fa_frame_stride, frames);
+      y, fa, s2, y_frame_stride, fa_frame_stride, frames, aligned);
   return cudaGetLastError();
 }
 

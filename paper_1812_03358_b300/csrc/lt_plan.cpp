@@ -275,6 +275,7 @@ static void free_camera(CameraPlan& c) {
   cudaFree(c.d_s2tab);
   cudaFree(c.d_s2desc);
   cudaFree(c.d_s2bits);
+  cudaFree(c.d_s2ivals);
   cudaFree(c.d_fa);
   cudaFree(c.d_stab);
   cudaFree(c.d_ttab);
@@ -818,6 +819,8 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   if (c.K >= (1 << 15)) return set_error(LT_EUNSUPPORTED, "camera %d: %d angular cells (limit 32767)", idx, c.K);
   std::vector<lt::S2Desc> desc((size_t)nmu * c.K);
   std::vector<uint32_t> bits((size_t)nmu * 16, 0u);
+  std::vector<uint32_t> ivals((size_t)nmu * 8, 0u);   // uint16 per row: c0 | c1 << 8
+  int iv_ok = 1;
   long long tab = 0;
   int tab_max = 0, pix_max = 0, w_max = 0, z_max = 0, y_max = 0;
   for (int m = 0; m < nmu; ++m) {
@@ -826,13 +829,28 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
     const int nsu = u.y - u.x + 1, ntu = u.w - u.z + 1;
     pix_max = std::max(pix_max, nr * nc);
     z_max = std::max(z_max, std::max(nsu, 0) * std::max(ntu, 0));
-    for (int r = 0; r < nr; ++r)
+    for (int r = 0; r < nr; ++r) {
+      int c0 = -1, c1 = -1, runs = 0;
       for (int cix = 0; cix < nc; ++cix) {
         const int o = r * nc + cix;
         const int own = owner[(size_t)(rows[m].x + r) * d.arr_ns + cols[m].x + cix];
-        if (own == m) bits[(size_t)m * 16 + (o >> 5)] |= 1u << (o & 31);
-        else if (!hex && own < 0) bits[(size_t)m * 16 + 8 + (o >> 5)] |= 1u << (o & 31);
+        if (own == m) {
+          bits[(size_t)m * 16 + (o >> 5)] |= 1u << (o & 31);
+          if (c1 != cix) {
+            ++runs;
+            c0 = cix;
+          }
+          c1 = cix + 1;
+        } else if (!hex && own < 0) {
+          bits[(size_t)m * 16 + 8 + (o >> 5)] |= 1u << (o & 31);
+        } else if (!hex) {
+          iv_ok = 0;   // another lenslet's pixel inside a tiling block: keep the bits
+        }
       }
+      if (runs > 1) iv_ok = 0;
+      const uint32_t iv = runs ? (uint32_t)c0 | (uint32_t)c1 << 8 : 0u;
+      ivals[(size_t)m * 8 + (r >> 1)] |= iv << (16 * (r & 1));
+    }
     for (int k = 0; k < c.K; ++k) {
       const int4 r = det_range[(size_t)k * nmu + m];
       const int nds = r.y - r.x + 1, ndt = r.w - r.z + 1;
@@ -863,7 +881,8 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   }
   auto up4 = [](int v) { return (std::max(v, 1) + 3) / 4 * 4; };
   s2.tab_max = up4(tab_max);
-  s2.pix_max = up4(pix_max);
+  s2.row_max = up4(max_cols + 3);                  // a block row copied in 16-byte chunks, shifted by up to 3
+  s2.pix_max = up4(std::max(max_rows, 1) * s2.row_max);
   s2.w_max = up4(w_max);
   s2.z_max = up4(z_max);
   s2.y_max = up4(y_max);
@@ -872,6 +891,9 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   s2.adj_warp_floats = 64 * 8 + 2 * s2.tab_max + 2 * s2.y_max + 2 * s2.pix_max + 32 + s2.w_max;
   if ((s = upload(desc, &c.d_s2desc, "stage-two descriptors")) != LT_OK) return s;
   if ((s = upload(bits, &c.d_s2bits, "lenslet ownership bits")) != LT_OK) return s;
+  if ((s = upload(ivals, &c.d_s2ivals, "lenslet row intervals")) != LT_OK) return s;
+  s2.ivals = c.d_s2ivals;
+  s2.iv_ok = iv_ok;
   c.s2tab_floats = tab;
   {
     const size_t tb = (size_t)std::max<long long>(tab, 4) * sizeof(float);
