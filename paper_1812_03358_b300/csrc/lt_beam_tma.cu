@@ -4,29 +4,30 @@
 // For one angular cell k and slice n the slice -> plane transport of a
 // 32 x 32 tile of target pixels reads a small rectangle of the slice (a
 // "brick": the voxel columns and rows the tile's footprints touch) and
-// contracts it twice, along s then along t (eq. xport,sep).  Here every warp
-// owns whole slices:
+// contracts it twice, along s then along t (eq. xport,sep).  A persistent
+// CTA is one producer warp and four consumer warps:
 //
-//   * a persistent CTA of four warps takes a work item (camera, cell or all
-//     cells, tile, frame) from a counter; its warps take every fourth
-//     (cell, slice) pair of the item;
-//   * the footprint weights of every (cell, slice, tile column) and
-//     (cell, slice, tile row) are evaluated once per plan into tables
-//     (lane = pixel column for s, lane = pixel row for t), together with the
-//     brick's origin;
-//   * three slices ahead of the one it contracts, lane 0 of a warp fills a
-//     stage of a four-stage ring: one cp.async.bulk.tensor load of the
-//     brick and two bulk copies of the slice's table entries, all completing
-//     one mbarrier, so volume and weights reach shared memory through TMA
-//     while the warp computes;
-//   * the contraction keeps the tile column of every lane: the s-contracted
-//     voxel rows T[k][col] of the brick (each computed once, into the lane's
-//     own column of shared memory) and 32 accumulators in registers, one per
-//     pixel row; pixel rows come in groups of four whose taps fall in one
-//     band of NB voxel rows, so a group is 4 x NB FMAs against broadcast
-//     band weights, with every load address known up front;
-//   * at the end of an item the four warps' partial tiles are summed in a
-//     fixed order and written with the mask M (Sec. II-D).
+//   * the producer takes work items (camera, cell or all cells, tile, frame;
+//     long items split into chunks of about 32 pairs) from a counter, in the
+//     order of a list sorted longest first, posts each item's pair count in a
+//     small record ring, and for every (cell, slice) pair of the item fills the next
+//     stage of an eight-stage ring with one cp.async.bulk.tensor load of the
+//     brick and two bulk copies of the pair's footprint-weight table entries
+//     (evaluated once per plan), all completing the stage's mbarrier.  Four
+//     lanes fill four stages at a time, so the mbarrier round trips of four
+//     pairs overlap; the brick origins of 32 consecutive slices come in with
+//     one coalesced load per lane;
+//   * consumer warp w takes pairs w, w + 4, ... of every item.  Per pair it
+//     s-contracts every brick row into its own rows of shared memory (lane =
+//     pixel column), then t-contracts them (lane = pixel row): each lane owns
+//     one pixel row of the tile, keeps its 32 accumulators in registers and
+//     its W tap rows' weights and first row in registers, so every load of
+//     the t-contraction is a conflict-free 8-byte load of two adjacent
+//     pixel columns at an address known before the pair starts, and every
+//     two multiply-adds are one packed f32x2 FMA (the same two
+//     round-to-nearest FMAs as fmaf);
+//   * at the end of an item the four consumers' partial tiles are summed in
+//     warp order and written with the mask M (Sec. II-D).
 //
 // Every matrix entry is the same product of the same footprint integrals as
 // in the other beam kernels (lt_beam_math.cuh), so forward and adjoint stay
@@ -34,9 +35,9 @@
 // TMA load fills zeros, which contribute exact zeros.  Every mbarrier wait is
 // bounded: a wait that gives up records bit 1 of the projector status word
 // and the CTA stops taking work.  A table entry whose taps would not fit
-// its brick or band is zeroed and reported when the tables are built (the
-// planner sizes both so that this cannot happen, and a plan whose tables
-// report it keeps the direct kernel).
+// its brick is zeroed and reported when the tables are built (the planner
+// sizes bricks so that this cannot happen, and a plan whose tables report
+// it keeps the direct kernel).
 #include <cuda.h>
 
 #include <algorithm>
@@ -52,39 +53,51 @@ namespace {
 
 __device__ int g_projector_status;
 
-constexpr int TM_WARPS = 4;
-constexpr int TM_STAGES = 3;
-constexpr int TM_EMPTY_BATCH = 16;   // empty tiles zeroed per work ticket
+constexpr int FC = 4;                   // consumer warps
+constexpr int FTHREADS = (FC + 1) * 32; // + the producer warp
+constexpr int FG = 4;                   // slices per stage fill
+constexpr int FSLOTS = 6;               // stages
+constexpr int FRECS = 4;                // item records
+constexpr int FTS = 34;                 // row stride (floats) of a consumer's s-contracted rows
+constexpr int FEMPTY = 16;              // empty tiles zeroed per work ticket
+constexpr int FMAX_BY = 64;             // brick rows the kernel accepts
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long kTmaWaitPolls = 1LL << 22;   // polls (with back-off) before a wait gives up
 
-// Weights of one (cell, slice) for a column of 32-pixel tiles (s) and a row
-// of 32-pixel tiles (t), built once per plan (beam_weight_tables) in exactly
-// the layout the kernel stages in shared memory, so that a bulk copy brings
-// them next to the brick.
+// Weights of one (cell, slice) for a column of 32-pixel tiles (s, lane =
+// pixel column) and a row of 32-pixel tiles (t, lane = pixel row), built
+// once per plan (beam_weight_tables) in exactly the layout the kernel
+// stages in shared memory, so that a bulk copy brings them next to the
+// brick.  The brick origins live in separate arrays, slices innermost.
 template <int W>
 struct __align__(16) SPart {
   float ws[W][32];   // s-weights of each pixel column
   int sx[32];        // first tap column of each pixel column, relative to the brick
-  int x0;            // brick's first column (a multiple of 4)
-  int ok;            // 0: the taps did not fit the planned brick (weights zeroed)
-  int pad[2];
 };
-template <int NB>
+template <int W>
 struct __align__(16) TPart {
-  float wl[32][NB];  // band weights of each pixel row (t-weight x slice scale at its taps)
-  int base[8];       // first band row of each group of four pixel rows, relative to the brick
-  int y0;            // brick's first row
-  int ok;
-  int pad[2];
+  float tw[W][32];   // t-weights x slice scale of each pixel row
+  int ty[32];        // first tap row of each pixel row, relative to the brick
 };
 
+// Item record: what the producer tells the consumers about the next item.
+struct FwdRec {
+  int kind;          // kRecItem, kRecEmpty or kRecEnd
+  int ticket;
+  int L;             // pairs of the item (this chunk's)
+  uint32_t g0;       // stage fill count of its first pair
+};
+constexpr int kRecItem = 0, kRecEmpty = 1, kRecEnd = 2;
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_init1(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t done;
@@ -97,7 +110,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait for phase `parity`; false if it gave up.
+// Bounded wait for the phase of parity `parity`; false if it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
   for (long long i = 0; i < kTmaWaitPolls; ++i) {
     if (mbar_try(bar, parity)) return true;
@@ -110,6 +123,11 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 // One target pixel's footprint along one axis: first tap (source index) and
@@ -130,199 +148,155 @@ __device__ __forceinline__ int taps(const AxisParam& ap, int i, float (&w)[W]) {
   return jc + mlo;
 }
 
-// s-part of one (cell, slice, tile column): lane = pixel column.
+// Table entries are grouped by FG consecutive slices: a stage fill brings
+// the bricks of one group (one 3-D TMA box, FG planes) and the group's FG
+// s- and t-parts (one bulk copy each), so entries are stored with slices
+// innermost, [cell][tile][slice] with the slice count rounded up to a
+// multiple of FG (padding entries are zero), and the brick origin is one per
+// group: the smallest first tap over the group's slices and the tile's
+// pixels (columns rounded down to 4, a TMA box starts on 16 bytes).
+__host__ __device__ __forceinline__ int padded_slices(int nz) { return (nz + FG - 1) / FG * FG; }
+
+// First pass, block (tile, slice, cell): the footprint weights of one slice
+// for a tile column (warp 0, lane = pixel column) and a tile row (warp 1,
+// lane = pixel row), with the absolute first taps; the second pass makes
+// them relative to the group's origin.
 template <int W>
-__device__ __forceinline__ void build_spart(const SliceParam& p, int is0, int lane, int bx, SPart<W>& S, int* bad) {
-  float ws[W];
-  const int sx0 = taps<W>(p.s, is0 + lane, ws);
-  const int smin = __reduce_min_sync(FULL, sx0), smax = __reduce_max_sync(FULL, sx0);
-  const int x0 = smin & ~3;   // floor to a multiple of 4 columns: a TMA box starts on 16 bytes
-  const bool ok = smax + W - 1 - x0 < bx;
-#pragma unroll
-  for (int a = 0; a < W; ++a) S.ws[a][lane] = ok ? ws[a] : 0.0f;
-  S.sx[lane] = ok ? sx0 - x0 : 0;
-  if (lane == 0) {
-    S.x0 = x0;
-    S.ok = ok;
-    S.pad[0] = S.pad[1] = 0;
-    if (!ok) atomicOr(bad, 1);
-  }
-}
-
-// t-part of one (cell, slice, tile row): lane = pixel row.  A group of four
-// rows keeps its taps in NB band rows from its smallest first tap.
-template <int W, int NB>
-__device__ __forceinline__ void build_tpart(const SliceParam& p, int it0, int lane, int by, TPart<NB>& T, int* bad) {
-  float tw[W];
-  const int ty0 = taps<W>(p.t, it0 + lane, tw);
-  const int tmin = __reduce_min_sync(FULL, ty0), tmax = __reduce_max_sync(FULL, ty0);
-  int gb = min(ty0, __shfl_xor_sync(FULL, ty0, 1));
-  gb = min(gb, __shfl_xor_sync(FULL, gb, 2));
-  const bool ok = __all_sync(FULL, tmax - tmin + NB <= by && ty0 + W - 1 - gb < NB);
-  float wl[NB];
-#pragma unroll
-  for (int m = 0; m < NB; ++m) wl[m] = 0.0f;
-  if (ok) {
-#pragma unroll
-    for (int b = 0; b < W; ++b) {
-      const int m = ty0 + b - gb;
-      const float v = __fmul_rn(tw[b], p.scale);
-#pragma unroll
-      for (int mm = 0; mm < NB; ++mm)
-        if (m == mm) wl[mm] = v;
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < NB; ++m) T.wl[lane][m] = wl[m];
-  if ((lane & 3) == 0) T.base[lane >> 2] = ok ? gb - tmin : 0;
-  if (lane == 0) {
-    T.y0 = tmin;
-    T.ok = ok;
-    T.pad[0] = T.pad[1] = 0;
-    if (!ok) atomicOr(bad, 1);
-  }
-}
-
-// Plan-time tables: block (tile, slice, cell); warp 0 the s-part of tile
-// column blockIdx.x, warp 1 the t-part of tile row blockIdx.x.
-template <int W, int NB>
 __global__ void __launch_bounds__(64) beam_weight_tables(const SliceParam* __restrict__ prm, int nz, int tiles_s,
-                                                         int tiles_t, int bx, int by, SPart<W>* __restrict__ stab,
-                                                         TPart<NB>* __restrict__ ttab, int* __restrict__ bad) {
+                                                         int tiles_t, SPart<W>* __restrict__ stab,
+                                                         TPart<W>* __restrict__ ttab) {
   const int tile = blockIdx.x, n = blockIdx.y, k = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const SliceParam p = prm[(long long)k * nz + n];
-  if (warp == 0 && tile < tiles_s)
-    build_spart<W>(p, tile * kBeamTileS, lane, bx, stab[((long long)k * nz + n) * tiles_s + tile], bad);
-  if (warp == 1 && tile < tiles_t)
-    build_tpart<W, NB>(p, tile * kBeamTileT, lane, by, ttab[((long long)k * nz + n) * tiles_t + tile], bad);
+  const long long nzp = padded_slices(nz);
+  if (warp == 0 && tile < tiles_s) {
+    float w[W];
+    SPart<W>& S = stab[((long long)k * tiles_s + tile) * nzp + n];
+    S.sx[lane] = taps<W>(p.s, tile * kBeamTileS + lane, w);
+#pragma unroll
+    for (int a = 0; a < W; ++a) S.ws[a][lane] = w[a];
+  }
+  if (warp == 1 && tile < tiles_t) {
+    float w[W];
+    TPart<W>& T = ttab[((long long)k * tiles_t + tile) * nzp + n];
+    T.ty[lane] = taps<W>(p.t, tile * kBeamTileT + lane, w);
+#pragma unroll
+    for (int a = 0; a < W; ++a) T.tw[a][lane] = __fmul_rn(w[a], p.scale);
+  }
 }
 
-// s-contraction of brick row `off` (a row start) for this lane's pixel column.
+// Second pass, block (tile, group, cell): the group origin of a tile column
+// (warp 0) and a tile row (warp 1), and every first tap of the group made
+// relative to it.  An entry whose taps would leave the planned brick is
+// zeroed and reported in *bad (the planner sizes bricks so that this does
+// not happen).  Origins: ox[(k * tiles_s + tile) * groups + group], oy
+// likewise.
 template <int W>
-__device__ __forceinline__ float trow(const float* bc, int off, const float (&ws)[W]) {
-  float u = 0.0f;
+__global__ void __launch_bounds__(64) beam_group_origins(int nz, int tiles_s, int tiles_t, int bx, int by,
+                                                         SPart<W>* __restrict__ stab, TPart<W>* __restrict__ ttab,
+                                                         int* __restrict__ ox, int* __restrict__ oy,
+                                                         int* __restrict__ bad) {
+  const int tile = blockIdx.x, grp = blockIdx.y, k = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long nzp = padded_slices(nz), groups = nzp / FG;
+  const int n0 = grp * FG, n1 = min(nz, n0 + FG);
+  const int tiles = warp == 0 ? tiles_s : tiles_t;
+  if (warp > 1 || tile >= tiles) return;
+  const long long base = ((long long)k * tiles + tile) * nzp;
+  int lo = 0x7fffffff;
+  for (int n = n0; n < n1; ++n) lo = min(lo, warp == 0 ? stab[base + n].sx[lane] : ttab[base + n].ty[lane]);
+  lo = __reduce_min_sync(FULL, lo);
+  const int org = warp == 0 ? (lo & ~3) : lo;
+  const int ext = warp == 0 ? bx : by;
+  for (int n = n0; n < n1; ++n) {
+    int& f = warp == 0 ? stab[base + n].sx[lane] : ttab[base + n].ty[lane];
+    const bool ok = __all_sync(FULL, f - org + W - 1 < ext);
+    f = ok ? f - org : 0;
 #pragma unroll
-  for (int a = 0; a < W; ++a) u = fmaf(ws[a], bc[off + a], u);
-  return u;
-}
-
-// One slice of one tile column (this lane's): the s-contraction of every
-// brick row into the lane's own column of Tw, then each group of four pixel
-// rows against its NB band rows.  Every load's address is known before any
-// of them is needed, so the loads of all groups overlap.
-template <int W, int NB>
-__device__ __forceinline__ void contract_slice(const SPart<W>& S, const TPart<NB>& T, const float* brick, int bx,
-                                               int by, float* Tw, int lane, float (&acc)[32]) {
-  float ws[W];
-#pragma unroll
-  for (int a = 0; a < W; ++a) ws[a] = S.ws[a][lane];
-  const float* bc = brick + S.sx[lane];
-#pragma unroll 2
-  for (int k = 0; k < by; ++k) Tw[k * 32] = trow<W>(bc, k * bx, ws);
-#pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    const int b = T.base[g];
-    float R[NB];
-#pragma unroll
-    for (int m = 0; m < NB; ++m) R[m] = Tw[(b + m) * 32];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int row = 4 * g + i;
-      const float4* wr = reinterpret_cast<const float4*>(T.wl[row]);
-      float a = acc[row];
-#pragma unroll
-      for (int q = 0; q < NB / 4; ++q) {
-        const float4 w = wr[q];
-        a = fmaf(w.x, R[4 * q], a);
-        a = fmaf(w.y, R[4 * q + 1], a);
-        a = fmaf(w.z, R[4 * q + 2], a);
-        a = fmaf(w.w, R[4 * q + 3], a);
-      }
-      acc[row] = a;
+    for (int a = 0; a < W; ++a) {
+      float& v = warp == 0 ? stab[base + n].ws[a][lane] : ttab[base + n].tw[a][lane];
+      if (!ok) v = 0.0f;
     }
+    if (!ok && lane == 0) atomicOr(bad, 1);
   }
+  if (lane == 0) (warp == 0 ? ox : oy)[((long long)k * tiles + tile) * groups + grp] = org;
 }
 
-// Position in an item's sequence of (cell, slice) pairs: cells k of
-// [k, k_end) that belong to the subset, slices [n, n1) of each.
-struct PairCursor {
-  int k, n, n1, k_end;
-  bool valid;
+// Byte offset of the origin array behind a camera's table parts.
+template <int W>
+__host__ __device__ __forceinline__ size_t s_origin_offset(int K, int nz, int tiles_s) {
+  return (size_t)K * tiles_s * padded_slices(nz) * sizeof(SPart<W>);
+}
+template <int W>
+__host__ __device__ __forceinline__ size_t t_origin_offset(int K, int nz, int tiles_t) {
+  return (size_t)K * tiles_t * padded_slices(nz) * sizeof(TPart<W>);
+}
+
+// Slot header written by the producer: the slices [first, first + count) of
+// the group that the consumer contracts.
+struct FillHdr {
+  int first, count, pad[2];
 };
 
-__device__ __forceinline__ void cursor_range(const BeamCam& C, int ts, int tt, PairCursor& c) {
-  while (c.k < c.k_end) {
-    if (cell_on(C.sub_n, C.sub_s, c.k)) {
-      const int2 rs = C.srange[c.k * C.tiles_s + ts];
-      const int2 rt = C.trange[c.k * C.tiles_t + tt];
-      c.n = max(rs.x, rt.x);
-      c.n1 = min(rs.y, rt.y);
-      if (c.n < c.n1) {
-        c.valid = true;
-        return;
-      }
-    }
-    ++c.k;
+// Shared-memory layout: FSLOTS stages of {FG brick planes (plane = floats
+// per brick plane, a multiple of 4), FG SParts, FG TParts, header}, the
+// consumers' s-contracted rows (FC x tsz floats), one partial tile (32 x 33
+// floats) the consumers sum into in warp order, FRECS item records and the
+// mbarriers.
+template <int W>
+struct FwdLayout {
+  static constexpr size_t parts = FG * (sizeof(SPart<W>) + sizeof(TPart<W>));
+  __host__ __device__ static size_t brick_bytes(int plane) { return ((size_t)FG * plane * 4 + 127) / 128 * 128; }
+  __host__ __device__ static size_t stage_bytes(int plane) {
+    return (brick_bytes(plane) + parts + sizeof(FillHdr) + 127) / 128 * 128;
   }
-  c.valid = false;
-}
-
-__device__ __forceinline__ void cursor_advance(const BeamCam& C, int ts, int tt, PairCursor& c, int steps) {
-  while (c.valid && steps > 0) {
-    const int left = c.n1 - c.n;
-    if (steps < left) {
-      c.n += steps;
-      return;
-    }
-    steps -= left;
-    ++c.k;
-    cursor_range(C, ts, tt, c);
-  }
-}
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-// Shared-memory layout of the brick-staged forward, per warp: TM_STAGES
-// stages of {brick, SPart, TPart}, the lane columns of the s-contracted rows
-// (Tw, by_max x 32 floats), and one mbarrier per stage.
-template <int W, int NB>
-struct StageLayout {
-  static constexpr size_t parts = sizeof(SPart<W>) + sizeof(TPart<NB>);
-  // 128-byte multiples: every stage's brick starts where a TMA box may land
-  __host__ __device__ static size_t stage_bytes(int bxy) {
-    return ((size_t)bxy * sizeof(float) + parts + 127) / 128 * 128;
-  }
-  static size_t bytes(int bxy, int tsz) {
-    return (size_t)TM_WARPS * (TM_STAGES * stage_bytes(bxy) + (size_t)tsz * sizeof(float)) +
-           (size_t)TM_WARPS * TM_STAGES * sizeof(uint64_t);
-  }
+  __host__ __device__ static size_t tw_off(int plane) { return FSLOTS * stage_bytes(plane); }
+  __host__ __device__ static size_t red_off(int plane, int tsz) { return tw_off(plane) + (size_t)FC * tsz * 4; }
+  __host__ __device__ static size_t rec_off(int plane, int tsz) { return red_off(plane, tsz) + 32 * 33 * 4; }
+  __host__ __device__ static size_t bar_off(int plane, int tsz) { return rec_off(plane, tsz) + FRECS * sizeof(FwdRec); }
+  // full[FSLOTS], empty[FSLOTS], rec_full[FRECS], rec_empty[FRECS], consumer barrier
+  static constexpr int n_bars = 2 * FSLOTS + 2 * FRECS + 1;
+  __host__ __device__ static size_t bytes(int plane, int tsz) { return bar_off(plane, tsz) + n_bars * 8; }
 };
 
-// Stage fill for the cursor's (cell, slice) pair by lane 0: the pair's table
-// parts and its brick, all completing one mbarrier.  (x0, y0), the brick's
-// origin, were read from the tables one pair earlier (px, py).
-template <int W, int NB>
-__device__ __forceinline__ void issue_stage(const CUtensorMap* map, const SPart<W>* S, const TPart<NB>* T,
-                                            unsigned char* stage, int bxy, uint32_t brick_bytes, uint32_t bar,
-                                            int x0, int y0, int z) {
-  fence_proxy_async();   // this stage's earlier generic reads precede the new async-proxy writes
-  mbar_expect_tx(bar, brick_bytes + (uint32_t)(sizeof(SPart<W>) + sizeof(TPart<NB>)));
-  const uint32_t dst = smem_addr(stage);
-  tma_load_3d(dst, map, x0, y0, z, bar);
-  bulk_copy(dst + (uint32_t)bxy * 4, S, (uint32_t)sizeof(SPart<W>), bar);
-  bulk_copy(dst + (uint32_t)bxy * 4 + (uint32_t)sizeof(SPart<W>), T, (uint32_t)sizeof(TPart<NB>), bar);
+// Slice interval [nlo, nlo + len) in which the footprints of tile (ts, tt)
+// meet the volume for cell k (len = 0 outside [0, ke) or the subset).
+__device__ __forceinline__ void cell_interval(const BeamCam& C, int ts, int tt, int k, int ke, int& len, int& nlo) {
+  len = 0;
+  nlo = 0;
+  if (k < ke && cell_on(C.sub_n, C.sub_s, k)) {
+    const int2 a = C.srange[k * C.tiles_s + ts], b = C.trange[k * C.tiles_t + tt];
+    nlo = max(a.x, b.x);
+    len = max(0, min(a.y, b.y) - nlo);
+  }
+}
+
+// Sum of v over the lanes below this one.
+__device__ __forceinline__ int exclusive_sum(int v, int lane) {
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x - v;
+}
+
+// Barrier of the four consumer warps (an mbarrier of FC arrivals, waited
+// with a bound): lane 0 arrives after the warp's earlier shared writes.
+__device__ __forceinline__ bool consumer_sync(uint32_t bar, uint32_t& uses, int lane) {
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+  const bool ok = __all_sync(FULL, mbar_wait_bounded(bar, uses & 1));
+  ++uses;
+  return ok;
 }
 
 // Work tickets from *counter: ticket t < n_real * F * chunks is chunk
 // t % chunks of unit u = t / chunks, i.e. of (item u / F, frame u % F) among
 // the first n_real items (those whose tile meets the volume, listed first);
-// the tickets after those each zero TM_EMPTY_BATCH (item, frame) tiles of
-// the remaining items, which no slice reaches.
+// the tickets after those each zero FEMPTY (item, frame) tiles of the
+// remaining items, which no slice reaches.
 //
 // Chunks split an item's (cell, slice) sequence into TB.chunks[camera]
 // consecutive parts (at most `chunks`) processed by different CTAs, so that
@@ -331,257 +305,384 @@ __device__ __forceinline__ void issue_stage(const CUtensorMap* map, const SPart<
 // last chunk (a per-unit ticket count, reset by that CTA) sums the partials
 // in chunk order and writes the tile, so the result does not depend on which
 // CTA ran what.
-template <int W, int NB>
-__global__ void __launch_bounds__(TM_WARPS * 32, 7)
+template <int W>
+__global__ void __launch_bounds__(FTHREADS, 4)
 beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ TmaBatch TB,
-                 const int4* __restrict__ items, int n_items, int n_real, int* __restrict__ counter, int bxy,
+                 const int4* __restrict__ items, int n_items, int n_real, int* __restrict__ counter, int plane,
                  int tsz, int chunks, float* __restrict__ scratch, int* __restrict__ unit_count) {
-  using L = StageLayout<W, NB>;
+  using L = FwdLayout<W>;
   extern __shared__ __align__(128) unsigned char dsm[];
-  const size_t stage_bytes = L::stage_bytes(bxy);
-  unsigned char* stages = dsm;                                                       // [warp][stage]
-  float* tws = reinterpret_cast<float*>(dsm + (size_t)TM_WARPS * TM_STAGES * stage_bytes);   // [warp][tsz]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tws + (size_t)TM_WARPS * tsz);      // [warp][stage]
-  float(*red)[32][33] = reinterpret_cast<float(*)[32][33]>(dsm);                    // aliases the stages
-  __shared__ int s_item;
+  const size_t stage_bytes = L::stage_bytes(plane);
+  float* tws = reinterpret_cast<float*>(dsm + L::tw_off(plane));
+  float(*red)[33] = reinterpret_cast<float(*)[33]>(dsm + L::red_off(plane, tsz));
+  FwdRec* recs = reinterpret_cast<FwdRec*>(dsm + L::rec_off(plane, tsz));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + L::bar_off(plane, tsz));
+  const uint32_t full0 = smem_addr(bars), empty0 = smem_addr(bars + FSLOTS);
+  const uint32_t rfull0 = smem_addr(bars + 2 * FSLOTS), rempty0 = smem_addr(bars + 2 * FSLOTS + FRECS);
+  const uint32_t cbar = smem_addr(bars + 2 * FSLOTS + 2 * FRECS);
   __shared__ int s_fail;
   __shared__ int s_last;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) s_fail = 0;
-  if (threadIdx.x < TM_WARPS * TM_STAGES) mbar_init1(smem_addr(bars + threadIdx.x));
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < FSLOTS; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int r = 0; r < FRECS; ++r) {
+      mbar_init(rfull0 + 8 * r, 1);
+      mbar_init(rempty0 + 8 * r, FC);
+    }
+    mbar_init(cbar, FC);
+  }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
 
-  unsigned char* my_stages = stages + (size_t)warp * TM_STAGES * stage_bytes;
-  float* Tw = tws + (size_t)warp * tsz + lane;
-  uint32_t n_issued = 0, n_done = 0;   // this warp's stage fills (stage = count % S, phase = count / S)
-  bool failed = false;
   const long long real = (long long)n_real * B.frames * chunks;
   const long long empty = (long long)(n_items - n_real) * B.frames;
-  const long long total = real + (empty + TM_EMPTY_BATCH - 1) / TM_EMPTY_BATCH;
+  const long long total = real + (empty + FEMPTY - 1) / FEMPTY;
 
+  if (warp == FC) {
+    // ------------------------------ producer ------------------------------
+    // Tickets come from *counter in list order (items longest first); the
+    // next ticket is requested when an item starts, so its atomic is done by
+    // the time it is needed.  An item's pairs are issued as fills of slice
+    // groups (the group's slices in the item, for one cell), in steps of up
+    // to four consecutive fills, lane q < 4 filling the stage of fill g + q.
+    uint32_t g = 0;   // stage fills issued
+    uint32_t r = 0;   // records written
+    bool failed = false;
+    int next = 0;
+    if (lane == 0) next = atomicAdd(counter, 1);
+    for (;;) {
+      const long long ticket = __shfl_sync(FULL, next, 0);
+      if (lane == 0 && ticket < total) next = atomicAdd(counter, 1);
+      const int rs = (int)(r % FRECS);
+      if (lane == 0 && r >= FRECS && !failed && !mbar_wait_bounded(rempty0 + 8 * rs, (r / FRECS - 1) & 1))
+        failed = true;
+      int sf = 0;
+      if (lane == 0) sf = *(volatile int*)&s_fail;
+      failed = __shfl_sync(FULL, (int)failed, 0) != 0;
+      const bool stop = failed || ticket >= total || __shfl_sync(FULL, sf, 0) != 0;
+      if (stop || ticket >= real) {
+        if (lane == 0 && !failed) {
+          recs[rs] = FwdRec{stop ? kRecEnd : kRecEmpty, (int)ticket, 0, g};
+          mbar_arrive(rfull0 + 8 * rs);
+        }
+        ++r;
+        if (stop) break;
+        continue;
+      }
+      const long long unit = ticket / chunks;
+      const int chunk = (int)(ticket % chunks);
+      const int4 item = items[unit / B.frames];
+      const int frame = (int)(unit % B.frames);
+      const BeamCam& C = B.cam[item.x];
+      const int cc = TB.chunks[item.x];
+      if (chunk >= cc || (item.y >= 0 && !cell_on(C.sub_n, C.sub_s, item.y))) continue;   // nothing to write
+      const int ts = item.z % C.tiles_s, tt = item.z / C.tiles_s;
+      const int kb = item.y >= 0 ? item.y : 0, ke = item.y >= 0 ? item.y + 1 : C.K;
+      const int nzp = padded_slices(C.nz), groups = nzp / FG;
+      // The item's pairs: cells k of [kb, ke) in the subset, the slices of
+      // each in the tile's interval [nlo, nlo + len), at positions
+      // [jk, jk + len) of the item's sequence; the chunk takes positions
+      // [j_lo, j_hi).  Lanes over cells.
+      int L_all = 0;
+      for (int k0 = kb; k0 < ke; k0 += 32) {
+        int len, nlo;
+        cell_interval(C, ts, tt, k0 + lane, ke, len, nlo);
+        L_all += __reduce_add_sync(FULL, len);
+      }
+      const int j_lo = (int)((long long)L_all * chunk / cc), j_hi = (int)((long long)L_all * (chunk + 1) / cc);
+      int n_fills = 0;
+      for (int k0 = kb, jb = 0; k0 < ke; k0 += 32) {
+        int len, nlo;
+        cell_interval(C, ts, tt, k0 + lane, ke, len, nlo);
+        const int jk = jb + exclusive_sum(len, lane);
+        const int a = max(jk, j_lo), b = min(jk + len, j_hi);
+        const int f = b > a ? (nlo + b - jk - 1) / FG - (nlo + a - jk) / FG + 1 : 0;
+        n_fills += __reduce_add_sync(FULL, f);
+        jb += __reduce_add_sync(FULL, len);
+      }
+      if (lane == 0) {
+        recs[rs] = FwdRec{kRecItem, (int)ticket, n_fills, g};
+        mbar_arrive(rfull0 + 8 * rs);
+      }
+      ++r;
+      const int bx = TB.bx[item.x], by = TB.by[item.x];
+      const uint32_t tx_bytes = (uint32_t)(FG * bx * by * 4) + (uint32_t)L::parts;
+      const CUtensorMap* map = &TB.map[item.x];
+      const char* stab = static_cast<const char*>(TB.stab[item.x]);
+      const char* ttab = static_cast<const char*>(TB.ttab[item.x]);
+      const int* oxa = reinterpret_cast<const int*>(stab + s_origin_offset<W>(C.K, C.nz, C.tiles_s));
+      const int* oya = reinterpret_cast<const int*>(ttab + t_origin_offset<W>(C.K, C.nz, C.tiles_t));
+      for (int k0 = kb, jb = 0; k0 < ke && !failed; k0 += 32) {
+        int len, nlo;
+        cell_interval(C, ts, tt, k0 + lane, ke, len, nlo);
+        const int jkl = jb + exclusive_sum(len, lane);
+        jb += __reduce_add_sync(FULL, len);
+        for (int q = 0; q < 32 && k0 + q < ke && !failed; ++q) {
+          const int lq = __shfl_sync(FULL, len, q), nq = __shfl_sync(FULL, nlo, q), jk = __shfl_sync(FULL, jkl, q);
+          const int a = max(jk, j_lo), b = min(jk + lq, j_hi);
+          if (b <= a) continue;
+          const int k = k0 + q;
+          const int n_a = nq + a - jk, n_b = nq + b - jk;   // this cell's slices in the chunk
+          const int g_a = n_a / FG, g_b = (n_b - 1) / FG;    // its groups, inclusive
+          const long long sbase = (long long)k * C.tiles_s + ts, tbase = (long long)k * C.tiles_t + tt;
+          for (int gb0 = g_a; gb0 <= g_b && !failed; gb0 += 32) {
+            const int cnt = min(32, g_b - gb0 + 1);
+            int ox = 0, oy = 0;
+            if (lane < cnt) {
+              ox = __ldg(oxa + sbase * groups + gb0 + lane);
+              oy = __ldg(oya + tbase * groups + gb0 + lane);
+            }
+            for (int p = 0; p < cnt && !failed; p += 4) {
+              const int nb = min(4, cnt - p);
+              const int x0 = __shfl_sync(FULL, ox, (p + lane) & 31), y0 = __shfl_sync(FULL, oy, (p + lane) & 31);
+              bool ok = true;
+              if (lane < nb) {
+                const uint32_t gq = g + lane;
+                const int slot = (int)(gq % FSLOTS);
+                if (gq >= FSLOTS && !mbar_wait_bounded(empty0 + 8 * slot, (gq / FSLOTS - 1) & 1)) {
+                  ok = false;
+                } else {
+                  const int grp = gb0 + p + lane, n0 = grp * FG;
+                  unsigned char* stg = dsm + slot * stage_bytes;
+                  const uint32_t dst = smem_addr(stg), bar = full0 + 8 * slot;
+                  const uint32_t pb = (uint32_t)L::brick_bytes(plane);
+                  const int first = max(n_a, n0) - n0;
+                  *reinterpret_cast<FillHdr*>(stg + pb + L::parts) = FillHdr{first, min(n_b, n0 + FG) - n0 - first, {0, 0}};
+                  fence_proxy_async();   // the stage's earlier generic reads precede the async-proxy writes
+                  mbar_expect_tx(bar, tx_bytes);
+                  tma_load_3d(dst, map, x0, y0, frame * C.nz + n0, bar);
+                  bulk_copy(dst + pb, stab + (sbase * nzp + n0) * sizeof(SPart<W>), FG * (uint32_t)sizeof(SPart<W>), bar);
+                  bulk_copy(dst + pb + FG * (uint32_t)sizeof(SPart<W>), ttab + (tbase * nzp + n0) * sizeof(TPart<W>),
+                            FG * (uint32_t)sizeof(TPart<W>), bar);
+                }
+              }
+              failed = !__all_sync(FULL, ok);
+              g += (uint32_t)nb;
+            }
+          }
+        }
+      }
+      if (failed) {
+        if (lane == 0) {
+          atomicOr(&g_projector_status, 2);
+          s_fail = 1;
+        }
+        break;   // consumers waiting for fills that were not issued give up on their own bounded waits
+      }
+    }
+    // leave no copy in flight behind: wait (bounded) for the last fill of every stage
+    if (lane == 0) {
+      const uint32_t q0 = g > FSLOTS ? g - FSLOTS : 0;
+      for (uint32_t q = q0; q < g; ++q) mbar_wait_bounded(full0 + 8 * (q % FSLOTS), (q / FSLOTS) & 1);
+    }
+    return;
+  }
+
+  // ------------------------------ consumers -------------------------------
+  float* Tw = tws + (size_t)warp * tsz;
+  uint32_t r = 0, cuses = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const long long it = s_item;
-    if (it >= total || s_fail) break;
-    if (it >= real) {   // a batch of tiles no slice reaches: zeros
-      const long long e0 = (it - real) * TM_EMPTY_BATCH;
-      for (long long e = e0; e < e0 + TM_EMPTY_BATCH && e < empty; ++e) {
+    const int rs = (int)(r % FRECS);
+    if (!__all_sync(FULL, mbar_wait_bounded(rfull0 + 8 * rs, (r / FRECS) & 1))) {
+      if (lane == 0) {
+        atomicOr(&g_projector_status, 2);
+        s_fail = 1;
+      }
+      break;
+    }
+    const FwdRec rec = recs[rs];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(rempty0 + 8 * rs);
+    ++r;
+    if (rec.kind == kRecEnd) break;
+    if (rec.kind == kRecEmpty) {   // a batch of tiles no slice reaches: zeros
+      const long long e0 = (rec.ticket - real) * FEMPTY;
+      for (long long e = e0 + warp; e < e0 + FEMPTY && e < empty; e += FC) {
         const int4 item = items[n_real + e / B.frames];
         const int frame = (int)(e % B.frames);
         const BeamCam& C = B.cam[item.x];
         if (item.y >= 0 && !cell_on(C.sub_n, C.sub_s, item.y)) continue;
-        const int is0 = (item.z % C.tiles_s) * kBeamTileS, it0 = (item.z / C.tiles_s) * kBeamTileT;
+        const int is = (item.z % C.tiles_s) * kBeamTileS + lane, it0 = (item.z / C.tiles_s) * kBeamTileT;
         float* o = C.out + (long long)frame * C.out_fs + (C.per_cell ? (long long)item.y * C.ns * C.nt : 0);
-        for (int q = threadIdx.x; q < kBeamTileS * kBeamTileT; q += TM_WARPS * 32) {
-          const int r = it0 + q / kBeamTileS, c = is0 + q % kBeamTileS;
-          if (r < C.nt && c < C.ns) o[(long long)r * C.ns + c] = 0.0f;
-        }
+        if (is < C.ns)
+          for (int i = 0; i < kBeamTileT && it0 + i < C.nt; ++i) o[(long long)(it0 + i) * C.ns + is] = 0.0f;
       }
-      __syncthreads();   // s_item is rewritten by the next take
       continue;
     }
-    const long long unit = it / chunks;
-    const int chunk = (int)(it % chunks);
+    const long long unit = rec.ticket / chunks;
+    const int chunk = (int)(rec.ticket % chunks);
     const int4 item = items[unit / B.frames];
     const int frame = (int)(unit % B.frames);
     const BeamCam& C = B.cam[item.x];
     const int cc = TB.chunks[item.x];
-    if (chunk >= cc) {   // this camera splits its items into fewer chunks
-      __syncthreads();
-      continue;
-    }
-    const CUtensorMap* map = &TB.map[item.x];
-    const SPart<W>* stab = static_cast<const SPart<W>*>(TB.stab[item.x]);
-    const TPart<NB>* ttab = static_cast<const TPart<NB>*>(TB.ttab[item.x]);
     const int bx = TB.bx[item.x], by = TB.by[item.x];
-    const uint32_t brick_bytes = (uint32_t)(bx * by * sizeof(float));
-    const int tile_s = item.z % C.tiles_s;
-    const int tile_t = item.z / C.tiles_s;
-    const int is0 = tile_s * kBeamTileS;
-    const int it0 = tile_t * kBeamTileT;
-    const int k_begin = item.y >= 0 ? item.y : 0;
-    const int k_end = item.y >= 0 ? item.y + 1 : C.K;
-    if (item.y >= 0 && !cell_on(C.sub_n, C.sub_s, item.y)) {   // cell outside the subset: its plane is not written
-      __syncthreads();
-      continue;
-    }
 
-    float acc[32];
+    float2 acc[16];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) acc[r] = 0.0f;
-
-    // this warp's pairs: every TM_WARPS-th (cell, slice) of the item
-    // this warp's pairs: every TM_WARPS-th (cell, slice) pair of the chunk,
-    // pairs [j_lo, j_hi) of the item's sequence of L pairs
-    PairCursor pf{k_begin, 0, 0, k_end, false};
-    cursor_range(C, tile_s, tile_t, pf);
-    int j_hi = 0x7fffffff, pj = warp;
-    if (cc > 1) {
-      int L = 0;
-      for (PairCursor q = pf; q.valid; ++q.k, cursor_range(C, tile_s, tile_t, q)) L += q.n1 - q.n;
-      const int j_lo = (int)((long long)L * chunk / cc);
-      j_hi = (int)((long long)L * (chunk + 1) / cc);
-      pj = j_lo + warp;
-    }
-    cursor_advance(C, tile_s, tile_t, pf, pj);
-    if (pj >= j_hi) pf.valid = false;
-    // the cursor's table parts and brick origin (lane 0 reads the origin one
-    // pair before it issues the pair's stage fill)
-    const SPart<W>* sp = stab;
-    const TPart<NB>* tp = ttab;
-    int px = 0, py = 0;
-    if (pf.valid) {
-      const long long kn = (long long)pf.k * C.nz + pf.n;
-      sp = stab + kn * C.tiles_s + tile_s;
-      tp = ttab + kn * C.tiles_t + tile_t;
-      if (lane == 0) {
-        px = __ldg(&sp->x0);
-        py = __ldg(&tp->y0);
+    for (int c = 0; c < 16; ++c) acc[c] = make_float2(0.0f, 0.0f);
+    bool ok = true;
+    for (int j = warp; j < rec.L; j += FC) {
+      const uint32_t gg = rec.g0 + (uint32_t)j;
+      const int slot = (int)(gg % FSLOTS);
+      if (!__all_sync(FULL, mbar_wait_bounded(full0 + 8 * slot, (gg / FSLOTS) & 1))) {
+        ok = false;
+        break;
       }
-    }
-    int inflight = 0;
-    if (!failed) {
-      for (;;) {
-        while (pf.valid && inflight < TM_STAGES) {
-          const int st = (int)(n_issued % TM_STAGES);
-          if (lane == 0)
-            issue_stage<W, NB>(map, sp, tp, my_stages + st * stage_bytes, bxy, brick_bytes,
-                               smem_addr(bars + warp * TM_STAGES + st), px, py, frame * C.nz + pf.n);
-          ++n_issued;
-          ++inflight;
-          cursor_advance(C, tile_s, tile_t, pf, TM_WARPS);
-          pj += TM_WARPS;
-          if (pj >= j_hi) pf.valid = false;
-          if (pf.valid) {
-            const long long kn = (long long)pf.k * C.nz + pf.n;
-            sp = stab + kn * C.tiles_s + tile_s;
-            tp = ttab + kn * C.tiles_t + tile_t;
-            if (lane == 0) {
-              px = __ldg(&sp->x0);
-              py = __ldg(&tp->y0);
-            }
+      const unsigned char* stg = dsm + slot * stage_bytes;
+      const size_t pb = L::brick_bytes(plane);
+      const FillHdr hdr = *reinterpret_cast<const FillHdr*>(stg + pb + L::parts);
+      const SPart<W>* Sg = reinterpret_cast<const SPart<W>*>(stg + pb);
+      const TPart<W>* Tg = reinterpret_cast<const TPart<W>*>(stg + pb + FG * sizeof(SPart<W>));
+      for (int q = hdr.first; q < hdr.first + hdr.count; ++q) {
+        const float* brick = reinterpret_cast<const float*>(stg) + q * bx * by;
+        const SPart<W>& S = Sg[q];
+        const TPart<W>& T = Tg[q];
+        // s: every brick row for this lane's pixel column, two rows per packed FMA
+        {
+          float2 ws2[W];
+#pragma unroll
+          for (int a = 0; a < W; ++a) ws2[a] = make_float2(S.ws[a][lane], S.ws[a][lane]);
+          const float* bc = brick + S.sx[lane];
+          int row = 0;
+#pragma unroll 2
+          for (; row + 1 < by; row += 2) {
+            float2 u = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int a = 0; a < W; ++a)
+              u = __ffma2_rn(ws2[a], make_float2(bc[row * bx + a], bc[(row + 1) * bx + a]), u);
+            Tw[row * FTS + lane] = u.x;
+            Tw[(row + 1) * FTS + lane] = u.y;
+          }
+          if (row < by) {
+            float u = 0.0f;
+#pragma unroll
+            for (int a = 0; a < W; ++a) u = fmaf(ws2[a].x, bc[row * bx + a], u);
+            Tw[row * FTS + lane] = u;
           }
         }
-        if (inflight == 0) break;
-        const int st = (int)(n_done % TM_STAGES);
-        if (!mbar_wait_bounded(smem_addr(bars + warp * TM_STAGES + st), (n_done / TM_STAGES) & 1)) {
-          failed = true;
-          if (lane == 0) {
-            atomicOr(&g_projector_status, 2);
-            s_fail = 1;
+        __syncwarp();
+        // t: this lane's pixel row over the tile's 32 columns, two per packed FMA
+        {
+          const int ty = T.ty[lane];
+#pragma unroll
+          for (int a = 0; a < W; ++a) {
+            const float2 w2 = make_float2(T.tw[a][lane], T.tw[a][lane]);
+            const float2* row = reinterpret_cast<const float2*>(Tw + (ty + a) * FTS);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = __ffma2_rn(w2, row[c], acc[c]);
           }
-          break;
         }
-        const unsigned char* stg = my_stages + st * stage_bytes;
-        contract_slice<W, NB>(*reinterpret_cast<const SPart<W>*>(stg + (size_t)bxy * 4),
-                              *reinterpret_cast<const TPart<NB>*>(stg + (size_t)bxy * 4 + sizeof(SPart<W>)),
-                              reinterpret_cast<const float*>(stg), bx, by, Tw, lane, acc);
-        ++n_done;
-        --inflight;
         __syncwarp();
       }
+      if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+    }
+    int sf = 0;
+    if (lane == 0) sf = *(volatile int*)&s_fail;
+    if (!ok || __shfl_sync(FULL, sf, 0) != 0) {
+      if (lane == 0) {
+        if (!ok) atomicOr(&g_projector_status, 2);
+        s_fail = 1;
+      }
+      break;
     }
 
-    // the four warps' partial tiles, summed in warp order; then either the
-    // tile (one chunk) or this chunk's partial, the unit's last chunk summing
-    // every partial in chunk order; masked and written
-    __syncthreads();
-    if (!s_fail) {
-      if (warp > 0) {
+    // the four consumers' partial tiles, summed in warp order into one
+    // shared tile; then either the tile (one chunk) or this chunk's partial,
+    // the unit's last chunk summing every partial in chunk order; masked and
+    // written.  Warp w finishes tile rows w, w + 4, ... (lane = pixel column).
+    for (int w = 0; w < FC; ++w) {
+      if (warp == w) {
 #pragma unroll
-        for (int r = 0; r < 32; ++r) red[warp - 1][r][lane] = acc[r];
-      }
-      __syncthreads();
-      if (warp == 0) {
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-#pragma unroll
-          for (int g = 0; g < TM_WARPS - 1; ++g) acc[r] += red[g][r][lane];
+        for (int c = 0; c < 16; ++c) {
+          red[lane][2 * c] = w == 0 ? acc[c].x : red[lane][2 * c] + acc[c].x;
+          red[lane][2 * c + 1] = w == 0 ? acc[c].y : red[lane][2 * c + 1] + acc[c].y;
         }
       }
-      bool write = true;
+      if (!consumer_sync(cbar, cuses, lane)) ok = false;
+    }
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = red[warp + FC * q][lane];
+    if (!consumer_sync(cbar, cuses, lane)) ok = false;   // the shared tile is free again
+    if (!ok) {
+      if (lane == 0) {
+        atomicOr(&g_projector_status, 2);
+        s_fail = 1;
+      }
+      break;
+    }
+    const int ts = item.z % C.tiles_s, tt = item.z / C.tiles_s;
+    const int is = ts * kBeamTileS + lane, it0 = tt * kBeamTileT;
+    bool write = true;
+    if (cc > 1) {
       float* part = scratch + unit * (long long)chunks * 1024;
-      if (cc > 1) {
-        if (warp == 0) {
 #pragma unroll
-          for (int r = 0; r < 32; ++r) part[chunk * 1024 + r * 32 + lane] = acc[r];
-          __threadfence();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          const int done = atomicAdd(&unit_count[unit], 1);
-          s_last = done == cc - 1;
-          if (s_last) unit_count[unit] = 0;   // ready for the next launch
-        }
-        __syncthreads();
-        write = s_last;
-        if (write && warp == 0) {
-          __threadfence();
-#pragma unroll
-          for (int r = 0; r < 32; ++r) {
-            float v = __ldcg(part + r * 32 + lane);
-            for (int c = 1; c < cc; ++c) v += __ldcg(part + c * 1024 + r * 32 + lane);
-            acc[r] = v;
-          }
-        }
+      for (int q = 0; q < 8; ++q) part[chunk * 1024 + (warp + FC * q) * 32 + lane] = v[q];
+      __threadfence();
+      if (!consumer_sync(cbar, cuses, lane)) ok = false;
+      if (ok && warp == 0 && lane == 0) {
+        const int done = atomicAdd(&unit_count[unit], 1);
+        s_last = done == cc - 1;
+        if (s_last) unit_count[unit] = 0;   // ready for the next launch
       }
-      if (write && warp == 0) {
-        const int is = is0 + lane;
-        if (is < C.ns) {
-          float* o = C.out + (long long)frame * C.out_fs + (C.per_cell ? (long long)k_begin * C.ns * C.nt : 0);
+      if (!consumer_sync(cbar, cuses, lane)) ok = false;
+      if (!ok) {
+        if (lane == 0) {
+          atomicOr(&g_projector_status, 2);
+          s_fail = 1;
+        }
+        break;
+      }
+      write = s_last;
+      if (write) {
+        __threadfence();
 #pragma unroll
-          for (int r = 0; r < 32; ++r) {
-            const int itp = it0 + r;
-            if (itp < C.nt) {
-              float v = acc[r];
-              if (C.mask) v *= C.mask[(long long)itp * C.ns + is];   // M (Sec. II-D)
-              o[(long long)itp * C.ns + is] = v;
-            }
-          }
+        for (int q = 0; q < 8; ++q) {
+          const int row = warp + FC * q;
+          float sum = __ldcg(part + row * 32 + lane);
+          for (int c = 1; c < cc; ++c) sum += __ldcg(part + c * 1024 + row * 32 + lane);
+          v[q] = sum;
         }
       }
     }
-    __syncthreads();
-  }
-
-  // a warp that gave up leaves nothing in flight behind it: wait (bounded)
-  // for the fills it issued and did not consume
-  if (failed) {
-    for (uint32_t q = n_done; q < n_issued; ++q)
-      mbar_wait_bounded(smem_addr(bars + warp * TM_STAGES + (q % TM_STAGES)), (q / TM_STAGES) & 1);
+    if (write && is < C.ns) {
+      const int kb = item.y >= 0 ? item.y : 0;
+      float* o = C.out + (long long)frame * C.out_fs + (C.per_cell ? (long long)kb * C.ns * C.nt : 0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int itp = it0 + warp + FC * q;
+        if (itp < C.nt) {
+          float val = v[q];
+          if (C.mask) val *= C.mask[(long long)itp * C.ns + is];   // M (Sec. II-D)
+          o[(long long)itp * C.ns + is] = val;
+        }
+      }
+    }
   }
 }
 
-template <int W, int NB>
+template <int W>
 const void* tma_kernel() {
-  return (const void*)beam_forward_tma<W, NB>;
+  return (const void*)beam_forward_tma<W>;
 }
 
-const void* tma_select(int w, int nb) {
-  if (nb <= 4) {
-    switch (w) {
-      case 2: return tma_kernel<2, 4>();
-      case 3: return tma_kernel<3, 4>();
-      default: return tma_kernel<4, 4>();
-    }
-  }
+const void* tma_select(int w) {
   switch (w) {
-    case 2: return tma_kernel<2, 8>();
-    case 3: return tma_kernel<3, 8>();
-    default: return tma_kernel<4, 8>();
+    case 2: return tma_kernel<2>();
+    case 3: return tma_kernel<3>();
+    default: return tma_kernel<4>();
   }
 }
 
-size_t layout_bytes(int w, int nb, int bxy, int tsz) {
-  if (nb <= 4)
-    return w == 2 ? StageLayout<2, 4>::bytes(bxy, tsz) : w == 3 ? StageLayout<3, 4>::bytes(bxy, tsz)
-                                                                : StageLayout<4, 4>::bytes(bxy, tsz);
-  return w == 2 ? StageLayout<2, 8>::bytes(bxy, tsz) : w == 3 ? StageLayout<3, 8>::bytes(bxy, tsz)
-                                                              : StageLayout<4, 8>::bytes(bxy, tsz);
+size_t layout_bytes(int w, int plane, int tsz) {
+  return w == 2 ? FwdLayout<2>::bytes(plane, tsz) : w == 3 ? FwdLayout<3>::bytes(plane, tsz)
+                                                            : FwdLayout<4>::bytes(plane, tsz);
 }
 
 // cuTensorMapEncodeTiled from the driver, found once through the runtime.
@@ -617,85 +718,99 @@ cudaError_t projector_status(int* flags, bool clear) {
 }
 
 bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, int bx, int by) {
-  return tma_encode_planes(map, x, nx, ny, nz_total, (long long)nx * ny, bx, by);
+  return tma_encode_planes(map, x, nx, ny, nz_total, (long long)nx * ny, bx, by, FG);
 }
 
 bool tma_encode_planes(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, long long z_stride, int bx,
-                       int by) {
+                       int by, int bz) {
   EncodeTiled enc = encoder();
   if (!enc || !x || (reinterpret_cast<uintptr_t>(x) & 15) || (nx & 3) || (z_stride & 3) || bx <= 0 || by <= 0 ||
-      bx > 256 || by > 256 || (bx & 3))
+      bx > 256 || by > 256 || (bx & 3) || bz < 1 || bz > 256)
     return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz_total};
   const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)z_stride * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(x), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t tma_table_bytes(int w, int nb, int K, int nz, int tiles_s, int tiles_t) {
-  const size_t sp = w == 2 ? sizeof(SPart<2>) : w == 3 ? sizeof(SPart<3>) : sizeof(SPart<4>);
-  const size_t tp = nb <= 4 ? sizeof(TPart<4>) : sizeof(TPart<8>);
-  return (size_t)K * nz * ((size_t)tiles_s * sp + (size_t)tiles_t * tp);
+size_t tma_table_bytes(int w, int K, int nz, int tiles_s, int tiles_t) {
+  const size_t s = w == 2 ? s_origin_offset<2>(K, nz, tiles_s) : w == 3 ? s_origin_offset<3>(K, nz, tiles_s)
+                                                                        : s_origin_offset<4>(K, nz, tiles_s);
+  const size_t t = w == 2 ? t_origin_offset<2>(K, nz, tiles_t) : w == 3 ? t_origin_offset<3>(K, nz, tiles_t)
+                                                                        : t_origin_offset<4>(K, nz, tiles_t);
+  const size_t groups = (size_t)padded_slices(nz) / FG;
+  const size_t so = ((size_t)K * tiles_s * groups * 4 + 127) / 128 * 128;
+  const size_t to = ((size_t)K * tiles_t * groups * 4 + 127) / 128 * 128;
+  return (tiles_s > 0 ? s + so : 0) + (tiles_t > 0 ? t + to : 0);
 }
 
-cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int nb, int bx,
+cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int bx,
                                int by, void* stab, void* ttab, int* bad, cudaStream_t st) {
-  const dim3 grid(std::max(tiles_s, tiles_t), nz, K);
-#define LT_TABLES(WW, NN)                                                                                    \
-  beam_weight_tables<WW, NN><<<grid, 64, 0, st>>>(prm, nz, tiles_s, tiles_t, bx, by,                           \
-                                                  static_cast<SPart<WW>*>(stab), static_cast<TPart<NN>*>(ttab), bad)
-  if (nb <= 4) {
-    if (w == 2) LT_TABLES(2, 4);
-    else if (w == 3) LT_TABLES(3, 4);
-    else LT_TABLES(4, 4);
-  } else {
-    if (w == 2) LT_TABLES(2, 8);
-    else if (w == 3) LT_TABLES(3, 8);
-    else LT_TABLES(4, 8);
-  }
+  // padding entries (slices past nz in the last group) stay zero
+  cudaError_t e = cudaMemsetAsync(stab, 0, tma_table_bytes(w, K, nz, tiles_s, 0), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ttab, 0, tma_table_bytes(w, K, nz, 0, tiles_t), st);
+  if (e != cudaSuccess) return e;
+  const int tiles = std::max(tiles_s, tiles_t), groups = padded_slices(nz) / FG;
+#define LT_TABLES(WW)                                                                                          \
+  do {                                                                                                         \
+    beam_weight_tables<WW><<<dim3(tiles, nz, K), 64, 0, st>>>(prm, nz, tiles_s, tiles_t,                       \
+                                                              static_cast<SPart<WW>*>(stab),                  \
+                                                              static_cast<TPart<WW>*>(ttab));                 \
+    beam_group_origins<WW><<<dim3(tiles, groups, K), 64, 0, st>>>(                                             \
+        nz, tiles_s, tiles_t, bx, by, static_cast<SPart<WW>*>(stab), static_cast<TPart<WW>*>(ttab),           \
+        reinterpret_cast<int*>(static_cast<char*>(stab) + s_origin_offset<WW>(K, nz, tiles_s)),              \
+        reinterpret_cast<int*>(static_cast<char*>(ttab) + t_origin_offset<WW>(K, nz, tiles_t)), bad);        \
+  } while (0)
+  if (w == 2) LT_TABLES(2);
+  else if (w == 3) LT_TABLES(3);
+  else LT_TABLES(4);
 #undef LT_TABLES
   return cudaGetLastError();
 }
 
-int tma_forward_bxy(int max_brick, int w, int nb) {
-  // the reduction buffer of three warps' tiles aliases the stages
-  const size_t red = (size_t)(TM_WARPS - 1) * 32 * 33 * sizeof(float);
-  int bxy = (max_brick + 31) / 32 * 32;
-  const size_t parts = layout_bytes(w, nb, 0, 0) / TM_WARPS / TM_STAGES;   // stage bytes with bxy = 0 (+ bars)
-  while ((size_t)TM_WARPS * TM_STAGES * ((size_t)bxy * sizeof(float) + parts) < red) bxy += 32;
-  return bxy;
-}
+int tma_forward_group() { return FG; }
 
-int tma_forward_occupancy(int w, int nb, int bxy, int tsz) {
-  const void* fn = tma_select(w, nb);
-  const size_t smem = layout_bytes(w, nb, bxy, tsz);
+int tma_forward_tsz(int max_by) { return max_by * FTS; }
+
+int tma_forward_max_by() { return FMAX_BY; }
+
+int tma_forward_occupancy(int w, int plane, int tsz) {
+  const void* fn = tma_select(w);
+  const size_t smem = layout_bytes(w, plane, tsz);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb_ctas = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_ctas, fn, TM_WARPS * 32, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_ctas, fn, FTHREADS, smem) != cudaSuccess) return 0;
   return nb_ctas;
 }
 
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int chunks,
+                                    int n_real, int* counter, int w, int plane, int tsz, int chunks,
                                     float* scratch, int* unit_count, int ctas, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (w < 2 || w > 4) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  const void* fn = tma_select(w, nb);
-  const size_t smem = layout_bytes(w, nb, bxy, tsz);
+  const void* fn = tma_select(w);
+  const size_t smem = layout_bytes(w, plane, tsz);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (chunks < 1 || (chunks > 1 && (!scratch || !unit_count))) return cudaErrorInvalidValue;
-  const long long total = (long long)n_real * b.frames * chunks +
-                         ((long long)(n_items - n_real) * b.frames + TM_EMPTY_BATCH - 1) / TM_EMPTY_BATCH;
-  const int grid = (int)std::min<long long>(ctas, total);
-  void* args[] = {(void*)&b,   (void*)&tb,  (void*)&items,  (void*)&n_items, (void*)&n_real,  (void*)&counter,
-                  (void*)&bxy, (void*)&tsz, (void*)&chunks, (void*)&scratch, (void*)&unit_count};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(TM_WARPS * 32), args, smem, st);
+  const long long real = (long long)n_real * b.frames * chunks;
+  const long long total = real + ((long long)(n_items - n_real) * b.frames + FEMPTY - 1) / FEMPTY;
+  // with more units than resident CTAs, as many CTAs as give every CTA the
+  // same number of rounds (the units are listed longest first), so that the
+  // last round does not leave most of the grid idle
+  long long grid = std::min<long long>(ctas, total);
+  if (real > ctas) {
+    const long long rounds = (real + ctas - 1) / ctas;
+    grid = (real + rounds - 1) / rounds;
+  }
+  void* args[] = {(void*)&b,     (void*)&tb,  (void*)&items,  (void*)&n_items, (void*)&n_real,  (void*)&counter,
+                  (void*)&plane, (void*)&tsz, (void*)&chunks, (void*)&scratch, (void*)&unit_count};
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(FTHREADS), args, smem, st);
 }
 
 }  // namespace lt

@@ -183,8 +183,8 @@ struct BeamBatch {
 // camera's 32 x 32 tiles, and the camera's footprint-weight tables.
 struct TmaBatch {
   CUtensorMap map[kMaxBatchCams];
-  const void* stab[kMaxBatchCams];   // per-(cell, slice, tile column) s-weights (plan-built tables)
-  const void* ttab[kMaxBatchCams];   // per-(cell, slice, tile row) t band weights
+  const void* stab[kMaxBatchCams];   // per-(cell, slice, tile column) s-weights, then brick column origins
+  const void* ttab[kMaxBatchCams];   // per-(cell, slice, tile row) t-weights, then brick row origins
   int32_t bx[kMaxBatchCams];
   int32_t by[kMaxBatchCams];
   int32_t chunks[kMaxBatchCams];     // parts each of the camera's items is split into (>= 1)
@@ -216,29 +216,33 @@ cudaError_t launch_beam_forward_batched(const BeamBatch& b, const int4* items, i
 int beam_forward_occupancy(int wclass, int variant);
 int window_class(int w);
 
-// Brick-staged forward (lt_beam_tma.cu): W = forward window class (2..4),
-// nb = band rows per group of four pixel rows (4 or 8), bxy = floats per
-// brick stage (tma_forward_bxy of the largest bx * by in the launch).
-// tsz = floats of a warp's s-contracted rows (32 x the largest by).  Tables:
-// tma_table_bytes for one camera; launch_beam_tables fills them from the
-// camera's SliceParam table and sets *bad if a brick or band did not fit.
+// Brick-staged forward (lt_beam_tma.cu): W = forward window class (2..4).
+// A stage holds the bricks of tma_forward_group() consecutive slices; plane
+// = the largest bx * by of the launch, tsz = floats of a consumer warp's
+// s-contracted rows (tma_forward_tsz of the largest by; by at most
+// tma_forward_max_by()).  Tables: tma_table_bytes for one camera (tiles_t =
+// 0: the s-part alone); launch_beam_tables fills them from the camera's
+// SliceParam table and sets *bad if a group's brick did not fit.
 bool tma_forward_available();
+// Tensor map over [nz_total][ny][nx] floats with box {bx, by, tma_forward_group()}.
 bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, int bx, int by);
-// The same for a plane stack whose third-axis stride (floats) is z_stride.
+// The same for a plane stack whose third-axis stride (floats) is z_stride, box depth bz.
 bool tma_encode_planes(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, long long z_stride, int bx,
-                       int by);
-size_t tma_table_bytes(int w, int nb, int K, int nz, int tiles_s, int tiles_t);
-cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int nb, int bx,
+                       int by, int bz = 1);
+size_t tma_table_bytes(int w, int K, int nz, int tiles_s, int tiles_t);
+cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int bx,
                                int by, void* stab, void* ttab, int* bad, cudaStream_t st);
-int tma_forward_bxy(int max_brick, int w, int nb);
-int tma_forward_occupancy(int w, int nb, int bxy, int tsz);
+int tma_forward_group();
+int tma_forward_tsz(int max_by);
+int tma_forward_max_by();
+int tma_forward_occupancy(int w, int plane, int tsz);
 // items: the launch's work items, those of positive cost (the first n_real)
 // before those whose tile no slice reaches.  chunks: the largest
 // tb.chunks[] of the launch; with chunks > 1, scratch holds n_real * F *
 // chunks * 1024 floats and unit_count n_real * F ints, zero between launches.
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int n_real, int* counter, int w, int nb, int bxy, int tsz, int chunks,
-                                    float* scratch, int* unit_count, int ctas, cudaStream_t st);
+                                    int n_real, int* counter, int w, int plane, int tsz, int chunks, float* scratch,
+                                    int* unit_count, int ctas, cudaStream_t st);
 // Device status word of the projector kernels: bit 0 a brick or band that
 // did not fit (its weights were zeroed), bit 1 a TMA wait that gave up.
 // Read (and optionally cleared) synchronously.

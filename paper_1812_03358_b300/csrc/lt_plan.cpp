@@ -286,50 +286,51 @@ static void free_camera(CameraPlan& c) {
   c = CameraPlan();
 }
 
-// Brick box and band rows of the brick-staged forward for camera c.  For a
-// tile of 32 target pixels along an axis the first taps floor(xi(i) - Q + 1/2)
-// range over [lo, hi] (evaluated at the tile's two ends, widened by 1e-3 so
-// that float evaluation on the device stays inside); the kernel's brick
-// starts at the tile's smallest first tap (columns rounded down to a
-// multiple of 4) and must hold W taps past the largest, and a group of four
-// pixel rows must fit its taps in NB band rows.  Cameras whose window class
-// exceeds 4, whose bricks exceed 1024 floats or whose grid rows are not a
-// multiple of 4 floats keep the direct kernels.
-static void plan_bricks(CameraPlan& c, int grid_nx, const std::vector<Footprint>& fps,
+// Brick box of the brick-staged forward for camera c.  A stage fill brings
+// the bricks of a group of tma_forward_group() consecutive slices (groups
+// start at multiples of the group size) with one origin: for a tile of 32
+// target pixels along an axis the first taps floor(xi(i) - Q + 1/2) range
+// over [lo, hi] over the group's slices (evaluated at the tile's two ends,
+// widened by 1e-3 so that float evaluation on the device stays inside); the
+// brick starts at the smallest first tap (columns rounded down to a
+// multiple of 4) and must hold W taps past the largest.  Cameras whose
+// window class exceeds 4, whose bricks exceed 1024 floats or
+// tma_forward_max_by() rows, or whose grid rows are not a multiple of 4
+// floats keep the direct kernels.  tma_nb = 4 marks a camera that runs the
+// brick-staged kernel.
+static void plan_bricks(CameraPlan& c, int grid_nx, int nz, const std::vector<Footprint>& fps,
                         const std::vector<Footprint>& fpt, int tiles_s, int tiles_t) {
   c.tma_bx = c.tma_by = c.tma_nb = 0;
   const int W = window_class(std::max(c.wmax_s, c.wmax_t));
   if (W > 4 || grid_nx % 4 != 0) return;   // a TMA row stride is a multiple of 16 bytes
   auto tap_range = [](const Footprint& f, int i0, int i1, long long& lo, long long& hi) {
     const double a = f.C0 + f.C1 * i0 - (double)f.a.Q + 0.5, b = f.C0 + f.C1 * i1 - (double)f.a.Q + 0.5;
-    lo = (long long)std::floor(std::min(a, b) - 1e-3);
-    hi = (long long)std::floor(std::max(a, b) + 1e-3);
+    lo = std::min(lo, (long long)std::floor(std::min(a, b) - 1e-3));
+    hi = std::max(hi, (long long)std::floor(std::max(a, b) + 1e-3));
   };
-  long long need_bx = 0, span_t = 0, need_nb = 0;
-  for (size_t q = 0; q < fps.size(); ++q) {
-    for (int ts = 0; ts < tiles_s; ++ts) {
-      long long lo, hi;
-      tap_range(fps[q], ts * kBeamTileS, ts * kBeamTileS + kBeamTileS - 1, lo, hi);
-      need_bx = std::max(need_bx, hi + W - 1 - (lo & ~3LL) + 1);
-    }
-    for (int tt = 0; tt < tiles_t; ++tt) {
-      long long lo, hi;
-      tap_range(fpt[q], tt * kBeamTileT, tt * kBeamTileT + kBeamTileT - 1, lo, hi);
-      span_t = std::max(span_t, hi - lo);
-      for (int g = 0; g < kBeamTileT / 4; ++g) {
-        const int r0 = tt * kBeamTileT + 4 * g;
-        tap_range(fpt[q], r0, r0 + 3, lo, hi);
-        need_nb = std::max(need_nb, hi - lo + W);
+  const int G = tma_forward_group();
+  long long need_bx = 0, span_t = 0;
+  for (int k = 0; k < c.K; ++k)
+    for (int n0 = 0; n0 < nz; n0 += G) {
+      const int n1 = std::min(nz, n0 + G);
+      for (int ts = 0; ts < tiles_s; ++ts) {
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        for (int n = n0; n < n1; ++n)
+          tap_range(fps[(size_t)k * nz + n], ts * kBeamTileS, ts * kBeamTileS + kBeamTileS - 1, lo, hi);
+        need_bx = std::max(need_bx, hi + W - 1 - (lo & ~3LL) + 1);
+      }
+      for (int tt = 0; tt < tiles_t; ++tt) {
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        for (int n = n0; n < n1; ++n)
+          tap_range(fpt[(size_t)k * nz + n], tt * kBeamTileT, tt * kBeamTileT + kBeamTileT - 1, lo, hi);
+        span_t = std::max(span_t, hi - lo);
       }
     }
-  }
-  const int nb = need_nb <= 4 ? 4 : need_nb <= 8 ? 8 : 0;
-  if (nb == 0) return;
-  const long long bx = (need_bx + 3) / 4 * 4, by = span_t + nb;
-  if (bx > 256 || by > 256 || bx * by > 1024) return;
+  const long long bx = (need_bx + 3) / 4 * 4, by = span_t + W;
+  if (bx > 256 || by > tma_forward_max_by() || bx * by > 1024) return;
   c.tma_bx = (int)bx;
   c.tma_by = (int)by;
-  c.tma_nb = nb;
+  c.tma_nb = 4;
 }
 
 // Image box of the box-staged adjoint for camera c: per (cell, chunk of
@@ -440,12 +441,12 @@ static lt_status plan_weight_tables(CameraPlan& c, int nz, int idx) {
     return LT_OK;
   }
   const int W = window_class(std::max(c.wmax_s, c.wmax_t));
-  const size_t bytes = tma_table_bytes(W, c.tma_nb, c.K, nz, c.tiles_s, c.tiles_t);
+  const size_t bytes = tma_table_bytes(W, c.K, nz, c.tiles_s, c.tiles_t);
   if (bytes > kMaxTableBytes) {
     c.tma_nb = 0;
     return LT_OK;
   }
-  const size_t s_bytes = tma_table_bytes(W, c.tma_nb, c.K, nz, c.tiles_s, 0);
+  const size_t s_bytes = tma_table_bytes(W, c.K, nz, c.tiles_s, 0);
   int* d_bad = nullptr;
   if (device_alloc(&c.d_stab, s_bytes) != cudaSuccess ||
       device_alloc(&c.d_ttab, bytes - s_bytes) != cudaSuccess ||
@@ -456,8 +457,8 @@ static lt_status plan_weight_tables(CameraPlan& c, int nz, int idx) {
   int bad = 0;
   cudaError_t e = cudaMemset(d_bad, 0, sizeof(int));
   if (e == cudaSuccess)
-    e = launch_beam_tables(c.d_slice, c.K, nz, c.tiles_s, c.tiles_t, W, c.tma_nb, c.tma_bx, c.tma_by, c.d_stab,
-                           c.d_ttab, d_bad, 0);
+    e = launch_beam_tables(c.d_slice, c.K, nz, c.tiles_s, c.tiles_t, W, c.tma_bx, c.tma_by, c.d_stab, c.d_ttab,
+                           d_bad, 0);
   if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(d_bad);
   if (e != cudaSuccess) return cuda_error(e, "forward weight tables");
@@ -532,7 +533,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
     return set_error(LT_EUNSUPPORTED,
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
-  plan_bricks(c, v.nx, fps, fpt, tiles_s, tiles_t);
+  plan_bricks(c, v.nx, v.nz, fps, fpt, tiles_s, tiles_t);
   plan_adjoint_box(c, v, tgt_ns, fps, fpt);
   for (auto& r : srange)
     if (r.y < 0) r = make_int2(0, 0);
@@ -1151,13 +1152,13 @@ static lt_status plan_camera(const lt_volume_desc& v0, const lt_camera_desc& src
 // Chunks of the brick-staged forward: a camera whose tiles meeting the
 // volume (times frames) number at most a quarter of the CTAs the kernel
 // keeps resident splits each tile's slices into up to 4 parts, so that more
-// SMs share its work (measured: with about one tile per resident CTA the
-// extra per-chunk start-up and combining cost more than the better balance
-// gains, so larger workloads keep whole tiles); the partial tiles and
-// per-tile counts live in plan scratch sized for the largest launch (a
-// window-class group of the batched forward, or one camera).
+// SMs share its work (measured: splitting the items of larger workloads
+// costs more in combining the partial tiles than it gains in balance);
+// the partial tiles and per-tile counts live in plan scratch sized for the
+// largest launch (a window-class group of the batched forward, or one
+// camera).
 static lt_status plan_chunks(lt_plan* p) {
-  const long long slots = 7LL * p->sms;   // resident CTAs of the brick-staged kernel
+  const long long slots = 4LL * p->sms;   // resident CTAs of the brick-staged kernel
   long long need_part = 0, need_count = 0;
   for (auto& c : p->cams) {
     c.tma_chunks = 1;
@@ -1481,8 +1482,8 @@ static BeamCam beam_cam(const CameraPlan& c, const float* xc, float* out, const 
 
 // One persistent forward launch over `items` of the cameras in b (cps[i] is
 // the plan of b.cam[i]).  The brick-staged TMA kernel runs when the items
-// belong to cameras the planner sized bricks of `staged_nb` band rows for
-// (0: none), the plan's variant selects it and every source is 16-byte
+// belong to cameras the planner sized bricks for (staged_nb = their tma_nb,
+// 0: none), the plan's variant selects it and every source is 16-byte
 // aligned; otherwise the direct kernel of the variant (variant kTmaVariant
 // falls back to the default direct variant).
 static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* cps, const int4* items,
@@ -1492,8 +1493,7 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
     TmaBatch tb;
     std::memset(&tb, 0, sizeof(tb));
     bool ok = true;
-    const int nb = staged_nb;
-    int brick = 0, tsz = 0, chunks = 1;
+    int brick = 0, max_by = 1, chunks = 1;
     for (int i = 0; i < b.n_cams && ok; ++i) {
       const CameraPlan& c = *cps[i];
       const BeamCam& bc = b.cam[i];
@@ -1509,13 +1509,13 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       tb.bx[i] = c.tma_bx;
       tb.by[i] = c.tma_by;
       brick = std::max(brick, c.tma_bx * c.tma_by);
-      tsz = std::max(tsz, 32 * c.tma_by);
+      max_by = std::max(max_by, c.tma_by);
     }
     if (ok) {
-      const int bxy = tma_forward_bxy(brick, wclass, nb);
-      const int occ = tma_forward_occupancy(wclass, nb, bxy, tsz);
+      const int tsz = tma_forward_tsz(max_by);
+      const int occ = tma_forward_occupancy(wclass, brick, tsz);
       if (occ > 0) {
-        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, n_real, p->d_counter, wclass, nb, bxy, tsz,
+        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, n_real, p->d_counter, wclass, brick, tsz,
                                                 chunks, p->d_chunk_part, p->d_chunk_count, p->sms * occ, st);
         return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward (TMA bricks)");
       }

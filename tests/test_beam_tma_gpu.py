@@ -1,5 +1,5 @@
-"""The brick-staged forward (volume bricks brought to shared memory by TMA,
-one warp per slice) against the FP64 oracle and against the direct beam
+"""The brick-staged forward (volume bricks brought to shared memory by TMA
+by a producer warp, contracted by four consumer warps) against the FP64 oracle and against the direct beam
 kernel, through the C ABI.
 
 Plans use the brick-staged kernel by default (forward variant 5) wherever
@@ -57,6 +57,8 @@ def _cases():
         I.Camera(kind=0, det_ns=45, det_nt=37, det_ps=0.09, det_pt=0.08, ks=2, kt=2), True
     c = I.table_single_lens(44, 0.1, ks=3, kt=3)
     yield "coarse pixels (wide band), 3x3 cells", I.Volume(16, 20, 10, 4.0, 4.0, 4.0), c, True
+    c = I.table_single_lens(36, 0.09, ks=8, kt=8)
+    yield "8x8 cell grid (more cells than lanes)", I.Volume(20, 16, 10, 4.0, 4.0, 5.0), c, True
     c = I.table_single_lens(40, 0.08, ks=2, kt=1)
     c.basis = I.BASIS_DIRAC
     yield "Dirac cells", I.Volume(24, 16, 9, 3.0, 3.0, 5.0), c, True
