@@ -14,10 +14,13 @@
 // cell_weight of the same (pixel, cell) pair as the forward, the t entries
 // already multiplied by the slice scale as in the forward).  Buffers are
 // double so that the next cell's data arrives while this one is used.  Per
-// slice, warp r contracts along t into its own row of U (lanes over box
-// columns) and then every voxel along s from that row: no CTA barrier
-// inside a chunk.  Each image pixel is read from L2 once per (tile, cell,
-// chunk).  Outside the image the TMA load fills zeros.  Waits are bounded
+// slice, warp r contracts along t into its own row of U (lanes over pairs of
+// box columns, one packed f32x2 FMA per pair) and then every voxel along s
+// from that row: no CTA barrier inside a chunk.  The window tables are
+// trimmed at plan time to each (tile, slice)'s longest run of nonzero
+// entries, so the loops run over the entries the footprints reach rather
+// than the camera's largest window.  Each image pixel is read from L2 once
+// per (tile, cell, chunk).  Outside the image the TMA load fills zeros.  Waits are bounded
 // (status bit 1); a box the planner sized too small is reported when the
 // tables are built, and that camera keeps the direct adjoint.
 #include <cuda.h>
@@ -39,6 +42,19 @@ constexpr int AWMAX = 32;       // adjoint window cap (target pixels per voxel p
 constexpr long long kAdjWaitPolls = 1LL << 22;
 
 __device__ int g_adjoint_status;
+
+// Table entry sizes (floats).  S entry (cell, tile column, slice): float
+// sw[wqs][AX] (trimmed windows), int i0[AX] (first target pixel of each
+// voxel column's window), int {cnt, 0, 0, 0}.  T entry (cell, tile row,
+// slice): {float weight x slice scale, int target row}[wqt][AY], int {cnt,
+// 0, 0, 0}.  Both are multiples of 16 bytes (bulk copies).
+__host__ __device__ __forceinline__ int s_entry_floats(int wqs) { return wqs * AX + AX + 4; }
+__host__ __device__ __forceinline__ int t_entry_floats(int wqt) { return wqt * AY * 2 + 4; }
+
+// Column c of a warp's row of U lives at upad(c): one pad word per 32, so
+// that the s-contraction's reads (voxel columns about a magnification apart)
+// spread over more banks.
+__host__ __device__ __forceinline__ int upad(int c) { return c + (c >> 5); }
 
 __device__ __forceinline__ void a_mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -77,52 +93,89 @@ __device__ __forceinline__ void a_bulk(uint32_t dst, const void* src, uint32_t b
 }
 
 // ---------------------------------------------------------------------------
-// Plan-time tables.  S entry (cell k, tile column tx, slice n): float
-// sw[wqs][32] (column c's entries, zero past the slice's window or the
-// volume), int i0[32] (first target pixel of the window).  T entry (k, tile
-// row ty, n): float tw[wqt][8] (x slice scale), int tr[wqt][8] (target rows).
+// Plan-time tables (entry layouts at s_entry_floats / t_entry_floats).
 // Origin entries (k, chunk, tile): int2 {first box column (a multiple of 4)
 // or row, 1 if the chunk's windows fit the planned box}.
 // ---------------------------------------------------------------------------
+// Window of voxel column jx (or row) trimmed to its nonzero entries: the
+// first entry moves to the first nonzero one, and every voxel of the tile
+// keeps `cnt` entries, the tile's longest nonzero run; a run starts no later
+// than wq - cnt, so that every entry read stays inside the untrimmed window
+// (which the planned box covers).  Entries past a voxel's run are zero.
+__device__ __forceinline__ void trim_window(int qf, int ql, int wq, int& cnt, int& shift) {
+  const int span = ql >= qf ? ql - qf + 1 : 0;
+  cnt = __reduce_max_sync(0xffffffffu, span);
+  shift = span > 0 ? min(qf, wq - cnt) : 0;
+}
+
+__device__ __forceinline__ float s_entry(const SliceParam& p, int jx, int nx, int i0, int q) {
+  float w = 0.0f;
+  if (q < p.wis && jx < nx) {
+    int jc;
+    float fr;
+    footprint_centre(p.s, i0 + q, jc, fr);
+    w = cell_weight(jx - jc, fr, p.s);
+  }
+  return w;
+}
+
+__device__ __forceinline__ float t_entry(const SliceParam& p, int jy, int ny, int i0, int q) {
+  float w = 0.0f;
+  if (q < p.wit && jy < ny) {
+    int jc;
+    float fr;
+    footprint_centre(p.t, i0 + q, jc, fr);
+    w = __fmul_rn(cell_weight(jy - jc, fr, p.t), p.scale);
+  }
+  return w;
+}
+
+// Block (tile column, slice, cell), lane = voxel column.
 __global__ void adj_s_table(const SliceParam* __restrict__ prm, int nz, int nx, int wqs, int tiles_x,
                             float* __restrict__ tab) {
   const int tx = blockIdx.x, n = blockIdx.y, k = blockIdx.z, c = threadIdx.x;
   const SliceParam& p = prm[(long long)k * nz + n];
   const int jx = tx * AX + c, je = min(jx, nx - 1);
-  float* e = tab + (((long long)k * tiles_x + tx) * nz + n) * (wqs * AX + AX);
+  float* e = tab + (((long long)k * tiles_x + tx) * nz + n) * s_entry_floats(wqs);
   const int i0 = window_start(p.s, je);
-  for (int q = 0; q < wqs; ++q) {
-    float w = 0.0f;
-    if (q < p.wis && jx < nx) {
-      int jc;
-      float fr;
-      footprint_centre(p.s, i0 + q, jc, fr);
-      w = cell_weight(jx - jc, fr, p.s);
+  int qf = wqs, ql = -1;
+  for (int q = 0; q < wqs; ++q)
+    if (s_entry(p, jx, nx, i0, q) != 0.0f) {
+      qf = min(qf, q);
+      ql = q;
     }
-    e[q * AX + c] = w;
-  }
-  reinterpret_cast<int*>(e + wqs * AX)[c] = i0;
+  int cnt, shift;
+  trim_window(qf, ql, wqs, cnt, shift);
+  for (int q = 0; q < wqs; ++q) e[q * AX + c] = q < cnt ? s_entry(p, jx, nx, i0, shift + q) : 0.0f;
+  int* ei = reinterpret_cast<int*>(e + wqs * AX);
+  ei[c] = i0 + shift;
+  if (c < 4) ei[AX + c] = c == 0 ? cnt : 0;
 }
 
+// Block (tile row, slice, cell), lane r < AY = voxel row; entries {weight,
+// target row} interleaved so that one 8-byte broadcast load brings both.
 __global__ void adj_t_table(const SliceParam* __restrict__ prm, int nz, int ny, int wqt, int tiles_y,
                             float* __restrict__ tab) {
-  const int ty = blockIdx.x, n = blockIdx.y, k = blockIdx.z;
+  const int ty = blockIdx.x, n = blockIdx.y, k = blockIdx.z, r = threadIdx.x;
   const SliceParam& p = prm[(long long)k * nz + n];
-  float* e = tab + (((long long)k * tiles_y + ty) * nz + n) * (wqt * AY * 2);
-  for (int t = threadIdx.x; t < wqt * AY; t += blockDim.x) {
-    const int q = t / AY, r = t % AY;
-    const int jy = ty * AY + r, je = min(jy, ny - 1);
-    const int i = window_start(p.t, je) + q;
-    float w = 0.0f;
-    if (q < p.wit && jy < ny) {
-      int jc;
-      float fr;
-      footprint_centre(p.t, i, jc, fr);
-      w = __fmul_rn(cell_weight(jy - jc, fr, p.t), p.scale);
+  int* e = reinterpret_cast<int*>(tab + (((long long)k * tiles_y + ty) * nz + n) * t_entry_floats(wqt));
+  const int jy = ty * AY + r, je = min(jy, ny - 1);
+  const int i0 = window_start(p.t, je);
+  int qf = wqt, ql = -1;
+  if (r < AY)
+    for (int q = 0; q < wqt; ++q)
+      if (t_entry(p, jy, ny, i0, q) != 0.0f) {
+        qf = min(qf, q);
+        ql = q;
+      }
+  int cnt, shift;
+  trim_window(qf, ql, wqt, cnt, shift);
+  if (r < AY)
+    for (int q = 0; q < wqt; ++q) {
+      e[2 * (q * AY + r)] = __float_as_int(q < cnt ? t_entry(p, jy, ny, i0, shift + q) : 0.0f);
+      e[2 * (q * AY + r) + 1] = i0 + shift + min(q, cnt > 0 ? cnt - 1 : 0);
     }
-    e[q * AY + r] = w;
-    reinterpret_cast<int*>(e + wqt * AY)[q * AY + r] = i;
-  }
+  if (r < 4) e[2 * wqt * AY + r] = r == 0 ? cnt : 0;
 }
 
 // axis 0: columns (x, s), axis 1: rows (y, t).  Thread = tile; the union of
@@ -188,7 +241,7 @@ __device__ __forceinline__ void adj_issue(const BeamCam& C, const AdjBatch& A, c
   org[0] = ox.x;
   org[1] = oy.x;
   const int bx = A.bx[cam], by = A.by[cam];
-  const uint32_t sb = (uint32_t)(A.wqs[cam] * AX + AX) * 4, tb = (uint32_t)(A.wqt[cam] * AY * 2) * 4;
+  const uint32_t sb = (uint32_t)s_entry_floats(A.wqs[cam]) * 4, tb = (uint32_t)t_entry_floats(A.wqt[cam]) * 4;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   a_expect_tx(bar, (uint32_t)(bx * by * 4) + n_cnt * (sb + tb));
   const uint32_t dst = smem_addr(stage);
@@ -262,30 +315,38 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
     const float* S0 = reinterpret_cast<const float*>(stg + (size_t)L.box_floats * 4);
     const float* T0 = reinterpret_cast<const float*>(stg + (size_t)L.box_floats * 4 + (size_t)ASC * L.s_bytes);
     float* Ur = U + warp * ucols;
-#pragma unroll 1
-    for (int s = 0; s < n_cnt; ++s) {
-      // t: this warp's voxel row over every box column
-      const float* T = T0 + s * (wqt * AY * 2);
-      const int* Tr = reinterpret_cast<const int*>(T + wqt * AY);
-      float v[CI];
 #pragma unroll
-      for (int m = 0; m < CI; ++m) v[m] = 0.0f;
-      for (int q = 0; q < wqt; ++q) {
-        const float w = T[q * AY + warp];
-        const float* row = box + (Tr[q * AY + warp] - y0) * bx + lane;
+    for (int s = 0; s < ASC; ++s) {
+      if (s >= n_cnt) break;
+      // t: this warp's voxel row over every box column, two columns per
+      // packed FMA; each window entry's {weight, row} in one broadcast load
+      const int* T = reinterpret_cast<const int*>(T0 + s * t_entry_floats(wqt));
+      const int cnt_t = T[2 * wqt * AY];
+      float2 v[CI];
+#pragma unroll
+      for (int m = 0; m < CI; ++m) v[m] = make_float2(0.0f, 0.0f);
+      for (int q = 0; q < cnt_t; ++q) {
+        const int2 e = reinterpret_cast<const int2*>(T)[q * AY + warp];
+        const float2 w2 = make_float2(__int_as_float(e.x), __int_as_float(e.x));
+        const float2* row = reinterpret_cast<const float2*>(box + (e.y - y0) * bx) + lane;
 #pragma unroll
         for (int m = 0; m < CI; ++m)
-          if (lane + AX * m < bx) v[m] = fmaf(w, row[AX * m], v[m]);
+          if (2 * (lane + AX * m) < bx) v[m] = __ffma2_rn(w2, row[AX * m], v[m]);
       }
 #pragma unroll
       for (int m = 0; m < CI; ++m)
-        if (lane + AX * m < bx) Ur[lane + AX * m] = v[m];
+        if (2 * (lane + AX * m) < bx) {
+          const int c = 2 * (lane + AX * m);
+          Ur[upad(c)] = v[m].x;
+          Ur[upad(c + 1)] = v[m].y;
+        }
       __syncwarp();
       // s: this voxel from its row of U
-      const float* S = S0 + s * (wqs * AX + AX);
-      const float* Uc = Ur + (reinterpret_cast<const int*>(S + wqs * AX)[lane] - x0);
+      const float* S = S0 + s * s_entry_floats(wqs);
+      const int* Si = reinterpret_cast<const int*>(S + wqs * AX);
+      const int cnt_s = Si[AX], u0 = Si[lane] - x0;
       float a = 0.0f;
-      for (int q = 0; q < wqs; ++q) a = fmaf(S[q * AX + lane], Uc[q], a);
+      for (int q = 0; q < cnt_s; ++q) a = fmaf(S[q * AX + lane], Ur[upad(u0 + q)], a);
       acc[s] += a;
       __syncwarp();
     }
@@ -314,11 +375,7 @@ const void* adj_select(int ci) {
     case 1: return adj_kernel<1>();
     case 2: return adj_kernel<2>();
     case 3: return adj_kernel<3>();
-    case 4: return adj_kernel<4>();
-    case 5: return adj_kernel<5>();
-    case 6: return adj_kernel<6>();
-    case 7: return adj_kernel<7>();
-    default: return adj_kernel<8>();
+    default: return adj_kernel<4>();
   }
 }
 
@@ -340,8 +397,8 @@ int adjoint_chunk() { return ASC; }
 void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, size_t* s_bytes, size_t* t_bytes,
                          size_t* ox_count, size_t* oy_count) {
   const long long tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + ASC - 1) / ASC;
-  *s_bytes = (size_t)K * nz * tiles_x * (wqs * AX + AX) * 4;
-  *t_bytes = (size_t)K * nz * tiles_y * (wqt * AY * 2) * 4;
+  *s_bytes = (size_t)K * nz * tiles_x * s_entry_floats(wqs) * 4;
+  *t_bytes = (size_t)K * nz * tiles_y * t_entry_floats(wqt) * 4;
   *ox_count = (size_t)K * chunks * tiles_x;
   *oy_count = (size_t)K * chunks * tiles_y;
 }
@@ -350,7 +407,7 @@ cudaError_t launch_adjoint_tables(const SliceParam* prm, int K, int nz, int nx, 
                                   int by, float* stab, float* ttab, int2* ox, int2* oy, int* bad, cudaStream_t st) {
   const int tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + ASC - 1) / ASC;
   adj_s_table<<<dim3(tiles_x, nz, K), AX, 0, st>>>(prm, nz, nx, wqs, tiles_x, stab);
-  adj_t_table<<<dim3(tiles_y, nz, K), 128, 0, st>>>(prm, nz, ny, wqt, tiles_y, ttab);
+  adj_t_table<<<dim3(tiles_y, nz, K), 32, 0, st>>>(prm, nz, ny, wqt, tiles_y, ttab);
   adj_origins<<<dim3((tiles_x + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, nx, AX, tiles_x, 0, wqs, bx, chunks, ox,
                                                                    bad);
   adj_origins<<<dim3((tiles_y + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, ny, AY, tiles_y, 1, wqt, by, chunks, oy,
@@ -366,14 +423,14 @@ cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, float
     if (a.bx[c] <= 0 || a.by[c] <= 0 || a.wqs[c] > AWMAX || a.wqt[c] > AWMAX) return cudaErrorInvalidValue;
     box = std::max(box, a.bx[c] * a.by[c]);
     bxmax = std::max(bxmax, a.bx[c]);
-    sb = std::max(sb, (a.wqs[c] * AX + AX) * 4);
-    tb = std::max(tb, a.wqt[c] * AY * 2 * 4);
+    sb = std::max(sb, s_entry_floats(a.wqs[c]) * 4);
+    tb = std::max(tb, t_entry_floats(a.wqt[c]) * 4);
   }
   if (bxmax > AX * 8) return cudaErrorInvalidValue;
   AdjStage L{(box + 31) / 32 * 32, sb, tb};
-  int ucols = (bxmax + 31) / 32 * 32;
+  int ucols = upad((bxmax + 31) / 32 * 32);
   const size_t smem = 2 * L.bytes() + (size_t)AY * ucols * sizeof(float);
-  const void* fn = adj_select((bxmax + AX - 1) / AX);
+  const void* fn = adj_select((bxmax + 2 * AX - 1) / (2 * AX));   // column pairs per lane
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int tiles_x = (nx + AX - 1) / AX;
