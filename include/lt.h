@@ -260,6 +260,8 @@ typedef struct {
                              * direct kernel                                   */
   int64_t adjoint_box;      /* floats per image box of the box-staged adjoint,
                              * 0 if the camera takes the direct adjoint        */
+  int64_t adjoint_chunk;    /* slices per box of the box-staged adjoint (8, or
+                             * 4 where an 8-slice box would exceed its cap)    */
 } lt_camera_stats;
 
 LT_API lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_camera_stats* out);

@@ -4,7 +4,7 @@
 // x[n][jy][jx] = sum over cameras, cells k, target pixels (it, is) of
 // Bt[it][jy] Bs[is][jx] g_k[it][is] x scale_kn: the transpose of the beam
 // forward, evaluated as a gather (one writer per voxel, no atomics).  A CTA
-// owns a 32 x 8 voxel tile (thread = voxel) and a chunk of ASC consecutive
+// owns a 32 x 8 voxel tile (thread = voxel) and a chunk of SC consecutive
 // slices of one frame, and keeps one accumulator per slice of the chunk in
 // registers.  For each (camera, cell) one thread brings into shared memory,
 // all completing one mbarrier: the image box every slice of the chunk reads
@@ -37,8 +37,9 @@ namespace {
 
 constexpr int AX = 32;          // voxel columns per tile (lanes)
 constexpr int AY = 8;           // voxel rows per tile (warps)
-constexpr int ASC = 8;          // slices per chunk (register accumulators)
+constexpr int ASC_MAX = 8;      // slices per chunk (register accumulators): 8, or 4 where 8 slices' box is too big
 constexpr int AWMAX = 32;       // adjoint window cap (target pixels per voxel per axis)
+constexpr size_t kAdjDoubleMax = 74 * 1024;   // shared bytes up to which the stages are double buffered
 constexpr long long kAdjWaitPolls = 1LL << 22;
 
 __device__ int g_adjoint_status;
@@ -183,13 +184,13 @@ __global__ void adj_t_table(const SliceParam* __restrict__ prm, int nz, int ny, 
 // Every table row holds wq (the camera's largest window) entries, so the box
 // reaches wq pixels past each window start.
 __global__ void adj_origins(const SliceParam* __restrict__ prm, int nz, int nvox, int tile, int tiles, int axis,
-                            int wq, int box, int chunks, int2* __restrict__ out, int* __restrict__ bad) {
+                            int wq, int box, int sc, int chunks, int2* __restrict__ out, int* __restrict__ bad) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int ch = blockIdx.y, k = blockIdx.z;
   if (t >= tiles) return;
   const int j0 = t * tile, j1 = min(j0 + tile, nvox) - 1;
   int lo = 0x7fffffff, hi = -0x7fffffff;
-  for (int n = ch * ASC; n < min(ch * ASC + ASC, nz); ++n) {
+  for (int n = ch * sc; n < min(ch * sc + sc, nz); ++n) {
     const SliceParam& p = prm[(long long)k * nz + n];
     const AxisParam& a = axis == 0 ? p.s : p.t;
     const int s0 = window_start(a, j0), s1 = window_start(a, j1);
@@ -223,11 +224,12 @@ __device__ __forceinline__ void unit_next(const BeamBatch& B, UnitCursor& u) {
 }
 
 // Shared-memory stage of one (camera, cell): the image box, then the
-// chunk's S and T entries (sizes are the launch's largest).
+// chunk's sc S and T entries (sizes are the launch's largest).
 struct AdjStage {
-  int box_floats, s_bytes, t_bytes;
+  int box_floats, s_bytes, t_bytes, sc;
+  int nbuf;   // 2: double buffered over cells; 1: one stage (large boxes), refilled after each cell
   __host__ __device__ size_t bytes() const {
-    return ((size_t)box_floats * 4 + (size_t)ASC * s_bytes + (size_t)ASC * t_bytes + 127) / 128 * 128;
+    return ((size_t)box_floats * 4 + (size_t)sc * s_bytes + (size_t)sc * t_bytes + 127) / 128 * 128;
   }
 };
 
@@ -251,16 +253,16 @@ __device__ __forceinline__ void adj_issue(const BeamCam& C, const AdjBatch& A, c
   const char* t_src = reinterpret_cast<const char*>(A.ttab[cam]) +
                       (((long long)k * A.tiles_y[cam] + ty) * C.nz + n0) * (long long)tb;
   a_bulk(dst + (uint32_t)L.box_floats * 4, s_src, n_cnt * sb, bar);
-  a_bulk(dst + (uint32_t)L.box_floats * 4 + ASC * (uint32_t)L.s_bytes, t_src, n_cnt * tb, bar);
+  a_bulk(dst + (uint32_t)L.box_floats * 4 + (uint32_t)L.sc * (uint32_t)L.s_bytes, t_src, n_cnt * tb, bar);
 }
 
-template <int CI>
+template <int CI, int SC>
 __global__ void __launch_bounds__(AX * AY, 3)
 beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ AdjBatch A, float* __restrict__ x,
                  long long x_fs, int accumulate, int tiles_x, AdjStage L, int ucols) {
   extern __shared__ __align__(128) unsigned char dsm[];
   const size_t stage_bytes = L.bytes();
-  float* U = reinterpret_cast<float*>(dsm + 2 * stage_bytes);    // [AY][ucols]
+  float* U = reinterpret_cast<float*>(dsm + (size_t)L.nbuf * stage_bytes);    // [AY][ucols], after the stages
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int org[2][2];         // box origin (x0, y0) per buffer
   __shared__ int s_fail;
@@ -271,8 +273,8 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
   const int jx = tx * AX + lane, jy = ty * AY + warp;
   const int chunk = blockIdx.y;
-  const int n0 = chunk * ASC;
-  const int n_cnt = min(ASC, nz - n0);
+  const int n0 = chunk * SC;
+  const int n_cnt = min(SC, nz - n0);
   const int frame = blockIdx.z;
 
   if (threadIdx.x < 2) a_mbar_init(smem_addr(&bars[threadIdx.x]));
@@ -280,9 +282,9 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
 
-  float acc[ASC];
+  float acc[SC];
 #pragma unroll
-  for (int s = 0; s < ASC; ++s) acc[s] = 0.0f;
+  for (int s = 0; s < SC; ++s) acc[s] = 0.0f;
 
   UnitCursor cur{0, 0, false};
   unit_first(B, cur);
@@ -290,21 +292,22 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
     adj_issue(B.cam[cur.cam], A, L, cur.cam, cur.k, tx, ty, chunk, n0, n_cnt, frame, dsm, smem_addr(&bars[0]),
               org[0]);
   int u = 0;
+  const bool dbl = L.nbuf == 2;
   while (cur.valid) {
-    const int buf = u & 1;
+    const int buf = dbl ? (u & 1) : 0;
     UnitCursor nxt = cur;
     unit_next(B, nxt);
-    if (nxt.valid && threadIdx.x == 0)   // the other buffer was released by the barrier ending unit u - 1
+    if (dbl && nxt.valid && threadIdx.x == 0)   // the other buffer was released by the barrier ending unit u - 1
       adj_issue(B.cam[nxt.cam], A, L, nxt.cam, nxt.k, tx, ty, chunk, n0, n_cnt, frame, dsm + (buf ^ 1) * stage_bytes,
                 smem_addr(&bars[buf ^ 1]), org[buf ^ 1]);
-    if (!a_wait(smem_addr(&bars[buf]), (u >> 1) & 1)) {
+    if (!a_wait(smem_addr(&bars[buf]), dbl ? (u >> 1) & 1 : u & 1)) {
       if (threadIdx.x == 0) atomicOr(&g_adjoint_status, 2);
       s_fail = 1;
     }
     __syncthreads();
     if (s_fail) {
       // leave no copy in flight behind: wait (bounded) for the stage issued next
-      if (threadIdx.x == 0 && nxt.valid) a_wait(smem_addr(&bars[buf ^ 1]), ((u + 1) >> 1) & 1);
+      if (dbl && threadIdx.x == 0 && nxt.valid) a_wait(smem_addr(&bars[buf ^ 1]), ((u + 1) >> 1) & 1);
       break;
     }
     const int cam = cur.cam;
@@ -313,10 +316,10 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
     const int bx = A.bx[cam], wqs = A.wqs[cam], wqt = A.wqt[cam];
     const int x0 = org[buf][0], y0 = org[buf][1];
     const float* S0 = reinterpret_cast<const float*>(stg + (size_t)L.box_floats * 4);
-    const float* T0 = reinterpret_cast<const float*>(stg + (size_t)L.box_floats * 4 + (size_t)ASC * L.s_bytes);
+    const float* T0 = reinterpret_cast<const float*>(stg + (size_t)L.box_floats * 4 + (size_t)SC * L.s_bytes);
     float* Ur = U + warp * ucols;
 #pragma unroll
-    for (int s = 0; s < ASC; ++s) {
+    for (int s = 0; s < SC; ++s) {
       if (s >= n_cnt) break;
       // t: this warp's voxel row over every box column, two columns per
       // packed FMA; each window entry's {weight, row} in one broadcast load
@@ -351,13 +354,16 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
       __syncwarp();
     }
     __syncthreads();   // this buffer may be refilled
+    if (!dbl && nxt.valid && threadIdx.x == 0)
+      adj_issue(B.cam[nxt.cam], A, L, nxt.cam, nxt.k, tx, ty, chunk, n0, n_cnt, frame, dsm, smem_addr(&bars[0]),
+                org[0]);
     cur = nxt;
     ++u;
   }
   if (s_fail) return;
   if (jx < nx && jy < ny) {
 #pragma unroll
-    for (int s = 0; s < ASC; ++s) {
+    for (int s = 0; s < SC; ++s) {
       if (s < n_cnt) {
         float* o = x + (long long)frame * x_fs + ((long long)(n0 + s) * ny + jy) * nx + jx;
         *o = accumulate ? *o + acc[s] : acc[s];
@@ -366,18 +372,20 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
   }
 }
 
-template <int CI>
+template <int CI, int SC>
 const void* adj_kernel() {
-  return (const void*)beam_adjoint_tma<CI>;
+  return (const void*)beam_adjoint_tma<CI, SC>;
 }
-const void* adj_select(int ci) {
+template <int SC>
+const void* adj_select_ci(int ci) {
   switch (ci) {
-    case 1: return adj_kernel<1>();
-    case 2: return adj_kernel<2>();
-    case 3: return adj_kernel<3>();
-    default: return adj_kernel<4>();
+    case 1: return adj_kernel<1, SC>();
+    case 2: return adj_kernel<2, SC>();
+    case 3: return adj_kernel<3, SC>();
+    default: return adj_kernel<4, SC>();
   }
 }
+const void* adj_select(int ci, int sc) { return sc == 4 ? adj_select_ci<4>(ci) : adj_select_ci<8>(ci); }
 
 }  // namespace
 
@@ -392,11 +400,11 @@ cudaError_t adjoint_status(int* flags, bool clear) {
 
 int adjoint_tile_x() { return AX; }
 int adjoint_tile_y() { return AY; }
-int adjoint_chunk() { return ASC; }
+int adjoint_chunk_max() { return ASC_MAX; }
 
-void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, size_t* s_bytes, size_t* t_bytes,
+void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, int sc, size_t* s_bytes, size_t* t_bytes,
                          size_t* ox_count, size_t* oy_count) {
-  const long long tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + ASC - 1) / ASC;
+  const long long tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + sc - 1) / sc;
   *s_bytes = (size_t)K * nz * tiles_x * s_entry_floats(wqs) * 4;
   *t_bytes = (size_t)K * nz * tiles_y * t_entry_floats(wqt) * 4;
   *ox_count = (size_t)K * chunks * tiles_x;
@@ -404,19 +412,22 @@ void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, size_t
 }
 
 cudaError_t launch_adjoint_tables(const SliceParam* prm, int K, int nz, int nx, int ny, int wqs, int wqt, int bx,
-                                  int by, float* stab, float* ttab, int2* ox, int2* oy, int* bad, cudaStream_t st) {
-  const int tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + ASC - 1) / ASC;
+                                  int by, int sc, float* stab, float* ttab, int2* ox, int2* oy, int* bad,
+                                  cudaStream_t st) {
+  if (sc != 4 && sc != 8) return cudaErrorInvalidValue;
+  const int tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + sc - 1) / sc;
   adj_s_table<<<dim3(tiles_x, nz, K), AX, 0, st>>>(prm, nz, nx, wqs, tiles_x, stab);
   adj_t_table<<<dim3(tiles_y, nz, K), 32, 0, st>>>(prm, nz, ny, wqt, tiles_y, ttab);
-  adj_origins<<<dim3((tiles_x + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, nx, AX, tiles_x, 0, wqs, bx, chunks, ox,
-                                                                   bad);
-  adj_origins<<<dim3((tiles_y + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, ny, AY, tiles_y, 1, wqt, by, chunks, oy,
-                                                                   bad);
+  adj_origins<<<dim3((tiles_x + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, nx, AX, tiles_x, 0, wqs, bx, sc, chunks,
+                                                                   ox, bad);
+  adj_origins<<<dim3((tiles_y + 63) / 64, chunks, K), 64, 0, st>>>(prm, nz, ny, AY, tiles_y, 1, wqt, by, sc, chunks,
+                                                                   oy, bad);
   return cudaGetLastError();
 }
 
-cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, float* x, long long x_fs, int accumulate,
-                                    cudaStream_t st) {
+cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, int sc, float* x, long long x_fs,
+                                    int accumulate, cudaStream_t st) {
+  if (sc != 4 && sc != 8) return cudaErrorInvalidValue;
   const int nx = b.cam[0].nx, ny = b.cam[0].ny, nz = b.cam[0].nz;
   int box = 0, bxmax = 4, sb = 16, tb = 16;
   for (int c = 0; c < b.n_cams; ++c) {
@@ -427,15 +438,17 @@ cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, float
     tb = std::max(tb, t_entry_floats(a.wqt[c]) * 4);
   }
   if (bxmax > AX * 8) return cudaErrorInvalidValue;
-  AdjStage L{(box + 31) / 32 * 32, sb, tb};
+  AdjStage L{(box + 31) / 32 * 32, sb, tb, sc, 2};
   int ucols = upad((bxmax + 31) / 32 * 32);
-  const size_t smem = 2 * L.bytes() + (size_t)AY * ucols * sizeof(float);
-  const void* fn = adj_select((bxmax + 2 * AX - 1) / (2 * AX));   // column pairs per lane
+  // double buffering while it leaves room for three CTAs per SM, else one stage
+  if (2 * L.bytes() + (size_t)AY * ucols * sizeof(float) > kAdjDoubleMax) L.nbuf = 1;
+  const size_t smem = L.nbuf * L.bytes() + (size_t)AY * ucols * sizeof(float);
+  const void* fn = adj_select((bxmax + 2 * AX - 1) / (2 * AX), sc);   // column pairs per lane
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int tiles_x = (nx + AX - 1) / AX;
   const int tiles_y = (ny + AY - 1) / AY;
-  const dim3 grid(tiles_x * tiles_y, (nz + ASC - 1) / ASC, b.frames);
+  const dim3 grid(tiles_x * tiles_y, (nz + sc - 1) / sc, b.frames);
   void* args[] = {(void*)&b, (void*)&a, (void*)&x, (void*)&x_fs, (void*)&accumulate, (void*)&tiles_x, (void*)&L,
                   (void*)&ucols};
   return cudaLaunchKernel(fn, grid, dim3(AX * AY), args, smem, st);

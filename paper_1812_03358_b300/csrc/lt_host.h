@@ -70,6 +70,7 @@ struct CameraPlan {
   int tma_bx = 0, tma_by = 0, tma_nb = 0;
   int tma_chunks = 1;              // parts each forward item is split into (few tiles: more CTAs per tile)
   int adj_bx = 0, adj_by = 0;      // box-staged adjoint: image box (0: the direct adjoint serves it)
+  int adj_sc = 8;                  // its slices per chunk (8 or 4)
   float* d_adj_s = nullptr;        // and its window tables (lt_beam_adj.cu layout)
   float* d_adj_t = nullptr;
   int2* d_adj_ox = nullptr;

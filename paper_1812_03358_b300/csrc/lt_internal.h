@@ -269,20 +269,23 @@ struct AdjBatch {
   int32_t tiles_y[kMaxBatchCams];
   int32_t chunks[kMaxBatchCams];
 };
-// Box-staged adjoint: voxel tile adjoint_tile_x() x adjoint_tile_y(),
-// adjoint_chunk() slices per CTA; x[F][nz][ny][nx] (= or +=) the sum over
-// the batch's cameras and cells.  Tables: adjoint_table_sizes gives the
-// bytes of the S and T tables and the origin counts of one camera;
-// launch_adjoint_tables fills them and sets *bad if a box does not fit.
+// Box-staged adjoint: voxel tile adjoint_tile_x() x adjoint_tile_y(), sc
+// slices per CTA (8, or 4 for cameras whose 8-slice boxes are too big; at
+// most adjoint_chunk_max()); x[F][nz][ny][nx] (= or +=) the sum over the
+// batch's cameras and cells (every camera of a launch planned for the same
+// sc).  Tables: adjoint_table_sizes gives the bytes of the S and T tables
+// and the origin counts of one camera; launch_adjoint_tables fills them and
+// sets *bad if a box does not fit.
 int adjoint_tile_x();
 int adjoint_tile_y();
-int adjoint_chunk();
-void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, size_t* s_bytes, size_t* t_bytes,
+int adjoint_chunk_max();
+void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, int sc, size_t* s_bytes, size_t* t_bytes,
                          size_t* ox_count, size_t* oy_count);
 cudaError_t launch_adjoint_tables(const SliceParam* prm, int K, int nz, int nx, int ny, int wqs, int wqt, int bx,
-                                  int by, float* stab, float* ttab, int2* ox, int2* oy, int* bad, cudaStream_t st);
-cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, float* x, long long x_fs, int accumulate,
-                                    cudaStream_t st);
+                                  int by, int sc, float* stab, float* ttab, int2* ox, int2* oy, int* bad,
+                                  cudaStream_t st);
+cudaError_t launch_beam_adjoint_tma(const BeamBatch& b, const AdjBatch& a, int sc, float* x, long long x_fs,
+                                    int accumulate, cudaStream_t st);
 // Status word of the box-staged adjoint (bits as the forward's).
 cudaError_t adjoint_status(int* flags, bool clear);
 

@@ -571,11 +571,13 @@ __device__ __forceinline__ void s2_copy_rows(float* dst, int dstride, const floa
   }
 }
 
+// acc += a * b elementwise as two packed f32x2 FMAs (each lane of a packed
+// FMA is the round-to-nearest fmaf of that element).
 __device__ __forceinline__ void fma4(float4& acc, float a, const float4& b) {
-  acc.x = fmaf(a, b.x, acc.x);
-  acc.y = fmaf(a, b.y, acc.y);
-  acc.z = fmaf(a, b.z, acc.z);
-  acc.w = fmaf(a, b.w, acc.w);
+  const float2 a2 = make_float2(a, a);
+  const float2 lo = __ffma2_rn(a2, make_float2(b.x, b.y), make_float2(acc.x, acc.y));
+  const float2 hi = __ffma2_rn(a2, make_float2(b.z, b.w), make_float2(acc.z, acc.w));
+  acc = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 // Forward, pass 1: each lenslet's contribution sum_k scale_k Bt (x) Bs fa_k

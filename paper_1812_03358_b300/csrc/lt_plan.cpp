@@ -333,56 +333,66 @@ static void plan_bricks(CameraPlan& c, int grid_nx, int nz, const std::vector<Fo
   c.tma_nb = 4;
 }
 
-// Image box of the box-staged adjoint for camera c: per (cell, chunk of
-// adjoint_chunk() slices, tile of adjoint_tile_x() x adjoint_tile_y()
-// voxels), the target pixels the tile's windows reach, [first window start,
-// last window start + largest window - 1] per axis over the chunk's slices (window
-// starts floor(min(lo, hi)) - 1 of (j -+ 1/2 -+ Q - c0) / c1 at the tile's
-// two ends, widened by 1e-3), the columns rounded to a multiple of 4.  The
-// box is the largest span; cameras whose box exceeds 8192 floats keep the
-// direct adjoint, and so do cameras whose target rows are not a multiple of
-// 4 floats.
+// Image box of the box-staged adjoint for camera c: per (cell, chunk of sc
+// slices, tile of adjoint_tile_x() x adjoint_tile_y() voxels), the target
+// pixels the tile's windows reach, [first window start, last window start +
+// largest window - 1] per axis over the chunk's slices (window starts
+// floor(min(lo, hi)) - 1 of (j -+ 1/2 -+ Q - c0) / c1 at the tile's two
+// ends, widened by 1e-3), the columns rounded to a multiple of 4.  The box
+// is the largest span.  Chunks are adjoint_chunk_max() = 8 slices where that
+// box holds at most 8192 floats, else 4 slices with boxes up to 12288
+// floats (strongly defocused cameras, whose windows span 15 or more pixels
+// per axis: the smaller chunk keeps the stage's tables small, and the
+// kernel single-buffers such stages to keep three CTAs per SM); cameras
+// whose 4-slice box exceeds that keep the direct adjoint, and so do cameras
+// whose target rows are not a multiple of 4 floats.
 static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns, const std::vector<Footprint>& fps,
                              const std::vector<Footprint>& fpt) {
   c.adj_bx = c.adj_by = 0;
-  if (tgt_ns % 4 != 0) return;   // a TMA row stride is a multiple of 16 bytes
-  const int TX = adjoint_tile_x(), TY = adjoint_tile_y(), SC = adjoint_chunk();
+  c.adj_sc = adjoint_chunk_max();
+  if (tgt_ns % 4 != 0 || c.wimax_s > 32 || c.wimax_t > 32) return;   // a TMA row stride is a multiple of 16 bytes
+  const int TX = adjoint_tile_x(), TY = adjoint_tile_y();
   auto start = [](const Footprint& f, int j, double eps) {
     const double lo = (j - 0.5 - (double)f.a.Q - f.C0) / f.C1, hi = (j + 0.5 + (double)f.a.Q - f.C0) / f.C1;
     return (long long)std::floor(std::min(lo, hi) + eps) - 1;
   };
-  long long need_bx = 0, need_by = 0;
-  for (int k = 0; k < c.K; ++k)
-    for (int n0 = 0; n0 < v.nz; n0 += SC) {
-      for (int j0 = 0; j0 < v.nx; j0 += TX) {
-        const int j1 = std::min(j0 + TX, v.nx) - 1;
-        long long lo = LLONG_MAX, hi = LLONG_MIN;
-        for (int n = n0; n < std::min(n0 + SC, v.nz); ++n) {
-          const size_t q = (size_t)k * v.nz + n;
-          for (int j : {j0, j1}) {
-            lo = std::min(lo, start(fps[q], j, -1e-3));
-            hi = std::max(hi, start(fps[q], j, 1e-3) + c.wimax_s - 1);
+  for (int SC = adjoint_chunk_max(); SC >= 4; SC /= 2) {
+    long long need_bx = 0, need_by = 0;
+    for (int k = 0; k < c.K; ++k)
+      for (int n0 = 0; n0 < v.nz; n0 += SC) {
+        for (int j0 = 0; j0 < v.nx; j0 += TX) {
+          const int j1 = std::min(j0 + TX, v.nx) - 1;
+          long long lo = LLONG_MAX, hi = LLONG_MIN;
+          for (int n = n0; n < std::min(n0 + SC, v.nz); ++n) {
+            const size_t q = (size_t)k * v.nz + n;
+            for (int j : {j0, j1}) {
+              lo = std::min(lo, start(fps[q], j, -1e-3));
+              hi = std::max(hi, start(fps[q], j, 1e-3) + c.wimax_s - 1);
+            }
           }
+          need_bx = std::max(need_bx, hi - (lo & ~3LL) + 1);
         }
-        need_bx = std::max(need_bx, hi - (lo & ~3LL) + 1);
-      }
-      for (int j0 = 0; j0 < v.ny; j0 += TY) {
-        const int j1 = std::min(j0 + TY, v.ny) - 1;
-        long long lo = LLONG_MAX, hi = LLONG_MIN;
-        for (int n = n0; n < std::min(n0 + SC, v.nz); ++n) {
-          const size_t q = (size_t)k * v.nz + n;
-          for (int j : {j0, j1}) {
-            lo = std::min(lo, start(fpt[q], j, -1e-3));
-            hi = std::max(hi, start(fpt[q], j, 1e-3) + c.wimax_t - 1);
+        for (int j0 = 0; j0 < v.ny; j0 += TY) {
+          const int j1 = std::min(j0 + TY, v.ny) - 1;
+          long long lo = LLONG_MAX, hi = LLONG_MIN;
+          for (int n = n0; n < std::min(n0 + SC, v.nz); ++n) {
+            const size_t q = (size_t)k * v.nz + n;
+            for (int j : {j0, j1}) {
+              lo = std::min(lo, start(fpt[q], j, -1e-3));
+              hi = std::max(hi, start(fpt[q], j, 1e-3) + c.wimax_t - 1);
+            }
           }
+          need_by = std::max(need_by, hi - lo + 1);
         }
-        need_by = std::max(need_by, hi - lo + 1);
       }
+    const long long bx = (need_bx + 3) / 4 * 4, by = need_by;
+    if (bx >= 4 && by >= 1 && bx <= 256 && by <= 256 && bx * by <= (SC == 8 ? 8192 : 12288)) {
+      c.adj_bx = (int)bx;
+      c.adj_by = (int)by;
+      c.adj_sc = SC;
+      return;
     }
-  const long long bx = (need_bx + 3) / 4 * 4, by = need_by;
-  if (bx < 4 || by < 1 || bx > 256 || by > 256 || bx * by > 8192 || c.wimax_s > 32 || c.wimax_t > 32) return;
-  c.adj_bx = (int)bx;
-  c.adj_by = (int)by;
+  }
 }
 
 // Window tables and box origins of the box-staged adjoint, built on the
@@ -396,7 +406,7 @@ static lt_status plan_adjoint_tables(CameraPlan& c, const lt_volume_desc& v, int
     return LT_OK;
   }
   size_t sb, tb, nox, noy;
-  adjoint_table_sizes(c.K, v.nz, v.nx, v.ny, c.wimax_s, c.wimax_t, &sb, &tb, &nox, &noy);
+  adjoint_table_sizes(c.K, v.nz, v.nx, v.ny, c.wimax_s, c.wimax_t, c.adj_sc, &sb, &tb, &nox, &noy);
   if (sb + tb > kMaxTableBytes) {
     c.adj_bx = c.adj_by = 0;
     return LT_OK;
@@ -412,8 +422,8 @@ static lt_status plan_adjoint_tables(CameraPlan& c, const lt_volume_desc& v, int
   int bad = 0;
   cudaError_t e = cudaMemset(d_bad, 0, sizeof(int));
   if (e == cudaSuccess)
-    e = launch_adjoint_tables(c.d_slice, c.K, v.nz, v.nx, v.ny, c.wimax_s, c.wimax_t, c.adj_bx, c.adj_by, c.d_adj_s,
-                              c.d_adj_t, c.d_adj_ox, c.d_adj_oy, d_bad, 0);
+    e = launch_adjoint_tables(c.d_slice, c.K, v.nz, v.nx, v.ny, c.wimax_s, c.wimax_t, c.adj_bx, c.adj_by, c.adj_sc,
+                              c.d_adj_s, c.d_adj_t, c.d_adj_ox, c.d_adj_oy, d_bad, 0);
   if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(d_bad);
   if (e != cudaSuccess) return cuda_error(e, "adjoint window tables");
@@ -1415,6 +1425,7 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
   st.ray_samples = st.stage1_samples + st.stage2_samples;
   st.forward_brick = (int64_t)c.tma_bx * c.tma_by;
   st.adjoint_box = (int64_t)c.adj_bx * c.adj_by;
+  st.adjoint_chunk = c.adj_sc;
   *out = st;
   return LT_OK;
 }
@@ -1544,7 +1555,7 @@ static lt_status run_adjoint(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       const CameraPlan& c = *cps[i];
       const BeamCam& bc = b.cam[i];
       const long long plane = (long long)bc.ns * bc.nt;
-      ok = c.adj_bx > 0 && (!bc.per_cell || bc.out_fs == plane * bc.K) &&
+      ok = c.adj_bx > 0 && c.adj_sc == cps[0]->adj_sc && (!bc.per_cell || bc.out_fs == plane * bc.K) &&
            tma_encode_planes(&a.map[i], bc.in, bc.ns, bc.nt, b.frames * (bc.per_cell ? bc.K : 1),
                              bc.per_cell ? plane : bc.out_fs, c.adj_bx, c.adj_by);
       a.stab[i] = c.d_adj_s;
@@ -1558,10 +1569,10 @@ static lt_status run_adjoint(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
       a.wqt[i] = c.wimax_t;
       a.tiles_x[i] = (bc.nx + adjoint_tile_x() - 1) / adjoint_tile_x();
       a.tiles_y[i] = (bc.ny + adjoint_tile_y() - 1) / adjoint_tile_y();
-      a.chunks[i] = (bc.nz + adjoint_chunk() - 1) / adjoint_chunk();
+      a.chunks[i] = (bc.nz + c.adj_sc - 1) / c.adj_sc;
     }
     if (ok) {
-      cudaError_t e = launch_beam_adjoint_tma(b, a, x, x_fs, accumulate, st);
+      cudaError_t e = launch_beam_adjoint_tma(b, a, cps[0]->adj_sc, x, x_fs, accumulate, st);
       return e == cudaSuccess ? LT_OK : cuda_error(e, "beam adjoint (TMA boxes)");
     }
   }

@@ -8,7 +8,9 @@ voxel sum; sampled rotated voxels of the first and last frames equal the
 oracle's; a yawed camera's image equals the unrotated camera's image of the
 rotated volume; sampled blocks of the plenoptic camera's array plane (every cell,
 first and last frames) equal the oracle's; a CUDA graph of the autotuned
-plan replays the eager result."""
+plan replays the eager result; the yawed cameras' box-staged adjoint (boxes
+of four slices: their footprints drift too far over eight) equals the direct
+gather adjoint."""
 import numpy as np
 import pytest
 
@@ -140,3 +142,22 @@ def test_graph_replay_of_autotuned_plan(multiview):
     gr.replay()
     torch.cuda.synchronize()
     assert torch.equal(yo, y_eager) and torch.equal(xo, x_eager)
+
+
+def test_yawed_box_adjoint_equals_direct_gather(multiview):
+    vol, cams, plan, x = multiview
+    for c, cam in enumerate(cams):
+        if cam.yaw == 0.0:
+            continue
+        st = plan.stats(c)
+        assert st["adjoint_box"] > 0 and st["adjoint_chunk"] in (4, 8)
+    yf = plan.forward(x)
+    out = {}
+    for variant in (1, 0):
+        lt.lt_plan_set_adjoint_variant(plan.handle, variant)
+        out[variant] = plan.adjoint(yf).double()
+    lt.lt_plan_set_adjoint_variant(plan.handle, 1)
+    a, b = out[1], out[0]
+    assert float((a - b).norm() / b.norm()) < 1e-6
+    assert bool(torch.all((a - b).abs() <= 1e-6 * b.abs().max() + 1e-6 * b.abs()))
+    assert lt.lt_projector_status() == 0
