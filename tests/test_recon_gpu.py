@@ -66,9 +66,11 @@ def test_single_lens_50_iterations_match_oracle():
     assert abs(fit - ref["fits"][-1]) <= TOL * ref["fits"][-1]
 
 
-@pytest.mark.parametrize("psi", [0, 1])
-def test_regularised_weighted_l1_iterations_match_oracle(psi):
-    vol = I.Volume(20, 18, 12, 4.0, 4.0, 5.0)
+# rows of 20 voxels take the four-voxels-per-thread update, rows of 19 the
+# one-voxel-per-thread update; ragged y and z in both
+@pytest.mark.parametrize("psi,nx", [(0, 20), (1, 20), (1, 19)])
+def test_regularised_weighted_l1_iterations_match_oracle(psi, nx):
+    vol = I.Volume(nx, 18, 12, 4.0, 4.0, 5.0)
     cam = I.table_single_lens(40, 0.2, ks=2, kt=2)
     x_true = I.gaussian_blobs(vol, seed=1003)
     ys = measure(vol, [cam], x_true)
