@@ -567,8 +567,10 @@ def run_ours(args):
     if args.no_autotune:
         lt.lt_plan_set_forward_variant(plan.handle, args.forward_variant)
         tuned, tune_ms = args.forward_variant, None
+        adj_tuned, adj_tune_ms = 1, None
     else:
         tuned, tune_ms = plan.autotune()
+        adj_tuned, adj_tune_ms = plan.autotune_adjoint()
     stats = plan.stats(0)
     xt = torch.from_numpy(x_true.reshape(1, -1)).cuda()
     y_clean = plan.forward(xt)
@@ -650,7 +652,7 @@ def run_ours(args):
              "stage2_forward (array->detector)": "stage2_lenslet_forward",
              "stage2_adjoint (detector->array)": "stage2_lenslet_adjoint",
              "beam_adjoint (stage 1^T, array->voxels)":
-             "beam_adjoint_tma" if stats["adjoint_box"] > 0 else "beam_adjoint_batched"}[dom]
+             "beam_adjoint_tma" if stats["adjoint_box"] > 0 and adj_tuned == 1 else "beam_adjoint_batched"}[dom]
     lv = levels[dom]
     mem = lv["memory_level"]
     peak = {"dram": peaks["hbm_GBps"], "l2": peaks["l2_GBps"], "smem": peaks["smem_GBps"]}[mem]
@@ -771,6 +773,7 @@ def run_ours(args):
                        "beta": beta, "l2": "flushed (512 MB write) between timed iterations",
                        "frames_per_rank": 1, "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "forward_variant": tuned, "autotune_ms": tune_ms,
+                       "adjoint_variant": adj_tuned, "adjoint_autotune_ms": adj_tune_ms,
                        "forward_brick": stats["forward_brick"], "adjoint_box": stats["adjoint_box"]},
             "stages_ms": stage_ms,
             "roofline": roofline,

@@ -236,6 +236,18 @@ LT_API lt_status lt_projector_status(int32_t* flags, int32_t clear);
  * order differs).  LT_EINVAL for another value. */
 LT_API lt_status lt_plan_set_adjoint_variant(lt_plan* plan, int32_t variant);
 
+/* Adjoint kernel choice by measurement (no counterpart in the paper): times
+ * the plan's whole adjoint (every camera and frame, stage two and the
+ * transposed rotations included) with variant 1 (box-staged, where a camera
+ * fits it) and variant 0 (direct gather), three timed runs each after a
+ * warm-up, and keeps the faster (lt_plan_set_adjoint_variant).  times_ms
+ * (host array of 2 entries, indexed by variant, may be NULL) receives the
+ * best time of each; *chosen (may be NULL) the variant kept.  Allocates and
+ * frees temporary device buffers and synchronises the stream: call it after
+ * lt_plan_create and before capturing graphs.  Errors: LT_EINVAL (NULL
+ * plan), LT_ENOMEM, LT_ECUDA; on an error the previous choice stays. */
+LT_API lt_status lt_plan_autotune_adjoint(lt_plan* plan, void* stream, double* times_ms, int32_t* chosen);
+
 /* Analytic work counts of one camera for one frame, computed on the host in
  * float64 from the plan's footprints (used for throughput and roofline
  * figures).  A ray-sample is one (beam, slice) pair: a beam is a target pixel

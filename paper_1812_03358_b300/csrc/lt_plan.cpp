@@ -1917,6 +1917,59 @@ extern "C" lt_status lt_plan_autotune(lt_plan* plan, void* stream, double* times
   return e == cudaSuccess ? LT_OK : cuda_error(e, "autotune");
 }
 
+// Times the plan's adjoint (every camera and frame) with each adjoint kernel
+// choice and keeps the faster.
+extern "C" lt_status lt_plan_autotune_adjoint(lt_plan* plan, void* stream, double* times_ms, int32_t* chosen) {
+  clear_error();
+  if (!plan) return set_error(LT_EINVAL, "plan is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nx = (size_t)plan->frames * plan->nvox, ny = (size_t)plan->frames * plan->m_total;
+  float *x = nullptr, *y = nullptr;
+  if (device_alloc((void**)&x, nx * sizeof(float)) != cudaSuccess ||
+      device_alloc((void**)&y, ny * sizeof(float)) != cudaSuccess) {
+    cudaFree(x);
+    return set_error(LT_ENOMEM, "autotune buffers");
+  }
+  cudaMemsetAsync(y, 0, ny * sizeof(float), st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  int best_v = 1;
+  lt_status s = LT_OK;
+  const int saved = plan->adj_variant;
+  for (int v = 1; v >= 0 && s == LT_OK; --v) {
+    plan->adj_variant = v;
+    double tv = 1e30;
+    for (int rep = 0; rep < 4 && s == LT_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      s = plan_adjoint(plan, y, x, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tv = std::min(tv, (double)ms);   // first run warms up
+    }
+    if (times_ms) times_ms[v] = tv;
+    if (tv < best) {
+      best = tv;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (s != LT_OK) {
+    plan->adj_variant = saved;
+    return s;
+  }
+  plan->adj_variant = best_v;
+  if (chosen) *chosen = best_v;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LT_OK : cuda_error(e, "adjoint autotune");
+}
+
 extern "C" lt_status lt_plan_set_forward_variant(lt_plan* plan, int32_t variant) {
   clear_error();
   if (!plan) return set_error(LT_EINVAL, "plan is NULL");

@@ -100,6 +100,7 @@ _SIGS = {
     "lt_plan_set_forward_variant": (c_int32, [c_void_p, c_int32]),
     "lt_projector_status": (c_int32, [POINTER(c_int32), c_int32]),
     "lt_plan_set_adjoint_variant": (c_int32, [c_void_p, c_int32]),
+    "lt_plan_autotune_adjoint": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
     "lt_last_error": (c_char_p, []),
     "lt_peak_smem_read": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
     "lt_peak_l2_read": (c_int32, [c_void_p, c_int64, c_void_p, c_int32, c_int32, c_void_p, POINTER(c_double)]),
@@ -261,6 +262,15 @@ def lt_projector_status(clear: bool = False) -> int:
     f = c_int32()
     _check(lib().lt_projector_status(byref(f), int(clear)))
     return f.value
+
+
+def lt_plan_autotune_adjoint(plan, stream: int = 0):
+    """Times both adjoint kernel choices and keeps the faster; returns
+    (chosen, [direct ms, box-staged ms])."""
+    times = (c_double * 2)()
+    chosen = c_int32(0)
+    _check(lib().lt_plan_autotune_adjoint(plan, stream, times, byref(chosen)))
+    return chosen.value, list(times)
 
 
 def lt_plan_set_adjoint_variant(plan, variant: int) -> None:
@@ -456,6 +466,10 @@ class Plan:
     def autotune(self):
         """Times the forward kernel variants on this plan and keeps the fastest."""
         return lt_plan_autotune(self.handle, _stream())
+
+    def autotune_adjoint(self):
+        """Times the adjoint kernel choices on this plan and keeps the faster."""
+        return lt_plan_autotune_adjoint(self.handle, _stream())
 
     def stats(self, cam):
         return lt_camera_stats_get(self.handle, cam)

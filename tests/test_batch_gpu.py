@@ -1,7 +1,8 @@
 """Batched launches: one persistent forward launch over cameras of uneven
 detector sizes (single-lens, rotated, plenoptic) x frames equals per-camera
 launches; the multi-camera gather adjoint equals the sum of per-camera
-adjoints; every autotuner variant agrees; a CUDA graph of forward + adjoint
+adjoints; every autotuner variant agrees, and the adjoint autotuner keeps
+the faster of the two adjoint kernels; a CUDA graph of forward + adjoint
 replays the eager result."""
 import numpy as np
 import pytest
@@ -77,6 +78,19 @@ def test_every_autotune_variant_agrees(mixed):
         assert np.abs(o - outs[0]).max() <= 1e-6 * np.abs(outs[0]).max()
     with pytest.raises(lt.LtError):
         lt.lt_plan_set_forward_variant(plan.handle, len(times))
+
+
+def test_adjoint_autotune_keeps_the_faster_of_two_equal_operators(mixed):
+    vol, cams, plan, x, y = mixed
+    chosen, times = plan.autotune_adjoint()
+    assert chosen in (0, 1) and all(t > 0 for t in times)
+    assert times[chosen] == min(times)
+    outs = {}
+    for v in (0, 1):
+        lt.lt_plan_set_adjoint_variant(plan.handle, v)
+        outs[v] = host(plan.adjoint(y))
+    lt.lt_plan_set_adjoint_variant(plan.handle, chosen)
+    assert np.abs(outs[1] - outs[0]).max() <= 1e-6 * np.abs(outs[0]).max()
 
 
 def test_graph_capture_replays_forward_and_adjoint(mixed):
