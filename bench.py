@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
-    ap.add_argument("--warm-samples", type=int, default=6000,
-                    help="training volumes for the warm-start time-to-residual measurement (0: skip)")
+    ap.add_argument("--warm-samples", type=int, default=10000,
+                    help="training volumes of the warm-start U-Net (the learned-warm-start configuration's 10k; 0 skips)")
+    ap.add_argument("--warm-eval", type=int, default=16, help="held-out volumes of the time-to-residual comparison")
     ap.add_argument("--no-autotune", action="store_true",
                     help="pin --forward-variant instead of tuning (fixed launch sequence, e.g. for profiling)")
     ap.add_argument("--forward-variant", type=int, default=5,
@@ -370,14 +371,14 @@ def shear_passes(flush, stream, reps=20):
     return out
 
 
-def time_to_residual(plan, n_samples, n_plain=200, n_eval=5):
+def time_to_residual(plan, n_samples, n_plain=200, n_eval=16):
     """Warm start vs plain solver on the bench workload: the U-Net is trained
     here for n_samples volumes made by the projector (seeds 1e6 + i), then both
     arms run on n_eval held-out volumes (seeds 2e6 + j): wall time (CUDA
     events) until the data fit reaches the plain solver's n_plain-iteration
     value, the warm arm including back-projection and U-Net inference (not
     training).  Reported: the median over the held-out volumes of each figure,
-    and every volume's gain."""
+    every volume's gain, and the smallest and largest gain."""
     import statistics
     import time as _t
     from paper_1812_03358_b300 import unet, warmstart
@@ -399,7 +400,8 @@ def time_to_residual(plan, n_samples, n_plain=200, n_eval=5):
             "n_plain": n_plain, "plain_ms": med("plain_ms"), "plain_first_cross_iters": med("plain_first_cross_iters"),
             "warm_ms": med("warm_ms"), "warm_iters": med("warm_iters"), "unet_ms": med("unet_ms"),
             "unet_tflops": med("unet_tflops"), "gain": statistics.median(ok) if ok else None,
-            "gain_per_volume": gains, "volume_error_plain": med("err_plain"),
+            "gain_per_volume": gains, "gain_min": min(ok) if ok else None, "gain_max": max(ok) if ok else None,
+            "volume_error_plain": med("err_plain"),
             "volume_error_warm_x0": med("err_x0"), "train_samples": n_samples, "train_s": round(t_train, 1),
             "beta": "1e-3 * mean(D)", "grad_clip_norm": 1.0, "train_reproducible": True, "held_out_seeds": [2_000_000 + j for j in range(n_eval)],
             "statistic": "median over the held-out volumes"}
@@ -678,7 +680,7 @@ def run_ours(args):
             extra[name] = fn(args.workload_steps, 3, stream)
 
     # --- time-to-residual, warm start vs plain (rank 0 only, outside the timed region) ---
-    ttr = time_to_residual(plan, args.warm_samples) if rank == 0 and args.warm_samples > 0 else None
+    ttr = time_to_residual(plan, args.warm_samples, n_eval=args.warm_eval) if rank == 0 and args.warm_samples > 0 else None
 
     # --- end to end through the public API: pinned host y in, volume and data fit out ---
     # Streaming use of the API: step i + 1's measurements are copied from
