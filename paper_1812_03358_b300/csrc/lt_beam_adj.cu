@@ -402,6 +402,19 @@ int adjoint_tile_x() { return AX; }
 int adjoint_tile_y() { return AY; }
 int adjoint_chunk_max() { return ASC_MAX; }
 
+int adjoint_occupancy(int bx, int by, int wqs, int wqt, int sc) {
+  if (sc != 4 && sc != 8) return 0;
+  AdjStage L{(bx * by + 31) / 32 * 32, s_entry_floats(wqs) * 4, t_entry_floats(wqt) * 4, sc, 2};
+  const int ucols = upad((bx + 31) / 32 * 32);
+  if (2 * L.bytes() + (size_t)AY * ucols * sizeof(float) > kAdjDoubleMax) L.nbuf = 1;
+  const size_t smem = L.nbuf * L.bytes() + (size_t)AY * ucols * sizeof(float);
+  const void* fn = adj_select((bx + 2 * AX - 1) / (2 * AX), sc);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, AX * AY, smem) != cudaSuccess) return 0;
+  return n;
+}
+
 void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, int sc, size_t* s_bytes, size_t* t_bytes,
                          size_t* ox_count, size_t* oy_count) {
   const long long tiles_x = (nx + AX - 1) / AX, tiles_y = (ny + AY - 1) / AY, chunks = (nz + sc - 1) / sc;

@@ -279,6 +279,9 @@ struct AdjBatch {
 int adjoint_tile_x();
 int adjoint_tile_y();
 int adjoint_chunk_max();
+// Resident CTAs per SM of the box-staged adjoint for one camera's box and
+// windows with sc slices per chunk (0 if it cannot run).
+int adjoint_occupancy(int bx, int by, int wqs, int wqt, int sc);
 void adjoint_table_sizes(int K, int nz, int nx, int ny, int wqs, int wqt, int sc, size_t* s_bytes, size_t* t_bytes,
                          size_t* ox_count, size_t* oy_count);
 cudaError_t launch_adjoint_tables(const SliceParam* prm, int K, int nz, int nx, int ny, int wqs, int wqt, int bx,

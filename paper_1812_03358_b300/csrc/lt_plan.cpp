@@ -339,15 +339,18 @@ static void plan_bricks(CameraPlan& c, int grid_nx, int nz, const std::vector<Fo
 // largest window - 1] per axis over the chunk's slices (window starts
 // floor(min(lo, hi)) - 1 of (j -+ 1/2 -+ Q - c0) / c1 at the tile's two
 // ends, widened by 1e-3), the columns rounded to a multiple of 4.  The box
-// is the largest span.  Chunks are adjoint_chunk_max() = 8 slices where that
-// box holds at most 8192 floats, else 4 slices with boxes up to 12288
-// floats (strongly defocused cameras, whose windows span 15 or more pixels
-// per axis: the smaller chunk keeps the stage's tables small, and the
-// kernel single-buffers such stages to keep three CTAs per SM); cameras
-// whose 4-slice box exceeds that keep the direct adjoint, and so do cameras
-// whose target rows are not a multiple of 4 floats.
-static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns, const std::vector<Footprint>& fps,
-                             const std::vector<Footprint>& fpt) {
+// is the largest span.  Chunks are adjoint_chunk_max() = 8 slices (boxes up
+// to 8192 floats) or 4 slices (boxes up to 12288 floats: strongly defocused
+// cameras, whose windows span 15 or more pixels per axis, fit only so, and
+// the kernel single-buffers such stages to keep three CTAs per SM); of the
+// depths that fit, the one whose grid takes fewer whole rounds of resident
+// CTAs (a 4-slice chunk counted as 55 % of an 8-slice one) is kept, so that
+// small workloads split into more CTAs (the bench camera: 1024 8-slice CTAs
+// on 444 resident slots ran 0.085 ms, 2048 4-slice CTAs 0.075 ms).  Cameras
+// that fit neither keep the direct adjoint, and so do cameras whose target
+// rows are not a multiple of 4 floats.
+static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns, int frames,
+                             const std::vector<Footprint>& fps, const std::vector<Footprint>& fpt) {
   c.adj_bx = c.adj_by = 0;
   c.adj_sc = adjoint_chunk_max();
   if (tgt_ns % 4 != 0 || c.wimax_s > 32 || c.wimax_t > 32) return;   // a TMA row stride is a multiple of 16 bytes
@@ -356,6 +359,11 @@ static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns,
     const double lo = (j - 0.5 - (double)f.a.Q - f.C0) / f.C1, hi = (j + 0.5 + (double)f.a.Q - f.C0) / f.C1;
     return (long long)std::floor(std::min(lo, hi) + eps) - 1;
   };
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (long long)((v.nx + TX - 1) / TX) * ((v.ny + TY - 1) / TY) * frames;
+  double best = 0.0;
   for (int SC = adjoint_chunk_max(); SC >= 4; SC /= 2) {
     long long need_bx = 0, need_by = 0;
     for (int k = 0; k < c.K; ++k)
@@ -386,11 +394,19 @@ static void plan_adjoint_box(CameraPlan& c, const lt_volume_desc& v, int tgt_ns,
         }
       }
     const long long bx = (need_bx + 3) / 4 * 4, by = need_by;
-    if (bx >= 4 && by >= 1 && bx <= 256 && by <= 256 && bx * by <= (SC == 8 ? 8192 : 12288)) {
+    if (bx < 4 || by < 1 || bx > 256 || by > 256 || bx * by > (SC == 8 ? 8192 : 12288)) continue;
+    // whole rounds of resident CTAs, in units of a 4-slice chunk's work (a
+    // 4-slice chunk costs about 10 % more per slice: its box is loaded twice
+    // as often)
+    const int occ = adjoint_occupancy((int)bx, (int)by, c.wimax_s, c.wimax_t, SC);
+    if (occ <= 0) continue;
+    const long long units = tiles * ((v.nz + SC - 1) / SC), slots = (long long)occ * std::max(1, sms);
+    const double cost = (double)((units + slots - 1) / slots) * (SC == 8 ? 2.0 : 1.1);
+    if (c.adj_bx == 0 || cost < best) {
+      best = cost;
       c.adj_bx = (int)bx;
       c.adj_by = (int)by;
       c.adj_sc = SC;
-      return;
     }
   }
 }
@@ -483,7 +499,7 @@ static lt_status plan_weight_tables(CameraPlan& c, int nz, int idx) {
 
 // Per (cell, slice) parameters of the slice -> image-plane transport.
 static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_img, int tgt_ns,
-                             int tgt_nt, double tgt_ps, double tgt_pt, double extra_scale, int idx) {
+                             int tgt_nt, double tgt_ps, double tgt_pt, double extra_scale, int frames, int idx) {
   const lt_camera_desc& d = c.desc;
   std::vector<SliceParam> sp((size_t)c.K * v.nz);
   const int tiles_s = (tgt_ns + kBeamTileS - 1) / kBeamTileS;
@@ -544,7 +560,7 @@ static lt_status plan_slices(const lt_volume_desc& v, CameraPlan& c, double d_im
                      "camera %d: a voxel is covered by %d x %d pixel footprints (kernel limit %d); use coarser pixels or finer voxels",
                      idx, c.wimax_s, c.wimax_t, kMaxAdjointWindow);
   plan_bricks(c, v.nx, v.nz, fps, fpt, tiles_s, tiles_t);
-  plan_adjoint_box(c, v, tgt_ns, fps, fpt);
+  plan_adjoint_box(c, v, tgt_ns, frames, fps, fpt);
   for (auto& r : srange)
     if (r.y < 0) r = make_int2(0, 0);
   for (auto& r : trange)
@@ -1148,11 +1164,11 @@ static lt_status plan_camera(const lt_volume_desc& v0, const lt_camera_desc& src
   if (c.K == 0) return set_error(LT_EINVAL, "camera %d: no angular cell inside the aperture", idx);
   c.M = (int64_t)src.det_ns * src.det_nt;
   if (src.kind == LT_CAM_SINGLE)
-    return plan_slices(v, c, src.d_lens_det, src.det_ns, src.det_nt, src.det_ps, src.det_pt, 1.0, idx);
+    return plan_slices(v, c, src.d_lens_det, src.det_ns, src.det_nt, src.det_ps, src.det_pt, 1.0, frames, idx);
   // plenoptic: V^a = (Da_s D0_s / D_mum)(Da_t D0_t / D_mum)
   const double va = (src.arr_ps * d0s / src.d_lens_mla) * (src.arr_pt * d0t / src.d_lens_mla);
   lt_status s = plan_slices(v, c, src.d_lens_mla, src.arr_ns, src.arr_nt, src.arr_ps, src.arr_pt,
-                            1.0 / va, idx);
+                            1.0 / va, frames, idx);
   if (s != LT_OK) return s;
   s = plan_stage_two(c, frames, idx);
   c.desc.arr_mask = nullptr;   // copied into the plan; the caller's array is not kept
@@ -1702,7 +1718,11 @@ lt_status plan_adjoint(lt_plan* p, const float* y, float* x, cudaStream_t st, Su
   CameraPlan* cps[kMaxBatchCams];
   int written = 0;
   for (int i = 0; i <= nc; ++i) {
-    const bool flush = (i == nc && b.n_cams > 0) || b.n_cams == kMaxBatchCams;
+    // a launch takes cameras of one box-staged chunk depth (or all direct):
+    // a camera that differs from the batch's first starts a new launch
+    const bool differs = i < nc && b.n_cams > 0 && !p->cams[i].rotated &&
+                         (p->cams[i].adj_sc != cps[0]->adj_sc || (p->cams[i].adj_bx > 0) != (cps[0]->adj_bx > 0));
+    const bool flush = (i == nc && b.n_cams > 0) || b.n_cams == kMaxBatchCams || differs;
     if (flush) {
       lt_status s = run_adjoint(p, b, cps, x, p->nvox, written ? 1 : 0, st);
       if (s != LT_OK) return s;
