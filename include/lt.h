@@ -274,6 +274,9 @@ typedef struct {
                              * 0 if the camera takes the direct adjoint        */
   int64_t adjoint_chunk;    /* slices per box of the box-staged adjoint (8, or
                              * 4 where an 8-slice box would exceed its cap)    */
+  int64_t forward_band;     /* 1 if the brick-staged forward takes its
+                             * t-contraction in band form (footprints of three
+                             * or more taps), 0 if per pixel row or direct     */
 } lt_camera_stats;
 
 LT_API lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_camera_stats* out);

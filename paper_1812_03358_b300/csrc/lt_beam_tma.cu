@@ -42,9 +42,11 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "lt_async.cuh"
 #include "lt_beam_math.cuh"
+#include "lt_host.h"
 #include "lt_internal.h"
 
 namespace lt {
@@ -58,7 +60,11 @@ constexpr int FTHREADS = (FC + 1) * 32; // + the producer warp
 constexpr int FG = 4;                   // slices per stage fill
 constexpr int FSLOTS = 6;               // stages
 constexpr int FRECS = 4;                // item records
-constexpr int FTS = 34;                 // row stride (floats) of a consumer's s-contracted rows
+// Row stride (floats) of a consumer's s-contracted rows: 34 for the per-row
+// t-contraction (a half-warp's 8-byte loads of rows r then sit 17 r apart in
+// bank pairs), 42 for the band form (row groups and column groups of a
+// half-warp land 5 r + 4 cg apart); rows are reserved at the larger.
+constexpr int FTS_ROW = 34, FTS_BAND = 42, FTS_MAX = 42;
 constexpr int FEMPTY = 16;              // empty tiles zeroed per work ticket
 constexpr int FMAX_BY = 64;             // brick rows the kernel accepts
 constexpr unsigned FULL = 0xffffffffu;
@@ -79,6 +85,19 @@ struct __align__(16) TPart {
   float tw[W][32];   // t-weights x slice scale of each pixel row
   int ty[32];        // first tap row of each pixel row, relative to the brick
 };
+// Band form of a t-part, for cameras whose four consecutive pixel rows keep
+// their taps within FNB brick rows: group g of rows 4g..4g+3 starts at band
+// row base[g]; wl[m][g] holds the weights of the group's four rows at band
+// row base[g] + m (zero off a row's taps).  A consumer lane then takes four
+// pixel rows of eight columns and reads each band row once for the four.
+constexpr int FNB = 4;
+template <int W>
+struct __align__(16) TPartB {
+  float4 wl[FNB][8];
+  int base[8];
+};
+template <int W, bool BAND>
+using TPartOf = typename std::conditional<BAND, TPartB<W>, TPart<W>>::type;
 
 // Item record: what the producer tells the consumers about the next item.
 struct FwdRec {
@@ -222,14 +241,53 @@ __global__ void __launch_bounds__(64) beam_group_origins(int nz, int tiles_s, in
   if (lane == 0) (warp == 0 ? ox : oy)[((long long)k * tiles + tile) * groups + grp] = org;
 }
 
+// Second pass of the band t-parts, block (tile row, group, cell), lane =
+// pixel row: the group origin as in beam_group_origins, then per slice each
+// four-row group's first band row and band weights, from the per-row
+// t-parts of the first pass (tin).  A group whose taps do not fit FNB band
+// rows, or a row whose taps leave the brick, zeroes that slice's entry and
+// is reported in *bad (the planner checks both in FP64).
+template <int W>
+__global__ void __launch_bounds__(32) beam_group_band(int nz, int tiles_t, int by, const TPart<W>* __restrict__ tin,
+                                                      TPartB<W>* __restrict__ tout, int* __restrict__ oy,
+                                                      int* __restrict__ bad) {
+  const int tile = blockIdx.x, grp = blockIdx.y, k = blockIdx.z, lane = threadIdx.x;
+  const long long nzp = padded_slices(nz), groups = nzp / FG;
+  const int n0 = grp * FG, n1 = min(nz, n0 + FG);
+  const long long base = ((long long)k * tiles_t + tile) * nzp;
+  int lo = 0x7fffffff;
+  for (int n = n0; n < n1; ++n) lo = min(lo, tin[base + n].ty[lane]);
+  lo = __reduce_min_sync(FULL, lo);
+  const int g = lane >> 2, r = lane & 3;
+  for (int n = n0; n < n1; ++n) {
+    const int ty = tin[base + n].ty[lane] - lo;
+    int b = min(ty, __shfl_xor_sync(FULL, ty, 1));
+    b = min(b, __shfl_xor_sync(FULL, b, 2));
+    const bool ok = __all_sync(FULL, ty - b + W <= FNB && ty + W - 1 < by);
+    float* wl = reinterpret_cast<float*>(tout[base + n].wl);
+#pragma unroll
+    for (int m = 0; m < FNB; ++m) {
+      const int a = m - (ty - b);
+      float v = 0.0f;
+#pragma unroll
+      for (int aa = 0; aa < W; ++aa)
+        if (aa == a) v = tin[base + n].tw[aa][lane];
+      wl[(m * 8 + g) * 4 + r] = ok ? v : 0.0f;
+    }
+    if (r == 0) tout[base + n].base[g] = ok ? b : 0;
+    if (!ok && lane == 0) atomicOr(bad, 1);
+  }
+  if (lane == 0) oy[((long long)k * tiles_t + tile) * groups + grp] = lo;
+}
+
 // Byte offset of the origin array behind a camera's table parts.
 template <int W>
 __host__ __device__ __forceinline__ size_t s_origin_offset(int K, int nz, int tiles_s) {
   return (size_t)K * tiles_s * padded_slices(nz) * sizeof(SPart<W>);
 }
-template <int W>
+template <int W, bool BAND>
 __host__ __device__ __forceinline__ size_t t_origin_offset(int K, int nz, int tiles_t) {
-  return (size_t)K * tiles_t * padded_slices(nz) * sizeof(TPart<W>);
+  return (size_t)K * tiles_t * padded_slices(nz) * sizeof(TPartOf<W, BAND>);
 }
 
 // Slot header written by the producer: the slices [first, first + count) of
@@ -243,9 +301,9 @@ struct FillHdr {
 // consumers' s-contracted rows (FC x tsz floats), one partial tile (32 x 33
 // floats) the consumers sum into in warp order, FRECS item records and the
 // mbarriers.
-template <int W>
+template <int W, bool BAND>
 struct FwdLayout {
-  static constexpr size_t parts = FG * (sizeof(SPart<W>) + sizeof(TPart<W>));
+  static constexpr size_t parts = FG * (sizeof(SPart<W>) + sizeof(TPartOf<W, BAND>));
   __host__ __device__ static size_t brick_bytes(int plane) { return ((size_t)FG * plane * 4 + 127) / 128 * 128; }
   __host__ __device__ static size_t stage_bytes(int plane) {
     return (brick_bytes(plane) + parts + sizeof(FillHdr) + 127) / 128 * 128;
@@ -305,12 +363,14 @@ __device__ __forceinline__ bool consumer_sync(uint32_t bar, uint32_t& uses, int 
 // last chunk (a per-unit ticket count, reset by that CTA) sums the partials
 // in chunk order and writes the tile, so the result does not depend on which
 // CTA ran what.
-template <int W>
+template <int W, bool BAND>
 __global__ void __launch_bounds__(FTHREADS, 4)
 beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ TmaBatch TB,
                  const int4* __restrict__ items, int n_items, int n_real, int* __restrict__ counter, int plane,
                  int tsz, int chunks, float* __restrict__ scratch, int* __restrict__ unit_count) {
-  using L = FwdLayout<W>;
+  using L = FwdLayout<W, BAND>;
+  using TP = TPartOf<W, BAND>;
+  constexpr int FTS = BAND ? FTS_BAND : FTS_ROW;
   extern __shared__ __align__(128) unsigned char dsm[];
   const size_t stage_bytes = L::stage_bytes(plane);
   float* tws = reinterpret_cast<float*>(dsm + L::tw_off(plane));
@@ -417,7 +477,7 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
       const char* stab = static_cast<const char*>(TB.stab[item.x]);
       const char* ttab = static_cast<const char*>(TB.ttab[item.x]);
       const int* oxa = reinterpret_cast<const int*>(stab + s_origin_offset<W>(C.K, C.nz, C.tiles_s));
-      const int* oya = reinterpret_cast<const int*>(ttab + t_origin_offset<W>(C.K, C.nz, C.tiles_t));
+      const int* oya = reinterpret_cast<const int*>(ttab + t_origin_offset<W, BAND>(C.K, C.nz, C.tiles_t));
       for (int k0 = kb, jb = 0; k0 < ke && !failed; k0 += 32) {
         int len, nlo;
         cell_interval(C, ts, tt, k0 + lane, ke, len, nlo);
@@ -458,8 +518,8 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
                   mbar_expect_tx(bar, tx_bytes);
                   tma_load_3d(dst, map, x0, y0, frame * C.nz + n0, bar);
                   bulk_copy(dst + pb, stab + (sbase * nzp + n0) * sizeof(SPart<W>), FG * (uint32_t)sizeof(SPart<W>), bar);
-                  bulk_copy(dst + pb + FG * (uint32_t)sizeof(SPart<W>), ttab + (tbase * nzp + n0) * sizeof(TPart<W>),
-                            FG * (uint32_t)sizeof(TPart<W>), bar);
+                  bulk_copy(dst + pb + FG * (uint32_t)sizeof(SPart<W>), ttab + (tbase * nzp + n0) * sizeof(TP),
+                            FG * (uint32_t)sizeof(TP), bar);
                 }
               }
               failed = !__all_sync(FULL, ok);
@@ -486,6 +546,10 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
 
   // ------------------------------ consumers -------------------------------
   float* Tw = tws + (size_t)warp * tsz;
+  // every value these rows ever hold is a finite product: band rows past a
+  // camera's brick rows read zeros or an earlier item's rows, times weight 0
+  for (int o = lane; o < tsz; o += 32) Tw[o] = 0.0f;
+  __syncwarp();
   uint32_t r = 0, cuses = 0;
   for (;;) {
     const int rs = (int)(r % FRECS);
@@ -538,11 +602,11 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
       const size_t pb = L::brick_bytes(plane);
       const FillHdr hdr = *reinterpret_cast<const FillHdr*>(stg + pb + L::parts);
       const SPart<W>* Sg = reinterpret_cast<const SPart<W>*>(stg + pb);
-      const TPart<W>* Tg = reinterpret_cast<const TPart<W>*>(stg + pb + FG * sizeof(SPart<W>));
+      const TP* Tg = reinterpret_cast<const TP*>(stg + pb + FG * sizeof(SPart<W>));
       for (int q = hdr.first; q < hdr.first + hdr.count; ++q) {
         const float* brick = reinterpret_cast<const float*>(stg) + q * bx * by;
         const SPart<W>& S = Sg[q];
-        const TPart<W>& T = Tg[q];
+        const TP& T = Tg[q];
         // s: every brick row for this lane's pixel column, two rows per packed FMA
         {
           float2 ws2[W];
@@ -567,8 +631,26 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
           }
         }
         __syncwarp();
-        // t: this lane's pixel row over the tile's 32 columns, two per packed FMA
-        {
+        if constexpr (BAND) {
+          // t, band form: this lane's four pixel rows 4g..4g+3 over columns
+          // 8cg..8cg+7; each of the group's FNB band rows read once
+          const int g = lane >> 2, cg = lane & 3;
+          const int b = T.base[g];
+#pragma unroll
+          for (int m = 0; m < FNB; ++m) {
+            const float4 w = T.wl[m][g];
+            const float2* row = reinterpret_cast<const float2*>(Tw + (b + m) * FTS + 8 * cg);
+            float2 R[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) R[j] = row[j];
+            const float wr[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[rr * 4 + j] = __ffma2_rn(make_float2(wr[rr], wr[rr]), R[j], acc[rr * 4 + j]);
+          }
+        } else {
+          // t: this lane's pixel row over the tile's 32 columns, two per packed FMA
           const int ty = T.ty[lane];
 #pragma unroll
           for (int a = 0; a < W; ++a) {
@@ -600,8 +682,12 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
       if (warp == w) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          red[lane][2 * c] = w == 0 ? acc[c].x : red[lane][2 * c] + acc[c].x;
-          red[lane][2 * c + 1] = w == 0 ? acc[c].y : red[lane][2 * c + 1] + acc[c].y;
+          // accumulator c: pixel row lane, columns 2c, 2c+1 (per-row form), or
+          // row 4g + c / 4, columns 8cg + 2 (c % 4) + {0, 1} (band form)
+          const int row = BAND ? 4 * (lane >> 2) + c / 4 : lane;
+          const int col = BAND ? 8 * (lane & 3) + 2 * (c % 4) : 2 * c;
+          red[row][col] = w == 0 ? acc[c].x : red[row][col] + acc[c].x;
+          red[row][col + 1] = w == 0 ? acc[c].y : red[row][col + 1] + acc[c].y;
         }
       }
       if (!consumer_sync(cbar, cuses, lane)) ok = false;
@@ -667,22 +753,25 @@ beam_forward_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Tm
   }
 }
 
-template <int W>
+template <int W, bool BAND>
 const void* tma_kernel() {
-  return (const void*)beam_forward_tma<W>;
+  return (const void*)beam_forward_tma<W, BAND>;
 }
 
-const void* tma_select(int w) {
+const void* tma_select(int w, bool band) {
   switch (w) {
-    case 2: return tma_kernel<2>();
-    case 3: return tma_kernel<3>();
-    default: return tma_kernel<4>();
+    case 2: return band ? tma_kernel<2, true>() : tma_kernel<2, false>();
+    case 3: return band ? tma_kernel<3, true>() : tma_kernel<3, false>();
+    default: return band ? tma_kernel<4, true>() : tma_kernel<4, false>();
   }
 }
 
-size_t layout_bytes(int w, int plane, int tsz) {
-  return w == 2 ? FwdLayout<2>::bytes(plane, tsz) : w == 3 ? FwdLayout<3>::bytes(plane, tsz)
-                                                            : FwdLayout<4>::bytes(plane, tsz);
+size_t layout_bytes(int w, bool band, int plane, int tsz) {
+  if (band)
+    return w == 2 ? FwdLayout<2, true>::bytes(plane, tsz) : w == 3 ? FwdLayout<3, true>::bytes(plane, tsz)
+                                                                  : FwdLayout<4, true>::bytes(plane, tsz);
+  return w == 2 ? FwdLayout<2, false>::bytes(plane, tsz) : w == 3 ? FwdLayout<3, false>::bytes(plane, tsz)
+                                                                   : FwdLayout<4, false>::bytes(plane, tsz);
 }
 
 // cuTensorMapEncodeTiled from the driver, found once through the runtime.
@@ -736,50 +825,75 @@ bool tma_encode_planes(CUtensorMap* map, const float* x, int nx, int ny, int nz_
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t tma_table_bytes(int w, int K, int nz, int tiles_s, int tiles_t) {
-  const size_t s = w == 2 ? s_origin_offset<2>(K, nz, tiles_s) : w == 3 ? s_origin_offset<3>(K, nz, tiles_s)
-                                                                        : s_origin_offset<4>(K, nz, tiles_s);
-  const size_t t = w == 2 ? t_origin_offset<2>(K, nz, tiles_t) : w == 3 ? t_origin_offset<3>(K, nz, tiles_t)
-                                                                        : t_origin_offset<4>(K, nz, tiles_t);
+template <int W>
+size_t table_bytes_w(bool band, int K, int nz, int tiles_s, int tiles_t) {
   const size_t groups = (size_t)padded_slices(nz) / FG;
-  const size_t so = ((size_t)K * tiles_s * groups * 4 + 127) / 128 * 128;
-  const size_t to = ((size_t)K * tiles_t * groups * 4 + 127) / 128 * 128;
-  return (tiles_s > 0 ? s + so : 0) + (tiles_t > 0 ? t + to : 0);
+  const size_t s = s_origin_offset<W>(K, nz, tiles_s) + ((size_t)K * tiles_s * groups * 4 + 127) / 128 * 128;
+  const size_t t = (band ? t_origin_offset<W, true>(K, nz, tiles_t) : t_origin_offset<W, false>(K, nz, tiles_t)) +
+                   ((size_t)K * tiles_t * groups * 4 + 127) / 128 * 128;
+  return (tiles_s > 0 ? s : 0) + (tiles_t > 0 ? t : 0);
 }
 
-cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int bx,
-                               int by, void* stab, void* ttab, int* bad, cudaStream_t st) {
-  // padding entries (slices past nz in the last group) stay zero
-  cudaError_t e = cudaMemsetAsync(stab, 0, tma_table_bytes(w, K, nz, tiles_s, 0), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ttab, 0, tma_table_bytes(w, K, nz, 0, tiles_t), st);
-  if (e != cudaSuccess) return e;
+size_t tma_table_bytes(int w, bool band, int K, int nz, int tiles_s, int tiles_t) {
+  return w == 2 ? table_bytes_w<2>(band, K, nz, tiles_s, tiles_t)
+                : w == 3 ? table_bytes_w<3>(band, K, nz, tiles_s, tiles_t) : table_bytes_w<4>(band, K, nz, tiles_s, tiles_t);
+}
+
+template <int W>
+cudaError_t beam_tables_w(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, bool band, int bx, int by,
+                          void* stab, void* ttab, int* bad, cudaStream_t st) {
   const int tiles = std::max(tiles_s, tiles_t), groups = padded_slices(nz) / FG;
-#define LT_TABLES(WW)                                                                                          \
-  do {                                                                                                         \
-    beam_weight_tables<WW><<<dim3(tiles, nz, K), 64, 0, st>>>(prm, nz, tiles_s, tiles_t,                       \
-                                                              static_cast<SPart<WW>*>(stab),                  \
-                                                              static_cast<TPart<WW>*>(ttab));                 \
-    beam_group_origins<WW><<<dim3(tiles, groups, K), 64, 0, st>>>(                                             \
-        nz, tiles_s, tiles_t, bx, by, static_cast<SPart<WW>*>(stab), static_cast<TPart<WW>*>(ttab),           \
-        reinterpret_cast<int*>(static_cast<char*>(stab) + s_origin_offset<WW>(K, nz, tiles_s)),              \
-        reinterpret_cast<int*>(static_cast<char*>(ttab) + t_origin_offset<WW>(K, nz, tiles_t)), bad);        \
-  } while (0)
-  if (w == 2) LT_TABLES(2);
-  else if (w == 3) LT_TABLES(3);
-  else LT_TABLES(4);
-#undef LT_TABLES
+  int* ox = reinterpret_cast<int*>(static_cast<char*>(stab) + s_origin_offset<W>(K, nz, tiles_s));
+  // the first pass writes per-row t-parts: into the table itself, or for the
+  // band form into a scratch buffer the second pass reads
+  TPart<W>* trow = static_cast<TPart<W>*>(ttab);
+  if (band) {
+    const size_t rb = t_origin_offset<W, false>(K, nz, tiles_t);
+    cudaError_t e = device_alloc((void**)&trow, rb);
+    if (e == cudaSuccess) e = cudaMemsetAsync(trow, 0, rb, st);
+    if (e != cudaSuccess) {
+      cudaFree(trow);
+      return e;
+    }
+  }
+  beam_weight_tables<W><<<dim3(tiles, nz, K), 64, 0, st>>>(prm, nz, tiles_s, tiles_t, static_cast<SPart<W>*>(stab),
+                                                            trow);
+  beam_group_origins<W><<<dim3(tiles, groups, K), 64, 0, st>>>(
+      nz, tiles_s, band ? 0 : tiles_t, bx, by, static_cast<SPart<W>*>(stab), trow, ox,
+      reinterpret_cast<int*>(static_cast<char*>(ttab) + t_origin_offset<W, false>(K, nz, tiles_t)), bad);
+  if (band) {
+    beam_group_band<W><<<dim3(tiles_t, groups, K), 32, 0, st>>>(
+        nz, tiles_t, by, trow, static_cast<TPartB<W>*>(ttab),
+        reinterpret_cast<int*>(static_cast<char*>(ttab) + t_origin_offset<W, true>(K, nz, tiles_t)), bad);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(trow);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
+}
+
+cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, bool band,
+                               int bx, int by, void* stab, void* ttab, int* bad, cudaStream_t st) {
+  // padding entries (slices past nz in the last group) stay zero
+  cudaError_t e = cudaMemsetAsync(stab, 0, tma_table_bytes(w, band, K, nz, tiles_s, 0), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ttab, 0, tma_table_bytes(w, band, K, nz, 0, tiles_t), st);
+  if (e != cudaSuccess) return e;
+  if (w == 2) return beam_tables_w<2>(prm, K, nz, tiles_s, tiles_t, band, bx, by, stab, ttab, bad, st);
+  if (w == 3) return beam_tables_w<3>(prm, K, nz, tiles_s, tiles_t, band, bx, by, stab, ttab, bad, st);
+  return beam_tables_w<4>(prm, K, nz, tiles_s, tiles_t, band, bx, by, stab, ttab, bad, st);
 }
 
 int tma_forward_group() { return FG; }
 
-int tma_forward_tsz(int max_by) { return max_by * FTS; }
+int tma_forward_tsz(int max_by) { return (max_by + FNB) * FTS_MAX; }
+
+int tma_forward_band_rows() { return FNB; }
 
 int tma_forward_max_by() { return FMAX_BY; }
 
-int tma_forward_occupancy(int w, int plane, int tsz) {
-  const void* fn = tma_select(w);
-  const size_t smem = layout_bytes(w, plane, tsz);
+int tma_forward_occupancy(int w, bool band, int plane, int tsz) {
+  const void* fn = tma_select(w, band);
+  const size_t smem = layout_bytes(w, band, plane, tsz);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb_ctas = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_ctas, fn, FTHREADS, smem) != cudaSuccess) return 0;
@@ -787,14 +901,14 @@ int tma_forward_occupancy(int w, int plane, int tsz) {
 }
 
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int n_real, int* counter, int w, int plane, int tsz, int chunks,
+                                    int n_real, int* counter, int w, bool band, int plane, int tsz, int chunks,
                                     float* scratch, int* unit_count, int ctas, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (w < 2 || w > 4) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  const void* fn = tma_select(w);
-  const size_t smem = layout_bytes(w, plane, tsz);
+  const void* fn = tma_select(w, band);
+  const size_t smem = layout_bytes(w, band, plane, tsz);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (chunks < 1 || (chunks > 1 && (!scratch || !unit_count))) return cudaErrorInvalidValue;

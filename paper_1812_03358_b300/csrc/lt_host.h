@@ -26,9 +26,10 @@ struct NvtxRange {
 constexpr int kMaxForwardWindow = 8;
 constexpr int kFwdClasses[4] = {8, 4, 3, 2};   // the forward kernels' window classes (window_class)
 // forward item groups g: window class kFwdClasses[g / 3]; g % 3 = 0: the
-// brick-staged kernel (tma_nb = 4), 1: unused, 2: the direct kernel
+// brick-staged kernel with band t-parts (tma_nb = 4), 1: with per-row
+// t-parts (tma_nb = 1), 2: the direct kernel
 constexpr int kForwardGroups = 12;
-inline int forward_group_kind(int tma_nb) { return tma_nb == 4 ? 0 : tma_nb == 8 ? 1 : 2; }
+inline int forward_group_kind(int tma_nb) { return tma_nb == 4 ? 0 : tma_nb == 1 ? 1 : 2; }
 constexpr int kMaxAdjointWindow = 32;
 constexpr int kMaxLensletPixels = 16;
 
@@ -66,7 +67,8 @@ struct CameraPlan {
   int2* d_trange = nullptr;        // [K][tiles_t] slice interval per forward tile row
   int wmax_s = 0, wmax_t = 0, wimax_s = 0, wimax_t = 0;
   // brick-staged (TMA) forward: brick box sized at plan time for every
-  // (cell, slice, tile); tma_nb = 4 when the camera runs that kernel, else 0
+  // (cell, slice, tile); tma_nb = 4 (band t-parts) or 1 (per-row t-parts)
+  // when the camera runs that kernel, else 0
   int tma_bx = 0, tma_by = 0, tma_nb = 0;
   int tma_chunks = 1;              // parts each forward item is split into (few tiles: more CTAs per tile)
   int adj_bx = 0, adj_by = 0;      // box-staged adjoint: image box (0: the direct adjoint serves it)

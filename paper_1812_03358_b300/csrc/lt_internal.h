@@ -229,20 +229,23 @@ bool tma_encode_volume(CUtensorMap* map, const float* x, int nx, int ny, int nz_
 // The same for a plane stack whose third-axis stride (floats) is z_stride, box depth bz.
 bool tma_encode_planes(CUtensorMap* map, const float* x, int nx, int ny, int nz_total, long long z_stride, int bx,
                        int by, int bz = 1);
-size_t tma_table_bytes(int w, int K, int nz, int tiles_s, int tiles_t);
-cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, int bx,
-                               int by, void* stab, void* ttab, int* bad, cudaStream_t st);
+size_t tma_table_bytes(int w, bool band, int K, int nz, int tiles_s, int tiles_t);
+cudaError_t launch_beam_tables(const SliceParam* prm, int K, int nz, int tiles_s, int tiles_t, int w, bool band,
+                               int bx, int by, void* stab, void* ttab, int* bad, cudaStream_t st);
 int tma_forward_group();
 int tma_forward_tsz(int max_by);
 int tma_forward_max_by();
-int tma_forward_occupancy(int w, int plane, int tsz);
+// band = the t-parts in band form (four-row groups within
+// tma_forward_band_rows() brick rows), else one row of taps per pixel row
+int tma_forward_band_rows();
+int tma_forward_occupancy(int w, bool band, int plane, int tsz);
 // items: the launch's work items, those of positive cost (the first n_real)
 // before those whose tile no slice reaches.  chunks: the largest
 // tb.chunks[] of the launch; with chunks > 1, scratch holds n_real * F *
 // chunks * 1024 floats and unit_count n_real * F ints, zero between launches.
 cudaError_t launch_beam_forward_tma(const BeamBatch& b, const TmaBatch& tb, const int4* items, int n_items,
-                                    int n_real, int* counter, int w, int plane, int tsz, int chunks, float* scratch,
-                                    int* unit_count, int ctas, cudaStream_t st);
+                                    int n_real, int* counter, int w, bool band, int plane, int tsz, int chunks,
+                                    float* scratch, int* unit_count, int ctas, cudaStream_t st);
 // Device status word of the projector kernels: bit 0 a brick or band that
 // did not fit (its weights were zeroed), bit 1 a TMA wait that gave up.
 // Read (and optionally cleared) synchronously.

@@ -296,8 +296,10 @@ static void free_camera(CameraPlan& c) {
 // multiple of 4) and must hold W taps past the largest.  Cameras whose
 // window class exceeds 4, whose bricks exceed 1024 floats or
 // tma_forward_max_by() rows, or whose grid rows are not a multiple of 4
-// floats keep the direct kernels.  tma_nb = 4 marks a camera that runs the
-// brick-staged kernel.
+// floats keep the direct kernels.  tma_nb marks a camera that runs the
+// brick-staged kernel: 4 with its t-parts in band form (footprints of three
+// or more taps whose groups of four pixel rows keep their taps within
+// tma_forward_band_rows() brick rows), 1 with one row of taps per pixel row.
 static void plan_bricks(CameraPlan& c, int grid_nx, int nz, const std::vector<Footprint>& fps,
                         const std::vector<Footprint>& fpt, int tiles_s, int tiles_t) {
   c.tma_bx = c.tma_by = c.tma_nb = 0;
@@ -309,7 +311,7 @@ static void plan_bricks(CameraPlan& c, int grid_nx, int nz, const std::vector<Fo
     hi = std::max(hi, (long long)std::floor(std::max(a, b) + 1e-3));
   };
   const int G = tma_forward_group();
-  long long need_bx = 0, span_t = 0;
+  long long need_bx = 0, span_t = 0, need_nb = 0;
   for (int k = 0; k < c.K; ++k)
     for (int n0 = 0; n0 < nz; n0 += G) {
       const int n1 = std::min(nz, n0 + G);
@@ -321,8 +323,14 @@ static void plan_bricks(CameraPlan& c, int grid_nx, int nz, const std::vector<Fo
       }
       for (int tt = 0; tt < tiles_t; ++tt) {
         long long lo = LLONG_MAX, hi = LLONG_MIN;
-        for (int n = n0; n < n1; ++n)
+        for (int n = n0; n < n1; ++n) {
           tap_range(fpt[(size_t)k * nz + n], tt * kBeamTileT, tt * kBeamTileT + kBeamTileT - 1, lo, hi);
+          for (int r0 = tt * kBeamTileT; r0 < tt * kBeamTileT + kBeamTileT; r0 += 4) {   // band rows of a 4-row group
+            long long glo = LLONG_MAX, ghi = LLONG_MIN;
+            tap_range(fpt[(size_t)k * nz + n], r0, r0 + 3, glo, ghi);
+            need_nb = std::max(need_nb, ghi - glo + W);
+          }
+        }
         span_t = std::max(span_t, hi - lo);
       }
     }
@@ -330,7 +338,12 @@ static void plan_bricks(CameraPlan& c, int grid_nx, int nz, const std::vector<Fo
   if (bx > 256 || by > tma_forward_max_by() || bx * by > 1024) return;
   c.tma_bx = (int)bx;
   c.tma_by = (int)by;
-  c.tma_nb = 4;
+  // band t-parts pay where footprints take three or more taps (the W per-row
+  // 8-byte loads of a pixel row become four band rows shared by four rows);
+  // at two taps the per-row form issues fewer instructions and is faster
+  // (measured: 0.079 against 0.085 ms on the 128^3 plenoptic camera; the
+  // multi-view step with three-tap cameras 275 -> 247 ms with bands)
+  c.tma_nb = W >= 3 && need_nb <= tma_forward_band_rows() ? 4 : 1;
 }
 
 // Image box of the box-staged adjoint for camera c: per (cell, chunk of sc
@@ -467,12 +480,13 @@ static lt_status plan_weight_tables(CameraPlan& c, int nz, int idx) {
     return LT_OK;
   }
   const int W = window_class(std::max(c.wmax_s, c.wmax_t));
-  const size_t bytes = tma_table_bytes(W, c.K, nz, c.tiles_s, c.tiles_t);
+  const bool band = c.tma_nb == 4;
+  const size_t bytes = tma_table_bytes(W, band, c.K, nz, c.tiles_s, c.tiles_t);
   if (bytes > kMaxTableBytes) {
     c.tma_nb = 0;
     return LT_OK;
   }
-  const size_t s_bytes = tma_table_bytes(W, c.K, nz, c.tiles_s, 0);
+  const size_t s_bytes = tma_table_bytes(W, band, c.K, nz, c.tiles_s, 0);
   int* d_bad = nullptr;
   if (device_alloc(&c.d_stab, s_bytes) != cudaSuccess ||
       device_alloc(&c.d_ttab, bytes - s_bytes) != cudaSuccess ||
@@ -483,8 +497,8 @@ static lt_status plan_weight_tables(CameraPlan& c, int nz, int idx) {
   int bad = 0;
   cudaError_t e = cudaMemset(d_bad, 0, sizeof(int));
   if (e == cudaSuccess)
-    e = launch_beam_tables(c.d_slice, c.K, nz, c.tiles_s, c.tiles_t, W, c.tma_bx, c.tma_by, c.d_stab, c.d_ttab,
-                           d_bad, 0);
+    e = launch_beam_tables(c.d_slice, c.K, nz, c.tiles_s, c.tiles_t, W, band, c.tma_bx, c.tma_by, c.d_stab,
+                           c.d_ttab, d_bad, 0);
   if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(d_bad);
   if (e != cudaSuccess) return cuda_error(e, "forward weight tables");
@@ -1200,7 +1214,8 @@ static lt_status plan_chunks(lt_plan* p) {
     if (g % 3 == 2 || p->class_count[g] == 0) continue;
     int cmax = 1;
     for (auto& c : p->cams)
-      if (c.tma_nb == (4 << (g % 3)) && window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g / 3])
+      if (c.tma_nb != 0 && forward_group_kind(c.tma_nb) == g % 3 &&
+          window_class(std::max(c.wmax_s, c.wmax_t)) == kFwdClasses[g / 3])
         cmax = std::max(cmax, c.tma_chunks);
     if (cmax > 1) {
       const long long units = (long long)p->class_real[g] * p->frames;
@@ -1442,6 +1457,7 @@ extern "C" lt_status lt_camera_stats_get(const lt_plan* plan, int32_t cam, lt_ca
   st.forward_brick = (int64_t)c.tma_bx * c.tma_by;
   st.adjoint_box = (int64_t)c.adj_bx * c.adj_by;
   st.adjoint_chunk = c.adj_sc;
+  st.forward_band = c.tma_nb == 4 ? 1 : 0;
   *out = st;
   return LT_OK;
 }
@@ -1540,9 +1556,10 @@ static lt_status run_forward(lt_plan* p, const BeamBatch& b, CameraPlan* const* 
     }
     if (ok) {
       const int tsz = tma_forward_tsz(max_by);
-      const int occ = tma_forward_occupancy(wclass, brick, tsz);
+      const bool band = staged_nb == 4;
+      const int occ = tma_forward_occupancy(wclass, band, brick, tsz);
       if (occ > 0) {
-        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, n_real, p->d_counter, wclass, brick, tsz,
+        cudaError_t e = launch_beam_forward_tma(b, tb, items, n_items, n_real, p->d_counter, wclass, band, brick, tsz,
                                                 chunks, p->d_chunk_part, p->d_chunk_count, p->sms * occ, st);
         return e == cudaSuccess ? LT_OK : cuda_error(e, "beam forward (TMA bricks)");
       }
@@ -1688,7 +1705,7 @@ lt_status plan_forward(lt_plan* p, const float* x, float* y, cudaStream_t st, Su
   for (int g = 0; g < kForwardGroups; ++g) {   // one persistent launch per window class and kernel present
     if (p->class_count[g] == 0) continue;
     lt_status s = run_forward(p, b, cps, p->d_items + p->class_begin[g], p->class_count[g], p->class_real[g],
-                              kFwdClasses[g / 3], g % 3 == 2 ? 0 : 4 << (g % 3), st);
+                              kFwdClasses[g / 3], g % 3 == 0 ? 4 : g % 3 == 1 ? 1 : 0, st);
     if (s != LT_OK) return s;
   }
   for (int i = 0; i < nc; ++i) {

@@ -51,7 +51,8 @@ class lt_camera_stats(ctypes.Structure):
     _fields_ = [("n_cells", c_int64), ("stage1_samples", c_int64), ("stage2_samples", c_int64),
                 ("ray_samples", c_int64), ("hit_samples", c_int64), ("stage1_nnz", c_int64),
                 ("stage2_nnz", c_int64), ("stage1_tile_voxels", c_int64),
-                ("forward_brick", c_int64), ("adjoint_box", c_int64), ("adjoint_chunk", c_int64)]
+                ("forward_brick", c_int64), ("adjoint_box", c_int64), ("adjoint_chunk", c_int64),
+                ("forward_band", c_int64)]
 
 
 class LtError(RuntimeError):

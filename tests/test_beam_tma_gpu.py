@@ -81,6 +81,28 @@ def test_brick_forward_matches_oracle(case):
     plan.close()
 
 
+def test_both_t_contraction_forms_match_oracle():
+    """Two-tap footprints take the per-row t-contraction, three-tap ones the
+    band form (four pixel rows per lane over shared band rows); both against
+    the oracle elementwise."""
+    forms = set()
+    # coarse voxels: two taps; 0.5 mm voxels 128 mm deep before a 5 um
+    # detector (the multi-view cameras' geometry, small): defocus gives three
+    # taps while four pixel rows still step through two voxel rows
+    for vol, cam in ((I.Volume(24, 20, 10, 3.0, 3.0, 4.0), I.table_single_lens(48, 0.07, ks=2, kt=2)),
+                     (I.Volume(16, 16, 8, 0.5, 0.5, 16.0), I.table_single_lens(64, 0.005, ks=2, kt=2))):
+        plan = lt.Plan(vol, [cam])
+        st = plan.stats(0)
+        assert st["forward_brick"] > 0
+        forms.add(st["forward_band"])
+        x = I.gaussian_blobs(vol, seed=1005)
+        yo = O.single_forward(vol, cam, x).ravel()
+        yg = host(plan.forward(dev(x).reshape(1, -1)))
+        assert rel_l2(yg, yo) < TOL and close_elementwise(yg, yo), st
+        plan.close()
+    assert forms == {0, 1}, forms
+
+
 def test_brick_forward_frames_are_independent():
     vol = I.Volume(20, 16, 12, 4.0, 4.0, 5.0)
     cams = [I.table_single_lens(36, 0.09), I.table_single_lens(28, 0.11, ks=2, kt=2)]
