@@ -442,9 +442,10 @@ beam_adjoint_batched(const __grid_constant__ BeamBatch B, float* __restrict__ x,
 // memory, cp.async already brings the next cell's table entry and pixels into
 // the other half of a double buffer; the descriptors of the next 64 cells sit
 // in a shared-memory ring.  No block barrier anywhere: each warp owns its
-// lenslets' outputs.  Every output is accumulated in the same order as the
-// plain double loop (c, then r; b, then q), so the result does not depend on
-// the blocking.
+// lenslets' outputs.  Every output is accumulated in a fixed order (the
+// plain double loop's, c then r, b then q, except the adjoint's last
+// contraction, which sums even and odd detector columns apart and adds the
+// two), so the result does not depend on the blocking or the schedule.
 // ---------------------------------------------------------------------------
 constexpr int L2_W = kStage2Window;
 static_assert(2 * L2_W <= 64, "one footprint task per thread of the table kernel");
@@ -871,16 +872,16 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
           if (mine) {
             const float* br = bs + cix * nds4;
             const float* ur = ub + r * nds4;
-            float g = 0.0f;
+            // two partial sums (even and odd detector columns), one packed
+            // FMA per pair of columns, added at the end
+            float2 g2 = make_float2(0.0f, 0.0f);
             for (int q = 0; q < nds4; q += 4) {
               const float4 a = *reinterpret_cast<const float4*>(br + q);
               const float4 b = *reinterpret_cast<const float4*>(ur + q);
-              g = fmaf(a.x, b.x, g);
-              g = fmaf(a.y, b.y, g);
-              g = fmaf(a.z, b.z, g);
-              g = fmaf(a.w, b.w, g);
+              g2 = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), g2);
+              g2 = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), g2);
             }
-            v = M[r * s2.row_max + cix] * (d.scale * g);
+            v = M[r * s2.row_max + cix] * (d.scale * (g2.x + g2.y));
           }
           fk[(long long)r * s2.arr_ns + cix] = v;
         }
