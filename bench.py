@@ -463,9 +463,13 @@ def workload_multiview(steps, warmup, stream):
         q = math.floor(cam.yaw / (math.pi / 2) + 0.5)
         n_mid = nzr * ny * (vol.nz if q % 2 else vol.nx)
         pass_bytes = 4 * frames * (vol.n + 2 * n_mid + nzr * ny * nxr)
+        xr_a = plan.rotate_adjoint(c, xc)
+        ra_ms = timed_steps(lambda: plan.rotate_adjoint(c, xc, xr_a), 3, 1, stream)
         rot.append({"camera": c, "yaw_deg": float(np.degrees(cam.yaw)), "grid": [nzr, ny, nxr], "ms": r_ms,
                     "bytes": pass_bytes, "GBps": pass_bytes / (r_ms * 1e-3) / 1e9,
-                    "frac": pass_bytes / (r_ms * 1e-3) / 1e9 / peak})
+                    "frac": pass_bytes / (r_ms * 1e-3) / 1e9 / peak,
+                    "adjoint_ms": ra_ms, "adjoint_GBps": pass_bytes / (ra_ms * 1e-3) / 1e9,
+                    "adjoint_frac": pass_bytes / (ra_ms * 1e-3) / 1e9 / peak})
     out = {"workload": workload_multiview.__doc__.split(";")[0].replace("\n", " ").strip(),
            "frames": frames, "cameras": len(cams), "volume": [vol.nx, vol.ny, vol.nz],
            "ray_samples_per_step": samples, "value": samples / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,

@@ -10,22 +10,23 @@
 //   * the producer takes work items (camera, cell or all cells, tile, frame;
 //     long items split into chunks of about 32 pairs) from a counter, in the
 //     order of a list sorted longest first, posts each item's pair count in a
-//     small record ring, and for every (cell, slice) pair of the item fills the next
-//     stage of an eight-stage ring with one cp.async.bulk.tensor load of the
-//     brick and two bulk copies of the pair's footprint-weight table entries
+//     small record ring, and for every group of four consecutive slices of a
+//     cell fills the next stage of a six-stage ring with one
+//     cp.async.bulk.tensor load of the four bricks (a box four slices deep)
+//     and two bulk copies of the group's footprint-weight table entries
 //     (evaluated once per plan), all completing the stage's mbarrier.  Four
-//     lanes fill four stages at a time, so the mbarrier round trips of four
-//     pairs overlap; the brick origins of 32 consecutive slices come in with
-//     one coalesced load per lane;
-//   * consumer warp w takes pairs w, w + 4, ... of every item.  Per pair it
+//     lanes fill four stages at a time, so the mbarrier round trips overlap;
+//   * consumer warp w takes slices w, w + 4, ... of every group.  Per slice it
 //     s-contracts every brick row into its own rows of shared memory (lane =
-//     pixel column), then t-contracts them (lane = pixel row): each lane owns
-//     one pixel row of the tile, keeps its 32 accumulators in registers and
-//     its W tap rows' weights and first row in registers, so every load of
-//     the t-contraction is a conflict-free 8-byte load of two adjacent
-//     pixel columns at an address known before the pair starts, and every
-//     two multiply-adds are one packed f32x2 FMA (the same two
-//     round-to-nearest FMAs as fmaf);
+//     pixel column), then t-contracts them.  Footprints of two taps use the
+//     per-row form: each lane owns one pixel row of the tile, keeps its 32
+//     accumulators in registers and its tap rows' weights and first row in
+//     registers, so every load is a conflict-free 8-byte load of two
+//     adjacent pixel columns at an address known before the slice starts.
+//     Footprints of three or more taps use the band form: a lane owns four
+//     pixel rows of eight columns and reads each of the four brick rows of
+//     their common band once for all four.  Every two multiply-adds are one
+//     packed f32x2 FMA (the same two round-to-nearest FMAs as fmaf);
 //   * at the end of an item the four consumers' partial tiles are summed in
 //     warp order and written with the mask M (Sec. II-D).
 //

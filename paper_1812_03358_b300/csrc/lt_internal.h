@@ -120,6 +120,7 @@ struct RotParam {
   // tz[c * nwz + q] = E^z(i, i - pz + jz[c] + q) for every output i (zero for
   // q >= wz); row r of E^x (r < nzr) likewise with jx[r], tx[r * wx + q].
   int32_t nwz;             // 8 or 16, >= wz (register window of the z passes)
+  int32_t djz;             // largest jz spread over 32 consecutive columns (c = 32k ...)
   float* tz;
   int32_t* jz;
   float* tx;

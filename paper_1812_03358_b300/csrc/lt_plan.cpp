@@ -1017,6 +1017,16 @@ static lt_status plan_rotation(const lt_volume_desc& v, CameraPlan& c, int frame
   cudaError_t e = launch_shear_tables(r, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) return cuda_error(e, "shear tables");
+  // Window spread of each 32-column tile, from the offsets just tabulated:
+  // it sizes the staged source rows of the transposed z adjoint.
+  std::vector<int32_t> jz(r.nxp);
+  e = cudaMemcpy(jz.data(), r.jz, jz.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "shear table offsets");
+  r.djz = 0;
+  for (int c0 = 0; c0 < r.nxp; c0 += 32) {
+    const auto first = jz.begin() + c0, last = jz.begin() + std::min(c0 + 32, r.nxp);
+    r.djz = std::max(r.djz, *std::max_element(first, last) - *std::min_element(first, last));
+  }
   return LT_OK;
 }
 

@@ -94,8 +94,20 @@ def test_rotate_volume_and_adjoint_match_oracle(yaw):
     """The rotation passes alone (lt_rotate_volume / _adjoint) against the
     oracle's x^r = E^x E^z P x and its transpose, elementwise, on a ragged
     non-cubic grid; the camera grid equals the oracle's rotated grid."""
+    check_rotation(I.Volume(13, 9, 11, 4.0, 4.5, 5.0), yaw)
+
+
+@pytest.mark.parametrize("yaw", [2.1, -1.2])
+def test_quarter_turn_passes_span_several_tiles(yaw):
+    """One and three quarter turns take the transposed z adjoint (tiles of 32
+    columns by 64 sources).  A 70 x 5 x 45 grid gives two column tiles (the
+    second ragged) and two tiles along the sheared axis (the second ragged),
+    checked elementwise against the oracle with the forward passes."""
+    check_rotation(I.Volume(70, 5, 45, 4.0, 4.5, 5.0), yaw)
+
+
+def check_rotation(vol, yaw):
     from oracle import rotation as OR_
-    vol = I.Volume(13, 9, 11, 4.0, 4.5, 5.0)
     cam = I.table_single_lens(28, 0.3, yaw=yaw)
     plan = lt.Plan(vol, [cam])
     x = I.gaussian_blobs(vol, seed=1012).reshape(vol.shape) + 0.1 * I.uniform_random(vol.shape, seed=33)
