@@ -47,10 +47,11 @@ __device__ int g_adjoint_status;
 // Table entry sizes (floats).  S entry (cell, tile column, slice): float
 // sw[wqs][AX] (trimmed windows), int i0[AX] (first target pixel of each
 // voxel column's window), int {cnt, 0, 0, 0}.  T entry (cell, tile row,
-// slice): {float weight x slice scale, int target row}[wqt][AY], int {cnt,
-// 0, 0, 0}.  Both are multiples of 16 bytes (bulk copies).
+// slice): float weight x slice scale [wqt][AY], int first target row [AY]
+// (the entries of a row are consecutive target rows), int {cnt, 0, 0, 0}.
+// Both are multiples of 16 bytes (bulk copies).
 __host__ __device__ __forceinline__ int s_entry_floats(int wqs) { return wqs * AX + AX + 4; }
-__host__ __device__ __forceinline__ int t_entry_floats(int wqt) { return wqt * AY * 2 + 4; }
+__host__ __device__ __forceinline__ int t_entry_floats(int wqt) { return wqt * AY + AY + 4; }
 
 // Column c of a warp's row of U lives at upad(c): one pad word per 32, so
 // that the s-contraction's reads (voxel columns about a magnification apart)
@@ -153,8 +154,10 @@ __global__ void adj_s_table(const SliceParam* __restrict__ prm, int nz, int nx, 
   if (c < 4) ei[AX + c] = c == 0 ? cnt : 0;
 }
 
-// Block (tile row, slice, cell), lane r < AY = voxel row; entries {weight,
-// target row} interleaved so that one 8-byte broadcast load brings both.
+// Block (tile row, slice, cell), lane r < AY = voxel row.  The window of a
+// row is a run of consecutive target rows, so an entry is its weight alone
+// (one 4-byte broadcast load per entry in the kernel) and the row's first
+// target row is stored once.
 __global__ void adj_t_table(const SliceParam* __restrict__ prm, int nz, int ny, int wqt, int tiles_y,
                             float* __restrict__ tab) {
   const int ty = blockIdx.x, n = blockIdx.y, k = blockIdx.z, r = threadIdx.x;
@@ -171,12 +174,11 @@ __global__ void adj_t_table(const SliceParam* __restrict__ prm, int nz, int ny, 
       }
   int cnt, shift;
   trim_window(qf, ql, wqt, cnt, shift);
-  if (r < AY)
-    for (int q = 0; q < wqt; ++q) {
-      e[2 * (q * AY + r)] = __float_as_int(q < cnt ? t_entry(p, jy, ny, i0, shift + q) : 0.0f);
-      e[2 * (q * AY + r) + 1] = i0 + shift + min(q, cnt > 0 ? cnt - 1 : 0);
-    }
-  if (r < 4) e[2 * wqt * AY + r] = r == 0 ? cnt : 0;
+  if (r < AY) {
+    for (int q = 0; q < wqt; ++q) e[q * AY + r] = __float_as_int(q < cnt ? t_entry(p, jy, ny, i0, shift + q) : 0.0f);
+    e[wqt * AY + r] = i0 + shift;
+  }
+  if (r < 4) e[wqt * AY + AY + r] = r == 0 ? cnt : 0;
 }
 
 // axis 0: columns (x, s), axis 1: rows (y, t).  Thread = tile; the union of
@@ -257,7 +259,7 @@ __device__ __forceinline__ void adj_issue(const BeamCam& C, const AdjBatch& A, c
 }
 
 template <int CI, int SC>
-__global__ void __launch_bounds__(AX * AY, 3)
+__global__ void __launch_bounds__(AX * AY, SC == 4 ? 4 : 3)
 beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ AdjBatch A, float* __restrict__ x,
                  long long x_fs, int accumulate, int tiles_x, AdjStage L, int ucols) {
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -322,16 +324,18 @@ beam_adjoint_tma(const __grid_constant__ BeamBatch B, const __grid_constant__ Ad
     for (int s = 0; s < SC; ++s) {
       if (s >= n_cnt) break;
       // t: this warp's voxel row over every box column, two columns per
-      // packed FMA; each window entry's {weight, row} in one broadcast load
-      const int* T = reinterpret_cast<const int*>(T0 + s * t_entry_floats(wqt));
-      const int cnt_t = T[2 * wqt * AY];
+      // packed FMA; the window's rows are consecutive box rows, each entry
+      // one 4-byte broadcast load of its weight
+      const float* Tw = T0 + s * t_entry_floats(wqt);
+      const int* Ti = reinterpret_cast<const int*>(Tw + wqt * AY);
+      const int cnt_t = Ti[AY];
+      const float2* row = reinterpret_cast<const float2*>(box + (Ti[warp] - y0) * bx) + lane;   // bx is even
       float2 v[CI];
 #pragma unroll
       for (int m = 0; m < CI; ++m) v[m] = make_float2(0.0f, 0.0f);
-      for (int q = 0; q < cnt_t; ++q) {
-        const int2 e = reinterpret_cast<const int2*>(T)[q * AY + warp];
-        const float2 w2 = make_float2(__int_as_float(e.x), __int_as_float(e.x));
-        const float2* row = reinterpret_cast<const float2*>(box + (e.y - y0) * bx) + lane;
+      for (int q = 0; q < cnt_t; ++q, row += bx >> 1) {
+        const float w = Tw[q * AY + warp];
+        const float2 w2 = make_float2(w, w);
 #pragma unroll
         for (int m = 0; m < CI; ++m)
           if (2 * (lane + AX * m) < bx) v[m] = __ffma2_rn(w2, row[AX * m], v[m]);

@@ -10,7 +10,9 @@ benchmark.  Ops: beam_forward / beam_adjoint (stage one and its adjoint),
 stage2_forward / stage2_adjoint (microlenses), forward / adjoint (the whole
 camera), recon_step (one Table V iteration), multiview_step (one Table V
 iteration of the batched multi-view workload: four yawed 2048^2 cameras and a
-200 x 200-lenslet plenoptic camera around 256^3 voxels, 16 frames), conv (one
+200 x 200-lenslet plenoptic camera around 256^3 voxels, 16 frames, or
+--frames), multiview_forward / multiview_adjoint (that workload's whole
+projector or back-projector), conv (one
 U-Net convolution
 layer: input channels, output channels, grid size; tcgen05 kernel where the
 shape allows it).  Each op runs once to warm up, then `reps` times, each
@@ -52,15 +54,19 @@ def _plenoptic_ops(variant):
     return ops, (plan, rec)
 
 
-def _multiview_op():
+def _multiview_op(op, frames):
     import torch
     from paper_1812_03358_b300 import inputs as I
     from paper_1812_03358_b300 import lt
-    frames = 16
     vol, cams = I.config_multiview()
     plan = lt.Plan(vol, cams, frames)
     x = torch.stack([I.plume_field_torch(vol, seed=3100, drift_voxels=float(f)) for f in range(frames)]).contiguous()
     y = I.poisson_images_torch(plan.forward(x), 1e4, seed=3200)
+    if op == "multiview_forward":
+        return (lambda: plan.forward(x, y)), (plan, x, y)
+    if op == "multiview_adjoint":
+        xa = plan.new_x()
+        return (lambda: plan.adjoint(y, xa)), (plan, xa, y)
     rec = lt.Recon(plan, y, beta=1e-3)
     del x
     return (lambda: rec.iterate(1)), (plan, rec, y)
@@ -83,6 +89,7 @@ def main(argv=None):
     ap.add_argument("--op", default="beam_forward")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--variant", type=int, default=None, help="forward kernel variant (default: the plan's)")
+    ap.add_argument("--frames", type=int, default=16, help="multi-view ops: frames of the workload")
     ap.add_argument("--conv", default="16,16,128", help="conv: input channels, output channels, grid size")
     ap.add_argument("--conv-path", type=int, default=0,
                     help="conv kernel: 0 automatic, 1 warp MMA, 2 tcgen05, 3 tcgen05 chunked, 4 tcgen05 z-walking")
@@ -93,8 +100,8 @@ def main(argv=None):
     if a.op == "conv":
         ci, co, n = (int(v) for v in a.conv.split(","))
         fn, keep = _conv_op(ci, co, n, a.conv_path)
-    elif a.op == "multiview_step":
-        fn, keep = _multiview_op()
+    elif a.op.startswith("multiview_"):
+        fn, keep = _multiview_op(a.op, a.frames)
     else:
         ops, keep = _plenoptic_ops(a.variant)
         fn = ops[a.op]
