@@ -59,6 +59,9 @@ static_assert(sizeof(S2Desc) == 32, "S2Desc is 32 bytes");
 
 // Threads per CTA of the stage-two kernels (one lenslet walk per warp).
 constexpr int kStage2Threads = 256;
+// Each warp's item descriptors come kS2Chunk at a time into a ring of
+// kS2Ring in its shared memory (S2Desc = 8 floats each).
+constexpr int kS2Chunk = 16, kS2Ring = 2 * kS2Chunk;
 
 struct StageTwo {
   const LensletParam* lens;   // [K][mla_nt*mla_ns]

@@ -526,15 +526,16 @@ __device__ __forceinline__ int div_small(int o, int d) { return __float2int_rz((
 // The warp's cells: item j is cell j % K of lenslet-frame unit
 // w0 + (j / K) * nw (unit = frame * N_mu + mu, fewer than 2^31).  The walk
 // keeps (unit, cell) of the next item to issue and of the item being
-// contracted as counters; descriptors come 32 at a time into a ring of 64 in
-// shared memory (slot j % 64), one per lane.
+// contracted as counters; descriptors come kS2Chunk at a time into a ring of
+// kS2Ring in shared memory (slot j % kS2Ring), one per lane of the first
+// kS2Chunk: while chunk c is contracted, chunk c + 1 is already in place.
 struct S2Walk {
   int w0, nw, n_items, K, nmu;
   __device__ __forceinline__ void load_chunk(const S2Desc* desc, S2Desc* ring, int chunk, int lane) const {
-    const int j = chunk * 32 + lane;
-    if (j < n_items) {
+    const int j = chunk * kS2Chunk + lane;
+    if (lane < kS2Chunk && j < n_items) {
       const int u = w0 + (j / K) * nw;
-      ring[j & 63] = desc[(long long)(u % nmu) * K + j % K];
+      ring[j & (kS2Ring - 1)] = desc[(long long)(u % nmu) * K + j % K];
     }
   }
 };
@@ -591,8 +592,8 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int TB = s2.tab_max, FB = s2.pix_max;
   float* base = s2_smem + (long long)warp * s2.fwd_warp_floats;
-  S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [64]
-  float* tab = base + 64 * 8;                          // [2][TB]
+  S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [kS2Ring]
+  float* tab = base + kS2Ring * 8;                     // [2][TB]
   float* fv = tab + 2 * TB;                            // [2][FB]: block rows of row_max
   uint32_t* own = reinterpret_cast<uint32_t*>(fv + 2 * FB);   // [2][8]: row intervals (or ownership bits)
   float* wb = reinterpret_cast<float*>(own + 16);      // [w_max]: W[r][q], rows of nds4
@@ -631,13 +632,13 @@ stage2_lenslet_forward(const float* __restrict__ fa, StageTwo s2, long long fa_f
   issue(nxt, ring[0], 0);
   nxt.next(wk);
   for (int j = 0; j < wk.n_items; ++j) {
-    if ((j & 31) == 0 && j > 0) {   // chunk j / 32 starts: bring in chunk j / 32 + 1
-      wk.load_chunk(s2.desc, ring, (j >> 5) + 1, lane);
+    if (j % kS2Chunk == 0 && j > 0) {   // chunk c = j / kS2Chunk starts: bring in chunk c + 1
+      wk.load_chunk(s2.desc, ring, j / kS2Chunk + 1, lane);
       __syncwarp();
     }
-    const S2Desc d = ring[j & 63];
+    const S2Desc d = ring[j & (kS2Ring - 1)];
     if (j + 1 < wk.n_items) {
-      issue(nxt, ring[(j + 1) & 63], (j + 1) & 1);
+      issue(nxt, ring[(j + 1) & (kS2Ring - 1)], (j + 1) & 1);
       nxt.next(wk);
     } else {
       cp_async_commit();
@@ -755,16 +756,15 @@ stage2_gather(const float* __restrict__ zbuf, float* __restrict__ y, StageTwo s2
 // their unowned pixels; a cell outside the subset leaves its plane unwritten.
 __global__ void __launch_bounds__(kStage2Threads)
 stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, StageTwo s2, long long y_fs,
-                       long long fa_fs, int frames, int aligned) {
+                       long long fa_fs, int frames) {
   extern __shared__ __align__(16) float s2_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int TB = s2.tab_max, FB = s2.pix_max, YB = s2.y_max;
+  const int TB = s2.tab_max, YB = s2.y_max;
   float* base = s2_smem + (long long)warp * s2.adj_warp_floats;
-  S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [64]
-  float* tab = base + 64 * 8;                          // [2][TB]
+  S2Desc* ring = reinterpret_cast<S2Desc*>(base);     // [kS2Ring]
+  float* tab = base + kS2Ring * 8;                     // [2][TB]
   float* yw = tab + 2 * TB;                            // [2][YB]: the cell's window of y, rows of nds4 (zero past nds)
-  float* mv = yw + 2 * YB;                             // [2][FB]: M on the block, rows of row_max
-  uint32_t* bits = reinterpret_cast<uint32_t*>(mv + 2 * FB);  // [2][16]: row intervals, or own (0..7), clear (8..15)
+  uint32_t* bits = reinterpret_cast<uint32_t*>(yw + 2 * YB);  // [2][16]: row intervals, or own (0..7), clear (8..15)
   float* ub = reinterpret_cast<float*>(bits + 32);     // [w_max]: U[r][q], rows of nds4
   S2Walk wk;
   wk.K = s2.K;
@@ -797,8 +797,6 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
             const int bb = div_small(o, nds4 - nds);
             yb[bb * nds4 + nds + (o - bb * (nds4 - nds))] = 0.0f;
           }
-        s2_copy_rows(mv + buf * FB, s2.row_max, s2.mask + d.px0, d_nr(dm), d_nc(dm), s2.arr_ns,
-                     aligned ? (d.px0 & 3) : 0, aligned, lane);
       }
       if (s2.iv_ok) {
         if (lane < 2) cp_async16(smem_addr(bits + buf * 16 + 4 * lane), s2.ivals + (long long)d.mu * 8 + 4 * lane, true);
@@ -812,13 +810,13 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
   issue(nxt, ring[0], 0);
   nxt.next(wk);
   for (int j = 0; j < wk.n_items; ++j) {
-    if ((j & 31) == 0 && j > 0) {
-      wk.load_chunk(s2.desc, ring, (j >> 5) + 1, lane);
+    if (j % kS2Chunk == 0 && j > 0) {   // chunk c = j / kS2Chunk starts: bring in chunk c + 1
+      wk.load_chunk(s2.desc, ring, j / kS2Chunk + 1, lane);
       __syncwarp();
     }
-    const S2Desc d = ring[j & 63];
+    const S2Desc d = ring[j & (kS2Ring - 1)];
     if (j + 1 < wk.n_items) {
-      issue(nxt, ring[(j + 1) & 63], (j + 1) & 1);
+      issue(nxt, ring[(j + 1) & (kS2Ring - 1)], (j + 1) & 1);
       nxt.next(wk);
     } else {
       cp_async_commit();
@@ -863,13 +861,14 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
           *reinterpret_cast<float4*>(ub + r * nds4 + q) = u;
         }
         __syncwarp();
-        const float* M = mv + buf * FB + (aligned ? (d.px0 & 3) : 0);
+        const float* M = s2.mask + d.px0;   // read once per pixel, from L2: no shared copy
         for (int o = lane; o < nr * nc; o += 32) {
           const int r = div_small(o, nc), cix = o - r * nc;
           const bool mine = mine_of(r, cix, o);
           if (!mine && !clear_of(o)) continue;
           float v = 0.0f;
           if (mine) {
+            const float m = __ldg(M + (long long)r * s2.arr_ns + cix);   // in flight during the dot product
             const float* br = bs + cix * nds4;
             const float* ur = ub + r * nds4;
             // two partial sums (even and odd detector columns), one packed
@@ -881,7 +880,7 @@ stage2_lenslet_adjoint(const float* __restrict__ y, float* __restrict__ fa, Stag
               g2 = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), g2);
               g2 = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), g2);
             }
-            v = M[r * s2.row_max + cix] * (d.scale * (g2.x + g2.y));
+            v = m * (d.scale * (g2.x + g2.y));
           }
           fk[(long long)r * s2.arr_ns + cix] = v;
         }
@@ -1024,9 +1023,8 @@ cudaError_t launch_stage2_adjoint(const float* y, float* fa, StageTwo s2, int fr
       cudaMemsetAsync(fa + (long long)f * fa_frame_stride, 0,
                       (size_t)s2.K * s2.arr_ns * s2.arr_nt * sizeof(float), st);
   }
-  const int aligned = (reinterpret_cast<uintptr_t>(s2.mask) & 15) == 0 && s2.arr_ns % 4 == 0;
   stage2_lenslet_adjoint<<<stage2_ctas(s2, s2.adj_per_sm, frames), kStage2Threads, stage2_smem_bytes(s2, true), st>>>(
-      y, fa, s2, y_frame_stride, fa_frame_stride, frames, aligned);
+      y, fa, s2, y_frame_stride, fa_frame_stride, frames);
   return cudaGetLastError();
 }
 
