@@ -927,7 +927,7 @@ static lt_status plan_stage_two(CameraPlan& c, int frames, int idx) {
   s2.w_max = up4(w_max);
   s2.z_max = up4(z_max);
   s2.y_max = up4(y_max);
-  // per warp: a ring of 64 descriptors (8 floats each), then the buffers
+  // per warp: a ring of kS2Ring descriptors (8 floats each), then the buffers
   s2.fwd_warp_floats = kS2Ring * 8 + 2 * s2.tab_max + 2 * s2.pix_max + 16 + s2.w_max + s2.z_max;
   s2.adj_warp_floats = kS2Ring * 8 + 2 * s2.tab_max + 2 * s2.y_max + 32 + s2.w_max;
   if ((s = upload(desc, &c.d_s2desc, "stage-two descriptors")) != LT_OK) return s;

@@ -513,8 +513,10 @@ static lt_status recon_step(lt_recon* R, int sel, int sub, cudaStream_t st) {
   const float sbeta = (float)(R->prm.reg_scale * R->prm.beta);
   if (v.nx % 4 == 0) {   // rows of 16-byte multiples (the state buffers are cudaMalloc'ed, 256-byte aligned)
     const long long cols = (long long)((v.nx + U4_X - 1) / U4_X) * ((v.ny + U4_TY - 1) / U4_TY) * R->F;
+    // deep columns (fewer halo planes per slice) unless that leaves SMs
+    // without a CTA: at 128^3, 8 slices per CTA (256 CTAs) beat 2 (1024 CTAs)
     int zb = U4_ZB;
-    while (zb > 1 && cols * ((v.nz + zb - 1) / zb) < 4LL * P->sms) zb /= 2;
+    while (zb > 1 && cols * ((v.nz + zb - 1) / zb) < (long long)P->sms) zb /= 2;
     const dim3 g4((v.nx + U4_X - 1) / U4_X, (v.ny + U4_TY - 1) / U4_TY, ((v.nz + zb - 1) / zb) * R->F);
     update_kernel4<<<g4, dim3(U4_TX, U4_TY), 0, st>>>(R->x, z, R->z[1 - sel], R->g, R->D, v.nx, v.ny, v.nz, zb,
                                                       R->N, beta, (float)R->prm.nu, R->prm.psi, inv_delta, sbeta,
