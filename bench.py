@@ -688,10 +688,10 @@ def run_ours(args):
 
     # --- end to end through the public API: pinned host y in, volume and data fit out ---
     # Streaming use of the API: step i + 1's measurements are copied from
-    # pinned host memory on a copy stream (double buffer) while step i
+    # pinned host memory on one copy stream (double buffer) while step i
     # iterates; after step i the reconstructed volume is copied into a device
     # staging buffer (lt_recon_get, no synchronisation) and from there into
-    # pinned host memory on the copy stream, and the data fit and gains come
+    # pinned host memory on another, and the data fit and gains come
     # back asynchronously into pinned memory; the host reads step i's fit
     # and volume one step later.  Every step's copy in and result reads
     # happen inside the timed region.
@@ -701,7 +701,9 @@ def run_ours(args):
     x_stage = [torch.empty(nfr, plan.nvox, dtype=torch.float32, device="cuda") for _ in range(2)]
     x_host = [torch.empty(nfr, plan.nvox, dtype=torch.float32).pin_memory() for _ in range(2)]
     res = [torch.empty(nfr * (ncam + 1), dtype=torch.float64).pin_memory() for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
+    # one stream per direction, so that step i + 1's measurements come in
+    # while step i - 1's volume goes out (the host link is full duplex)
+    h2d_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
     comp = torch.cuda.current_stream()
     h2d_done = [torch.cuda.Event() for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
@@ -711,19 +713,19 @@ def run_ours(args):
 
     def e2e_run(n):
         fits, vol_sums = [], []
-        with torch.cuda.stream(copy_stream):
+        with torch.cuda.stream(h2d_stream):
             y_stage[0].copy_(y_pin, non_blocking=True)
-            h2d_done[0].record(copy_stream)
+            h2d_done[0].record(h2d_stream)
         for i in range(n):
             cur, nxt = i % 2, (i + 1) % 2
             comp.wait_event(h2d_done[cur])
             rec.set_data(y_stage[cur])
             consumed[cur].record(comp)
             if i + 1 < n:
-                with torch.cuda.stream(copy_stream):
-                    copy_stream.wait_event(consumed[nxt])   # its last reader was step i - 1
+                with torch.cuda.stream(h2d_stream):
+                    h2d_stream.wait_event(consumed[nxt])   # its last reader was step i - 1
                     y_stage[nxt].copy_(y_pin, non_blocking=True)
-                    h2d_done[nxt].record(copy_stream)
+                    h2d_done[nxt].record(h2d_stream)
             rec.iterate(1)
             if i >= 2:
                 comp.wait_event(x_home[cur])               # step i - 2's volume has left x_stage[cur]
@@ -731,10 +733,10 @@ def run_ours(args):
             x_staged[cur].record(comp)
             rec.get_async(res[cur])
             step_done[cur].record(comp)
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(x_staged[cur])
+            with torch.cuda.stream(d2h_stream):
+                d2h_stream.wait_event(x_staged[cur])
                 x_host[cur].copy_(x_stage[cur], non_blocking=True)
-                x_home[cur].record(copy_stream)
+                x_home[cur].record(d2h_stream)
             if i >= 1:
                 step_done[nxt].synchronize()               # step i - 1's results are on the host
                 x_home[nxt].synchronize()
@@ -759,10 +761,10 @@ def run_ours(args):
            "h2d_bytes_per_step": int(y_pin.numel() * 4),
            "d2h_bytes_per_step": int(8 * nfr * (ncam + 1) + 4 * nfr * plan.nvox),
            "steps": args.e2e_steps,
-           "path": "pinned host y -> device copy (copy stream, double buffered, overlapping the previous step), "
+           "path": "pinned host y -> device copy (its own stream, double buffered, overlapping the previous step), "
                    "lt_recon_set_data, lt_recon_iterate(1), lt_recon_get(x) into a device staging buffer, "
-                   "volume -> pinned host memory on the copy stream, lt_recon_get_async(data fit, gains) into "
-                   "pinned memory; both read on the host one step later"}
+                   "volume -> pinned host memory on a second copy stream (the two directions overlap), "
+                   "lt_recon_get_async(data fit, gains) into pinned memory; both read on the host one step later"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
