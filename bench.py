@@ -687,65 +687,75 @@ def run_ours(args):
     ttr = time_to_residual(plan, args.warm_samples, n_eval=args.warm_eval) if rank == 0 and args.warm_samples > 0 else None
 
     # --- end to end through the public API: pinned host y in, volume and data fit out ---
-    # Streaming use of the API: step i + 1's measurements are copied from
-    # pinned host memory on one copy stream (double buffer) while step i
-    # iterates; after step i the reconstructed volume is copied into a device
-    # staging buffer (lt_recon_get, no synchronisation) and from there into
-    # pinned host memory on another, and the data fit and gains come
-    # back asynchronously into pinned memory; the host reads step i's fit
-    # and volume one step later.  Every step's copy in and result reads
-    # happen inside the timed region.
+    # Streaming use of the API, NB steps in flight: step i + NB - 1's
+    # measurements are copied from pinned host memory on one copy stream
+    # while step i iterates (a 4 MB host-to-device copy takes about 0.35 ms
+    # on its own, more than one step); after step i the reconstructed volume
+    # is copied into a device staging buffer (lt_recon_get, no
+    # synchronisation) and from there into pinned host memory on another
+    # stream, and the data fit and gains come back asynchronously into
+    # pinned memory; the host reads step i's fit and volume NB - 1 steps
+    # later.  Every step's copy in and result reads happen inside the timed
+    # region.
+    NB = 3
     y_pin = torch.from_numpy(y_host.reshape(1, -1)).pin_memory()
     nfr, ncam = plan.frames, len(plan.cams)
-    y_stage = [torch.empty_like(y_dev) for _ in range(2)]
-    x_stage = [torch.empty(nfr, plan.nvox, dtype=torch.float32, device="cuda") for _ in range(2)]
-    x_host = [torch.empty(nfr, plan.nvox, dtype=torch.float32).pin_memory() for _ in range(2)]
-    res = [torch.empty(nfr * (ncam + 1), dtype=torch.float64).pin_memory() for _ in range(2)]
-    # one stream per direction, so that step i + 1's measurements come in
-    # while step i - 1's volume goes out (the host link is full duplex)
+    y_stage = [torch.empty_like(y_dev) for _ in range(NB)]
+    x_stage = [torch.empty(nfr, plan.nvox, dtype=torch.float32, device="cuda") for _ in range(NB)]
+    x_host = [torch.empty(nfr, plan.nvox, dtype=torch.float32).pin_memory() for _ in range(NB)]
+    res = [torch.empty(nfr * (ncam + 1), dtype=torch.float64).pin_memory() for _ in range(NB)]
+    # one stream per direction, so that measurements come in while volumes
+    # go out (the host link is full duplex)
     h2d_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
     comp = torch.cuda.current_stream()
-    h2d_done = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
-    step_done = [torch.cuda.Event() for _ in range(2)]
-    x_staged = [torch.cuda.Event() for _ in range(2)]
-    x_home = [torch.cuda.Event() for _ in range(2)]
+    h2d_done = [torch.cuda.Event() for _ in range(NB)]
+    consumed = [torch.cuda.Event() for _ in range(NB)]
+    step_done = [torch.cuda.Event() for _ in range(NB)]
+    x_staged = [torch.cuda.Event() for _ in range(NB)]
+    x_home = [torch.cuda.Event() for _ in range(NB)]
 
     def e2e_run(n):
         fits, vol_sums = [], []
-        with torch.cuda.stream(h2d_stream):
-            y_stage[0].copy_(y_pin, non_blocking=True)
-            h2d_done[0].record(h2d_stream)
+
+        def fetch(j):   # step j's measurements into y_stage[j % NB]
+            b = j % NB
+            with torch.cuda.stream(h2d_stream):
+                if j >= NB:
+                    h2d_stream.wait_event(consumed[b])   # its last reader was step j - NB
+                y_stage[b].copy_(y_pin, non_blocking=True)
+                h2d_done[b].record(h2d_stream)
+
+        def collect(j):   # step j's results, on the host
+            b = j % NB
+            step_done[b].synchronize()
+            x_home[b].synchronize()
+            fits.append(float(res[b][0]))
+            vol_sums.append(float(x_host[b][0, :: 4096].sum()))
+
+        for j in range(min(NB - 1, n)):
+            fetch(j)
         for i in range(n):
-            cur, nxt = i % 2, (i + 1) % 2
-            comp.wait_event(h2d_done[cur])
-            rec.set_data(y_stage[cur])
-            consumed[cur].record(comp)
-            if i + 1 < n:
-                with torch.cuda.stream(h2d_stream):
-                    h2d_stream.wait_event(consumed[nxt])   # its last reader was step i - 1
-                    y_stage[nxt].copy_(y_pin, non_blocking=True)
-                    h2d_done[nxt].record(h2d_stream)
+            b = i % NB
+            comp.wait_event(h2d_done[b])
+            rec.set_data(y_stage[b])
+            consumed[b].record(comp)
+            if i + NB - 1 < n:
+                fetch(i + NB - 1)
             rec.iterate(1)
-            if i >= 2:
-                comp.wait_event(x_home[cur])               # step i - 2's volume has left x_stage[cur]
-            rec.copy_x(x_stage[cur])
-            x_staged[cur].record(comp)
-            rec.get_async(res[cur])
-            step_done[cur].record(comp)
+            if i >= NB:
+                comp.wait_event(x_home[b])                 # step i - NB's volume has left x_stage[b]
+            rec.copy_x(x_stage[b])
+            x_staged[b].record(comp)
+            rec.get_async(res[b])
+            step_done[b].record(comp)
             with torch.cuda.stream(d2h_stream):
-                d2h_stream.wait_event(x_staged[cur])
-                x_host[cur].copy_(x_stage[cur], non_blocking=True)
-                x_home[cur].record(d2h_stream)
-            if i >= 1:
-                step_done[nxt].synchronize()               # step i - 1's results are on the host
-                x_home[nxt].synchronize()
-                fits.append(float(res[nxt][0]))
-                vol_sums.append(float(x_host[nxt][0, :: 4096].sum()))
-        step_done[(n - 1) % 2].synchronize()
-        x_home[(n - 1) % 2].synchronize()
-        fits.append(float(res[(n - 1) % 2][0]))
-        vol_sums.append(float(x_host[(n - 1) % 2][0, :: 4096].sum()))
+                d2h_stream.wait_event(x_staged[b])
+                x_host[b].copy_(x_stage[b], non_blocking=True)
+                x_home[b].record(d2h_stream)
+            if i >= NB - 1:
+                collect(i - (NB - 1))
+        for j in range(max(0, n - (NB - 1)), n):
+            collect(j)
         return fits, vol_sums
 
     e2e_run(3)
@@ -761,10 +771,10 @@ def run_ours(args):
            "h2d_bytes_per_step": int(y_pin.numel() * 4),
            "d2h_bytes_per_step": int(8 * nfr * (ncam + 1) + 4 * nfr * plan.nvox),
            "steps": args.e2e_steps,
-           "path": "pinned host y -> device copy (its own stream, double buffered, overlapping the previous step), "
+           "path": "pinned host y -> device copy (its own stream, three buffers, issued two steps ahead), "
                    "lt_recon_set_data, lt_recon_iterate(1), lt_recon_get(x) into a device staging buffer, "
                    "volume -> pinned host memory on a second copy stream (the two directions overlap), "
-                   "lt_recon_get_async(data fit, gains) into pinned memory; both read on the host one step later"}
+                   "lt_recon_get_async(data fit, gains) into pinned memory; both read on the host two steps later"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -327,11 +327,14 @@ LT_API lt_status lt_recon_get(lt_recon* rec, float* x, double* gains, double* da
                               void* stream);
 
 /* The same data fit and gains without synchronising: enqueues on the stream
- * a device reduction and a copy into host_out = [data_fit[F], gains[F][n_cams]]
+ * a device reduction into host_out = [data_fit[F], gains[F][n_cams]]
  * (F + F * n_cams doubles), valid once the stream has passed this point (an
- * event or a synchronise).  host_out should be page-locked memory for the
- * copy to overlap other work; it must stay alive until then.  For pipelined
- * use: read step i's result while step i + 1 runs. */
+ * event or a synchronise).  Page-locked host_out (cudaHostAlloc, or a pinned
+ * torch tensor) is written by the reduction kernel itself through its
+ * device mapping, so nothing on the stream waits for a copy engine; other
+ * memory is filled by a copy after the reduction.  host_out must stay
+ * alive until then.  For pipelined use: read step i's result while step
+ * i + 1 runs. */
 LT_API lt_status lt_recon_get_async(lt_recon* rec, double* host_out, void* stream);
 
 /* Replaces the measurements (and weights, if w is not NULL; the majoriser D

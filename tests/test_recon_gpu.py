@@ -158,3 +158,9 @@ def test_async_result_read_matches_synchronous_read():
     assert np.array_equal(out[1:].numpy(), np.ravel(gains))
     with pytest.raises(ValueError):
         rec.get_async(torch.empty(3, dtype=torch.float64))   # not page-locked
+    # the C entry point itself takes pageable memory too (filled by a copy
+    # instead of the kernel's write through the device mapping)
+    pageable = np.zeros(len(cams) + 1)
+    lt.lt_recon_get_async(rec.handle, pageable.ctypes.data, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(pageable, out.numpy())
