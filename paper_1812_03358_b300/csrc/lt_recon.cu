@@ -563,10 +563,12 @@ static lt_status load_data(lt_recon* R, const float* y, const float* w, bool new
     s = plan_adjoint(P, R->r, R->D, st);
     if (s != LT_OK) return s;
   }
-  for (int c = 0; c < R->C; ++c)
-    dot_partials<<<dim3(R->nb, R->F), RED_THREADS, 0, st>>>(R->y, R->y, R->w, P->cams[c].offset,
-                                                                 P->cams[c].M, R->M, R->C, c, R->part, 1.0);
-  finalize_dots<<<1, 256, 0, st>>>(R->part, R->ywy, R->F * R->C, R->nb);
+  if (R->prm.estimate_gains && R->C > 1) {   // y^T W y of each camera: the gains' denominators (Table V, step 1b)
+    for (int c = 0; c < R->C; ++c)
+      dot_partials<<<dim3(R->nb, R->F), RED_THREADS, 0, st>>>(R->y, R->y, R->w, P->cams[c].offset,
+                                                                   P->cams[c].M, R->M, R->C, c, R->part, 1.0);
+    finalize_dots<<<1, 256, 0, st>>>(R->part, R->ywy, R->F * R->C, R->nb);
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LT_OK : cuda_error(e, "loading measurements");
 }
