@@ -430,8 +430,9 @@ __global__ void mul_kernel(float* out, const float* a, const float* b, long long
 
 // Device-to-device copy done by the SMs.  A copy-engine transfer on the
 // solver's stream would queue behind host transfers that a streaming caller
-// keeps in flight on its own copy streams (measured: 45 us per 4 MB copy
-// of measurements instead of about 2 us).
+// keeps in flight on its own copy streams: in such a loop the engine copies
+// of the measurements, the volume and the result cost the solver's stream
+// about 0.1 ms per step.
 __global__ void copy_kernel(float* __restrict__ dst, const float* __restrict__ src, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
